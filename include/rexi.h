@@ -1,0 +1,224 @@
+/*
+ * rexi.h -- C ABI of the GB300 REXI engine.
+ *
+ * The engine advances the semi-discrete Schroedinger equation (Eq. (1) of
+ * Rittich & Speck, "Time-parallel simulation of the Schroedinger equation",
+ * arXiv:1912.03312) by rational approximation of the exponential (Sec. 3.1):
+ *
+ *     psi(t + tau) ~= alpha_0 psi + sum_{k=1}^{K} alpha_k (tau H - z_k I)^{-1} psi,     (Eq. (5))
+ *
+ * with H = -(hbar^2/2m) Lap_h + diag(V) on a periodic, second-order
+ * finite-difference grid (the B = I discretisation of Sec. 5, scaled by hbar),
+ * poles/weights from the Faber-Caratheodory-Fejer construction (Sec. 3.2,
+ * Algorithms 1 and 2, conformal map Eq. (9)), and the accuracy condition
+ * Eq. (10) met by substeps.  Each pole's system is an independent GMRES solve;
+ * all K solves (and, in the batched call, all problems) run in one persistent
+ * CUDA launch.
+ *
+ * Conventions for every call:
+ *   - Status: 0 = REXI_OK, negative = error, positive = warning.  No call
+ *     aborts or throws.  rexi_status_string() names each code.
+ *   - Complex vectors are interleaved (re, im) IEEE doubles ("c128"), the
+ *     storage of a torch.complex128 tensor.  Grids are stored x fastest:
+ *     index = ix + nx * (iy + ny * iz).
+ *   - "device" pointers are CUDA global-memory pointers on the plan's device;
+ *     "host" pointers are ordinary CPU memory.  The caller owns every buffer
+ *     it passes; the plan owns its own workspace.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Calls on one plan must not overlap in time (the workspace is shared).
+ */
+#ifndef REXI_H
+#define REXI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define REXI_OK          0
+#define REXI_EINVAL     -1   /* bad argument (size, pointer, NaN/Inf in V, ...) */
+#define REXI_ENOMEM     -2   /* device or host allocation failed                 */
+#define REXI_ECUDA      -3   /* a CUDA runtime call failed (no device, launch...) */
+#define REXI_ENOCONV    -4   /* a pole's GMRES hit max_iters above tolerance     */
+#define REXI_ETIMEOUT   -5   /* a bounded device-side wait gave up               */
+#define REXI_EPLAN      -6   /* FCF construction failed (root count, spurious pole,
+                                non-unique CF approximant)                        */
+#define REXI_WACCURACY   1   /* Eq. (10) violated: tau*W/hbar > R1 (only with
+                                allow_substeps = 0, or a potential outside the
+                                plan's spectral enclosure)                         */
+
+/* ---- precision forms ----------------------------------------------------- */
+#define REXI_FP64   0   /* Krylov basis, matvecs and orthogonalisation in c128   */
+#define REXI_MIXED  1   /* Krylov basis/matvecs/orthogonalisation in c64; FP64 for
+                           the residual at every restart (iterative refinement),
+                           the Hessenberg least squares and the pole sum          */
+
+#define REXI_MAX_POLES   256
+#define REXI_MAX_RESTART 32
+
+/* Periodic grid: N_d points on [lo_d, hi_d), h_d = (hi_d - lo_d) / N_d,
+ * points x_j = lo_d + j h_d.  ndim in {1, 2, 3}; unused n[] entries ignored. */
+typedef struct {
+    int    ndim;
+    int    n[3];
+    double lo[3], hi[3];
+    double hbar, mass;
+} rexi_grid;
+
+typedef struct {
+    int    precision;      /* REXI_FP64 or REXI_MIXED (default REXI_MIXED)                */
+    int    restart_m;      /* GMRES restart length, 1..REXI_MAX_RESTART (default 30)      */
+    int    max_iters;      /* Arnoldi iterations per pole solve before ENOCONV (default 2000) */
+    double tol;            /* per-pole stop: ||b - A x|| <= tol ||b||; 0 = choose from the
+                              pole-sum amplification (see rexi_plan_info.tol)              */
+    double inner_tol;      /* REXI_MIXED: relative residual reduction at which an FP32
+                              cycle ends and an FP64 residual is formed (default 1e-5)     */
+    double R1;             /* half-length of the approximation interval i[-R1, R1] of
+                              Eq. (9); 0 = the largest R1 with 2 sigma_{K+1} <= eps_target */
+    double eps_target;     /* approximation error target for the default R1 (default 1e-9,
+                              the level of Table 1)                                         */
+    int    allow_substeps; /* 1 (default): n_sub = ceil(dt W / (hbar R1)) substeps so that
+                              Eq. (10) holds; 0: a single rational step, REXI_WACCURACY if
+                              Eq. (10) fails                                                 */
+    double stabilize_eps;  /* Sec. 3.4: scale every beta_j by (1 - eps); 0 = off (default,
+                              as in the paper)                                              */
+    int    want_backward;  /* allocate the adjoint workspace at create time (default 0:
+                              allocated by the first rexi_step_backward call)               */
+    int    device;         /* CUDA device ordinal; -1 = current device (default)          */
+} rexi_options;
+
+/* What a plan computed (host copy, filled by rexi_plan_info). */
+typedef struct {
+    int    K, n_sub, n_total, restart_m, precision;
+    double dt, tau;        /* user step and substep tau = dt / n_sub                       */
+    double R1;             /* approximation interval half-length                           */
+    double sigma_K1;       /* sigma_{K+1} of Theorem 1 (CF error; the FCF error is <= ~2x)  */
+    double E_min, E_max;   /* spectral enclosure of H                                      */
+    double c, W;           /* centre and half-width of the enclosure                       */
+    double amplification;  /* A = max_{w in i[-R1,R1]} sum |beta_j| / |w - sigma_j|         */
+    double tol;            /* per-pole relative residual target in use                     */
+    double min_re_sigma;   /* distance of the nearest pole from the approximation interval */
+} rexi_plan_info;
+
+/* Per-call statistics (host).  iters/resid are per pole, summed over substeps
+ * (iters) and the maximum over substeps (resid, true relative residual). */
+typedef struct {
+    int    status;                    /* same as the call's return value                */
+    int    n_sub;
+    int    max_iters_seen;            /* largest per-pole Arnoldi count in one substep   */
+    int    total_iters;               /* sum over poles and substeps                     */
+    int    total_cycles;              /* restart cycles (FP64 residual evaluations)      */
+    int    iters[REXI_MAX_POLES];
+    int    cycles[REXI_MAX_POLES];
+    int    iters_sq[REXI_MAX_POLES];  /* sum over restart cycles of (cycle length)^2       */
+    double resid[REXI_MAX_POLES];
+} rexi_stats;
+
+typedef struct rexi_plan rexi_plan;   /* opaque, owned by the library */
+
+/* Fill *opt with the defaults documented above. */
+int rexi_options_default(rexi_options* opt);
+
+/* Build a plan for one problem (Sec. 3.1-3.3).
+ *   g   : host, the grid.
+ *   V   : host, n = prod(n[d]) doubles, the potential, x fastest.  Copied.
+ *   dt  : user time step (> 0).
+ *   K   : number of poles, 1..REXI_MAX_POLES.
+ *   opt : host, NULL = defaults.
+ * Computes the spectral enclosure [E_min, E_max] of H (min V; max V plus the
+ * exact bound (hbar^2/2m) sum_d 4/h_d^2 of the periodic Laplacian), centres the
+ * exponential at c, picks R1 and n_sub (Eq. (10)), builds the FCF poles and
+ * weights in double-double arithmetic (Algorithms 1-2), maps them to
+ * z_k = tau c + i hbar sigma_k, alpha_k = i hbar beta_k e^{-i tau c / hbar},
+ * alpha_0 = 0, and allocates all device workspace (no call below allocates,
+ * except the first rexi_step_backward when want_backward = 0).
+ * Returns REXI_OK, REXI_WACCURACY (plan usable), or an error (then *out = NULL). */
+int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V,
+                     double dt, int K, const rexi_options* opt);
+
+void rexi_plan_destroy(rexi_plan* plan);
+
+/* Host copy of the plan's parameters. */
+int rexi_plan_get_info(const rexi_plan* plan, rexi_plan_info* info);
+
+/* Per-substep poles and weights of Eq. (5): z[2K], alpha[2K] interleaved
+ * (re, im), alpha0[2], n_sub.  Any output pointer may be NULL. */
+int rexi_plan_poles(const rexi_plan* plan, double* z, double* alpha, double* alpha0, int* n_sub);
+
+/* FCF poles/weights of exp on i[-R1, R1] (Algorithm 2 output, before the
+ * mapping to Eq. (5)): sigma[2K], beta[2K] interleaved.  Host only. */
+int rexi_plan_fcf(const rexi_plan* plan, double* sigma, double* beta);
+
+/* Standalone FCF construction (Algorithms 1-2 in double-double), host only:
+ * sigma[2K], beta[2K] interleaved; sigma_K1 (Theorem 1), min_re_sigma and
+ * amplification may be NULL.  R1 = 0 picks the default radius for eps_target
+ * (eps_target <= 0 means 1e-9); *R1_used (may be NULL) receives it. */
+int rexi_fcf(int K, double R1, double eps_target, double* sigma, double* beta,
+             double* R1_used, double* sigma_K1, double* min_re_sigma, double* amplification);
+
+/* Replace the potential (host or device pointer, n doubles), keeping the
+ * plan's c, W, poles and n_sub (for a learnable V).  Returns REXI_WACCURACY if
+ * the new potential's enclosure leaves [E_min, E_max] (Eq. (10) may fail). */
+int rexi_plan_set_potential(rexi_plan* plan, const double* V, int V_on_device, void* stream);
+
+/* One user step dt (n_sub rational evaluations of Eq. (5)) on the device.
+ *   psi_in, psi_out : device c128[n]; psi_in == psi_out allowed.
+ *   st              : host, may be NULL.
+ * With st == NULL the call only enqueues work on stream and returns launch
+ * errors; convergence failures are then reported by rexi_plan_last_status().
+ * With st != NULL the call synchronises the stream and returns REXI_ENOCONV /
+ * REXI_ETIMEOUT when a pole failed. */
+int rexi_step(rexi_plan* plan, const void* psi_in, void* psi_out, void* stream, rexi_stats* st);
+
+/* Same as rexi_step with host buffers (c128[n] each): copies in, steps,
+ * copies out and synchronises. */
+int rexi_step_host(rexi_plan* plan, const double* psi_in, double* psi_out, void* stream,
+                   rexi_stats* st);
+
+/* B independent problems (each with its own plan, grid, K and n_sub) in one
+ * persistent launch: all problems x all poles share the GPU.  All plans must
+ * be on the same device and have the same precision and restart length.
+ * psi_in[b], psi_out[b] : device c128 of plan b's size.  st: B entries or NULL. */
+int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
+                      void* const* psi_out, void* stream, rexi_stats* st);
+
+/* Vector-Jacobian product of one user step psi_{n+1} = S(V) psi_n
+ * (the step is linear in psi; S^H = sum conj(alpha_k) (tau H - conj(z_k) I)^{-1}
+ * because H is real symmetric).
+ *   psi_n    : device c128[n], the state the forward step started from.
+ *   grad_out : device c128[n], G = 2 dL/dconj(psi_{n+1}) (torch.autograd's
+ *              convention for a real loss L).
+ *   grad_in  : device c128[n], receives 2 dL/dconj(psi_n) = S^H G.
+ *   dLdV     : device double[n], ACCUMULATED: += dL/dV_i =
+ *              -tau sum_substeps Re sum_k alpha_k conj(Y_{k,i}) X_{k,i},
+ *              X_k = (tau H - z_k)^{-1} psi_s, Y_k = (tau H - conj(z_k))^{-1} G_s.
+ *   grad_in may equal grad_out.  Intermediate substep states are recomputed. */
+int rexi_step_backward(rexi_plan* plan, const void* psi_n, const void* grad_out, void* grad_in,
+                       double* dLdV, void* stream, rexi_stats* st);
+
+/* --- single stages of the hot path, for parity checks and profiling ------- */
+
+/* K1: w_k = (tau H - z_k I) v_k for every pole k, complex FP64.
+ * v, w : device c128[K][n] (pole-major).  One substep's tau. */
+int rexi_apply_poles(rexi_plan* plan, const void* v, void* w, void* stream);
+
+/* K1-K5: x_k = (tau H - z_k I)^{-1} b for every pole, by the plan's GMRES form
+ * (precision, restart, tolerance).  b: device c128[n]; x: device c128[K][n]. */
+int rexi_solve_poles(rexi_plan* plan, const void* b, void* x, void* stream, rexi_stats* st);
+
+/* K4b: out = alpha_0 psi + sum_k alpha_k x_k in FP64.  psi, out: device
+ * c128[n]; x: device c128[K][n]. */
+int rexi_pole_sum(rexi_plan* plan, const void* psi, const void* x, void* out, void* stream);
+
+/* Status of the last call on the plan (synchronises the plan's last stream). */
+int rexi_plan_last_status(rexi_plan* plan);
+
+/* Number of CUDA kernel launches issued by the last call on the plan. */
+int rexi_plan_last_launches(const rexi_plan* plan);
+
+const char* rexi_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REXI_H */

@@ -1,0 +1,826 @@
+// C ABI of the REXI engine (declared in include/rexi.h): plan construction on
+// the host (Sec. 3.1-3.3 of Rittich & Speck, arXiv:1912.03312), device
+// workspace, and the launches of the persistent engine.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/rexi.h"
+#include "engine.h"
+#include "fcf.h"
+
+using rexi::EngineArgs;
+using rexi::IOArgs;
+using rexi::ItemDesc;
+using rexi::ItemState;
+using rexi::ItemStats;
+using rexi::ProblemDesc;
+typedef std::complex<double> cd;
+
+namespace {
+
+constexpr unsigned long long kTimeoutNs = 4000000000ull;   // 4 s per barrier wait
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// One descriptor set: a problem descriptor and its items on the device.
+struct DescSet {
+    ProblemDesc* d_prob = nullptr;
+    ItemDesc* d_items = nullptr;
+    int nitems = 0;
+    int ntiles_items = 0;
+};
+
+}  // namespace
+
+struct rexi_plan {
+    int device = 0;
+    rexi_grid grid{};
+    rexi_options opt{};
+    int n = 0, K = 0, m = 30, n_sub = 1;
+    int dims[3] = {1, 1, 1};
+    double h[3] = {1, 1, 1};
+    double dt = 0, tau = 0, R1 = 0, E_min = 0, E_max = 0, c = 0, W = 0, tol = 0;
+    bool fp32 = true;
+    rexi::FcfResult fcf;
+    std::vector<cd> z, alpha;
+    cd alpha0 = 0.0;
+    double a[3] = {0, 0, 0};
+    std::vector<double> V;                       // host copy of the potential
+    int ntiles = 0, pv = 32;
+    int warn = REXI_OK;
+    // device memory
+    std::vector<void*> allocs;
+    double* d_diag = nullptr;
+    float* d_diagf = nullptr;
+    double2* d_alpha = nullptr;
+    double2* d_tmp0 = nullptr;
+    double2* d_tmp1 = nullptr;
+    double2* d_hin = nullptr;                    // staging for rexi_step_host
+    double2* d_hout = nullptr;
+    unsigned* d_bar = nullptr;
+    int* d_err = nullptr;
+    int nit_cap = 0;                             // items with workspace (K or 2K)
+    double2* d_x = nullptr;
+    void* d_basis = nullptr;
+    ItemState* d_st = nullptr;
+    ItemStats* d_stats = nullptr;
+    double2* d_part1 = nullptr;
+    double2* d_part2 = nullptr;
+    double* d_partn = nullptr;
+    double2* d_ckpt = nullptr;
+    DescSet fwd, one, bwd;
+    ProblemDesc hprob{};                         // forward problem descriptor (host copy)
+    int last_status = REXI_OK;
+    int last_launches = 0;
+    cudaStream_t last_stream = nullptr;
+    bool has_backward = false;
+    int generation = 0;                          // bumped when the item workspace moves
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? REXI_ENOMEM : REXI_ECUDA; }
+
+template <typename T>
+int dalloc(rexi_plan* p, T** out, size_t count) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(count * sizeof(T), 16));
+    if (e != cudaSuccess) { *out = nullptr; return cuda_fail(e); }
+    p->allocs.push_back(ptr);
+    *out = (T*)ptr;
+    return REXI_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite_all(const double* v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+// diag_i = tau (V_i - c) - 2 sum_d a_d (the centred diagonal of tau H) in FP64 and FP32.
+int upload_diag(rexi_plan* p, cudaStream_t stream, bool sync) {
+    std::vector<double> d(p->n);
+    std::vector<float> f(p->n);
+    const double sa = 2.0 * (p->a[0] + p->a[1] + p->a[2]);
+    for (int i = 0; i < p->n; ++i) {
+        d[i] = p->tau * (p->V[i] - p->c) - sa;
+        f[i] = (float)d[i];
+    }
+    cudaError_t e = cudaMemcpyAsync(p->d_diag, d.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_diagf, f.data(), sizeof(float) * p->n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && sync) e = cudaStreamSynchronize(stream);
+    return e == cudaSuccess ? REXI_OK : cuda_fail(e);
+}
+
+// Allocate the solver workspace for `nit` items and build descriptor sets.
+int alloc_items(rexi_plan* p, int nit) {
+    const size_t n = (size_t)p->n;
+    const size_t esz = p->fp32 ? sizeof(float2) : sizeof(double2);
+    int st;
+    double2* x;
+    void* basis;
+    ItemState* sts;
+    ItemStats* stats;
+    double2 *p1, *p2;
+    double* pn;
+    if ((st = dalloc(p, &x, (size_t)nit * n))) return st;
+    {
+        void* ptr = nullptr;
+        cudaError_t e = cudaMalloc(&ptr, (size_t)nit * (p->m + 1) * n * esz);
+        if (e != cudaSuccess) return cuda_fail(e);
+        p->allocs.push_back(ptr);
+        basis = ptr;
+    }
+    if ((st = dalloc(p, &sts, (size_t)nit))) return st;
+    if ((st = dalloc(p, &stats, (size_t)nit))) return st;
+    if ((st = dalloc(p, &p1, (size_t)nit * p->ntiles * p->pv))) return st;
+    if ((st = dalloc(p, &p2, (size_t)nit * p->ntiles * p->pv))) return st;
+    if ((st = dalloc(p, &pn, (size_t)nit * p->ntiles))) return st;
+    p->d_x = x;
+    p->d_basis = basis;
+    p->d_st = sts;
+    p->d_stats = stats;
+    p->d_part1 = p1;
+    p->d_part2 = p2;
+    p->d_partn = pn;
+    p->nit_cap = nit;
+    p->generation++;
+    return REXI_OK;
+}
+
+ItemDesc make_item(const rexi_plan* p, int idx, int pole, bool adjoint, int problem, int tile_base) {
+    ItemDesc it{};
+    it.problem = problem;
+    it.pole = pole;
+    it.adjoint = adjoint ? 1 : 0;
+    it.tile_off = idx * p->ntiles;               // offset inside this plan's partial buffers
+    (void)tile_base;
+    it.n = p->n;
+    it.ntiles = p->ntiles;
+    const cd s = p->z[pole] - p->tau * p->c;    // centred shift: A = tau (H - c) - s
+    const cd sh = adjoint ? std::conj(s) : s;
+    it.shift = make_double2(sh.real(), sh.imag());
+    it.shiftf = make_float2((float)sh.real(), (float)sh.imag());
+    const size_t esz = p->fp32 ? sizeof(float2) : sizeof(double2);
+    it.x = p->d_x + (size_t)idx * p->n;
+    it.basis = (char*)p->d_basis + (size_t)idx * (p->m + 1) * p->n * esz;
+    it.st = p->d_st + idx;
+    it.stats = p->d_stats + idx;
+    it.part1 = p->d_part1;
+    it.part2 = p->d_part2;
+    it.partn = p->d_partn;
+    return it;
+}
+
+ProblemDesc make_problem(const rexi_plan* p, int nsub, int item0, int nitems) {
+    ProblemDesc pr{};
+    pr.n = p->n;
+    pr.nx = p->dims[0];
+    pr.ny = p->dims[1];
+    pr.nz = p->dims[2];
+    pr.ntiles = p->ntiles;
+    pr.K = p->K;
+    pr.item0 = item0;
+    pr.nitems = nitems;
+    pr.nsub = nsub;
+    for (int d = 0; d < 3; ++d) {
+        pr.a[d] = p->a[d];
+        pr.af[d] = (float)p->a[d];
+    }
+    pr.tau = p->tau;
+    pr.alpha0 = make_double2(p->alpha0.real(), p->alpha0.imag());
+    pr.alpha = p->d_alpha;
+    pr.diag = p->d_diag;
+    pr.diagf = p->d_diagf;
+    pr.tmp0 = p->d_tmp0;
+    pr.tmp1 = p->d_tmp1;
+    pr.ckpt = p->d_ckpt;
+    return pr;
+}
+
+int upload_set(rexi_plan* p, DescSet* set, const ProblemDesc& pr, const std::vector<ItemDesc>& items) {
+    int st;
+    if (!set->d_prob && (st = dalloc(p, &set->d_prob, 1))) return st;
+    if (set->nitems < (int)items.size() || !set->d_items) {
+        if ((st = dalloc(p, &set->d_items, items.size()))) return st;
+    }
+    set->nitems = (int)items.size();
+    cudaError_t e = cudaMemcpy(set->d_prob, &pr, sizeof(pr), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(set->d_items, items.data(), sizeof(ItemDesc) * items.size(), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? REXI_OK : cuda_fail(e);
+}
+
+int build_sets(rexi_plan* p) {
+    std::vector<ItemDesc> f;
+    for (int k = 0; k < p->K; ++k) f.push_back(make_item(p, k, k, false, 0, 0));
+    p->hprob = make_problem(p, p->n_sub, 0, p->K);
+    int st = upload_set(p, &p->fwd, p->hprob, f);
+    if (st) return st;
+    st = upload_set(p, &p->one, make_problem(p, 1, 0, p->K), f);
+    if (st) return st;
+    if (p->nit_cap >= 2 * p->K) {
+        std::vector<ItemDesc> b;
+        for (int k = 0; k < p->K; ++k) b.push_back(make_item(p, k, k, false, 0, 0));
+        for (int k = 0; k < p->K; ++k) b.push_back(make_item(p, p->K + k, k, true, 0, 0));
+        st = upload_set(p, &p->bwd, make_problem(p, p->n_sub, 0, 2 * p->K), b);
+        if (st) return st;
+        p->has_backward = true;
+    }
+    return REXI_OK;
+}
+
+int ensure_backward(rexi_plan* p) {
+    if (p->has_backward) return REXI_OK;
+    // re-allocate the item workspace for 2K items and the substep checkpoints
+    int st = alloc_items(p, 2 * p->K);
+    if (st) return st;
+    if ((st = dalloc(p, &p->d_ckpt, (size_t)std::max(1, p->n_sub) * p->n))) return st;
+    return build_sets(p);
+}
+
+EngineArgs base_args(const rexi_plan* p, int mode, const DescSet& set, int nproblems, int max_sub) {
+    EngineArgs A{};
+    A.mode = mode;
+    A.nproblems = nproblems;
+    A.nitems = set.nitems;
+    A.m = p->m;
+    A.max_iters = p->opt.max_iters;
+    A.max_sub = max_sub;
+    A.pv = p->pv;
+    A.tol = p->tol;
+    A.inner_tol = p->fp32 ? p->opt.inner_tol : 0.0;
+    A.timeout_ns = kTimeoutNs;
+    A.prob = set.d_prob;
+    A.item = set.d_items;
+    A.bar = p->d_bar;
+    A.err = p->d_err;
+    return A;
+}
+
+// Largest co-resident grid of the persistent kernel (cooperative launch limit).
+int max_grid_cached(bool fp32, size_t smem, int device) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<int, size_t>, int>> cache;
+    const std::pair<int, size_t> key(device * 2 + (fp32 ? 1 : 0), smem);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto& c : cache)
+            if (c.first == key) return c.second;
+    }
+    const int g = rexi::engine_max_grid(fp32, smem, device);
+    if (g > 0) {
+        std::lock_guard<std::mutex> lk(mu);
+        cache.push_back(std::make_pair(key, g));
+    }
+    return g;
+}
+
+int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(p->d_bar, 0, 2 * sizeof(unsigned), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stats, 0, sizeof(ItemStats) * A.nitems, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const size_t smem = rexi::engine_smem_bytes(A.nitems);
+    const int maxg = max_grid_cached(p->fp32, smem, p->device);
+    if (maxg <= 0) return REXI_ECUDA;
+    const int grid = std::max(1, std::min(maxg, total_tiles));
+    e = rexi::launch_engine(p->fp32, A, io, grid, smem, stream);
+    p->last_stream = stream;
+    p->last_launches = 1;
+    return e == cudaSuccess ? REXI_OK : cuda_fail(e);
+}
+
+// Read back the error word and the per-item statistics (synchronises).
+int collect(rexi_plan* p, cudaStream_t stream, int nitems, int item_offset, int poles, rexi_stats* st,
+            int n_sub) {
+    int err = 0;
+    std::vector<ItemStats> s(nitems);
+    cudaError_t e = cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s.data(), p->d_stats, sizeof(ItemStats) * nitems, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int status = err != 0 ? err : REXI_OK;
+    bool failed = false;
+    for (const ItemStats& x : s) failed = failed || x.failed;
+    if (status == REXI_OK && failed) status = REXI_ENOCONV;
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->n_sub = n_sub;
+        for (int k = 0; k < poles && k < REXI_MAX_POLES; ++k) {
+            const ItemStats& x = s[item_offset + k];
+            st->iters[k] = x.iters;
+            st->cycles[k] = x.cycles;
+            st->iters_sq[k] = x.iters_sq;
+            st->resid[k] = x.resid;
+        }
+        for (const ItemStats& x : s) {
+            st->total_iters += x.iters;
+            st->total_cycles += x.cycles;
+            st->max_iters_seen = std::max(st->max_iters_seen, x.max_sub_iters);
+        }
+        st->status = status;
+    }
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rexi_status_string(int s) {
+    switch (s) {
+        case REXI_OK: return "REXI_OK";
+        case REXI_EINVAL: return "REXI_EINVAL: invalid argument";
+        case REXI_ENOMEM: return "REXI_ENOMEM: allocation failed";
+        case REXI_ECUDA: return "REXI_ECUDA: CUDA runtime error";
+        case REXI_ENOCONV: return "REXI_ENOCONV: a pole solve did not converge";
+        case REXI_ETIMEOUT: return "REXI_ETIMEOUT: bounded device wait expired";
+        case REXI_EPLAN: return "REXI_EPLAN: FCF construction failed";
+        case REXI_WACCURACY: return "REXI_WACCURACY: accuracy condition (Eq. (10)) violated";
+        default: return "unknown status";
+    }
+}
+
+int rexi_options_default(rexi_options* o) {
+    if (!o) return REXI_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = REXI_MIXED;
+    o->restart_m = 30;
+    o->max_iters = 2000;
+    o->tol = 0.0;
+    o->inner_tol = 1e-5;
+    o->R1 = 0.0;
+    o->eps_target = 1e-9;
+    o->allow_substeps = 1;
+    o->stabilize_eps = 0.0;
+    o->want_backward = 0;
+    o->device = -1;
+    return REXI_OK;
+}
+
+int rexi_fcf(int K, double R1, double eps_target, double* sigma, double* beta, double* R1_used,
+             double* sigma_K1, double* min_re_sigma, double* amplification) {
+    if (K < 1 || K > REXI_MAX_POLES || !(R1 >= 0.0) || !std::isfinite(R1)) return REXI_EINVAL;
+    if (!(eps_target > 0.0)) eps_target = 1e-9;
+    const double R = R1 > 0.0 ? R1 : rexi::fcf_default_R1_cached(K, eps_target);
+    rexi::FcfResult r;
+    const int st = rexi::fcf_cached(K, R, &r);
+    if (R1_used) *R1_used = R;
+    if (st != 0) return st == -1 ? REXI_EINVAL : REXI_EPLAN;
+    for (int k = 0; k < K; ++k) {
+        if (sigma) { sigma[2 * k] = r.sigma[k].real(); sigma[2 * k + 1] = r.sigma[k].imag(); }
+        if (beta) { beta[2 * k] = r.beta[k].real(); beta[2 * k + 1] = r.beta[k].imag(); }
+    }
+    if (sigma_K1) *sigma_K1 = r.sigma_K1;
+    if (min_re_sigma) *min_re_sigma = r.min_re_sigma;
+    if (amplification) *amplification = r.amplification;
+    return REXI_OK;
+}
+
+int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, double dt, int K,
+                     const rexi_options* opt_in) {
+    if (!out) return REXI_EINVAL;
+    *out = nullptr;
+    if (!g || !V || !(dt > 0.0) || !std::isfinite(dt) || K < 1 || K > REXI_MAX_POLES) return REXI_EINVAL;
+    if (g->ndim < 1 || g->ndim > 3 || !(g->hbar > 0.0) || !(g->mass > 0.0)) return REXI_EINVAL;
+    rexi_options opt;
+    if (opt_in) opt = *opt_in; else rexi_options_default(&opt);
+    if (opt.precision != REXI_FP64 && opt.precision != REXI_MIXED) return REXI_EINVAL;
+    if (opt.restart_m < 1 || opt.restart_m > REXI_MAX_RESTART || opt.max_iters < 1) return REXI_EINVAL;
+    if (!(opt.tol >= 0.0) || !(opt.R1 >= 0.0) || !(opt.inner_tol >= 0.0) || !(opt.stabilize_eps >= 0.0) ||
+        !(opt.stabilize_eps < 1.0))
+        return REXI_EINVAL;
+    long long n = 1;
+    int dims[3] = {1, 1, 1};
+    double h[3] = {1.0, 1.0, 1.0};
+    for (int d = 0; d < g->ndim; ++d) {
+        if (g->n[d] < 1 || !(g->hi[d] > g->lo[d]) || !std::isfinite(g->hi[d] - g->lo[d])) return REXI_EINVAL;
+        dims[d] = g->n[d];
+        h[d] = (g->hi[d] - g->lo[d]) / g->n[d];
+        n *= g->n[d];
+    }
+    if (n > (1ll << 30)) return REXI_EINVAL;
+    if (!finite_all(V, (size_t)n)) return REXI_EINVAL;
+
+    rexi_plan* p = new (std::nothrow) rexi_plan();
+    if (!p) return REXI_ENOMEM;
+    p->grid = *g;
+    p->opt = opt;
+    p->n = (int)n;
+    p->K = K;
+    p->m = opt.restart_m;
+    p->dt = dt;
+    p->fp32 = opt.precision == REXI_MIXED;
+    for (int d = 0; d < 3; ++d) { p->dims[d] = dims[d]; p->h[d] = h[d]; }
+    p->V.assign(V, V + n);
+
+    // spectral enclosure of H (exact bound of the periodic Laplacian plus diag(V))
+    double vmin = V[0], vmax = V[0];
+    for (long long i = 1; i < n; ++i) { vmin = std::min(vmin, V[i]); vmax = std::max(vmax, V[i]); }
+    double kin = 0.0;
+    for (int d = 0; d < g->ndim; ++d) kin += 4.0 / (h[d] * h[d]);
+    kin *= g->hbar * g->hbar / (2.0 * g->mass);
+    p->E_min = vmin;
+    p->E_max = vmax + kin;
+    p->c = 0.5 * (p->E_min + p->E_max);
+    p->W = 0.5 * (p->E_max - p->E_min);
+
+    // R1, FCF poles and weights (Algorithms 1-2), substeps (Eq. (10))
+    const double eps_t = opt.eps_target > 0.0 ? opt.eps_target : 1e-9;
+    p->R1 = opt.R1 > 0.0 ? opt.R1 : rexi::fcf_default_R1_cached(K, eps_t);
+    int fst = rexi::fcf_cached(K, p->R1, &p->fcf);
+    if (fst != 0) { delete p; return fst == -1 ? REXI_EINVAL : REXI_EPLAN; }
+    const double x = dt * p->W / (g->hbar * p->R1);
+    if (opt.allow_substeps) {
+        p->n_sub = std::max(1, (int)std::ceil(x - 1e-12 * std::max(1.0, x)));
+    } else {
+        p->n_sub = 1;
+        if (x > 1.0 + 1e-12) p->warn = REXI_WACCURACY;
+    }
+    p->tau = dt / p->n_sub;
+    p->z.resize(K);
+    p->alpha.resize(K);
+    const cd I(0.0, 1.0);
+    const cd phase = std::exp(-I * (p->tau * p->c / g->hbar));
+    for (int k = 0; k < K; ++k) {
+        const cd beta = p->fcf.beta[k] * (1.0 - opt.stabilize_eps);
+        p->z[k] = p->tau * p->c + I * g->hbar * p->fcf.sigma[k];
+        p->alpha[k] = I * g->hbar * beta * phase;
+    }
+    p->alpha0 = 0.0;
+    for (int d = 0; d < g->ndim; ++d) p->a[d] = -p->tau * g->hbar * g->hbar / (2.0 * g->mass * h[d] * h[d]);
+    p->tol = opt.tol > 0.0 ? opt.tol
+                           : std::max(2e-14, std::min(1e-10, 1e-6 / std::max(1.0, p->fcf.amplification)));
+    p->ntiles = (p->n + rexi::kTile - 1) / rexi::kTile;
+    p->pv = 32;
+
+    // device
+    int dev = opt.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) { delete p; return REXI_ECUDA; }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || dev >= ndev) { delete p; return REXI_ECUDA; }
+    p->device = dev;
+    DeviceGuard guard(dev);
+    int st;
+    auto fail = [&](int code) { rexi_plan_destroy(p); return code; };
+    if ((st = dalloc(p, &p->d_diag, n))) return fail(st);
+    if ((st = dalloc(p, &p->d_diagf, n))) return fail(st);
+    if ((st = dalloc(p, &p->d_alpha, K))) return fail(st);
+    if ((st = dalloc(p, &p->d_tmp0, n))) return fail(st);
+    if ((st = dalloc(p, &p->d_tmp1, n))) return fail(st);
+    if ((st = dalloc(p, &p->d_hin, n))) return fail(st);
+    if ((st = dalloc(p, &p->d_hout, n))) return fail(st);
+    if ((st = dalloc(p, &p->d_bar, 2))) return fail(st);
+    if ((st = dalloc(p, &p->d_err, 1))) return fail(st);
+    {
+        std::vector<double2> al(K);
+        for (int k = 0; k < K; ++k) al[k] = make_double2(p->alpha[k].real(), p->alpha[k].imag());
+        if (cudaMemcpy(p->d_alpha, al.data(), sizeof(double2) * K, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(REXI_ECUDA);
+    }
+    if ((st = upload_diag(p, 0, true))) return fail(st);
+    if (cudaMemset(p->d_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess) return fail(REXI_ECUDA);
+    if (cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return fail(REXI_ECUDA);
+    if (opt.want_backward) {
+        if ((st = alloc_items(p, 2 * K))) return fail(st);
+        if ((st = dalloc(p, &p->d_ckpt, (size_t)std::max(1, p->n_sub) * n))) return fail(st);
+    } else {
+        if ((st = alloc_items(p, K))) return fail(st);
+    }
+    if ((st = build_sets(p))) return fail(st);
+    *out = p;
+    return p->warn;
+}
+
+void rexi_plan_destroy(rexi_plan* p) {
+    if (!p) return;
+    DeviceGuard guard(p->device);
+    for (void* a : p->allocs) cudaFree(a);
+    delete p;
+}
+
+int rexi_plan_get_info(const rexi_plan* p, rexi_plan_info* info) {
+    if (!p || !info) return REXI_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->K = p->K;
+    info->n_sub = p->n_sub;
+    info->n_total = p->n;
+    info->restart_m = p->m;
+    info->precision = p->opt.precision;
+    info->dt = p->dt;
+    info->tau = p->tau;
+    info->R1 = p->R1;
+    info->sigma_K1 = p->fcf.sigma_K1;
+    info->E_min = p->E_min;
+    info->E_max = p->E_max;
+    info->c = p->c;
+    info->W = p->W;
+    info->amplification = p->fcf.amplification;
+    info->tol = p->tol;
+    info->min_re_sigma = p->fcf.min_re_sigma;
+    return REXI_OK;
+}
+
+int rexi_plan_poles(const rexi_plan* p, double* z, double* alpha, double* alpha0, int* n_sub) {
+    if (!p) return REXI_EINVAL;
+    for (int k = 0; k < p->K; ++k) {
+        if (z) { z[2 * k] = p->z[k].real(); z[2 * k + 1] = p->z[k].imag(); }
+        if (alpha) { alpha[2 * k] = p->alpha[k].real(); alpha[2 * k + 1] = p->alpha[k].imag(); }
+    }
+    if (alpha0) { alpha0[0] = p->alpha0.real(); alpha0[1] = p->alpha0.imag(); }
+    if (n_sub) *n_sub = p->n_sub;
+    return REXI_OK;
+}
+
+int rexi_plan_fcf(const rexi_plan* p, double* sigma, double* beta) {
+    if (!p) return REXI_EINVAL;
+    for (int k = 0; k < p->K; ++k) {
+        if (sigma) { sigma[2 * k] = p->fcf.sigma[k].real(); sigma[2 * k + 1] = p->fcf.sigma[k].imag(); }
+        if (beta) { beta[2 * k] = p->fcf.beta[k].real(); beta[2 * k + 1] = p->fcf.beta[k].imag(); }
+    }
+    return REXI_OK;
+}
+
+int rexi_plan_set_potential(rexi_plan* p, const double* V, int on_device, void* stream) {
+    if (!p || !V) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> v(p->n);
+    if (on_device) {
+        if (cudaMemcpyAsync(v.data(), V, sizeof(double) * p->n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return REXI_ECUDA;
+    } else {
+        std::memcpy(v.data(), V, sizeof(double) * p->n);
+    }
+    if (!finite_all(v.data(), v.size())) return REXI_EINVAL;
+    p->V.swap(v);
+    double vmin = p->V[0], vmax = p->V[0];
+    for (double x : p->V) { vmin = std::min(vmin, x); vmax = std::max(vmax, x); }
+    int st = upload_diag(p, s, true);
+    if (st) return st;
+    double lap = 0.0;
+    for (int d = 0; d < p->grid.ndim; ++d) lap += 4.0 / (p->h[d] * p->h[d]);
+    lap *= p->grid.hbar * p->grid.hbar / (2.0 * p->grid.mass);
+    const bool inside = vmin >= p->E_min - 1e-12 * std::fabs(p->E_min) && vmax + lap <= p->E_max + 1e-12 * std::fabs(p->E_max);
+    return inside ? REXI_OK : REXI_WACCURACY;
+}
+
+int rexi_step(rexi_plan* p, const void* psi_in, void* psi_out, void* stream, rexi_stats* st) {
+    if (!p || !psi_in || !psi_out) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    IOArgs io{};
+    io.in[0] = (const double2*)psi_in;
+    io.out[0] = (double2*)psi_out;
+    EngineArgs A = base_args(p, rexi::MODE_STEP, p->fwd, 1, p->n_sub);
+    int r = launch(p, A, io, p->K * p->ntiles, s);
+    if (r) return p->last_status = r;
+    if (!st) return p->last_status = REXI_OK;
+    return p->last_status = collect(p, s, p->K, 0, p->K, st, p->n_sub);
+}
+
+int rexi_step_host(rexi_plan* p, const double* psi_in, double* psi_out, void* stream, rexi_stats* st) {
+    if (!p || !psi_in || !psi_out) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double2) * p->n;
+    if (cudaMemcpyAsync(p->d_hin, psi_in, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return REXI_ECUDA;
+    int r = rexi_step(p, p->d_hin, p->d_hout, stream, st);
+    if (r < 0) return r;
+    if (cudaMemcpyAsync(psi_out, p->d_hout, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return REXI_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return REXI_ECUDA;
+    if (!st) return rexi_plan_last_status(p);
+    return r;
+}
+
+int rexi_solve_poles(rexi_plan* p, const void* b, void* x, void* stream, rexi_stats* st) {
+    if (!p || !b || !x) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    IOArgs io{};
+    io.in[0] = (const double2*)b;
+    EngineArgs A = base_args(p, rexi::MODE_SOLVE, p->one, 1, 1);
+    int r = launch(p, A, io, p->K * p->ntiles, s);
+    if (r) return p->last_status = r;
+    cudaError_t e = cudaMemcpyAsync(x, p->d_x, sizeof(double2) * (size_t)p->K * p->n, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return p->last_status = REXI_ECUDA;
+    p->last_launches = 1;
+    if (!st) return p->last_status = REXI_OK;
+    return p->last_status = collect(p, s, p->K, 0, p->K, st, 1);
+}
+
+int rexi_apply_poles(rexi_plan* p, const void* v, void* w, void* stream) {
+    if (!p || !v || !w) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    cudaError_t e = rexi::launch_apply(p->one.d_prob, p->one.d_items, p->K, (const double2*)v, (double2*)w, p->n,
+                                       (cudaStream_t)stream);
+    p->last_launches = 1;
+    p->last_stream = (cudaStream_t)stream;
+    return p->last_status = (e == cudaSuccess ? REXI_OK : REXI_ECUDA);
+}
+
+int rexi_pole_sum(rexi_plan* p, const void* psi, const void* x, void* out, void* stream) {
+    if (!p || !psi || !x || !out) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    cudaError_t e = rexi::launch_pole_sum(p->one.d_prob, (const double2*)psi, (const double2*)x, (double2*)out,
+                                          p->n, p->K, (cudaStream_t)stream);
+    p->last_launches = 1;
+    p->last_stream = (cudaStream_t)stream;
+    return p->last_status = (e == cudaSuccess ? REXI_OK : REXI_ECUDA);
+}
+
+int rexi_step_backward(rexi_plan* p, const void* psi_n, const void* grad_out, void* grad_in, double* dLdV,
+                       void* stream, rexi_stats* st) {
+    if (!p || !psi_n || !grad_out || !grad_in || !dLdV) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int r = ensure_backward(p);
+    if (r) return p->last_status = r;
+    int launches = 0;
+    // forward substeps 0..n_sub-2 from psi_n, saving their outputs as checkpoints
+    for (int sub = 0; sub + 1 < p->n_sub; ++sub) {
+        IOArgs io{};
+        io.in[0] = sub == 0 ? (const double2*)psi_n : p->d_ckpt + (size_t)sub * p->n;
+        io.out[0] = p->d_ckpt + (size_t)(sub + 1) * p->n;
+        EngineArgs A = base_args(p, rexi::MODE_STEP, p->one, 1, 1);
+        r = launch(p, A, io, p->K * p->ntiles, s);
+        if (r) return p->last_status = r;
+        ++launches;
+    }
+    IOArgs io{};
+    io.in[0] = (const double2*)psi_n;
+    io.out[0] = (double2*)grad_in;
+    io.gout[0] = (const double2*)grad_out;
+    io.dLdV[0] = dLdV;
+    EngineArgs A = base_args(p, rexi::MODE_BACKWARD, p->bwd, 1, p->n_sub);
+    r = launch(p, A, io, 2 * p->K * p->ntiles, s);
+    if (r) return p->last_status = r;
+    p->last_launches = launches + 1;
+    if (!st) return p->last_status = REXI_OK;
+    return p->last_status = collect(p, s, 2 * p->K, p->K, p->K, st, p->n_sub);
+}
+
+int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in, void* const* psi_out,
+                      void* stream, rexi_stats* st) {
+    if (!plans || B < 1 || B > rexi::kMaxBatch || !psi_in || !psi_out) return REXI_EINVAL;
+    rexi_plan* p0 = plans[0];
+    if (!p0) return REXI_EINVAL;
+    int total_items = 0, max_sub = 0, total_tiles = 0;
+    for (int b = 0; b < B; ++b) {
+        rexi_plan* p = plans[b];
+        if (!p || !psi_in[b] || !psi_out[b]) return REXI_EINVAL;
+        if (p->device != p0->device || p->fp32 != p0->fp32 || p->m != p0->m) return REXI_EINVAL;
+        for (int c = 0; c < b; ++c)
+            if (plans[c] == p) return REXI_EINVAL;         // one plan's workspace per problem
+        total_items += p->K;
+        total_tiles += p->K * p->ntiles;
+        max_sub = std::max(max_sub, p->n_sub);
+    }
+    if (total_items > rexi::kMaxItems) return REXI_EINVAL;
+    DeviceGuard guard(p0->device);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // Descriptor set of this combination of plans, cached in the first plan.
+    struct BatchCache {
+        std::vector<rexi_plan*> key;
+        std::vector<int> gens;
+        ProblemDesc* d_prob = nullptr;
+        ItemDesc* d_items = nullptr;
+        int nitems = 0;
+    };
+    static std::mutex mu;
+    static std::vector<std::pair<rexi_plan*, BatchCache>> caches;
+    std::lock_guard<std::mutex> lk(mu);
+    BatchCache* bc = nullptr;
+    for (auto& c : caches)
+        if (c.first == p0) bc = &c.second;
+    const std::vector<rexi_plan*> key(plans, plans + B);
+    std::vector<int> gens(B);
+    for (int b = 0; b < B; ++b) gens[b] = plans[b]->generation;
+    if (!bc || bc->key != key || bc->gens != gens) {
+        std::vector<ProblemDesc> probs;
+        std::vector<ItemDesc> items;
+        for (int b = 0; b < B; ++b) {
+            rexi_plan* p = plans[b];
+            probs.push_back(make_problem(p, p->n_sub, (int)items.size(), p->K));
+            for (int k = 0; k < p->K; ++k) items.push_back(make_item(p, k, k, false, b, 0));
+        }
+        if (!bc) {
+            caches.push_back(std::make_pair(p0, BatchCache()));
+            bc = &caches.back().second;
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) return REXI_ECUDA;
+        int r;
+        if ((r = dalloc(p0, &bc->d_prob, probs.size()))) return r;
+        if ((r = dalloc(p0, &bc->d_items, items.size()))) return r;
+        if (cudaMemcpy(bc->d_prob, probs.data(), sizeof(ProblemDesc) * probs.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(bc->d_items, items.data(), sizeof(ItemDesc) * items.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+            return REXI_ECUDA;
+        bc->key = key;
+        bc->gens = gens;
+        bc->nitems = (int)items.size();
+    }
+    IOArgs io{};
+    for (int b = 0; b < B; ++b) {
+        io.in[b] = (const double2*)psi_in[b];
+        io.out[b] = (double2*)psi_out[b];
+    }
+    DescSet set;
+    set.d_prob = bc->d_prob;
+    set.d_items = bc->d_items;
+    set.nitems = bc->nitems;
+    EngineArgs A = base_args(p0, rexi::MODE_STEP, set, B, max_sub);
+    // statistics of every plan are zeroed, the barrier/error words are p0's
+    for (int b = 1; b < B; ++b)
+        if (cudaMemsetAsync(plans[b]->d_stats, 0, sizeof(ItemStats) * plans[b]->K, s) != cudaSuccess)
+            return REXI_ECUDA;
+    cudaError_t e = cudaMemsetAsync(p0->d_bar, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_stats, 0, sizeof(ItemStats) * p0->K, s);
+    if (e != cudaSuccess) return REXI_ECUDA;
+    const size_t smem = rexi::engine_smem_bytes(A.nitems);
+    const int maxg = max_grid_cached(p0->fp32, smem, p0->device);
+    if (maxg <= 0) return REXI_ECUDA;
+    const int grid = std::max(1, std::min(maxg, total_tiles));
+    e = rexi::launch_engine(p0->fp32, A, io, grid, smem, s);
+    for (int b = 0; b < B; ++b) {
+        plans[b]->last_stream = s;
+        plans[b]->last_launches = 1;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (!st) return REXI_OK;
+    int status = REXI_OK;
+    for (int b = 0; b < B; ++b) {
+        rexi_plan* p = plans[b];
+        int err = 0;
+        std::vector<ItemStats> sv(p->K);
+        if (cudaMemcpyAsync(&err, p0->d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(sv.data(), p->d_stats, sizeof(ItemStats) * p->K, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return REXI_ECUDA;
+        rexi_stats& o = st[b];
+        std::memset(&o, 0, sizeof(o));
+        o.n_sub = p->n_sub;
+        bool failed = false;
+        for (int k = 0; k < p->K; ++k) {
+            if (k < REXI_MAX_POLES) {
+                o.iters[k] = sv[k].iters;
+                o.cycles[k] = sv[k].cycles;
+                o.iters_sq[k] = sv[k].iters_sq;
+                o.resid[k] = sv[k].resid;
+            }
+            o.total_iters += sv[k].iters;
+            o.total_cycles += sv[k].cycles;
+            o.max_iters_seen = std::max(o.max_iters_seen, sv[k].max_sub_iters);
+            failed = failed || sv[k].failed;
+        }
+        o.status = err ? err : (failed ? REXI_ENOCONV : REXI_OK);
+        if (o.status != REXI_OK && status == REXI_OK) status = o.status;
+        p->last_status = o.status;
+    }
+    return status;
+}
+
+int rexi_plan_last_status(rexi_plan* p) {
+    if (!p) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    int err = 0;
+    if (cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, p->last_stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->last_stream) != cudaSuccess)
+        return REXI_ECUDA;
+    if (err) return err;
+    return p->last_status;
+}
+
+int rexi_plan_last_launches(const rexi_plan* p) { return p ? p->last_launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,957 @@
+// Persistent REXI engine for sm_103a.
+//
+// One cooperative launch runs a whole call: n_sub substeps of Eq. (5) of
+// Rittich & Speck (arXiv:1912.03312), each made of K independent restarted
+// GMRES solves of (tau H - z_k I) x_k = b (Sec. 3.1: the K systems are
+// independent tasks) followed by the weighted pole sum.  All solves of all
+// problems advance in lock step through grid-wide phases separated by bounded
+// grid barriers:
+//
+//   E3  residual   r = b - A x in FP64 (x = 0 on the first cycle), stored as u_0
+//   E4  decide     per item: converged / failed / start a cycle with s_0 = 1/||r||
+//   P1  matvec     w = A (s_j u_j) (stencil, fused diagonal shift), p1 = U_j^H w
+//   P2  CGS pass 2 p2 = U_j^H (w - V_j h1)
+//   P3  update     w <- w - V_j (h1 + h2), ||w||^2                (CGS2)
+//   P4  Givens     per item: rotate the Hessenberg column, update |g_{j+1}|
+//   E2  update     x += V_k y, y = R^{-1} g                      (FP64 accumulation)
+//   PS  pole sum   psi' = alpha_0 b + sum_k alpha_k x_k          (FP64)
+//   BA  adjoint    G' = conj(alpha_0) G + sum conj(alpha_k) Y_k,
+//                  dL/dV -= tau Re sum alpha_k conj(Y_k) X_k
+//
+// A "phase" is the flat list of (item, tile) tasks of the items in the right
+// state, split evenly over the CTAs.  Partial dot products are written per tile
+// and reduced in FP64 by the CTAs of the next phase.  Basis vectors u_i are
+// stored unnormalised; v_i = s_i u_i with an FP64 scale s_i.
+#include <cstdint>
+
+#include "engine.h"
+
+namespace rexi {
+
+namespace {
+
+constexpr int kWarps = kBlock / 32;
+constexpr int kErrTimeout = -5;   // REXI_ETIMEOUT
+
+template <typename T> struct C2;
+template <> struct C2<float> { typedef float2 t; };
+template <> struct C2<double> { typedef double2 t; };
+
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+
+template <typename V> __device__ __forceinline__ V cvt2(double2 a);
+template <> __device__ __forceinline__ float2 cvt2<float2>(double2 a) {
+    return make_float2((float)a.x, (float)a.y);
+}
+template <> __device__ __forceinline__ double2 cvt2<double2>(double2 a) { return a; }
+__device__ __forceinline__ double2 up2(float2 a) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 up2(double2 a) { return a; }
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// Loads of data written inside this launch go through L2 only (.cg): L1 is
+// not coherent across SMs.
+__device__ __forceinline__ float2 ldp(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ldp(const double2* p) { return __ldcg(p); }
+__device__ __forceinline__ double ldd(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ int ldi(const int* p) { return __ldcg(p); }
+
+template <typename V> __device__ __forceinline__ V item_shift(const ItemDesc& it);
+template <> __device__ __forceinline__ float2 item_shift<float2>(const ItemDesc& it) { return it.shiftf; }
+template <> __device__ __forceinline__ double2 item_shift<double2>(const ItemDesc& it) { return it.shift; }
+template <typename T> __device__ __forceinline__ const T* prob_diag(const ProblemDesc& pr);
+template <> __device__ __forceinline__ const float* prob_diag<float>(const ProblemDesc& pr) { return pr.diagf; }
+template <> __device__ __forceinline__ const double* prob_diag<double>(const ProblemDesc& pr) { return pr.diag; }
+template <typename T> __device__ __forceinline__ T prob_a(const ProblemDesc& pr, int d);
+template <> __device__ __forceinline__ float prob_a<float>(const ProblemDesc& pr, int d) { return pr.af[d]; }
+template <> __device__ __forceinline__ double prob_a<double>(const ProblemDesc& pr, int d) { return pr.a[d]; }
+
+// ---- grid barrier ---------------------------------------------------------
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All CTAs of the co-resident (cooperative) grid meet here.  Every wait is
+// bounded by timeout_ns; on expiry the sticky error word is set and every CTA
+// leaves the kernel at its next barrier.  Returns false when the launch must end.
+__device__ bool grid_sync(unsigned* bar, int* err, unsigned long long timeout_ns) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned* count = bar;
+        unsigned* gen = bar + 1;
+        const unsigned g = ld_acquire_u32(gen);
+        __threadfence();
+        const unsigned prev = atomicAdd(count, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            st_release_u32(gen, g + 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(gen) == g) {
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicExch(err, kErrTimeout);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int*)err == 0;
+}
+
+// ---- reductions -------------------------------------------------------------
+
+// Transpose-reduce NV per-lane values across a warp: afterwards lane l holds
+// the warp-wide sum of value (l % NV); 31 shuffles for NV = 32.
+template <int NV, typename T>
+__device__ __forceinline__ T warp_transpose_reduce(T (&v)[NV], int lane) {
+#pragma unroll
+    for (int off = 16; off >= NV; off >>= 1) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    }
+#pragma unroll
+    for (int half = NV / 2; half >= 1; half >>= 1) {
+        const bool up = (lane & half) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            T send = up ? v[k] : v[k + half];
+            T keep = up ? v[k + half] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+        }
+    }
+    return v[0];
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__device__ __forceinline__ double2 shfl2(double2 v, int src) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+struct Smem {
+    EngineArgs A;
+    IOArgs io;
+    double2 red[kWarps][32];
+    double redn[kWarps];
+    double2 h1[kMaxM + 1];
+    double2 h2[kMaxM + 1];
+    double2 coef[kMaxM + 1];       // FP64 coefficients of the current item
+    float2 coeff[kMaxM + 1];       // the same, rounded for the FP32 path
+    double ssm[kMaxM + 1];
+    double2 gsm[kMaxM + 1];
+    double2 Rsm[kMaxM * (kMaxM + 1) / 2];
+    int cnt[kBlock];
+    int tls[kBlock];
+    int nl;
+    int ntasks;
+    int kk;                        // Arnoldi steps of the current item (E2)
+};
+
+template <typename V> __device__ __forceinline__ V coef_at(const Smem& sm, int q);
+template <> __device__ __forceinline__ float2 coef_at<float2>(const Smem& sm, int q) { return sm.coeff[q]; }
+template <> __device__ __forceinline__ double2 coef_at<double2>(const Smem& sm, int q) { return sm.coef[q]; }
+
+// CTA sum of NV complex values per thread; thread t < nvalid receives value t.
+template <int NV, typename T>
+__device__ __forceinline__ double2 cta_reduce_vec(Smem& sm, T (&re)[NV], T (&im)[NV], int nvalid) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T r = warp_transpose_reduce<NV, T>(re, lane);
+    T i = warp_transpose_reduce<NV, T>(im, lane);
+    if (lane < NV) sm.red[warp][lane] = make_double2((double)r, (double)i);
+    __syncthreads();
+    double2 out = make_double2(0.0, 0.0);
+    if (threadIdx.x < nvalid) {
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) out = cadd(out, sm.red[w][threadIdx.x]);
+    }
+    __syncthreads();
+    return out;
+}
+
+__device__ __forceinline__ double cta_reduce_scalar(Smem& sm, double v) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sm.redn[warp] = v;
+    __syncthreads();
+    double out = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) out += sm.redn[w];
+    }
+    __syncthreads();
+    return out;   // valid in thread 0
+}
+
+// ---- work lists -------------------------------------------------------------
+
+// List (in shared memory) of the items whose status bit is set in `mask`, and
+// the prefix sums of their tile counts.  Identical in every CTA: statuses are
+// read after a grid barrier and only changed in per-item phases.
+__device__ void build_list(Smem& sm, int* list, int* prefix, unsigned mask) {
+    const EngineArgs& A = sm.A;
+    const int nit = A.nitems;
+    const int per = (nit + kBlock - 1) / kBlock;
+    const int i0 = threadIdx.x * per;
+    const int i1 = min(nit, i0 + per);
+    int c = 0, t = 0;
+    for (int i = i0; i < i1; ++i) {
+        const int s = ldi(&A.item[i].st->status);
+        if (mask & (1u << s)) { ++c; t += A.item[i].ntiles; }
+    }
+    sm.cnt[threadIdx.x] = c;
+    sm.tls[threadIdx.x] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ac = 0, at = 0;
+        for (int k = 0; k < kBlock; ++k) {
+            const int cc = sm.cnt[k], tt = sm.tls[k];
+            sm.cnt[k] = ac;
+            sm.tls[k] = at;
+            ac += cc;
+            at += tt;
+        }
+        sm.nl = ac;
+        sm.ntasks = at;
+        prefix[ac] = at;
+    }
+    __syncthreads();
+    c = sm.cnt[threadIdx.x];
+    t = sm.tls[threadIdx.x];
+    for (int i = i0; i < i1; ++i) {
+        const int s = ldi(&A.item[i].st->status);
+        if (mask & (1u << s)) {
+            list[c] = i;
+            prefix[c] = t;
+            ++c;
+            t += A.item[i].ntiles;
+        }
+    }
+    __syncthreads();
+}
+
+// Problems live in (backward) substep `sub`, with their tile prefix sums.
+__device__ void build_problem_list(Smem& sm, int* list, int* prefix, int sub) {
+    const EngineArgs& A = sm.A;
+    if (threadIdx.x == 0) {
+        int c = 0, t = 0;
+        for (int p = 0; p < A.nproblems; ++p) {
+            if (sub < A.prob[p].nsub) {
+                list[c] = p;
+                prefix[c] = t;
+                ++c;
+                t += A.prob[p].ntiles;
+            }
+        }
+        prefix[c] = t;
+        sm.nl = c;
+        sm.ntasks = t;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int find_slot(const int* prefix, int nl, int task) {
+    int lo = 0, hi = nl - 1;                  // largest l with prefix[l] <= task
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= task) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---- stencil ----------------------------------------------------------------
+
+struct Nb { int xm, xp, ym, yp, zm, zp; };
+
+__device__ __forceinline__ Nb neighbours(int p, int nx, int ny, int nz) {
+    Nb b;
+    const int ix = p % nx;
+    const int q = p / nx;
+    const int iy = q % ny;
+    const int iz = q / ny;
+    b.xm = ix == 0 ? p + nx - 1 : p - 1;
+    b.xp = ix == nx - 1 ? p - nx + 1 : p + 1;
+    const int sy = nx;
+    b.ym = iy == 0 ? p + sy * (ny - 1) : p - sy;
+    b.yp = iy == ny - 1 ? p - sy * (ny - 1) : p + sy;
+    const int sz = nx * ny;
+    b.zm = iz == 0 ? p + sz * (nz - 1) : p - sz;
+    b.zp = iz == nz - 1 ? p - sz * (nz - 1) : p + sz;
+    return b;
+}
+
+// (A u)_p = sum_d a_d (u_{p+e_d} + u_{p-e_d}) + (diag_p - shift) u_p in precision
+// T: the periodic second-order Laplacian of tau H with the diagonal tau (V - c)
+// and the pole shift fused.
+template <typename T, typename V>
+__device__ __forceinline__ V stencil_apply(const V* __restrict__ u, int p, const ProblemDesc& pr,
+                                           const T* __restrict__ diag, const T a0, const T a1,
+                                           const T a2, const V shift) {
+    const Nb b = neighbours(p, pr.nx, pr.ny, pr.nz);
+    const V c = ldp(u + p);
+    V s;
+    {
+        const V l = ldp(u + b.xm), r = ldp(u + b.xp);
+        s = mk2(a0 * (l.x + r.x), a0 * (l.y + r.y));
+    }
+    if (pr.ny > 1) {
+        const V l = ldp(u + b.ym), r = ldp(u + b.yp);
+        s.x += a1 * (l.x + r.x);
+        s.y += a1 * (l.y + r.y);
+    }
+    if (pr.nz > 1) {
+        const V l = ldp(u + b.zm), r = ldp(u + b.zp);
+        s.x += a2 * (l.x + r.x);
+        s.y += a2 * (l.y + r.y);
+    }
+    const T d = __ldg(diag + p);
+    s.x += d * c.x - (shift.x * c.x - shift.y * c.y);
+    s.y += d * c.y - (shift.x * c.y + shift.y * c.x);
+    return s;
+}
+
+// ---- per-problem state buffers ---------------------------------------------
+
+// Problem q's state buffers; io holds the caller's pointers of this call.
+__device__ __forceinline__ const double2* step_in(const IOArgs& io, const ProblemDesc& pr, int q, int sub) {
+    if (sub == 0) return io.in[q];
+    return (sub & 1) ? pr.tmp0 : pr.tmp1;
+}
+__device__ __forceinline__ double2* step_out(const IOArgs& io, const ProblemDesc& pr, int q, int sub) {
+    if (sub == pr.nsub - 1) return io.out[q];
+    return (sub & 1) ? pr.tmp1 : pr.tmp0;
+}
+// Backward substep bs = 0 undoes the last forward substep.
+__device__ __forceinline__ const double2* adj_in(const IOArgs& io, const ProblemDesc& pr, int q, int bs) {
+    if (bs == 0) return io.gout[q];
+    return (bs & 1) ? pr.tmp0 : pr.tmp1;
+}
+__device__ __forceinline__ double2* adj_out(const IOArgs& io, const ProblemDesc& pr, int q, int bs) {
+    if (bs == pr.nsub - 1) return io.out[q];
+    return (bs & 1) ? pr.tmp1 : pr.tmp0;
+}
+__device__ __forceinline__ const double2* fwd_state(const IOArgs& io, const ProblemDesc& pr, int q, int bs) {
+    const int s = pr.nsub - 1 - bs;
+    return s == 0 ? io.in[q] : pr.ckpt + (size_t)s * (size_t)pr.n;
+}
+__device__ __forceinline__ const double2* item_rhs(int mode, const IOArgs& io, const ItemDesc& it,
+                                                  const ProblemDesc& pr, int sub) {
+    const int q = it.problem;
+    if (mode == MODE_BACKWARD) return it.adjoint ? adj_in(io, pr, q, sub) : fwd_state(io, pr, q, sub);
+    if (mode == MODE_SOLVE) return io.in[q];
+    return step_in(io, pr, q, sub);
+}
+
+// ---- phases -------------------------------------------------------------------
+
+// out[i] = scale_i * sum_tiles part[tile][i], i < nv (nv <= 32).
+__device__ void reduce_partials(Smem& sm, const double2* part, const ItemDesc& it, int nv,
+                                const double* scale, double2* out) {
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    double2 acc = make_double2(0.0, 0.0);
+    if (lane < nv) {
+        for (int t = grp; t < it.ntiles; t += kWarps)
+            acc = cadd(acc, ldp(part + (size_t)(it.tile_off + t) * sm.A.pv + lane));
+    }
+    sm.red[grp][lane] = acc;
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int g = 0; g < kWarps; ++g) s = cadd(s, sm.red[g][threadIdx.x]);
+        out[threadIdx.x] = cscale(s, scale[threadIdx.x]);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void load_scales(Smem& sm, const ItemState* S, int cnt) {
+    if (threadIdx.x < cnt) sm.ssm[threadIdx.x] = ldd(&S->s[threadIdx.x]);
+    __syncthreads();
+}
+
+template <typename T, int VG>
+struct Phases {
+    typedef typename C2<T>::t V;
+
+    // E3: residual r = b - A x (FP64), stored as u_0; x = 0 on the first cycle.
+    static __device__ void e3(Smem& sm, int sub, int item, int tile) {
+        const EngineArgs& A = sm.A;
+        const ItemDesc& it = A.item[item];
+        const ProblemDesc& pr = A.prob[it.problem];
+        const ItemState* S = it.st;
+        const int cycles = ldi(&S->cycles);
+        const double2* b = item_rhs(A.mode, sm.io, it, pr, sub);
+        V* U = (V*)it.basis;
+        double2* x = it.x;
+        const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+        double acc = 0.0;
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            if (p < pend) {
+                double2 rv = ldp(b + p);
+                if (cycles == 0) {
+                    x[p] = make_double2(0.0, 0.0);
+                } else {
+                    const double2 ax = stencil_apply<double, double2>(x, p, pr, pr.diag, pr.a[0], pr.a[1],
+                                                                      pr.a[2], it.shift);
+                    rv = csub(rv, ax);
+                }
+                U[p] = cvt2<V>(rv);
+                acc += rv.x * rv.x + rv.y * rv.y;
+            }
+        }
+        const double tot = cta_reduce_scalar(sm, acc);
+        if (threadIdx.x == 0) it.partn[it.tile_off + tile] = tot;
+    }
+
+    // P1: w = A (s_j u_j) into slot j+1; p1_i = sum conj(u_i) w, i <= j.
+    static __device__ void p1(Smem& sm, int item, int tile, int j) {
+        const EngineArgs& A = sm.A;
+        const ItemDesc& it = A.item[item];
+        const ProblemDesc& pr = A.prob[it.problem];
+        const size_t n = (size_t)it.n;
+        V* U = (V*)it.basis;
+        const V* uj = U + (size_t)j * n;
+        V* wv = U + (size_t)(j + 1) * n;
+        const T sj = (T)ldd(&it.st->s[j]);
+        const V shift = item_shift<V>(it);
+        const T* diag = prob_diag<T>(pr);
+        const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
+        const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+        for (int i0 = 0; i0 <= j; i0 += VG) {
+            T ar[VG], ai[VG];
+#pragma unroll
+            for (int q = 0; q < VG; ++q) { ar[q] = T(0); ai[q] = T(0); }
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                if (p < pend) {
+                    V w;
+                    if (i0 == 0) {
+                        w = stencil_apply<T, V>(uj, p, pr, diag, a0, a1, a2, shift);
+                        w.x *= sj;
+                        w.y *= sj;
+                        wv[p] = w;
+                    } else {
+                        w = ldp(wv + p);
+                    }
+#pragma unroll
+                    for (int q = 0; q < VG; ++q) {
+                        if (i0 + q <= j) {
+                            const V u = ldp(U + (size_t)(i0 + q) * n + p);
+                            ar[q] += u.x * w.x + u.y * w.y;
+                            ai[q] += u.x * w.y - u.y * w.x;
+                        }
+                    }
+                }
+            }
+            const int nv = min(VG, j + 1 - i0);
+            const double2 v = cta_reduce_vec<VG, T>(sm, ar, ai, nv);
+            if (threadIdx.x < nv) it.part1[(size_t)(it.tile_off + tile) * A.pv + i0 + threadIdx.x] = v;
+        }
+    }
+
+    // P2 prologue: h1_i = s_i sum p1_i; coefficients s_i h1_i of u_i.
+    static __device__ void p2_pro(Smem& sm, int item, int j) {
+        const EngineArgs& A = sm.A;
+        const ItemDesc& it = A.item[item];
+        load_scales(sm, it.st, j + 1);
+        reduce_partials(sm, it.part1, it, j + 1, sm.ssm, sm.h1);
+        if (threadIdx.x <= j) {
+            const double2 c = cscale(sm.h1[threadIdx.x], sm.ssm[threadIdx.x]);
+            sm.coef[threadIdx.x] = c;
+            sm.coeff[threadIdx.x] = make_float2((float)c.x, (float)c.y);
+        }
+        __syncthreads();
+    }
+
+    // P2: w' = w - sum_i c_i u_i (not stored); p2_i = sum conj(u_i) w'.
+    static __device__ void p2(Smem& sm, int item, int tile, int j) {
+        const EngineArgs& A = sm.A;
+        const ItemDesc& it = A.item[item];
+        const size_t n = (size_t)it.n;
+        const V* U = (const V*)it.basis;
+        const V* wv = U + (size_t)(j + 1) * n;
+        const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+        for (int i0 = 0; i0 <= j; i0 += VG) {
+            T ar[VG], ai[VG];
+#pragma unroll
+            for (int q = 0; q < VG; ++q) { ar[q] = T(0); ai[q] = T(0); }
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                if (p < pend) {
+                    V w = ldp(wv + p);
+#pragma unroll
+                    for (int q = 0; q < kMaxM; ++q) {
+                        if (q <= j) {
+                            const V u = ldp(U + (size_t)q * n + p);
+                            const V c = coef_at<V>(sm, q);
+                            w.x -= c.x * u.x - c.y * u.y;
+                            w.y -= c.x * u.y + c.y * u.x;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < VG; ++q) {
+                        if (i0 + q <= j) {
+                            const V u = ldp(U + (size_t)(i0 + q) * n + p);
+                            ar[q] += u.x * w.x + u.y * w.y;
+                            ai[q] += u.x * w.y - u.y * w.x;
+                        }
+                    }
+                }
+            }
+            const int nv = min(VG, j + 1 - i0);
+            const double2 v = cta_reduce_vec<VG, T>(sm, ar, ai, nv);
+            if (threadIdx.x < nv) it.part2[(size_t)(it.tile_off + tile) * A.pv + i0 + threadIdx.x] = v;
+        }
+    }
+
+    // P3 prologue: h = h1 + h2; coefficients s_i h_i.
+    static __device__ void p3_pro(Smem& sm, int item, int j) {
+        const EngineArgs& A = sm.A;
+        const ItemDesc& it = A.item[item];
+        load_scales(sm, it.st, j + 1);
+        reduce_partials(sm, it.part1, it, j + 1, sm.ssm, sm.h1);
+        reduce_partials(sm, it.part2, it, j + 1, sm.ssm, sm.h2);
+        if (threadIdx.x <= j) {
+            const double2 h = cadd(sm.h1[threadIdx.x], sm.h2[threadIdx.x]);
+            sm.h1[threadIdx.x] = h;
+            const double2 c = cscale(h, sm.ssm[threadIdx.x]);
+            sm.coef[threadIdx.x] = c;
+            sm.coeff[threadIdx.x] = make_float2((float)c.x, (float)c.y);
+        }
+        __syncthreads();
+    }
+
+    // P3: w <- w - sum_i c_i u_i (stored), ||w||^2; tile 0 publishes the column.
+    static __device__ void p3(Smem& sm, int item, int tile, int j) {
+        const EngineArgs& A = sm.A;
+        const ItemDesc& it = A.item[item];
+        const size_t n = (size_t)it.n;
+        V* U = (V*)it.basis;
+        V* wv = U + (size_t)(j + 1) * n;
+        if (tile == 0 && threadIdx.x <= j) it.st->hcol[threadIdx.x] = sm.h1[threadIdx.x];
+        const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+        T acc = T(0);
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            if (p < pend) {
+                V w = ldp(wv + p);
+#pragma unroll
+                for (int q = 0; q < kMaxM; ++q) {
+                    if (q <= j) {
+                        const V u = ldp(U + (size_t)q * n + p);
+                        const V c = coef_at<V>(sm, q);
+                        w.x -= c.x * u.x - c.y * u.y;
+                        w.y -= c.x * u.y + c.y * u.x;
+                    }
+                }
+                wv[p] = w;
+                acc += w.x * w.x + w.y * w.y;
+            }
+        }
+        const double tot = cta_reduce_scalar(sm, (double)acc);
+        if (threadIdx.x == 0) it.partn[it.tile_off + tile] = tot;
+    }
+
+    // E2 prologue: y = R^{-1} g (back substitution, FP64), coefficients y_i s_i.
+    static __device__ void e2_pro(Smem& sm, int item) {
+        const ItemState* S = sm.A.item[item].st;
+        const int k = ldi(&S->k);
+        const int nR = k * (k + 1) / 2;
+        for (int t = threadIdx.x; t < nR; t += kBlock) sm.Rsm[t] = ldp(&S->R[t]);
+        if (threadIdx.x < k) {
+            sm.gsm[threadIdx.x] = ldp(&S->g[threadIdx.x]);
+            sm.ssm[threadIdx.x] = ldd(&S->s[threadIdx.x]);
+        }
+        if (threadIdx.x == 0) sm.kk = k;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = k - 1; i >= 0; --i) {
+                double2 acc = sm.gsm[i];
+                for (int l = i + 1; l < k; ++l) acc = csub(acc, cmul(sm.Rsm[l * (l + 1) / 2 + i], sm.h2[l]));
+                const double2 d = sm.Rsm[i * (i + 1) / 2 + i];
+                const double den = d.x * d.x + d.y * d.y;
+                double2 y = make_double2(0.0, 0.0);
+                if (den > 0.0) y = cscale(cmul(acc, cconj(d)), 1.0 / den);
+                sm.h2[i] = y;                              // y_i
+            }
+            for (int i = 0; i < k; ++i) sm.coef[i] = cscale(sm.h2[i], sm.ssm[i]);
+        }
+        __syncthreads();
+    }
+
+    // E2: x += sum_i c_i u_i (FP64 accumulation).
+    static __device__ void e2(Smem& sm, int item, int tile) {
+        const EngineArgs& A = sm.A;
+        const ItemDesc& it = A.item[item];
+        const size_t n = (size_t)it.n;
+        const V* U = (const V*)it.basis;
+        double2* x = it.x;
+        const int k = sm.kk;
+        const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            if (p < pend) {
+                double2 xv = ldp(x + p);
+#pragma unroll
+                for (int q = 0; q < kMaxM; ++q) {
+                    if (q < k) {
+                        const double2 u = up2(ldp(U + (size_t)q * n + p));
+                        const double2 c = sm.coef[q];
+                        xv.x += c.x * u.x - c.y * u.y;
+                        xv.y += c.x * u.y + c.y * u.x;
+                    }
+                }
+                x[p] = xv;
+            }
+        }
+    }
+};
+
+// E4 (one warp per item): true relative residual, decide, start a cycle.
+__device__ void item_e4(const EngineArgs& A, int item) {
+    const int lane = threadIdx.x & 31;
+    const ItemDesc& it = A.item[item];
+    ItemState* S = it.st;
+    double ss = 0.0;
+    for (int t = lane; t < it.ntiles; t += 32) ss += ldd(it.partn + it.tile_off + t);
+    ss = warp_sum(ss);
+    if (lane != 0) return;
+    const double beta = sqrt(ss);
+    const int cycles = ldi(&S->cycles);
+    double bnorm = cycles == 0 ? beta : ldd(&S->bnorm);
+    if (cycles == 0) S->bnorm = beta;
+    const double relres = bnorm > 0.0 ? beta / bnorm : 0.0;
+    S->relres = relres;
+    const int total = ldi(&S->total_iters);
+    int status;
+    if (!(relres <= 1e300)) {
+        status = ST_FAILED;                         // NaN / Inf
+    } else if (bnorm == 0.0 || relres <= A.tol) {
+        status = ST_CONVERGED;
+    } else if (total >= A.max_iters) {
+        status = ST_FAILED;
+    } else {
+        status = ST_ARNOLDI;
+        S->s[0] = 1.0 / beta;
+        S->g[0] = make_double2(beta, 0.0);
+        S->k = 0;
+        S->cycles = cycles + 1;
+        S->cycle_tol_abs = fmax(A.tol * bnorm, A.inner_tol * beta);
+    }
+    if (status != ST_ARNOLDI) {
+        ItemStats* T = it.stats;
+        T->iters += total;
+        T->iters_sq += ldi(&S->sum_k2);
+        T->cycles += cycles;
+        T->max_sub_iters = max(T->max_sub_iters, total);
+        T->resid = fmax(T->resid, relres);
+        if (status == ST_FAILED) T->failed = 1;
+    }
+    __threadfence();
+    S->status = status;
+}
+
+// P4 (one warp per item): Givens rotations of the new Hessenberg column.
+__device__ void item_p4(const EngineArgs& A, int item, int j) {
+    const int lane = threadIdx.x & 31;
+    const ItemDesc& it = A.item[item];
+    ItemState* S = it.st;
+    const double2 hl = lane <= j ? ldp(&S->hcol[lane]) : make_double2(0.0, 0.0);
+    const double csl = lane < j ? ldd(&S->cs[lane]) : 0.0;
+    const double2 snl = lane < j ? ldp(&S->sn[lane]) : make_double2(0.0, 0.0);
+    double ss = 0.0;
+    for (int t = lane; t < it.ntiles; t += 32) ss += ldd(it.partn + it.tile_off + t);
+    ss = warp_sum(ss);
+    const double hn = sqrt(ss);                  // h_{j+1,j} = ||w||
+    double2 carry = shfl2(hl, 0);
+    const int col = j * (j + 1) / 2;
+    for (int i = 0; i < j; ++i) {
+        const double2 b = shfl2(hl, i + 1);
+        const double c = __shfl_sync(0xffffffffu, csl, i);
+        const double2 s = shfl2(snl, i);
+        const double2 nh = cadd(cscale(carry, c), cmul(s, b));
+        carry = cadd(cscale(cmul(cconj(s), carry), -1.0), cscale(b, c));
+        if (lane == 0) S->R[col + i] = nh;
+    }
+    if (lane != 0) return;
+    const double aa = sqrt(carry.x * carry.x + carry.y * carry.y);
+    const double rr = sqrt(aa * aa + hn * hn);
+    double c;
+    double2 s, rjj;
+    if (aa == 0.0) {
+        c = 0.0;
+        s = make_double2(1.0, 0.0);
+        rjj = make_double2(hn, 0.0);
+    } else {
+        c = aa / rr;
+        s = cscale(carry, hn / (aa * rr));
+        rjj = cscale(carry, rr / aa);
+    }
+    const double2 gj = ldp(&S->g[j]);
+    const double2 gj1 = cscale(cmul(cconj(s), gj), -1.0);
+    S->R[col + j] = rjj;
+    S->cs[j] = c;
+    S->sn[j] = s;
+    S->g[j] = cscale(gj, c);
+    S->g[j + 1] = gj1;
+    S->s[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    S->k = j + 1;
+    const int total = ldi(&S->total_iters) + 1;
+    S->total_iters = total;
+    const double res = sqrt(gj1.x * gj1.x + gj1.y * gj1.y);
+    const bool end = !(res > ldd(&S->cycle_tol_abs)) || j + 1 >= A.m || total >= A.max_iters ||
+                     !(hn > 0.0) || !(rr > 0.0);
+    if (end) S->sum_k2 = ldi(&S->sum_k2) + (j + 1) * (j + 1);
+    __threadfence();
+    S->status = end ? ST_CYCLE_END : ST_ARNOLDI;
+}
+
+// PS: psi' = alpha_0 b + sum_k alpha_k x_k for one tile of a problem.
+__device__ void task_pole_sum(const EngineArgs& A, const IOArgs& io, int prob, int tile, int sub) {
+    const ProblemDesc& pr = A.prob[prob];
+    const double2* b = step_in(io, pr, prob, sub);
+    double2* out = step_out(io, pr, prob, sub);
+    const int p0 = tile * kTile, pend = min(pr.n, p0 + kTile);
+    for (int r = 0; r < kPPT; ++r) {
+        const int p = p0 + r * kBlock + threadIdx.x;
+        if (p < pend) {
+            double2 acc = cmul(pr.alpha0, ldp(b + p));
+            for (int k = 0; k < pr.K; ++k) {
+                const double2 al = __ldg(pr.alpha + k);
+                acc = cadd(acc, cmul(al, ldp(A.item[pr.item0 + k].x + p)));
+            }
+            out[p] = acc;
+        }
+    }
+}
+
+// BA: adjoint accumulation for one tile of a problem (backward substep bs).
+__device__ void task_adjoint(const EngineArgs& A, const IOArgs& io, int prob, int tile, int bs) {
+    const ProblemDesc& pr = A.prob[prob];
+    const double2* gin = adj_in(io, pr, prob, bs);
+    double2* gout = adj_out(io, pr, prob, bs);
+    double* dV = io.dLdV[prob];
+    const int p0 = tile * kTile, pend = min(pr.n, p0 + kTile);
+    for (int r = 0; r < kPPT; ++r) {
+        const int p = p0 + r * kBlock + threadIdx.x;
+        if (p < pend) {
+            double2 g = cmul(cconj(pr.alpha0), ldp(gin + p));
+            double dv = 0.0;
+            for (int k = 0; k < pr.K; ++k) {
+                const double2 al = __ldg(pr.alpha + k);
+                const double2 X = ldp(A.item[pr.item0 + k].x + p);
+                const double2 Y = ldp(A.item[pr.item0 + pr.K + k].x + p);
+                g = cadd(g, cmul(cconj(al), Y));
+                dv += cmul(al, cmul(cconj(Y), X)).x;
+            }
+            gout[p] = g;
+            dV[p] += -pr.tau * dv;
+        }
+    }
+}
+
+// Contiguous share of the task range for this CTA.
+__device__ __forceinline__ void my_range(int ntasks, int* s, int* e) {
+    *s = (int)(((long long)blockIdx.x * ntasks) / gridDim.x);
+    *e = (int)(((long long)(blockIdx.x + 1) * ntasks) / gridDim.x);
+}
+
+template <typename T, int VG>
+__global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant__ EngineArgs gA,
+                                                           const __grid_constant__ IOArgs gio) {
+    typedef Phases<T, VG> P;
+    extern __shared__ int dyn[];
+    __shared__ Smem sm;
+    if (threadIdx.x == 0) sm.A = gA;
+    for (int q = threadIdx.x; q < kMaxBatch; q += kBlock) {
+        sm.io.in[q] = gio.in[q];
+        sm.io.out[q] = gio.out[q];
+        sm.io.gout[q] = gio.gout[q];
+        sm.io.dLdV[q] = gio.dLdV[q];
+    }
+    __syncthreads();
+    const EngineArgs& A = sm.A;
+    int* list = dyn;
+    int* prefix = dyn + A.nitems;
+    const int warp = threadIdx.x >> 5;
+    const int gwarp = blockIdx.x * kWarps + warp;
+    const int nwarps = gridDim.x * kWarps;
+
+    for (int sub = 0; sub < A.max_sub; ++sub) {
+        // substep start: every item of a live problem needs a first residual
+        for (int i = blockIdx.x * kBlock + threadIdx.x; i < A.nitems; i += gridDim.x * kBlock) {
+            const ItemDesc& it = A.item[i];
+            ItemState* S = it.st;
+            S->cycles = 0;
+            S->total_iters = 0;
+            S->sum_k2 = 0;
+            S->k = 0;
+            S->status = sub < A.prob[it.problem].nsub ? ST_NEED_RES : ST_IDLE;
+        }
+        if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+
+        for (;;) {
+            build_list(sm, list, prefix, (1u << ST_NEED_RES) | (1u << ST_CYCLE_END));
+            if (sm.nl == 0) break;
+            {
+                int s, e;
+                my_range(sm.ntasks, &s, &e);
+                for (int t = s; t < e; ++t) {
+                    const int l = find_slot(prefix, sm.nl, t);
+                    P::e3(sm, sub, list[l], t - prefix[l]);
+                }
+            }
+            if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+            for (int l = gwarp; l < sm.nl; l += nwarps) item_e4(A, list[l]);
+            if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+
+            for (int j = 0; j < A.m; ++j) {
+                build_list(sm, list, prefix, 1u << ST_ARNOLDI);
+                if (sm.nl == 0) break;
+                int s, e;
+                my_range(sm.ntasks, &s, &e);
+                for (int t = s; t < e; ++t) {
+                    const int l = find_slot(prefix, sm.nl, t);
+                    P::p1(sm, list[l], t - prefix[l], j);
+                }
+                if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+                int cur = -1;
+                for (int t = s; t < e; ++t) {
+                    const int l = find_slot(prefix, sm.nl, t);
+                    if (list[l] != cur) { cur = list[l]; P::p2_pro(sm, cur, j); }
+                    P::p2(sm, cur, t - prefix[l], j);
+                }
+                if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+                cur = -1;
+                for (int t = s; t < e; ++t) {
+                    const int l = find_slot(prefix, sm.nl, t);
+                    if (list[l] != cur) { cur = list[l]; P::p3_pro(sm, cur, j); }
+                    P::p3(sm, cur, t - prefix[l], j);
+                }
+                if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+                for (int l = gwarp; l < sm.nl; l += nwarps) item_p4(A, list[l], j);
+                if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+            }
+
+            build_list(sm, list, prefix, 1u << ST_CYCLE_END);
+            if (sm.nl > 0) {
+                int s, e;
+                my_range(sm.ntasks, &s, &e);
+                int cur = -1;
+                for (int t = s; t < e; ++t) {
+                    const int l = find_slot(prefix, sm.nl, t);
+                    if (list[l] != cur) { cur = list[l]; P::e2_pro(sm, cur); }
+                    P::e2(sm, cur, t - prefix[l]);
+                }
+                if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+            }
+        }
+
+        if (A.mode != MODE_SOLVE) {
+            build_problem_list(sm, list, prefix, sub);
+            int s, e;
+            my_range(sm.ntasks, &s, &e);
+            for (int t = s; t < e; ++t) {
+                const int l = find_slot(prefix, sm.nl, t);
+                if (A.mode == MODE_STEP) task_pole_sum(A, sm.io, list[l], t - prefix[l], sub);
+                else task_adjoint(A, sm.io, list[l], t - prefix[l], sub);
+            }
+            if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+        }
+    }
+}
+
+// ---- single-stage kernels ------------------------------------------------------
+
+// w_k = A_k v_k for all poles (FP64): grid (ceil(n / kBlock), K).
+__global__ void __launch_bounds__(kBlock) apply_kernel(const ProblemDesc* __restrict__ prob,
+                                                       const ItemDesc* __restrict__ items,
+                                                       const double2* __restrict__ v,
+                                                       double2* __restrict__ w, int n) {
+    const int p = blockIdx.x * kBlock + threadIdx.x;
+    const int k = blockIdx.y;
+    if (p >= n) return;
+    const ProblemDesc& pr = *prob;
+    const double2* vk = v + (size_t)k * n;
+    w[(size_t)k * n + p] = stencil_apply<double, double2>(vk, p, pr, pr.diag, pr.a[0], pr.a[1], pr.a[2],
+                                                          items[k].shift);
+}
+
+__global__ void __launch_bounds__(kBlock) pole_sum_kernel(const ProblemDesc* __restrict__ prob,
+                                                          const double2* __restrict__ psi,
+                                                          const double2* __restrict__ x,
+                                                          double2* __restrict__ out, int n, int K) {
+    const int p = blockIdx.x * kBlock + threadIdx.x;
+    if (p >= n) return;
+    const ProblemDesc& pr = *prob;
+    double2 acc = cmul(pr.alpha0, psi[p]);
+    for (int k = 0; k < K; ++k) acc = cadd(acc, cmul(pr.alpha[k], x[(size_t)k * n + p]));
+    out[p] = acc;
+}
+
+}  // namespace
+
+size_t engine_smem_bytes(int nitems) { return (size_t)(2 * nitems + 2) * sizeof(int); }
+
+static void* engine_fn(bool fp32) {
+    return fp32 ? (void*)engine_kernel<float, 32> : (void*)engine_kernel<double, 16>;
+}
+
+int engine_max_grid(bool fp32, size_t smem, int device) {
+    void* fn = engine_fn(fp32);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(64 * 1024)) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kBlock, smem) != cudaSuccess) return 0;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    return nb * sms;
+}
+
+cudaError_t launch_engine(bool fp32, const EngineArgs& a, const IOArgs& io, int grid, size_t smem,
+                          cudaStream_t stream) {
+    void* fn = engine_fn(fp32);
+    void* args[] = {(void*)&a, (void*)&io};
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, smem, stream);
+}
+
+cudaError_t launch_apply(const ProblemDesc* dprob, const ItemDesc* ditems, int K, const double2* v,
+                         double2* w, int n, cudaStream_t stream) {
+    dim3 grid((n + kBlock - 1) / kBlock, K);
+    apply_kernel<<<grid, kBlock, 0, stream>>>(dprob, ditems, v, w, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pole_sum(const ProblemDesc* dprob, const double2* psi, const double2* x, double2* out,
+                            int n, int K, cudaStream_t stream) {
+    pole_sum_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, stream>>>(dprob, psi, x, out, n, K);
+    return cudaGetLastError();
+}
+
+}  // namespace rexi

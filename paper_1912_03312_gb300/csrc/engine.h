@@ -1,0 +1,129 @@
+// Device-side descriptors of the persistent REXI engine (shared by the kernel
+// translation unit and the host API).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace rexi {
+
+constexpr int kBlock = 256;            // threads per CTA
+constexpr int kPPT = 16;               // points per thread per task
+constexpr int kTile = kBlock * kPPT;   // points per (item, tile) task
+constexpr int kMaxM = 32;              // largest restart length (dot accumulators live in registers)
+constexpr int kMaxItems = 4096;        // items (shifted solves) per launch
+constexpr int kMaxBatch = 128;         // problems per launch
+
+// item status values
+enum : int {
+    ST_NEED_RES = 0,   // FP64 residual (refinement) due
+    ST_ARNOLDI = 1,    // inside an Arnoldi cycle
+    ST_CYCLE_END = 2,  // cycle finished: x update due
+    ST_CONVERGED = 3,
+    ST_FAILED = 4,
+    ST_IDLE = 5,       // not part of the current substep
+};
+
+// kernel modes
+enum : int {
+    MODE_STEP = 0,       // substeps of Eq. (5): solves + pole sum
+    MODE_SOLVE = 1,      // one set of solves, x left in the item buffers
+    MODE_BACKWARD = 2,   // adjoint substeps: 2K solves + adjoint accumulation
+};
+
+struct ProblemDesc {
+    int n, nx, ny, nz;
+    int ntiles;
+    int K;               // poles of this problem (items per substep: K, or 2K backward)
+    int item0;           // first item of this problem in the launch
+    int nitems;          // items of this problem
+    int nsub;            // substeps to run
+    int pad0;
+    double a[3];         // stencil coefficients -tau hbar^2 / (2 m h_d^2) (0 for unused dims)
+    float af[3];
+    float pad1;
+    double tau;
+    double2 alpha0;
+    const double2* alpha;      // device [K]
+    const double* diag;        // device [n]: tau (V - c) - 2 sum_d a_d
+    const float* diagf;        // device [n], float copy (mixed precision)
+    double2* tmp0;             // ping-pong state buffer (c128)
+    double2* tmp1;             // ping-pong state buffer (c128)
+    double2* ckpt;             // backward: [nsub][n] forward states (ckpt[0] unused)
+};
+
+// Per-call buffers, passed by value in the kernel parameters.
+struct IOArgs {
+    const double2* in[kMaxBatch];     // step input / solve rhs / psi_n (backward)
+    double2* out[kMaxBatch];          // step output / grad_in (backward)
+    const double2* gout[kMaxBatch];   // backward: G at the step output
+    double* dLdV[kMaxBatch];          // backward: accumulated gradient
+};
+
+struct ItemDesc {
+    int problem;
+    int pole;            // pole index k
+    int adjoint;         // 1: solve with conj shift against the adjoint state
+    int tile_off;        // first tile of this item in the partial buffers
+    int n;               // points of the item's problem
+    int ntiles;          // tiles of the item's problem
+    double2 shift;       // A = stencil + diag - shift
+    float2 shiftf;
+    double2* x;          // c128 [n]
+    void* basis;         // T2 [m+1][n]
+    struct ItemState* st;
+    struct ItemStats* stats;
+    double2* part1;      // [tiles][pv] partial dots, first CGS pass
+    double2* part2;      // [tiles][pv] partial dots, second CGS pass
+    double* partn;       // [tiles] partial squared norms
+};
+
+struct ItemState {
+    int status, k, total_iters, cycles;
+    int sub_iters, sub_cycles, sum_k2, pad;
+    double bnorm, beta, cycle_tol_abs, relres;
+    double s[kMaxM + 1];
+    double cs[kMaxM];
+    double2 sn[kMaxM];
+    double2 g[kMaxM + 1];
+    double2 hcol[kMaxM + 1];
+    double2 R[kMaxM * (kMaxM + 1) / 2];    // packed upper triangle, column j at j(j+1)/2
+};
+
+// Per-call statistics of one item (zeroed before every launch).
+struct ItemStats {
+    int iters, cycles, failed, max_sub_iters;
+    double resid;
+    int iters_sq, pad;        // sum over cycles of (cycle length)^2
+};
+
+struct EngineArgs {
+    int mode;
+    int nproblems;
+    int nitems;
+    int m;               // restart length
+    int max_iters;
+    int max_sub;         // largest nsub over problems
+    int pv;              // pitch of the partial buffers (>= m)
+    int pad;
+    double tol;          // relative residual target
+    double inner_tol;    // relative reduction per cycle (mixed), 0 = none
+    unsigned long long timeout_ns;
+    const ProblemDesc* prob;
+    const ItemDesc* item;
+    unsigned* bar;       // [2]: count, generation
+    int* err;            // sticky error word
+};
+
+// Launch the persistent kernel; T = float (mixed) or double (fp64).
+cudaError_t launch_engine(bool fp32_basis, const EngineArgs& args, const IOArgs& io, int grid,
+                          size_t smem, cudaStream_t stream);
+int engine_max_grid(bool fp32_basis, size_t smem, int device);
+size_t engine_smem_bytes(int nitems);
+
+// Single-stage kernels.
+cudaError_t launch_apply(const ProblemDesc* dprob, const ItemDesc* ditems, int K, const double2* v,
+                         double2* w, int n, cudaStream_t stream);
+cudaError_t launch_pole_sum(const ProblemDesc* dprob, const double2* psi, const double2* x,
+                            double2* out, int n, int K, cudaStream_t stream);
+
+}  // namespace rexi

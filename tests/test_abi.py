@@ -1,0 +1,127 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+* librexi.so builds for sm_103a and exports every function include/rexi.h declares;
+* the library's double-double FCF construction (Algorithms 1-2) agrees with the
+  oracle's 60-digit tables;
+* the default R1 rule (largest R1 with 2 sigma_{K+1} <= 1e-9) gives the radii of
+  the oracle tables;
+* argument validation happens before any device call.
+"""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import tables
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1912_03312_gb300 import build, _native
+    build.build()
+    return _native.load()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "rexi.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(rexi_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 15
+    for nm in names:
+        assert hasattr(lib, nm), nm
+
+
+def test_binding_covers_header():
+    from paper_1912_03312_gb300 import _native
+    assert sorted(_native.SIGNATURES) == header_functions()
+
+
+def test_struct_sizes_match_header(lib):
+    # rexi_options_default writes sizeof(rexi_options) bytes: a canary after the
+    # ctypes struct must survive.
+    from paper_1912_03312_gb300 import _native as N
+
+    class Guarded(C.Structure):
+        _fields_ = [("o", N.Options), ("canary", C.c_uint64)]
+
+    g = Guarded()
+    g.canary = 0x5A5A5A5A5A5A5A5A
+    assert lib.rexi_options_default(C.byref(g.o)) == 0
+    assert g.canary == 0x5A5A5A5A5A5A5A5A
+    assert g.o.restart_m == 30 and g.o.precision == N.REXI_MIXED and g.o.allow_substeps == 1
+
+
+@pytest.mark.parametrize("K,R1", [(8, 8.0), (12, 14.0), (16, 10.0), (16, 24.0), (32, 68.0)])
+def test_library_fcf_matches_oracle_tables(lib, K, R1):
+    import paper_1912_03312_gb300 as R
+    s, b, info = R.fcf(K, R1)
+    so, bo, meta = tables.poles(K, R1)
+    idx = [int(np.argmin(np.abs(so - x))) for x in s]
+    assert len(set(idx)) == K
+    assert np.max(np.abs(s - so[idx]) / np.abs(so[idx])) < 1e-13
+    assert np.max(np.abs(b - bo[idx]) / np.abs(bo[idx])) < 1e-12
+    assert abs(info["sigma_K1"] - meta["sigma_K+1"]) < 1e-6 * meta["sigma_K+1"]
+
+
+def test_default_radius_rule(lib):
+    import paper_1912_03312_gb300 as R
+    assert R.fcf(16)[2]["R1"] == 24.0
+    assert R.fcf(32)[2]["R1"] == 68.0
+
+
+def test_status_strings(lib):
+    from paper_1912_03312_gb300 import _native as N
+    for code in (0, -1, -2, -3, -4, -5, -6, 1):
+        assert N.status_string(code).startswith("REXI_")
+
+
+def test_argument_validation_before_device(lib):
+    from paper_1912_03312_gb300 import _native as N
+    g = N.Grid()
+    g.ndim = 1
+    g.n[0] = 8
+    g.lo[0] = -1.0
+    g.hi[0] = 1.0
+    g.hbar = 1.0
+    g.mass = 1.0
+    V = (C.c_double * 8)(*([0.0] * 8))
+    h = C.c_void_p()
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 0, None) == N.REXI_EINVAL      # K = 0
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, -0.1, 4, None) == N.REXI_EINVAL     # dt < 0
+    V[3] = float("nan")
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, None) == N.REXI_EINVAL      # NaN in V
+    V[3] = 0.0
+    g.hi[0] = -2.0
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, None) == N.REXI_EINVAL      # empty box
+    g.hi[0] = 1.0
+    o = N.Options()
+    lib.rexi_options_default(C.byref(o))
+    o.restart_m = 64
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    assert h.value is None
+
+
+def test_no_device_is_an_error_not_a_fallback(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1912_03312_gb300 import _native as N
+    g = N.Grid()
+    g.ndim = 1
+    g.n[0] = 8
+    g.lo[0] = -1.0
+    g.hi[0] = 1.0
+    g.hbar = 1.0
+    g.mass = 1.0
+    V = (C.c_double * 8)(*([0.0] * 8))
+    h = C.c_void_p()
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 8, None) == N.REXI_ECUDA

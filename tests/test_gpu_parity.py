@@ -1,0 +1,192 @@
+"""GPU parity of every hot-path stage against the oracle, through the C ABI.
+
+Sizes span several 4096-point tiles with ragged tails; 1D/2D/3D grids,
+dimensions of length 1 and 2 (degenerate periodic wraps), K = 8/16/32.
+Tolerances (relative L2):
+* stencil matvec and pole sum: 1e-13 (same arithmetic up to rounding order and
+  the 1e-14 agreement of the two FCF constructions);
+* per-pole solutions: 1e-10 (FP64) / 1e-6 (mixed), the oracle solving to 1e-14;
+* full step: max(1e-10, 0.2 A tol) for FP64 and max(1e-6, 0.2 A tol) for mixed,
+  where A = max sum|beta|/|w - sigma| is the pole-sum amplification (two
+  independent solvers with relative residual tol can differ by up to ~A tol).
+"""
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import operator as op
+from oracle import step as ostep
+
+from _common import OraclePlan, library_plan, relerr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_03312_gb300 import build
+    build.build()
+
+
+GRIDS = [(37,), (33, 20), (9, 7, 5), (5, 1, 3), (2, 17), (130, 101)]
+
+
+@pytest.mark.parametrize("n", GRIDS)
+def test_apply_poles_matches_oracle(n):
+    g, V, _ = wl.random_problem(31, n, box=6.0)
+    K, R1, dt = 8, 8.0, 0.3
+    lp = library_plan(g, V, dt, K, R1, precision="fp64")
+    orc = OraclePlan(g, V, dt, K, R1)
+    assert lp.info()["n_sub"] == orc.n_sub
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=(K,) + tuple(reversed(n))) + 1j * rng.normal(size=(K,) + tuple(reversed(n)))
+    w = lp.apply_poles(to_dev(v)).cpu().numpy()
+    for k in range(K):
+        ref = op.apply_shifted(v[k], V, orc.h, orc.tau, orc.z[k])
+        assert relerr(w[k], ref) < 1e-13, k
+
+
+def test_poles_and_weights_match_oracle_mapping():
+    g, V, _ = wl.random_problem(32, (40, 30), box=8.0)
+    lp = library_plan(g, V, 0.7, 16, 24.0, precision="fp64")
+    orc = OraclePlan(g, V, 0.7, 16, 24.0)
+    z, alpha, a0, ns = lp.poles()
+    assert ns == orc.n_sub and a0 == 0
+    idx = [int(np.argmin(np.abs(orc.z - zk))) for zk in z]
+    assert np.max(np.abs(z - orc.z[idx]) / np.abs(orc.z[idx])) < 1e-13
+    assert np.max(np.abs(alpha - orc.alpha[idx]) / np.abs(orc.alpha[idx])) < 1e-12
+
+
+@pytest.mark.parametrize("n", [(37,), (130, 101)])
+def test_pole_sum_matches_oracle(n):
+    g, V, psi = wl.random_problem(33, n, box=6.0)
+    K, R1 = 16, 24.0
+    lp = library_plan(g, V, 0.4, K, R1, precision="fp64")
+    z, alpha, a0, _ = lp.poles()
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(K,) + psi.shape) + 1j * rng.normal(size=(K,) + psi.shape)
+    out = lp.pole_sum(to_dev(psi), to_dev(x)).cpu().numpy()
+    ref = a0 * psi + np.tensordot(alpha, x, axes=(0, 0))
+    assert relerr(out, ref) < 1e-13
+
+
+@pytest.mark.parametrize("precision,tol_pole", [("fp64", 1e-10), ("mixed", 1e-6)])
+@pytest.mark.parametrize("n", [(300,), (130, 101), (16, 12, 10)])
+def test_solve_poles_matches_oracle(precision, tol_pole, n):
+    g, V, psi = wl.random_problem(34, n, box=8.0)
+    K, R1, dt = 16, 24.0, 0.5
+    lp = library_plan(g, V, dt, K, R1, precision=precision, tol=1e-13)
+    orc = OraclePlan(g, V, dt, K, R1)
+    x, st = lp.solve_poles(to_dev(psi), stats=True)
+    assert st["status"] == 0, st
+    x = x.cpu().numpy()
+    z, _, _, _ = lp.poles()
+    for k in range(K):
+        kk = int(np.argmin(np.abs(orc.z - z[k])))
+        xo, info = ostep.solve_pole(V, orc.h, psi, orc.tau, orc.z[kk], tol=1e-14)
+        assert relerr(x[k], xo) < tol_pole, (k, relerr(x[k], xo))
+        assert st["resid"][k] <= 1e-13
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("K,R1,n,dt", [(8, 8.0, (130, 101), 0.4), (16, 24.0, (300,), 1.0),
+                                       (16, 24.0, (20, 18, 14), 0.3), (32, 68.0, (96, 80), 0.5)])
+def test_step_matches_oracle(precision, K, R1, n, dt):
+    g, V, psi = wl.random_problem(35, n, box=8.0)
+    tol = 1e-13
+    lp = library_plan(g, V, dt, K, R1, precision=precision, tol=tol)
+    orc = OraclePlan(g, V, dt, K, R1)
+    out, st = lp.step(to_dev(psi), stats=True)
+    assert st["status"] == 0 and st["n_sub"] == orc.n_sub
+    ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
+    floor = 1e-10 if precision == "fp64" else 1e-6
+    bound = max(floor, 0.2 * orc.A * tol)
+    err = relerr(out.cpu().numpy(), ref)
+    assert err < bound, (err, bound, orc.A)
+
+
+def test_step_in_place_and_host_buffers_agree():
+    g, V, psi = wl.random_problem(36, (64, 48), box=8.0)
+    lp = library_plan(g, V, 0.5, 16, 24.0, precision="mixed", tol=1e-12)
+    a = lp.step(to_dev(psi)).cpu().numpy()
+    buf = to_dev(psi)
+    lp.step(buf, out=buf)
+    b = buf.cpu().numpy()
+    c = lp.step_host(psi)
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, c)
+
+
+def test_zero_state_and_plane_wave_exactness():
+    # A plane wave is an exact eigenvector: the step multiplies it by the scalar
+    # alpha_0 + sum alpha_k / (tau lambda - z_k) of Eq. (4)-(5).
+    n = (512, 512)
+    g = wl.make_grid(n, (-30.0, -30.0), (30.0, 30.0))
+    V = np.full((512, 512), -0.8)
+    lp = library_plan(g, V, 0.5, 32, 68.0, precision="mixed", tol=4e-14)
+    X = wl.coords(g)
+    mx, my = 5, -3
+    psi = np.exp(1j * (2 * np.pi * mx * (X[0] + 30.0) / 60.0 + 2 * np.pi * my * (X[1] + 30.0) / 60.0))
+    out, st = lp.step(to_dev(psi), stats=True)
+    assert st["status"] == 0
+    z, alpha, a0, ns = lp.poles()
+    h = 60.0 / 512
+    lam = -0.8 + 0.5 * ((2 - 2 * np.cos(2 * np.pi * mx / 512)) + (2 - 2 * np.cos(2 * np.pi * my / 512))) / h ** 2
+    tau = lp.info()["tau"]
+    r = a0 + np.sum(alpha / (tau * lam - z))
+    expect = psi * r ** ns
+    info = lp.info()
+    assert relerr(out.cpu().numpy(), expect) < max(1e-9, 0.2 * info["amplification"] * info["tol"] * ns)
+    assert abs(abs(r ** ns) - 1.0) < 1e-7 and abs(r ** ns - np.exp(-1j * 0.5 * lam)) < 1e-7
+    zero = lp.step(torch.zeros_like(to_dev(psi)))
+    assert float(zero.abs().max()) == 0.0
+
+
+def test_batched_equals_single_and_oracle():
+    specs = [((130, 101), 16, 24.0, 0.5), ((64,), 16, 24.0, 1.0), ((40, 36), 32, 68.0, 0.5),
+             ((12, 10, 8), 8, 8.0, 0.2)]
+    plans, psis, refs, singles = [], [], [], []
+    for i, (n, K, R1, dt) in enumerate(specs):
+        g, V, psi = wl.random_problem(40 + i, n, box=8.0)
+        lp = library_plan(g, V, dt, K, R1, precision="mixed", tol=1e-13)
+        plans.append(lp)
+        psis.append(to_dev(psi))
+        singles.append(lp.step(to_dev(psi)).cpu().numpy())
+        orc = OraclePlan(g, V, dt, K, R1)
+        ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
+        refs.append((ref, orc.A))
+    from paper_1912_03312_gb300 import step_batched
+    outs, sts = step_batched(plans, psis, stats=True)
+    for o, s1, (ref, A), st in zip(outs, singles, refs, sts):
+        assert st["status"] == 0
+        o = o.cpu().numpy()
+        assert np.array_equal(o, s1)                 # same arithmetic, independent of the grid split
+        assert relerr(o, ref) < max(1e-6, 0.2 * A * 1e-13)
+
+
+def test_nonconvergence_is_reported():
+    g, V, psi = wl.random_problem(50, (64, 40), box=8.0)
+    lp = library_plan(g, V, 0.5, 16, 24.0, precision="fp64", tol=1e-13, max_iters=2)
+    from paper_1912_03312_gb300._native import RexiError
+    with pytest.raises(RexiError) as e:
+        lp.step(to_dev(psi), stats=True)
+    assert e.value.code == -4
+    assert lp.last_status() == -4
+
+
+def test_nan_input_fails_cleanly():
+    g, V, psi = wl.random_problem(51, (32, 32), box=8.0)
+    lp = library_plan(g, V, 0.5, 8, 8.0, precision="mixed")
+    bad = psi.copy()
+    bad[3, 4] = np.nan
+    from paper_1912_03312_gb300._native import RexiError
+    with pytest.raises(RexiError) as e:
+        lp.step(to_dev(bad), stats=True)
+    assert e.value.code == -4
+    good = lp.step(to_dev(psi), stats=True)[1]          # the plan stays usable
+    assert good["status"] == 0
