@@ -213,6 +213,18 @@ int rexi_pole_sum(rexi_plan* plan, const void* psi, const void* x, void* out, vo
 /* Status of the last call on the plan (synchronises the plan's last stream). */
 int rexi_plan_last_status(rexi_plan* plan);
 
+/* Phase tracing.  rexi_plan_set_trace allocates room for `capacity` records
+ * (0 disables); afterwards every engine launch of the plan records, at each
+ * grid-wide barrier, the phase that ended there and the GPU global timer (ns).
+ * Phase codes: 0 substep start, 1 FP64 residual, 2 cycle decision, 3 matvec +
+ * first dot sweep, 4 second CGS sweep, 5 CGS update, 6 Givens, 7 x update,
+ * 8 pole sum / adjoint accumulation, 99 launch start.
+ * rexi_plan_read_trace synchronises the plan's last stream, copies up to cap
+ * (phase, ns) pairs of the last launch into out[2*cap] and returns how many
+ * were recorded (which may exceed cap), or a negative status. */
+int rexi_plan_set_trace(rexi_plan* plan, int capacity);
+int rexi_plan_read_trace(rexi_plan* plan, long long* out, int cap);
+
 /* Number of CUDA kernel launches issued by the last call on the plan. */
 int rexi_plan_last_launches(const rexi_plan* plan);
 

@@ -75,6 +75,8 @@ SIGNATURES = {
     "rexi_pole_sum": (C.c_int, [_P, _P, _P, _P, _P]),
     "rexi_plan_last_status": (C.c_int, [_P]),
     "rexi_plan_last_launches": (C.c_int, [_P]),
+    "rexi_plan_set_trace": (C.c_int, [_P, C.c_int]),
+    "rexi_plan_read_trace": (C.c_int, [_P, C.POINTER(C.c_longlong), C.c_int]),
     "rexi_status_string": (C.c_char_p, [C.c_int]),
 }
 

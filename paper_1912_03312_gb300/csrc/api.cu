@@ -84,6 +84,8 @@ struct rexi_plan {
     int last_launches = 0;
     cudaStream_t last_stream = nullptr;
     bool has_backward = false;
+    unsigned long long* d_trace = nullptr;
+    int trace_cap = 0;
     int generation = 0;                          // bumped when the item workspace moves
 };
 
@@ -278,6 +280,8 @@ EngineArgs base_args(const rexi_plan* p, int mode, const DescSet& set, int nprob
     A.item = set.d_items;
     A.bar = p->d_bar;
     A.err = p->d_err;
+    A.trace = p->trace_cap > 0 ? p->d_trace : nullptr;
+    A.trace_cap = p->trace_cap;
     return A;
 }
 
@@ -473,7 +477,9 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
         p->alpha[k] = I * g->hbar * beta * phase;
     }
     p->alpha0 = 0.0;
-    for (int d = 0; d < g->ndim; ++d) p->a[d] = -p->tau * g->hbar * g->hbar / (2.0 * g->mass * h[d] * h[d]);
+    // A dimension of length 1 contributes (u + u - 2u)/h^2 = 0 to the periodic Laplacian: drop it.
+    for (int d = 0; d < g->ndim; ++d)
+        p->a[d] = dims[d] > 1 ? -p->tau * g->hbar * g->hbar / (2.0 * g->mass * h[d] * h[d]) : 0.0;
     p->tol = opt.tol > 0.0 ? opt.tol
                            : std::max(2e-14, std::min(1e-10, 1e-6 / std::max(1.0, p->fcf.amplification)));
     p->ntiles = (p->n + rexi::kTile - 1) / rexi::kTile;
@@ -822,5 +828,31 @@ int rexi_plan_last_status(rexi_plan* p) {
 }
 
 int rexi_plan_last_launches(const rexi_plan* p) { return p ? p->last_launches : 0; }
+
+int rexi_plan_set_trace(rexi_plan* p, int capacity) {
+    if (!p || capacity < 0) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    if (capacity > p->trace_cap) {
+        int st = dalloc(p, &p->d_trace, (size_t)1 + 2 * (size_t)capacity);
+        if (st) return st;
+        if (cudaMemset(p->d_trace, 0, sizeof(unsigned long long)) != cudaSuccess) return REXI_ECUDA;
+    }
+    p->trace_cap = capacity;
+    return REXI_OK;
+}
+
+int rexi_plan_read_trace(rexi_plan* p, long long* out, int cap) {
+    if (!p || (cap > 0 && !out)) return REXI_EINVAL;
+    if (p->trace_cap <= 0 || !p->d_trace) return 0;
+    DeviceGuard guard(p->device);
+    unsigned long long count = 0;
+    if (cudaStreamSynchronize(p->last_stream) != cudaSuccess ||
+        cudaMemcpy(&count, p->d_trace, sizeof(count), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return REXI_ECUDA;
+    const int n = (int)std::min<unsigned long long>(count, (unsigned long long)std::min(cap, p->trace_cap));
+    if (n > 0 && cudaMemcpy(out, p->d_trace + 1, sizeof(long long) * 2 * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return REXI_ECUDA;
+    return (int)count;
+}
 
 }  // extern "C"

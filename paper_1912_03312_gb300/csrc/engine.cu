@@ -120,6 +120,21 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long timeout_ns
     return *(volatile int*)err == 0;
 }
 
+// Barrier that also timestamps the end of phase `code` (CTA 0 only).
+__device__ __forceinline__ bool phase_sync(const EngineArgs& A, int code, int* tcount) {
+    const bool ok = grid_sync(A.bar, A.err, A.timeout_ns);
+    if (A.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int c = *tcount;
+        if (c < A.trace_cap) {
+            A.trace[1 + 2 * c] = (unsigned long long)code;
+            A.trace[2 + 2 * c] = global_ns();
+            A.trace[0] = (unsigned long long)(c + 1);
+        }
+        *tcount = c + 1;
+    }
+    return ok;
+}
+
 // ---- reductions -------------------------------------------------------------
 
 // Transpose-reduce NV per-lane values across a warp: afterwards lane l holds
@@ -169,6 +184,8 @@ struct Smem {
     double2 Rsm[kMaxM * (kMaxM + 1) / 2];
     int cnt[kBlock];
     int tls[kBlock];
+    const double2* xptr[2 * kMaxPoles];
+    double2 alpha[kMaxPoles];
     int nl;
     int ntasks;
     int kk;                        // Arnoldi steps of the current item (E2)
@@ -398,35 +415,98 @@ template <typename T, int VG>
 struct Phases {
     typedef typename C2<T>::t V;
 
+    // Every thread owns points p0 + r * kBlock + threadIdx.x, r < kPPT, of a
+    // task; per basis vector all of its kPPT loads are independent, which keeps
+    // enough bytes in flight to stream from HBM.
+
     // E3: residual r = b - A x (FP64), stored as u_0; x = 0 on the first cycle.
     static __device__ void e3(Smem& sm, int sub, int item, int tile) {
         const EngineArgs& A = sm.A;
         const ItemDesc& it = A.item[item];
         const ProblemDesc& pr = A.prob[it.problem];
-        const ItemState* S = it.st;
-        const int cycles = ldi(&S->cycles);
+        const int cycles = ldi(&it.st->cycles);
         const double2* b = item_rhs(A.mode, sm.io, it, pr, sub);
         V* U = (V*)it.basis;
         double2* x = it.x;
         const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
         double acc = 0.0;
+        double2 rv[kPPT];
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            rv[r] = p < pend ? ldp(b + p) : make_double2(0.0, 0.0);
+        }
+        if (cycles == 0) {
+#pragma unroll
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                if (p < pend) x[p] = make_double2(0.0, 0.0);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                if (p < pend)
+                    rv[r] = csub(rv[r], stencil_apply<double, double2>(x, p, pr, pr.diag, pr.a[0], pr.a[1], pr.a[2],
+                                                                        it.shift));
+            }
+        }
+#pragma unroll
         for (int r = 0; r < kPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
             if (p < pend) {
-                double2 rv = ldp(b + p);
-                if (cycles == 0) {
-                    x[p] = make_double2(0.0, 0.0);
-                } else {
-                    const double2 ax = stencil_apply<double, double2>(x, p, pr, pr.diag, pr.a[0], pr.a[1],
-                                                                      pr.a[2], it.shift);
-                    rv = csub(rv, ax);
-                }
-                U[p] = cvt2<V>(rv);
-                acc += rv.x * rv.x + rv.y * rv.y;
+                U[p] = cvt2<V>(rv[r]);
+                acc += rv[r].x * rv[r].x + rv[r].y * rv[r].y;
             }
         }
         const double tot = cta_reduce_scalar(sm, acc);
         if (threadIdx.x == 0) it.partn[it.tile_off + tile] = tot;
+    }
+
+    // Partial dots conj(u_i) . w for i in [i0, min(i0 + VG, j + 1)), into part.
+    static __device__ void dots(Smem& sm, const ItemDesc& it, const V* U, const V (&w)[kPPT], int p0, int pend,
+                                int tile, int j, double2* part) {
+        const size_t n = (size_t)it.n;
+        for (int i0 = 0; i0 <= j; i0 += VG) {
+            T ar[VG], ai[VG];
+#pragma unroll
+            for (int q = 0; q < VG; ++q) {
+                T sr = T(0), si = T(0);
+                if (i0 + q <= j) {
+                    const V* uq = U + (size_t)(i0 + q) * n;
+#pragma unroll
+                    for (int r = 0; r < kPPT; ++r) {
+                        const int p = p0 + r * kBlock + threadIdx.x;
+                        const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                        sr += u.x * w[r].x + u.y * w[r].y;
+                        si += u.x * w[r].y - u.y * w[r].x;
+                    }
+                }
+                ar[q] = sr;
+                ai[q] = si;
+            }
+            const int nv = min(VG, j + 1 - i0);
+            const double2 v = cta_reduce_vec<VG, T>(sm, ar, ai, nv);
+            if (threadIdx.x < nv) part[(size_t)(it.tile_off + tile) * sm.A.pv + i0 + threadIdx.x] = v;
+        }
+    }
+
+    // w[r] -= sum_{q <= j} c_q u_q at the thread's points.
+    static __device__ void subtract(const Smem& sm, const V* U, size_t n, V (&w)[kPPT], int p0, int pend, int j) {
+#pragma unroll
+        for (int q = 0; q < kMaxM; ++q) {
+            if (q <= j) {
+                const V* uq = U + (size_t)q * n;
+                const V c = coef_at<V>(sm, q);
+#pragma unroll
+                for (int r = 0; r < kPPT; ++r) {
+                    const int p = p0 + r * kBlock + threadIdx.x;
+                    const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                    w[r].x -= c.x * u.x - c.y * u.y;
+                    w[r].y -= c.x * u.y + c.y * u.x;
+                }
+            }
+        }
     }
 
     // P1: w = A (s_j u_j) into slot j+1; p1_i = sum conj(u_i) w, i <= j.
@@ -443,42 +523,30 @@ struct Phases {
         const T* diag = prob_diag<T>(pr);
         const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
         const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
-        for (int i0 = 0; i0 <= j; i0 += VG) {
-            T ar[VG], ai[VG];
+        V w[kPPT];
 #pragma unroll
-            for (int q = 0; q < VG; ++q) { ar[q] = T(0); ai[q] = T(0); }
-            for (int r = 0; r < kPPT; ++r) {
-                const int p = p0 + r * kBlock + threadIdx.x;
-                if (p < pend) {
-                    V w;
-                    if (i0 == 0) {
-                        w = stencil_apply<T, V>(uj, p, pr, diag, a0, a1, a2, shift);
-                        w.x *= sj;
-                        w.y *= sj;
-                        wv[p] = w;
-                    } else {
-                        w = ldp(wv + p);
-                    }
-#pragma unroll
-                    for (int q = 0; q < VG; ++q) {
-                        if (i0 + q <= j) {
-                            const V u = ldp(U + (size_t)(i0 + q) * n + p);
-                            ar[q] += u.x * w.x + u.y * w.y;
-                            ai[q] += u.x * w.y - u.y * w.x;
-                        }
-                    }
-                }
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            if (p < pend) {
+                V v = stencil_apply<T, V>(uj, p, pr, diag, a0, a1, a2, shift);
+                v.x *= sj;
+                v.y *= sj;
+                w[r] = v;
+            } else {
+                w[r] = mk2(T(0), T(0));
             }
-            const int nv = min(VG, j + 1 - i0);
-            const double2 v = cta_reduce_vec<VG, T>(sm, ar, ai, nv);
-            if (threadIdx.x < nv) it.part1[(size_t)(it.tile_off + tile) * A.pv + i0 + threadIdx.x] = v;
         }
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            if (p < pend) wv[p] = w[r];
+        }
+        dots(sm, it, U, w, p0, pend, tile, j, it.part1);
     }
 
     // P2 prologue: h1_i = s_i sum p1_i; coefficients s_i h1_i of u_i.
     static __device__ void p2_pro(Smem& sm, int item, int j) {
-        const EngineArgs& A = sm.A;
-        const ItemDesc& it = A.item[item];
+        const ItemDesc& it = sm.A.item[item];
         load_scales(sm, it.st, j + 1);
         reduce_partials(sm, it.part1, it, j + 1, sm.ssm, sm.h1);
         if (threadIdx.x <= j) {
@@ -489,51 +557,26 @@ struct Phases {
         __syncthreads();
     }
 
-    // P2: w' = w - sum_i c_i u_i (not stored); p2_i = sum conj(u_i) w'.
+    // P2: w' = w - sum_i c_i u_i (registers only); p2_i = sum conj(u_i) w'.
     static __device__ void p2(Smem& sm, int item, int tile, int j) {
-        const EngineArgs& A = sm.A;
-        const ItemDesc& it = A.item[item];
+        const ItemDesc& it = sm.A.item[item];
         const size_t n = (size_t)it.n;
         const V* U = (const V*)it.basis;
         const V* wv = U + (size_t)(j + 1) * n;
         const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
-        for (int i0 = 0; i0 <= j; i0 += VG) {
-            T ar[VG], ai[VG];
+        V w[kPPT];
 #pragma unroll
-            for (int q = 0; q < VG; ++q) { ar[q] = T(0); ai[q] = T(0); }
-            for (int r = 0; r < kPPT; ++r) {
-                const int p = p0 + r * kBlock + threadIdx.x;
-                if (p < pend) {
-                    V w = ldp(wv + p);
-#pragma unroll
-                    for (int q = 0; q < kMaxM; ++q) {
-                        if (q <= j) {
-                            const V u = ldp(U + (size_t)q * n + p);
-                            const V c = coef_at<V>(sm, q);
-                            w.x -= c.x * u.x - c.y * u.y;
-                            w.y -= c.x * u.y + c.y * u.x;
-                        }
-                    }
-#pragma unroll
-                    for (int q = 0; q < VG; ++q) {
-                        if (i0 + q <= j) {
-                            const V u = ldp(U + (size_t)(i0 + q) * n + p);
-                            ar[q] += u.x * w.x + u.y * w.y;
-                            ai[q] += u.x * w.y - u.y * w.x;
-                        }
-                    }
-                }
-            }
-            const int nv = min(VG, j + 1 - i0);
-            const double2 v = cta_reduce_vec<VG, T>(sm, ar, ai, nv);
-            if (threadIdx.x < nv) it.part2[(size_t)(it.tile_off + tile) * A.pv + i0 + threadIdx.x] = v;
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            w[r] = p < pend ? ldp(wv + p) : mk2(T(0), T(0));
         }
+        subtract(sm, U, n, w, p0, pend, j);
+        dots(sm, it, U, w, p0, pend, tile, j, it.part2);
     }
 
     // P3 prologue: h = h1 + h2; coefficients s_i h_i.
     static __device__ void p3_pro(Smem& sm, int item, int j) {
-        const EngineArgs& A = sm.A;
-        const ItemDesc& it = A.item[item];
+        const ItemDesc& it = sm.A.item[item];
         load_scales(sm, it.st, j + 1);
         reduce_partials(sm, it.part1, it, j + 1, sm.ssm, sm.h1);
         reduce_partials(sm, it.part2, it, j + 1, sm.ssm, sm.h2);
@@ -549,29 +592,26 @@ struct Phases {
 
     // P3: w <- w - sum_i c_i u_i (stored), ||w||^2; tile 0 publishes the column.
     static __device__ void p3(Smem& sm, int item, int tile, int j) {
-        const EngineArgs& A = sm.A;
-        const ItemDesc& it = A.item[item];
+        const ItemDesc& it = sm.A.item[item];
         const size_t n = (size_t)it.n;
         V* U = (V*)it.basis;
         V* wv = U + (size_t)(j + 1) * n;
         if (tile == 0 && threadIdx.x <= j) it.st->hcol[threadIdx.x] = sm.h1[threadIdx.x];
         const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+        V w[kPPT];
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            w[r] = p < pend ? ldp(wv + p) : mk2(T(0), T(0));
+        }
+        subtract(sm, U, n, w, p0, pend, j);
         T acc = T(0);
+#pragma unroll
         for (int r = 0; r < kPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
             if (p < pend) {
-                V w = ldp(wv + p);
-#pragma unroll
-                for (int q = 0; q < kMaxM; ++q) {
-                    if (q <= j) {
-                        const V u = ldp(U + (size_t)q * n + p);
-                        const V c = coef_at<V>(sm, q);
-                        w.x -= c.x * u.x - c.y * u.y;
-                        w.y -= c.x * u.y + c.y * u.x;
-                    }
-                }
-                wv[p] = w;
-                acc += w.x * w.x + w.y * w.y;
+                wv[p] = w[r];
+                acc += w[r].x * w[r].x + w[r].y * w[r].y;
             }
         }
         const double tot = cta_reduce_scalar(sm, (double)acc);
@@ -600,35 +640,46 @@ struct Phases {
                 if (den > 0.0) y = cscale(cmul(acc, cconj(d)), 1.0 / den);
                 sm.h2[i] = y;                              // y_i
             }
-            for (int i = 0; i < k; ++i) sm.coef[i] = cscale(sm.h2[i], sm.ssm[i]);
+            for (int i = 0; i < k; ++i) {
+                const double2 c = cscale(sm.h2[i], sm.ssm[i]);
+                sm.coef[i] = c;
+                sm.coeff[i] = make_float2((float)c.x, (float)c.y);
+            }
         }
         __syncthreads();
     }
 
-    // E2: x += sum_i c_i u_i (FP64 accumulation).
+    // E2: x += sum_i c_i u_i.  The correction is accumulated in the basis
+    // precision (a cycle's correction is only accurate to the cycle's residual
+    // reduction) and added to x in FP64.
     static __device__ void e2(Smem& sm, int item, int tile) {
-        const EngineArgs& A = sm.A;
-        const ItemDesc& it = A.item[item];
+        const ItemDesc& it = sm.A.item[item];
         const size_t n = (size_t)it.n;
         const V* U = (const V*)it.basis;
         double2* x = it.x;
         const int k = sm.kk;
         const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+        V d[kPPT];
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) d[r] = mk2(T(0), T(0));
+#pragma unroll
+        for (int q = 0; q < kMaxM; ++q) {
+            if (q < k) {
+                const V* uq = U + (size_t)q * n;
+                const V c = coef_at<V>(sm, q);
+#pragma unroll
+                for (int r = 0; r < kPPT; ++r) {
+                    const int p = p0 + r * kBlock + threadIdx.x;
+                    const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                    d[r].x += c.x * u.x - c.y * u.y;
+                    d[r].y += c.x * u.y + c.y * u.x;
+                }
+            }
+        }
+#pragma unroll
         for (int r = 0; r < kPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
-            if (p < pend) {
-                double2 xv = ldp(x + p);
-#pragma unroll
-                for (int q = 0; q < kMaxM; ++q) {
-                    if (q < k) {
-                        const double2 u = up2(ldp(U + (size_t)q * n + p));
-                        const double2 c = sm.coef[q];
-                        xv.x += c.x * u.x - c.y * u.y;
-                        xv.y += c.x * u.y + c.y * u.x;
-                    }
-                }
-                x[p] = xv;
-            }
+            if (p < pend) x[p] = cadd(ldp(x + p), up2(d[r]));
         }
     }
 };
@@ -650,8 +701,8 @@ __device__ void item_e4(const EngineArgs& A, int item) {
     S->relres = relres;
     const int total = ldi(&S->total_iters);
     int status;
-    if (!(relres <= 1e300)) {
-        status = ST_FAILED;                         // NaN / Inf
+    if (!(beta <= 1e300) || !(bnorm <= 1e300) || !(relres <= 1e300)) {
+        status = ST_FAILED;                         // NaN / Inf in the data
     } else if (bnorm == 0.0 || relres <= A.tol) {
         status = ST_CONVERGED;
     } else if (total >= A.max_iters) {
@@ -732,46 +783,78 @@ __device__ void item_p4(const EngineArgs& A, int item, int j) {
     S->status = end ? ST_CYCLE_END : ST_ARNOLDI;
 }
 
+// Cache the solution pointers and weights of problem `prob` in shared memory.
+__device__ void load_problem_items(Smem& sm, int prob) {
+    const ProblemDesc& pr = sm.A.prob[prob];
+    const int nx = sm.A.mode == MODE_BACKWARD ? 2 * pr.K : pr.K;
+    for (int k = threadIdx.x; k < nx; k += kBlock) sm.xptr[k] = sm.A.item[pr.item0 + k].x;
+    for (int k = threadIdx.x; k < pr.K; k += kBlock) sm.alpha[k] = __ldg(pr.alpha + k);
+    __syncthreads();
+}
+
 // PS: psi' = alpha_0 b + sum_k alpha_k x_k for one tile of a problem.
-__device__ void task_pole_sum(const EngineArgs& A, const IOArgs& io, int prob, int tile, int sub) {
-    const ProblemDesc& pr = A.prob[prob];
-    const double2* b = step_in(io, pr, prob, sub);
-    double2* out = step_out(io, pr, prob, sub);
+__device__ void task_pole_sum(const Smem& sm, int prob, int tile, int sub) {
+    const ProblemDesc& pr = sm.A.prob[prob];
+    const double2* b = step_in(sm.io, pr, prob, sub);
+    double2* out = step_out(sm.io, pr, prob, sub);
     const int p0 = tile * kTile, pend = min(pr.n, p0 + kTile);
+    double2 acc[kPPT];
+#pragma unroll
     for (int r = 0; r < kPPT; ++r) {
         const int p = p0 + r * kBlock + threadIdx.x;
-        if (p < pend) {
-            double2 acc = cmul(pr.alpha0, ldp(b + p));
-            for (int k = 0; k < pr.K; ++k) {
-                const double2 al = __ldg(pr.alpha + k);
-                acc = cadd(acc, cmul(al, ldp(A.item[pr.item0 + k].x + p)));
-            }
-            out[p] = acc;
+        acc[r] = p < pend ? cmul(pr.alpha0, ldp(b + p)) : make_double2(0.0, 0.0);
+    }
+    for (int k = 0; k < pr.K; ++k) {
+        const double2* xk = sm.xptr[k];
+        const double2 al = sm.alpha[k];
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            if (p < pend) acc[r] = cadd(acc[r], cmul(al, ldp(xk + p)));
         }
+    }
+#pragma unroll
+    for (int r = 0; r < kPPT; ++r) {
+        const int p = p0 + r * kBlock + threadIdx.x;
+        if (p < pend) out[p] = acc[r];
     }
 }
 
 // BA: adjoint accumulation for one tile of a problem (backward substep bs).
-__device__ void task_adjoint(const EngineArgs& A, const IOArgs& io, int prob, int tile, int bs) {
-    const ProblemDesc& pr = A.prob[prob];
-    const double2* gin = adj_in(io, pr, prob, bs);
-    double2* gout = adj_out(io, pr, prob, bs);
-    double* dV = io.dLdV[prob];
+__device__ void task_adjoint(const Smem& sm, int prob, int tile, int bs) {
+    const ProblemDesc& pr = sm.A.prob[prob];
+    const double2* gin = adj_in(sm.io, pr, prob, bs);
+    double2* gout = adj_out(sm.io, pr, prob, bs);
+    double* dV = sm.io.dLdV[prob];
     const int p0 = tile * kTile, pend = min(pr.n, p0 + kTile);
+    double2 g[kPPT];
+    double dv[kPPT];
+#pragma unroll
+    for (int r = 0; r < kPPT; ++r) {
+        const int p = p0 + r * kBlock + threadIdx.x;
+        g[r] = p < pend ? cmul(cconj(pr.alpha0), ldp(gin + p)) : make_double2(0.0, 0.0);
+        dv[r] = 0.0;
+    }
+    for (int k = 0; k < pr.K; ++k) {
+        const double2* X = sm.xptr[k];
+        const double2* Y = sm.xptr[pr.K + k];
+        const double2 al = sm.alpha[k];
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            if (p < pend) {
+                const double2 xv = ldp(X + p), yv = ldp(Y + p);
+                g[r] = cadd(g[r], cmul(cconj(al), yv));
+                dv[r] += cmul(al, cmul(cconj(yv), xv)).x;
+            }
+        }
+    }
+#pragma unroll
     for (int r = 0; r < kPPT; ++r) {
         const int p = p0 + r * kBlock + threadIdx.x;
         if (p < pend) {
-            double2 g = cmul(cconj(pr.alpha0), ldp(gin + p));
-            double dv = 0.0;
-            for (int k = 0; k < pr.K; ++k) {
-                const double2 al = __ldg(pr.alpha + k);
-                const double2 X = ldp(A.item[pr.item0 + k].x + p);
-                const double2 Y = ldp(A.item[pr.item0 + pr.K + k].x + p);
-                g = cadd(g, cmul(cconj(al), Y));
-                dv += cmul(al, cmul(cconj(Y), X)).x;
-            }
-            gout[p] = g;
-            dV[p] += -pr.tau * dv;
+            gout[p] = g[r];
+            dV[p] += -pr.tau * dv[r];
         }
     }
 }
@@ -802,6 +885,18 @@ __global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant
     const int warp = threadIdx.x >> 5;
     const int gwarp = blockIdx.x * kWarps + warp;
     const int nwarps = gridDim.x * kWarps;
+    __shared__ int tcount;
+    if (threadIdx.x == 0) {
+        tcount = 0;
+        if (A.trace != nullptr && blockIdx.x == 0) A.trace[0] = 0ull;
+    }
+    __syncthreads();
+    if (A.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0 && A.trace_cap > 0) {
+        A.trace[1] = 99ull;                   // launch start marker
+        A.trace[2] = global_ns();
+        A.trace[0] = 1ull;
+        tcount = 1;
+    }
 
     for (int sub = 0; sub < A.max_sub; ++sub) {
         // substep start: every item of a live problem needs a first residual
@@ -814,7 +909,7 @@ __global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant
             S->k = 0;
             S->status = sub < A.prob[it.problem].nsub ? ST_NEED_RES : ST_IDLE;
         }
-        if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+        if (!phase_sync(A, TR_INIT, &tcount)) return;
 
         for (;;) {
             build_list(sm, list, prefix, (1u << ST_NEED_RES) | (1u << ST_CYCLE_END));
@@ -827,9 +922,9 @@ __global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant
                     P::e3(sm, sub, list[l], t - prefix[l]);
                 }
             }
-            if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+            if (!phase_sync(A, TR_E3, &tcount)) return;
             for (int l = gwarp; l < sm.nl; l += nwarps) item_e4(A, list[l]);
-            if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+            if (!phase_sync(A, TR_E4, &tcount)) return;
 
             for (int j = 0; j < A.m; ++j) {
                 build_list(sm, list, prefix, 1u << ST_ARNOLDI);
@@ -840,23 +935,23 @@ __global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant
                     const int l = find_slot(prefix, sm.nl, t);
                     P::p1(sm, list[l], t - prefix[l], j);
                 }
-                if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+                if (!phase_sync(A, TR_P1, &tcount)) return;
                 int cur = -1;
                 for (int t = s; t < e; ++t) {
                     const int l = find_slot(prefix, sm.nl, t);
                     if (list[l] != cur) { cur = list[l]; P::p2_pro(sm, cur, j); }
                     P::p2(sm, cur, t - prefix[l], j);
                 }
-                if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+                if (!phase_sync(A, TR_P2, &tcount)) return;
                 cur = -1;
                 for (int t = s; t < e; ++t) {
                     const int l = find_slot(prefix, sm.nl, t);
                     if (list[l] != cur) { cur = list[l]; P::p3_pro(sm, cur, j); }
                     P::p3(sm, cur, t - prefix[l], j);
                 }
-                if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+                if (!phase_sync(A, TR_P3, &tcount)) return;
                 for (int l = gwarp; l < sm.nl; l += nwarps) item_p4(A, list[l], j);
-                if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+                if (!phase_sync(A, TR_P4, &tcount)) return;
             }
 
             build_list(sm, list, prefix, 1u << ST_CYCLE_END);
@@ -869,7 +964,7 @@ __global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant
                     if (list[l] != cur) { cur = list[l]; P::e2_pro(sm, cur); }
                     P::e2(sm, cur, t - prefix[l]);
                 }
-                if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+                if (!phase_sync(A, TR_E2, &tcount)) return;
             }
         }
 
@@ -877,12 +972,14 @@ __global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant
             build_problem_list(sm, list, prefix, sub);
             int s, e;
             my_range(sm.ntasks, &s, &e);
+            int cur = -1;
             for (int t = s; t < e; ++t) {
                 const int l = find_slot(prefix, sm.nl, t);
-                if (A.mode == MODE_STEP) task_pole_sum(A, sm.io, list[l], t - prefix[l], sub);
-                else task_adjoint(A, sm.io, list[l], t - prefix[l], sub);
+                if (list[l] != cur) { cur = list[l]; load_problem_items(sm, cur); }
+                if (A.mode == MODE_STEP) task_pole_sum(sm, cur, t - prefix[l], sub);
+                else task_adjoint(sm, cur, t - prefix[l], sub);
             }
-            if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+            if (!phase_sync(A, TR_SUM, &tcount)) return;
         }
     }
 }

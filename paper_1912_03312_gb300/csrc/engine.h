@@ -7,11 +7,12 @@
 namespace rexi {
 
 constexpr int kBlock = 256;            // threads per CTA
-constexpr int kPPT = 16;               // points per thread per task
+constexpr int kPPT = 8;                // points per thread per task
 constexpr int kTile = kBlock * kPPT;   // points per (item, tile) task
 constexpr int kMaxM = 32;              // largest restart length (dot accumulators live in registers)
 constexpr int kMaxItems = 4096;        // items (shifted solves) per launch
 constexpr int kMaxBatch = 128;         // problems per launch
+constexpr int kMaxPoles = 256;         // poles per problem
 
 // item status values
 enum : int {
@@ -112,7 +113,14 @@ struct EngineArgs {
     const ItemDesc* item;
     unsigned* bar;       // [2]: count, generation
     int* err;            // sticky error word
+    unsigned long long* trace;   // optional: [1 + 2*cap] (count, then (phase, ns) pairs)
+    int trace_cap;
+    int pad2;
 };
+
+// phase codes recorded in the trace at the barrier that ends each phase
+enum : int { TR_INIT = 0, TR_E3 = 1, TR_E4 = 2, TR_P1 = 3, TR_P2 = 4, TR_P3 = 5, TR_P4 = 6, TR_E2 = 7,
+             TR_SUM = 8 };
 
 // Launch the persistent kernel; T = float (mixed) or double (fp64).
 cudaError_t launch_engine(bool fp32_basis, const EngineArgs& args, const IOArgs& io, int grid,

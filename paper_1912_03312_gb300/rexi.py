@@ -220,6 +220,34 @@ class Plan:
     def last_launches(self):
         return N.load().rexi_plan_last_launches(self._h)
 
+    PHASES = {0: "substep start", 1: "FP64 residual", 2: "cycle decision", 3: "matvec + dot sweep 1",
+              4: "CGS sweep 2", 5: "CGS update", 6: "Givens", 7: "x update", 8: "pole sum", 99: "launch"}
+
+    def set_trace(self, capacity=65536):
+        N.check(N.load().rexi_plan_set_trace(self._h, int(capacity)), "rexi_plan_set_trace")
+
+    def read_trace(self):
+        """[(phase code, seconds since the launch started)] of the last launch."""
+        cap = 1 << 16
+        buf = (C.c_longlong * (2 * cap))()
+        cnt = N.check(N.load().rexi_plan_read_trace(self._h, buf, cap), "rexi_plan_read_trace")
+        cnt = min(cnt, cap)
+        rec = [(int(buf[2 * i]), int(buf[2 * i + 1])) for i in range(cnt)]
+        if not rec:
+            return []
+        t0 = rec[0][1]
+        return [(c, (t - t0) * 1e-9) for c, t in rec]
+
+    def trace_summary(self):
+        """Total seconds and count per phase of the last launch."""
+        rec = self.read_trace()
+        out = {}
+        for (c0, t0), (c1, t1) in zip(rec, rec[1:]):
+            name = self.PHASES.get(c1, str(c1))
+            tot, cnt = out.get(name, (0.0, 0))
+            out[name] = (tot + (t1 - t0), cnt + 1)
+        return out
+
 
 def step_batched(plans, psis, outs=None, stream=None, stats=False):
     """One step of every problem in one persistent launch (``rexi_step_batched``)."""

