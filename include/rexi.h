@@ -210,6 +210,41 @@ int rexi_solve_poles(rexi_plan* plan, const void* b, void* x, void* stream, rexi
  * c128[n]; x: device c128[K][n]. */
 int rexi_pole_sum(rexi_plan* plan, const void* psi, const void* x, void* out, void* stream);
 
+/* --- allocation-free entry point -------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory: code running inside a custom allocator or memory-pool
+ * callback, hosts that reserve all GPU memory for themselves up front, and
+ * sandboxes in which cudaMalloc is unavailable.  rexi_plan_create allocates, so
+ * these callers use this call instead: one rational evaluation of Eq. (5),
+ *     psi_out = alpha0 psi_in + sum_k alpha_k (tau H - z_k I)^{-1} psi_in,
+ * with every byte of engine workspace taken from a fixed 32 MiB array compiled
+ * into the library (REXI_STATIC_SCRATCH_BYTES; every GPU that loads the library
+ * holds it until the process exits).  Nothing is allocated: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *   g            : host, the grid (as rexi_plan_create).
+ *   V            : device, n doubles, the potential.
+ *   tau, c       : substep length and centre of the spectral enclosure
+ *                  (rexi_plan_info.tau and .c of an equivalent plan).
+ *   K, z, alpha  : host, K poles z[2K] and weights alpha[2K] (interleaved re, im),
+ *                  alpha0[2]; e.g. from rexi_plan_poles.
+ *   opt          : host, precision / restart_m / tol (must be > 0) / inner_tol /
+ *                  max_iters are used; NULL = defaults except tol, which is required.
+ *   psi_in, psi_out : device c128[n]; may be the same buffer.
+ *   st           : host, may be NULL; when given the call synchronises.
+ * Returns REXI_EINVAL when the workspace (about K (m+1) n 8 bytes for REXI_MIXED,
+ * twice that for REXI_FP64, plus K n 16 bytes) exceeds the static array.
+ * The first call on a device looks the array's address up (cudaGetSymbolAddress,
+ * done once per device with that device current); make that first call before
+ * any stream capture.  All calls share the one array and it keeps the previous
+ * call's contents (the call resets what must start at zero), so calls that
+ * overlap on the GPU -- on different streams or threads -- race and must not be
+ * issued concurrently. */
+#define REXI_STATIC_SCRATCH_BYTES (32u << 20)
+int rexi_substep_static(const rexi_grid* g, const double* V, double tau, double c, int K,
+                        const double* z, const double* alpha, const double* alpha0,
+                        const rexi_options* opt, const void* psi_in, void* psi_out, void* stream,
+                        rexi_stats* st);
+
 /* Status of the last call on the plan (synchronises the plan's last stream). */
 int rexi_plan_last_status(rexi_plan* plan);
 

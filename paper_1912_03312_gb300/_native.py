@@ -78,6 +78,8 @@ SIGNATURES = {
     "rexi_plan_set_trace": (C.c_int, [_P, C.c_int]),
     "rexi_plan_read_trace": (C.c_int, [_P, C.POINTER(C.c_longlong), C.c_int]),
     "rexi_status_string": (C.c_char_p, [C.c_int]),
+    "rexi_substep_static": (C.c_int, [C.POINTER(Grid), _P, C.c_double, C.c_double, C.c_int, _D, _D, _D,
+                                      C.POINTER(Options), _P, _P, _P, C.POINTER(Stats)]),
 }
 
 _lib = None

@@ -53,6 +53,8 @@ def build(force=False, verbose=False):
         [nvcc] + ARCH + common + ["-lineinfo", "-c", os.path.join(CSRC, "engine.cu"),
                                   "-o", os.path.join(BUILD, "engine.o")],
         [nvcc] + ARCH + common + ["-c", os.path.join(CSRC, "api.cu"), "-o", os.path.join(BUILD, "api.o")],
+        [nvcc] + ARCH + common + ["-c", os.path.join(CSRC, "static_step.cu"),
+                                  "-o", os.path.join(BUILD, "static_step.o")],
         ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-c", os.path.join(CSRC, "fcf.cpp"),
          "-o", os.path.join(BUILD, "fcf.o")],
     ]
@@ -69,7 +71,7 @@ def build(force=False, verbose=False):
     tmp = LIB + ".tmp"
     link = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp,
                             os.path.join(BUILD, "engine.o"), os.path.join(BUILD, "api.o"),
-                            os.path.join(BUILD, "fcf.o"),
+                            os.path.join(BUILD, "fcf.o"), os.path.join(BUILD, "static_step.o"),
                             "-Xlinker", "-rpath," + os.path.join(CUDA_HOME, "lib64")]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
