@@ -387,23 +387,68 @@ __device__ __forceinline__ const double2* item_rhs(int mode, const IOArgs& io, c
 
 // ---- phases -------------------------------------------------------------------
 
-// out[i] = scale_i * sum_tiles part[tile][i], i < nv (nv <= 32).
-__device__ void reduce_partials(Smem& sm, const double2* part, const ItemDesc& it, int nv,
+// Partials are written once per "run": a maximal range of consecutive tiles of
+// one item inside one CTA's share of the task range, at the slot of the run's
+// first tile.  The partition (T tasks split evenly over G CTAs) is the same in
+// every CTA, so a consumer can enumerate the run starts of an item itself.
+__device__ __forceinline__ int range_start(int c, int T, int G) { return (int)(((long long)c * T) / G); }
+__device__ __forceinline__ int task_owner(int task, int T, int G) {
+    return (int)((((long long)task + 1) * G - 1) / T);
+}
+
+// Runs of list slot l: candidate r (0 <= r < count) is the run of CTA c0 + r,
+// starting at tile(r), or -1 when that CTA's share is empty (fewer tasks than
+// CTAs: several CTAs then have the same start and only the last one owns it).
+struct Runs {
+    int t0, c0, count, T, G;
+    __device__ __forceinline__ int tile(int r) const {
+        if (r == 0) return 0;
+        const int c = c0 + r;
+        const int st = range_start(c, T, G);
+        return st < range_start(c + 1, T, G) ? st - t0 : -1;
+    }
+};
+__device__ __forceinline__ Runs item_runs(const int* prefix, int l, int T) {
+    Runs R;
+    R.T = T;
+    R.G = gridDim.x;
+    R.t0 = prefix[l];
+    const int t1 = prefix[l + 1];
+    R.c0 = task_owner(R.t0, T, R.G);
+    R.count = task_owner(t1 - 1, T, R.G) - R.c0 + 1;
+    return R;
+}
+
+// out[i] = scale_i * sum over the runs of item slot l of part[run][i], i < nv (nv <= 32).
+__device__ void reduce_partials(Smem& sm, const double2* part, const ItemDesc& it, const Runs& R, int nv,
                                 const double* scale, double2* out) {
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
     double2 acc = make_double2(0.0, 0.0);
     if (lane < nv) {
-        for (int t = grp; t < it.ntiles; t += kWarps)
-            acc = cadd(acc, ldp(part + (size_t)(it.tile_off + t) * sm.A.pv + lane));
+        for (int r = grp; r < R.count; r += kWarps) {
+            const int tl = R.tile(r);
+            if (tl >= 0) acc = cadd(acc, ldp(part + (size_t)(it.tile_off + tl) * sm.A.pv + lane));
+        }
     }
     sm.red[grp][lane] = acc;
     __syncthreads();
     if (threadIdx.x < nv) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int g = 0; g < kWarps; ++g) s = cadd(s, sm.red[g][threadIdx.x]);
-        out[threadIdx.x] = cscale(s, scale[threadIdx.x]);
+        double2 s2 = make_double2(0.0, 0.0);
+        for (int g = 0; g < kWarps; ++g) s2 = cadd(s2, sm.red[g][threadIdx.x]);
+        out[threadIdx.x] = cscale(s2, scale[threadIdx.x]);
     }
     __syncthreads();
+}
+
+// Warp-level sum of the norm partials of item slot l (all lanes get the sum).
+__device__ __forceinline__ double warp_norm_partials(const ItemDesc& it, const Runs& R) {
+    const int lane = threadIdx.x & 31;
+    double ss = 0.0;
+    for (int r = lane; r < R.count; r += 32) {
+        const int tl = R.tile(r);
+        if (tl >= 0) ss += ldd(it.partn + it.tile_off + tl);
+    }
+    return warp_sum(ss);
 }
 
 __device__ __forceinline__ void load_scales(Smem& sm, const ItemState* S, int cnt) {
@@ -416,11 +461,12 @@ struct Phases {
     typedef typename C2<T>::t V;
 
     // Every thread owns points p0 + r * kBlock + threadIdx.x, r < kPPT, of a
-    // task; per basis vector all of its kPPT loads are independent, which keeps
-    // enough bytes in flight to stream from HBM.
+    // tile; per basis vector all of its kPPT loads are independent.  A CTA
+    // walks the tiles [tb, te) of one item (a run) accumulating its partial
+    // sums in registers and reduces them once per run.
 
     // E3: residual r = b - A x (FP64), stored as u_0; x = 0 on the first cycle.
-    static __device__ void e3(Smem& sm, int sub, int item, int tile) {
+    static __device__ void e3(Smem& sm, int sub, int item, int tb, int te) {
         const EngineArgs& A = sm.A;
         const ItemDesc& it = A.item[item];
         const ProblemDesc& pr = A.prob[it.problem];
@@ -428,71 +474,74 @@ struct Phases {
         const double2* b = item_rhs(A.mode, sm.io, it, pr, sub);
         V* U = (V*)it.basis;
         double2* x = it.x;
-        const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
         double acc = 0.0;
-        double2 rv[kPPT];
-#pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
-            const int p = p0 + r * kBlock + threadIdx.x;
-            rv[r] = p < pend ? ldp(b + p) : make_double2(0.0, 0.0);
-        }
-        if (cycles == 0) {
+        for (int tile = tb; tile < te; ++tile) {
+            const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+            double2 rv[kPPT];
 #pragma unroll
             for (int r = 0; r < kPPT; ++r) {
                 const int p = p0 + r * kBlock + threadIdx.x;
-                if (p < pend) x[p] = make_double2(0.0, 0.0);
+                rv[r] = p < pend ? ldp(b + p) : make_double2(0.0, 0.0);
             }
-        } else {
+            if (cycles == 0) {
+#pragma unroll
+                for (int r = 0; r < kPPT; ++r) {
+                    const int p = p0 + r * kBlock + threadIdx.x;
+                    if (p < pend) x[p] = make_double2(0.0, 0.0);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < kPPT; ++r) {
+                    const int p = p0 + r * kBlock + threadIdx.x;
+                    if (p < pend)
+                        rv[r] = csub(rv[r], stencil_apply<double, double2>(x, p, pr, pr.diag, pr.a[0], pr.a[1],
+                                                                            pr.a[2], it.shift));
+                }
+            }
 #pragma unroll
             for (int r = 0; r < kPPT; ++r) {
                 const int p = p0 + r * kBlock + threadIdx.x;
-                if (p < pend)
-                    rv[r] = csub(rv[r], stencil_apply<double, double2>(x, p, pr, pr.diag, pr.a[0], pr.a[1], pr.a[2],
-                                                                        it.shift));
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
-            const int p = p0 + r * kBlock + threadIdx.x;
-            if (p < pend) {
-                U[p] = cvt2<V>(rv[r]);
-                acc += rv[r].x * rv[r].x + rv[r].y * rv[r].y;
+                if (p < pend) {
+                    U[p] = cvt2<V>(rv[r]);
+                    acc += rv[r].x * rv[r].x + rv[r].y * rv[r].y;
+                }
             }
         }
         const double tot = cta_reduce_scalar(sm, acc);
-        if (threadIdx.x == 0) it.partn[it.tile_off + tile] = tot;
+        if (threadIdx.x == 0) it.partn[it.tile_off + tb] = tot;
     }
 
-    // Partial dots conj(u_i) . w for i in [i0, min(i0 + VG, j + 1)), into part.
-    static __device__ void dots(Smem& sm, const ItemDesc& it, const V* U, const V (&w)[kPPT], int p0, int pend,
-                                int tile, int j, double2* part) {
-        const size_t n = (size_t)it.n;
-        for (int i0 = 0; i0 <= j; i0 += VG) {
-            T ar[VG], ai[VG];
+    // ar/ai[q] += sum over the thread's points of conj(u_{i0+q}) w.
+    static __device__ __forceinline__ void accumulate_dots(const V* U, size_t n, const V (&w)[kPPT], int p0,
+                                                           int pend, int i0, int j, T (&ar)[VG], T (&ai)[VG]) {
 #pragma unroll
-            for (int q = 0; q < VG; ++q) {
+        for (int q = 0; q < VG; ++q) {
+            if (i0 + q <= j) {
+                const V* uq = U + (size_t)(i0 + q) * n;
                 T sr = T(0), si = T(0);
-                if (i0 + q <= j) {
-                    const V* uq = U + (size_t)(i0 + q) * n;
 #pragma unroll
-                    for (int r = 0; r < kPPT; ++r) {
-                        const int p = p0 + r * kBlock + threadIdx.x;
-                        const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
-                        sr += u.x * w[r].x + u.y * w[r].y;
-                        si += u.x * w[r].y - u.y * w[r].x;
-                    }
+                for (int r = 0; r < kPPT; ++r) {
+                    const int p = p0 + r * kBlock + threadIdx.x;
+                    const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                    sr += u.x * w[r].x + u.y * w[r].y;
+                    si += u.x * w[r].y - u.y * w[r].x;
                 }
-                ar[q] = sr;
-                ai[q] = si;
+                ar[q] += sr;
+                ai[q] += si;
             }
-            const int nv = min(VG, j + 1 - i0);
-            const double2 v = cta_reduce_vec<VG, T>(sm, ar, ai, nv);
-            if (threadIdx.x < nv) part[(size_t)(it.tile_off + tile) * sm.A.pv + i0 + threadIdx.x] = v;
         }
     }
 
+    static __device__ __forceinline__ void write_dots(Smem& sm, const ItemDesc& it, double2* part, int tb, int i0,
+                                                      int j, T (&ar)[VG], T (&ai)[VG]) {
+        const int nv = min(VG, j + 1 - i0);
+        const double2 v = cta_reduce_vec<VG, T>(sm, ar, ai, nv);
+        if (threadIdx.x < nv) part[(size_t)(it.tile_off + tb) * sm.A.pv + i0 + threadIdx.x] = v;
+    }
+
     // w[r] -= sum_{q <= j} c_q u_q at the thread's points.
-    static __device__ void subtract(const Smem& sm, const V* U, size_t n, V (&w)[kPPT], int p0, int pend, int j) {
+    static __device__ __forceinline__ void subtract(const Smem& sm, const V* U, size_t n, V (&w)[kPPT], int p0,
+                                                    int pend, int j) {
 #pragma unroll
         for (int q = 0; q < kMaxM; ++q) {
             if (q <= j) {
@@ -509,8 +558,16 @@ struct Phases {
         }
     }
 
+    static __device__ __forceinline__ void load_tile(const V* src, V (&w)[kPPT], int p0, int pend) {
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            w[r] = p < pend ? ldp(src + p) : mk2(T(0), T(0));
+        }
+    }
+
     // P1: w = A (s_j u_j) into slot j+1; p1_i = sum conj(u_i) w, i <= j.
-    static __device__ void p1(Smem& sm, int item, int tile, int j) {
+    static __device__ void p1(Smem& sm, int item, int tb, int te, int j) {
         const EngineArgs& A = sm.A;
         const ItemDesc& it = A.item[item];
         const ProblemDesc& pr = A.prob[it.problem];
@@ -522,33 +579,41 @@ struct Phases {
         const V shift = item_shift<V>(it);
         const T* diag = prob_diag<T>(pr);
         const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
-        const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
-        V w[kPPT];
+        for (int i0 = 0; i0 <= j; i0 += VG) {
+            T ar[VG], ai[VG];
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
-            const int p = p0 + r * kBlock + threadIdx.x;
-            if (p < pend) {
-                V v = stencil_apply<T, V>(uj, p, pr, diag, a0, a1, a2, shift);
-                v.x *= sj;
-                v.y *= sj;
-                w[r] = v;
-            } else {
-                w[r] = mk2(T(0), T(0));
+            for (int q = 0; q < VG; ++q) { ar[q] = T(0); ai[q] = T(0); }
+            for (int tile = tb; tile < te; ++tile) {
+                const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+                V w[kPPT];
+                if (i0 == 0) {
+#pragma unroll
+                    for (int r = 0; r < kPPT; ++r) {
+                        const int p = p0 + r * kBlock + threadIdx.x;
+                        if (p < pend) {
+                            V v = stencil_apply<T, V>(uj, p, pr, diag, a0, a1, a2, shift);
+                            v.x *= sj;
+                            v.y *= sj;
+                            w[r] = v;
+                            wv[p] = v;
+                        } else {
+                            w[r] = mk2(T(0), T(0));
+                        }
+                    }
+                } else {
+                    load_tile(wv, w, p0, pend);
+                }
+                accumulate_dots(U, n, w, p0, pend, i0, j, ar, ai);
             }
+            write_dots(sm, it, it.part1, tb, i0, j, ar, ai);
         }
-#pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
-            const int p = p0 + r * kBlock + threadIdx.x;
-            if (p < pend) wv[p] = w[r];
-        }
-        dots(sm, it, U, w, p0, pend, tile, j, it.part1);
     }
 
     // P2 prologue: h1_i = s_i sum p1_i; coefficients s_i h1_i of u_i.
-    static __device__ void p2_pro(Smem& sm, int item, int j) {
+    static __device__ void p2_pro(Smem& sm, int item, const Runs& R, int j) {
         const ItemDesc& it = sm.A.item[item];
         load_scales(sm, it.st, j + 1);
-        reduce_partials(sm, it.part1, it, j + 1, sm.ssm, sm.h1);
+        reduce_partials(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);
         if (threadIdx.x <= j) {
             const double2 c = cscale(sm.h1[threadIdx.x], sm.ssm[threadIdx.x]);
             sm.coef[threadIdx.x] = c;
@@ -558,28 +623,32 @@ struct Phases {
     }
 
     // P2: w' = w - sum_i c_i u_i (registers only); p2_i = sum conj(u_i) w'.
-    static __device__ void p2(Smem& sm, int item, int tile, int j) {
+    static __device__ void p2(Smem& sm, int item, int tb, int te, int j) {
         const ItemDesc& it = sm.A.item[item];
         const size_t n = (size_t)it.n;
         const V* U = (const V*)it.basis;
         const V* wv = U + (size_t)(j + 1) * n;
-        const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
-        V w[kPPT];
+        for (int i0 = 0; i0 <= j; i0 += VG) {
+            T ar[VG], ai[VG];
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
-            const int p = p0 + r * kBlock + threadIdx.x;
-            w[r] = p < pend ? ldp(wv + p) : mk2(T(0), T(0));
+            for (int q = 0; q < VG; ++q) { ar[q] = T(0); ai[q] = T(0); }
+            for (int tile = tb; tile < te; ++tile) {
+                const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+                V w[kPPT];
+                load_tile(wv, w, p0, pend);
+                subtract(sm, U, n, w, p0, pend, j);
+                accumulate_dots(U, n, w, p0, pend, i0, j, ar, ai);
+            }
+            write_dots(sm, it, it.part2, tb, i0, j, ar, ai);
         }
-        subtract(sm, U, n, w, p0, pend, j);
-        dots(sm, it, U, w, p0, pend, tile, j, it.part2);
     }
 
     // P3 prologue: h = h1 + h2; coefficients s_i h_i.
-    static __device__ void p3_pro(Smem& sm, int item, int j) {
+    static __device__ void p3_pro(Smem& sm, int item, const Runs& R, int j) {
         const ItemDesc& it = sm.A.item[item];
         load_scales(sm, it.st, j + 1);
-        reduce_partials(sm, it.part1, it, j + 1, sm.ssm, sm.h1);
-        reduce_partials(sm, it.part2, it, j + 1, sm.ssm, sm.h2);
+        reduce_partials(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);
+        reduce_partials(sm, it.part2, it, R, j + 1, sm.ssm, sm.h2);
         if (threadIdx.x <= j) {
             const double2 h = cadd(sm.h1[threadIdx.x], sm.h2[threadIdx.x]);
             sm.h1[threadIdx.x] = h;
@@ -590,32 +659,31 @@ struct Phases {
         __syncthreads();
     }
 
-    // P3: w <- w - sum_i c_i u_i (stored), ||w||^2; tile 0 publishes the column.
-    static __device__ void p3(Smem& sm, int item, int tile, int j) {
+    // P3: w <- w - sum_i c_i u_i (stored), ||w||^2; the run starting at tile 0
+    // publishes the Hessenberg column.
+    static __device__ void p3(Smem& sm, int item, int tb, int te, int j) {
         const ItemDesc& it = sm.A.item[item];
         const size_t n = (size_t)it.n;
         V* U = (V*)it.basis;
         V* wv = U + (size_t)(j + 1) * n;
-        if (tile == 0 && threadIdx.x <= j) it.st->hcol[threadIdx.x] = sm.h1[threadIdx.x];
-        const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
-        V w[kPPT];
-#pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
-            const int p = p0 + r * kBlock + threadIdx.x;
-            w[r] = p < pend ? ldp(wv + p) : mk2(T(0), T(0));
-        }
-        subtract(sm, U, n, w, p0, pend, j);
+        if (tb == 0 && threadIdx.x <= j) it.st->hcol[threadIdx.x] = sm.h1[threadIdx.x];
         T acc = T(0);
+        for (int tile = tb; tile < te; ++tile) {
+            const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+            V w[kPPT];
+            load_tile(wv, w, p0, pend);
+            subtract(sm, U, n, w, p0, pend, j);
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
-            const int p = p0 + r * kBlock + threadIdx.x;
-            if (p < pend) {
-                wv[p] = w[r];
-                acc += w[r].x * w[r].x + w[r].y * w[r].y;
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                if (p < pend) {
+                    wv[p] = w[r];
+                    acc += w[r].x * w[r].x + w[r].y * w[r].y;
+                }
             }
         }
         const double tot = cta_reduce_scalar(sm, (double)acc);
-        if (threadIdx.x == 0) it.partn[it.tile_off + tile] = tot;
+        if (threadIdx.x == 0) it.partn[it.tile_off + tb] = tot;
     }
 
     // E2 prologue: y = R^{-1} g (back substitution, FP64), coefficients y_i s_i.
@@ -652,46 +720,46 @@ struct Phases {
     // E2: x += sum_i c_i u_i.  The correction is accumulated in the basis
     // precision (a cycle's correction is only accurate to the cycle's residual
     // reduction) and added to x in FP64.
-    static __device__ void e2(Smem& sm, int item, int tile) {
+    static __device__ void e2(Smem& sm, int item, int tb, int te) {
         const ItemDesc& it = sm.A.item[item];
         const size_t n = (size_t)it.n;
         const V* U = (const V*)it.basis;
         double2* x = it.x;
         const int k = sm.kk;
-        const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
-        V d[kPPT];
+        for (int tile = tb; tile < te; ++tile) {
+            const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+            V d[kPPT];
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) d[r] = mk2(T(0), T(0));
+            for (int r = 0; r < kPPT; ++r) d[r] = mk2(T(0), T(0));
 #pragma unroll
-        for (int q = 0; q < kMaxM; ++q) {
-            if (q < k) {
-                const V* uq = U + (size_t)q * n;
-                const V c = coef_at<V>(sm, q);
+            for (int q = 0; q < kMaxM; ++q) {
+                if (q < k) {
+                    const V* uq = U + (size_t)q * n;
+                    const V c = coef_at<V>(sm, q);
 #pragma unroll
-                for (int r = 0; r < kPPT; ++r) {
-                    const int p = p0 + r * kBlock + threadIdx.x;
-                    const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
-                    d[r].x += c.x * u.x - c.y * u.y;
-                    d[r].y += c.x * u.y + c.y * u.x;
+                    for (int r = 0; r < kPPT; ++r) {
+                        const int p = p0 + r * kBlock + threadIdx.x;
+                        const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                        d[r].x += c.x * u.x - c.y * u.y;
+                        d[r].y += c.x * u.y + c.y * u.x;
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
-            const int p = p0 + r * kBlock + threadIdx.x;
-            if (p < pend) x[p] = cadd(ldp(x + p), up2(d[r]));
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                if (p < pend) x[p] = cadd(ldp(x + p), up2(d[r]));
+            }
         }
     }
 };
 
 // E4 (one warp per item): true relative residual, decide, start a cycle.
-__device__ void item_e4(const EngineArgs& A, int item) {
+__device__ void item_e4(const EngineArgs& A, int item, const Runs& R) {
     const int lane = threadIdx.x & 31;
     const ItemDesc& it = A.item[item];
     ItemState* S = it.st;
-    double ss = 0.0;
-    for (int t = lane; t < it.ntiles; t += 32) ss += ldd(it.partn + it.tile_off + t);
-    ss = warp_sum(ss);
+    const double ss = warp_norm_partials(it, R);
     if (lane != 0) return;
     const double beta = sqrt(ss);
     const int cycles = ldi(&S->cycles);
@@ -729,16 +797,14 @@ __device__ void item_e4(const EngineArgs& A, int item) {
 }
 
 // P4 (one warp per item): Givens rotations of the new Hessenberg column.
-__device__ void item_p4(const EngineArgs& A, int item, int j) {
+__device__ void item_p4(const EngineArgs& A, int item, const Runs& R, int j) {
     const int lane = threadIdx.x & 31;
     const ItemDesc& it = A.item[item];
     ItemState* S = it.st;
     const double2 hl = lane <= j ? ldp(&S->hcol[lane]) : make_double2(0.0, 0.0);
     const double csl = lane < j ? ldd(&S->cs[lane]) : 0.0;
     const double2 snl = lane < j ? ldp(&S->sn[lane]) : make_double2(0.0, 0.0);
-    double ss = 0.0;
-    for (int t = lane; t < it.ntiles; t += 32) ss += ldd(it.partn + it.tile_off + t);
-    ss = warp_sum(ss);
+    const double ss = warp_norm_partials(it, R);
     const double hn = sqrt(ss);                  // h_{j+1,j} = ||w||
     double2 carry = shfl2(hl, 0);
     const int col = j * (j + 1) / 2;
@@ -914,55 +980,58 @@ __global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant
         for (;;) {
             build_list(sm, list, prefix, (1u << ST_NEED_RES) | (1u << ST_CYCLE_END));
             if (sm.nl == 0) break;
-            {
-                int s, e;
-                my_range(sm.ntasks, &s, &e);
-                for (int t = s; t < e; ++t) {
-                    const int l = find_slot(prefix, sm.nl, t);
-                    P::e3(sm, sub, list[l], t - prefix[l]);
-                }
+            int s, e;
+            my_range(sm.ntasks, &s, &e);
+            for (int t = s; t < e;) {
+                const int l = find_slot(prefix, sm.nl, t);
+                const int te = min(prefix[l + 1], e) - prefix[l];
+                P::e3(sm, sub, list[l], t - prefix[l], te);
+                t = prefix[l] + te;
             }
             if (!phase_sync(A, TR_E3, &tcount)) return;
-            for (int l = gwarp; l < sm.nl; l += nwarps) item_e4(A, list[l]);
+            for (int l = gwarp; l < sm.nl; l += nwarps) item_e4(A, list[l], item_runs(prefix, l, sm.ntasks));
             if (!phase_sync(A, TR_E4, &tcount)) return;
 
             for (int j = 0; j < A.m; ++j) {
                 build_list(sm, list, prefix, 1u << ST_ARNOLDI);
                 if (sm.nl == 0) break;
-                int s, e;
                 my_range(sm.ntasks, &s, &e);
-                for (int t = s; t < e; ++t) {
+                for (int t = s; t < e;) {
                     const int l = find_slot(prefix, sm.nl, t);
-                    P::p1(sm, list[l], t - prefix[l], j);
+                    const int te = min(prefix[l + 1], e) - prefix[l];
+                    P::p1(sm, list[l], t - prefix[l], te, j);
+                    t = prefix[l] + te;
                 }
                 if (!phase_sync(A, TR_P1, &tcount)) return;
-                int cur = -1;
-                for (int t = s; t < e; ++t) {
+                for (int t = s; t < e;) {
                     const int l = find_slot(prefix, sm.nl, t);
-                    if (list[l] != cur) { cur = list[l]; P::p2_pro(sm, cur, j); }
-                    P::p2(sm, cur, t - prefix[l], j);
+                    const int te = min(prefix[l + 1], e) - prefix[l];
+                    P::p2_pro(sm, list[l], item_runs(prefix, l, sm.ntasks), j);
+                    P::p2(sm, list[l], t - prefix[l], te, j);
+                    t = prefix[l] + te;
                 }
                 if (!phase_sync(A, TR_P2, &tcount)) return;
-                cur = -1;
-                for (int t = s; t < e; ++t) {
+                for (int t = s; t < e;) {
                     const int l = find_slot(prefix, sm.nl, t);
-                    if (list[l] != cur) { cur = list[l]; P::p3_pro(sm, cur, j); }
-                    P::p3(sm, cur, t - prefix[l], j);
+                    const int te = min(prefix[l + 1], e) - prefix[l];
+                    P::p3_pro(sm, list[l], item_runs(prefix, l, sm.ntasks), j);
+                    P::p3(sm, list[l], t - prefix[l], te, j);
+                    t = prefix[l] + te;
                 }
                 if (!phase_sync(A, TR_P3, &tcount)) return;
-                for (int l = gwarp; l < sm.nl; l += nwarps) item_p4(A, list[l], j);
+                for (int l = gwarp; l < sm.nl; l += nwarps) item_p4(A, list[l], item_runs(prefix, l, sm.ntasks), j);
                 if (!phase_sync(A, TR_P4, &tcount)) return;
             }
 
             build_list(sm, list, prefix, 1u << ST_CYCLE_END);
             if (sm.nl > 0) {
-                int s, e;
                 my_range(sm.ntasks, &s, &e);
-                int cur = -1;
-                for (int t = s; t < e; ++t) {
+                for (int t = s; t < e;) {
                     const int l = find_slot(prefix, sm.nl, t);
-                    if (list[l] != cur) { cur = list[l]; P::e2_pro(sm, cur); }
-                    P::e2(sm, cur, t - prefix[l]);
+                    const int te = min(prefix[l + 1], e) - prefix[l];
+                    P::e2_pro(sm, list[l]);
+                    P::e2(sm, list[l], t - prefix[l], te);
+                    t = prefix[l] + te;
                 }
                 if (!phase_sync(A, TR_E2, &tcount)) return;
             }
