@@ -511,49 +511,113 @@ struct Phases {
         if (threadIdx.x == 0) it.partn[it.tile_off + tb] = tot;
     }
 
-    // ar/ai[q] += sum over the thread's points of conj(u_{i0+q}) w.
-    static __device__ __forceinline__ void accumulate_dots(const V* U, size_t n, const V (&w)[kPPT], int p0,
-                                                           int pend, int i0, int j, T (&ar)[VG], T (&ai)[VG]) {
+    // Dot sweeps: the tile of w sits in shared memory (ws); each warp owns up
+    // to 4 basis vectors (or, when there are fewer vectors than warps, a row
+    // range of one vector), so the per-lane accumulators stay in a few
+    // registers and a run needs one reduction.
+    struct DotPlan {
+        int nvec;
+        int q[4];
+        int row0, row1;        // rows of 32 points of the tile
+    };
+    static __device__ __forceinline__ DotPlan dot_plan(int J) {
+        const int wp = threadIdx.x >> 5;
+        constexpr int rows = kTile / 32;
+        DotPlan d;
+        d.nvec = 0;
+        if (J >= kWarps) {
 #pragma unroll
-        for (int q = 0; q < VG; ++q) {
-            if (i0 + q <= j) {
-                const V* uq = U + (size_t)(i0 + q) * n;
-                T sr = T(0), si = T(0);
+            for (int k = 0; k < 4; ++k) {
+                const int q = wp + kWarps * k;
+                d.q[k] = q;
+                if (q < J) d.nvec = k + 1;
+            }
+            d.row0 = 0;
+            d.row1 = rows;
+        } else {
+            const int vpw = kWarps / J;
+            const int q = wp / vpw;
+            d.q[0] = d.q[1] = d.q[2] = d.q[3] = q;
+            if (q < J) {
+                d.nvec = 1;
+                const int ch = wp - q * vpw;
+                d.row0 = ch * rows / vpw;
+                d.row1 = (ch + 1) * rows / vpw;
+            } else {
+                d.row0 = d.row1 = 0;
+            }
+        }
+        return d;
+    }
+
+    // acc[s] += sum over the warp's rows of conj(u_q) w for the warp's vectors.
+    static __device__ __forceinline__ void dot_tile(const V* U, size_t n, const V* ws, int p0, int pend,
+                                                    const DotPlan& d, T (&ar)[4], T (&ai)[4]) {
+        const int lane = threadIdx.x & 31;
+        for (int sl = 0; sl < d.nvec; ++sl) {
+            const V* uq = U + (size_t)d.q[sl] * n + p0;
+            T sr = T(0), si = T(0);
+            for (int row = d.row0; row < d.row1; row += 8) {
+                V u[8];
 #pragma unroll
-                for (int r = 0; r < kPPT; ++r) {
-                    const int p = p0 + r * kBlock + threadIdx.x;
-                    const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
-                    sr += u.x * w[r].x + u.y * w[r].y;
-                    si += u.x * w[r].y - u.y * w[r].x;
+                for (int k = 0; k < 8; ++k) {
+                    const int pl = (row + k) * 32 + lane;
+                    u[k] = (row + k < d.row1 && p0 + pl < pend) ? ldp(uq + pl) : mk2(T(0), T(0));
                 }
-                ar[q] += sr;
-                ai[q] += si;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int pl = (row + k) * 32 + lane;
+                    const V w = ws[pl & (kTile - 1)];
+                    sr += u[k].x * w.x + u[k].y * w.y;
+                    si += u[k].x * w.y - u[k].y * w.x;
+                }
+            }
+            // slot sl of this warp (fixed unrolled index to stay in registers)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k == sl) { ar[k] += sr; ai[k] += si; }
             }
         }
     }
 
-    static __device__ __forceinline__ void write_dots(Smem& sm, const ItemDesc& it, double2* part, int tb, int i0,
-                                                      int j, T (&ar)[VG], T (&ai)[VG]) {
-        const int nv = min(VG, j + 1 - i0);
-        const double2 v = cta_reduce_vec<VG, T>(sm, ar, ai, nv);
-        if (threadIdx.x < nv) part[(size_t)(it.tile_off + tb) * sm.A.pv + i0 + threadIdx.x] = v;
+    // End of a run: partial dots of the warps' vectors into part[tb][0..J).
+    static __device__ void dot_finish(Smem& sm, const ItemDesc& it, double2* part, int tb, int J,
+                                      const DotPlan& d, T (&ar)[4], T (&ai)[4]) {
+        const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const T r = warp_sum(ar[k]);
+            const T i = warp_sum(ai[k]);
+            if (lane == 0) sm.red[wp][k] = make_double2((double)r, (double)i);
+        }
+        __syncthreads();
+        if (threadIdx.x < J) {
+            const int q = threadIdx.x;
+            double2 acc = make_double2(0.0, 0.0);
+            if (J >= kWarps) {
+                acc = sm.red[q % kWarps][q / kWarps];
+            } else {
+                const int vpw = kWarps / J;
+                for (int w = q * vpw; w < (q + 1) * vpw; ++w) acc = cadd(acc, sm.red[w][0]);
+            }
+            part[(size_t)(it.tile_off + tb) * sm.A.pv + q] = acc;
+        }
+        __syncthreads();
     }
 
     // w[r] -= sum_{q <= j} c_q u_q at the thread's points.
     static __device__ __forceinline__ void subtract(const Smem& sm, const V* U, size_t n, V (&w)[kPPT], int p0,
                                                     int pend, int j) {
+#pragma unroll 2
+        for (int q = 0; q <= j; ++q) {
+            const V* uq = U + (size_t)q * n;
+            const V c = coef_at<V>(sm, q);
 #pragma unroll
-        for (int q = 0; q < kMaxM; ++q) {
-            if (q <= j) {
-                const V* uq = U + (size_t)q * n;
-                const V c = coef_at<V>(sm, q);
-#pragma unroll
-                for (int r = 0; r < kPPT; ++r) {
-                    const int p = p0 + r * kBlock + threadIdx.x;
-                    const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
-                    w[r].x -= c.x * u.x - c.y * u.y;
-                    w[r].y -= c.x * u.y + c.y * u.x;
-                }
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                w[r].x -= c.x * u.x - c.y * u.y;
+                w[r].y -= c.x * u.y + c.y * u.x;
             }
         }
     }
@@ -566,8 +630,13 @@ struct Phases {
         }
     }
 
+    static __device__ __forceinline__ void stage_tile(V* ws, const V (&w)[kPPT]) {
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) ws[r * kBlock + threadIdx.x] = w[r];
+    }
+
     // P1: w = A (s_j u_j) into slot j+1; p1_i = sum conj(u_i) w, i <= j.
-    static __device__ void p1(Smem& sm, int item, int tb, int te, int j) {
+    static __device__ void p1(Smem& sm, V* ws, int item, int tb, int te, int j) {
         const EngineArgs& A = sm.A;
         const ItemDesc& it = A.item[item];
         const ProblemDesc& pr = A.prob[it.problem];
@@ -579,34 +648,30 @@ struct Phases {
         const V shift = item_shift<V>(it);
         const T* diag = prob_diag<T>(pr);
         const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
-        for (int i0 = 0; i0 <= j; i0 += VG) {
-            T ar[VG], ai[VG];
+        const DotPlan d = dot_plan(j + 1);
+        T ar[4] = {T(0), T(0), T(0), T(0)}, ai[4] = {T(0), T(0), T(0), T(0)};
+        for (int tile = tb; tile < te; ++tile) {
+            const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+            V w[kPPT];
 #pragma unroll
-            for (int q = 0; q < VG; ++q) { ar[q] = T(0); ai[q] = T(0); }
-            for (int tile = tb; tile < te; ++tile) {
-                const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
-                V w[kPPT];
-                if (i0 == 0) {
-#pragma unroll
-                    for (int r = 0; r < kPPT; ++r) {
-                        const int p = p0 + r * kBlock + threadIdx.x;
-                        if (p < pend) {
-                            V v = stencil_apply<T, V>(uj, p, pr, diag, a0, a1, a2, shift);
-                            v.x *= sj;
-                            v.y *= sj;
-                            w[r] = v;
-                            wv[p] = v;
-                        } else {
-                            w[r] = mk2(T(0), T(0));
-                        }
-                    }
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                if (p < pend) {
+                    V v = stencil_apply<T, V>(uj, p, pr, diag, a0, a1, a2, shift);
+                    v.x *= sj;
+                    v.y *= sj;
+                    w[r] = v;
+                    wv[p] = v;
                 } else {
-                    load_tile(wv, w, p0, pend);
+                    w[r] = mk2(T(0), T(0));
                 }
-                accumulate_dots(U, n, w, p0, pend, i0, j, ar, ai);
             }
-            write_dots(sm, it, it.part1, tb, i0, j, ar, ai);
+            stage_tile(ws, w);
+            __syncthreads();
+            dot_tile(U, n, ws, p0, pend, d, ar, ai);
+            __syncthreads();
         }
+        dot_finish(sm, it, it.part1, tb, j + 1, d, ar, ai);
     }
 
     // P2 prologue: h1_i = s_i sum p1_i; coefficients s_i h1_i of u_i.
@@ -622,25 +687,25 @@ struct Phases {
         __syncthreads();
     }
 
-    // P2: w' = w - sum_i c_i u_i (registers only); p2_i = sum conj(u_i) w'.
-    static __device__ void p2(Smem& sm, int item, int tb, int te, int j) {
+    // P2: w' = w - sum_i c_i u_i (staged in shared memory); p2_i = sum conj(u_i) w'.
+    static __device__ void p2(Smem& sm, V* ws, int item, int tb, int te, int j) {
         const ItemDesc& it = sm.A.item[item];
         const size_t n = (size_t)it.n;
         const V* U = (const V*)it.basis;
         const V* wv = U + (size_t)(j + 1) * n;
-        for (int i0 = 0; i0 <= j; i0 += VG) {
-            T ar[VG], ai[VG];
-#pragma unroll
-            for (int q = 0; q < VG; ++q) { ar[q] = T(0); ai[q] = T(0); }
-            for (int tile = tb; tile < te; ++tile) {
-                const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
-                V w[kPPT];
-                load_tile(wv, w, p0, pend);
-                subtract(sm, U, n, w, p0, pend, j);
-                accumulate_dots(U, n, w, p0, pend, i0, j, ar, ai);
-            }
-            write_dots(sm, it, it.part2, tb, i0, j, ar, ai);
+        const DotPlan d = dot_plan(j + 1);
+        T ar[4] = {T(0), T(0), T(0), T(0)}, ai[4] = {T(0), T(0), T(0), T(0)};
+        for (int tile = tb; tile < te; ++tile) {
+            const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+            V w[kPPT];
+            load_tile(wv, w, p0, pend);
+            subtract(sm, U, n, w, p0, pend, j);
+            stage_tile(ws, w);
+            __syncthreads();
+            dot_tile(U, n, ws, p0, pend, d, ar, ai);
+            __syncthreads();
         }
+        dot_finish(sm, it, it.part2, tb, j + 1, d, ar, ai);
     }
 
     // P3 prologue: h = h1 + h2; coefficients s_i h_i.
@@ -731,18 +796,16 @@ struct Phases {
             V d[kPPT];
 #pragma unroll
             for (int r = 0; r < kPPT; ++r) d[r] = mk2(T(0), T(0));
+#pragma unroll 2
+            for (int q = 0; q < k; ++q) {
+                const V* uq = U + (size_t)q * n;
+                const V c = coef_at<V>(sm, q);
 #pragma unroll
-            for (int q = 0; q < kMaxM; ++q) {
-                if (q < k) {
-                    const V* uq = U + (size_t)q * n;
-                    const V c = coef_at<V>(sm, q);
-#pragma unroll
-                    for (int r = 0; r < kPPT; ++r) {
-                        const int p = p0 + r * kBlock + threadIdx.x;
-                        const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
-                        d[r].x += c.x * u.x - c.y * u.y;
-                        d[r].y += c.x * u.y + c.y * u.x;
-                    }
+                for (int r = 0; r < kPPT; ++r) {
+                    const int p = p0 + r * kBlock + threadIdx.x;
+                    const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                    d[r].x += c.x * u.x - c.y * u.y;
+                    d[r].y += c.x * u.y + c.y * u.x;
                 }
             }
 #pragma unroll
@@ -932,7 +995,7 @@ __device__ __forceinline__ void my_range(int ntasks, int* s, int* e) {
 }
 
 template <typename T, int VG>
-__global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant__ EngineArgs gA,
+__global__ void __launch_bounds__(kBlock, 3) engine_kernel(const __grid_constant__ EngineArgs gA,
                                                            const __grid_constant__ IOArgs gio) {
     typedef Phases<T, VG> P;
     extern __shared__ int dyn[];
@@ -948,6 +1011,8 @@ __global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant
     const EngineArgs& A = sm.A;
     int* list = dyn;
     int* prefix = dyn + A.nitems;
+    // tile staging buffer (16-byte aligned) after the list and prefix arrays
+    typename C2<T>::t* ws = (typename C2<T>::t*)(dyn + ((2 * A.nitems + 2 + 3) & ~3));
     const int warp = threadIdx.x >> 5;
     const int gwarp = blockIdx.x * kWarps + warp;
     const int nwarps = gridDim.x * kWarps;
@@ -999,7 +1064,7 @@ __global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant
                 for (int t = s; t < e;) {
                     const int l = find_slot(prefix, sm.nl, t);
                     const int te = min(prefix[l + 1], e) - prefix[l];
-                    P::p1(sm, list[l], t - prefix[l], te, j);
+                    P::p1(sm, ws, list[l], t - prefix[l], te, j);
                     t = prefix[l] + te;
                 }
                 if (!phase_sync(A, TR_P1, &tcount)) return;
@@ -1007,7 +1072,7 @@ __global__ void __launch_bounds__(kBlock, 2) engine_kernel(const __grid_constant
                     const int l = find_slot(prefix, sm.nl, t);
                     const int te = min(prefix[l + 1], e) - prefix[l];
                     P::p2_pro(sm, list[l], item_runs(prefix, l, sm.ntasks), j);
-                    P::p2(sm, list[l], t - prefix[l], te, j);
+                    P::p2(sm, ws, list[l], t - prefix[l], te, j);
                     t = prefix[l] + te;
                 }
                 if (!phase_sync(A, TR_P2, &tcount)) return;
@@ -1083,7 +1148,10 @@ __global__ void __launch_bounds__(kBlock) pole_sum_kernel(const ProblemDesc* __r
 
 }  // namespace
 
-size_t engine_smem_bytes(int nitems) { return (size_t)(2 * nitems + 2) * sizeof(int); }
+size_t engine_smem_bytes(int nitems) {
+    // list + prefix (ints, rounded to 16 bytes) + one tile of double2 for staging
+    return (size_t)((2 * nitems + 2 + 3) & ~3) * sizeof(int) + (size_t)kTile * sizeof(double2);
+}
 
 static void* engine_fn(bool fp32) {
     return fp32 ? (void*)engine_kernel<float, 32> : (void*)engine_kernel<double, 16>;
@@ -1091,7 +1159,7 @@ static void* engine_fn(bool fp32) {
 
 int engine_max_grid(bool fp32, size_t smem, int device) {
     void* fn = engine_fn(fp32);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(64 * 1024)) != cudaSuccess)
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(96 * 1024)) != cudaSuccess)
         return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kBlock, smem) != cudaSuccess) return 0;
