@@ -44,6 +44,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--n", type=int, default=512,
                     help="grid side (512 = the benchmark workload; smaller sides are for profiling captures)")
     return ap.parse_args()
@@ -281,6 +282,8 @@ def ours(args):
     s_bytes = 8 if args.precision == "mixed" else 16
     stream = torch.cuda.current_stream()
     psi0 = torch.from_numpy(cfg["psi0"]).to(dev)
+    from paper_1912_03312_gb300 import autotune
+    tuned = autotune.autotune(plan, psi0) if not args.no_autotune else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     cur = psi0.clone()
@@ -331,6 +334,8 @@ def ours(args):
     extra = {}
     if not args.no_fp64_path and rank == 0:
         p64 = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], K, precision="fp64", R1=R1)
+        if not args.no_autotune:
+            autotune.autotune(p64, psi0)
         ref = p64.step(psi0)
         out = plan.step(psi0)
         torch.cuda.synchronize()
@@ -390,7 +395,8 @@ def ours(args):
                        "R1": info["R1"], "restart": info["restart_m"], "precision": args.precision,
                        "tol": info["tol"], "amplification": info["amplification"],
                        "l2": "flushed (256 MiB write) before every timed step; Krylov basis 2 GB > L2",
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "autotuned": tuned},
             "grid_pts_poles_per_s": value * n * K * info["n_sub"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

@@ -85,6 +85,11 @@ typedef struct {
     int    want_backward;  /* allocate the adjoint workspace at create time (default 0:
                               allocated by the first rexi_step_backward call)               */
     int    device;         /* CUDA device ordinal; -1 = current device (default)          */
+    int    shared_first_cycle; /* 1 (default): the first GMRES cycle of every substep runs on
+                              one Krylov basis shared by all K poles (the shifted-systems
+                              observation of Sec. 5: K(tau H - z_k I, b) is the same space for
+                              every k), each pole with its own Hessenberg, rotations and stop;
+                              later cycles are per pole.  0: K independent bases throughout  */
 } rexi_options;
 
 /* What a plan computed (host copy, filled by rexi_plan_info). */
@@ -247,6 +252,14 @@ int rexi_substep_static(const rexi_grid* g, const double* V, double tau, double 
 
 /* Status of the last call on the plan (synchronises the plan's last stream). */
 int rexi_plan_last_status(rexi_plan* plan);
+
+/* Work decomposition of the plan's launches (the autotuner's knobs):
+ * pole_tile / group_tile = points per task of pole items / shared-cycle group
+ * items, each one of 256, 512, 1024, 2048; ctas_per_sm caps the resident CTAs
+ * per SM of the persistent grid (0 = as many as fit).  Synchronises the device
+ * and rewrites the plan's descriptors; results do not depend on these values
+ * beyond floating-point summation order. */
+int rexi_plan_set_tiles(rexi_plan* plan, int pole_tile, int group_tile, int ctas_per_sm);
 
 /* Phase tracing.  rexi_plan_set_trace allocates room for `capacity` records
  * (0 disables); afterwards every engine launch of the plan records, at each

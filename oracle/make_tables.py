@@ -15,7 +15,7 @@ import time
 from . import fcf, tables
 
 # (K, R1) pairs used by the tests, the smoke check and the benchmark workloads.
-DEFAULT_SET = [(8, 8), (12, 14), (16, 10), (16, 24), (32, 68)]
+DEFAULT_SET = [(8, 8), (12, 14), (16, 10), (16, 24), (32, 68), (64, 162)]
 
 
 def write(K, R1):

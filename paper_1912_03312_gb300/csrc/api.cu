@@ -57,6 +57,10 @@ struct rexi_plan {
     double a[3] = {0, 0, 0};
     std::vector<double> V;                       // host copy of the potential
     int ntiles = 0, pv = 32;
+    int tile_pole = rexi::kTile;                 // points per tile of pole items
+    int tile_group = rexi::kBlock * 2;           // points per tile of shared-cycle group items
+    int max_tiles = 0;                           // partial-buffer slots per item (256-point tiles)
+    int ctas_per_sm = 0;                         // 0: as many as fit
     int warn = REXI_OK;
     // device memory
     std::vector<void*> allocs;
@@ -69,7 +73,11 @@ struct rexi_plan {
     double2* d_hout = nullptr;
     unsigned* d_bar = nullptr;
     int* d_err = nullptr;
-    int nit_cap = 0;                             // items with workspace (K or 2K)
+    int nit_cap = 0;                             // pole items with workspace (K or 2K)
+    int ngroups = 0;                             // shared-cycle group items (0, 1 or 2)
+    bool shared = true;
+    double* d_gcs = nullptr;                     // group Givens cosines [ngroups][kMaxM][K]
+    double2* d_gsn = nullptr;
     double2* d_x = nullptr;
     void* d_basis = nullptr;
     ItemState* d_st = nullptr;
@@ -137,10 +145,13 @@ int upload_diag(rexi_plan* p, cudaStream_t stream, bool sync) {
     return e == cudaSuccess ? REXI_OK : cuda_fail(e);
 }
 
-// Allocate the solver workspace for `nit` items and build descriptor sets.
+// Allocate the solver workspace for `nit` pole items (plus one group item per
+// K poles when the first cycle is shared) and build descriptor sets.
 int alloc_items(rexi_plan* p, int nit) {
     const size_t n = (size_t)p->n;
     const size_t esz = p->fp32 ? sizeof(float2) : sizeof(double2);
+    const int ng = p->shared ? nit / p->K : 0;
+    const int nall = nit + ng;
     int st;
     double2* x;
     void* basis;
@@ -151,16 +162,21 @@ int alloc_items(rexi_plan* p, int nit) {
     if ((st = dalloc(p, &x, (size_t)nit * n))) return st;
     {
         void* ptr = nullptr;
-        cudaError_t e = cudaMalloc(&ptr, (size_t)nit * (p->m + 1) * n * esz);
+        cudaError_t e = cudaMalloc(&ptr, (size_t)nall * (p->m + 1) * n * esz);
         if (e != cudaSuccess) return cuda_fail(e);
         p->allocs.push_back(ptr);
         basis = ptr;
     }
-    if ((st = dalloc(p, &sts, (size_t)nit))) return st;
-    if ((st = dalloc(p, &stats, (size_t)nit))) return st;
-    if ((st = dalloc(p, &p1, (size_t)nit * p->ntiles * p->pv))) return st;
-    if ((st = dalloc(p, &p2, (size_t)nit * p->ntiles * p->pv))) return st;
-    if ((st = dalloc(p, &pn, (size_t)nit * p->ntiles))) return st;
+    if ((st = dalloc(p, &sts, (size_t)nall))) return st;
+    if ((st = dalloc(p, &stats, (size_t)nall))) return st;
+    if ((st = dalloc(p, &p1, (size_t)nall * p->max_tiles * p->pv))) return st;
+    if ((st = dalloc(p, &p2, (size_t)nall * p->max_tiles * p->pv))) return st;
+    if ((st = dalloc(p, &pn, (size_t)nall * p->max_tiles))) return st;
+    if (ng > 0) {
+        if ((st = dalloc(p, &p->d_gcs, (size_t)ng * rexi::kMaxM * p->K))) return st;
+        if ((st = dalloc(p, &p->d_gsn, (size_t)ng * rexi::kMaxM * p->K))) return st;
+    }
+    p->ngroups = ng;
     p->d_x = x;
     p->d_basis = basis;
     p->d_st = sts;
@@ -173,15 +189,19 @@ int alloc_items(rexi_plan* p, int nit) {
     return REXI_OK;
 }
 
-ItemDesc make_item(const rexi_plan* p, int idx, int pole, bool adjoint, int problem, int tile_base) {
+// Pole item in workspace slot idx; group_item is the launch-wide index of its
+// shared-cycle group (-1: none).
+ItemDesc make_item(const rexi_plan* p, int idx, int pole, bool adjoint, int problem, int group_item) {
     ItemDesc it{};
     it.problem = problem;
     it.pole = pole;
     it.adjoint = adjoint ? 1 : 0;
-    it.tile_off = idx * p->ntiles;               // offset inside this plan's partial buffers
-    (void)tile_base;
+    it.tile_off = idx * p->max_tiles;            // offset inside this plan's partial buffers
+    it.group = group_item;
+    it.is_group = 0;
+    it.tile = p->tile_pole;
     it.n = p->n;
-    it.ntiles = p->ntiles;
+    it.ntiles = (p->n + it.tile - 1) / it.tile;
     const cd s = p->z[pole] - p->tau * p->c;    // centred shift: A = tau (H - c) - s
     const cd sh = adjoint ? std::conj(s) : s;
     it.shift = make_double2(sh.real(), sh.imag());
@@ -195,6 +215,52 @@ ItemDesc make_item(const rexi_plan* p, int idx, int pole, bool adjoint, int prob
     it.part2 = p->d_part2;
     it.partn = p->d_partn;
     return it;
+}
+
+// Group item g (workspace slot nit_cap + g): Arnoldi on the unshifted operator
+// tau (H - c) for members [member0, member0 + K) (launch-wide indices).
+ItemDesc make_group(const rexi_plan* p, int g, bool adjoint, int problem, int member0) {
+    ItemDesc it{};
+    const int idx = p->nit_cap + g;
+    it.problem = problem;
+    it.pole = -1;
+    it.adjoint = adjoint ? 1 : 0;
+    it.tile_off = idx * p->max_tiles;
+    it.n = p->n;
+    it.tile = p->tile_group;
+    it.ntiles = (p->n + it.tile - 1) / it.tile;
+    it.shift = make_double2(0.0, 0.0);
+    it.shiftf = make_float2(0.0f, 0.0f);
+    it.x = nullptr;
+    const size_t esz = p->fp32 ? sizeof(float2) : sizeof(double2);
+    it.basis = (char*)p->d_basis + (size_t)idx * (p->m + 1) * p->n * esz;
+    it.group = -1;
+    it.is_group = 1;
+    it.member0 = member0;
+    it.nmembers = p->K;
+    it.gcs = p->d_gcs + (size_t)g * rexi::kMaxM * p->K;
+    it.gsn = p->d_gsn + (size_t)g * rexi::kMaxM * p->K;
+    it.st = p->d_st + idx;
+    it.stats = p->d_stats + idx;
+    it.part1 = p->d_part1;
+    it.part2 = p->d_part2;
+    it.partn = p->d_partn;
+    return it;
+}
+
+// Items of one plan appended to a launch-wide list starting at `base`:
+// poles first (the pole sum and the adjoint address them by pole index), then
+// the group items.  backward: X poles, Y poles, X group, Y group.
+void append_items(const rexi_plan* p, bool backward, int problem, int base, std::vector<ItemDesc>* out) {
+    const int K = p->K;
+    const int nsets = backward ? 2 : 1;
+    for (int sset = 0; sset < nsets; ++sset)
+        for (int k = 0; k < K; ++k) {
+            const int grp = p->ngroups > 0 ? base + nsets * K + sset : -1;
+            out->push_back(make_item(p, sset * K + k, k, sset == 1, problem, grp));
+        }
+    if (p->ngroups > 0)
+        for (int sset = 0; sset < nsets; ++sset) out->push_back(make_group(p, sset, sset == 1, problem, base + sset * K));
 }
 
 ProblemDesc make_problem(const rexi_plan* p, int nsub, int item0, int nitems) {
@@ -230,6 +296,8 @@ int upload_set(rexi_plan* p, DescSet* set, const ProblemDesc& pr, const std::vec
         if ((st = dalloc(p, &set->d_items, items.size()))) return st;
     }
     set->nitems = (int)items.size();
+    set->ntiles_items = 0;
+    for (const ItemDesc& it : items) set->ntiles_items += it.ntiles;
     cudaError_t e = cudaMemcpy(set->d_prob, &pr, sizeof(pr), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(set->d_items, items.data(), sizeof(ItemDesc) * items.size(), cudaMemcpyHostToDevice);
@@ -238,17 +306,16 @@ int upload_set(rexi_plan* p, DescSet* set, const ProblemDesc& pr, const std::vec
 
 int build_sets(rexi_plan* p) {
     std::vector<ItemDesc> f;
-    for (int k = 0; k < p->K; ++k) f.push_back(make_item(p, k, k, false, 0, 0));
-    p->hprob = make_problem(p, p->n_sub, 0, p->K);
+    append_items(p, false, 0, 0, &f);
+    p->hprob = make_problem(p, p->n_sub, 0, (int)f.size());
     int st = upload_set(p, &p->fwd, p->hprob, f);
     if (st) return st;
-    st = upload_set(p, &p->one, make_problem(p, 1, 0, p->K), f);
+    st = upload_set(p, &p->one, make_problem(p, 1, 0, (int)f.size()), f);
     if (st) return st;
     if (p->nit_cap >= 2 * p->K) {
         std::vector<ItemDesc> b;
-        for (int k = 0; k < p->K; ++k) b.push_back(make_item(p, k, k, false, 0, 0));
-        for (int k = 0; k < p->K; ++k) b.push_back(make_item(p, p->K + k, k, true, 0, 0));
-        st = upload_set(p, &p->bwd, make_problem(p, p->n_sub, 0, 2 * p->K), b);
+        append_items(p, true, 0, 0, &b);
+        st = upload_set(p, &p->bwd, make_problem(p, p->n_sub, 0, (int)b.size()), b);
         if (st) return st;
         p->has_backward = true;
     }
@@ -303,14 +370,21 @@ int max_grid_cached(bool fp32, size_t smem, int device) {
     return g;
 }
 
+int sm_count(int device) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 1;
+    return std::max(1, sms);
+}
+
 int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(p->d_bar, 0, 2 * sizeof(unsigned), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stats, 0, sizeof(ItemStats) * A.nitems, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     const size_t smem = rexi::engine_smem_bytes(A.nitems);
-    const int maxg = max_grid_cached(p->fp32, smem, p->device);
+    int maxg = max_grid_cached(p->fp32, smem, p->device);
     if (maxg <= 0) return REXI_ECUDA;
+    if (p->ctas_per_sm > 0) maxg = std::min(maxg, p->ctas_per_sm * sm_count(p->device));
     const int grid = std::max(1, std::min(maxg, total_tiles));
     e = rexi::launch_engine(p->fp32, A, io, grid, smem, stream);
     p->last_stream = stream;
@@ -384,6 +458,7 @@ int rexi_options_default(rexi_options* o) {
     o->stabilize_eps = 0.0;
     o->want_backward = 0;
     o->device = -1;
+    o->shared_first_cycle = 1;
     return REXI_OK;
 }
 
@@ -440,6 +515,7 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     p->m = opt.restart_m;
     p->dt = dt;
     p->fp32 = opt.precision == REXI_MIXED;
+    p->shared = opt.shared_first_cycle != 0;
     for (int d = 0; d < 3; ++d) { p->dims[d] = dims[d]; p->h[d] = h[d]; }
     p->V.assign(V, V + n);
 
@@ -483,6 +559,7 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     p->tol = opt.tol > 0.0 ? opt.tol
                            : std::max(2e-14, std::min(1e-10, 1e-6 / std::max(1.0, p->fcf.amplification)));
     p->ntiles = (p->n + rexi::kTile - 1) / rexi::kTile;
+    p->max_tiles = (p->n + rexi::kBlock - 1) / rexi::kBlock;
     p->pv = 32;
 
     // device
@@ -605,7 +682,7 @@ int rexi_step(rexi_plan* p, const void* psi_in, void* psi_out, void* stream, rex
     io.in[0] = (const double2*)psi_in;
     io.out[0] = (double2*)psi_out;
     EngineArgs A = base_args(p, rexi::MODE_STEP, p->fwd, 1, p->n_sub);
-    int r = launch(p, A, io, p->K * p->ntiles, s);
+    int r = launch(p, A, io, p->fwd.ntiles_items, s);
     if (r) return p->last_status = r;
     if (!st) return p->last_status = REXI_OK;
     return p->last_status = collect(p, s, p->K, 0, p->K, st, p->n_sub);
@@ -632,7 +709,7 @@ int rexi_solve_poles(rexi_plan* p, const void* b, void* x, void* stream, rexi_st
     IOArgs io{};
     io.in[0] = (const double2*)b;
     EngineArgs A = base_args(p, rexi::MODE_SOLVE, p->one, 1, 1);
-    int r = launch(p, A, io, p->K * p->ntiles, s);
+    int r = launch(p, A, io, p->one.ntiles_items, s);
     if (r) return p->last_status = r;
     cudaError_t e = cudaMemcpyAsync(x, p->d_x, sizeof(double2) * (size_t)p->K * p->n, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return p->last_status = REXI_ECUDA;
@@ -675,7 +752,7 @@ int rexi_step_backward(rexi_plan* p, const void* psi_n, const void* grad_out, vo
         io.in[0] = sub == 0 ? (const double2*)psi_n : p->d_ckpt + (size_t)sub * p->n;
         io.out[0] = p->d_ckpt + (size_t)(sub + 1) * p->n;
         EngineArgs A = base_args(p, rexi::MODE_STEP, p->one, 1, 1);
-        r = launch(p, A, io, p->K * p->ntiles, s);
+        r = launch(p, A, io, p->one.ntiles_items, s);
         if (r) return p->last_status = r;
         ++launches;
     }
@@ -685,7 +762,7 @@ int rexi_step_backward(rexi_plan* p, const void* psi_n, const void* grad_out, vo
     io.gout[0] = (const double2*)grad_out;
     io.dLdV[0] = dLdV;
     EngineArgs A = base_args(p, rexi::MODE_BACKWARD, p->bwd, 1, p->n_sub);
-    r = launch(p, A, io, 2 * p->K * p->ntiles, s);
+    r = launch(p, A, io, p->bwd.ntiles_items, s);
     if (r) return p->last_status = r;
     p->last_launches = launches + 1;
     if (!st) return p->last_status = REXI_OK;
@@ -702,10 +779,12 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
         rexi_plan* p = plans[b];
         if (!p || !psi_in[b] || !psi_out[b]) return REXI_EINVAL;
         if (p->device != p0->device || p->fp32 != p0->fp32 || p->m != p0->m) return REXI_EINVAL;
+        const int ng = p->shared ? 1 : 0;
         for (int c = 0; c < b; ++c)
             if (plans[c] == p) return REXI_EINVAL;         // one plan's workspace per problem
-        total_items += p->K;
-        total_tiles += p->K * p->ntiles;
+        total_items += p->K + ng;
+        total_tiles += p->K * ((p->n + p->tile_pole - 1) / p->tile_pole) +
+                       ng * ((p->n + p->tile_group - 1) / p->tile_group);
         max_sub = std::max(max_sub, p->n_sub);
     }
     if (total_items > rexi::kMaxItems) return REXI_EINVAL;
@@ -734,8 +813,9 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
         std::vector<ItemDesc> items;
         for (int b = 0; b < B; ++b) {
             rexi_plan* p = plans[b];
-            probs.push_back(make_problem(p, p->n_sub, (int)items.size(), p->K));
-            for (int k = 0; k < p->K; ++k) items.push_back(make_item(p, k, k, false, b, 0));
+            const int base = (int)items.size();
+            append_items(p, false, b, base, &items);
+            probs.push_back(make_problem(p, p->n_sub, base, (int)items.size() - base));
         }
         if (!bc) {
             caches.push_back(std::make_pair(p0, BatchCache()));
@@ -766,15 +846,17 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
     EngineArgs A = base_args(p0, rexi::MODE_STEP, set, B, max_sub);
     // statistics of every plan are zeroed, the barrier/error words are p0's
     for (int b = 1; b < B; ++b)
-        if (cudaMemsetAsync(plans[b]->d_stats, 0, sizeof(ItemStats) * plans[b]->K, s) != cudaSuccess)
+        if (cudaMemsetAsync(plans[b]->d_stats, 0, sizeof(ItemStats) * (plans[b]->K + plans[b]->ngroups), s) !=
+            cudaSuccess)
             return REXI_ECUDA;
     cudaError_t e = cudaMemsetAsync(p0->d_bar, 0, 2 * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_stats, 0, sizeof(ItemStats) * p0->K, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_stats, 0, sizeof(ItemStats) * (p0->K + p0->ngroups), s);
     if (e != cudaSuccess) return REXI_ECUDA;
     const size_t smem = rexi::engine_smem_bytes(A.nitems);
-    const int maxg = max_grid_cached(p0->fp32, smem, p0->device);
+    int maxg = max_grid_cached(p0->fp32, smem, p0->device);
     if (maxg <= 0) return REXI_ECUDA;
+    if (p0->ctas_per_sm > 0) maxg = std::min(maxg, p0->ctas_per_sm * sm_count(p0->device));
     const int grid = std::max(1, std::min(maxg, total_tiles));
     e = rexi::launch_engine(p0->fp32, A, io, grid, smem, s);
     for (int b = 0; b < B; ++b) {
@@ -828,6 +910,19 @@ int rexi_plan_last_status(rexi_plan* p) {
 }
 
 int rexi_plan_last_launches(const rexi_plan* p) { return p ? p->last_launches : 0; }
+
+int rexi_plan_set_tiles(rexi_plan* p, int pole_tile, int group_tile, int ctas_per_sm) {
+    if (!p) return REXI_EINVAL;
+    auto ok = [](int t) { return t == 256 || t == 512 || t == 1024 || t == 2048; };
+    if (!ok(pole_tile) || !ok(group_tile) || ctas_per_sm < 0 || ctas_per_sm > 32) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    if (cudaDeviceSynchronize() != cudaSuccess) return REXI_ECUDA;
+    p->tile_pole = pole_tile;
+    p->tile_group = group_tile;
+    p->ctas_per_sm = ctas_per_sm;
+    p->generation++;                              // batched descriptor caches rebuild
+    return build_sets(p);
+}
 
 int rexi_plan_set_trace(rexi_plan* p, int capacity) {
     if (!p || capacity < 0) return REXI_EINVAL;

@@ -189,6 +189,7 @@ struct Smem {
     int nl;
     int ntasks;
     int kk;                        // Arnoldi steps of the current item (E2)
+    const void* basis;             // basis the current item's E2 reads
 };
 
 template <typename V> __device__ __forceinline__ V coef_at(const Smem& sm, int q);
@@ -469,6 +470,7 @@ struct Phases {
     static __device__ void e3(Smem& sm, int sub, int item, int tb, int te) {
         const EngineArgs& A = sm.A;
         const ItemDesc& it = A.item[item];
+        const int it_n = it.n, it_tile = it.tile;
         const ProblemDesc& pr = A.prob[it.problem];
         const int cycles = ldi(&it.st->cycles);
         const double2* b = item_rhs(A.mode, sm.io, it, pr, sub);
@@ -476,7 +478,7 @@ struct Phases {
         double2* x = it.x;
         double acc = 0.0;
         for (int tile = tb; tile < te; ++tile) {
-            const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+            const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
             double2 rv[kPPT];
 #pragma unroll
             for (int r = 0; r < kPPT; ++r) {
@@ -484,10 +486,12 @@ struct Phases {
                 rv[r] = p < pend ? ldp(b + p) : make_double2(0.0, 0.0);
             }
             if (cycles == 0) {
+                if (x != nullptr) {
 #pragma unroll
-                for (int r = 0; r < kPPT; ++r) {
-                    const int p = p0 + r * kBlock + threadIdx.x;
-                    if (p < pend) x[p] = make_double2(0.0, 0.0);
+                    for (int r = 0; r < kPPT; ++r) {
+                        const int p = p0 + r * kBlock + threadIdx.x;
+                        if (p < pend) x[p] = make_double2(0.0, 0.0);
+                    }
                 }
             } else {
 #pragma unroll
@@ -498,11 +502,13 @@ struct Phases {
                                                                             pr.a[2], it.shift));
                 }
             }
+            // a pole whose first cycle runs on its group's basis needs no u_0
+            const bool store = !(it.group >= 0 && cycles == 0);
 #pragma unroll
             for (int r = 0; r < kPPT; ++r) {
                 const int p = p0 + r * kBlock + threadIdx.x;
                 if (p < pend) {
-                    U[p] = cvt2<V>(rv[r]);
+                    if (store) U[p] = cvt2<V>(rv[r]);
                     acc += rv[r].x * rv[r].x + rv[r].y * rv[r].y;
                 }
             }
@@ -520,9 +526,9 @@ struct Phases {
         int q[4];
         int row0, row1;        // rows of 32 points of the tile
     };
-    static __device__ __forceinline__ DotPlan dot_plan(int J) {
+    static __device__ __forceinline__ DotPlan dot_plan(int J, int tile) {
         const int wp = threadIdx.x >> 5;
-        constexpr int rows = kTile / 32;
+        const int rows = tile / 32;
         DotPlan d;
         d.nvec = 0;
         if (J >= kWarps) {
@@ -566,10 +572,11 @@ struct Phases {
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const int pl = (row + k) * 32 + lane;
-                    const V w = ws[pl & (kTile - 1)];
-                    sr += u[k].x * w.x + u[k].y * w.y;
-                    si += u[k].x * w.y - u[k].y * w.x;
+                    if (row + k < d.row1) {
+                        const V w = ws[(row + k) * 32 + lane];
+                        sr += u[k].x * w.x + u[k].y * w.y;
+                        si += u[k].x * w.y - u[k].y * w.x;
+                    }
                 }
             }
             // slot sl of this warp (fixed unrolled index to stay in registers)
@@ -639,8 +646,9 @@ struct Phases {
     static __device__ void p1(Smem& sm, V* ws, int item, int tb, int te, int j) {
         const EngineArgs& A = sm.A;
         const ItemDesc& it = A.item[item];
+        const int it_n = it.n, it_tile = it.tile;
         const ProblemDesc& pr = A.prob[it.problem];
-        const size_t n = (size_t)it.n;
+        const size_t n = (size_t)it_n;
         V* U = (V*)it.basis;
         const V* uj = U + (size_t)j * n;
         V* wv = U + (size_t)(j + 1) * n;
@@ -648,10 +656,10 @@ struct Phases {
         const V shift = item_shift<V>(it);
         const T* diag = prob_diag<T>(pr);
         const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
-        const DotPlan d = dot_plan(j + 1);
+        const DotPlan d = dot_plan(j + 1, it_tile);
         T ar[4] = {T(0), T(0), T(0), T(0)}, ai[4] = {T(0), T(0), T(0), T(0)};
         for (int tile = tb; tile < te; ++tile) {
-            const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+            const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
             V w[kPPT];
 #pragma unroll
             for (int r = 0; r < kPPT; ++r) {
@@ -677,6 +685,7 @@ struct Phases {
     // P2 prologue: h1_i = s_i sum p1_i; coefficients s_i h1_i of u_i.
     static __device__ void p2_pro(Smem& sm, int item, const Runs& R, int j) {
         const ItemDesc& it = sm.A.item[item];
+        const int it_n = it.n, it_tile = it.tile;
         load_scales(sm, it.st, j + 1);
         reduce_partials(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);
         if (threadIdx.x <= j) {
@@ -690,13 +699,14 @@ struct Phases {
     // P2: w' = w - sum_i c_i u_i (staged in shared memory); p2_i = sum conj(u_i) w'.
     static __device__ void p2(Smem& sm, V* ws, int item, int tb, int te, int j) {
         const ItemDesc& it = sm.A.item[item];
-        const size_t n = (size_t)it.n;
+        const int it_n = it.n, it_tile = it.tile;
+        const size_t n = (size_t)it_n;
         const V* U = (const V*)it.basis;
         const V* wv = U + (size_t)(j + 1) * n;
-        const DotPlan d = dot_plan(j + 1);
+        const DotPlan d = dot_plan(j + 1, it_tile);
         T ar[4] = {T(0), T(0), T(0), T(0)}, ai[4] = {T(0), T(0), T(0), T(0)};
         for (int tile = tb; tile < te; ++tile) {
-            const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+            const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
             V w[kPPT];
             load_tile(wv, w, p0, pend);
             subtract(sm, U, n, w, p0, pend, j);
@@ -711,6 +721,7 @@ struct Phases {
     // P3 prologue: h = h1 + h2; coefficients s_i h_i.
     static __device__ void p3_pro(Smem& sm, int item, const Runs& R, int j) {
         const ItemDesc& it = sm.A.item[item];
+        const int it_n = it.n, it_tile = it.tile;
         load_scales(sm, it.st, j + 1);
         reduce_partials(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);
         reduce_partials(sm, it.part2, it, R, j + 1, sm.ssm, sm.h2);
@@ -728,13 +739,14 @@ struct Phases {
     // publishes the Hessenberg column.
     static __device__ void p3(Smem& sm, int item, int tb, int te, int j) {
         const ItemDesc& it = sm.A.item[item];
-        const size_t n = (size_t)it.n;
+        const int it_n = it.n, it_tile = it.tile;
+        const size_t n = (size_t)it_n;
         V* U = (V*)it.basis;
         V* wv = U + (size_t)(j + 1) * n;
         if (tb == 0 && threadIdx.x <= j) it.st->hcol[threadIdx.x] = sm.h1[threadIdx.x];
         T acc = T(0);
         for (int tile = tb; tile < te; ++tile) {
-            const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+            const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
             V w[kPPT];
             load_tile(wv, w, p0, pend);
             subtract(sm, U, n, w, p0, pend, j);
@@ -753,15 +765,22 @@ struct Phases {
 
     // E2 prologue: y = R^{-1} g (back substitution, FP64), coefficients y_i s_i.
     static __device__ void e2_pro(Smem& sm, int item) {
-        const ItemState* S = sm.A.item[item].st;
+        const ItemDesc& it = sm.A.item[item];
+        const int it_n = it.n, it_tile = it.tile;
+        const ItemState* S = it.st;
         const int k = ldi(&S->k);
+        const bool shared = ldi(&S->shared) != 0;
+        const ItemDesc& src = shared ? sm.A.item[it.group] : it;   // owner of the basis used
         const int nR = k * (k + 1) / 2;
         for (int t = threadIdx.x; t < nR; t += kBlock) sm.Rsm[t] = ldp(&S->R[t]);
         if (threadIdx.x < k) {
             sm.gsm[threadIdx.x] = ldp(&S->g[threadIdx.x]);
-            sm.ssm[threadIdx.x] = ldd(&S->s[threadIdx.x]);
+            sm.ssm[threadIdx.x] = ldd(&src.st->s[threadIdx.x]);
         }
-        if (threadIdx.x == 0) sm.kk = k;
+        if (threadIdx.x == 0) {
+            sm.kk = k;
+            sm.basis = src.basis;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             for (int i = k - 1; i >= 0; --i) {
@@ -787,12 +806,13 @@ struct Phases {
     // reduction) and added to x in FP64.
     static __device__ void e2(Smem& sm, int item, int tb, int te) {
         const ItemDesc& it = sm.A.item[item];
-        const size_t n = (size_t)it.n;
-        const V* U = (const V*)it.basis;
+        const int it_n = it.n, it_tile = it.tile;
+        const size_t n = (size_t)it_n;
+        const V* U = (const V*)sm.basis;
         double2* x = it.x;
         const int k = sm.kk;
         for (int tile = tb; tile < te; ++tile) {
-            const int p0 = tile * kTile, pend = min(it.n, p0 + kTile);
+            const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
             V d[kPPT];
 #pragma unroll
             for (int r = 0; r < kPPT; ++r) d[r] = mk2(T(0), T(0));
@@ -832,6 +852,20 @@ __device__ void item_e4(const EngineArgs& A, int item, const Runs& R) {
     S->relres = relres;
     const int total = ldi(&S->total_iters);
     int status;
+    if (it.is_group) {                              // shared Krylov basis of the members
+        if (cycles == 0 && beta > 0.0 && beta <= 1e300) {
+            S->s[0] = 1.0 / beta;
+            S->k = 0;
+            S->cycles = 1;
+            S->total_iters = 0;
+            status = ST_ARNOLDI;
+        } else {
+            status = ST_IDLE;
+        }
+        __threadfence();
+        S->status = status;
+        return;
+    }
     if (!(beta <= 1e300) || !(bnorm <= 1e300) || !(relres <= 1e300)) {
         status = ST_FAILED;                         // NaN / Inf in the data
     } else if (bnorm == 0.0 || relres <= A.tol) {
@@ -839,14 +873,16 @@ __device__ void item_e4(const EngineArgs& A, int item, const Runs& R) {
     } else if (total >= A.max_iters) {
         status = ST_FAILED;
     } else {
-        status = ST_ARNOLDI;
+        const bool shared = cycles == 0 && it.group >= 0;
+        status = shared ? ST_SHARED : ST_ARNOLDI;
+        S->shared = shared ? 1 : 0;
         S->s[0] = 1.0 / beta;
         S->g[0] = make_double2(beta, 0.0);
         S->k = 0;
         S->cycles = cycles + 1;
         S->cycle_tol_abs = fmax(A.tol * bnorm, A.inner_tol * beta);
     }
-    if (status != ST_ARNOLDI) {
+    if (status == ST_CONVERGED || status == ST_FAILED) {
         ItemStats* T = it.stats;
         T->iters += total;
         T->iters_sq += ldi(&S->sum_k2);
@@ -919,6 +955,74 @@ __device__ void load_problem_items(Smem& sm, int prob) {
     for (int k = threadIdx.x; k < nx; k += kBlock) sm.xptr[k] = sm.A.item[pr.item0 + k].x;
     for (int k = threadIdx.x; k < pr.K; k += kBlock) sm.alpha[k] = __ldg(pr.alpha + k);
     __syncthreads();
+}
+
+// P4 of a group (one warp, lane = member): every member's Hessenberg column is
+// the group's column with its shift subtracted on the diagonal, because
+// (B - s I) Q_j = Q_{j+1} (H_B - s [I; 0]) for the unshifted operator B; the
+// members share the Krylov basis and keep their own rotations and residuals.
+__device__ void group_p4(const EngineArgs& A, int gitem, const Runs& R, int j) {
+    const int lane = threadIdx.x & 31;
+    const ItemDesc& gd = A.item[gitem];
+    ItemState* G = gd.st;
+    const double hn = sqrt(warp_norm_partials(gd, R));
+    const int col = j * (j + 1) / 2;
+    const int nm = gd.nmembers;
+    bool active = false;
+    for (int mi = lane; mi < nm; mi += 32) {
+        const ItemDesc& md = A.item[gd.member0 + mi];
+        ItemState* S = md.st;
+        if (ldi(&S->status) != ST_SHARED) continue;
+        const double2 sh = md.shift;
+        double2 carry = ldp(&G->hcol[0]);
+        if (j == 0) carry = csub(carry, sh);
+        for (int i = 0; i < j; ++i) {
+            double2 b = ldp(&G->hcol[i + 1]);
+            if (i + 1 == j) b = csub(b, sh);
+            const double c = ldd(gd.gcs + (size_t)i * nm + mi);
+            const double2 sn = ldp(gd.gsn + (size_t)i * nm + mi);
+            const double2 nh = cadd(cscale(carry, c), cmul(sn, b));
+            carry = cadd(cscale(cmul(cconj(sn), carry), -1.0), cscale(b, c));
+            S->R[col + i] = nh;
+        }
+        const double aa = sqrt(carry.x * carry.x + carry.y * carry.y);
+        const double rr = sqrt(aa * aa + hn * hn);
+        double c;
+        double2 sn, rjj;
+        if (aa == 0.0) {
+            c = 0.0;
+            sn = make_double2(1.0, 0.0);
+            rjj = make_double2(hn, 0.0);
+        } else {
+            c = aa / rr;
+            sn = cscale(carry, hn / (aa * rr));
+            rjj = cscale(carry, rr / aa);
+        }
+        const double2 gj = ldp(&S->g[j]);
+        const double2 gj1 = cscale(cmul(cconj(sn), gj), -1.0);
+        gd.gcs[(size_t)j * nm + mi] = c;
+        gd.gsn[(size_t)j * nm + mi] = sn;
+        S->R[col + j] = rjj;
+        S->g[j] = cscale(gj, c);
+        S->g[j + 1] = gj1;
+        S->k = j + 1;
+        const int total = ldi(&S->total_iters) + 1;
+        S->total_iters = total;
+        const double res = sqrt(gj1.x * gj1.x + gj1.y * gj1.y);
+        const bool end = !(res > ldd(&S->cycle_tol_abs)) || j + 1 >= A.m || total >= A.max_iters ||
+                         !(hn > 0.0) || !(rr > 0.0);
+        if (end) S->sum_k2 = ldi(&S->sum_k2) + (j + 1) * (j + 1);
+        __threadfence();
+        S->status = end ? ST_CYCLE_END : ST_SHARED;
+        active = active || !end;
+    }
+    const bool any = __any_sync(0xffffffffu, active);
+    if (lane == 0) {
+        G->s[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+        G->k = j + 1;
+        __threadfence();
+        G->status = any ? ST_ARNOLDI : ST_IDLE;
+    }
 }
 
 // PS: psi' = alpha_0 b + sum_k alpha_k x_k for one tile of a problem.
@@ -1037,6 +1141,7 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(const __grid_constant
             S->cycles = 0;
             S->total_iters = 0;
             S->sum_k2 = 0;
+            S->shared = 0;
             S->k = 0;
             S->status = sub < A.prob[it.problem].nsub ? ST_NEED_RES : ST_IDLE;
         }
@@ -1084,7 +1189,10 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(const __grid_constant
                     t = prefix[l] + te;
                 }
                 if (!phase_sync(A, TR_P3, &tcount)) return;
-                for (int l = gwarp; l < sm.nl; l += nwarps) item_p4(A, list[l], item_runs(prefix, l, sm.ntasks), j);
+                for (int l = gwarp; l < sm.nl; l += nwarps) {
+                    if (A.item[list[l]].is_group) group_p4(A, list[l], item_runs(prefix, l, sm.ntasks), j);
+                    else item_p4(A, list[l], item_runs(prefix, l, sm.ntasks), j);
+                }
                 if (!phase_sync(A, TR_P4, &tcount)) return;
             }
 

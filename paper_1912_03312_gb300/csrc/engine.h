@@ -22,6 +22,7 @@ enum : int {
     ST_CONVERGED = 3,
     ST_FAILED = 4,
     ST_IDLE = 5,       // not part of the current substep
+    ST_SHARED = 6,     // pole in its first cycle on its group's shared Krylov basis
 };
 
 // kernel modes
@@ -66,11 +67,18 @@ struct ItemDesc {
     int adjoint;         // 1: solve with conj shift against the adjoint state
     int tile_off;        // first tile of this item in the partial buffers
     int n;               // points of the item's problem
-    int ntiles;          // tiles of the item's problem
+    int ntiles;          // tiles of this item (ceil(n / tile))
+    int tile;            // points per tile: kBlock * {1, 2, 4, 8}
     double2 shift;       // A = stencil + diag - shift
     float2 shiftf;
     double2* x;          // c128 [n]
     void* basis;         // T2 [m+1][n]
+    int group;           // pole items: item index of the shared-cycle group, -1 if none
+    int is_group;        // 1: group item (Arnoldi on the unshifted operator for its members)
+    int member0;         // group items: first member item index
+    int nmembers;        // group items: number of members
+    double* gcs;         // group items: Givens cosines [kMaxM][nmembers]
+    double2* gsn;        // group items: Givens sines   [kMaxM][nmembers]
     struct ItemState* st;
     struct ItemStats* stats;
     double2* part1;      // [tiles][pv] partial dots, first CGS pass
@@ -80,7 +88,7 @@ struct ItemDesc {
 
 struct ItemState {
     int status, k, total_iters, cycles;
-    int sub_iters, sub_cycles, sum_k2, pad;
+    int sub_iters, sub_cycles, sum_k2, shared;
     double bnorm, beta, cycle_tol_abs, relres;
     double s[kMaxM + 1];
     double cs[kMaxM];

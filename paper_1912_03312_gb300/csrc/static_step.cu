@@ -135,9 +135,12 @@ extern "C" int rexi_substep_static(const rexi_grid* g, const double* V, double t
         ItemDesc& it = items[k];
         it.problem = 0;
         it.pole = k;
+        it.group = -1;                                            // independent bases only
+        it.is_group = 0;
         it.tile_off = k * ntiles;
         it.n = (int)n;
         it.ntiles = ntiles;
+        it.tile = rexi::kTile;
         const double sr = z[2 * k] - tau * c, si = z[2 * k + 1];   // centred shift z_k - tau c
         it.shift = make_double2(sr, si);
         it.shiftf = make_float2((float)sr, (float)si);

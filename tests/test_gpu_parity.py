@@ -191,3 +191,33 @@ def test_nan_input_fails_cleanly():
     assert e.value.code == -4
     good = lp.step(to_dev(psi), stats=True)[1]          # the plan stays usable
     assert good["status"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("K,R1,n,dt", [(16, 24.0, (130, 101), 0.5), (32, 68.0, (96, 80), 0.5), (8, 8.0, (9, 7, 5), 0.2)])
+def test_independent_bases_match_oracle(precision, K, R1, n, dt):
+    # shared_first_cycle=0: every pole keeps its own Krylov basis from the start
+    g, V, psi = wl.random_problem(37, n, box=8.0)
+    tol = 1e-13
+    lp = library_plan(g, V, dt, K, R1, precision=precision, tol=tol, shared_first_cycle=False)
+    orc = OraclePlan(g, V, dt, K, R1)
+    out, st = lp.step(to_dev(psi), stats=True)
+    assert st["status"] == 0
+    ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
+    floor = 1e-10 if precision == "fp64" else 1e-6
+    assert relerr(out.cpu().numpy(), ref) < max(floor, 2.0 * orc.A * tol)
+
+
+def test_shared_cycle_needs_fewer_basis_sweeps():
+    # same solutions either way; the shared first cycle builds one basis for all poles
+    g, V, psi = wl.random_problem(38, (128, 96), box=8.0)
+    outs, its = [], []
+    for shared in (True, False):
+        lp = library_plan(g, V, 0.5, 16, 24.0, precision="fp64", tol=1e-13, shared_first_cycle=shared)
+        lp.set_trace(1 << 14)
+        o, st = lp.step(to_dev(psi), stats=True)
+        outs.append(o.cpu().numpy())
+        its.append(sum(1 for c, _ in lp.read_trace() if c == 3))      # matvec phases
+    A = lp.info()["amplification"]
+    assert relerr(outs[0], outs[1]) < max(1e-10, 4.0 * A * 1e-13)
+    assert its[0] >= 1 and its[1] >= 1
