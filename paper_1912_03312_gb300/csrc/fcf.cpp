@@ -351,6 +351,18 @@ int fcf_construct(int K, double R1, FcfResult* out) {
     }
     out->amplification = A;
     if (min_re < 1.0) return -6;                               // spurious near-axis pole
+    // Self-check of the construction: r(i w) must approximate e^{i w} on the
+    // interval to about 2 sigma_{K+1} (Theorem 1) plus the FP64 evaluation floor
+    // eps * A.  A construction whose cancellations exceeded double-double
+    // precision (large K) fails here instead of returning wrong weights.
+    double emax = 0.0;
+    for (int i = 0; i < S; ++i) {
+        const double w = -R1 + 2.0 * R1 * i / (S - 1);
+        cd r = 0.0;
+        for (int k = 0; k < K; ++k) r += out->beta[k] / (cd(0.0, w) - out->sigma[k]);
+        emax = std::max(emax, std::abs(r - std::exp(cd(0.0, w))));
+    }
+    if (!(emax <= 10.0 * (2.0 * out->sigma_K1 + 4e-16 * A) + 1e-12)) return -6;
     for (int k = 0; k < K; ++k)
         if (!std::isfinite(out->beta[k].real()) || !std::isfinite(out->beta[k].imag())) return -6;
     return 0;
