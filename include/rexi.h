@@ -90,6 +90,11 @@ typedef struct {
                               observation of Sec. 5: K(tau H - z_k I, b) is the same space for
                               every k), each pole with its own Hessenberg, rotations and stop;
                               later cycles are per pole.  0: K independent bases throughout  */
+    int    ortho;          /* Arnoldi orthogonalisation: 1 (default) delayed classical Gram-
+                              Schmidt with reorthogonalisation, one global reduction per step
+                              (the previous vector is reorthogonalised and normalised together
+                              with the projection of the new one; restart_m at most
+                              REXI_MAX_RESTART - 1); 0: CGS2, two reductions per step        */
 } rexi_options;
 
 /* What a plan computed (host copy, filled by rexi_plan_info). */
@@ -182,7 +187,7 @@ int rexi_step_host(rexi_plan* plan, const double* psi_in, double* psi_out, void*
 
 /* B independent problems (each with its own plan, grid, K and n_sub) in one
  * persistent launch: all problems x all poles share the GPU.  All plans must
- * be on the same device and have the same precision and restart length.
+ * be on the same device and have the same precision, restart length and orthogonalisation.
  * psi_in[b], psi_out[b] : device c128 of plan b's size.  st: B entries or NULL. */
 int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
                       void* const* psi_out, void* stream, rexi_stats* st);

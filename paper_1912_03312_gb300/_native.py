@@ -34,7 +34,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("restart_m", C.c_int), ("max_iters", C.c_int),
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("R1", C.c_double),
                 ("eps_target", C.c_double), ("allow_substeps", C.c_int), ("stabilize_eps", C.c_double),
-                ("want_backward", C.c_int), ("device", C.c_int), ("shared_first_cycle", C.c_int)]
+                ("want_backward", C.c_int), ("device", C.c_int), ("shared_first_cycle", C.c_int),
+                ("ortho", C.c_int)]
 
 
 class PlanInfo(C.Structure):

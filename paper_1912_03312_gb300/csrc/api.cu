@@ -340,6 +340,7 @@ EngineArgs base_args(const rexi_plan* p, int mode, const DescSet& set, int nprob
     A.max_iters = p->opt.max_iters;
     A.max_sub = max_sub;
     A.pv = p->pv;
+    A.ortho = p->opt.ortho;
     A.tol = p->tol;
     A.inner_tol = p->fp32 ? p->opt.inner_tol : 0.0;
     A.timeout_ns = kTimeoutNs;
@@ -381,7 +382,7 @@ int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles,
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stats, 0, sizeof(ItemStats) * A.nitems, stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    const size_t smem = rexi::engine_smem_bytes(A.nitems);
+    const size_t smem = rexi::engine_smem_bytes(A.nitems, p->fp32, A.ortho);
     int maxg = max_grid_cached(p->fp32, smem, p->device);
     if (maxg <= 0) return REXI_ECUDA;
     if (p->ctas_per_sm > 0) maxg = std::min(maxg, p->ctas_per_sm * sm_count(p->device));
@@ -459,6 +460,7 @@ int rexi_options_default(rexi_options* o) {
     o->want_backward = 0;
     o->device = -1;
     o->shared_first_cycle = 1;
+    o->ortho = 1;
     return REXI_OK;
 }
 
@@ -491,6 +493,8 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     if (opt_in) opt = *opt_in; else rexi_options_default(&opt);
     if (opt.precision != REXI_FP64 && opt.precision != REXI_MIXED) return REXI_EINVAL;
     if (opt.restart_m < 1 || opt.restart_m > REXI_MAX_RESTART || opt.max_iters < 1) return REXI_EINVAL;
+    if (opt.ortho != 0 && opt.ortho != 1) return REXI_EINVAL;
+    if (opt.ortho == 1 && opt.restart_m > REXI_MAX_RESTART - 1) return REXI_EINVAL;   // m+1 dot vectors
     if (!(opt.tol >= 0.0) || !(opt.R1 >= 0.0) || !(opt.inner_tol >= 0.0) || !(opt.stabilize_eps >= 0.0) ||
         !(opt.stabilize_eps < 1.0))
         return REXI_EINVAL;
@@ -560,7 +564,7 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
                            : std::max(2e-14, std::min(1e-10, 1e-6 / std::max(1.0, p->fcf.amplification)));
     p->ntiles = (p->n + rexi::kTile - 1) / rexi::kTile;
     p->max_tiles = (p->n + rexi::kBlock - 1) / rexi::kBlock;
-    p->pv = 32;
+    p->pv = 40;
 
     // device
     int dev = opt.device;
@@ -778,7 +782,8 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
     for (int b = 0; b < B; ++b) {
         rexi_plan* p = plans[b];
         if (!p || !psi_in[b] || !psi_out[b]) return REXI_EINVAL;
-        if (p->device != p0->device || p->fp32 != p0->fp32 || p->m != p0->m) return REXI_EINVAL;
+        if (p->device != p0->device || p->fp32 != p0->fp32 || p->m != p0->m ||
+            p->opt.ortho != p0->opt.ortho) return REXI_EINVAL;
         const int ng = p->shared ? 1 : 0;
         for (int c = 0; c < b; ++c)
             if (plans[c] == p) return REXI_EINVAL;         // one plan's workspace per problem
@@ -853,7 +858,7 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_stats, 0, sizeof(ItemStats) * (p0->K + p0->ngroups), s);
     if (e != cudaSuccess) return REXI_ECUDA;
-    const size_t smem = rexi::engine_smem_bytes(A.nitems);
+    const size_t smem = rexi::engine_smem_bytes(A.nitems, p0->fp32, A.ortho);
     int maxg = max_grid_cached(p0->fp32, smem, p0->device);
     if (maxg <= 0) return REXI_ECUDA;
     if (p0->ctas_per_sm > 0) maxg = std::min(maxg, p0->ctas_per_sm * sm_count(p0->device));

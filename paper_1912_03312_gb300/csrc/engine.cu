@@ -181,7 +181,15 @@ struct Smem {
     float2 coeff[kMaxM + 1];       // the same, rounded for the FP32 path
     double ssm[kMaxM + 1];
     double2 gsm[kMaxM + 1];
-    double2 Rsm[kMaxM * (kMaxM + 1) / 2];
+    double2 Rsm[kMaxM * (kMaxM + 3) / 2];   // R (E2) or the unrotated Hessenberg columns (Y)
+    double2 hfin[kMaxM + 2];       // Y: column j-1 completed
+    double2 hnew[kMaxM + 2];       // Y: column j (pending)
+    double2 coefG[kMaxM + 1];      // Y: coefficients of v_{j+1}
+    float2 coefGf[kMaxM + 1];
+    double yscal[4];               // Y: nu, t_j / nu, 1 / nu
+    double gcs_s[kMaxM];           // Y: staged Givens cosines of the committed item
+    double2 gsn_s[kMaxM];          //    and sines
+    double2 ygq;                   // Y: gamma_j (coefficient of q_j in v_{j+1})
     int cnt[kBlock];
     int tls[kBlock];
     const double2* xptr[2 * kMaxPoles];
@@ -192,6 +200,9 @@ struct Smem {
     const void* basis;             // basis the current item's E2 reads
 };
 
+template <typename V> __device__ __forceinline__ V coefg_at(const Smem& sm, int q);
+template <> __device__ __forceinline__ float2 coefg_at<float2>(const Smem& sm, int q) { return sm.coefGf[q]; }
+template <> __device__ __forceinline__ double2 coefg_at<double2>(const Smem& sm, int q) { return sm.coefG[q]; }
 template <typename V> __device__ __forceinline__ V coef_at(const Smem& sm, int q);
 template <> __device__ __forceinline__ float2 coef_at<float2>(const Smem& sm, int q) { return sm.coeff[q]; }
 template <> __device__ __forceinline__ double2 coef_at<double2>(const Smem& sm, int q) { return sm.coef[q]; }
@@ -763,6 +774,215 @@ struct Phases {
         if (threadIdx.x == 0) it.partn[it.tile_off + tb] = tot;
     }
 
+    // ---- delayed CGS2 (one global reduction per Arnoldi step) -------------
+    //
+    // Entering step j, slots 0..j-1 hold the orthonormal q_0..q_{j-1} and slot
+    // j holds v_j = t_j u_j: A q_{j-1} projected once against them (j = 0: the
+    // normalised residual).  X computes w = A v_j and, in the same sweep,
+    // a = Q^H v_j, c = v_j^H v_j, b = Q^H w, d = v_j^H w.  Y reorthogonalises
+    // and normalises v_j (q_j = (v_j - Q a)/nu, nu^2 = c - |a|^2), which
+    // completes Hessenberg column j-1 (h += a, h_{j,j-1} = nu), and uses the
+    // Arnoldi relation A Q = Q_j H to form column j of A q_j = (w - Q_j H a)/nu
+    // and the next candidate v_{j+1} = A q_j - Q_j h_{:,j} in one sweep.
+
+    // Two dot products per basis vector in one read: with the v tile and the w tile.
+    static __device__ __forceinline__ void dot_tile2(const V* U, size_t n, const V* wsv, const V* wsw, int p0,
+                                                     int pend, const DotPlan& d, bool withw, T (&ar)[4],
+                                                     T (&ai)[4], T (&br)[4], T (&bi)[4]) {
+        const int lane = threadIdx.x & 31;
+        for (int sl = 0; sl < d.nvec; ++sl) {
+            const V* uq = U + (size_t)d.q[sl] * n + p0;
+            T sr = T(0), si = T(0), tr = T(0), ti = T(0);
+            for (int row = d.row0; row < d.row1; row += 8) {
+                V u[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int pl = (row + k) * 32 + lane;
+                    u[k] = (row + k < d.row1 && p0 + pl < pend) ? ldp(uq + pl) : mk2(T(0), T(0));
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (row + k < d.row1) {
+                        const int pl = (row + k) * 32 + lane;
+                        const V v = wsv[pl];
+                        sr += u[k].x * v.x + u[k].y * v.y;
+                        si += u[k].x * v.y - u[k].y * v.x;
+                        if (withw) {
+                            const V w = wsw[pl];
+                            tr += u[k].x * w.x + u[k].y * w.y;
+                            ti += u[k].x * w.y - u[k].y * w.x;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k == sl) { ar[k] += sr; ai[k] += si; br[k] += tr; bi[k] += ti; }
+            }
+        }
+    }
+
+    static __device__ void dx(Smem& sm, V* wsv, V* wsw, int item, int tb, int te, int j, bool matvec) {
+        const EngineArgs& A = sm.A;
+        const ItemDesc& it = A.item[item];
+        const int it_n = it.n, it_tile = it.tile;
+        const ProblemDesc& pr = A.prob[it.problem];
+        const size_t n = (size_t)it_n;
+        V* U = (V*)it.basis;
+        const V* uj = U + (size_t)j * n;
+        V* wv = U + (size_t)(j + 1) * n;
+        const T tj = (T)ldd(&it.st->vt[j & 1]);
+        const V shift = item_shift<V>(it);
+        const T* diag = prob_diag<T>(pr);
+        const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
+        const DotPlan d = dot_plan(j + 1, it_tile);
+        T ar[4] = {T(0), T(0), T(0), T(0)}, ai[4] = {T(0), T(0), T(0), T(0)};
+        T br[4] = {T(0), T(0), T(0), T(0)}, bi[4] = {T(0), T(0), T(0), T(0)};
+        for (int tile = tb; tile < te; ++tile) {
+            const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
+#pragma unroll
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                V v = mk2(T(0), T(0)), w = mk2(T(0), T(0));
+                if (p < pend) {
+                    const V u = ldp(uj + p);
+                    v = mk2(tj * u.x, tj * u.y);
+                    if (matvec) {
+                        w = stencil_apply<T, V>(uj, p, pr, diag, a0, a1, a2, shift);
+                        w.x *= tj;
+                        w.y *= tj;
+                        wv[p] = w;
+                    }
+                }
+                wsv[r * kBlock + threadIdx.x] = v;
+                wsw[r * kBlock + threadIdx.x] = w;
+            }
+            __syncthreads();
+            dot_tile2(U, n, wsv, wsw, p0, pend, d, matvec, ar, ai, br, bi);
+            __syncthreads();
+        }
+        dot_finish(sm, it, it.part1, tb, j + 1, d, ar, ai);
+        if (matvec) dot_finish(sm, it, it.part2, tb, j + 1, d, br, bi);
+    }
+
+    // Y prologue: every CTA of the item reduces X's partials and forms the
+    // step's coefficients; the CTA owning tile 0 also stores the columns.
+    static __device__ void dy_pro(Smem& sm, int item, const Runs& R, int j, bool last) {
+        const EngineArgs& A = sm.A;
+        const ItemDesc& it = A.item[item];
+        ItemState* S = it.st;
+        if (threadIdx.x <= j) sm.ssm[threadIdx.x] = threadIdx.x < j ? 1.0 : ldd(&S->vt[j & 1]);
+        __syncthreads();                                                   // q_i normalised; t_j
+        reduce_partials(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);        // a_i, c
+        if (!last) reduce_partials(sm, it.part2, it, R, j + 1, sm.ssm, sm.h2);   // b_i, d
+        const int nH = j >= 2 ? (j - 1) * (j + 2) / 2 : 0;                 // columns 0..j-2
+        for (int t = threadIdx.x; t < nH; t += kBlock) sm.Rsm[t] = ldp(&S->H[t]);
+        if (threadIdx.x < j) sm.hfin[threadIdx.x] = ldp(((j - 1) & 1 ? S->hcol2 : S->hcol) + threadIdx.x);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double aa2 = 0.0;
+            double2 ab = make_double2(0.0, 0.0);
+            for (int i = 0; i < j; ++i) {
+                const double2 a = sm.h1[i];
+                aa2 += a.x * a.x + a.y * a.y;
+                if (!last) ab = cadd(ab, cmul(cconj(a), sm.h2[i]));
+            }
+            const double nu2 = sm.h1[j].x - aa2;
+            const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
+            sm.yscal[0] = nu;
+            sm.yscal[1] = nu > 0.0 ? sm.ssm[j] / nu : 0.0;
+            sm.yscal[2] = nu > 0.0 ? 1.0 / nu : 0.0;
+            sm.ygq = ab;                                                    // a^H b, used below
+        }
+        __syncthreads();
+        const double nu = sm.yscal[0];
+        if (j >= 1 && threadIdx.x <= j)                                    // complete column j-1
+            sm.hfin[threadIdx.x] = threadIdx.x < j ? cadd(sm.hfin[threadIdx.x], sm.h1[threadIdx.x])
+                                                   : make_double2(nu, 0.0);
+        __syncthreads();
+        if (!last && threadIdx.x <= j) {
+            const int i = threadIdx.x;
+            double2 Ha = make_double2(0.0, 0.0);                            // (H a)_i over columns l < j
+            for (int l = max(i - 1, 0); l < j; ++l) {
+                const double2 Hil = l == j - 1 ? sm.hfin[i] : sm.Rsm[l * (l + 3) / 2 + i];
+                Ha = cadd(Ha, cmul(Hil, sm.h1[l]));
+            }
+            const double inv = sm.yscal[2];
+            double2 h;
+            if (i < j) h = cscale(csub(sm.h2[i], Ha), inv);
+            else h = cscale(csub(cscale(csub(sm.h2[j], sm.ygq), inv), Ha), inv);
+            sm.hnew[i] = h;
+            const double2 gam = cadd(cscale(Ha, inv), h);
+            if (i < j) {
+                const double2 ca = cscale(sm.h1[i], sm.ssm[i] * inv);      // q_j = t_j/nu u_j - sum ca_i u_i
+                sm.coef[i] = ca;
+                sm.coeff[i] = make_float2((float)ca.x, (float)ca.y);
+                const double2 cg = cscale(gam, sm.ssm[i]);                  // v_{j+1} = w/nu - sum cg_i u_i - gam_j q_j
+                sm.coefG[i] = cg;
+                sm.coefGf[i] = make_float2((float)cg.x, (float)cg.y);
+            }
+        }
+        __syncthreads();
+        if (!last && threadIdx.x == 0) {
+            const int i = j;
+            double2 Ha = make_double2(0.0, 0.0);
+            for (int l = max(i - 1, 0); l < j; ++l) {
+                const double2 Hil = l == j - 1 ? sm.hfin[i] : sm.Rsm[l * (l + 3) / 2 + i];
+                Ha = cadd(Ha, cmul(Hil, sm.h1[l]));
+            }
+            sm.ygq = cadd(cscale(Ha, sm.yscal[2]), sm.hnew[j]);            // gamma_j
+        }
+        __syncthreads();
+    }
+
+    // Y sweep: q_j into slot j, v_{j+1} into slot j+1.
+    static __device__ void dy(Smem& sm, int item, int tb, int te, int j) {
+        const ItemDesc& it = sm.A.item[item];
+        const int it_n = it.n, it_tile = it.tile;
+        const size_t n = (size_t)it_n;
+        V* U = (V*)it.basis;
+        V* uj = U + (size_t)j * n;
+        V* wv = U + (size_t)(j + 1) * n;
+        const T tq = (T)sm.yscal[1], tw = (T)sm.yscal[2];
+        const V gq = cvt2<V>(sm.ygq);
+        for (int tile = tb; tile < te; ++tile) {
+            const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
+            V qa[kPPT], va[kPPT];
+#pragma unroll
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                const V u = p < pend ? ldp(uj + p) : mk2(T(0), T(0));
+                const V w = p < pend ? ldp(wv + p) : mk2(T(0), T(0));
+                qa[r] = mk2(tq * u.x, tq * u.y);
+                va[r] = mk2(tw * w.x, tw * w.y);
+            }
+#pragma unroll 2
+            for (int q = 0; q < j; ++q) {
+                const V* uq = U + (size_t)q * n;
+                const V ca = coef_at<V>(sm, q), cg = coefg_at<V>(sm, q);
+#pragma unroll
+                for (int r = 0; r < kPPT; ++r) {
+                    const int p = p0 + r * kBlock + threadIdx.x;
+                    const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                    qa[r].x -= ca.x * u.x - ca.y * u.y;
+                    qa[r].y -= ca.x * u.y + ca.y * u.x;
+                    va[r].x -= cg.x * u.x - cg.y * u.y;
+                    va[r].y -= cg.x * u.y + cg.y * u.x;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                if (p < pend) {
+                    va[r].x -= gq.x * qa[r].x - gq.y * qa[r].y;
+                    va[r].y -= gq.x * qa[r].y + gq.y * qa[r].x;
+                    uj[p] = qa[r];
+                    wv[p] = va[r];
+                }
+            }
+        }
+    }
+
     // E2 prologue: y = R^{-1} g (back substitution, FP64), coefficients y_i s_i.
     static __device__ void e2_pro(Smem& sm, int item) {
         const ItemDesc& it = sm.A.item[item];
@@ -775,7 +995,7 @@ struct Phases {
         for (int t = threadIdx.x; t < nR; t += kBlock) sm.Rsm[t] = ldp(&S->R[t]);
         if (threadIdx.x < k) {
             sm.gsm[threadIdx.x] = ldp(&S->g[threadIdx.x]);
-            sm.ssm[threadIdx.x] = ldd(&src.st->s[threadIdx.x]);
+            sm.ssm[threadIdx.x] = sm.A.ortho ? 1.0 : ldd(&src.st->s[threadIdx.x]);
         }
         if (threadIdx.x == 0) {
             sm.kk = k;
@@ -855,6 +1075,7 @@ __device__ void item_e4(const EngineArgs& A, int item, const Runs& R) {
     if (it.is_group) {                              // shared Krylov basis of the members
         if (cycles == 0 && beta > 0.0 && beta <= 1e300) {
             S->s[0] = 1.0 / beta;
+            S->vt[0] = 1.0 / beta;
             S->k = 0;
             S->cycles = 1;
             S->total_iters = 0;
@@ -877,6 +1098,7 @@ __device__ void item_e4(const EngineArgs& A, int item, const Runs& R) {
         status = shared ? ST_SHARED : ST_ARNOLDI;
         S->shared = shared ? 1 : 0;
         S->s[0] = 1.0 / beta;
+        S->vt[0] = 1.0 / beta;
         S->g[0] = make_double2(beta, 0.0);
         S->k = 0;
         S->cycles = cycles + 1;
@@ -1025,6 +1247,137 @@ __device__ void group_p4(const EngineArgs& A, int gitem, const Runs& R, int j) {
     }
 }
 
+// Delayed CGS2, step j: the CTA owning tile 0 of the item stores the completed
+// column j-1 and the pending column j, and applies the Givens rotation of
+// column j-1 (one warp; for a group, lane = member with its shifted column).
+__device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool last) {
+    const ItemDesc& it = A.item[item];
+    ItemState* S = it.st;
+    const double nu = sm.yscal[0];
+    if (j >= 1 && threadIdx.x <= j) S->H[(j - 1) * (j + 2) / 2 + threadIdx.x] = sm.hfin[threadIdx.x];
+    if (!last && threadIdx.x <= j) ((j & 1) ? S->hcol2 : S->hcol)[threadIdx.x] = sm.hnew[threadIdx.x];
+    if (threadIdx.x == 0) S->vt[(j + 1) & 1] = 1.0;                 // v_{j+1} is stored raw
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const int jj = j - 1;                                            // column completed at this step
+    if (!it.is_group) {
+        if (j == 0) {
+            if (lane == 0) S->g[0] = cscale(ldp(&S->g[0]), nu);      // q_0 renormalised by nu
+            return;
+        }
+        if (lane < jj) {
+            sm.gcs_s[lane] = ldd(&S->cs[lane]);
+            sm.gsn_s[lane] = ldp(&S->sn[lane]);
+        }
+        __syncwarp();
+        if (lane != 0) return;
+        const int col = jj * (jj + 1) / 2;
+        double2 carry = sm.hfin[0];
+        for (int i = 0; i < jj; ++i) {
+            const double2 b = sm.hfin[i + 1];
+            const double c = sm.gcs_s[i];
+            const double2 sn = sm.gsn_s[i];
+            const double2 nh = cadd(cscale(carry, c), cmul(sn, b));
+            carry = cadd(cscale(cmul(cconj(sn), carry), -1.0), cscale(b, c));
+            S->R[col + i] = nh;
+        }
+        const double hn = nu;
+        const double aa = sqrt(carry.x * carry.x + carry.y * carry.y);
+        const double rr = sqrt(aa * aa + hn * hn);
+        double c;
+        double2 sn, rjj;
+        if (aa == 0.0) {
+            c = 0.0;
+            sn = make_double2(1.0, 0.0);
+            rjj = make_double2(hn, 0.0);
+        } else {
+            c = aa / rr;
+            sn = cscale(carry, hn / (aa * rr));
+            rjj = cscale(carry, rr / aa);
+        }
+        const double2 gj = ldp(&S->g[jj]);
+        const double2 gj1 = cscale(cmul(cconj(sn), gj), -1.0);
+        S->R[col + jj] = rjj;
+        S->cs[jj] = c;
+        S->sn[jj] = sn;
+        S->g[jj] = cscale(gj, c);
+        S->g[jj + 1] = gj1;
+        S->k = j;
+        const int total = ldi(&S->total_iters) + 1;
+        S->total_iters = total;
+        const double res = sqrt(gj1.x * gj1.x + gj1.y * gj1.y);
+        const bool end = !(res > ldd(&S->cycle_tol_abs)) || last || total >= A.max_iters || !(hn > 0.0) ||
+                         !(rr > 0.0);
+        if (end) S->sum_k2 = ldi(&S->sum_k2) + j * j;
+        __threadfence();
+        S->status = end ? ST_CYCLE_END : ST_ARNOLDI;
+        return;
+    }
+    // group: members' rotations of their shifted copies of column jj
+    const int nm = it.nmembers;
+    bool active = false;
+    for (int mi = lane; mi < nm; mi += 32) {
+        const ItemDesc& md = A.item[it.member0 + mi];
+        ItemState* M = md.st;
+        if (ldi(&M->status) != ST_SHARED) continue;
+        if (j == 0) {
+            M->g[0] = cscale(ldp(&M->g[0]), nu);
+            active = true;
+            continue;
+        }
+        const double2 sh = md.shift;
+        double2 carry = sm.hfin[0];
+        if (jj == 0) carry = csub(carry, sh);
+        const int col = jj * (jj + 1) / 2;
+        for (int i = 0; i < jj; ++i) {
+            double2 b = sm.hfin[i + 1];
+            if (i + 1 == jj) b = csub(b, sh);
+            const double c = ldd(it.gcs + (size_t)i * nm + mi);
+            const double2 sn = ldp(it.gsn + (size_t)i * nm + mi);
+            const double2 nh = cadd(cscale(carry, c), cmul(sn, b));
+            carry = cadd(cscale(cmul(cconj(sn), carry), -1.0), cscale(b, c));
+            M->R[col + i] = nh;
+        }
+        const double hn = nu;
+        const double aa = sqrt(carry.x * carry.x + carry.y * carry.y);
+        const double rr = sqrt(aa * aa + hn * hn);
+        double c;
+        double2 sn, rjj;
+        if (aa == 0.0) {
+            c = 0.0;
+            sn = make_double2(1.0, 0.0);
+            rjj = make_double2(hn, 0.0);
+        } else {
+            c = aa / rr;
+            sn = cscale(carry, hn / (aa * rr));
+            rjj = cscale(carry, rr / aa);
+        }
+        const double2 gj = ldp(&M->g[jj]);
+        const double2 gj1 = cscale(cmul(cconj(sn), gj), -1.0);
+        it.gcs[(size_t)jj * nm + mi] = c;
+        it.gsn[(size_t)jj * nm + mi] = sn;
+        M->R[col + jj] = rjj;
+        M->g[jj] = cscale(gj, c);
+        M->g[jj + 1] = gj1;
+        M->k = j;
+        const int total = ldi(&M->total_iters) + 1;
+        M->total_iters = total;
+        const double res = sqrt(gj1.x * gj1.x + gj1.y * gj1.y);
+        const bool end = !(res > ldd(&M->cycle_tol_abs)) || last || total >= A.max_iters || !(hn > 0.0) ||
+                         !(rr > 0.0);
+        if (end) M->sum_k2 = ldi(&M->sum_k2) + j * j;
+        __threadfence();
+        M->status = end ? ST_CYCLE_END : ST_SHARED;
+        active = active || !end;
+    }
+    const bool any = __any_sync(0xffffffffu, active);
+    if (lane == 0) {
+        S->k = j;
+        __threadfence();
+        S->status = (any && !last) ? ST_ARNOLDI : ST_IDLE;
+    }
+}
+
 // PS: psi' = alpha_0 b + sum_k alpha_k x_k for one tile of a problem.
 __device__ void task_pole_sum(const Smem& sm, int prob, int tile, int sub) {
     const ProblemDesc& pr = sm.A.prob[prob];
@@ -1162,7 +1515,31 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(const __grid_constant
             for (int l = gwarp; l < sm.nl; l += nwarps) item_e4(A, list[l], item_runs(prefix, l, sm.ntasks));
             if (!phase_sync(A, TR_E4, &tcount)) return;
 
-            for (int j = 0; j < A.m; ++j) {
+            for (int j = 0; A.ortho && j <= A.m; ++j) {             // delayed CGS2
+                build_list(sm, list, prefix, 1u << ST_ARNOLDI);
+                if (sm.nl == 0) break;
+                const bool last = j == A.m;
+                my_range(sm.ntasks, &s, &e);
+                for (int t = s; t < e;) {
+                    const int l = find_slot(prefix, sm.nl, t);
+                    const int te = min(prefix[l + 1], e) - prefix[l];
+                    P::dx(sm, ws, ws + kTile, list[l], t - prefix[l], te, j, !last);
+                    t = prefix[l] + te;
+                }
+                if (!phase_sync(A, TR_P1, &tcount)) return;
+                for (int t = s; t < e;) {
+                    const int l = find_slot(prefix, sm.nl, t);
+                    const int te = min(prefix[l + 1], e) - prefix[l];
+                    const int tb = t - prefix[l];
+                    P::dy_pro(sm, list[l], item_runs(prefix, l, sm.ntasks), j, last);
+                    if (tb == 0) dy_commit(A, sm, list[l], j, last);
+                    __syncthreads();
+                    if (!last) P::dy(sm, list[l], tb, te, j);
+                    t = prefix[l] + te;
+                }
+                if (!phase_sync(A, TR_P3, &tcount)) return;
+            }
+            for (int j = 0; !A.ortho && j < A.m; ++j) {             // CGS2
                 build_list(sm, list, prefix, 1u << ST_ARNOLDI);
                 if (sm.nl == 0) break;
                 my_range(sm.ntasks, &s, &e);
@@ -1256,9 +1633,11 @@ __global__ void __launch_bounds__(kBlock) pole_sum_kernel(const ProblemDesc* __r
 
 }  // namespace
 
-size_t engine_smem_bytes(int nitems) {
-    // list + prefix (ints, rounded to 16 bytes) + one tile of double2 for staging
-    return (size_t)((2 * nitems + 2 + 3) & ~3) * sizeof(int) + (size_t)kTile * sizeof(double2);
+size_t engine_smem_bytes(int nitems, bool fp32, int ortho) {
+    // list + prefix (ints, rounded to 16 bytes) + staging tiles of the basis type
+    // (delayed CGS2 stages the v and w tiles of a step together)
+    return (size_t)((2 * nitems + 2 + 3) & ~3) * sizeof(int) +
+           (ortho ? 2 : 1) * (size_t)kTile * (fp32 ? sizeof(float2) : sizeof(double2));
 }
 
 static void* engine_fn(bool fp32) {
@@ -1267,7 +1646,7 @@ static void* engine_fn(bool fp32) {
 
 int engine_max_grid(bool fp32, size_t smem, int device) {
     void* fn = engine_fn(fp32);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(96 * 1024)) != cudaSuccess)
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(160 * 1024)) != cudaSuccess)
         return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kBlock, smem) != cudaSuccess) return 0;

@@ -94,8 +94,11 @@ struct ItemState {
     double cs[kMaxM];
     double2 sn[kMaxM];
     double2 g[kMaxM + 1];
-    double2 hcol[kMaxM + 1];
+    double2 hcol[kMaxM + 1];               // pending column (CGS2; delayed CGS2: even steps)
+    double2 hcol2[kMaxM + 1];              // delayed CGS2: pending column of odd steps
+    double vt[2];                          // delayed CGS2: scale of v_j, by parity of j
     double2 R[kMaxM * (kMaxM + 1) / 2];    // packed upper triangle, column j at j(j+1)/2
+    double2 H[kMaxM * (kMaxM + 3) / 2];    // unrotated Hessenberg, column l (l+2 entries) at l(l+3)/2
 };
 
 // Per-call statistics of one item (zeroed before every launch).
@@ -112,8 +115,8 @@ struct EngineArgs {
     int m;               // restart length
     int max_iters;
     int max_sub;         // largest nsub over problems
-    int pv;              // pitch of the partial buffers (>= m)
-    int pad;
+    int pv;              // pitch of the partial buffers (>= m + 1)
+    int ortho;           // 0: CGS2 (two reductions per step), 1: delayed CGS2 (one reduction)
     double tol;          // relative residual target
     double inner_tol;    // relative reduction per cycle (mixed), 0 = none
     unsigned long long timeout_ns;
@@ -134,7 +137,7 @@ enum : int { TR_INIT = 0, TR_E3 = 1, TR_E4 = 2, TR_P1 = 3, TR_P2 = 4, TR_P3 = 5,
 cudaError_t launch_engine(bool fp32_basis, const EngineArgs& args, const IOArgs& io, int grid,
                           size_t smem, cudaStream_t stream);
 int engine_max_grid(bool fp32_basis, size_t smem, int device);
-size_t engine_smem_bytes(int nitems);
+size_t engine_smem_bytes(int nitems, bool fp32, int ortho);
 
 // Single-stage kernels.
 cudaError_t launch_apply(const ProblemDesc* dprob, const ItemDesc* ditems, int K, const double2* v,

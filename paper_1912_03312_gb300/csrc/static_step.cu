@@ -70,6 +70,8 @@ extern "C" int rexi_substep_static(const rexi_grid* g, const double* V, double t
     if (opt.precision != REXI_FP64 && opt.precision != REXI_MIXED) return REXI_EINVAL;
     if (opt.restart_m < 1 || opt.restart_m > REXI_MAX_RESTART || opt.max_iters < 1 || !(opt.tol > 0.0))
         return REXI_EINVAL;
+    if ((opt.ortho != 0 && opt.ortho != 1) || (opt.ortho == 1 && opt.restart_m > REXI_MAX_RESTART - 1))
+        return REXI_EINVAL;
     long long n = 1;
     int dims[3] = {1, 1, 1};
     double a[3] = {0.0, 0.0, 0.0};
@@ -83,7 +85,7 @@ extern "C" int rexi_substep_static(const rexi_grid* g, const double* V, double t
     const bool fp32 = opt.precision == REXI_MIXED;
     const int m = opt.restart_m;
     const int ntiles = (int)((n + rexi::kTile - 1) / rexi::kTile);
-    const int pv = 32;
+    const int pv = 40;
     const size_t esz = fp32 ? sizeof(float2) : sizeof(double2);
 
     // Carve the workspace; reject what does not fit.
@@ -176,6 +178,7 @@ extern "C" int rexi_substep_static(const rexi_grid* g, const double* V, double t
     A.max_iters = opt.max_iters;
     A.max_sub = 1;
     A.pv = pv;
+    A.ortho = opt.ortho;
     A.tol = opt.tol;
     A.inner_tol = fp32 ? opt.inner_tol : 0.0;
     A.timeout_ns = 4000000000ull;
@@ -187,7 +190,7 @@ extern "C" int rexi_substep_static(const rexi_grid* g, const double* V, double t
     std::memset(&io, 0, sizeof(io));
     io.in[0] = (const double2*)psi_in;
     io.out[0] = (double2*)psi_out;
-    const size_t smem = rexi::engine_smem_bytes(K);
+    const size_t smem = rexi::engine_smem_bytes(K, fp32, A.ortho);
     const int maxg = rexi::engine_max_grid(fp32, smem, dev);
     if (maxg <= 0) return REXI_ECUDA;
     const int grid = std::max(1, std::min(maxg, K * ntiles));

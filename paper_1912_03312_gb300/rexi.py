@@ -33,7 +33,7 @@ def _check_state(t, n, name):
 
 def options(precision="mixed", restart=30, max_iters=2000, tol=0.0, inner_tol=1e-5, R1=0.0,
             eps_target=1e-9, allow_substeps=True, stabilize_eps=0.0, want_backward=False, device=-1,
-            shared_first_cycle=True):
+            shared_first_cycle=True, ortho="dcgs2"):
     o = N.Options()
     N.load().rexi_options_default(C.byref(o))
     o.precision = N.REXI_MIXED if precision == "mixed" else N.REXI_FP64
@@ -48,6 +48,9 @@ def options(precision="mixed", restart=30, max_iters=2000, tol=0.0, inner_tol=1e
     o.want_backward = 1 if want_backward else 0
     o.device = int(device)
     o.shared_first_cycle = 1 if shared_first_cycle else 0
+    if ortho not in ("dcgs2", "cgs2"):
+        raise ValueError("ortho must be 'dcgs2' or 'cgs2'")
+    o.ortho = 1 if ortho == "dcgs2" else 0
     return o
 
 

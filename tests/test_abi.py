@@ -107,6 +107,12 @@ def test_argument_validation_before_device(lib):
     lib.rexi_options_default(C.byref(o))
     o.restart_m = 64
     assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    o.restart_m = N.REXI_MAX_RESTART          # delayed CGS2 projects m+1 vectors: at most MAX-1
+    assert o.ortho == 1
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    o.ortho = 2
+    o.restart_m = 30
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
     assert h.value is None
 
 

@@ -93,13 +93,14 @@ def test_solve_poles_matches_oracle(precision, tol_pole, n):
         assert st["resid"][k] <= 1e-13
 
 
+@pytest.mark.parametrize("ortho", ["dcgs2", "cgs2"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("K,R1,n,dt", [(8, 8.0, (130, 101), 0.4), (16, 24.0, (300,), 1.0),
                                        (16, 24.0, (20, 18, 14), 0.3), (32, 68.0, (96, 80), 0.5)])
-def test_step_matches_oracle(precision, K, R1, n, dt):
+def test_step_matches_oracle(precision, K, R1, n, dt, ortho):
     g, V, psi = wl.random_problem(35, n, box=8.0)
     tol = 2e-14 if K == 8 else 1e-13
-    lp = library_plan(g, V, dt, K, R1, precision=precision, tol=tol)
+    lp = library_plan(g, V, dt, K, R1, precision=precision, tol=tol, ortho=ortho)
     orc = OraclePlan(g, V, dt, K, R1)
     out, st = lp.step(to_dev(psi), stats=True)
     assert st["status"] == 0 and st["n_sub"] == orc.n_sub
@@ -193,13 +194,14 @@ def test_nan_input_fails_cleanly():
     assert good["status"] == 0
 
 
+@pytest.mark.parametrize("ortho", ["dcgs2", "cgs2"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("K,R1,n,dt", [(16, 24.0, (130, 101), 0.5), (32, 68.0, (96, 80), 0.5), (8, 8.0, (9, 7, 5), 0.2)])
-def test_independent_bases_match_oracle(precision, K, R1, n, dt):
+def test_independent_bases_match_oracle(precision, K, R1, n, dt, ortho):
     # shared_first_cycle=0: every pole keeps its own Krylov basis from the start
     g, V, psi = wl.random_problem(37, n, box=8.0)
     tol = 1e-13
-    lp = library_plan(g, V, dt, K, R1, precision=precision, tol=tol, shared_first_cycle=False)
+    lp = library_plan(g, V, dt, K, R1, precision=precision, tol=tol, shared_first_cycle=False, ortho=ortho)
     orc = OraclePlan(g, V, dt, K, R1)
     out, st = lp.step(to_dev(psi), stats=True)
     assert st["status"] == 0
@@ -221,3 +223,19 @@ def test_shared_cycle_needs_fewer_basis_sweeps():
     A = lp.info()["amplification"]
     assert relerr(outs[0], outs[1]) < max(1e-10, 4.0 * A * 1e-13)
     assert its[0] >= 1 and its[1] >= 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("m", [1, 2, 7, 31])
+def test_restart_lengths_match_oracle(precision, m):
+    # short restarts exercise the first and last steps of a cycle; 31 is the
+    # longest the one-reduction Arnoldi accepts
+    g, V, psi = wl.random_problem(39, (72, 56), box=8.0)
+    K, R1, dt, tol = 16, 24.0, 0.5, 1e-13
+    lp = library_plan(g, V, dt, K, R1, precision=precision, tol=tol, restart=m, max_iters=20000)
+    orc = OraclePlan(g, V, dt, K, R1)
+    out, st = lp.step(to_dev(psi), stats=True)
+    assert st["status"] == 0, st["status"]
+    ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
+    floor = 1e-10 if precision == "fp64" else 1e-6
+    assert relerr(out.cpu().numpy(), ref) < max(floor, 2.0 * orc.A * tol)
