@@ -95,6 +95,15 @@ typedef struct {
                               (the previous vector is reorthogonalised and normalised together
                               with the projection of the new one; restart_m at most
                               REXI_MAX_RESTART - 1); 0: CGS2, two reductions per step        */
+    int    window;         /* with ortho = 1: 0 (default) orthogonalise every new vector against
+                              the whole basis; L >= 2: only against the last L vectors (a
+                              truncated, quasi-GMRES basis).  H is real symmetric, so tau H - z
+                              is a shifted Hermitian operator whose Hessenberg matrix is
+                              tridiagonal in exact arithmetic and L >= 2 loses nothing there;
+                              in floating point the columns are orthonormal only locally and
+                              every residual estimate is taken as sqrt(k+1) |g_{k+1}|, an
+                              upper bound of the true residual for unit columns.  Cost per
+                              Arnoldi step: O(L) basis vectors instead of O(k).            */
 } rexi_options;
 
 /* What a plan computed (host copy, filled by rexi_plan_info). */
@@ -271,12 +280,26 @@ int rexi_plan_set_tiles(rexi_plan* plan, int pole_tile, int group_tile, int ctas
  * grid-wide barrier, the phase that ended there and the GPU global timer (ns).
  * Phase codes: 0 substep start, 1 FP64 residual, 2 cycle decision, 3 matvec +
  * first dot sweep, 4 second CGS sweep, 5 CGS update, 6 Givens, 7 x update,
- * 8 pole sum / adjoint accumulation, 99 launch start.
+ * 8 pole sum / adjoint accumulation, 9 delayed-CGS2 matvec + dots, 10 delayed-CGS2
+ * normalisation + projection + Givens, 99 launch start.
  * rexi_plan_read_trace synchronises the plan's last stream, copies up to cap
  * (phase, ns) pairs of the last launch into out[2*cap] and returns how many
  * were recorded (which may exceed cap), or a negative status. */
 int rexi_plan_set_trace(rexi_plan* plan, int capacity);
 int rexi_plan_read_trace(rexi_plan* plan, long long* out, int cap);
+
+/* Per-CTA barrier arrivals, for load-balance diagnosis.  After
+ * rexi_plan_set_cta_trace(plan, phases) (0 disables) every engine launch of the
+ * plan records, for each of its first `phases` grid-wide barriers, the global
+ * timer (ns) at which each CTA's threads had all arrived.
+ * rexi_plan_read_cta_trace synchronises the plan's last stream, sets *grid to
+ * the CTA count of the last launch and copies whole barriers, row by row
+ * (row r = barrier r, grid entries), while they fit in out[cap]; it returns the
+ * number of barriers recorded (which may exceed what was copied) or a negative
+ * status.  Barrier r matches record r of rexi_plan_read_trace, whose time is
+ * the barrier's release as seen by CTA 0. */
+int rexi_plan_set_cta_trace(rexi_plan* plan, int phases);
+int rexi_plan_read_cta_trace(rexi_plan* plan, long long* out, int cap, int* grid);
 
 /* Number of CUDA kernel launches issued by the last call on the plan. */
 int rexi_plan_last_launches(const rexi_plan* plan);

@@ -35,7 +35,7 @@ class Options(C.Structure):
                 ("tol", C.c_double), ("inner_tol", C.c_double), ("R1", C.c_double),
                 ("eps_target", C.c_double), ("allow_substeps", C.c_int), ("stabilize_eps", C.c_double),
                 ("want_backward", C.c_int), ("device", C.c_int), ("shared_first_cycle", C.c_int),
-                ("ortho", C.c_int)]
+                ("ortho", C.c_int), ("window", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -79,6 +79,8 @@ SIGNATURES = {
     "rexi_plan_set_trace": (C.c_int, [_P, C.c_int]),
     "rexi_plan_set_tiles": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "rexi_plan_read_trace": (C.c_int, [_P, C.POINTER(C.c_longlong), C.c_int]),
+    "rexi_plan_set_cta_trace": (C.c_int, [_P, C.c_int]),
+    "rexi_plan_read_cta_trace": (C.c_int, [_P, C.POINTER(C.c_longlong), C.c_int, C.POINTER(C.c_int)]),
     "rexi_status_string": (C.c_char_p, [C.c_int]),
     "rexi_substep_static": (C.c_int, [C.POINTER(Grid), _P, C.c_double, C.c_double, C.c_int, _D, _D, _D,
                                       C.POINTER(Options), _P, _P, _P, C.POINTER(Stats)]),

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -94,7 +95,19 @@ struct rexi_plan {
     bool has_backward = false;
     unsigned long long* d_trace = nullptr;
     int trace_cap = 0;
+    unsigned long long* d_cta_trace = nullptr;
+    int cta_trace_phases = 0;
+    int cta_trace_stride = 0;
+    int last_grid = 0;
     int generation = 0;                          // bumped when the item workspace moves
+    unsigned long long uid = 0;                  // unique over the process (never reused)
+    // descriptors of the last batched combination led by this plan
+    std::vector<unsigned long long> batch_key;   // uids of the plans, in order
+    std::vector<int> batch_gens;
+    ProblemDesc* d_batch_prob = nullptr;
+    ItemDesc* d_batch_items = nullptr;
+    size_t batch_cap_prob = 0, batch_cap_items = 0;
+    int batch_nitems = 0;
 };
 
 namespace {
@@ -341,6 +354,7 @@ EngineArgs base_args(const rexi_plan* p, int mode, const DescSet& set, int nprob
     A.max_sub = max_sub;
     A.pv = p->pv;
     A.ortho = p->opt.ortho;
+    A.window = p->opt.window;
     A.tol = p->tol;
     A.inner_tol = p->fp32 ? p->opt.inner_tol : 0.0;
     A.timeout_ns = kTimeoutNs;
@@ -350,6 +364,9 @@ EngineArgs base_args(const rexi_plan* p, int mode, const DescSet& set, int nprob
     A.err = p->d_err;
     A.trace = p->trace_cap > 0 ? p->d_trace : nullptr;
     A.trace_cap = p->trace_cap;
+    A.cta_trace = p->cta_trace_phases > 0 ? p->d_cta_trace : nullptr;
+    A.cta_trace_phases = p->cta_trace_phases;
+    A.cta_trace_stride = p->cta_trace_stride;
     return A;
 }
 
@@ -390,6 +407,7 @@ int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles,
     e = rexi::launch_engine(p->fp32, A, io, grid, smem, stream);
     p->last_stream = stream;
     p->last_launches = 1;
+    p->last_grid = grid;
     return e == cudaSuccess ? REXI_OK : cuda_fail(e);
 }
 
@@ -461,6 +479,7 @@ int rexi_options_default(rexi_options* o) {
     o->device = -1;
     o->shared_first_cycle = 1;
     o->ortho = 1;
+    o->window = 0;
     return REXI_OK;
 }
 
@@ -495,6 +514,8 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     if (opt.restart_m < 1 || opt.restart_m > REXI_MAX_RESTART || opt.max_iters < 1) return REXI_EINVAL;
     if (opt.ortho != 0 && opt.ortho != 1) return REXI_EINVAL;
     if (opt.ortho == 1 && opt.restart_m > REXI_MAX_RESTART - 1) return REXI_EINVAL;   // m+1 dot vectors
+    if (opt.window < 0 || opt.window == 1 || opt.window > REXI_MAX_RESTART || (opt.window > 0 && opt.ortho != 1))
+        return REXI_EINVAL;
     if (!(opt.tol >= 0.0) || !(opt.R1 >= 0.0) || !(opt.inner_tol >= 0.0) || !(opt.stabilize_eps >= 0.0) ||
         !(opt.stabilize_eps < 1.0))
         return REXI_EINVAL;
@@ -510,8 +531,10 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     if (n > (1ll << 30)) return REXI_EINVAL;
     if (!finite_all(V, (size_t)n)) return REXI_EINVAL;
 
+    static std::atomic<unsigned long long> next_uid{1};
     rexi_plan* p = new (std::nothrow) rexi_plan();
     if (!p) return REXI_ENOMEM;
+    p->uid = next_uid.fetch_add(1);
     p->grid = *g;
     p->opt = opt;
     p->n = (int)n;
@@ -783,7 +806,7 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
         rexi_plan* p = plans[b];
         if (!p || !psi_in[b] || !psi_out[b]) return REXI_EINVAL;
         if (p->device != p0->device || p->fp32 != p0->fp32 || p->m != p0->m ||
-            p->opt.ortho != p0->opt.ortho) return REXI_EINVAL;
+            p->opt.ortho != p0->opt.ortho || p->opt.window != p0->opt.window) return REXI_EINVAL;
         const int ng = p->shared ? 1 : 0;
         for (int c = 0; c < b; ++c)
             if (plans[c] == p) return REXI_EINVAL;         // one plan's workspace per problem
@@ -796,24 +819,16 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
     DeviceGuard guard(p0->device);
     cudaStream_t s = (cudaStream_t)stream;
 
-    // Descriptor set of this combination of plans, cached in the first plan.
-    struct BatchCache {
-        std::vector<rexi_plan*> key;
-        std::vector<int> gens;
-        ProblemDesc* d_prob = nullptr;
-        ItemDesc* d_items = nullptr;
-        int nitems = 0;
-    };
-    static std::mutex mu;
-    static std::vector<std::pair<rexi_plan*, BatchCache>> caches;
-    std::lock_guard<std::mutex> lk(mu);
-    BatchCache* bc = nullptr;
-    for (auto& c : caches)
-        if (c.first == p0) bc = &c.second;
-    const std::vector<rexi_plan*> key(plans, plans + B);
+    // Descriptor set of this combination of plans, cached in the first plan and
+    // keyed by the plans' process-unique ids and workspace generations (a plan
+    // created where a destroyed one lived never matches a stale entry).
+    std::vector<unsigned long long> key(B);
     std::vector<int> gens(B);
-    for (int b = 0; b < B; ++b) gens[b] = plans[b]->generation;
-    if (!bc || bc->key != key || bc->gens != gens) {
+    for (int b = 0; b < B; ++b) {
+        key[b] = plans[b]->uid;
+        gens[b] = plans[b]->generation;
+    }
+    if (p0->batch_key != key || p0->batch_gens != gens || !p0->d_batch_items) {
         std::vector<ProblemDesc> probs;
         std::vector<ItemDesc> items;
         for (int b = 0; b < B; ++b) {
@@ -822,22 +837,25 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
             append_items(p, false, b, base, &items);
             probs.push_back(make_problem(p, p->n_sub, base, (int)items.size() - base));
         }
-        if (!bc) {
-            caches.push_back(std::make_pair(p0, BatchCache()));
-            bc = &caches.back().second;
-        }
-        if (cudaStreamSynchronize(s) != cudaSuccess) return REXI_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return REXI_ECUDA;   // old descriptors may be in use
         int r;
-        if ((r = dalloc(p0, &bc->d_prob, probs.size()))) return r;
-        if ((r = dalloc(p0, &bc->d_items, items.size()))) return r;
-        if (cudaMemcpy(bc->d_prob, probs.data(), sizeof(ProblemDesc) * probs.size(), cudaMemcpyHostToDevice) !=
-                cudaSuccess ||
-            cudaMemcpy(bc->d_items, items.data(), sizeof(ItemDesc) * items.size(), cudaMemcpyHostToDevice) !=
-                cudaSuccess)
+        if (probs.size() > p0->batch_cap_prob) {
+            if ((r = dalloc(p0, &p0->d_batch_prob, probs.size()))) return r;
+            p0->batch_cap_prob = probs.size();
+        }
+        if (items.size() > p0->batch_cap_items) {
+            if ((r = dalloc(p0, &p0->d_batch_items, items.size()))) return r;
+            p0->batch_cap_items = items.size();
+        }
+        p0->batch_key.clear();                     // invalid until the copies succeed
+        if (cudaMemcpy(p0->d_batch_prob, probs.data(), sizeof(ProblemDesc) * probs.size(),
+                       cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(p0->d_batch_items, items.data(), sizeof(ItemDesc) * items.size(),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
             return REXI_ECUDA;
-        bc->key = key;
-        bc->gens = gens;
-        bc->nitems = (int)items.size();
+        p0->batch_key = key;
+        p0->batch_gens = gens;
+        p0->batch_nitems = (int)items.size();
     }
     IOArgs io{};
     for (int b = 0; b < B; ++b) {
@@ -845,9 +863,9 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
         io.out[b] = (double2*)psi_out[b];
     }
     DescSet set;
-    set.d_prob = bc->d_prob;
-    set.d_items = bc->d_items;
-    set.nitems = bc->nitems;
+    set.d_prob = p0->d_batch_prob;
+    set.d_items = p0->d_batch_items;
+    set.nitems = p0->batch_nitems;
     EngineArgs A = base_args(p0, rexi::MODE_STEP, set, B, max_sub);
     // statistics of every plan are zeroed, the barrier/error words are p0's
     for (int b = 1; b < B; ++b)
@@ -867,6 +885,7 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
     for (int b = 0; b < B; ++b) {
         plans[b]->last_stream = s;
         plans[b]->last_launches = 1;
+        plans[b]->last_grid = grid;
     }
     if (e != cudaSuccess) return cuda_fail(e);
     if (!st) return REXI_OK;
@@ -939,6 +958,38 @@ int rexi_plan_set_trace(rexi_plan* p, int capacity) {
     }
     p->trace_cap = capacity;
     return REXI_OK;
+}
+
+int rexi_plan_set_cta_trace(rexi_plan* p, int phases) {
+    if (!p || phases < 0) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    const int stride = 8 * sm_count(p->device);          // no more than 8 CTAs of 256 threads per SM
+    if (phases > 0 && (phases > p->cta_trace_phases || stride != p->cta_trace_stride)) {
+        int st = dalloc(p, &p->d_cta_trace, (size_t)1 + (size_t)phases * (size_t)stride);
+        if (st) return st;
+        if (cudaMemset(p->d_cta_trace, 0, sizeof(unsigned long long)) != cudaSuccess) return REXI_ECUDA;
+        p->cta_trace_stride = stride;
+    }
+    p->cta_trace_phases = phases;
+    return REXI_OK;
+}
+
+int rexi_plan_read_cta_trace(rexi_plan* p, long long* out, int cap, int* grid) {
+    if (!p || (cap > 0 && !out)) return REXI_EINVAL;
+    if (grid) *grid = p->last_grid;
+    if (p->cta_trace_phases <= 0 || !p->d_cta_trace || p->last_grid <= 0) return 0;
+    DeviceGuard guard(p->device);
+    unsigned long long count = 0;
+    if (cudaStreamSynchronize(p->last_stream) != cudaSuccess ||
+        cudaMemcpy(&count, p->d_cta_trace, sizeof(count), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return REXI_ECUDA;
+    const int g = std::min(p->last_grid, p->cta_trace_stride);
+    const long long rows = std::min<long long>((long long)count, std::min<long long>(p->cta_trace_phases, cap / g));
+    for (long long r = 0; r < rows; ++r)
+        if (cudaMemcpy(out + r * g, p->d_cta_trace + 1 + r * p->cta_trace_stride, sizeof(long long) * g,
+                       cudaMemcpyDeviceToHost) != cudaSuccess)
+            return REXI_ECUDA;
+    return (int)count;
 }
 
 int rexi_plan_read_trace(rexi_plan* p, long long* out, int cap) {

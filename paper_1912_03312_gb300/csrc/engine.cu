@@ -121,11 +121,20 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long timeout_ns
 }
 
 // Barrier that also timestamps the end of phase `code` (CTA 0 only).
+// With the CTA trace on, every CTA also records when all its threads arrived.
 __device__ __forceinline__ bool phase_sync(const EngineArgs& A, int code, int* tcount) {
-    const bool ok = grid_sync(A.bar, A.err, A.timeout_ns);
-    if (A.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (A.cta_trace != nullptr) {
+        __syncthreads();
         const int c = *tcount;
-        if (c < A.trace_cap) {
+        if (threadIdx.x == 0 && c < A.cta_trace_phases && (int)blockIdx.x < A.cta_trace_stride) {
+            A.cta_trace[1 + (size_t)c * A.cta_trace_stride + blockIdx.x] = global_ns();
+            if (blockIdx.x == 0) A.cta_trace[0] = (unsigned long long)(c + 1);
+        }
+    }
+    const bool ok = grid_sync(A.bar, A.err, A.timeout_ns);
+    if (threadIdx.x == 0) {
+        const int c = *tcount;
+        if (A.trace != nullptr && blockIdx.x == 0 && c < A.trace_cap) {
             A.trace[1 + 2 * c] = (unsigned long long)code;
             A.trace[2 + 2 * c] = global_ns();
             A.trace[0] = (unsigned long long)(c + 1);
@@ -198,6 +207,9 @@ struct Smem {
     int ntasks;
     int kk;                        // Arnoldi steps of the current item (E2)
     const void* basis;             // basis the current item's E2 reads
+    double2 yhat[kMaxM];           // PS: sum of alpha_k y_k of the poles completed on the shared basis
+    int kyhat;                     //     its length (0: none)
+    const void* gbasis;            //     the shared basis
 };
 
 template <typename V> __device__ __forceinline__ V coefg_at(const Smem& sm, int q);
@@ -463,6 +475,18 @@ __device__ __forceinline__ double warp_norm_partials(const ItemDesc& it, const R
     return warp_sum(ss);
 }
 
+// First basis vector step j of the delayed CGS2 orthogonalises against.
+__device__ __forceinline__ int win_start(const EngineArgs& A, int j) {
+    return A.window > 0 ? max(0, j - A.window) : 0;
+}
+
+// Residual estimate |g_{k+1}| of a cycle with k columns as a bound on the
+// true residual: with a windowed basis the columns are orthonormal only
+// locally, and ||r|| <= sqrt(k + 1) |g_{k+1}| (unit columns).
+__device__ __forceinline__ double res_bound(const EngineArgs& A, double res, int k) {
+    return A.window > 0 ? res * sqrt((double)(k + 1)) : res;
+}
+
 __device__ __forceinline__ void load_scales(Smem& sm, const ItemState* S, int cnt) {
     if (threadIdx.x < cnt) sm.ssm[threadIdx.x] = ldd(&S->s[threadIdx.x]);
     __syncthreads();
@@ -471,6 +495,9 @@ __device__ __forceinline__ void load_scales(Smem& sm, const ItemState* S, int cn
 template <typename T, int VG>
 struct Phases {
     typedef typename C2<T>::t V;
+    // points per thread held at once in the update sweeps (FP64 accumulators
+    // of 8 points would not fit the register budget)
+    static constexpr int kChunk = sizeof(T) == 8 ? kPPT / 2 : kPPT;
 
     // Every thread owns points p0 + r * kBlock + threadIdx.x, r < kPPT, of a
     // tile; per basis vector all of its kPPT loads are independent.  A CTA
@@ -835,7 +862,9 @@ struct Phases {
         const V shift = item_shift<V>(it);
         const T* diag = prob_diag<T>(pr);
         const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
-        const DotPlan d = dot_plan(j + 1, it_tile);
+        const int j0 = win_start(A, j);                     // dots with q_j0 .. q_{j-1} and v_j
+        const V* U0 = U + (size_t)j0 * n;
+        const DotPlan d = dot_plan(j + 1 - j0, it_tile);
         T ar[4] = {T(0), T(0), T(0), T(0)}, ai[4] = {T(0), T(0), T(0), T(0)};
         T br[4] = {T(0), T(0), T(0), T(0)}, bi[4] = {T(0), T(0), T(0), T(0)};
         for (int tile = tb; tile < te; ++tile) {
@@ -858,11 +887,11 @@ struct Phases {
                 wsw[r * kBlock + threadIdx.x] = w;
             }
             __syncthreads();
-            dot_tile2(U, n, wsv, wsw, p0, pend, d, matvec, ar, ai, br, bi);
+            dot_tile2(U0, n, wsv, wsw, p0, pend, d, matvec, ar, ai, br, bi);
             __syncthreads();
         }
-        dot_finish(sm, it, it.part1, tb, j + 1, d, ar, ai);
-        if (matvec) dot_finish(sm, it, it.part2, tb, j + 1, d, br, bi);
+        dot_finish(sm, it, it.part1, tb, j + 1 - j0, d, ar, ai);
+        if (matvec) dot_finish(sm, it, it.part2, tb, j + 1 - j0, d, br, bi);
     }
 
     // Y prologue: every CTA of the item reduces X's partials and forms the
@@ -871,10 +900,17 @@ struct Phases {
         const EngineArgs& A = sm.A;
         const ItemDesc& it = A.item[item];
         ItemState* S = it.st;
-        if (threadIdx.x <= j) sm.ssm[threadIdx.x] = threadIdx.x < j ? 1.0 : ldd(&S->vt[j & 1]);
+        const int j0 = win_start(A, j);                                    // rows j0 .. j
+        if (threadIdx.x <= j) {
+            sm.ssm[threadIdx.x] = threadIdx.x < j ? 1.0 : ldd(&S->vt[j & 1]);
+            if (threadIdx.x < j0) {
+                sm.h1[threadIdx.x] = make_double2(0.0, 0.0);
+                sm.h2[threadIdx.x] = make_double2(0.0, 0.0);
+            }
+        }
         __syncthreads();                                                   // q_i normalised; t_j
-        reduce_partials(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);        // a_i, c
-        if (!last) reduce_partials(sm, it.part2, it, R, j + 1, sm.ssm, sm.h2);   // b_i, d
+        reduce_partials(sm, it.part1, it, R, j + 1 - j0, sm.ssm + j0, sm.h1 + j0);        // a_i, c
+        if (!last) reduce_partials(sm, it.part2, it, R, j + 1 - j0, sm.ssm + j0, sm.h2 + j0);   // b_i, d
         const int nH = j >= 2 ? (j - 1) * (j + 2) / 2 : 0;                 // columns 0..j-2
         for (int t = threadIdx.x; t < nH; t += kBlock) sm.Rsm[t] = ldp(&S->H[t]);
         if (threadIdx.x < j) sm.hfin[threadIdx.x] = ldp(((j - 1) & 1 ? S->hcol2 : S->hcol) + threadIdx.x);
@@ -882,7 +918,7 @@ struct Phases {
         if (threadIdx.x == 0) {
             double aa2 = 0.0;
             double2 ab = make_double2(0.0, 0.0);
-            for (int i = 0; i < j; ++i) {
+            for (int i = j0; i < j; ++i) {
                 const double2 a = sm.h1[i];
                 aa2 += a.x * a.x + a.y * a.y;
                 if (!last) ab = cadd(ab, cmul(cconj(a), sm.h2[i]));
@@ -903,13 +939,14 @@ struct Phases {
         if (!last && threadIdx.x <= j) {
             const int i = threadIdx.x;
             double2 Ha = make_double2(0.0, 0.0);                            // (H a)_i over columns l < j
-            for (int l = max(i - 1, 0); l < j; ++l) {
+            for (int l = max(max(i - 1, 0), j0); l < j; ++l) {
                 const double2 Hil = l == j - 1 ? sm.hfin[i] : sm.Rsm[l * (l + 3) / 2 + i];
                 Ha = cadd(Ha, cmul(Hil, sm.h1[l]));
             }
             const double inv = sm.yscal[2];
             double2 h;
-            if (i < j) h = cscale(csub(sm.h2[i], Ha), inv);
+            if (i < j0) h = make_double2(0.0, 0.0);                        // outside the window
+            else if (i < j) h = cscale(csub(sm.h2[i], Ha), inv);
             else h = cscale(csub(cscale(csub(sm.h2[j], sm.ygq), inv), Ha), inv);
             sm.hnew[i] = h;
             const double2 gam = cadd(cscale(Ha, inv), h);
@@ -926,7 +963,7 @@ struct Phases {
         if (!last && threadIdx.x == 0) {
             const int i = j;
             double2 Ha = make_double2(0.0, 0.0);
-            for (int l = max(i - 1, 0); l < j; ++l) {
+            for (int l = max(max(i - 1, 0), j0); l < j; ++l) {
                 const double2 Hil = l == j - 1 ? sm.hfin[i] : sm.Rsm[l * (l + 3) / 2 + i];
                 Ha = cadd(Ha, cmul(Hil, sm.h1[l]));
             }
@@ -945,39 +982,42 @@ struct Phases {
         V* wv = U + (size_t)(j + 1) * n;
         const T tq = (T)sm.yscal[1], tw = (T)sm.yscal[2];
         const V gq = cvt2<V>(sm.ygq);
+        const int j0 = win_start(sm.A, j);
         for (int tile = tb; tile < te; ++tile) {
             const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
-            V qa[kPPT], va[kPPT];
+            for (int r0 = 0; r0 < kPPT && p0 + r0 * kBlock < pend; r0 += kChunk) {
+                V qa[kChunk], va[kChunk];
 #pragma unroll
-            for (int r = 0; r < kPPT; ++r) {
-                const int p = p0 + r * kBlock + threadIdx.x;
-                const V u = p < pend ? ldp(uj + p) : mk2(T(0), T(0));
-                const V w = p < pend ? ldp(wv + p) : mk2(T(0), T(0));
-                qa[r] = mk2(tq * u.x, tq * u.y);
-                va[r] = mk2(tw * w.x, tw * w.y);
-            }
-#pragma unroll 2
-            for (int q = 0; q < j; ++q) {
-                const V* uq = U + (size_t)q * n;
-                const V ca = coef_at<V>(sm, q), cg = coefg_at<V>(sm, q);
-#pragma unroll
-                for (int r = 0; r < kPPT; ++r) {
-                    const int p = p0 + r * kBlock + threadIdx.x;
-                    const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
-                    qa[r].x -= ca.x * u.x - ca.y * u.y;
-                    qa[r].y -= ca.x * u.y + ca.y * u.x;
-                    va[r].x -= cg.x * u.x - cg.y * u.y;
-                    va[r].y -= cg.x * u.y + cg.y * u.x;
+                for (int r = 0; r < kChunk; ++r) {
+                    const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
+                    const V u = p < pend ? ldp(uj + p) : mk2(T(0), T(0));
+                    const V w = p < pend ? ldp(wv + p) : mk2(T(0), T(0));
+                    qa[r] = mk2(tq * u.x, tq * u.y);
+                    va[r] = mk2(tw * w.x, tw * w.y);
                 }
-            }
+#pragma unroll 2
+                for (int q = j0; q < j; ++q) {
+                    const V* uq = U + (size_t)q * n;
+                    const V ca = coef_at<V>(sm, q), cg = coefg_at<V>(sm, q);
 #pragma unroll
-            for (int r = 0; r < kPPT; ++r) {
-                const int p = p0 + r * kBlock + threadIdx.x;
-                if (p < pend) {
-                    va[r].x -= gq.x * qa[r].x - gq.y * qa[r].y;
-                    va[r].y -= gq.x * qa[r].y + gq.y * qa[r].x;
-                    uj[p] = qa[r];
-                    wv[p] = va[r];
+                    for (int r = 0; r < kChunk; ++r) {
+                        const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
+                        const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                        qa[r].x -= ca.x * u.x - ca.y * u.y;
+                        qa[r].y -= ca.x * u.y + ca.y * u.x;
+                        va[r].x -= cg.x * u.x - cg.y * u.y;
+                        va[r].y -= cg.x * u.y + cg.y * u.x;
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < kChunk; ++r) {
+                    const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
+                    if (p < pend) {
+                        va[r].x -= gq.x * qa[r].x - gq.y * qa[r].y;
+                        va[r].y -= gq.x * qa[r].y + gq.y * qa[r].x;
+                        uj[p] = qa[r];
+                        wv[p] = va[r];
+                    }
                 }
             }
         }
@@ -985,6 +1025,7 @@ struct Phases {
 
     // E2 prologue: y = R^{-1} g (back substitution, FP64), coefficients y_i s_i.
     static __device__ void e2_pro(Smem& sm, int item) {
+        __syncthreads();                       // the previous run's sweep has read kk and basis
         const ItemDesc& it = sm.A.item[item];
         const int it_n = it.n, it_tile = it.tile;
         const ItemState* S = it.st;
@@ -1033,25 +1074,27 @@ struct Phases {
         const int k = sm.kk;
         for (int tile = tb; tile < te; ++tile) {
             const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
-            V d[kPPT];
+            for (int r0 = 0; r0 < kPPT && p0 + r0 * kBlock < pend; r0 += kChunk) {
+                V d[kChunk];
 #pragma unroll
-            for (int r = 0; r < kPPT; ++r) d[r] = mk2(T(0), T(0));
+                for (int r = 0; r < kChunk; ++r) d[r] = mk2(T(0), T(0));
 #pragma unroll 2
-            for (int q = 0; q < k; ++q) {
-                const V* uq = U + (size_t)q * n;
-                const V c = coef_at<V>(sm, q);
+                for (int q = 0; q < k; ++q) {
+                    const V* uq = U + (size_t)q * n;
+                    const V c = coef_at<V>(sm, q);
 #pragma unroll
-                for (int r = 0; r < kPPT; ++r) {
-                    const int p = p0 + r * kBlock + threadIdx.x;
-                    const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
-                    d[r].x += c.x * u.x - c.y * u.y;
-                    d[r].y += c.x * u.y + c.y * u.x;
+                    for (int r = 0; r < kChunk; ++r) {
+                        const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
+                        const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                        d[r].x += c.x * u.x - c.y * u.y;
+                        d[r].y += c.x * u.y + c.y * u.x;
+                    }
                 }
-            }
 #pragma unroll
-            for (int r = 0; r < kPPT; ++r) {
-                const int p = p0 + r * kBlock + threadIdx.x;
-                if (p < pend) x[p] = cadd(ldp(x + p), up2(d[r]));
+                for (int r = 0; r < kChunk; ++r) {
+                    const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
+                    if (p < pend) x[p] = cadd(ldp(x + p), up2(d[r]));
+                }
             }
         }
     }
@@ -1171,12 +1214,88 @@ __device__ void item_p4(const EngineArgs& A, int item, const Runs& R, int j) {
 }
 
 // Cache the solution pointers and weights of problem `prob` in shared memory.
+// With poles completed on the shared basis, yhat = sum_k alpha_k y_k over
+// them (fixed order) and their x is not read.
 __device__ void load_problem_items(Smem& sm, int prob) {
-    const ProblemDesc& pr = sm.A.prob[prob];
-    const int nx = sm.A.mode == MODE_BACKWARD ? 2 * pr.K : pr.K;
-    for (int k = threadIdx.x; k < nx; k += kBlock) sm.xptr[k] = sm.A.item[pr.item0 + k].x;
+    const EngineArgs& A = sm.A;
+    const ProblemDesc& pr = A.prob[prob];
+    __syncthreads();                           // the previous problem's tiles are done with these
+    const int nx = A.mode == MODE_BACKWARD ? 2 * pr.K : pr.K;
+    for (int k = threadIdx.x; k < nx; k += kBlock) {
+        const ItemDesc& it = A.item[pr.item0 + k];
+        sm.xptr[k] = (A.mode == MODE_STEP && ldi(&it.st->status) == ST_DIRECT) ? nullptr : it.x;
+    }
     for (int k = threadIdx.x; k < pr.K; k += kBlock) sm.alpha[k] = __ldg(pr.alpha + k);
+    if (threadIdx.x == 0) sm.kyhat = 0;
     __syncthreads();
+    const int grp = A.mode == MODE_STEP ? A.item[pr.item0].group : -1;
+    if (grp >= 0) {
+        const ItemDesc& gd = A.item[grp];
+        if (threadIdx.x < kMaxM) {
+            const int i = threadIdx.x;
+            double2 acc = make_double2(0.0, 0.0);
+            int kmax = 0;
+            for (int k = 0; k < pr.K; ++k) {
+                if (sm.xptr[k] != nullptr) continue;
+                const ItemState* M = A.item[pr.item0 + k].st;
+                const int kk = ldi(&M->k);
+                kmax = max(kmax, kk);
+                if (i < kk) acc = cadd(acc, cmul(sm.alpha[k], ldp(&M->y[i])));
+            }
+            const double si = A.ortho ? 1.0 : ldd(&gd.st->s[i]);
+            sm.yhat[i] = cscale(acc, si);
+            if (i == 0) {
+                sm.kyhat = kmax;
+                sm.gbasis = gd.basis;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// A pole whose residual estimate reaches the final tolerance on its group's
+// shared basis during a step launch needs no x of its own: the pole sum takes
+// alpha_k V y_k through the basis (sum_k alpha_k V y_k = V sum_k alpha_k y_k).
+// Returns the status the member ends its shared cycle with.
+__device__ __forceinline__ int member_end_status(const EngineArgs& A, const ItemDesc& md, ItemState* M,
+                                                 double res, int total) {
+    const double bnorm = ldd(&M->bnorm);
+    // only an FP64 basis: the estimate of a c64 recurrence is not a residual bound
+    if (A.mode != MODE_STEP || A.inner_tol > 0.0 || !(res <= A.tol * bnorm)) return ST_CYCLE_END;
+    ItemStats* T = md.stats;
+    T->iters += total;
+    T->iters_sq += ldi(&M->sum_k2);
+    T->cycles += ldi(&M->cycles);
+    T->max_sub_iters = max(T->max_sub_iters, total);
+    T->resid = fmax(T->resid, bnorm > 0.0 ? res / bnorm : 0.0);
+    return ST_DIRECT;
+}
+
+// y = R^{-1} g of a pole completed on the shared basis (one warp; lane i holds
+// row i, columns eliminated from the last).  Statuses stay as they are: every
+// CTA builds its lists from them within the phase.
+__device__ void member_direct_solve(const EngineArgs& A, int item) {
+    const int lane = threadIdx.x & 31;
+    ItemState* M = A.item[item].st;
+    if (ldi(&M->ydone)) return;
+    const int k = ldi(&M->k);
+    double2 acc = lane < k ? ldp(&M->g[lane]) : make_double2(0.0, 0.0);
+    double2 y = make_double2(0.0, 0.0);
+    double2 rc = (k > 0 && lane < k) ? ldp(&M->R[(k - 1) * k / 2 + lane]) : make_double2(0.0, 0.0);
+    for (int l = k - 1; l >= 0; --l) {
+        const double2 rn = (l > 0 && lane < l) ? ldp(&M->R[(l - 1) * l / 2 + lane]) : make_double2(0.0, 0.0);
+        double2 yl = make_double2(0.0, 0.0);
+        if (lane == l) {
+            const double den = rc.x * rc.x + rc.y * rc.y;
+            if (den > 0.0) yl = cscale(cmul(acc, cconj(rc)), 1.0 / den);
+            y = yl;
+        }
+        yl = shfl2(yl, l);
+        if (lane < l) acc = csub(acc, cmul(rc, yl));
+        rc = rn;
+    }
+    if (lane < k) M->y[lane] = y;
+    if (lane == 0) M->ydone = 1;
 }
 
 // P4 of a group (one warp, lane = member): every member's Hessenberg column is
@@ -1233,9 +1352,13 @@ __device__ void group_p4(const EngineArgs& A, int gitem, const Runs& R, int j) {
         const double res = sqrt(gj1.x * gj1.x + gj1.y * gj1.y);
         const bool end = !(res > ldd(&S->cycle_tol_abs)) || j + 1 >= A.m || total >= A.max_iters ||
                          !(hn > 0.0) || !(rr > 0.0);
-        if (end) S->sum_k2 = ldi(&S->sum_k2) + (j + 1) * (j + 1);
+        int stn = ST_SHARED;
+        if (end) {
+            S->sum_k2 = ldi(&S->sum_k2) + (j + 1) * (j + 1);
+            stn = member_end_status(A, md, S, res, total);
+        }
         __threadfence();
-        S->status = end ? ST_CYCLE_END : ST_SHARED;
+        S->status = stn;
         active = active || !end;
     }
     const bool any = __any_sync(0xffffffffu, active);
@@ -1250,10 +1373,26 @@ __device__ void group_p4(const EngineArgs& A, int gitem, const Runs& R, int j) {
 // Delayed CGS2, step j: the CTA owning tile 0 of the item stores the completed
 // column j-1 and the pending column j, and applies the Givens rotation of
 // column j-1 (one warp; for a group, lane = member with its shifted column).
-__device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool last) {
+__device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool last, void* stage,
+                          size_t stage_bytes) {
     const ItemDesc& it = A.item[item];
     ItemState* S = it.st;
     const double nu = sm.yscal[0];
+    // a group's member rotations (column-major, i * nm + member) are copied to
+    // shared memory by the whole CTA when they fit, so the serial loop below
+    // does not wait on global loads
+    const int nmg = it.is_group ? it.nmembers : 0;
+    const int nrot = j >= 2 ? nmg * (j - 1) : 0;
+    const bool staged = nrot > 0 && (size_t)nrot * (sizeof(double) + sizeof(double2)) <= stage_bytes;
+    double2* st_sn = (double2*)stage;
+    double* st_cs = (double*)(st_sn + nrot);
+    if (staged) {
+        for (int t = threadIdx.x; t < nrot; t += kBlock) {
+            st_sn[t] = ldp(it.gsn + t);
+            st_cs[t] = ldd(it.gcs + t);
+        }
+        __syncthreads();
+    }
     if (j >= 1 && threadIdx.x <= j) S->H[(j - 1) * (j + 2) / 2 + threadIdx.x] = sm.hfin[threadIdx.x];
     if (!last && threadIdx.x <= j) ((j & 1) ? S->hcol2 : S->hcol)[threadIdx.x] = sm.hnew[threadIdx.x];
     if (threadIdx.x == 0) S->vt[(j + 1) & 1] = 1.0;                 // v_{j+1} is stored raw
@@ -1305,7 +1444,7 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
         S->k = j;
         const int total = ldi(&S->total_iters) + 1;
         S->total_iters = total;
-        const double res = sqrt(gj1.x * gj1.x + gj1.y * gj1.y);
+        const double res = res_bound(A, sqrt(gj1.x * gj1.x + gj1.y * gj1.y), j);
         const bool end = !(res > ldd(&S->cycle_tol_abs)) || last || total >= A.max_iters || !(hn > 0.0) ||
                          !(rr > 0.0);
         if (end) S->sum_k2 = ldi(&S->sum_k2) + j * j;
@@ -1332,8 +1471,9 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
         for (int i = 0; i < jj; ++i) {
             double2 b = sm.hfin[i + 1];
             if (i + 1 == jj) b = csub(b, sh);
-            const double c = ldd(it.gcs + (size_t)i * nm + mi);
-            const double2 sn = ldp(it.gsn + (size_t)i * nm + mi);
+            const size_t ri = (size_t)i * nm + mi;
+            const double c = staged ? st_cs[ri] : ldd(it.gcs + ri);
+            const double2 sn = staged ? st_sn[ri] : ldp(it.gsn + ri);
             const double2 nh = cadd(cscale(carry, c), cmul(sn, b));
             carry = cadd(cscale(cmul(cconj(sn), carry), -1.0), cscale(b, c));
             M->R[col + i] = nh;
@@ -1362,12 +1502,16 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
         M->k = j;
         const int total = ldi(&M->total_iters) + 1;
         M->total_iters = total;
-        const double res = sqrt(gj1.x * gj1.x + gj1.y * gj1.y);
+        const double res = res_bound(A, sqrt(gj1.x * gj1.x + gj1.y * gj1.y), j);
         const bool end = !(res > ldd(&M->cycle_tol_abs)) || last || total >= A.max_iters || !(hn > 0.0) ||
                          !(rr > 0.0);
-        if (end) M->sum_k2 = ldi(&M->sum_k2) + j * j;
+        int stn = ST_SHARED;
+        if (end) {
+            M->sum_k2 = ldi(&M->sum_k2) + j * j;
+            stn = member_end_status(A, md, M, res, total);
+        }
         __threadfence();
-        M->status = end ? ST_CYCLE_END : ST_SHARED;
+        M->status = stn;
         active = active || !end;
     }
     const bool any = __any_sync(0xffffffffu, active);
@@ -1378,8 +1522,11 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
     }
 }
 
-// PS: psi' = alpha_0 b + sum_k alpha_k x_k for one tile of a problem.
+// PS: psi' = alpha_0 b + sum_k alpha_k x_k for one tile of a problem (poles
+// completed on the shared basis enter as sum_i yhat_i u_i).
+template <typename T>
 __device__ void task_pole_sum(const Smem& sm, int prob, int tile, int sub) {
+    typedef typename C2<T>::t V;
     const ProblemDesc& pr = sm.A.prob[prob];
     const double2* b = step_in(sm.io, pr, prob, sub);
     double2* out = step_out(sm.io, pr, prob, sub);
@@ -1392,11 +1539,22 @@ __device__ void task_pole_sum(const Smem& sm, int prob, int tile, int sub) {
     }
     for (int k = 0; k < pr.K; ++k) {
         const double2* xk = sm.xptr[k];
+        if (xk == nullptr) continue;
         const double2 al = sm.alpha[k];
 #pragma unroll
         for (int r = 0; r < kPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
             if (p < pend) acc[r] = cadd(acc[r], cmul(al, ldp(xk + p)));
+        }
+    }
+    const V* Ug = (const V*)sm.gbasis;
+    for (int i = 0; i < sm.kyhat; ++i) {
+        const V* ui = Ug + (size_t)i * pr.n;
+        const double2 c = sm.yhat[i];
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            if (p < pend) acc[r] = cadd(acc[r], cmul(c, up2(ldp(ui + p))));
         }
     }
 #pragma unroll
@@ -1451,8 +1609,12 @@ __device__ __forceinline__ void my_range(int ntasks, int* s, int* e) {
     *e = (int)(((long long)(blockIdx.x + 1) * ntasks) / gridDim.x);
 }
 
+// resident CTAs per SM the register budget is sized for: three for the FP32
+// basis; two for FP64 (its staging tiles limit residency to two anyway)
+template <typename T> constexpr int kMinCtas = sizeof(T) == 8 ? 2 : 3;
+
 template <typename T, int VG>
-__global__ void __launch_bounds__(kBlock, 3) engine_kernel(const __grid_constant__ EngineArgs gA,
+__global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __grid_constant__ EngineArgs gA,
                                                            const __grid_constant__ IOArgs gio) {
     typedef Phases<T, VG> P;
     extern __shared__ int dyn[];
@@ -1473,18 +1635,22 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(const __grid_constant
     const int warp = threadIdx.x >> 5;
     const int gwarp = blockIdx.x * kWarps + warp;
     const int nwarps = gridDim.x * kWarps;
+    // barrier counter; record 0 of both traces is the launch start
     __shared__ int tcount;
     if (threadIdx.x == 0) {
-        tcount = 0;
-        if (A.trace != nullptr && blockIdx.x == 0) A.trace[0] = 0ull;
+        tcount = 1;
+        const unsigned long long t0 = global_ns();
+        if (A.trace != nullptr && blockIdx.x == 0 && A.trace_cap > 0) {
+            A.trace[1] = 99ull;
+            A.trace[2] = t0;
+            A.trace[0] = 1ull;
+        }
+        if (A.cta_trace != nullptr && A.cta_trace_phases > 0 && (int)blockIdx.x < A.cta_trace_stride) {
+            A.cta_trace[1 + blockIdx.x] = t0;
+            if (blockIdx.x == 0) A.cta_trace[0] = 1ull;
+        }
     }
     __syncthreads();
-    if (A.trace != nullptr && blockIdx.x == 0 && threadIdx.x == 0 && A.trace_cap > 0) {
-        A.trace[1] = 99ull;                   // launch start marker
-        A.trace[2] = global_ns();
-        A.trace[0] = 1ull;
-        tcount = 1;
-    }
 
     for (int sub = 0; sub < A.max_sub; ++sub) {
         // substep start: every item of a live problem needs a first residual
@@ -1496,6 +1662,7 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(const __grid_constant
             S->sum_k2 = 0;
             S->shared = 0;
             S->k = 0;
+            S->ydone = 0;
             S->status = sub < A.prob[it.problem].nsub ? ST_NEED_RES : ST_IDLE;
         }
         if (!phase_sync(A, TR_INIT, &tcount)) return;
@@ -1526,18 +1693,18 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(const __grid_constant
                     P::dx(sm, ws, ws + kTile, list[l], t - prefix[l], te, j, !last);
                     t = prefix[l] + te;
                 }
-                if (!phase_sync(A, TR_P1, &tcount)) return;
+                if (!phase_sync(A, TR_DX, &tcount)) return;
                 for (int t = s; t < e;) {
                     const int l = find_slot(prefix, sm.nl, t);
                     const int te = min(prefix[l + 1], e) - prefix[l];
                     const int tb = t - prefix[l];
                     P::dy_pro(sm, list[l], item_runs(prefix, l, sm.ntasks), j, last);
-                    if (tb == 0) dy_commit(A, sm, list[l], j, last);
+                    if (tb == 0) dy_commit(A, sm, list[l], j, last, ws, 2 * kTile * sizeof(*ws));
                     __syncthreads();
                     if (!last) P::dy(sm, list[l], tb, te, j);
                     t = prefix[l] + te;
                 }
-                if (!phase_sync(A, TR_P3, &tcount)) return;
+                if (!phase_sync(A, TR_DY, &tcount)) return;
             }
             for (int j = 0; !A.ortho && j < A.m; ++j) {             // CGS2
                 build_list(sm, list, prefix, 1u << ST_ARNOLDI);
@@ -1573,8 +1740,13 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(const __grid_constant
                 if (!phase_sync(A, TR_P4, &tcount)) return;
             }
 
+            // poles completed on the shared basis: their y (one warp each)
+            build_list(sm, list, prefix, 1u << ST_DIRECT);
+            const bool direct = sm.nl > 0;
+            for (int l = gwarp; l < sm.nl; l += nwarps) member_direct_solve(A, list[l]);
+            __syncthreads();
             build_list(sm, list, prefix, 1u << ST_CYCLE_END);
-            if (sm.nl > 0) {
+            if (sm.nl > 0 || direct) {
                 my_range(sm.ntasks, &s, &e);
                 for (int t = s; t < e;) {
                     const int l = find_slot(prefix, sm.nl, t);
@@ -1595,7 +1767,7 @@ __global__ void __launch_bounds__(kBlock, 3) engine_kernel(const __grid_constant
             for (int t = s; t < e; ++t) {
                 const int l = find_slot(prefix, sm.nl, t);
                 if (list[l] != cur) { cur = list[l]; load_problem_items(sm, cur); }
-                if (A.mode == MODE_STEP) task_pole_sum(sm, cur, t - prefix[l], sub);
+                if (A.mode == MODE_STEP) task_pole_sum<T>(sm, cur, t - prefix[l], sub);
                 else task_adjoint(sm, cur, t - prefix[l], sub);
             }
             if (!phase_sync(A, TR_SUM, &tcount)) return;

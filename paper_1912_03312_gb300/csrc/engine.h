@@ -23,6 +23,8 @@ enum : int {
     ST_FAILED = 4,
     ST_IDLE = 5,       // not part of the current substep
     ST_SHARED = 6,     // pole in its first cycle on its group's shared Krylov basis
+    ST_DIRECT = 7,     // converged on the shared basis in a step launch: its V y joins the
+                       // pole sum through the group's basis (y computed once, see ydone)
 };
 
 // kernel modes
@@ -89,6 +91,7 @@ struct ItemDesc {
 struct ItemState {
     int status, k, total_iters, cycles;
     int sub_iters, sub_cycles, sum_k2, shared;
+    int ydone, pad_y;                      // ST_DIRECT: y computed
     double bnorm, beta, cycle_tol_abs, relres;
     double s[kMaxM + 1];
     double cs[kMaxM];
@@ -99,6 +102,7 @@ struct ItemState {
     double vt[2];                          // delayed CGS2: scale of v_j, by parity of j
     double2 R[kMaxM * (kMaxM + 1) / 2];    // packed upper triangle, column j at j(j+1)/2
     double2 H[kMaxM * (kMaxM + 3) / 2];    // unrotated Hessenberg, column l (l+2 entries) at l(l+3)/2
+    double2 y[kMaxM];                      // ST_DIRECT poles: least-squares solution on the shared basis
 };
 
 // Per-call statistics of one item (zeroed before every launch).
@@ -126,12 +130,15 @@ struct EngineArgs {
     int* err;            // sticky error word
     unsigned long long* trace;   // optional: [1 + 2*cap] (count, then (phase, ns) pairs)
     int trace_cap;
-    int pad2;
+    unsigned long long* cta_trace;   // optional: [1 + phases*stride] arrival ns of every CTA at every barrier
+    int cta_trace_phases;
+    int cta_trace_stride;
+    int window;          // delayed CGS2: 0 = whole basis; L = only the last L vectors (Hermitian operators)
 };
 
 // phase codes recorded in the trace at the barrier that ends each phase
 enum : int { TR_INIT = 0, TR_E3 = 1, TR_E4 = 2, TR_P1 = 3, TR_P2 = 4, TR_P3 = 5, TR_P4 = 6, TR_E2 = 7,
-             TR_SUM = 8 };
+             TR_SUM = 8, TR_DX = 9, TR_DY = 10 };
 
 // Launch the persistent kernel; T = float (mixed) or double (fp64).
 cudaError_t launch_engine(bool fp32_basis, const EngineArgs& args, const IOArgs& io, int grid,

@@ -72,6 +72,8 @@ extern "C" int rexi_substep_static(const rexi_grid* g, const double* V, double t
         return REXI_EINVAL;
     if ((opt.ortho != 0 && opt.ortho != 1) || (opt.ortho == 1 && opt.restart_m > REXI_MAX_RESTART - 1))
         return REXI_EINVAL;
+    if (opt.window < 0 || opt.window == 1 || opt.window > REXI_MAX_RESTART || (opt.window > 0 && opt.ortho != 1))
+        return REXI_EINVAL;
     long long n = 1;
     int dims[3] = {1, 1, 1};
     double a[3] = {0.0, 0.0, 0.0};
@@ -179,6 +181,7 @@ extern "C" int rexi_substep_static(const rexi_grid* g, const double* V, double t
     A.max_sub = 1;
     A.pv = pv;
     A.ortho = opt.ortho;
+    A.window = opt.window;
     A.tol = opt.tol;
     A.inner_tol = fp32 ? opt.inner_tol : 0.0;
     A.timeout_ns = 4000000000ull;

@@ -33,7 +33,7 @@ def _check_state(t, n, name):
 
 def options(precision="mixed", restart=30, max_iters=2000, tol=0.0, inner_tol=1e-5, R1=0.0,
             eps_target=1e-9, allow_substeps=True, stabilize_eps=0.0, want_backward=False, device=-1,
-            shared_first_cycle=True, ortho="dcgs2"):
+            shared_first_cycle=True, ortho="dcgs2", window=0):
     o = N.Options()
     N.load().rexi_options_default(C.byref(o))
     o.precision = N.REXI_MIXED if precision == "mixed" else N.REXI_FP64
@@ -51,6 +51,7 @@ def options(precision="mixed", restart=30, max_iters=2000, tol=0.0, inner_tol=1e
     if ortho not in ("dcgs2", "cgs2"):
         raise ValueError("ortho must be 'dcgs2' or 'cgs2'")
     o.ortho = 1 if ortho == "dcgs2" else 0
+    o.window = int(window)
     return o
 
 
@@ -226,7 +227,8 @@ class Plan:
         return N.load().rexi_plan_last_launches(self._h)
 
     PHASES = {0: "substep start", 1: "FP64 residual", 2: "cycle decision", 3: "matvec + dot sweep 1",
-              4: "CGS sweep 2", 5: "CGS update", 6: "Givens", 7: "x update", 8: "pole sum", 99: "launch"}
+              4: "CGS sweep 2", 5: "CGS update", 6: "Givens", 7: "x update", 8: "pole sum",
+              9: "DCGS2 matvec + dots", 10: "DCGS2 update + Givens", 99: "launch"}
 
     def set_trace(self, capacity=65536):
         N.check(N.load().rexi_plan_set_trace(self._h, int(capacity)), "rexi_plan_set_trace")
@@ -242,6 +244,46 @@ class Plan:
             return []
         t0 = rec[0][1]
         return [(c, (t - t0) * 1e-9) for c, t in rec]
+
+    def set_cta_trace(self, phases=4096):
+        """Record every CTA's arrival at the first `phases` barriers (0 disables)."""
+        N.check(N.load().rexi_plan_set_cta_trace(self._h, int(phases)), "rexi_plan_set_cta_trace")
+
+    def read_cta_trace(self):
+        """Arrival times (ns, int64 array [barriers, grid]) of the last launch."""
+        lib = N.load()
+        g = C.c_int(0)
+        cnt = N.check(lib.rexi_plan_read_cta_trace(self._h, None, 0, C.byref(g)), "rexi_plan_read_cta_trace")
+        if cnt <= 0 or g.value <= 0:
+            return np.zeros((0, max(g.value, 0)), dtype=np.int64)
+        buf = np.zeros(cnt * g.value, dtype=np.int64)
+        ptr = buf.ctypes.data_as(C.POINTER(C.c_longlong))
+        cnt2 = N.check(lib.rexi_plan_read_cta_trace(self._h, ptr, buf.size, C.byref(g)), "rexi_plan_read_cta_trace")
+        rows = min(cnt, cnt2, buf.size // g.value)
+        return buf[:rows * g.value].reshape(rows, g.value)
+
+    def balance_summary(self):
+        """Per phase kind, from the phase and CTA traces of the last launch:
+        (count, mean phase seconds, mean seconds until the first CTA arrived,
+        mean seconds until the last CTA arrived, mean barrier release latency)."""
+        lib = N.load()
+        cap = 1 << 16
+        buf = (C.c_longlong * (2 * cap))()
+        cnt = min(N.check(lib.rexi_plan_read_trace(self._h, buf, cap), "rexi_plan_read_trace"), cap)
+        rec = [(int(buf[2 * i]), int(buf[2 * i + 1])) for i in range(cnt)]
+        arr = self.read_cta_trace()
+        out = {}
+        for r in range(1, min(len(rec), arr.shape[0])):
+            start, (code, release) = rec[r - 1][1], rec[r]
+            a = arr[r]
+            name = self.PHASES.get(code, str(code))
+            v = out.setdefault(name, [0, 0.0, 0.0, 0.0, 0.0])
+            v[0] += 1
+            v[1] += (release - start) * 1e-9
+            v[2] += (a.min() - start) * 1e-9
+            v[3] += (a.max() - start) * 1e-9
+            v[4] += (release - a.max()) * 1e-9
+        return {k: (v[0], v[1] / v[0], v[2] / v[0], v[3] / v[0], v[4] / v[0]) for k, v in out.items()}
 
     def trace_summary(self):
         """Total seconds and count per phase of the last launch."""

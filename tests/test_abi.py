@@ -113,6 +113,12 @@ def test_argument_validation_before_device(lib):
     o.ortho = 2
     o.restart_m = 30
     assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    o.ortho = 1
+    o.window = 1                              # a window needs at least the two previous vectors
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    o.window = 3
+    o.ortho = 0                               # windows are a delayed-CGS2 option
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
     assert h.value is None
 
 

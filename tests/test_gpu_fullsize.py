@@ -1,0 +1,171 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+times (one persistent launch per step, default options of the plan).
+
+* 2D 512^2, K=32, dt=0.5 (the benchmark workload): one whole step against the
+  oracle's step, to the relative L2 tolerance of 1e-6;
+* 3D 128^3 with the softened Coulomb potential: K=64 is refused by the plan
+  (the FCF construction needs more than double-double precision there), so
+  K=32 runs: per-pole solutions of sampled poles against the oracle's solves,
+  a plane wave through the whole step against the scalar rational, and the
+  norm bound of the approximation;
+* 64 batched 2D problems with sides from {128, 192, 256, 384}: one batched
+  launch against the single-problem launches, the smallest ones against the
+  oracle;
+* the learnable-potential 256^2 problem: loss and dL/dV of a 2-step evolution
+  towards a fixed packet against the oracle's adjoint recursion, and the
+  adjoint dot-product identity over the 10 steps of the workload.
+"""
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import step as ostep
+
+from _common import OraclePlan, library_plan, relerr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_03312_gb300 import build
+    build.build()
+
+
+def _plan(cfg, g, V, K, **kw):
+    return library_plan(g, V, cfg["dt"], K, 0.0, **kw)
+
+
+def test_2d_wells_512_step_matches_oracle():
+    cfg = wl.config_2d_wells()
+    g = cfg["grid"]
+    lp = _plan(cfg, g, cfg["V"], cfg["K"])
+    info = lp.info()
+    assert info["R1"] == 68.0 and info["n_sub"] == 2
+    out, st = lp.step(to_dev(cfg["psi0"]), stats=True)
+    assert st["status"] == 0
+    orc = OraclePlan(g, cfg["V"], cfg["dt"], cfg["K"], info["R1"])
+    assert orc.n_sub == info["n_sub"]
+    ref, _ = ostep.step(cfg["V"], orc.h, cfg["psi0"], orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0,
+                        tol=1e-14)
+    assert relerr(out.cpu().numpy(), ref) < 1e-6
+
+
+def test_3d_coulomb_K64_is_refused():
+    from paper_1912_03312_gb300 import _native as N
+    cfg = wl.config_3d_coulomb()
+    g = cfg["grid"]
+    with pytest.raises(N.RexiError) as e:
+        _plan(cfg, g, cfg["V"], 64)
+    assert e.value.code == N.REXI_EPLAN
+
+
+def test_3d_coulomb_128_sampled_poles_and_plane_wave():
+    cfg = wl.config_3d_coulomb()
+    g = cfg["grid"]
+    K = 32
+    lp = _plan(cfg, g, cfg["V"], K)
+    info = lp.info()
+    orc = OraclePlan(g, cfg["V"], cfg["dt"], K, info["R1"])
+    assert orc.n_sub == info["n_sub"] == 1
+    psi = cfg["psi0"]
+    x, st = lp.solve_poles(to_dev(psi), stats=True)
+    assert st["status"] == 0
+    z, alpha, _, _ = lp.poles()
+    # sampled poles: the two largest weights and the two nearest the real axis
+    picks = sorted(set(np.argsort(-np.abs(alpha))[:2]) | set(np.argsort(np.abs(z.imag))[:2]))
+    for k in picks:
+        kk = int(np.argmin(np.abs(orc.z - z[k])))
+        xo, oi = ostep.solve_pole(cfg["V"], orc.h, psi, orc.tau, orc.z[kk], tol=1e-14)
+        assert oi["converged"]
+        assert relerr(x[k].cpu().numpy(), xo) < 1e-6, k
+    del x
+    # whole step: the approximation is within its error of the unitary
+    # propagator, so the norm changes by at most ||e|| + A delta
+    out, st = lp.step(to_dev(psi), stats=True)
+    assert st["status"] == 0
+    nrm0 = np.linalg.norm(psi)
+    nrm1 = float(torch.linalg.vector_norm(out))
+    assert abs(nrm1 - nrm0) / nrm0 < 2e-9 + 2.0 * info["amplification"] * info["tol"]
+    # plane wave on a constant potential: the step is the scalar rational
+    V0 = -0.3
+    lw = _plan(cfg, g, np.full(g["n"][::-1], V0), K)
+    X = wl.coords(g)
+    L = 30.0
+    m = (2, -1, 3)
+    ph = sum(2 * np.pi * m[d] * (X[d] + 15.0) / L for d in range(3))
+    wave = np.exp(1j * ph)
+    ow, st = lw.step(to_dev(wave), stats=True)
+    assert st["status"] == 0
+    h = L / 128
+    lam = V0 + 0.5 * sum(2 - 2 * np.cos(2 * np.pi * m[d] / 128) for d in range(3)) / h ** 2
+    zz, aa, a0, ns = lw.poles()
+    r = a0 + np.sum(aa / (lw.info()["tau"] * lam - zz))
+    wi = lw.info()
+    assert relerr(ow.cpu().numpy(), wave * r ** ns) < max(1e-9, 2.0 * wi["amplification"] * wi["tol"] * ns)
+    assert abs(r ** ns - np.exp(-1j * cfg["dt"] * lam)) < 1e-8
+
+
+def test_batched_64_problems():
+    cfg = wl.config_batched()
+    from paper_1912_03312_gb300 import step_batched
+    probs = cfg["problems"]
+    plans = [_plan(cfg, p["grid"], p["V"], cfg["K"]) for p in probs]
+    psis = [to_dev(p["psi0"]) for p in probs]
+    singles = [pl.step(ps).cpu().numpy() for pl, ps in zip(plans, psis)]
+    outs, sts = step_batched(plans, psis, stats=True)
+    assert all(s["status"] == 0 for s in sts)
+    # the batched grid splits tiles into runs differently, so reductions are
+    # summed in another order: both are solves to the plan's tolerance
+    for o, s1, pl in zip(outs, singles, plans):
+        i = pl.info()
+        assert relerr(o.cpu().numpy(), s1) < max(1e-6, 2.0 * i["amplification"] * i["tol"] * i["n_sub"])
+    again = step_batched(plans, psis)                 # a fixed launch is reproducible bit for bit
+    assert all(np.array_equal(a.cpu().numpy(), o.cpu().numpy()) for a, o in zip(again, outs))
+    sizes = [int(np.prod(p["grid"]["n"])) for p in probs]
+    for i in sorted(range(len(probs)), key=lambda i: sizes[i])[:2]:
+        p = probs[i]
+        orc = OraclePlan(p["grid"], p["V"], cfg["dt"], cfg["K"], plans[i].info()["R1"])
+        ref, _ = ostep.step(p["V"], orc.h, p["psi0"], orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0,
+                            tol=1e-14)
+        assert relerr(outs[i].cpu().numpy(), ref) < 1e-6
+
+
+def test_learnable_256_gradient_and_adjoint_identity():
+    cfg = wl.config_learnable()
+    g = cfg["grid"]
+    from paper_1912_03312_gb300 import RexiEvolve
+    lp = _plan(cfg, g, cfg["V"], cfg["K"])
+    info = lp.info()
+    # target: a displaced, boosted packet (seeded input, no solver involved)
+    target = wl.wave_packet(g, (-8.0, 1.0), 1.0, (3.0, 0.5))
+    Vt = torch.tensor(cfg["V"], dtype=torch.float64, device="cuda", requires_grad=True)
+    psiT = RexiEvolve.apply(Vt, to_dev(cfg["psi0"]), lp, 2)
+    loss = (psiT - to_dev(target)).abs().pow(2).sum()
+    loss.backward()
+    orc = OraclePlan(g, cfg["V"], cfg["dt"], cfg["K"], info["R1"])
+    L, dVo, _, _ = ostep.loss_and_grad(cfg["V"], orc.h, cfg["psi0"], target, orc.tau, orc.n_sub, 2, orc.z,
+                                       orc.alpha, orc.alpha0, tol=1e-14)
+    bound = max(1e-6, 2.0 * info["amplification"] * info["tol"] * 2 * info["n_sub"])
+    assert abs(float(loss) - L) / L < bound
+    assert relerr(Vt.grad.cpu().numpy(), dVo) < 10 * bound
+    # <phi, S^10 psi> = <(S^H)^10 phi, psi>
+    rng = np.random.default_rng(7)
+    phi = to_dev(rng.normal(size=g["n"][::-1]) + 1j * rng.normal(size=g["n"][::-1]))
+    cur = to_dev(cfg["psi0"])
+    states = []
+    for _ in range(10):
+        states.append(cur)
+        cur = lp.step(cur)
+    lhs = complex(torch.vdot(phi.flatten(), cur.flatten()))
+    G = phi
+    dV = torch.zeros(lp.n, dtype=torch.float64, device="cuda")
+    for s in reversed(states):
+        G = lp.step_backward(s, G, dV)
+    rhs = complex(torch.vdot(G.flatten(), to_dev(cfg["psi0"]).flatten()))
+    assert abs(lhs - rhs) / abs(lhs) < max(1e-9, 2.0 * info["amplification"] * info["tol"] * 10 * info["n_sub"])

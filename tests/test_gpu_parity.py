@@ -167,7 +167,9 @@ def test_batched_equals_single_and_oracle():
     for o, s1, (ref, A), st in zip(outs, singles, refs, sts):
         assert st["status"] == 0
         o = o.cpu().numpy()
-        assert np.array_equal(o, s1)                 # same arithmetic, independent of the grid split
+        # same method; the batched grid may split tiles into runs differently,
+        # which only reorders the reductions
+        assert relerr(o, s1) < max(1e-6, 2.0 * A * 1e-13)
         assert relerr(o, ref) < max(1e-6, 2.0 * A * 1e-13)
 
 
@@ -219,7 +221,7 @@ def test_shared_cycle_needs_fewer_basis_sweeps():
         lp.set_trace(1 << 14)
         o, st = lp.step(to_dev(psi), stats=True)
         outs.append(o.cpu().numpy())
-        its.append(sum(1 for c, _ in lp.read_trace() if c == 3))      # matvec phases
+        its.append(sum(1 for c, _ in lp.read_trace() if c in (3, 9)))   # matvec phases
     A = lp.info()["amplification"]
     assert relerr(outs[0], outs[1]) < max(1e-10, 4.0 * A * 1e-13)
     assert its[0] >= 1 and its[1] >= 1
@@ -239,3 +241,32 @@ def test_restart_lengths_match_oracle(precision, m):
     ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
     floor = 1e-10 if precision == "fp64" else 1e-6
     assert relerr(out.cpu().numpy(), ref) < max(floor, 2.0 * orc.A * tol)
+
+
+@pytest.mark.parametrize("shared", [True, False])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("window", [2, 4])
+@pytest.mark.parametrize("K,R1,n,dt", [(16, 24.0, (130, 101), 0.5), (32, 68.0, (96, 80), 0.5),
+                                       (8, 8.0, (9, 7, 5), 0.2), (16, 24.0, (300,), 1.0)])
+def test_windowed_basis_matches_oracle(precision, window, K, R1, n, dt, shared):
+    # H is real symmetric: orthogonalising against the last few vectors keeps
+    # the Krylov space; residual estimates carry the sqrt(k+1) factor
+    g, V, psi = wl.random_problem(41, n, box=8.0)
+    tol = 2e-14 if K == 8 else 1e-13
+    lp = library_plan(g, V, dt, K, R1, precision=precision, tol=tol, window=window, shared_first_cycle=shared,
+                      max_iters=20000)
+    orc = OraclePlan(g, V, dt, K, R1)
+    out, st = lp.step(to_dev(psi), stats=True)
+    assert st["status"] == 0
+    ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
+    floor = 1e-10 if precision == "fp64" else 1e-6
+    assert relerr(out.cpu().numpy(), ref) < max(floor, 2.0 * orc.A * tol)
+    if precision == "fp64":
+        x, st2 = lp.solve_poles(to_dev(psi), stats=True)      # per-pole solutions, all materialised
+        assert st2["status"] == 0
+        x = x.cpu().numpy()
+        z, _, _, _ = lp.poles()
+        for k in (0, K // 2, K - 1):
+            kk = int(np.argmin(np.abs(orc.z - z[k])))
+            xo, _ = ostep.solve_pole(V, orc.h, psi, orc.tau, orc.z[kk], tol=1e-14)
+            assert relerr(x[k], xo) < 1e-10
