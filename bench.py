@@ -3,8 +3,11 @@
 
 Workload: the 2D four-well problem -- 512 x 512 periodic grid on [-30, 30)^2,
 V = four Gaussian wells (seeded), Gaussian packet at (-10, 0) with k0 = (3, 0),
-K = 32 FCF poles (R1 = 68), user step dt = 0.5 (two rational substeps),
-complex FP32 Krylov with FP64 refinement.  One benchmark step = one user step
+K = 32 FCF poles (R1 = 68), user step dt = 0.5 (two rational substeps).  The
+timed path is the plan's FP64 path with the shared first cycle and a
+two-vector orthogonalisation window (--precision, --window select others);
+the FP64 path with full orthogonalisation is the accuracy reference and the
+mixed-precision path is timed beside it.  One benchmark step = one user step
 psi <- S(dt) psi through rexi_step; the state evolves from step to step.
 
     python bench.py [--steps 20] [--warmup 3] [--impl ours|reference] [--gpus N]
@@ -40,7 +43,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64")
+    ap.add_argument("--window", type=int, default=2,
+                    help="orthogonalisation window (0 = whole basis)")
+    ap.add_argument("--restart", type=int, default=0,
+                    help="GMRES restart length (0: 64 with a window, 30 without)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -148,13 +155,19 @@ def algorithmic_bytes(st, n, K, s_bytes, n_sub):
     return tot
 
 
-def engine_traffic(kernel_src_hash):
-    """ncu DRAM bytes per launch recorded under profiles/, if taken on this source."""
+def config_key(args):
+    return "%s|window=%d" % (args.precision, args.window)
+
+
+def engine_traffic(kernel_src_hash, key):
+    """ncu DRAM bytes per launch recorded under profiles/, if taken on this
+    source, workload and path."""
     p = os.path.join(ROOT, "profiles", "engine_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        if d.get("engine_cu_sha256") == kernel_src_hash and d.get("workload") == WORKLOAD:
+        if (d.get("engine_cu_sha256") == kernel_src_hash and d.get("workload") == WORKLOAD and
+                d.get("path") == key):
             return float(d["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -277,7 +290,9 @@ def ours(args):
     n = int(np.prod(g["n"]))
     K = cfg["K"]
     R1 = 68.0
-    plan = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], K, precision=args.precision, R1=R1)
+    restart = args.restart or (64 if args.window else 30)
+    plan = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], K, precision=args.precision, R1=R1,
+                window=args.window, restart=restart)
     info = plan.info()
     s_bytes = 8 if args.precision == "mixed" else 16
     stream = torch.cuda.current_stream()
@@ -303,12 +318,15 @@ def ours(args):
         dist.barrier()
     cur = psi0.clone()
     nxt = torch.empty_like(cur)
+    states = []                         # the inputs of the timed steps, for the end-to-end pass
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
         plan.step(cur, out=nxt)
         ev[i][1].record(stream)
         launches += plan.last_launches()
+        if not args.no_e2e and len(states) < 10:
+            states.append(cur.clone())
         cur, nxt = nxt, cur
     torch.cuda.synchronize()
     if dist:
@@ -318,58 +336,77 @@ def ours(args):
     total_ms = reduce_max(sum(step_ms), dist, dev)
     ms = total_ms / args.steps
 
-    # per-step statistics for the algorithmic byte count (a separate, untimed pass)
+    # per-step statistics (a separate, untimed pass over the same states): the
+    # kernel's own count of the bytes its passes move, and the count of the
+    # independent-pole method for context
     cur = psi0.clone()
-    alg = []
+    alg, survey = [], []
     for i in range(args.steps):
         cur, st = plan.step(cur, stats=True)
-        alg.append(algorithmic_bytes(st, n, K, s_bytes, info["n_sub"]))
+        alg.append(st["bytes"])
+        survey.append(algorithmic_bytes(st, n, K, s_bytes, info["n_sub"]))
         stats.append(st)
     bytes_per_step = statistics.mean(alg)
+    survey_bytes = statistics.mean(survey)
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_per_step / (ms * 1e-3) / 1e9
-    traffic = engine_traffic(src_hash())
+    traffic = engine_traffic(src_hash(), config_key(args))
 
-    # accuracy of the mixed path against the plain FP64 GPU path (one step)
+    # accuracy against the FP64 path with full orthogonalisation (one step), and
+    # the other paths of the plan timed the same way
     extra = {}
     if not args.no_fp64_path and rank == 0:
-        p64 = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], K, precision="fp64", R1=R1)
-        if not args.no_autotune:
-            autotune.autotune(p64, psi0)
-        ref = p64.step(psi0)
-        out = plan.step(psi0)
-        torch.cuda.synchronize()
-        extra["rel_err_vs_fp64_path"] = float((out - ref).norm() / ref.norm())
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c64 = psi0.clone()
-        p64.step(c64)
-        torch.cuda.synchronize()
-        nt = 3
-        tot64 = 0.0
-        for _ in range(nt):
-            flush.zero_()
-            a.record(stream)
-            c64 = p64.step(c64)
-            b.record(stream)
+        def timed(p, nt=3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c = psi0.clone()
+            c = p.step(c)
             torch.cuda.synchronize()
-            tot64 += a.elapsed_time(b)
-        extra["fp64_path"] = {"ms_per_step": tot64 / nt, "steps_per_s": 1000.0 * nt / tot64}
-        del p64
+            tot = 0.0
+            for _ in range(nt):
+                flush.zero_()
+                a.record(stream)
+                c = p.step(c)
+                b.record(stream)
+                torch.cuda.synchronize()
+                tot += a.elapsed_time(b)
+            return tot / nt
+        out = plan.step(psi0)
+        ref = None
+        paths = {}
+        for name, prec, win in (("fp64_full", "fp64", 0), ("mixed_full", "mixed", 0), ("mixed_window", "mixed", 2)):
+            if prec == args.precision and win == args.window:
+                continue
+            p2 = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], K, precision=prec, R1=R1, window=win,
+                      restart=64 if win else 30)
+            if not args.no_autotune:
+                autotune.autotune(p2, psi0)
+            o2 = p2.step(psi0)
+            if name == "fp64_full":
+                ref = o2
+            ms2 = timed(p2)
+            paths[name] = {"ms_per_step": ms2, "steps_per_s": 1000.0 / ms2}
+            if ref is not None and name != "fp64_full":
+                paths[name]["rel_err_vs_fp64_full"] = float((o2 - ref).norm() / ref.norm())
+            del p2
+        if ref is None:                 # the timed path is the reference itself
+            ref = out
+        extra["rel_err_vs_fp64_full"] = float((out - ref).norm() / ref.norm())
+        extra["other_paths"] = paths
 
-    # end to end through the C ABI with host buffers (copies inside the timed region)
+    # end to end through the C ABI with host buffers (copies inside the timed
+    # region), on the same states the device-timed steps started from
     e2e_s = None
     if not args.no_e2e:
-        host_in = torch.from_numpy(cfg["psi0"]).pin_memory()
-        host_out = torch.empty_like(host_in).pin_memory()
-        plan.step_host(host_in, host_out)
+        host_in = [s_.cpu().pin_memory() for s_ in states]
+        host_out = torch.empty_like(host_in[0]).pin_memory()
+        plan.step_host(host_in[0], host_out)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
-        ne = max(3, min(args.steps, 10))
-        for _ in range(ne):
-            plan.step_host(host_in, host_out)
-        e2e_s = reduce_max((time.perf_counter() - t0) / ne, dist, dev)
+        for h in host_in:
+            plan.step_host(h, host_out)
+        e2e_s = reduce_max((time.perf_counter() - t0) / len(host_in), dist, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -393,6 +430,7 @@ def ours(args):
             "config": {"workload": WORKLOAD if args.n == 512 else "2d_wells_%dx%d_K32_dt0.5" % (args.n, args.n),
                        "grid": list(g["n"]), "K": K, "dt": cfg["dt"], "n_sub": info["n_sub"],
                        "R1": info["R1"], "restart": info["restart_m"], "precision": args.precision,
+                       "window": args.window, "shared_first_cycle": True,
                        "tol": info["tol"], "amplification": info["amplification"],
                        "l2": "flushed (256 MiB write) before every timed step; Krylov basis 2 GB > L2",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
@@ -400,8 +438,13 @@ def ours(args):
             "grid_pts_poles_per_s": value * n * K * info["n_sub"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_kind": peak_kind, "kernel": "engine_kernel<float,32> (one launch per step)",
-                         "algorithmic_bytes_per_launch": bytes_per_step},
+                         "peak_kind": peak_kind,
+                         "kernel": "engine_kernel<%s,32> (one launch per step)" %
+                                   ("float" if args.precision == "mixed" else "double"),
+                         "algorithmic_bytes_per_launch": bytes_per_step,
+                         "bytes_source": "kernel count of the vectors its passes read and write",
+                         "independent_pole_bytes_per_launch": survey_bytes,
+                         "independent_pole_effective_gbs": survey_bytes / (ms * 1e-3) / 1e9},
             "cpu_baseline": cpu,
             "e2e": None if e2e_s is None else {"value": job_throughput(1, ws, e2e_s * 1e3), "unit": "REXI steps/s",
                                                "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n},

@@ -54,7 +54,9 @@ extern "C" {
                            the Hessenberg least squares and the pole sum          */
 
 #define REXI_MAX_POLES   256
-#define REXI_MAX_RESTART 32
+#define REXI_MAX_RESTART 64   /* windowed bases; with full orthogonalisation 31 (delayed
+                                 CGS2) or 32 (CGS2) */
+#define REXI_MAX_RESTART_FULL 31
 
 /* Periodic grid: N_d points on [lo_d, hi_d), h_d = (hi_d - lo_d) / N_d,
  * points x_j = lo_d + j h_d.  ndim in {1, 2, 3}; unused n[] entries ignored. */
@@ -67,7 +69,8 @@ typedef struct {
 
 typedef struct {
     int    precision;      /* REXI_FP64 or REXI_MIXED (default REXI_MIXED)                */
-    int    restart_m;      /* GMRES restart length, 1..REXI_MAX_RESTART (default 30)      */
+    int    restart_m;      /* GMRES restart length (default 30): 1..REXI_MAX_RESTART with a
+                              window, else 1..REXI_MAX_RESTART_FULL (32 with CGS2)        */
     int    max_iters;      /* Arnoldi iterations per pole solve before ENOCONV (default 2000) */
     double tol;            /* per-pole stop: ||b - A x|| <= tol ||b||; 0 = choose from the
                               pole-sum amplification (see rexi_plan_info.tol)              */
@@ -93,8 +96,8 @@ typedef struct {
     int    ortho;          /* Arnoldi orthogonalisation: 1 (default) delayed classical Gram-
                               Schmidt with reorthogonalisation, one global reduction per step
                               (the previous vector is reorthogonalised and normalised together
-                              with the projection of the new one; restart_m at most
-                              REXI_MAX_RESTART - 1); 0: CGS2, two reductions per step        */
+                              with the projection of the new one); 0: CGS2, two reductions
+                              per step                                                     */
     int    window;         /* with ortho = 1: 0 (default) orthogonalise every new vector against
                               the whole basis; L >= 2: only against the last L vectors (a
                               truncated, quasi-GMRES basis).  H is real symmetric, so tau H - z
@@ -131,6 +134,10 @@ typedef struct {
     int    cycles[REXI_MAX_POLES];
     int    iters_sq[REXI_MAX_POLES];  /* sum over restart cycles of (cycle length)^2       */
     double resid[REXI_MAX_POLES];
+    double bytes;                     /* algorithmic bytes of the launch: every vector a pass
+                                         reads or writes (basis, state, x, potential),
+                                         counted once per pass by the kernel as it works;
+                                         batched: the whole launch, in every entry        */
 } rexi_stats;
 
 typedef struct rexi_plan rexi_plan;   /* opaque, owned by the library */

@@ -22,7 +22,8 @@ REXI_WACCURACY = 1
 REXI_FP64 = 0
 REXI_MIXED = 1
 REXI_MAX_POLES = 256
-REXI_MAX_RESTART = 32
+REXI_MAX_RESTART = 64
+REXI_MAX_RESTART_FULL = 31
 
 
 class Grid(C.Structure):
@@ -50,7 +51,8 @@ class Stats(C.Structure):
     _fields_ = [("status", C.c_int), ("n_sub", C.c_int), ("max_iters_seen", C.c_int),
                 ("total_iters", C.c_int), ("total_cycles", C.c_int),
                 ("iters", C.c_int * REXI_MAX_POLES), ("cycles", C.c_int * REXI_MAX_POLES),
-                ("iters_sq", C.c_int * REXI_MAX_POLES), ("resid", C.c_double * REXI_MAX_POLES)]
+                ("iters_sq", C.c_int * REXI_MAX_POLES), ("resid", C.c_double * REXI_MAX_POLES),
+                ("bytes", C.c_double)]
 
 
 _P = C.c_void_p

@@ -3,7 +3,8 @@
 For one plan it times ``rexi_step`` under candidate settings of
 ``rexi_plan_set_tiles`` -- points per task for pole items and for shared-cycle
 group items, and resident CTAs per SM -- and keeps the fastest.  Results are
-cached in a JSON file keyed by device, grid, K, precision and restart length
+cached in a JSON file keyed by device, grid, K, precision, restart length and
+orthogonalisation
 (``$REXI_AUTOTUNE_CACHE``, default ``~/.cache/rexi_autotune.json``), so a
 problem shape is tuned once per machine.  Timing uses CUDA events on the
 launch stream; the state is not advanced (the same input is stepped).
@@ -21,7 +22,7 @@ from . import _native as N
 
 DEFAULT_CANDIDATES = {
     "pole_tile": (2048, 1024),
-    "group_tile": (512, 256, 1024),
+    "group_tile": (512, 256, 1024, 2048),
     "ctas_per_sm": (0, 2),
 }
 
@@ -34,9 +35,9 @@ def cache_path():
 def _key(plan):
     info = plan.info()
     dev = torch.cuda.get_device_name()
-    return "%s|grid=%s|K=%d|prec=%d|m=%d|shared=%d" % (
+    return "%s|grid=%s|K=%d|prec=%d|m=%d|shared=%d|ortho=%d|window=%d" % (
         dev, "x".join(str(v) for v in reversed(plan.shape)), plan.K, info["precision"], info["restart_m"],
-        plan.opts.shared_first_cycle)
+        plan.opts.shared_first_cycle, plan.opts.ortho, plan.opts.window)
 
 
 def _load():

@@ -74,6 +74,7 @@ struct rexi_plan {
     double2* d_hout = nullptr;
     unsigned* d_bar = nullptr;
     int* d_err = nullptr;
+    unsigned long long* d_bytes = nullptr;       // algorithmic bytes of the last launch
     int nit_cap = 0;                             // pole items with workspace (K or 2K)
     int ngroups = 0;                             // shared-cycle group items (0, 1 or 2)
     bool shared = true;
@@ -362,6 +363,7 @@ EngineArgs base_args(const rexi_plan* p, int mode, const DescSet& set, int nprob
     A.item = set.d_items;
     A.bar = p->d_bar;
     A.err = p->d_err;
+    A.bytes = p->d_bytes;
     A.trace = p->trace_cap > 0 ? p->d_trace : nullptr;
     A.trace_cap = p->trace_cap;
     A.cta_trace = p->cta_trace_phases > 0 ? p->d_cta_trace : nullptr;
@@ -397,6 +399,7 @@ int sm_count(int device) {
 int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(p->d_bar, 0, 2 * sizeof(unsigned), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stats, 0, sizeof(ItemStats) * A.nitems, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     const size_t smem = rexi::engine_smem_bytes(A.nitems, p->fp32, A.ortho);
@@ -415,8 +418,11 @@ int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles,
 int collect(rexi_plan* p, cudaStream_t stream, int nitems, int item_offset, int poles, rexi_stats* st,
             int n_sub) {
     int err = 0;
+    unsigned long long nbytes = 0;
     std::vector<ItemStats> s(nitems);
     cudaError_t e = cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&nbytes, p->d_bytes, sizeof(nbytes), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s.data(), p->d_stats, sizeof(ItemStats) * nitems, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -441,6 +447,7 @@ int collect(rexi_plan* p, cudaStream_t stream, int nitems, int item_offset, int 
             st->max_iters_seen = std::max(st->max_iters_seen, x.max_sub_iters);
         }
         st->status = status;
+        st->bytes = (double)nbytes;
     }
     return status;
 }
@@ -513,7 +520,9 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     if (opt.precision != REXI_FP64 && opt.precision != REXI_MIXED) return REXI_EINVAL;
     if (opt.restart_m < 1 || opt.restart_m > REXI_MAX_RESTART || opt.max_iters < 1) return REXI_EINVAL;
     if (opt.ortho != 0 && opt.ortho != 1) return REXI_EINVAL;
-    if (opt.ortho == 1 && opt.restart_m > REXI_MAX_RESTART - 1) return REXI_EINVAL;   // m+1 dot vectors
+    // full orthogonalisation keeps m + 1 dot products per step in registers
+    if (opt.window == 0 && opt.restart_m > (opt.ortho == 1 ? REXI_MAX_RESTART_FULL : REXI_MAX_RESTART_FULL + 1))
+        return REXI_EINVAL;
     if (opt.window < 0 || opt.window == 1 || opt.window > REXI_MAX_RESTART || (opt.window > 0 && opt.ortho != 1))
         return REXI_EINVAL;
     if (!(opt.tol >= 0.0) || !(opt.R1 >= 0.0) || !(opt.inner_tol >= 0.0) || !(opt.stabilize_eps >= 0.0) ||
@@ -607,6 +616,7 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     if ((st = dalloc(p, &p->d_hout, n))) return fail(st);
     if ((st = dalloc(p, &p->d_bar, 2))) return fail(st);
     if ((st = dalloc(p, &p->d_err, 1))) return fail(st);
+    if ((st = dalloc(p, &p->d_bytes, 1))) return fail(st);
     {
         std::vector<double2> al(K);
         for (int k = 0; k < K; ++k) al[k] = make_double2(p->alpha[k].real(), p->alpha[k].imag());
@@ -874,6 +884,7 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
             return REXI_ECUDA;
     cudaError_t e = cudaMemsetAsync(p0->d_bar, 0, 2 * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_bytes, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_stats, 0, sizeof(ItemStats) * (p0->K + p0->ngroups), s);
     if (e != cudaSuccess) return REXI_ECUDA;
     const size_t smem = rexi::engine_smem_bytes(A.nitems, p0->fp32, A.ortho);
@@ -890,6 +901,9 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
     if (e != cudaSuccess) return cuda_fail(e);
     if (!st) return REXI_OK;
     int status = REXI_OK;
+    unsigned long long nbytes = 0;
+    if (cudaMemcpyAsync(&nbytes, p0->d_bytes, sizeof(nbytes), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return REXI_ECUDA;
     for (int b = 0; b < B; ++b) {
         rexi_plan* p = plans[b];
         int err = 0;
@@ -916,6 +930,7 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
             failed = failed || sv[k].failed;
         }
         o.status = err ? err : (failed ? REXI_ENOCONV : REXI_OK);
+        o.bytes = (double)nbytes;
         if (o.status != REXI_OK && status == REXI_OK) status = o.status;
         p->last_status = o.status;
     }

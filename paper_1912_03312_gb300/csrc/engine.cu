@@ -22,6 +22,7 @@
 // state, split evenly over the CTAs.  Partial dot products are written per tile
 // and reduced in FP64 by the CTAs of the next phase.  Basis vectors u_i are
 // stored unnormalised; v_i = s_i u_i with an FP64 scale s_i.
+#include <algorithm>
 #include <cstdint>
 
 #include "engine.h"
@@ -190,7 +191,6 @@ struct Smem {
     float2 coeff[kMaxM + 1];       // the same, rounded for the FP32 path
     double ssm[kMaxM + 1];
     double2 gsm[kMaxM + 1];
-    double2 Rsm[kMaxM * (kMaxM + 3) / 2];   // R (E2) or the unrotated Hessenberg columns (Y)
     double2 hfin[kMaxM + 2];       // Y: column j-1 completed
     double2 hnew[kMaxM + 2];       // Y: column j (pending)
     double2 coefG[kMaxM + 1];      // Y: coefficients of v_{j+1}
@@ -207,8 +207,12 @@ struct Smem {
     int ntasks;
     int kk;                        // Arnoldi steps of the current item (E2)
     const void* basis;             // basis the current item's E2 reads
+    double2* scratch;              // dynamic shared memory aliased with the staging tiles:
+                                   // R (E2) or Hessenberg columns (Y), kScratch entries
     double2 yhat[kMaxM];           // PS: sum of alpha_k y_k of the poles completed on the shared basis
     int kyhat;                     //     its length (0: none)
+    int nxlive;                    //     poles whose x the pole sum reads
+    unsigned long long nbytes;     // algorithmic bytes this CTA moved (thread 0)
     const void* gbasis;            //     the shared basis
 };
 
@@ -298,6 +302,11 @@ __device__ void build_list(Smem& sm, int* list, int* prefix, unsigned mask) {
 }
 
 // Problems live in (backward) substep `sub`, with their tile prefix sums.
+// The pole sum and the adjoint accumulation are FP64 work with no reuse:
+// small tasks spread them over every SM.
+constexpr int kPsPPT = 2;
+constexpr int kPsTile = kBlock * kPsPPT;
+
 __device__ void build_problem_list(Smem& sm, int* list, int* prefix, int sub) {
     const EngineArgs& A = sm.A;
     if (threadIdx.x == 0) {
@@ -307,7 +316,7 @@ __device__ void build_problem_list(Smem& sm, int* list, int* prefix, int sub) {
                 list[c] = p;
                 prefix[c] = t;
                 ++c;
-                t += A.prob[p].ntiles;
+                t += (A.prob[p].n + kPsTile - 1) / kPsTile;
             }
         }
         prefix[c] = t;
@@ -444,23 +453,31 @@ __device__ __forceinline__ Runs item_runs(const int* prefix, int l, int T) {
 }
 
 // out[i] = scale_i * sum over the runs of item slot l of part[run][i], i < nv (nv <= 32).
+// The CTA's threads split into nvp-wide groups (nvp = nv rounded up to a
+// power of two) that stride over the runs, so an item spread over hundreds of
+// CTAs costs a few rounds of independent loads, then a tree over the groups.
 __device__ void reduce_partials(Smem& sm, const double2* part, const ItemDesc& it, const Runs& R, int nv,
                                 const double* scale, double2* out) {
-    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    int nvp = 1;
+    while (nvp < nv) nvp <<= 1;
+    const int v = threadIdx.x & (nvp - 1), g = threadIdx.x / nvp, ng = kBlock / nvp;
     double2 acc = make_double2(0.0, 0.0);
-    if (lane < nv) {
-        for (int r = grp; r < R.count; r += kWarps) {
+    if (v < nv) {
+        const double2* pv = part + (size_t)it.tile_off * sm.A.pv + v;
+#pragma unroll 4
+        for (int r = g; r < R.count; r += ng) {
             const int tl = R.tile(r);
-            if (tl >= 0) acc = cadd(acc, ldp(part + (size_t)(it.tile_off + tl) * sm.A.pv + lane));
+            if (tl >= 0) acc = cadd(acc, ldp(pv + (size_t)tl * sm.A.pv));
         }
     }
-    sm.red[grp][lane] = acc;
+    double2* red = &sm.red[0][0];              // kBlock entries
+    red[threadIdx.x] = acc;
     __syncthreads();
-    if (threadIdx.x < nv) {
-        double2 s2 = make_double2(0.0, 0.0);
-        for (int g = 0; g < kWarps; ++g) s2 = cadd(s2, sm.red[g][threadIdx.x]);
-        out[threadIdx.x] = cscale(s2, scale[threadIdx.x]);
+    for (int h = ng >> 1; h > 0; h >>= 1) {
+        if (g < h) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + h * nvp]);
+        __syncthreads();
     }
+    if (threadIdx.x < nv) out[threadIdx.x] = cscale(red[threadIdx.x], scale[threadIdx.x]);
     __syncthreads();
 }
 
@@ -485,6 +502,38 @@ __device__ __forceinline__ int win_start(const EngineArgs& A, int j) {
 // locally, and ||r|| <= sqrt(k + 1) |g_{k+1}| (unit columns).
 __device__ __forceinline__ double res_bound(const EngineArgs& A, double res, int k) {
     return A.window > 0 ? res * sqrt((double)(k + 1)) : res;
+}
+
+// y = R^{-1} g for the packed upper triangle R (column l at l(l+1)/2) in
+// shared memory, k <= 64, by one warp: lane i holds rows i and i + 32 and the
+// columns are eliminated from the last; y lands in shared memory.
+__device__ void back_substitute(const double2* R, const double2* g, double2* y, int k) {
+    const int lane = threadIdx.x & 31;
+    double2 a0 = lane < k ? g[lane] : make_double2(0.0, 0.0);
+    double2 a1 = lane + 32 < k ? g[lane + 32] : make_double2(0.0, 0.0);
+    for (int l = k - 1; l >= 0; --l) {
+        const double2* col = R + l * (l + 1) / 2;
+        double2 yl = make_double2(0.0, 0.0);
+        if (lane == (l & 31)) {
+            const double2 d = col[l];
+            const double2 a = l < 32 ? a0 : a1;
+            const double den = d.x * d.x + d.y * d.y;
+            if (den > 0.0) yl = cscale(cmul(a, cconj(d)), 1.0 / den);
+            y[l] = yl;
+        }
+        yl = shfl2(yl, l & 31);
+        if (lane < l) a0 = csub(a0, cmul(col[lane], yl));
+        if (lane + 32 < l) a1 = csub(a1, cmul(col[lane + 32], yl));
+    }
+    __syncwarp();
+}
+
+// Algorithmic byte count: points of a run times the bytes a point moves.
+__device__ __forceinline__ long long run_points(int n, int tile, int tb, int te) {
+    return (long long)min(n, te * tile) - (long long)tb * tile;
+}
+__device__ __forceinline__ void acct(Smem& sm, long long pts, long long bytes_per_point) {
+    if (threadIdx.x == 0) sm.nbytes += (unsigned long long)(pts * bytes_per_point);
 }
 
 __device__ __forceinline__ void load_scales(Smem& sm, const ItemState* S, int cnt) {
@@ -515,6 +564,9 @@ struct Phases {
         V* U = (V*)it.basis;
         double2* x = it.x;
         double acc = 0.0;
+        acct(sm, run_points(it_n, it_tile, tb, te),
+             16 + (cycles > 0 ? 16 + 8 : (x != nullptr ? 16 : 0)) +
+                 ((it.group >= 0 && cycles == 0) ? 0 : (long long)sizeof(V)));
         for (int tile = tb; tile < te; ++tile) {
             const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
             double2 rv[kPPT];
@@ -685,6 +737,7 @@ struct Phases {
         const EngineArgs& A = sm.A;
         const ItemDesc& it = A.item[item];
         const int it_n = it.n, it_tile = it.tile;
+        acct(sm, run_points(it_n, it_tile, tb, te), (j + 3) * (long long)sizeof(V) + (long long)sizeof(T));
         const ProblemDesc& pr = A.prob[it.problem];
         const size_t n = (size_t)it_n;
         V* U = (V*)it.basis;
@@ -738,6 +791,7 @@ struct Phases {
     static __device__ void p2(Smem& sm, V* ws, int item, int tb, int te, int j) {
         const ItemDesc& it = sm.A.item[item];
         const int it_n = it.n, it_tile = it.tile;
+        acct(sm, run_points(it_n, it_tile, tb, te), (2 * j + 3) * (long long)sizeof(V));
         const size_t n = (size_t)it_n;
         const V* U = (const V*)it.basis;
         const V* wv = U + (size_t)(j + 1) * n;
@@ -778,6 +832,7 @@ struct Phases {
     static __device__ void p3(Smem& sm, int item, int tb, int te, int j) {
         const ItemDesc& it = sm.A.item[item];
         const int it_n = it.n, it_tile = it.tile;
+        acct(sm, run_points(it_n, it_tile, tb, te), (j + 3) * (long long)sizeof(V));
         const size_t n = (size_t)it_n;
         V* U = (V*)it.basis;
         V* wv = U + (size_t)(j + 1) * n;
@@ -864,6 +919,8 @@ struct Phases {
         const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
         const int j0 = win_start(A, j);                     // dots with q_j0 .. q_{j-1} and v_j
         const V* U0 = U + (size_t)j0 * n;
+        acct(sm, run_points(it_n, it_tile, tb, te),
+             (j - j0 + 1) * (long long)sizeof(V) + (matvec ? (long long)sizeof(V) + (long long)sizeof(T) : 0));
         const DotPlan d = dot_plan(j + 1 - j0, it_tile);
         T ar[4] = {T(0), T(0), T(0), T(0)}, ai[4] = {T(0), T(0), T(0), T(0)};
         T br[4] = {T(0), T(0), T(0), T(0)}, bi[4] = {T(0), T(0), T(0), T(0)};
@@ -911,8 +968,12 @@ struct Phases {
         __syncthreads();                                                   // q_i normalised; t_j
         reduce_partials(sm, it.part1, it, R, j + 1 - j0, sm.ssm + j0, sm.h1 + j0);        // a_i, c
         if (!last) reduce_partials(sm, it.part2, it, R, j + 1 - j0, sm.ssm + j0, sm.h2 + j0);   // b_i, d
-        const int nH = j >= 2 ? (j - 1) * (j + 2) / 2 : 0;                 // columns 0..j-2
-        for (int t = threadIdx.x; t < nH; t += kBlock) sm.Rsm[t] = ldp(&S->H[t]);
+        double2* Hw = sm.scratch;                                          // columns j0..j-2, pitch kHld
+        const int ncol = max(0, j - 1 - j0);
+        for (int t = threadIdx.x; t < ncol * kHld; t += kBlock) {
+            const int l = j0 + t / kHld, i = t - (t / kHld) * kHld;
+            if (i <= l + 1) Hw[t] = ldp(&S->H[l * (l + 3) / 2 + i]);
+        }
         if (threadIdx.x < j) sm.hfin[threadIdx.x] = ldp(((j - 1) & 1 ? S->hcol2 : S->hcol) + threadIdx.x);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -940,7 +1001,7 @@ struct Phases {
             const int i = threadIdx.x;
             double2 Ha = make_double2(0.0, 0.0);                            // (H a)_i over columns l < j
             for (int l = max(max(i - 1, 0), j0); l < j; ++l) {
-                const double2 Hil = l == j - 1 ? sm.hfin[i] : sm.Rsm[l * (l + 3) / 2 + i];
+                const double2 Hil = l == j - 1 ? sm.hfin[i] : Hw[(l - j0) * kHld + i];
                 Ha = cadd(Ha, cmul(Hil, sm.h1[l]));
             }
             const double inv = sm.yscal[2];
@@ -964,7 +1025,7 @@ struct Phases {
             const int i = j;
             double2 Ha = make_double2(0.0, 0.0);
             for (int l = max(max(i - 1, 0), j0); l < j; ++l) {
-                const double2 Hil = l == j - 1 ? sm.hfin[i] : sm.Rsm[l * (l + 3) / 2 + i];
+                const double2 Hil = l == j - 1 ? sm.hfin[i] : Hw[(l - j0) * kHld + i];
                 Ha = cadd(Ha, cmul(Hil, sm.h1[l]));
             }
             sm.ygq = cadd(cscale(Ha, sm.yscal[2]), sm.hnew[j]);            // gamma_j
@@ -983,6 +1044,7 @@ struct Phases {
         const T tq = (T)sm.yscal[1], tw = (T)sm.yscal[2];
         const V gq = cvt2<V>(sm.ygq);
         const int j0 = win_start(sm.A, j);
+        acct(sm, run_points(it_n, it_tile, tb, te), (j - j0 + 4) * (long long)sizeof(V));
         for (int tile = tb; tile < te; ++tile) {
             const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
             for (int r0 = 0; r0 < kPPT && p0 + r0 * kBlock < pend; r0 += kChunk) {
@@ -1033,7 +1095,8 @@ struct Phases {
         const bool shared = ldi(&S->shared) != 0;
         const ItemDesc& src = shared ? sm.A.item[it.group] : it;   // owner of the basis used
         const int nR = k * (k + 1) / 2;
-        for (int t = threadIdx.x; t < nR; t += kBlock) sm.Rsm[t] = ldp(&S->R[t]);
+        double2* Rs = sm.scratch;
+        for (int t = threadIdx.x; t < nR; t += kBlock) Rs[t] = ldp(&S->R[t]);
         if (threadIdx.x < k) {
             sm.gsm[threadIdx.x] = ldp(&S->g[threadIdx.x]);
             sm.ssm[threadIdx.x] = sm.A.ortho ? 1.0 : ldd(&src.st->s[threadIdx.x]);
@@ -1043,21 +1106,12 @@ struct Phases {
             sm.basis = src.basis;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int i = k - 1; i >= 0; --i) {
-                double2 acc = sm.gsm[i];
-                for (int l = i + 1; l < k; ++l) acc = csub(acc, cmul(sm.Rsm[l * (l + 1) / 2 + i], sm.h2[l]));
-                const double2 d = sm.Rsm[i * (i + 1) / 2 + i];
-                const double den = d.x * d.x + d.y * d.y;
-                double2 y = make_double2(0.0, 0.0);
-                if (den > 0.0) y = cscale(cmul(acc, cconj(d)), 1.0 / den);
-                sm.h2[i] = y;                              // y_i
-            }
-            for (int i = 0; i < k; ++i) {
-                const double2 c = cscale(sm.h2[i], sm.ssm[i]);
-                sm.coef[i] = c;
-                sm.coeff[i] = make_float2((float)c.x, (float)c.y);
-            }
+        if (threadIdx.x < 32) back_substitute(Rs, sm.gsm, sm.h2, k);      // y_i into h2
+        __syncthreads();
+        if (threadIdx.x < k) {
+            const double2 c = cscale(sm.h2[threadIdx.x], sm.ssm[threadIdx.x]);
+            sm.coef[threadIdx.x] = c;
+            sm.coeff[threadIdx.x] = make_float2((float)c.x, (float)c.y);
         }
         __syncthreads();
     }
@@ -1072,6 +1126,7 @@ struct Phases {
         const V* U = (const V*)sm.basis;
         double2* x = it.x;
         const int k = sm.kk;
+        acct(sm, run_points(it_n, it_tile, tb, te), k * (long long)sizeof(V) + 32);
         for (int tile = tb; tile < te; ++tile) {
             const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
             for (int r0 = 0; r0 < kPPT && p0 + r0 * kBlock < pend; r0 += kChunk) {
@@ -1228,6 +1283,11 @@ __device__ void load_problem_items(Smem& sm, int prob) {
     for (int k = threadIdx.x; k < pr.K; k += kBlock) sm.alpha[k] = __ldg(pr.alpha + k);
     if (threadIdx.x == 0) sm.kyhat = 0;
     __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int k = 0; k < nx; ++k) c += sm.xptr[k] != nullptr;
+        sm.nxlive = c;
+    }
     const int grp = A.mode == MODE_STEP ? A.item[pr.item0].group : -1;
     if (grp >= 0) {
         const ItemDesc& gd = A.item[grp];
@@ -1279,22 +1339,35 @@ __device__ void member_direct_solve(const EngineArgs& A, int item) {
     ItemState* M = A.item[item].st;
     if (ldi(&M->ydone)) return;
     const int k = ldi(&M->k);
-    double2 acc = lane < k ? ldp(&M->g[lane]) : make_double2(0.0, 0.0);
-    double2 y = make_double2(0.0, 0.0);
-    double2 rc = (k > 0 && lane < k) ? ldp(&M->R[(k - 1) * k / 2 + lane]) : make_double2(0.0, 0.0);
+    double2 a0 = lane < k ? ldp(&M->g[lane]) : make_double2(0.0, 0.0);
+    double2 a1 = lane + 32 < k ? ldp(&M->g[lane + 32]) : make_double2(0.0, 0.0);
+    double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
+    // column l of R for rows lane and lane + 32, the next column fetched ahead
+    auto col = [&](int l, double2& c0, double2& c1) {
+        const double2* R = M->R + l * (l + 1) / 2;
+        c0 = (l >= 0 && lane <= l) ? ldp(R + lane) : make_double2(0.0, 0.0);
+        c1 = (l >= 0 && lane + 32 <= l) ? ldp(R + lane + 32) : make_double2(0.0, 0.0);
+    };
+    double2 c0, c1, n0, n1;
+    col(k - 1, c0, c1);
     for (int l = k - 1; l >= 0; --l) {
-        const double2 rn = (l > 0 && lane < l) ? ldp(&M->R[(l - 1) * l / 2 + lane]) : make_double2(0.0, 0.0);
+        col(l - 1, n0, n1);
         double2 yl = make_double2(0.0, 0.0);
-        if (lane == l) {
-            const double den = rc.x * rc.x + rc.y * rc.y;
-            if (den > 0.0) yl = cscale(cmul(acc, cconj(rc)), 1.0 / den);
-            y = yl;
+        if (lane == (l & 31)) {
+            const double2 d = l < 32 ? c0 : c1;
+            const double2 a = l < 32 ? a0 : a1;
+            const double den = d.x * d.x + d.y * d.y;
+            if (den > 0.0) yl = cscale(cmul(a, cconj(d)), 1.0 / den);
+            if (l < 32) y0 = yl; else y1 = yl;
         }
-        yl = shfl2(yl, l);
-        if (lane < l) acc = csub(acc, cmul(rc, yl));
-        rc = rn;
+        yl = shfl2(yl, l & 31);
+        if (lane < l) a0 = csub(a0, cmul(c0, yl));
+        if (lane + 32 < l) a1 = csub(a1, cmul(c1, yl));
+        c0 = n0;
+        c1 = n1;
     }
-    if (lane < k) M->y[lane] = y;
+    if (lane < k) M->y[lane] = y0;
+    if (lane + 32 < k) M->y[lane + 32] = y1;
     if (lane == 0) M->ydone = 1;
 }
 
@@ -1525,66 +1598,71 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
 // PS: psi' = alpha_0 b + sum_k alpha_k x_k for one tile of a problem (poles
 // completed on the shared basis enter as sum_i yhat_i u_i).
 template <typename T>
-__device__ void task_pole_sum(const Smem& sm, int prob, int tile, int sub) {
+__device__ void task_pole_sum(Smem& sm, int prob, int tile, int sub) {
     typedef typename C2<T>::t V;
     const ProblemDesc& pr = sm.A.prob[prob];
     const double2* b = step_in(sm.io, pr, prob, sub);
     double2* out = step_out(sm.io, pr, prob, sub);
-    const int p0 = tile * kTile, pend = min(pr.n, p0 + kTile);
-    double2 acc[kPPT];
+    const int p0 = tile * kPsTile, pend = min(pr.n, p0 + kPsTile);
+    acct(sm, pend - p0, 32 + 16 * (long long)sm.nxlive + (long long)sm.kyhat * (long long)sizeof(V));
+    double2 acc[kPsPPT];
 #pragma unroll
-    for (int r = 0; r < kPPT; ++r) {
+    for (int r = 0; r < kPsPPT; ++r) {
         const int p = p0 + r * kBlock + threadIdx.x;
         acc[r] = p < pend ? cmul(pr.alpha0, ldp(b + p)) : make_double2(0.0, 0.0);
     }
+#pragma unroll 4
     for (int k = 0; k < pr.K; ++k) {
         const double2* xk = sm.xptr[k];
         if (xk == nullptr) continue;
         const double2 al = sm.alpha[k];
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
+        for (int r = 0; r < kPsPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
             if (p < pend) acc[r] = cadd(acc[r], cmul(al, ldp(xk + p)));
         }
     }
     const V* Ug = (const V*)sm.gbasis;
+#pragma unroll 4
     for (int i = 0; i < sm.kyhat; ++i) {
         const V* ui = Ug + (size_t)i * pr.n;
         const double2 c = sm.yhat[i];
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
+        for (int r = 0; r < kPsPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
             if (p < pend) acc[r] = cadd(acc[r], cmul(c, up2(ldp(ui + p))));
         }
     }
 #pragma unroll
-    for (int r = 0; r < kPPT; ++r) {
+    for (int r = 0; r < kPsPPT; ++r) {
         const int p = p0 + r * kBlock + threadIdx.x;
         if (p < pend) out[p] = acc[r];
     }
 }
 
 // BA: adjoint accumulation for one tile of a problem (backward substep bs).
-__device__ void task_adjoint(const Smem& sm, int prob, int tile, int bs) {
+__device__ void task_adjoint(Smem& sm, int prob, int tile, int bs) {
     const ProblemDesc& pr = sm.A.prob[prob];
     const double2* gin = adj_in(sm.io, pr, prob, bs);
     double2* gout = adj_out(sm.io, pr, prob, bs);
     double* dV = sm.io.dLdV[prob];
-    const int p0 = tile * kTile, pend = min(pr.n, p0 + kTile);
-    double2 g[kPPT];
-    double dv[kPPT];
+    const int p0 = tile * kPsTile, pend = min(pr.n, p0 + kPsTile);
+    acct(sm, pend - p0, 32 + 32 * (long long)pr.K + 16);
+    double2 g[kPsPPT];
+    double dv[kPsPPT];
 #pragma unroll
-    for (int r = 0; r < kPPT; ++r) {
+    for (int r = 0; r < kPsPPT; ++r) {
         const int p = p0 + r * kBlock + threadIdx.x;
         g[r] = p < pend ? cmul(cconj(pr.alpha0), ldp(gin + p)) : make_double2(0.0, 0.0);
         dv[r] = 0.0;
     }
+#pragma unroll 2
     for (int k = 0; k < pr.K; ++k) {
         const double2* X = sm.xptr[k];
         const double2* Y = sm.xptr[pr.K + k];
         const double2 al = sm.alpha[k];
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
+        for (int r = 0; r < kPsPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
             if (p < pend) {
                 const double2 xv = ldp(X + p), yv = ldp(Y + p);
@@ -1594,7 +1672,7 @@ __device__ void task_adjoint(const Smem& sm, int prob, int tile, int bs) {
         }
     }
 #pragma unroll
-    for (int r = 0; r < kPPT; ++r) {
+    for (int r = 0; r < kPsPPT; ++r) {
         const int p = p0 + r * kBlock + threadIdx.x;
         if (p < pend) {
             gout[p] = g[r];
@@ -1632,6 +1710,7 @@ __global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __gri
     int* prefix = dyn + A.nitems;
     // tile staging buffer (16-byte aligned) after the list and prefix arrays
     typename C2<T>::t* ws = (typename C2<T>::t*)(dyn + ((2 * A.nitems + 2 + 3) & ~3));
+    if (threadIdx.x == 0) sm.scratch = (double2*)ws;
     const int warp = threadIdx.x >> 5;
     const int gwarp = blockIdx.x * kWarps + warp;
     const int nwarps = gridDim.x * kWarps;
@@ -1639,6 +1718,7 @@ __global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __gri
     __shared__ int tcount;
     if (threadIdx.x == 0) {
         tcount = 1;
+        sm.nbytes = 0ull;
         const unsigned long long t0 = global_ns();
         if (A.trace != nullptr && blockIdx.x == 0 && A.trace_cap > 0) {
             A.trace[1] = 99ull;
@@ -1773,6 +1853,7 @@ __global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __gri
             if (!phase_sync(A, TR_SUM, &tcount)) return;
         }
     }
+    if (threadIdx.x == 0 && A.bytes != nullptr) atomicAdd(A.bytes, sm.nbytes);
 }
 
 // ---- single-stage kernels ------------------------------------------------------
@@ -1808,8 +1889,9 @@ __global__ void __launch_bounds__(kBlock) pole_sum_kernel(const ProblemDesc* __r
 size_t engine_smem_bytes(int nitems, bool fp32, int ortho) {
     // list + prefix (ints, rounded to 16 bytes) + staging tiles of the basis type
     // (delayed CGS2 stages the v and w tiles of a step together)
+    const size_t tiles = (ortho ? 2 : 1) * (size_t)kTile * (fp32 ? sizeof(float2) : sizeof(double2));
     return (size_t)((2 * nitems + 2 + 3) & ~3) * sizeof(int) +
-           (ortho ? 2 : 1) * (size_t)kTile * (fp32 ? sizeof(float2) : sizeof(double2));
+           std::max(tiles, (size_t)kScratch * sizeof(double2));
 }
 
 static void* engine_fn(bool fp32) {

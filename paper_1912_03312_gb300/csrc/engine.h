@@ -9,7 +9,9 @@ namespace rexi {
 constexpr int kBlock = 256;            // threads per CTA
 constexpr int kPPT = 8;                // points per thread per task
 constexpr int kTile = kBlock * kPPT;   // points per (item, tile) task
-constexpr int kMaxM = 32;              // largest restart length (dot accumulators live in registers)
+constexpr int kMaxM = 64;              // largest restart length (windowed bases; full ones: 31 / 32)
+constexpr int kHld = kMaxM + 2;        // pitch of Hessenberg columns staged in shared memory
+constexpr int kScratch = kMaxM * (kMaxM + 3) / 2;   // shared scratch entries (R or H columns)
 constexpr int kMaxItems = 4096;        // items (shifted solves) per launch
 constexpr int kMaxBatch = 128;         // problems per launch
 constexpr int kMaxPoles = 256;         // poles per problem
@@ -134,6 +136,8 @@ struct EngineArgs {
     int cta_trace_phases;
     int cta_trace_stride;
     int window;          // delayed CGS2: 0 = whole basis; L = only the last L vectors (Hermitian operators)
+    int pad3;
+    unsigned long long* bytes;   // optional: algorithmic bytes of the launch (atomic sum over CTAs)
 };
 
 // phase codes recorded in the trace at the barrier that ends each phase

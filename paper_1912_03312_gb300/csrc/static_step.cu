@@ -70,7 +70,8 @@ extern "C" int rexi_substep_static(const rexi_grid* g, const double* V, double t
     if (opt.precision != REXI_FP64 && opt.precision != REXI_MIXED) return REXI_EINVAL;
     if (opt.restart_m < 1 || opt.restart_m > REXI_MAX_RESTART || opt.max_iters < 1 || !(opt.tol > 0.0))
         return REXI_EINVAL;
-    if ((opt.ortho != 0 && opt.ortho != 1) || (opt.ortho == 1 && opt.restart_m > REXI_MAX_RESTART - 1))
+    if (opt.ortho != 0 && opt.ortho != 1) return REXI_EINVAL;
+    if (opt.window == 0 && opt.restart_m > (opt.ortho == 1 ? REXI_MAX_RESTART_FULL : REXI_MAX_RESTART_FULL + 1))
         return REXI_EINVAL;
     if (opt.window < 0 || opt.window == 1 || opt.window > REXI_MAX_RESTART || (opt.window > 0 && opt.ortho != 1))
         return REXI_EINVAL;

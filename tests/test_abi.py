@@ -107,9 +107,13 @@ def test_argument_validation_before_device(lib):
     lib.rexi_options_default(C.byref(o))
     o.restart_m = 64
     assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
-    o.restart_m = N.REXI_MAX_RESTART          # delayed CGS2 projects m+1 vectors: at most MAX-1
-    assert o.ortho == 1
+    o.restart_m = N.REXI_MAX_RESTART_FULL + 1  # full delayed CGS2 keeps m+1 dots in registers
+    assert o.ortho == 1 and o.window == 0
     assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    o.restart_m = N.REXI_MAX_RESTART + 1
+    o.window = 2
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    o.window = 0
     o.ortho = 2
     o.restart_m = 30
     assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL

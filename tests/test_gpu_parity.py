@@ -270,3 +270,21 @@ def test_windowed_basis_matches_oracle(precision, window, K, R1, n, dt, shared):
             kk = int(np.argmin(np.abs(orc.z - z[k])))
             xo, _ = ostep.solve_pole(V, orc.h, psi, orc.tau, orc.z[kk], tol=1e-14)
             assert relerr(x[k], xo) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("m", [40, 64])
+def test_long_windowed_cycles_match_oracle(precision, m):
+    # a window keeps the per-step cost fixed, so restart lengths past the
+    # full-orthogonalisation limit are allowed; tol is tight enough that the
+    # shared cycle runs long
+    g, V, psi = wl.random_problem(43, (150, 120), box=8.0)
+    K, R1, dt, tol = 32, 68.0, 0.5, 1e-13
+    lp = library_plan(g, V, dt, K, R1, precision=precision, tol=tol, window=2, restart=m, max_iters=20000)
+    orc = OraclePlan(g, V, dt, K, R1)
+    out, st = lp.step(to_dev(psi), stats=True)
+    assert st["status"] == 0
+    ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
+    floor = 1e-10 if precision == "fp64" else 1e-6
+    assert relerr(out.cpu().numpy(), ref) < max(floor, 2.0 * orc.A * tol)
+    assert max(st["iters"]) <= 20000
