@@ -138,6 +138,8 @@ typedef struct {
                                          reads or writes (basis, state, x, potential),
                                          counted once per pass by the kernel as it works;
                                          batched: the whole launch, in every entry        */
+    double flops64;                   /* FP64 flops of the launch's arithmetic (an FMA is 2),
+                                         counted the same way                              */
 } rexi_stats;
 
 typedef struct rexi_plan rexi_plan;   /* opaque, owned by the library */

@@ -52,7 +52,7 @@ class Stats(C.Structure):
                 ("total_iters", C.c_int), ("total_cycles", C.c_int),
                 ("iters", C.c_int * REXI_MAX_POLES), ("cycles", C.c_int * REXI_MAX_POLES),
                 ("iters_sq", C.c_int * REXI_MAX_POLES), ("resid", C.c_double * REXI_MAX_POLES),
-                ("bytes", C.c_double)]
+                ("bytes", C.c_double), ("flops64", C.c_double)]
 
 
 _P = C.c_void_p

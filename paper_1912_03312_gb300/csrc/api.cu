@@ -74,7 +74,7 @@ struct rexi_plan {
     double2* d_hout = nullptr;
     unsigned* d_bar = nullptr;
     int* d_err = nullptr;
-    unsigned long long* d_bytes = nullptr;       // algorithmic bytes of the last launch
+    unsigned long long* d_bytes = nullptr;       // [2] algorithmic bytes and FP64 flops of the last launch
     int nit_cap = 0;                             // pole items with workspace (K or 2K)
     int ngroups = 0;                             // shared-cycle group items (0, 1 or 2)
     bool shared = true;
@@ -399,7 +399,7 @@ int sm_count(int device) {
 int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(p->d_bar, 0, 2 * sizeof(unsigned), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, 2 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stats, 0, sizeof(ItemStats) * A.nitems, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     const size_t smem = rexi::engine_smem_bytes(A.nitems, p->fp32, A.ortho);
@@ -418,11 +418,11 @@ int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles,
 int collect(rexi_plan* p, cudaStream_t stream, int nitems, int item_offset, int poles, rexi_stats* st,
             int n_sub) {
     int err = 0;
-    unsigned long long nbytes = 0;
+    unsigned long long nbytes[2] = {0, 0};
     std::vector<ItemStats> s(nitems);
     cudaError_t e = cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&nbytes, p->d_bytes, sizeof(nbytes), cudaMemcpyDeviceToHost, stream);
+        e = cudaMemcpyAsync(nbytes, p->d_bytes, sizeof(nbytes), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s.data(), p->d_stats, sizeof(ItemStats) * nitems, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -447,7 +447,8 @@ int collect(rexi_plan* p, cudaStream_t stream, int nitems, int item_offset, int 
             st->max_iters_seen = std::max(st->max_iters_seen, x.max_sub_iters);
         }
         st->status = status;
-        st->bytes = (double)nbytes;
+        st->bytes = (double)nbytes[0];
+        st->flops64 = (double)nbytes[1];
     }
     return status;
 }
@@ -616,7 +617,7 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     if ((st = dalloc(p, &p->d_hout, n))) return fail(st);
     if ((st = dalloc(p, &p->d_bar, 2))) return fail(st);
     if ((st = dalloc(p, &p->d_err, 1))) return fail(st);
-    if ((st = dalloc(p, &p->d_bytes, 1))) return fail(st);
+    if ((st = dalloc(p, &p->d_bytes, 2))) return fail(st);
     {
         std::vector<double2> al(K);
         for (int k = 0; k < K; ++k) al[k] = make_double2(p->alpha[k].real(), p->alpha[k].imag());
@@ -884,7 +885,7 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
             return REXI_ECUDA;
     cudaError_t e = cudaMemsetAsync(p0->d_bar, 0, 2 * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_bytes, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_bytes, 0, 2 * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_stats, 0, sizeof(ItemStats) * (p0->K + p0->ngroups), s);
     if (e != cudaSuccess) return REXI_ECUDA;
     const size_t smem = rexi::engine_smem_bytes(A.nitems, p0->fp32, A.ortho);
@@ -901,8 +902,8 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
     if (e != cudaSuccess) return cuda_fail(e);
     if (!st) return REXI_OK;
     int status = REXI_OK;
-    unsigned long long nbytes = 0;
-    if (cudaMemcpyAsync(&nbytes, p0->d_bytes, sizeof(nbytes), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    unsigned long long nbytes[2] = {0, 0};
+    if (cudaMemcpyAsync(nbytes, p0->d_bytes, sizeof(nbytes), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return REXI_ECUDA;
     for (int b = 0; b < B; ++b) {
         rexi_plan* p = plans[b];
@@ -930,7 +931,8 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
             failed = failed || sv[k].failed;
         }
         o.status = err ? err : (failed ? REXI_ENOCONV : REXI_OK);
-        o.bytes = (double)nbytes;
+        o.bytes = (double)nbytes[0];
+        o.flops64 = (double)nbytes[1];
         if (o.status != REXI_OK && status == REXI_OK) status = o.status;
         p->last_status = o.status;
     }

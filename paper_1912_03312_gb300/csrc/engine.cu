@@ -49,6 +49,20 @@ template <> __device__ __forceinline__ double2 cvt2<double2>(double2 a) { return
 __device__ __forceinline__ double2 up2(float2 a) { return make_double2(a.x, a.y); }
 __device__ __forceinline__ double2 up2(double2 a) { return a; }
 
+// Double to float by integer operations only (rounding toward zero; results
+// below the float range become signed zero, above it (and NaN) signed
+// infinity), so the conversion does not occupy the FP64 pipe.
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ float2 dot_f2(double2 a) { return make_float2(f64_to_f32_rz(a.x), f64_to_f32_rz(a.y)); }
+__device__ __forceinline__ float2 dot_f2(float2 a) { return a; }
+
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -213,6 +227,7 @@ struct Smem {
     int kyhat;                     //     its length (0: none)
     int nxlive;                    //     poles whose x the pole sum reads
     unsigned long long nbytes;     // algorithmic bytes this CTA moved (thread 0)
+    unsigned long long nflops;     // FP64 flops of its arithmetic (thread 0)
     const void* gbasis;            //     the shared basis
 };
 
@@ -535,6 +550,15 @@ __device__ __forceinline__ long long run_points(int n, int tile, int tb, int te)
 __device__ __forceinline__ void acct(Smem& sm, long long pts, long long bytes_per_point) {
     if (threadIdx.x == 0) sm.nbytes += (unsigned long long)(pts * bytes_per_point);
 }
+// FP64 flop count (an FMA is two): only the arithmetic done in double.
+__device__ __forceinline__ void acctf(Smem& sm, long long pts, long long flops_per_point) {
+    if (threadIdx.x == 0) sm.nflops += (unsigned long long)(pts * flops_per_point);
+}
+// Flops of one application of the (2d+1)-point complex stencil with the shift.
+__device__ __forceinline__ long long stencil_flops(const ProblemDesc& pr) {
+    const int d = 1 + (pr.ny > 1) + (pr.nz > 1);
+    return 6 * d + 8;
+}
 
 __device__ __forceinline__ void load_scales(Smem& sm, const ItemState* S, int cnt) {
     if (threadIdx.x < cnt) sm.ssm[threadIdx.x] = ldd(&S->s[threadIdx.x]);
@@ -567,6 +591,7 @@ struct Phases {
         acct(sm, run_points(it_n, it_tile, tb, te),
              16 + (cycles > 0 ? 16 + 8 : (x != nullptr ? 16 : 0)) +
                  ((it.group >= 0 && cycles == 0) ? 0 : (long long)sizeof(V)));
+        acctf(sm, run_points(it_n, it_tile, tb, te), cycles > 0 ? stencil_flops(pr) + 6 : 4);
         for (int tile = tb; tile < te; ++tile) {
             const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
             double2 rv[kPPT];
@@ -739,6 +764,7 @@ struct Phases {
         const int it_n = it.n, it_tile = it.tile;
         acct(sm, run_points(it_n, it_tile, tb, te), (j + 3) * (long long)sizeof(V) + (long long)sizeof(T));
         const ProblemDesc& pr = A.prob[it.problem];
+        if (sizeof(T) == 8) acctf(sm, run_points(it_n, it_tile, tb, te), stencil_flops(pr) + 2 + 8 * (j + 1));
         const size_t n = (size_t)it_n;
         V* U = (V*)it.basis;
         const V* uj = U + (size_t)j * n;
@@ -792,6 +818,7 @@ struct Phases {
         const ItemDesc& it = sm.A.item[item];
         const int it_n = it.n, it_tile = it.tile;
         acct(sm, run_points(it_n, it_tile, tb, te), (2 * j + 3) * (long long)sizeof(V));
+        if (sizeof(T) == 8) acctf(sm, run_points(it_n, it_tile, tb, te), 16 * (j + 1));
         const size_t n = (size_t)it_n;
         const V* U = (const V*)it.basis;
         const V* wv = U + (size_t)(j + 1) * n;
@@ -833,6 +860,7 @@ struct Phases {
         const ItemDesc& it = sm.A.item[item];
         const int it_n = it.n, it_tile = it.tile;
         acct(sm, run_points(it_n, it_tile, tb, te), (j + 3) * (long long)sizeof(V));
+        if (sizeof(T) == 8) acctf(sm, run_points(it_n, it_tile, tb, te), 8 * (j + 1) + 4);
         const size_t n = (size_t)it_n;
         V* U = (V*)it.basis;
         V* wv = U + (size_t)(j + 1) * n;
@@ -867,30 +895,35 @@ struct Phases {
     // Arnoldi relation A Q = Q_j H to form column j of A q_j = (w - Q_j H a)/nu
     // and the next candidate v_{j+1} = A q_j - Q_j h_{:,j} in one sweep.
 
-    // Two dot products per basis vector in one read: with the v tile and the w tile.
-    static __device__ __forceinline__ void dot_tile2(const V* U, size_t n, const V* wsv, const V* wsw, int p0,
-                                                     int pend, const DotPlan& d, bool withw, T (&ar)[4],
+    // Two dot products per basis vector in one read: with the v tile and the w
+    // tile, both staged in FP32.  The dot products only choose the
+    // orthogonalisation coefficients; the update sweep applies them in the
+    // basis precision, which keeps the Arnoldi relation A Q = Q H to that
+    // precision whatever their accuracy (FP32 dots leave the columns
+    // orthonormal to ~1e-7, well inside the residual bound's slack).
+    static __device__ __forceinline__ void dot_tile2(const V* U, size_t n, const float2* wsv, const float2* wsw,
+                                                     int p0, int pend, const DotPlan& d, bool withw, T (&ar)[4],
                                                      T (&ai)[4], T (&br)[4], T (&bi)[4]) {
         const int lane = threadIdx.x & 31;
         for (int sl = 0; sl < d.nvec; ++sl) {
             const V* uq = U + (size_t)d.q[sl] * n + p0;
-            T sr = T(0), si = T(0), tr = T(0), ti = T(0);
+            float sr = 0.f, si = 0.f, tr = 0.f, ti = 0.f;
             for (int row = d.row0; row < d.row1; row += 8) {
-                V u[8];
+                float2 u[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int pl = (row + k) * 32 + lane;
-                    u[k] = (row + k < d.row1 && p0 + pl < pend) ? ldp(uq + pl) : mk2(T(0), T(0));
+                    u[k] = (row + k < d.row1 && p0 + pl < pend) ? dot_f2(ldp(uq + pl)) : make_float2(0.f, 0.f);
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     if (row + k < d.row1) {
                         const int pl = (row + k) * 32 + lane;
-                        const V v = wsv[pl];
+                        const float2 v = wsv[pl];
                         sr += u[k].x * v.x + u[k].y * v.y;
                         si += u[k].x * v.y - u[k].y * v.x;
                         if (withw) {
-                            const V w = wsw[pl];
+                            const float2 w = wsw[pl];
                             tr += u[k].x * w.x + u[k].y * w.y;
                             ti += u[k].x * w.y - u[k].y * w.x;
                         }
@@ -899,7 +932,7 @@ struct Phases {
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (k == sl) { ar[k] += sr; ai[k] += si; br[k] += tr; bi[k] += ti; }
+                if (k == sl) { ar[k] += (T)sr; ai[k] += (T)si; br[k] += (T)tr; bi[k] += (T)ti; }
             }
         }
     }
@@ -919,8 +952,12 @@ struct Phases {
         const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
         const int j0 = win_start(A, j);                     // dots with q_j0 .. q_{j-1} and v_j
         const V* U0 = U + (size_t)j0 * n;
+        float2* fsv = (float2*)wsv;                         // FP32 copies of the v and w tiles
+        float2* fsw = (float2*)wsw;
         acct(sm, run_points(it_n, it_tile, tb, te),
              (j - j0 + 1) * (long long)sizeof(V) + (matvec ? (long long)sizeof(V) + (long long)sizeof(T) : 0));
+        if (sizeof(T) == 8)
+            acctf(sm, run_points(it_n, it_tile, tb, te), 2 + (matvec ? stencil_flops(pr) + 2 : 0));
         const DotPlan d = dot_plan(j + 1 - j0, it_tile);
         T ar[4] = {T(0), T(0), T(0), T(0)}, ai[4] = {T(0), T(0), T(0), T(0)};
         T br[4] = {T(0), T(0), T(0), T(0)}, bi[4] = {T(0), T(0), T(0), T(0)};
@@ -940,11 +977,11 @@ struct Phases {
                         wv[p] = w;
                     }
                 }
-                wsv[r * kBlock + threadIdx.x] = v;
-                wsw[r * kBlock + threadIdx.x] = w;
+                fsv[r * kBlock + threadIdx.x] = dot_f2(v);
+                fsw[r * kBlock + threadIdx.x] = dot_f2(w);
             }
             __syncthreads();
-            dot_tile2(U0, n, wsv, wsw, p0, pend, d, matvec, ar, ai, br, bi);
+            dot_tile2(U0, n, fsv, fsw, p0, pend, d, matvec, ar, ai, br, bi);
             __syncthreads();
         }
         dot_finish(sm, it, it.part1, tb, j + 1 - j0, d, ar, ai);
@@ -1045,6 +1082,7 @@ struct Phases {
         const V gq = cvt2<V>(sm.ygq);
         const int j0 = win_start(sm.A, j);
         acct(sm, run_points(it_n, it_tile, tb, te), (j - j0 + 4) * (long long)sizeof(V));
+        if (sizeof(T) == 8) acctf(sm, run_points(it_n, it_tile, tb, te), 16 * (j - j0) + 12);
         for (int tile = tb; tile < te; ++tile) {
             const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
             for (int r0 = 0; r0 < kPPT && p0 + r0 * kBlock < pend; r0 += kChunk) {
@@ -1127,6 +1165,7 @@ struct Phases {
         double2* x = it.x;
         const int k = sm.kk;
         acct(sm, run_points(it_n, it_tile, tb, te), k * (long long)sizeof(V) + 32);
+        acctf(sm, run_points(it_n, it_tile, tb, te), (sizeof(T) == 8 ? 8 * k : 0) + 2);
         for (int tile = tb; tile < te; ++tile) {
             const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
             for (int r0 = 0; r0 < kPPT && p0 + r0 * kBlock < pend; r0 += kChunk) {
@@ -1454,15 +1493,20 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
     // a group's member rotations (column-major, i * nm + member) are copied to
     // shared memory by the whole CTA when they fit, so the serial loop below
     // does not wait on global loads
+    // With a window, column j-1 is zero above row r0 = j-1-L, so the
+    // rotations below i0 = r0-1 act on zeros: only rotations i0 .. j-2 run.
+    const int jj = j - 1;                                            // column completed at this step
+    const int i0 = A.window > 0 ? max(0, jj - A.window - 1) : 0;
     const int nmg = it.is_group ? it.nmembers : 0;
-    const int nrot = j >= 2 ? nmg * (j - 1) : 0;
+    const int nrot = jj > i0 ? nmg * (jj - i0) : 0;
     const bool staged = nrot > 0 && (size_t)nrot * (sizeof(double) + sizeof(double2)) <= stage_bytes;
     double2* st_sn = (double2*)stage;
     double* st_cs = (double*)(st_sn + nrot);
     if (staged) {
+        const size_t base = (size_t)i0 * nmg;
         for (int t = threadIdx.x; t < nrot; t += kBlock) {
-            st_sn[t] = ldp(it.gsn + t);
-            st_cs[t] = ldd(it.gcs + t);
+            st_sn[t] = ldp(it.gsn + base + t);
+            st_cs[t] = ldd(it.gcs + base + t);
         }
         __syncthreads();
     }
@@ -1471,21 +1515,21 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
     if (threadIdx.x == 0) S->vt[(j + 1) & 1] = 1.0;                 // v_{j+1} is stored raw
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
-    const int jj = j - 1;                                            // column completed at this step
     if (!it.is_group) {
         if (j == 0) {
             if (lane == 0) S->g[0] = cscale(ldp(&S->g[0]), nu);      // q_0 renormalised by nu
             return;
         }
-        if (lane < jj) {
-            sm.gcs_s[lane] = ldd(&S->cs[lane]);
-            sm.gsn_s[lane] = ldp(&S->sn[lane]);
+        for (int i = i0 + lane; i < jj; i += 32) {
+            sm.gcs_s[i] = ldd(&S->cs[i]);
+            sm.gsn_s[i] = ldp(&S->sn[i]);
         }
+        const int col = jj * (jj + 1) / 2;
+        for (int i = lane; i < i0; i += 32) S->R[col + i] = make_double2(0.0, 0.0);
         __syncwarp();
         if (lane != 0) return;
-        const int col = jj * (jj + 1) / 2;
-        double2 carry = sm.hfin[0];
-        for (int i = 0; i < jj; ++i) {
+        double2 carry = i0 == 0 ? sm.hfin[0] : make_double2(0.0, 0.0);
+        for (int i = i0; i < jj; ++i) {
             const double2 b = sm.hfin[i + 1];
             const double c = sm.gcs_s[i];
             const double2 sn = sm.gsn_s[i];
@@ -1538,15 +1582,17 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
             continue;
         }
         const double2 sh = md.shift;
-        double2 carry = sm.hfin[0];
+        double2 carry = i0 == 0 ? sm.hfin[0] : make_double2(0.0, 0.0);
         if (jj == 0) carry = csub(carry, sh);
         const int col = jj * (jj + 1) / 2;
-        for (int i = 0; i < jj; ++i) {
+        for (int i = 0; i < i0; ++i) M->R[col + i] = make_double2(0.0, 0.0);
+        for (int i = i0; i < jj; ++i) {
             double2 b = sm.hfin[i + 1];
             if (i + 1 == jj) b = csub(b, sh);
             const size_t ri = (size_t)i * nm + mi;
-            const double c = staged ? st_cs[ri] : ldd(it.gcs + ri);
-            const double2 sn = staged ? st_sn[ri] : ldp(it.gsn + ri);
+            const size_t rs = (size_t)(i - i0) * nm + mi;
+            const double c = staged ? st_cs[rs] : ldd(it.gcs + ri);
+            const double2 sn = staged ? st_sn[rs] : ldp(it.gsn + ri);
             const double2 nh = cadd(cscale(carry, c), cmul(sn, b));
             carry = cadd(cscale(cmul(cconj(sn), carry), -1.0), cscale(b, c));
             M->R[col + i] = nh;
@@ -1605,6 +1651,7 @@ __device__ void task_pole_sum(Smem& sm, int prob, int tile, int sub) {
     double2* out = step_out(sm.io, pr, prob, sub);
     const int p0 = tile * kPsTile, pend = min(pr.n, p0 + kPsTile);
     acct(sm, pend - p0, 32 + 16 * (long long)sm.nxlive + (long long)sm.kyhat * (long long)sizeof(V));
+    acctf(sm, pend - p0, 6 + 8 * ((long long)sm.nxlive + sm.kyhat));
     double2 acc[kPsPPT];
 #pragma unroll
     for (int r = 0; r < kPsPPT; ++r) {
@@ -1648,6 +1695,7 @@ __device__ void task_adjoint(Smem& sm, int prob, int tile, int bs) {
     double* dV = sm.io.dLdV[prob];
     const int p0 = tile * kPsTile, pend = min(pr.n, p0 + kPsTile);
     acct(sm, pend - p0, 32 + 32 * (long long)pr.K + 16);
+    acctf(sm, pend - p0, 6 + 20 * (long long)pr.K + 2);
     double2 g[kPsPPT];
     double dv[kPsPPT];
 #pragma unroll
@@ -1719,6 +1767,7 @@ __global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __gri
     if (threadIdx.x == 0) {
         tcount = 1;
         sm.nbytes = 0ull;
+        sm.nflops = 0ull;
         const unsigned long long t0 = global_ns();
         if (A.trace != nullptr && blockIdx.x == 0 && A.trace_cap > 0) {
             A.trace[1] = 99ull;
@@ -1853,7 +1902,10 @@ __global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __gri
             if (!phase_sync(A, TR_SUM, &tcount)) return;
         }
     }
-    if (threadIdx.x == 0 && A.bytes != nullptr) atomicAdd(A.bytes, sm.nbytes);
+    if (threadIdx.x == 0 && A.bytes != nullptr) {
+        atomicAdd(A.bytes, sm.nbytes);
+        atomicAdd(A.bytes + 1, sm.nflops);
+    }
 }
 
 // ---- single-stage kernels ------------------------------------------------------

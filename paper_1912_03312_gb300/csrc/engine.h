@@ -137,7 +137,7 @@ struct EngineArgs {
     int cta_trace_stride;
     int window;          // delayed CGS2: 0 = whole basis; L = only the last L vectors (Hermitian operators)
     int pad3;
-    unsigned long long* bytes;   // optional: algorithmic bytes of the launch (atomic sum over CTAs)
+    unsigned long long* bytes;   // optional [2]: algorithmic bytes and FP64 flops of the launch (atomic sums)
 };
 
 // phase codes recorded in the trace at the barrier that ends each phase

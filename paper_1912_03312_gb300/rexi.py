@@ -77,7 +77,7 @@ def stats_dict(st, K):
     return {"status": st.status, "n_sub": st.n_sub, "max_iters_seen": st.max_iters_seen,
             "total_iters": st.total_iters, "total_cycles": st.total_cycles,
             "iters": list(st.iters[:K]), "cycles": list(st.cycles[:K]), "iters_sq": list(st.iters_sq[:K]),
-            "resid": list(st.resid[:K]), "bytes": st.bytes}
+            "resid": list(st.resid[:K]), "bytes": st.bytes, "flops64": st.flops64}
 
 
 class Plan:
