@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tiles", default="",
+                    help="pole_tile,group_tile,ctas_per_sm to apply instead of autotuning (profiling runs)")
     ap.add_argument("--n", type=int, default=512,
                     help="grid side (512 = the benchmark workload; smaller sides are for profiling captures)")
     return ap.parse_args()
@@ -323,7 +325,12 @@ def ours(args):
     stream = torch.cuda.current_stream()
     psi0 = torch.from_numpy(cfg["psi0"]).to(dev)
     from paper_1912_03312_gb300 import autotune
-    tuned = autotune.autotune(plan, psi0) if not args.no_autotune else None
+    if args.tiles:
+        pt, gt, cps = (int(v) for v in args.tiles.split(","))
+        tuned = {"pole_tile": pt, "group_tile": gt, "ctas_per_sm": cps, "fixed": True}
+        autotune.apply(plan, tuned)
+    else:
+        tuned = autotune.autotune(plan, psi0) if not args.no_autotune else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     cur = psi0.clone()
