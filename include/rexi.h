@@ -278,7 +278,7 @@ int rexi_plan_last_status(rexi_plan* plan);
 
 /* Work decomposition of the plan's launches (the autotuner's knobs):
  * pole_tile / group_tile = points per task of pole items / shared-cycle group
- * items, each one of 256, 512, 1024, 2048; ctas_per_sm caps the resident CTAs
+ * items, each a multiple of 256 up to 2048; ctas_per_sm caps the resident CTAs
  * per SM of the persistent grid (0 = as many as fit).  Synchronises the device
  * and rewrites the plan's descriptors; results do not depend on these values
  * beyond floating-point summation order. */

@@ -22,8 +22,8 @@ from . import _native as N
 
 DEFAULT_CANDIDATES = {
     "pole_tile": (2048, 1024),
-    "group_tile": (512, 256, 1024, 2048),
-    "ctas_per_sm": (0, 2),
+    "group_tile": (512, 1024, 1536, 1792, 2048),
+    "ctas_per_sm": (0, 1, 2),
 }
 
 

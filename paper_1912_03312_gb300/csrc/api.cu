@@ -954,7 +954,7 @@ int rexi_plan_last_launches(const rexi_plan* p) { return p ? p->last_launches : 
 
 int rexi_plan_set_tiles(rexi_plan* p, int pole_tile, int group_tile, int ctas_per_sm) {
     if (!p) return REXI_EINVAL;
-    auto ok = [](int t) { return t == 256 || t == 512 || t == 1024 || t == 2048; };
+    auto ok = [](int t) { return t >= rexi::kBlock && t <= rexi::kTile && t % rexi::kBlock == 0; };
     if (!ok(pole_tile) || !ok(group_tile) || ctas_per_sm < 0 || ctas_per_sm > 32) return REXI_EINVAL;
     DeviceGuard guard(p->device);
     if (cudaDeviceSynchronize() != cudaSuccess) return REXI_ECUDA;

@@ -439,7 +439,10 @@ __device__ __forceinline__ const double2* item_rhs(int mode, const IOArgs& io, c
 // one item inside one CTA's share of the task range, at the slot of the run's
 // first tile.  The partition (T tasks split evenly over G CTAs) is the same in
 // every CTA, so a consumer can enumerate the run starts of an item itself.
-__device__ __forceinline__ int range_start(int c, int T, int G) { return (int)(((long long)c * T) / G); }
+__device__ __forceinline__ int range_start(int c, int T, int G) {
+    const unsigned long long prod = (unsigned long long)c * (unsigned)T;     // 32-bit division when it fits
+    return prod < (1ull << 32) ? (int)((unsigned)prod / (unsigned)G) : (int)(prod / (unsigned)G);
+}
 __device__ __forceinline__ int task_owner(int task, int T, int G) {
     return (int)((((long long)task + 1) * G - 1) / T);
 }
@@ -468,31 +471,43 @@ __device__ __forceinline__ Runs item_runs(const int* prefix, int l, int T) {
 }
 
 // out[i] = scale_i * sum over the runs of item slot l of part[run][i], i < nv (nv <= 32).
-// The CTA's threads split into nvp-wide groups (nvp = nv rounded up to a
-// power of two) that stride over the runs, so an item spread over hundreds of
-// CTAs costs a few rounds of independent loads, then a tree over the groups.
+// Each warp's lanes split into nvp-wide groups (nvp = nv rounded up to a power
+// of two) that stride over the runs; the groups are summed with shuffles and
+// the warps through shared memory (one block barrier).  AT is the accumulation
+// type: float where the partials are FP32 inner products (the one-reduction
+// Arnoldi), double otherwise.
+template <typename AT>
 __device__ void reduce_partials(Smem& sm, const double2* part, const ItemDesc& it, const Runs& R, int nv,
                                 const double* scale, double2* out) {
     int nvp = 1;
     while (nvp < nv) nvp <<= 1;
-    const int v = threadIdx.x & (nvp - 1), g = threadIdx.x / nvp, ng = kBlock / nvp;
-    double2 acc = make_double2(0.0, 0.0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v = lane & (nvp - 1), rl = lane / nvp, rpw = 32 / nvp;
+    AT ax = AT(0), ay = AT(0);
     if (v < nv) {
         const double2* pv = part + (size_t)it.tile_off * sm.A.pv + v;
 #pragma unroll 4
-        for (int r = g; r < R.count; r += ng) {
+        for (int r = warp * rpw + rl; r < R.count; r += rpw * kWarps) {
             const int tl = R.tile(r);
-            if (tl >= 0) acc = cadd(acc, ldp(pv + (size_t)tl * sm.A.pv));
+            if (tl >= 0) {
+                const double2 q = ldp(pv + (size_t)tl * sm.A.pv);
+                ax += (AT)q.x;
+                ay += (AT)q.y;
+            }
         }
     }
-    double2* red = &sm.red[0][0];              // kBlock entries
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int h = ng >> 1; h > 0; h >>= 1) {
-        if (g < h) red[threadIdx.x] = cadd(red[threadIdx.x], red[threadIdx.x + h * nvp]);
-        __syncthreads();
+    for (int off = nvp; off < 32; off <<= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, off);
+        ay += __shfl_xor_sync(0xffffffffu, ay, off);
     }
-    if (threadIdx.x < nv) out[threadIdx.x] = cscale(red[threadIdx.x], scale[threadIdx.x]);
+    if (rl == 0) sm.red[warp][v] = make_double2((double)ax, (double)ay);
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double2 s2 = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s2 = cadd(s2, sm.red[w][threadIdx.x]);
+        out[threadIdx.x] = cscale(s2, scale[threadIdx.x]);
+    }
     __syncthreads();
 }
 
@@ -518,11 +533,16 @@ __device__ __forceinline__ int win_start(const EngineArgs& A, int j) {
 __device__ __forceinline__ double res_bound(const EngineArgs& A, double res, int k) {
     return A.window > 0 ? res * sqrt((double)(k + 1)) : res;
 }
+// Its square from g_{k+1} (no square root on the per-step path).
+__device__ __forceinline__ double res2_bound(const EngineArgs& A, double2 g, int k) {
+    const double r2 = g.x * g.x + g.y * g.y;
+    return A.window > 0 ? r2 * (double)(k + 1) : r2;
+}
 
 // y = R^{-1} g for the packed upper triangle R (column l at l(l+1)/2) in
 // shared memory, k <= 64, by one warp: lane i holds rows i and i + 32 and the
 // columns are eliminated from the last; y lands in shared memory.
-__device__ void back_substitute(const double2* R, const double2* g, double2* y, int k) {
+__device__ void back_substitute(const double2* R, const double2* g, double2* y, int k, int win) {
     const int lane = threadIdx.x & 31;
     double2 a0 = lane < k ? g[lane] : make_double2(0.0, 0.0);
     double2 a1 = lane + 32 < k ? g[lane + 32] : make_double2(0.0, 0.0);
@@ -537,8 +557,9 @@ __device__ void back_substitute(const double2* R, const double2* g, double2* y, 
             y[l] = yl;
         }
         yl = shfl2(yl, l & 31);
-        if (lane < l) a0 = csub(a0, cmul(col[lane], yl));
-        if (lane + 32 < l) a1 = csub(a1, cmul(col[lane + 32], yl));
+        const int lo = win > 0 ? max(0, l - win - 1) : 0;   // a windowed column is zero above row lo
+        if (lane < l && lane >= lo) a0 = csub(a0, cmul(col[lane], yl));
+        if (lane + 32 < l && lane + 32 >= lo) a1 = csub(a1, cmul(col[lane + 32], yl));
     }
     __syncwarp();
 }
@@ -703,13 +724,14 @@ struct Phases {
     }
 
     // End of a run: partial dots of the warps' vectors into part[tb][0..J).
+    template <typename AT>
     static __device__ void dot_finish(Smem& sm, const ItemDesc& it, double2* part, int tb, int J,
-                                      const DotPlan& d, T (&ar)[4], T (&ai)[4]) {
+                                      const DotPlan& d, AT (&ar)[4], AT (&ai)[4]) {
         const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const T r = warp_sum(ar[k]);
-            const T i = warp_sum(ai[k]);
+            const AT r = warp_sum(ar[k]);
+            const AT i = warp_sum(ai[k]);
             if (lane == 0) sm.red[wp][k] = make_double2((double)r, (double)i);
         }
         __syncthreads();
@@ -804,7 +826,7 @@ struct Phases {
         const ItemDesc& it = sm.A.item[item];
         const int it_n = it.n, it_tile = it.tile;
         load_scales(sm, it.st, j + 1);
-        reduce_partials(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);
+        reduce_partials<double>(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);
         if (threadIdx.x <= j) {
             const double2 c = cscale(sm.h1[threadIdx.x], sm.ssm[threadIdx.x]);
             sm.coef[threadIdx.x] = c;
@@ -842,8 +864,8 @@ struct Phases {
         const ItemDesc& it = sm.A.item[item];
         const int it_n = it.n, it_tile = it.tile;
         load_scales(sm, it.st, j + 1);
-        reduce_partials(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);
-        reduce_partials(sm, it.part2, it, R, j + 1, sm.ssm, sm.h2);
+        reduce_partials<double>(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);
+        reduce_partials<double>(sm, it.part2, it, R, j + 1, sm.ssm, sm.h2);
         if (threadIdx.x <= j) {
             const double2 h = cadd(sm.h1[threadIdx.x], sm.h2[threadIdx.x]);
             sm.h1[threadIdx.x] = h;
@@ -902,8 +924,8 @@ struct Phases {
     // precision whatever their accuracy (FP32 dots leave the columns
     // orthonormal to ~1e-7, well inside the residual bound's slack).
     static __device__ __forceinline__ void dot_tile2(const V* U, size_t n, const float2* wsv, const float2* wsw,
-                                                     int p0, int pend, const DotPlan& d, bool withw, T (&ar)[4],
-                                                     T (&ai)[4], T (&br)[4], T (&bi)[4]) {
+                                                     int p0, int pend, const DotPlan& d, bool withw, float (&ar)[4],
+                                                     float (&ai)[4], float (&br)[4], float (&bi)[4]) {
         const int lane = threadIdx.x & 31;
         for (int sl = 0; sl < d.nvec; ++sl) {
             const V* uq = U + (size_t)d.q[sl] * n + p0;
@@ -932,7 +954,7 @@ struct Phases {
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (k == sl) { ar[k] += (T)sr; ai[k] += (T)si; br[k] += (T)tr; bi[k] += (T)ti; }
+                if (k == sl) { ar[k] += sr; ai[k] += si; br[k] += tr; bi[k] += ti; }
             }
         }
     }
@@ -959,8 +981,8 @@ struct Phases {
         if (sizeof(T) == 8)
             acctf(sm, run_points(it_n, it_tile, tb, te), 2 + (matvec ? stencil_flops(pr) + 2 : 0));
         const DotPlan d = dot_plan(j + 1 - j0, it_tile);
-        T ar[4] = {T(0), T(0), T(0), T(0)}, ai[4] = {T(0), T(0), T(0), T(0)};
-        T br[4] = {T(0), T(0), T(0), T(0)}, bi[4] = {T(0), T(0), T(0), T(0)};
+        float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};   // FP32 inner products
+        float br[4] = {0.f, 0.f, 0.f, 0.f}, bi[4] = {0.f, 0.f, 0.f, 0.f};
         for (int tile = tb; tile < te; ++tile) {
             const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
 #pragma unroll
@@ -1003,8 +1025,8 @@ struct Phases {
             }
         }
         __syncthreads();                                                   // q_i normalised; t_j
-        reduce_partials(sm, it.part1, it, R, j + 1 - j0, sm.ssm + j0, sm.h1 + j0);        // a_i, c
-        if (!last) reduce_partials(sm, it.part2, it, R, j + 1 - j0, sm.ssm + j0, sm.h2 + j0);   // b_i, d
+        reduce_partials<float>(sm, it.part1, it, R, j + 1 - j0, sm.ssm + j0, sm.h1 + j0);        // a_i, c
+        if (!last) reduce_partials<float>(sm, it.part2, it, R, j + 1 - j0, sm.ssm + j0, sm.h2 + j0);   // b_i, d
         double2* Hw = sm.scratch;                                          // columns j0..j-2, pitch kHld
         const int ncol = max(0, j - 1 - j0);
         for (int t = threadIdx.x; t < ncol * kHld; t += kBlock) {
@@ -1144,7 +1166,7 @@ struct Phases {
             sm.basis = src.basis;
         }
         __syncthreads();
-        if (threadIdx.x < 32) back_substitute(Rs, sm.gsm, sm.h2, k);      // y_i into h2
+        if (threadIdx.x < 32) back_substitute(Rs, sm.gsm, sm.h2, k, sm.A.window);   // y_i into h2
         __syncthreads();
         if (threadIdx.x < k) {
             const double2 c = cscale(sm.h2[threadIdx.x], sm.ssm[threadIdx.x]);
@@ -1382,10 +1404,12 @@ __device__ void member_direct_solve(const EngineArgs& A, int item) {
     double2 a1 = lane + 32 < k ? ldp(&M->g[lane + 32]) : make_double2(0.0, 0.0);
     double2 y0 = make_double2(0.0, 0.0), y1 = make_double2(0.0, 0.0);
     // column l of R for rows lane and lane + 32, the next column fetched ahead
+    // a windowed column l is zero above row l - L - 1 (those entries are not stored)
     auto col = [&](int l, double2& c0, double2& c1) {
         const double2* R = M->R + l * (l + 1) / 2;
-        c0 = (l >= 0 && lane <= l) ? ldp(R + lane) : make_double2(0.0, 0.0);
-        c1 = (l >= 0 && lane + 32 <= l) ? ldp(R + lane + 32) : make_double2(0.0, 0.0);
+        const int lo = A.window > 0 ? max(0, l - A.window - 1) : 0;
+        c0 = (l >= 0 && lane <= l && lane >= lo) ? ldp(R + lane) : make_double2(0.0, 0.0);
+        c1 = (l >= 0 && lane + 32 <= l && lane + 32 >= lo) ? ldp(R + lane + 32) : make_double2(0.0, 0.0);
     };
     double2 c0, c1, n0, n1;
     col(k - 1, c0, c1);
@@ -1482,6 +1506,27 @@ __device__ void group_p4(const EngineArgs& A, int gitem, const Runs& R, int j) {
     }
 }
 
+// Complex Givens rotation that zeroes h against the (real, >= 0) subdiagonal
+// hn: c = |a|/r, s = a hn/(|a| r), the new diagonal a r/|a| (a = carry,
+// r = sqrt(|a|^2 + hn^2)); two reciprocal square roots instead of two square
+// roots and three divisions.
+__device__ __forceinline__ void givens(double2 a, double hn, double* c, double2* s, double2* rjj, double* r) {
+    const double a2 = a.x * a.x + a.y * a.y;
+    const double r2 = a2 + hn * hn;
+    if (a2 == 0.0) {
+        *c = 0.0;
+        *s = make_double2(1.0, 0.0);
+        *rjj = make_double2(hn, 0.0);
+        *r = hn;
+        return;
+    }
+    const double ia = rsqrt(a2), ir = rsqrt(r2);
+    *c = a2 * ia * ir;                           // |a| / r
+    *s = cscale(a, hn * ia * ir);
+    *rjj = cscale(a, r2 * ir * ia);              // a r / |a|
+    *r = r2 * ir;
+}
+
 // Delayed CGS2, step j: the CTA owning tile 0 of the item stores the completed
 // column j-1 and the pending column j, and applies the Givens rotation of
 // column j-1 (one warp; for a group, lane = member with its shifted column).
@@ -1525,7 +1570,6 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
             sm.gsn_s[i] = ldp(&S->sn[i]);
         }
         const int col = jj * (jj + 1) / 2;
-        for (int i = lane; i < i0; i += 32) S->R[col + i] = make_double2(0.0, 0.0);
         __syncwarp();
         if (lane != 0) return;
         double2 carry = i0 == 0 ? sm.hfin[0] : make_double2(0.0, 0.0);
@@ -1538,19 +1582,9 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
             S->R[col + i] = nh;
         }
         const double hn = nu;
-        const double aa = sqrt(carry.x * carry.x + carry.y * carry.y);
-        const double rr = sqrt(aa * aa + hn * hn);
-        double c;
+        double c, rr;
         double2 sn, rjj;
-        if (aa == 0.0) {
-            c = 0.0;
-            sn = make_double2(1.0, 0.0);
-            rjj = make_double2(hn, 0.0);
-        } else {
-            c = aa / rr;
-            sn = cscale(carry, hn / (aa * rr));
-            rjj = cscale(carry, rr / aa);
-        }
+        givens(carry, hn, &c, &sn, &rjj, &rr);
         const double2 gj = ldp(&S->g[jj]);
         const double2 gj1 = cscale(cmul(cconj(sn), gj), -1.0);
         S->R[col + jj] = rjj;
@@ -1561,12 +1595,11 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
         S->k = j;
         const int total = ldi(&S->total_iters) + 1;
         S->total_iters = total;
-        const double res = res_bound(A, sqrt(gj1.x * gj1.x + gj1.y * gj1.y), j);
-        const bool end = !(res > ldd(&S->cycle_tol_abs)) || last || total >= A.max_iters || !(hn > 0.0) ||
-                         !(rr > 0.0);
+        const double tola = ldd(&S->cycle_tol_abs);
+        const bool end = !(res2_bound(A, gj1, j) > tola * tola) || last || total >= A.max_iters ||
+                         !(hn > 0.0) || !(rr > 0.0);
         if (end) S->sum_k2 = ldi(&S->sum_k2) + j * j;
-        __threadfence();
-        S->status = end ? ST_CYCLE_END : ST_ARNOLDI;
+        S->status = end ? ST_CYCLE_END : ST_ARNOLDI;     // published by the phase barrier
         return;
     }
     // group: members' rotations of their shifted copies of column jj
@@ -1585,7 +1618,6 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
         double2 carry = i0 == 0 ? sm.hfin[0] : make_double2(0.0, 0.0);
         if (jj == 0) carry = csub(carry, sh);
         const int col = jj * (jj + 1) / 2;
-        for (int i = 0; i < i0; ++i) M->R[col + i] = make_double2(0.0, 0.0);
         for (int i = i0; i < jj; ++i) {
             double2 b = sm.hfin[i + 1];
             if (i + 1 == jj) b = csub(b, sh);
@@ -1598,19 +1630,9 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
             M->R[col + i] = nh;
         }
         const double hn = nu;
-        const double aa = sqrt(carry.x * carry.x + carry.y * carry.y);
-        const double rr = sqrt(aa * aa + hn * hn);
-        double c;
+        double c, rr;
         double2 sn, rjj;
-        if (aa == 0.0) {
-            c = 0.0;
-            sn = make_double2(1.0, 0.0);
-            rjj = make_double2(hn, 0.0);
-        } else {
-            c = aa / rr;
-            sn = cscale(carry, hn / (aa * rr));
-            rjj = cscale(carry, rr / aa);
-        }
+        givens(carry, hn, &c, &sn, &rjj, &rr);
         const double2 gj = ldp(&M->g[jj]);
         const double2 gj1 = cscale(cmul(cconj(sn), gj), -1.0);
         it.gcs[(size_t)jj * nm + mi] = c;
@@ -1621,22 +1643,20 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
         M->k = j;
         const int total = ldi(&M->total_iters) + 1;
         M->total_iters = total;
-        const double res = res_bound(A, sqrt(gj1.x * gj1.x + gj1.y * gj1.y), j);
-        const bool end = !(res > ldd(&M->cycle_tol_abs)) || last || total >= A.max_iters || !(hn > 0.0) ||
-                         !(rr > 0.0);
+        const double res2 = res2_bound(A, gj1, j);
+        const double tola = ldd(&M->cycle_tol_abs);
+        const bool end = !(res2 > tola * tola) || last || total >= A.max_iters || !(hn > 0.0) || !(rr > 0.0);
         int stn = ST_SHARED;
         if (end) {
             M->sum_k2 = ldi(&M->sum_k2) + j * j;
-            stn = member_end_status(A, md, M, res, total);
+            stn = member_end_status(A, md, M, sqrt(res2), total);
         }
-        __threadfence();
-        M->status = stn;
+        M->status = stn;                                 // published by the phase barrier
         active = active || !end;
     }
     const bool any = __any_sync(0xffffffffu, active);
     if (lane == 0) {
         S->k = j;
-        __threadfence();
         S->status = (any && !last) ? ST_ARNOLDI : ST_IDLE;
     }
 }
@@ -1829,7 +1849,6 @@ __global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __gri
                     const int tb = t - prefix[l];
                     P::dy_pro(sm, list[l], item_runs(prefix, l, sm.ntasks), j, last);
                     if (tb == 0) dy_commit(A, sm, list[l], j, last, ws, 2 * kTile * sizeof(*ws));
-                    __syncthreads();
                     if (!last) P::dy(sm, list[l], tb, te, j);
                     t = prefix[l] + te;
                 }

@@ -72,7 +72,7 @@ struct ItemDesc {
     int tile_off;        // first tile of this item in the partial buffers
     int n;               // points of the item's problem
     int ntiles;          // tiles of this item (ceil(n / tile))
-    int tile;            // points per tile: kBlock * {1, 2, 4, 8}
+    int tile;            // points per tile: a multiple of kBlock, at most kTile
     double2 shift;       // A = stencil + diag - shift
     float2 shiftf;
     double2* x;          // c128 [n]

@@ -59,13 +59,19 @@ def test_batched_captured_in_cuda_graph():
     outs = [torch.empty_like(t) for t in ins]
     step_batched(plans, ins, outs)                  # builds the cached descriptor set
     torch.cuda.synchronize()
+    eager_b = [o.clone() for o in outs]
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         step_batched(plans, ins, outs)
+    for o in outs:
+        o.zero_()
     graph.replay()
     torch.cuda.synchronize()
-    for o, e in zip(outs, eager):
-        assert torch.equal(o, e)
+    for o, eb, e, lp in zip(outs, eager_b, eager, plans):
+        assert torch.equal(o, eb)                   # the replay is the batched launch, bit for bit
+        # against the single-problem launches: same solves, reductions split differently
+        A = lp.info()["amplification"]
+        assert relerr(o.cpu().numpy(), e.cpu().numpy()) < max(1e-6, 2.0 * A * 1e-12)
 
 
 def test_tile_settings_agree_and_autotune(tmp_path, monkeypatch):
@@ -76,10 +82,18 @@ def test_tile_settings_agree_and_autotune(tmp_path, monkeypatch):
     x = to_dev(psi)
     ref = lp.step(x).cpu().numpy()
     A = lp.info()["amplification"]
-    for pt, gt, c in [(256, 256, 1), (1024, 2048, 2), (2048, 512, 0)]:
+    for pt, gt, c in [(256, 256, 1), (1024, 2048, 2), (2048, 512, 0), (1792, 1536, 1), (768, 1280, 0)]:
         autotune.apply(lp, {"pole_tile": pt, "group_tile": gt, "ctas_per_sm": c})
         got = lp.step(x).cpu().numpy()
         assert relerr(got, ref) < max(1e-6, 2.0 * A * 1e-13)
+    # the FP64 windowed path (direct pole sum) under the same settings
+    lw = library_plan(g, V, 0.5, 16, 24.0, precision="fp64", tol=1e-13, window=2, restart=64)
+    refw = lw.step(x).cpu().numpy()
+    for pt, gt, c in [(1792, 1792, 1), (1024, 1536, 2), (256, 512, 0)]:
+        autotune.apply(lw, {"pole_tile": pt, "group_tile": gt, "ctas_per_sm": c})
+        assert relerr(lw.step(x).cpu().numpy(), refw) < max(1e-10, 2.0 * A * 1e-13)
+    with pytest.raises(Exception):
+        autotune.apply(lw, {"pole_tile": 300, "group_tile": 512, "ctas_per_sm": 0})   # not a multiple of 256
     cfg = autotune.autotune(lp, x, steps=1)
     assert not cfg["cached"] and cfg["ms"] > 0
     cfg2 = autotune.autotune(lp, x, steps=1)
