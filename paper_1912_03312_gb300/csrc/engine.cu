@@ -1092,8 +1092,9 @@ struct Phases {
         __syncthreads();
     }
 
-    // Y sweep: q_j into slot j, v_{j+1} into slot j+1.
-    static __device__ void dy(Smem& sm, int item, int tb, int te, int j) {
+    // Y sweep: q_j into slot j, v_{j+1} into slot j+1, by threads tid of nthr
+    // (the whole CTA, or warps 1.. while warp 0 applies the rotations).
+    static __device__ void dy(Smem& sm, int item, int tb, int te, int j, int tid, int nthr) {
         const ItemDesc& it = sm.A.item[item];
         const int it_n = it.n, it_tile = it.tile;
         const size_t n = (size_t)it_n;
@@ -1103,15 +1104,18 @@ struct Phases {
         const T tq = (T)sm.yscal[1], tw = (T)sm.yscal[2];
         const V gq = cvt2<V>(sm.ygq);
         const int j0 = win_start(sm.A, j);
-        acct(sm, run_points(it_n, it_tile, tb, te), (j - j0 + 4) * (long long)sizeof(V));
-        if (sizeof(T) == 8) acctf(sm, run_points(it_n, it_tile, tb, te), 16 * (j - j0) + 12);
+        if (tid == 0) {
+            sm.nbytes += (unsigned long long)(run_points(it_n, it_tile, tb, te) * ((j - j0 + 4) * (long long)sizeof(V)));
+            if (sizeof(T) == 8)
+                sm.nflops += (unsigned long long)(run_points(it_n, it_tile, tb, te) * (16 * (j - j0) + 12));
+        }
         for (int tile = tb; tile < te; ++tile) {
             const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
-            for (int r0 = 0; r0 < kPPT && p0 + r0 * kBlock < pend; r0 += kChunk) {
+            for (int base = p0; base < pend; base += nthr * kChunk) {
                 V qa[kChunk], va[kChunk];
 #pragma unroll
                 for (int r = 0; r < kChunk; ++r) {
-                    const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
+                    const int p = base + r * nthr + tid;
                     const V u = p < pend ? ldp(uj + p) : mk2(T(0), T(0));
                     const V w = p < pend ? ldp(wv + p) : mk2(T(0), T(0));
                     qa[r] = mk2(tq * u.x, tq * u.y);
@@ -1123,7 +1127,7 @@ struct Phases {
                     const V ca = coef_at<V>(sm, q), cg = coefg_at<V>(sm, q);
 #pragma unroll
                     for (int r = 0; r < kChunk; ++r) {
-                        const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
+                        const int p = base + r * nthr + tid;
                         const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
                         qa[r].x -= ca.x * u.x - ca.y * u.y;
                         qa[r].y -= ca.x * u.y + ca.y * u.x;
@@ -1133,7 +1137,7 @@ struct Phases {
                 }
 #pragma unroll
                 for (int r = 0; r < kChunk; ++r) {
-                    const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
+                    const int p = base + r * nthr + tid;
                     if (p < pend) {
                         va[r].x -= gq.x * qa[r].x - gq.y * qa[r].y;
                         va[r].y -= gq.x * qa[r].y + gq.y * qa[r].x;
@@ -1848,8 +1852,14 @@ __global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __gri
                     const int te = min(prefix[l + 1], e) - prefix[l];
                     const int tb = t - prefix[l];
                     P::dy_pro(sm, list[l], item_runs(prefix, l, sm.ntasks), j, last);
-                    if (tb == 0) dy_commit(A, sm, list[l], j, last, ws, 2 * kTile * sizeof(*ws));
-                    if (!last) P::dy(sm, list[l], tb, te, j);
+                    if (tb == 0) {
+                        // warp 0 applies the rotations while warps 1.. sweep this CTA's tiles
+                        dy_commit(A, sm, list[l], j, last, ws, 2 * kTile * sizeof(*ws));
+                        if (!last && threadIdx.x >= 32) P::dy(sm, list[l], tb, te, j, threadIdx.x - 32, kBlock - 32);
+                        __syncthreads();
+                    } else if (!last) {
+                        P::dy(sm, list[l], tb, te, j, threadIdx.x, kBlock);
+                    }
                     t = prefix[l] + te;
                 }
                 if (!phase_sync(A, TR_DY, &tcount)) return;
