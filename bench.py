@@ -425,6 +425,30 @@ def ours(args):
         if ref is None:                 # the timed path is the reference itself
             ref = out
         extra["rel_err_vs_fp64_full"] = float((out - ref).norm() / ref.norm())
+        # the Chebyshev propagator the paper compares with (Sec. 4), same operator
+        # and step, truncation 1e-10 (the FCF approximant's accuracy level)
+        cheb_out, deg = plan.cheb_step(psi0, tol=1e-10)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c = psi0.clone()
+        nxt2 = torch.empty_like(c)
+        tot = 0.0
+        for _ in range(3):
+            flush.zero_()
+            a.record(stream)
+            plan.cheb_step(c, out=nxt2, tol=1e-10)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+            c, nxt2 = nxt2, c
+        cb, cf = plan.last_work()
+        cms = tot / 3
+        paths["chebyshev"] = {"ms_per_step": cms, "steps_per_s": 1000.0 / cms, "degree": deg,
+                              "rel_diff_vs_fp64_full": float((cheb_out - ref).norm() / ref.norm()),
+                              "roofline": {"kernel": "cheb_kernel (one launch per step)",
+                                           "fp64_tflops": cf / (cms * 1e-3) / 1e12,
+                                           "fp64_frac_of_nominal": cf / (cms * 1e-3) / 1e12 / NOMINAL_FP64_TFLOPS,
+                                           "gbs": cb / (cms * 1e-3) / 1e9,
+                                           "hbm_frac_of_measured": cb / (cms * 1e-3) / 1e9 / peak}}
         extra["other_paths"] = paths
 
     # end to end through the C ABI with host buffers (copies inside the timed

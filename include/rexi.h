@@ -207,6 +207,21 @@ int rexi_step_host(rexi_plan* plan, const double* psi_in, double* psi_out, void*
  * persistent launch: all problems x all poles share the GPU.  All plans must
  * be on the same device and have the same precision, restart length and orthogonalisation.
  * psi_in[b], psi_out[b] : device c128 of plan b's size.  st: B entries or NULL. */
+/* The Chebyshev propagator the paper compares REXI with (Sec. 4): psi_out =
+ * p(Ht) psi_in with p(x) = sum_{k<=N} a_k T_k(x) approximating exp(-i R x) on
+ * [-1, 1], Ht = (H - c)/W on the plan's spectral enclosure, R = dt W / hbar,
+ * a_k = (2 - delta_k0)(-i)^k J_k(R) exp(-i dt c / hbar) (the Chebyshev
+ * coefficients Sec. 4 computes by FFT; here in closed form, Jacobi-Anger),
+ * evaluated by the Clenshaw recurrence in one persistent FP64 launch (one grid
+ * barrier per degree).  N is the smallest degree >= R with
+ * sum_{k>N} |a_k| <= tol (tol = 0: 1e-10), so |p - exp| <= tol on the
+ * spectrum; returned in *degree (may be NULL).  One user step dt of the plan,
+ * no substeps.  psi_in / psi_out: device c128 of the plan's size, may alias.
+ * Uses the plan's two state buffers; asynchronous like rexi_step (status of the
+ * bounded barriers via rexi_plan_last_status). */
+int rexi_cheb_step(rexi_plan* plan, const void* psi_in, void* psi_out, double tol, void* stream,
+                   int* degree);
+
 int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
                       void* const* psi_out, void* stream, rexi_stats* st);
 
@@ -309,6 +324,11 @@ int rexi_plan_read_trace(rexi_plan* plan, long long* out, int cap);
  * the barrier's release as seen by CTA 0. */
 int rexi_plan_set_cta_trace(rexi_plan* plan, int phases);
 int rexi_plan_read_cta_trace(rexi_plan* plan, long long* out, int cap, int* grid);
+
+/* Kernel-counted algorithmic bytes and FP64 flops of the plan's last launch
+ * (engine or Chebyshev; the same counts rexi_stats reports).  Synchronises the
+ * plan's last stream. */
+int rexi_plan_last_work(rexi_plan* plan, double* bytes, double* flops64);
 
 /* Number of CUDA kernel launches issued by the last call on the plan. */
 int rexi_plan_last_launches(const rexi_plan* plan);

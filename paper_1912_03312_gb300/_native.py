@@ -82,6 +82,8 @@ SIGNATURES = {
     "rexi_plan_set_tiles": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "rexi_plan_read_trace": (C.c_int, [_P, C.POINTER(C.c_longlong), C.c_int]),
     "rexi_plan_set_cta_trace": (C.c_int, [_P, C.c_int]),
+    "rexi_cheb_step": (C.c_int, [_P, _P, _P, C.c_double, _P, C.POINTER(C.c_int)]),
+    "rexi_plan_last_work": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "rexi_plan_read_cta_trace": (C.c_int, [_P, C.POINTER(C.c_longlong), C.c_int, C.POINTER(C.c_int)]),
     "rexi_status_string": (C.c_char_p, [C.c_int]),
     "rexi_substep_static": (C.c_int, [C.POINTER(Grid), _P, C.c_double, C.c_double, C.c_int, _D, _D, _D,

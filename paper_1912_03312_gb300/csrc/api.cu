@@ -75,6 +75,8 @@ struct rexi_plan {
     unsigned* d_bar = nullptr;
     int* d_err = nullptr;
     unsigned long long* d_bytes = nullptr;       // [2] algorithmic bytes and FP64 flops of the last launch
+    double2* d_cheb = nullptr;                   // Chebyshev coefficients (rexi_cheb_step)
+    int cheb_cap = 0;
     int nit_cap = 0;                             // pole items with workspace (K or 2K)
     int ngroups = 0;                             // shared-cycle group items (0, 1 or 2)
     bool shared = true;
@@ -724,6 +726,83 @@ int rexi_step(rexi_plan* p, const void* psi_in, void* psi_out, void* stream, rex
     if (r) return p->last_status = r;
     if (!st) return p->last_status = REXI_OK;
     return p->last_status = collect(p, s, p->K, 0, p->K, st, p->n_sub);
+}
+
+int rexi_cheb_step(rexi_plan* p, const void* psi_in, void* psi_out, double tol, void* stream, int* degree) {
+    if (!p || !psi_in || !psi_out) return REXI_EINVAL;
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return REXI_EINVAL;
+    if (tol == 0.0) tol = 1e-10;
+    const double hbar = p->grid.hbar;
+    const double R = p->dt * p->W / hbar;
+    if (!(p->W > 0.0) || !(p->tau > 0.0) || !std::isfinite(R) || R > 1e6) return REXI_EINVAL;
+    // degree: smallest N >= ceil(R) with sum_{k > N} |a_k| <= tol, |a_k| = 2 |J_k(R)|
+    const int Lmax = (int)std::ceil(R) + 400;
+    const std::vector<double> J = rexi::bessel_j(Lmax, R);
+    std::vector<double> tail(Lmax + 2, 0.0);
+    for (int k = Lmax; k >= 0; --k) tail[k] = tail[k + 1] + 2.0 * std::fabs(J[k]);
+    int N = -1;
+    for (int k = (int)std::ceil(R); k < Lmax; ++k)
+        if (tail[k + 1] <= tol) { N = k; break; }
+    if (N < 0) return REXI_EINVAL;
+    // a_k = (2 - delta_k0) (-i)^k J_k(R), times exp(-i dt c / hbar) (centring)
+    const std::complex<double> ph = std::exp(std::complex<double>(0.0, -p->dt * p->c / hbar));
+    std::vector<double2> coef(N + 1);
+    const std::complex<double> mi(0.0, -1.0);
+    std::complex<double> ik(1.0, 0.0);
+    for (int k = 0; k <= N; ++k) {
+        const std::complex<double> a = (k == 0 ? 1.0 : 2.0) * ik * J[k] * ph;
+        coef[k] = make_double2(a.real(), a.imag());
+        ik *= mi;
+    }
+    DeviceGuard guard(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (N + 1 > p->cheb_cap) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return REXI_ECUDA;
+        int r = dalloc(p, &p->d_cheb, (size_t)N + 1);
+        if (r) return r;
+        p->cheb_cap = N + 1;
+    }
+    cudaError_t e = cudaMemcpyAsync(p->d_cheb, coef.data(), sizeof(double2) * (N + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bar, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return p->last_status = cuda_fail(e);
+    rexi::ChebArgs a{};
+    a.prob = p->fwd.d_prob;
+    a.psi = (const double2*)psi_in;
+    a.out = (double2*)psi_out;
+    a.b1 = p->d_tmp0;
+    a.b2 = p->d_tmp1;
+    a.coef = p->d_cheb;
+    a.N = N;
+    a.n = p->n;
+    a.scale = 1.0 / (p->tau * p->W);
+    a.bar = p->d_bar;
+    a.err = p->d_err;
+    a.timeout_ns = kTimeoutNs;
+    a.counters = p->d_bytes;
+    const int maxg = rexi::cheb_max_grid(p->device);
+    if (maxg <= 0) return p->last_status = REXI_ECUDA;
+    const int grid = std::max(1, std::min(maxg, (p->n + rexi::kBlock - 1) / rexi::kBlock));
+    e = rexi::launch_cheb(a, grid, s);
+    p->last_stream = s;
+    p->last_launches = 1;
+    p->last_grid = grid;
+    if (e != cudaSuccess) return p->last_status = cuda_fail(e);
+    if (degree) *degree = N;
+    return p->last_status = REXI_OK;
+}
+
+int rexi_plan_last_work(rexi_plan* p, double* bytes, double* flops64) {
+    if (!p) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    unsigned long long c[2] = {0, 0};
+    if (cudaMemcpyAsync(c, p->d_bytes, sizeof(c), cudaMemcpyDeviceToHost, p->last_stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->last_stream) != cudaSuccess)
+        return REXI_ECUDA;
+    if (bytes) *bytes = (double)c[0];
+    if (flops64) *flops64 = (double)c[1];
+    return REXI_OK;
 }
 
 int rexi_step_host(rexi_plan* p, const double* psi_in, double* psi_out, void* stream, rexi_stats* st) {

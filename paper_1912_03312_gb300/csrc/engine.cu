@@ -1937,6 +1937,63 @@ __global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __gri
     }
 }
 
+// ---- Chebyshev propagator (Sec. 4's comparison method) ---------------------------
+//
+// Clenshaw: b_{N+1} = b_{N+2} = 0, b_k = a_k u + 2 Ht b_{k+1} - b_{k+2}
+// (k = N .. 1), out = a_0 u + Ht b_1 - b_2.  One grid barrier per degree: the
+// stencil of b_{k+1} reads neighbours other CTAs wrote; b_k overwrites
+// b_{k+2} in place (each point reads its own b_{k+2} only).
+
+__global__ void __launch_bounds__(kBlock) cheb_kernel(const __grid_constant__ ChebArgs a) {
+    const ProblemDesc& pr = *a.prob;
+    const double* diag = pr.diag;
+    const double a0 = pr.a[0], a1 = pr.a[1], a2 = pr.a[2];
+    const double2 zero = make_double2(0.0, 0.0);
+    const int gt = blockIdx.x * kBlock + threadIdx.x, gs = gridDim.x * kBlock;
+    const int N = a.N, n = a.n;
+    double2* X = a.b1;                       // b_{k+1}
+    double2* Y = a.b2;                       // b_{k+2}, overwritten by b_k
+    const double2 cN = __ldg(a.coef + N);
+    for (int p = gt; p < n; p += gs) {
+        X[p] = N > 0 ? cmul(cN, ldp(a.psi + p)) : zero;     // b_N (or 0 when N = 0)
+        Y[p] = zero;                                        // b_{N+1}
+    }
+    if (!grid_sync(a.bar, a.err, a.timeout_ns)) return;
+    const double s2 = 2.0 * a.scale;
+    for (int k = N - 1; k >= 1; --k) {
+        const double2 ck = __ldg(a.coef + k);
+        for (int p = gt; p < n; p += gs) {
+            const double2 h = stencil_apply<double, double2>(X, p, pr, diag, a0, a1, a2, zero);
+            const double2 u = ldp(a.psi + p);
+            const double2 y = ldp(Y + p);
+            const double2 au = cmul(ck, u);
+            Y[p] = make_double2(au.x + s2 * h.x - y.x, au.y + s2 * h.y - y.y);
+        }
+        double2* t = X;
+        X = Y;
+        Y = t;
+        if (!grid_sync(a.bar, a.err, a.timeout_ns)) return;
+    }
+    const double2 c0 = __ldg(a.coef);
+    for (int p = gt; p < n; p += gs) {
+        const double2 u = ldp(a.psi + p);
+        double2 r = cmul(c0, u);
+        if (N > 0) {
+            const double2 h = stencil_apply<double, double2>(X, p, pr, diag, a0, a1, a2, zero);
+            const double2 y = ldp(Y + p);
+            r = make_double2(r.x + a.scale * h.x - y.x, r.y + a.scale * h.y - y.y);
+        }
+        a.out[p] = r;
+    }
+    if (a.counters != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int d = 1 + (pr.ny > 1) + (pr.nz > 1);
+        const unsigned long long nn = (unsigned long long)n;
+        // per degree: read b_{k+1} (stencil), u, b_{k+2} and the diagonal, write b_k
+        atomicAdd(a.counters, nn * (16ull * 4 + 8ull) * (unsigned long long)(N > 0 ? N : 1) + nn * 32ull);
+        atomicAdd(a.counters + 1, nn * (unsigned long long)(6 * d + 20) * (unsigned long long)(N > 0 ? N : 1));
+    }
+}
+
 // ---- single-stage kernels ------------------------------------------------------
 
 // w_k = A_k v_k for all poles (FP64): grid (ceil(n / kBlock), K).
@@ -2008,6 +2065,18 @@ cudaError_t launch_pole_sum(const ProblemDesc* dprob, const double2* psi, const 
                             int n, int K, cudaStream_t stream) {
     pole_sum_kernel<<<(n + kBlock - 1) / kBlock, kBlock, 0, stream>>>(dprob, psi, x, out, n, K);
     return cudaGetLastError();
+}
+
+cudaError_t launch_cheb(const ChebArgs& args, int grid, cudaStream_t stream) {
+    void* params[] = {(void*)&args};
+    return cudaLaunchCooperativeKernel((const void*)cheb_kernel, dim3(grid), dim3(kBlock), params, 0, stream);
+}
+
+int cheb_max_grid(int device) {
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cheb_kernel, kBlock, 0) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1;
+    return per_sm * sms;
 }
 
 }  // namespace rexi

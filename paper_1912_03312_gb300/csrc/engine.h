@@ -144,6 +144,27 @@ struct EngineArgs {
 enum : int { TR_INIT = 0, TR_E3 = 1, TR_E4 = 2, TR_P1 = 3, TR_P2 = 4, TR_P3 = 5, TR_P4 = 6, TR_E2 = 7,
              TR_SUM = 8, TR_DX = 9, TR_DY = 10 };
 
+// Chebyshev propagator of the comparison method of Sec. 4, evaluated with the
+// Clenshaw recurrence on the plan's FP64 operator B = tau (H - c):
+// Ht = scale B has its spectrum in [-1, 1]; out = sum_k coef_k T_k(Ht) psi.
+struct ChebArgs {
+    const ProblemDesc* prob;     // the plan's problem descriptor (stencil of B, FP64 diagonal)
+    const double2* psi;          // input, [n]
+    double2* out;                // result, [n] (may alias psi)
+    double2* b1;                 // Clenshaw buffers, [n] each
+    double2* b2;
+    const double2* coef;         // [N + 1]: a_k exp(-i dt c / hbar)
+    int N;
+    int n;
+    double scale;                // 1 / (tau W)
+    unsigned* bar;               // [2] grid barrier
+    int* err;
+    unsigned long long timeout_ns;
+    unsigned long long* counters;   // optional [2]: algorithmic bytes, FP64 flops
+};
+cudaError_t launch_cheb(const ChebArgs& args, int grid, cudaStream_t stream);
+int cheb_max_grid(int device);   // co-resident CTAs of the Chebyshev kernel (<= 0: error)
+
 // Launch the persistent kernel; T = float (mixed) or double (fp64).
 cudaError_t launch_engine(bool fp32_basis, const EngineArgs& args, const IOArgs& io, int grid,
                           size_t smem, cudaStream_t stream);

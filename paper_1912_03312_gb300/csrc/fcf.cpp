@@ -413,4 +413,11 @@ double fcf_default_R1_cached(int K, double eps_target) {
     return R;
 }
 
+std::vector<double> bessel_j(int L, double R) {
+    std::vector<dd> j = bessel_miller<dd>(L, R);
+    std::vector<double> out(L + 1);
+    for (int i = 0; i <= L; ++i) out[i] = (double)j[i];
+    return out;
+}
+
 }  // namespace rexi

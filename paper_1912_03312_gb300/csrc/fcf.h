@@ -26,5 +26,7 @@ int fcf_cached(int K, double R1, FcfResult* out);
 // Largest R1 (floored to an integer when >= 2) with 2 sigma_{K+1}(R1) <= eps_target.
 double fcf_default_R1(int K, double eps_target);
 double fcf_default_R1_cached(int K, double eps_target);
+// J_0(R) .. J_L(R) (Miller's backward recurrence in double-double, rounded).
+std::vector<double> bessel_j(int L, double R);
 
 }  // namespace rexi

@@ -180,6 +180,18 @@ class Plan:
         N.check(rc, "rexi_step_host")
         return dst
 
+    def cheb_step(self, psi, out=None, tol=0.0, stream=None):
+        """One step dt by the Chebyshev propagator of Sec. 4 (``rexi_cheb_step``):
+        returns (out, degree)."""
+        _check_state(psi, self.n, "psi")
+        if out is None:
+            out = torch.empty_like(psi)
+        _check_state(out, self.n, "out")
+        deg = C.c_int(0)
+        N.check(N.load().rexi_cheb_step(self._h, _ptr(psi), _ptr(out), float(tol), _stream_handle(stream),
+                                        C.byref(deg)), "rexi_cheb_step")
+        return out, deg.value
+
     def solve_poles(self, b, stream=None, stats=False):
         """x_k = (tau H - z_k)^{-1} b for every pole: (K, *shape) complex128."""
         _check_state(b, self.n, "b")
@@ -222,6 +234,12 @@ class Plan:
 
     def last_status(self):
         return N.load().rexi_plan_last_status(self._h)
+
+    def last_work(self):
+        """(bytes, FP64 flops) the last launch counted (``rexi_plan_last_work``)."""
+        b, f = C.c_double(0.0), C.c_double(0.0)
+        N.check(N.load().rexi_plan_last_work(self._h, C.byref(b), C.byref(f)), "rexi_plan_last_work")
+        return b.value, f.value
 
     def last_launches(self):
         return N.load().rexi_plan_last_launches(self._h)
