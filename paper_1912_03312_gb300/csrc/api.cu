@@ -364,6 +364,7 @@ EngineArgs base_args(const rexi_plan* p, int mode, const DescSet& set, int nprob
     A.prob = set.d_prob;
     A.item = set.d_items;
     A.bar = p->d_bar;
+    A.epoch = p->d_bar + 2;
     A.err = p->d_err;
     A.bytes = p->d_bytes;
     A.trace = p->trace_cap > 0 ? p->d_trace : nullptr;
@@ -399,7 +400,7 @@ int sm_count(int device) {
 }
 
 int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles, cudaStream_t stream) {
-    cudaError_t e = cudaMemsetAsync(p->d_bar, 0, 2 * sizeof(unsigned), stream);
+    cudaError_t e = cudaMemsetAsync(p->d_bar, 0, 3 * sizeof(unsigned), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, 2 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stats, 0, sizeof(ItemStats) * A.nitems, stream);
@@ -617,7 +618,7 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     if ((st = dalloc(p, &p->d_tmp1, n))) return fail(st);
     if ((st = dalloc(p, &p->d_hin, n))) return fail(st);
     if ((st = dalloc(p, &p->d_hout, n))) return fail(st);
-    if ((st = dalloc(p, &p->d_bar, 2))) return fail(st);
+    if ((st = dalloc(p, &p->d_bar, 4))) return fail(st);
     if ((st = dalloc(p, &p->d_err, 1))) return fail(st);
     if ((st = dalloc(p, &p->d_bytes, 2))) return fail(st);
     {
@@ -627,7 +628,7 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
             return fail(REXI_ECUDA);
     }
     if ((st = upload_diag(p, 0, true))) return fail(st);
-    if (cudaMemset(p->d_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess) return fail(REXI_ECUDA);
+    if (cudaMemset(p->d_bar, 0, 4 * sizeof(unsigned)) != cudaSuccess) return fail(REXI_ECUDA);
     if (cudaMemset(p->d_err, 0, sizeof(int)) != cudaSuccess) return fail(REXI_ECUDA);
     if (opt.want_backward) {
         if ((st = alloc_items(p, 2 * K))) return fail(st);
@@ -962,7 +963,7 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
         if (cudaMemsetAsync(plans[b]->d_stats, 0, sizeof(ItemStats) * (plans[b]->K + plans[b]->ngroups), s) !=
             cudaSuccess)
             return REXI_ECUDA;
-    cudaError_t e = cudaMemsetAsync(p0->d_bar, 0, 2 * sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(p0->d_bar, 0, 3 * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_bytes, 0, 2 * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_stats, 0, sizeof(ItemStats) * (p0->K + p0->ngroups), s);

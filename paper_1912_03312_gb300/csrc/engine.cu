@@ -220,6 +220,8 @@ struct Smem {
     int nl;
     int ntasks;
     int kk;                        // Arnoldi steps of the current item (E2)
+    bool xassign;                  // E2 writes x instead of adding (first update after a shared cycle)
+    unsigned ep_now, ep_seen;      // Arnoldi-list epoch (delayed CGS2 loop)
     const void* basis;             // basis the current item's E2 reads
     double2* scratch;              // dynamic shared memory aliased with the staging tiles:
                                    // R (E2) or Hessenberg columns (Y), kScratch entries
@@ -274,7 +276,16 @@ __device__ __forceinline__ double cta_reduce_scalar(Smem& sm, double v) {
 // List (in shared memory) of the items whose status bit is set in `mask`, and
 // the prefix sums of their tile counts.  Identical in every CTA: statuses are
 // read after a grid barrier and only changed in per-item phases.
-__device__ void build_list(Smem& sm, int* list, int* prefix, unsigned mask) {
+// Tasks an item of the list gets: its tiles, or none for a pole starting its
+// shared first cycle in a step launch when `e3` is set (its residual is b; the
+// group item does the work and E4 reads the norm there).
+__device__ __forceinline__ int list_tiles(const EngineArgs& A, int i, int s, bool e3) {
+    const ItemDesc& it = A.item[i];
+    if (e3 && s == ST_NEED_RES && A.mode == MODE_STEP && it.group >= 0 && ldi(&it.st->cycles) == 0) return 0;
+    return it.ntiles;
+}
+
+__device__ void build_list(Smem& sm, int* list, int* prefix, unsigned mask, bool e3 = false) {
     const EngineArgs& A = sm.A;
     const int nit = A.nitems;
     const int per = (nit + kBlock - 1) / kBlock;
@@ -283,7 +294,7 @@ __device__ void build_list(Smem& sm, int* list, int* prefix, unsigned mask) {
     int c = 0, t = 0;
     for (int i = i0; i < i1; ++i) {
         const int s = ldi(&A.item[i].st->status);
-        if (mask & (1u << s)) { ++c; t += A.item[i].ntiles; }
+        if (mask & (1u << s)) { ++c; t += list_tiles(A, i, s, e3); }
     }
     sm.cnt[threadIdx.x] = c;
     sm.tls[threadIdx.x] = t;
@@ -310,7 +321,7 @@ __device__ void build_list(Smem& sm, int* list, int* prefix, unsigned mask) {
             list[c] = i;
             prefix[c] = t;
             ++c;
-            t += A.item[i].ntiles;
+            t += list_tiles(A, i, s, e3);
         }
     }
     __syncthreads();
@@ -374,6 +385,33 @@ __device__ __forceinline__ Nb neighbours(int p, int nx, int ny, int nz) {
 // (A u)_p = sum_d a_d (u_{p+e_d} + u_{p-e_d}) + (diag_p - shift) u_p in precision
 // T: the periodic second-order Laplacian of tau H with the diagonal tau (V - c)
 // and the pole shift fused.
+// t A u at point p with the scale t folded into the coefficients (at = t a_d,
+// st = t shift): sum_d at_d (u_{p+e_d} + u_{p-e_d}) + (t diag_p - st) u_p.
+template <typename T, typename V>
+__device__ __forceinline__ V stencil_scaled(const V* __restrict__ u, int p, const ProblemDesc& pr,
+                                            const T* __restrict__ diag, T t, T a0t, T a1t, T a2t, V st, V c) {
+    const Nb b = neighbours(p, pr.nx, pr.ny, pr.nz);
+    V s;
+    {
+        const V l = ldp(u + b.xm), r = ldp(u + b.xp);
+        s = mk2(a0t * (l.x + r.x), a0t * (l.y + r.y));
+    }
+    if (pr.ny > 1) {
+        const V l = ldp(u + b.ym), r = ldp(u + b.yp);
+        s.x += a1t * (l.x + r.x);
+        s.y += a1t * (l.y + r.y);
+    }
+    if (pr.nz > 1) {
+        const V l = ldp(u + b.zm), r = ldp(u + b.zp);
+        s.x += a2t * (l.x + r.x);
+        s.y += a2t * (l.y + r.y);
+    }
+    const T dd = __ldg(diag + p) * t - st.x;
+    s.x += dd * c.x + st.y * c.y;
+    s.y += dd * c.y - st.y * c.x;
+    return s;
+}
+
 template <typename T, typename V>
 __device__ __forceinline__ V stencil_apply(const V* __restrict__ u, int p, const ProblemDesc& pr,
                                            const T* __restrict__ diag, const T a0, const T a1,
@@ -605,12 +643,15 @@ struct Phases {
         const int it_n = it.n, it_tile = it.tile;
         const ProblemDesc& pr = A.prob[it.problem];
         const int cycles = ldi(&it.st->cycles);
+        // a pole starting its shared first cycle in a step launch: its residual is b,
+        // whose norm the group item computes (E4 reads it there)
+        if (cycles == 0 && A.mode == MODE_STEP && it.group >= 0) return;
         const double2* b = item_rhs(A.mode, sm.io, it, pr, sub);
         V* U = (V*)it.basis;
         double2* x = it.x;
         double acc = 0.0;
         acct(sm, run_points(it_n, it_tile, tb, te),
-             16 + (cycles > 0 ? 16 + 8 : (x != nullptr ? 16 : 0)) +
+             16 + (cycles > 0 ? 16 + 8 : (x != nullptr && !(A.mode == MODE_STEP && it.group >= 0) ? 16 : 0)) +
                  ((it.group >= 0 && cycles == 0) ? 0 : (long long)sizeof(V)));
         acctf(sm, run_points(it_n, it_tile, tb, te), cycles > 0 ? stencil_flops(pr) + 6 : 4);
         for (int tile = tb; tile < te; ++tile) {
@@ -622,7 +663,9 @@ struct Phases {
                 rv[r] = p < pend ? ldp(b + p) : make_double2(0.0, 0.0);
             }
             if (cycles == 0) {
-                if (x != nullptr) {
+                // x0 = 0; in a step launch a pole on a shared first cycle gets x assigned by its
+                // first update, or never reads it (finished on the shared basis, or b = 0)
+                if (x != nullptr && !(A.mode == MODE_STEP && it.group >= 0)) {
 #pragma unroll
                     for (int r = 0; r < kPPT; ++r) {
                         const int p = p0 + r * kBlock + threadIdx.x;
@@ -974,12 +1017,15 @@ struct Phases {
         const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
         const int j0 = win_start(A, j);                     // dots with q_j0 .. q_{j-1} and v_j
         const V* U0 = U + (size_t)j0 * n;
+        const T a0t = a0 * tj, a1t = a1 * tj, a2t = a2 * tj;   // t_j folded into the stencil
+        const V sht = mk2(shift.x * tj, shift.y * tj);
+        const float tjf = (float)tj;
         float2* fsv = (float2*)wsv;                         // FP32 copies of the v and w tiles
         float2* fsw = (float2*)wsw;
         acct(sm, run_points(it_n, it_tile, tb, te),
              (j - j0 + 1) * (long long)sizeof(V) + (matvec ? (long long)sizeof(V) + (long long)sizeof(T) : 0));
         if (sizeof(T) == 8)
-            acctf(sm, run_points(it_n, it_tile, tb, te), 2 + (matvec ? stencil_flops(pr) + 2 : 0));
+            acctf(sm, run_points(it_n, it_tile, tb, te), matvec ? stencil_flops(pr) : 0);
         const DotPlan d = dot_plan(j + 1 - j0, it_tile);
         float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};   // FP32 inner products
         float br[4] = {0.f, 0.f, 0.f, 0.f}, bi[4] = {0.f, 0.f, 0.f, 0.f};
@@ -988,18 +1034,18 @@ struct Phases {
 #pragma unroll
             for (int r = 0; r < kPPT; ++r) {
                 const int p = p0 + r * kBlock + threadIdx.x;
-                V v = mk2(T(0), T(0)), w = mk2(T(0), T(0));
+                float2 vf = make_float2(0.f, 0.f);
+                V w = mk2(T(0), T(0));
                 if (p < pend) {
                     const V u = ldp(uj + p);
-                    v = mk2(tj * u.x, tj * u.y);
+                    const float2 uf = dot_f2(u);
+                    vf = make_float2(tjf * uf.x, tjf * uf.y);      // v_j = t_j u_j, only its FP32 copy is needed
                     if (matvec) {
-                        w = stencil_apply<T, V>(uj, p, pr, diag, a0, a1, a2, shift);
-                        w.x *= tj;
-                        w.y *= tj;
+                        w = stencil_scaled<T, V>(uj, p, pr, diag, tj, a0t, a1t, a2t, sht, u);
                         wv[p] = w;
                     }
                 }
-                fsv[r * kBlock + threadIdx.x] = dot_f2(v);
+                fsv[r * kBlock + threadIdx.x] = vf;
                 fsw[r * kBlock + threadIdx.x] = dot_f2(w);
             }
             __syncthreads();
@@ -1168,6 +1214,7 @@ struct Phases {
         if (threadIdx.x == 0) {
             sm.kk = k;
             sm.basis = src.basis;
+            sm.xassign = shared && ldi(&S->cycles) == 1;
         }
         __syncthreads();
         if (threadIdx.x < 32) back_substitute(Rs, sm.gsm, sm.h2, k, sm.A.window);   // y_i into h2
@@ -1190,6 +1237,7 @@ struct Phases {
         const V* U = (const V*)sm.basis;
         double2* x = it.x;
         const int k = sm.kk;
+        const bool assign = sm.xassign;                     // x not yet written (shared first cycle)
         acct(sm, run_points(it_n, it_tile, tb, te), k * (long long)sizeof(V) + 32);
         acctf(sm, run_points(it_n, it_tile, tb, te), (sizeof(T) == 8 ? 8 * k : 0) + 2);
         for (int tile = tb; tile < te; ++tile) {
@@ -1213,7 +1261,7 @@ struct Phases {
 #pragma unroll
                 for (int r = 0; r < kChunk; ++r) {
                     const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
-                    if (p < pend) x[p] = cadd(ldp(x + p), up2(d[r]));
+                    if (p < pend) x[p] = assign ? up2(d[r]) : cadd(ldp(x + p), up2(d[r]));
                 }
             }
         }
@@ -1221,14 +1269,26 @@ struct Phases {
 };
 
 // E4 (one warp per item): true relative residual, decide, start a cycle.
-__device__ void item_e4(const EngineArgs& A, int item, const Runs& R) {
+__device__ void item_e4(const EngineArgs& A, int item, const Runs& R, const int* list, const int* prefix, int nl,
+                        int ntasks) {
     const int lane = threadIdx.x & 31;
     const ItemDesc& it = A.item[item];
     ItemState* S = it.st;
-    const double ss = warp_norm_partials(it, R);
+    const int cycles = ldi(&S->cycles);
+    double ss;
+    if (cycles == 0 && A.mode == MODE_STEP && it.group >= 0) {
+        // shared first cycle: ||b|| from the group item's partials (same b, same list)
+        int lo = 0, hi = nl - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (list[mid] < it.group) lo = mid + 1; else hi = mid;
+        }
+        ss = warp_norm_partials(A.item[it.group], item_runs(prefix, lo, ntasks));
+    } else {
+        ss = warp_norm_partials(it, R);
+    }
     if (lane != 0) return;
     const double beta = sqrt(ss);
-    const int cycles = ldi(&S->cycles);
     double bnorm = cycles == 0 ? beta : ldd(&S->bnorm);
     if (cycles == 0) S->bnorm = beta;
     const double relres = bnorm > 0.0 ? beta / bnorm : 0.0;
@@ -1267,7 +1327,12 @@ __device__ void item_e4(const EngineArgs& A, int item, const Runs& R) {
         S->cycles = cycles + 1;
         S->cycle_tol_abs = fmax(A.tol * bnorm, A.inner_tol * beta);
     }
-    if (status == ST_CONVERGED || status == ST_FAILED) {
+    if (status == ST_CONVERGED && cycles == 0 && A.mode == MODE_STEP && it.group >= 0) {
+        S->k = 0;                                   // b = 0: x = 0, nothing to add (its x was not zeroed)
+        S->ydone = 1;
+        status = ST_DIRECT;
+    }
+    if (status == ST_CONVERGED || status == ST_FAILED || status == ST_DIRECT) {
         ItemStats* T = it.stats;
         T->iters += total;
         T->iters_sq += ldi(&S->sum_k2);
@@ -1415,16 +1480,21 @@ __device__ void member_direct_solve(const EngineArgs& A, int item) {
         c0 = (l >= 0 && lane <= l && lane >= lo) ? ldp(R + lane) : make_double2(0.0, 0.0);
         c1 = (l >= 0 && lane + 32 <= l && lane + 32 >= lo) ? ldp(R + lane + 32) : make_double2(0.0, 0.0);
     };
+    // reciprocals of the diagonal, all rows at once (a division costs ~0.3 us)
+    auto recip = [&](int i) {
+        if (i >= k) return make_double2(0.0, 0.0);
+        const double2 d = ldp(M->R + i * (i + 1) / 2 + i);
+        const double den = d.x * d.x + d.y * d.y;
+        return den > 0.0 ? cscale(cconj(d), 1.0 / den) : make_double2(0.0, 0.0);
+    };
+    const double2 inv0 = recip(lane), inv1 = recip(lane + 32);
     double2 c0, c1, n0, n1;
     col(k - 1, c0, c1);
     for (int l = k - 1; l >= 0; --l) {
         col(l - 1, n0, n1);
         double2 yl = make_double2(0.0, 0.0);
         if (lane == (l & 31)) {
-            const double2 d = l < 32 ? c0 : c1;
-            const double2 a = l < 32 ? a0 : a1;
-            const double den = d.x * d.x + d.y * d.y;
-            if (den > 0.0) yl = cscale(cmul(a, cconj(d)), 1.0 / den);
+            yl = l < 32 ? cmul(a0, inv0) : cmul(a1, inv1);
             if (l < 32) y0 = yl; else y1 = yl;
         }
         yl = shfl2(yl, l & 31);
@@ -1602,7 +1672,10 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
         const double tola = ldd(&S->cycle_tol_abs);
         const bool end = !(res2_bound(A, gj1, j) > tola * tola) || last || total >= A.max_iters ||
                          !(hn > 0.0) || !(rr > 0.0);
-        if (end) S->sum_k2 = ldi(&S->sum_k2) + j * j;
+        if (end) {
+            S->sum_k2 = ldi(&S->sum_k2) + j * j;
+            atomicAdd(A.epoch, 1u);                      // the Arnoldi list changes
+        }
         S->status = end ? ST_CYCLE_END : ST_ARNOLDI;     // published by the phase barrier
         return;
     }
@@ -1661,6 +1734,7 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
     const bool any = __any_sync(0xffffffffu, active);
     if (lane == 0) {
         S->k = j;
+        if (!(any && !last)) atomicAdd(A.epoch, 1u);     // the Arnoldi list changes
         S->status = (any && !last) ? ST_ARNOLDI : ST_IDLE;
     }
 }
@@ -1821,7 +1895,7 @@ __global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __gri
         if (!phase_sync(A, TR_INIT, &tcount)) return;
 
         for (;;) {
-            build_list(sm, list, prefix, (1u << ST_NEED_RES) | (1u << ST_CYCLE_END));
+            build_list(sm, list, prefix, (1u << ST_NEED_RES) | (1u << ST_CYCLE_END), true);
             if (sm.nl == 0) break;
             int s, e;
             my_range(sm.ntasks, &s, &e);
@@ -1832,11 +1906,18 @@ __global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __gri
                 t = prefix[l] + te;
             }
             if (!phase_sync(A, TR_E3, &tcount)) return;
-            for (int l = gwarp; l < sm.nl; l += nwarps) item_e4(A, list[l], item_runs(prefix, l, sm.ntasks));
+            for (int l = gwarp; l < sm.nl; l += nwarps)
+                item_e4(A, list[l], item_runs(prefix, l, sm.ntasks), list, prefix, sm.nl, sm.ntasks);
             if (!phase_sync(A, TR_E4, &tcount)) return;
 
             for (int j = 0; A.ortho && j <= A.m; ++j) {             // delayed CGS2
-                build_list(sm, list, prefix, 1u << ST_ARNOLDI);
+                // the list changes only when a commit ends an item (epoch bump)
+                if (threadIdx.x == 0) sm.ep_now = __ldcg(A.epoch);
+                __syncthreads();
+                if (j == 0 || sm.ep_now != sm.ep_seen) {
+                    build_list(sm, list, prefix, 1u << ST_ARNOLDI);
+                    if (threadIdx.x == 0) sm.ep_seen = sm.ep_now;
+                }
                 if (sm.nl == 0) break;
                 const bool last = j == A.m;
                 my_range(sm.ntasks, &s, &e);

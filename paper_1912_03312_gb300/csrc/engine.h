@@ -129,6 +129,7 @@ struct EngineArgs {
     const ProblemDesc* prob;
     const ItemDesc* item;
     unsigned* bar;       // [2]: count, generation
+    unsigned* epoch;     // bumped when an Arnoldi item leaves the Arnoldi state (list rebuilds)
     int* err;            // sticky error word
     unsigned long long* trace;   // optional: [1 + 2*cap] (count, then (phase, ns) pairs)
     int trace_cap;

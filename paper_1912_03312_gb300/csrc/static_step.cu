@@ -189,6 +189,7 @@ extern "C" int rexi_substep_static(const rexi_grid* g, const double* V, double t
     A.prob = (const ProblemDesc*)(base + o_prob);
     A.item = (const ItemDesc*)(base + o_items);
     A.bar = (unsigned*)(base + o_bar);
+    A.epoch = (unsigned*)(base + o_bar) + 3;
     A.err = (int*)(base + o_bar) + 2;
     IOArgs io;
     std::memset(&io, 0, sizeof(io));
