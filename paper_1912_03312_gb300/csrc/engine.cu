@@ -549,6 +549,51 @@ __device__ void reduce_partials(Smem& sm, const double2* part, const ItemDesc& i
     __syncthreads();
 }
 
+// Two partial sets at once (nv <= 16): one read loop, one block barrier.
+__device__ void reduce_partials2(Smem& sm, const double2* partA, const double2* partB, const ItemDesc& it,
+                                 const Runs& R, int nv, const double* scale, double2* outA, double2* outB) {
+    int nvp = 1;
+    while (nvp < nv) nvp <<= 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v = lane & (nvp - 1), rl = lane / nvp, rpw = 32 / nvp;
+    float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+    if (v < nv) {
+        const size_t off = (size_t)it.tile_off * sm.A.pv + v;
+#pragma unroll 4
+        for (int r = warp * rpw + rl; r < R.count; r += rpw * kWarps) {
+            const int tl = R.tile(r);
+            if (tl >= 0) {
+                const double2 qa = ldp(partA + off + (size_t)tl * sm.A.pv);
+                const double2 qb = ldp(partB + off + (size_t)tl * sm.A.pv);
+                ax += (float)qa.x;
+                ay += (float)qa.y;
+                bx += (float)qb.x;
+                by += (float)qb.y;
+            }
+        }
+    }
+    for (int o = nvp; o < 32; o <<= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        bx += __shfl_xor_sync(0xffffffffu, bx, o);
+        by += __shfl_xor_sync(0xffffffffu, by, o);
+    }
+    if (rl == 0) {
+        sm.red[warp][v] = make_double2((double)ax, (double)ay);
+        sm.red[warp][16 + v] = make_double2((double)bx, (double)by);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * nv) {
+        const int t = threadIdx.x < nv ? threadIdx.x : threadIdx.x - nv;
+        const int col = threadIdx.x < nv ? t : 16 + t;
+        double2 s2 = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s2 = cadd(s2, sm.red[w][col]);
+        (threadIdx.x < nv ? outA : outB)[t] = cscale(s2, scale[t]);
+    }
+    __syncthreads();
+}
+
 // Warp-level sum of the norm partials of item slot l (all lanes get the sum).
 __device__ __forceinline__ double warp_norm_partials(const ItemDesc& it, const Runs& R) {
     const int lane = threadIdx.x & 31;
@@ -788,6 +833,35 @@ struct Phases {
                 for (int w = q * vpw; w < (q + 1) * vpw; ++w) acc = cadd(acc, sm.red[w][0]);
             }
             part[(size_t)(it.tile_off + tb) * sm.A.pv + q] = acc;
+        }
+        __syncthreads();
+    }
+
+    // Both partial sets of the one-reduction Arnoldi in one pass (one barrier
+    // fewer): warps' sums of (ar, ai) in red[w][0..4), of (br, bi) in red[w][4..8).
+    static __device__ void dot_finish2(Smem& sm, const ItemDesc& it, int tb, int J, const DotPlan& d,
+                                       float (&ar)[4], float (&ai)[4], float (&br)[4], float (&bi)[4]) {
+        const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float r = warp_sum(ar[k]), i = warp_sum(ai[k]);
+            const float r2 = warp_sum(br[k]), i2 = warp_sum(bi[k]);
+            if (lane == 0) {
+                sm.red[wp][k] = make_double2((double)r, (double)i);
+                sm.red[wp][4 + k] = make_double2((double)r2, (double)i2);
+            }
+        }
+        __syncthreads();
+        const int q = threadIdx.x & 31, set = threadIdx.x >> 5;      // warp 0: first set, warp 1: second
+        if (set < 2 && q < J) {
+            double2 acc = make_double2(0.0, 0.0);
+            if (J >= kWarps) {
+                acc = sm.red[q % kWarps][4 * set + q / kWarps];
+            } else {
+                const int vpw = kWarps / J;
+                for (int w = q * vpw; w < (q + 1) * vpw; ++w) acc = cadd(acc, sm.red[w][4 * set]);
+            }
+            (set == 0 ? it.part1 : it.part2)[(size_t)(it.tile_off + tb) * sm.A.pv + q] = acc;
         }
         __syncthreads();
     }
@@ -1052,8 +1126,8 @@ struct Phases {
             dot_tile2(U0, n, fsv, fsw, p0, pend, d, matvec, ar, ai, br, bi);
             __syncthreads();
         }
-        dot_finish(sm, it, it.part1, tb, j + 1 - j0, d, ar, ai);
-        if (matvec) dot_finish(sm, it, it.part2, tb, j + 1 - j0, d, br, bi);
+        if (matvec) dot_finish2(sm, it, tb, j + 1 - j0, d, ar, ai, br, bi);
+        else dot_finish(sm, it, it.part1, tb, j + 1 - j0, d, ar, ai);
     }
 
     // Y prologue: every CTA of the item reduces X's partials and forms the
@@ -1071,8 +1145,12 @@ struct Phases {
             }
         }
         __syncthreads();                                                   // q_i normalised; t_j
-        reduce_partials<float>(sm, it.part1, it, R, j + 1 - j0, sm.ssm + j0, sm.h1 + j0);        // a_i, c
-        if (!last) reduce_partials<float>(sm, it.part2, it, R, j + 1 - j0, sm.ssm + j0, sm.h2 + j0);   // b_i, d
+        if (!last && j + 1 - j0 <= 16) {                                   // a_i, c and b_i, d together
+            reduce_partials2(sm, it.part1, it.part2, it, R, j + 1 - j0, sm.ssm + j0, sm.h1 + j0, sm.h2 + j0);
+        } else {
+            reduce_partials<float>(sm, it.part1, it, R, j + 1 - j0, sm.ssm + j0, sm.h1 + j0);      // a_i, c
+            if (!last) reduce_partials<float>(sm, it.part2, it, R, j + 1 - j0, sm.ssm + j0, sm.h2 + j0);  // b_i, d
+        }
         double2* Hw = sm.scratch;                                          // columns j0..j-2, pitch kHld
         const int ncol = max(0, j - 1 - j0);
         for (int t = threadIdx.x; t < ncol * kHld; t += kBlock) {
