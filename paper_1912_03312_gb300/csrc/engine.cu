@@ -1159,59 +1159,54 @@ struct Phases {
         }
         if (threadIdx.x < j) sm.hfin[threadIdx.x] = ldp(((j - 1) & 1 ? S->hcol2 : S->hcol) + threadIdx.x);
         __syncthreads();
-        if (threadIdx.x == 0) {
+        // Thread i <= j finishes row i on its own (the window sums are recomputed
+        // by every such thread): nu from one reciprocal square root, row i of
+        // column j-1, row i of column j, and the sweep's coefficients.
+        if (threadIdx.x <= j) {
+            const int i = threadIdx.x;
             double aa2 = 0.0;
-            double2 ab = make_double2(0.0, 0.0);
-            for (int i = j0; i < j; ++i) {
-                const double2 a = sm.h1[i];
+            double2 ab = make_double2(0.0, 0.0);                            // a^H b
+            for (int l = j0; l < j; ++l) {
+                const double2 a = sm.h1[l];
                 aa2 += a.x * a.x + a.y * a.y;
-                if (!last) ab = cadd(ab, cmul(cconj(a), sm.h2[i]));
+                if (!last) ab = cadd(ab, cmul(cconj(a), sm.h2[l]));
             }
             const double nu2 = sm.h1[j].x - aa2;
-            const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
-            sm.yscal[0] = nu;
-            sm.yscal[1] = nu > 0.0 ? sm.ssm[j] / nu : 0.0;
-            sm.yscal[2] = nu > 0.0 ? 1.0 / nu : 0.0;
-            sm.ygq = ab;                                                    // a^H b, used below
-        }
-        __syncthreads();
-        const double nu = sm.yscal[0];
-        if (j >= 1 && threadIdx.x <= j)                                    // complete column j-1
-            sm.hfin[threadIdx.x] = threadIdx.x < j ? cadd(sm.hfin[threadIdx.x], sm.h1[threadIdx.x])
-                                                   : make_double2(nu, 0.0);
-        __syncthreads();
-        if (!last && threadIdx.x <= j) {
-            const int i = threadIdx.x;
-            double2 Ha = make_double2(0.0, 0.0);                            // (H a)_i over columns l < j
-            for (int l = max(max(i - 1, 0), j0); l < j; ++l) {
-                const double2 Hil = l == j - 1 ? sm.hfin[i] : Hw[(l - j0) * kHld + i];
-                Ha = cadd(Ha, cmul(Hil, sm.h1[l]));
+            const double inv = nu2 > 0.0 ? rsqrt(nu2) : 0.0;
+            const double nu = nu2 > 0.0 ? nu2 * inv : 0.0;
+            double2 hf = make_double2(0.0, 0.0);                           // column j-1, row i
+            if (j >= 1) {
+                hf = i < j ? cadd(sm.hfin[i], sm.h1[i]) : make_double2(nu, 0.0);
+                sm.hfin[i] = hf;
             }
-            const double inv = sm.yscal[2];
-            double2 h;
-            if (i < j0) h = make_double2(0.0, 0.0);                        // outside the window
-            else if (i < j) h = cscale(csub(sm.h2[i], Ha), inv);
-            else h = cscale(csub(cscale(csub(sm.h2[j], sm.ygq), inv), Ha), inv);
-            sm.hnew[i] = h;
-            const double2 gam = cadd(cscale(Ha, inv), h);
-            if (i < j) {
-                const double2 ca = cscale(sm.h1[i], sm.ssm[i] * inv);      // q_j = t_j/nu u_j - sum ca_i u_i
-                sm.coef[i] = ca;
-                sm.coeff[i] = make_float2((float)ca.x, (float)ca.y);
-                const double2 cg = cscale(gam, sm.ssm[i]);                  // v_{j+1} = w/nu - sum cg_i u_i - gam_j q_j
-                sm.coefG[i] = cg;
-                sm.coefGf[i] = make_float2((float)cg.x, (float)cg.y);
+            if (i == 0) {
+                sm.yscal[0] = nu;
+                sm.yscal[1] = sm.ssm[j] * inv;
+                sm.yscal[2] = inv;
             }
-        }
-        __syncthreads();
-        if (!last && threadIdx.x == 0) {
-            const int i = j;
-            double2 Ha = make_double2(0.0, 0.0);
-            for (int l = max(max(i - 1, 0), j0); l < j; ++l) {
-                const double2 Hil = l == j - 1 ? sm.hfin[i] : Hw[(l - j0) * kHld + i];
-                Ha = cadd(Ha, cmul(Hil, sm.h1[l]));
+            if (!last) {
+                double2 Ha = make_double2(0.0, 0.0);                        // (H a)_i over columns l < j
+                for (int l = max(max(i - 1, 0), j0); l < j; ++l) {
+                    const double2 Hil = l == j - 1 ? hf : Hw[(l - j0) * kHld + i];
+                    Ha = cadd(Ha, cmul(Hil, sm.h1[l]));
+                }
+                double2 h;
+                if (i < j0) h = make_double2(0.0, 0.0);                    // outside the window
+                else if (i < j) h = cscale(csub(sm.h2[i], Ha), inv);
+                else h = cscale(csub(cscale(csub(sm.h2[j], ab), inv), Ha), inv);
+                sm.hnew[i] = h;
+                const double2 gam = cadd(cscale(Ha, inv), h);
+                if (i < j) {
+                    const double2 ca = cscale(sm.h1[i], sm.ssm[i] * inv);  // q_j = t_j/nu u_j - sum ca_i u_i
+                    sm.coef[i] = ca;
+                    sm.coeff[i] = make_float2((float)ca.x, (float)ca.y);
+                    const double2 cg = cscale(gam, sm.ssm[i]);              // v_{j+1} = w/nu - sum cg_i u_i - gam_j q_j
+                    sm.coefG[i] = cg;
+                    sm.coefGf[i] = make_float2((float)cg.x, (float)cg.y);
+                } else {
+                    sm.ygq = gam;                                           // gamma_j
+                }
             }
-            sm.ygq = cadd(cscale(Ha, sm.yscal[2]), sm.hnew[j]);            // gamma_j
         }
         __syncthreads();
     }
