@@ -330,7 +330,7 @@ __device__ void build_list(Smem& sm, int* list, int* prefix, unsigned mask, bool
 // Problems live in (backward) substep `sub`, with their tile prefix sums.
 // The pole sum and the adjoint accumulation are FP64 work with no reuse:
 // small tasks spread them over every SM.
-constexpr int kPsPPT = 2;
+constexpr int kPsPPT = 4;
 constexpr int kPsTile = kBlock * kPsPPT;
 
 __device__ void build_problem_list(Smem& sm, int* list, int* prefix, int sub) {
@@ -1841,7 +1841,7 @@ __device__ void task_pole_sum(Smem& sm, int prob, int tile, int sub) {
         }
     }
     const V* Ug = (const V*)sm.gbasis;
-#pragma unroll 4
+#pragma unroll 8
     for (int i = 0; i < sm.kyhat; ++i) {
         const V* ui = Ug + (size_t)i * pr.n;
         const double2 c = sm.yhat[i];
