@@ -294,7 +294,9 @@ int rexi_plan_last_status(rexi_plan* plan);
 /* Work decomposition of the plan's launches (the autotuner's knobs):
  * pole_tile / group_tile = points per task of pole items / shared-cycle group
  * items, each a multiple of 256 up to 2048; ctas_per_sm caps the resident CTAs
- * per SM of the persistent grid (0 = as many as fit).  Synchronises the device
+ * per SM of the persistent grid (0 = as many as fit; 1 on an FP64 plan selects
+ * the kernel compiled for one CTA per SM, with twice the registers per thread
+ * and wider update sweeps).  Synchronises the device
  * and rewrites the plan's descriptors; results do not depend on these values
  * beyond floating-point summation order. */
 int rexi_plan_set_tiles(rexi_plan* plan, int pole_tile, int group_tile, int ctas_per_sm);

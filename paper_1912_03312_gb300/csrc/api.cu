@@ -376,16 +376,16 @@ EngineArgs base_args(const rexi_plan* p, int mode, const DescSet& set, int nprob
 }
 
 // Largest co-resident grid of the persistent kernel (cooperative launch limit).
-int max_grid_cached(bool fp32, size_t smem, int device) {
+int max_grid_cached(bool fp32, size_t smem, int device, bool wide) {
     static std::mutex mu;
     static std::vector<std::pair<std::pair<int, size_t>, int>> cache;
-    const std::pair<int, size_t> key(device * 2 + (fp32 ? 1 : 0), smem);
+    const std::pair<int, size_t> key(device * 4 + (fp32 ? 1 : 0) + (wide ? 2 : 0), smem);
     {
         std::lock_guard<std::mutex> lk(mu);
         for (auto& c : cache)
             if (c.first == key) return c.second;
     }
-    const int g = rexi::engine_max_grid(fp32, smem, device);
+    const int g = rexi::engine_max_grid(fp32, smem, device, wide);
     if (g > 0) {
         std::lock_guard<std::mutex> lk(mu);
         cache.push_back(std::make_pair(key, g));
@@ -406,11 +406,12 @@ int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles,
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stats, 0, sizeof(ItemStats) * A.nitems, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     const size_t smem = rexi::engine_smem_bytes(A.nitems, p->fp32, A.ortho);
-    int maxg = max_grid_cached(p->fp32, smem, p->device);
+    const bool wide = !p->fp32 && p->ctas_per_sm == 1;     // one CTA per SM: the wide-register kernel
+    int maxg = max_grid_cached(p->fp32, smem, p->device, wide);
     if (maxg <= 0) return REXI_ECUDA;
     if (p->ctas_per_sm > 0) maxg = std::min(maxg, p->ctas_per_sm * sm_count(p->device));
     const int grid = std::max(1, std::min(maxg, total_tiles));
-    e = rexi::launch_engine(p->fp32, A, io, grid, smem, stream);
+    e = rexi::launch_engine(p->fp32, A, io, grid, smem, stream, wide);
     p->last_stream = stream;
     p->last_launches = 1;
     p->last_grid = grid;
@@ -969,11 +970,12 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_stats, 0, sizeof(ItemStats) * (p0->K + p0->ngroups), s);
     if (e != cudaSuccess) return REXI_ECUDA;
     const size_t smem = rexi::engine_smem_bytes(A.nitems, p0->fp32, A.ortho);
-    int maxg = max_grid_cached(p0->fp32, smem, p0->device);
+    const bool wide = !p0->fp32 && p0->ctas_per_sm == 1;
+    int maxg = max_grid_cached(p0->fp32, smem, p0->device, wide);
     if (maxg <= 0) return REXI_ECUDA;
     if (p0->ctas_per_sm > 0) maxg = std::min(maxg, p0->ctas_per_sm * sm_count(p0->device));
     const int grid = std::max(1, std::min(maxg, total_tiles));
-    e = rexi::launch_engine(p0->fp32, A, io, grid, smem, s);
+    e = rexi::launch_engine(p0->fp32, A, io, grid, smem, s, wide);
     for (int b = 0; b < B; ++b) {
         plans[b]->last_stream = s;
         plans[b]->last_launches = 1;

@@ -71,6 +71,24 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 
+// acc + c u and acc - c u as chains of fused multiply-adds, two per component
+// (written out so that no separate multiply or add is left over: the FP64
+// pipe is the scarce unit of the sweeps).
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double2 cfma(double2 acc, double2 c, double2 u) {
+    return make_double2(fma(-c.y, u.y, fma(c.x, u.x, acc.x)), fma(c.y, u.x, fma(c.x, u.y, acc.y)));
+}
+__device__ __forceinline__ double2 cfms(double2 acc, double2 c, double2 u) {
+    return make_double2(fma(c.y, u.y, fma(-c.x, u.x, acc.x)), fma(-c.y, u.x, fma(-c.x, u.y, acc.y)));
+}
+__device__ __forceinline__ float2 cfma(float2 acc, float2 c, float2 u) {
+    return make_float2(fmaf(-c.y, u.y, fmaf(c.x, u.x, acc.x)), fmaf(c.y, u.x, fmaf(c.x, u.y, acc.y)));
+}
+__device__ __forceinline__ float2 cfms(float2 acc, float2 c, float2 u) {
+    return make_float2(fmaf(c.y, u.y, fmaf(-c.x, u.x, acc.x)), fmaf(-c.y, u.x, fmaf(-c.x, u.y, acc.y)));
+}
+
 // Loads of data written inside this launch go through L2 only (.cg): L1 is
 // not coherent across SMs.
 __device__ __forceinline__ float2 ldp(const float2* p) { return __ldcg(p); }
@@ -406,9 +424,13 @@ __device__ __forceinline__ V stencil_scaled(const V* __restrict__ u, int p, cons
         s.x += a2t * (l.x + r.x);
         s.y += a2t * (l.y + r.y);
     }
-    const T dd = __ldg(diag + p) * t - st.x;
-    s.x += dd * c.x + st.y * c.y;
-    s.y += dd * c.y - st.y * c.x;
+    const T dd = fmat(__ldg(diag + p), t, -st.x);
+    s.x = fmat(dd, c.x, s.x);
+    s.y = fmat(dd, c.y, s.y);
+    if (st.y != T(0)) {                 // uniform: a shared basis has no shift
+        s.x = fmat(st.y, c.y, s.x);
+        s.y = fmat(-st.y, c.x, s.y);
+    }
     return s;
 }
 
@@ -433,9 +455,13 @@ __device__ __forceinline__ V stencil_apply(const V* __restrict__ u, int p, const
         s.x += a2 * (l.x + r.x);
         s.y += a2 * (l.y + r.y);
     }
-    const T d = __ldg(diag + p);
-    s.x += d * c.x - (shift.x * c.x - shift.y * c.y);
-    s.y += d * c.y - (shift.x * c.y + shift.y * c.x);
+    const T dd = __ldg(diag + p) - shift.x;
+    s.x = fmat(dd, c.x, s.x);
+    s.y = fmat(dd, c.y, s.y);
+    if (shift.y != T(0)) {
+        s.x = fmat(shift.y, c.y, s.x);
+        s.y = fmat(-shift.y, c.x, s.y);
+    }
     return s;
 }
 
@@ -669,12 +695,12 @@ __device__ __forceinline__ void load_scales(Smem& sm, const ItemState* S, int cn
     __syncthreads();
 }
 
-template <typename T, int VG>
+template <typename T, int VG, int MINB>
 struct Phases {
     typedef typename C2<T>::t V;
-    // points per thread held at once in the update sweeps (FP64 accumulators
-    // of 8 points would not fit the register budget)
-    static constexpr int kChunk = sizeof(T) == 8 ? kPPT / 2 : kPPT;
+    // points per thread held at once in the update sweeps: FP64 accumulators
+    // of 8 points fit the register budget of one CTA per SM, not of two
+    static constexpr int kChunk = (sizeof(T) == 8 && MINB > 1) ? kPPT / 2 : kPPT;
 
     // Every thread owns points p0 + r * kBlock + threadIdx.x, r < kPPT, of a
     // tile; per basis vector all of its kPPT loads are independent.  A CTA
@@ -877,8 +903,7 @@ struct Phases {
             for (int r = 0; r < kPPT; ++r) {
                 const int p = p0 + r * kBlock + threadIdx.x;
                 const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
-                w[r].x -= c.x * u.x - c.y * u.y;
-                w[r].y -= c.x * u.y + c.y * u.x;
+                w[r] = cfms(w[r], c, u);
             }
         }
     }
@@ -1169,7 +1194,7 @@ struct Phases {
             for (int l = j0; l < j; ++l) {
                 const double2 a = sm.h1[l];
                 aa2 += a.x * a.x + a.y * a.y;
-                if (!last) ab = cadd(ab, cmul(cconj(a), sm.h2[l]));
+                if (!last) ab = cfma(ab, cconj(a), sm.h2[l]);
             }
             const double nu2 = sm.h1[j].x - aa2;
             const double inv = nu2 > 0.0 ? rsqrt(nu2) : 0.0;
@@ -1188,7 +1213,7 @@ struct Phases {
                 double2 Ha = make_double2(0.0, 0.0);                        // (H a)_i over columns l < j
                 for (int l = max(max(i - 1, 0), j0); l < j; ++l) {
                     const double2 Hil = l == j - 1 ? hf : Hw[(l - j0) * kHld + i];
-                    Ha = cadd(Ha, cmul(Hil, sm.h1[l]));
+                    Ha = cfma(Ha, Hil, sm.h1[l]);
                 }
                 double2 h;
                 if (i < j0) h = make_double2(0.0, 0.0);                    // outside the window
@@ -1248,18 +1273,15 @@ struct Phases {
                     for (int r = 0; r < kChunk; ++r) {
                         const int p = base + r * nthr + tid;
                         const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
-                        qa[r].x -= ca.x * u.x - ca.y * u.y;
-                        qa[r].y -= ca.x * u.y + ca.y * u.x;
-                        va[r].x -= cg.x * u.x - cg.y * u.y;
-                        va[r].y -= cg.x * u.y + cg.y * u.x;
+                        qa[r] = cfms(qa[r], ca, u);
+                        va[r] = cfms(va[r], cg, u);
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < kChunk; ++r) {
                     const int p = base + r * nthr + tid;
                     if (p < pend) {
-                        va[r].x -= gq.x * qa[r].x - gq.y * qa[r].y;
-                        va[r].y -= gq.x * qa[r].y + gq.y * qa[r].x;
+                        va[r] = cfms(va[r], gq, qa[r]);
                         uj[p] = qa[r];
                         wv[p] = va[r];
                     }
@@ -1327,8 +1349,7 @@ struct Phases {
                     for (int r = 0; r < kChunk; ++r) {
                         const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
                         const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
-                        d[r].x += c.x * u.x - c.y * u.y;
-                        d[r].y += c.x * u.y + c.y * u.x;
+                        d[r] = cfma(d[r], c, u);
                     }
                 }
 #pragma unroll
@@ -1434,8 +1455,8 @@ __device__ void item_p4(const EngineArgs& A, int item, const Runs& R, int j) {
         const double2 b = shfl2(hl, i + 1);
         const double c = __shfl_sync(0xffffffffu, csl, i);
         const double2 s = shfl2(snl, i);
-        const double2 nh = cadd(cscale(carry, c), cmul(s, b));
-        carry = cadd(cscale(cmul(cconj(s), carry), -1.0), cscale(b, c));
+        const double2 nh = cfma(cscale(carry, c), s, b);
+        carry = cfms(cscale(b, c), cconj(s), carry);
         if (lane == 0) S->R[col + i] = nh;
     }
     if (lane != 0) return;
@@ -1605,8 +1626,8 @@ __device__ void group_p4(const EngineArgs& A, int gitem, const Runs& R, int j) {
             if (i + 1 == j) b = csub(b, sh);
             const double c = ldd(gd.gcs + (size_t)i * nm + mi);
             const double2 sn = ldp(gd.gsn + (size_t)i * nm + mi);
-            const double2 nh = cadd(cscale(carry, c), cmul(sn, b));
-            carry = cadd(cscale(cmul(cconj(sn), carry), -1.0), cscale(b, c));
+            const double2 nh = cfma(cscale(carry, c), sn, b);
+            carry = cfms(cscale(b, c), cconj(sn), carry);
             S->R[col + i] = nh;
         }
         const double aa = sqrt(carry.x * carry.x + carry.y * carry.y);
@@ -1719,20 +1740,23 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
         const int col = jj * (jj + 1) / 2;
         __syncwarp();
         if (lane != 0) return;
+        // the state this commit reads is loaded before the serial rotations
+        const double2 gj = ldp(&S->g[jj]);
+        const int total = ldi(&S->total_iters) + 1;
+        const double tola = ldd(&S->cycle_tol_abs);
         double2 carry = i0 == 0 ? sm.hfin[0] : make_double2(0.0, 0.0);
         for (int i = i0; i < jj; ++i) {
             const double2 b = sm.hfin[i + 1];
             const double c = sm.gcs_s[i];
             const double2 sn = sm.gsn_s[i];
-            const double2 nh = cadd(cscale(carry, c), cmul(sn, b));
-            carry = cadd(cscale(cmul(cconj(sn), carry), -1.0), cscale(b, c));
+            const double2 nh = cfma(cscale(carry, c), sn, b);
+            carry = cfms(cscale(b, c), cconj(sn), carry);
             S->R[col + i] = nh;
         }
         const double hn = nu;
         double c, rr;
         double2 sn, rjj;
         givens(carry, hn, &c, &sn, &rjj, &rr);
-        const double2 gj = ldp(&S->g[jj]);
         const double2 gj1 = cscale(cmul(cconj(sn), gj), -1.0);
         S->R[col + jj] = rjj;
         S->cs[jj] = c;
@@ -1740,9 +1764,7 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
         S->g[jj] = cscale(gj, c);
         S->g[jj + 1] = gj1;
         S->k = j;
-        const int total = ldi(&S->total_iters) + 1;
         S->total_iters = total;
-        const double tola = ldd(&S->cycle_tol_abs);
         const bool end = !(res2_bound(A, gj1, j) > tola * tola) || last || total >= A.max_iters ||
                          !(hn > 0.0) || !(rr > 0.0);
         if (end) {
@@ -1758,9 +1780,14 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
     for (int mi = lane; mi < nm; mi += 32) {
         const ItemDesc& md = A.item[it.member0 + mi];
         ItemState* M = md.st;
-        if (ldi(&M->status) != ST_SHARED) continue;
+        // every load of the member's state is issued before the serial rotations
+        const int mstatus = ldi(&M->status);
+        const double2 gj = ldp(&M->g[max(jj, 0)]);
+        const int total = ldi(&M->total_iters) + 1;
+        const double tola = ldd(&M->cycle_tol_abs);
+        if (mstatus != ST_SHARED) continue;
         if (j == 0) {
-            M->g[0] = cscale(ldp(&M->g[0]), nu);
+            M->g[0] = cscale(gj, nu);
             active = true;
             continue;
         }
@@ -1775,15 +1802,14 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
             const size_t rs = (size_t)(i - i0) * nm + mi;
             const double c = staged ? st_cs[rs] : ldd(it.gcs + ri);
             const double2 sn = staged ? st_sn[rs] : ldp(it.gsn + ri);
-            const double2 nh = cadd(cscale(carry, c), cmul(sn, b));
-            carry = cadd(cscale(cmul(cconj(sn), carry), -1.0), cscale(b, c));
+            const double2 nh = cfma(cscale(carry, c), sn, b);
+            carry = cfms(cscale(b, c), cconj(sn), carry);
             M->R[col + i] = nh;
         }
         const double hn = nu;
         double c, rr;
         double2 sn, rjj;
         givens(carry, hn, &c, &sn, &rjj, &rr);
-        const double2 gj = ldp(&M->g[jj]);
         const double2 gj1 = cscale(cmul(cconj(sn), gj), -1.0);
         it.gcs[(size_t)jj * nm + mi] = c;
         it.gsn[(size_t)jj * nm + mi] = sn;
@@ -1791,10 +1817,8 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
         M->g[jj] = cscale(gj, c);
         M->g[jj + 1] = gj1;
         M->k = j;
-        const int total = ldi(&M->total_iters) + 1;
         M->total_iters = total;
         const double res2 = res2_bound(A, gj1, j);
-        const double tola = ldd(&M->cycle_tol_abs);
         const bool end = !(res2 > tola * tola) || last || total >= A.max_iters || !(hn > 0.0) || !(rr > 0.0);
         int stn = ST_SHARED;
         if (end) {
@@ -1837,7 +1861,7 @@ __device__ void task_pole_sum(Smem& sm, int prob, int tile, int sub) {
 #pragma unroll
         for (int r = 0; r < kPsPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
-            if (p < pend) acc[r] = cadd(acc[r], cmul(al, ldp(xk + p)));
+            if (p < pend) acc[r] = cfma(acc[r], al, ldp(xk + p));
         }
     }
     const V* Ug = (const V*)sm.gbasis;
@@ -1848,7 +1872,7 @@ __device__ void task_pole_sum(Smem& sm, int prob, int tile, int sub) {
 #pragma unroll
         for (int r = 0; r < kPsPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
-            if (p < pend) acc[r] = cadd(acc[r], cmul(c, up2(ldp(ui + p))));
+            if (p < pend) acc[r] = cfma(acc[r], c, up2(ldp(ui + p)));
         }
     }
 #pragma unroll
@@ -1885,7 +1909,7 @@ __device__ void task_adjoint(Smem& sm, int prob, int tile, int bs) {
             const int p = p0 + r * kBlock + threadIdx.x;
             if (p < pend) {
                 const double2 xv = ldp(X + p), yv = ldp(Y + p);
-                g[r] = cadd(g[r], cmul(cconj(al), yv));
+                g[r] = cfma(g[r], cconj(al), yv);
                 dv[r] += cmul(al, cmul(cconj(yv), xv)).x;
             }
         }
@@ -1908,12 +1932,12 @@ __device__ __forceinline__ void my_range(int ntasks, int* s, int* e) {
 
 // resident CTAs per SM the register budget is sized for: three for the FP32
 // basis; two for FP64 (its staging tiles limit residency to two anyway)
-template <typename T> constexpr int kMinCtas = sizeof(T) == 8 ? 2 : 3;
-
-template <typename T, int VG>
-__global__ void __launch_bounds__(kBlock, kMinCtas<T>) engine_kernel(const __grid_constant__ EngineArgs gA,
-                                                           const __grid_constant__ IOArgs gio) {
-    typedef Phases<T, VG> P;
+// MINB: CTAs per SM the register budget is sized for (FP64: 2 at 128
+// registers, or 1 at up to 255 with wider update chunks; c64: 3).
+template <typename T, int VG, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) engine_kernel(const __grid_constant__ EngineArgs gA,
+                                                            const __grid_constant__ IOArgs gio) {
+    typedef Phases<T, VG, MINB> P;
     extern __shared__ int dyn[];
     __shared__ Smem sm;
     if (threadIdx.x == 0) sm.A = gA;
@@ -2120,8 +2144,9 @@ __global__ void __launch_bounds__(kBlock) cheb_kernel(const __grid_constant__ Ch
             const double2 h = stencil_apply<double, double2>(X, p, pr, diag, a0, a1, a2, zero);
             const double2 u = ldp(a.psi + p);
             const double2 y = ldp(Y + p);
-            const double2 au = cmul(ck, u);
-            Y[p] = make_double2(au.x + s2 * h.x - y.x, au.y + s2 * h.y - y.y);
+            // b_k = c_k u + 2 Ht b_{k+1} - b_{k+2}, three fused multiply-adds per component
+            Y[p] = make_double2(fma(s2, h.x, fma(ck.x, u.x, fma(-ck.y, u.y, -y.x))),
+                                fma(s2, h.y, fma(ck.x, u.y, fma(ck.y, u.x, -y.y))));
         }
         double2* t = X;
         X = Y;
@@ -2186,12 +2211,13 @@ size_t engine_smem_bytes(int nitems, bool fp32, int ortho) {
            std::max(tiles, (size_t)kScratch * sizeof(double2));
 }
 
-static void* engine_fn(bool fp32) {
-    return fp32 ? (void*)engine_kernel<float, 32> : (void*)engine_kernel<double, 16>;
+static void* engine_fn(bool fp32, bool wide) {
+    if (fp32) return (void*)engine_kernel<float, 32, 3>;
+    return wide ? (void*)engine_kernel<double, 16, 1> : (void*)engine_kernel<double, 16, 2>;
 }
 
-int engine_max_grid(bool fp32, size_t smem, int device) {
-    void* fn = engine_fn(fp32);
+int engine_max_grid(bool fp32, size_t smem, int device, bool wide) {
+    void* fn = engine_fn(fp32, wide);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(160 * 1024)) != cudaSuccess)
         return 0;
     int nb = 0;
@@ -2202,8 +2228,8 @@ int engine_max_grid(bool fp32, size_t smem, int device) {
 }
 
 cudaError_t launch_engine(bool fp32, const EngineArgs& a, const IOArgs& io, int grid, size_t smem,
-                          cudaStream_t stream) {
-    void* fn = engine_fn(fp32);
+                          cudaStream_t stream, bool wide) {
+    void* fn = engine_fn(fp32, wide);
     void* args[] = {(void*)&a, (void*)&io};
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, smem, stream);
 }

@@ -166,10 +166,12 @@ struct ChebArgs {
 cudaError_t launch_cheb(const ChebArgs& args, int grid, cudaStream_t stream);
 int cheb_max_grid(int device);   // co-resident CTAs of the Chebyshev kernel (<= 0: error)
 
-// Launch the persistent kernel; T = float (mixed) or double (fp64).
+// Launch the persistent kernel; T = float (mixed) or double (fp64).  wide
+// (FP64 only): the instantiation for one CTA per SM (up to 255 registers,
+// 8-point update chunks); its largest co-resident grid is one CTA per SM.
 cudaError_t launch_engine(bool fp32_basis, const EngineArgs& args, const IOArgs& io, int grid,
-                          size_t smem, cudaStream_t stream);
-int engine_max_grid(bool fp32_basis, size_t smem, int device);
+                          size_t smem, cudaStream_t stream, bool wide = false);
+int engine_max_grid(bool fp32_basis, size_t smem, int device, bool wide = false);
 size_t engine_smem_bytes(int nitems, bool fp32, int ortho);
 
 // Single-stage kernels.
