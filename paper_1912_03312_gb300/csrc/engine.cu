@@ -89,8 +89,18 @@ __device__ __forceinline__ float2 cfms(float2 acc, float2 c, float2 u) {
     return make_float2(fmaf(c.y, u.y, fmaf(-c.x, u.x, acc.x)), fmaf(-c.y, u.x, fmaf(-c.x, u.y, acc.y)));
 }
 
-// Loads of data written inside this launch go through L2 only (.cg): L1 is
-// not coherent across SMs.
+// State words, Hessenberg columns and partial sums written inside this launch
+// are loaded through L2 only (.cg).
+//
+// Vector data (basis vectors, w, x, the step states) is loaded with plain
+// loads, which may be served by L1: every read of such data is separated from
+// the stores it depends on by a grid barrier (release by the arriving CTAs,
+// ld.acquire.gpu plus fence by each waiting CTA, then a CTA barrier), so by the
+// PTX memory model the load observes those stores whatever the cache operator.
+// The stencil's neighbour loads then mostly hit the lines of the CTA's own
+// centre loads.
+__device__ __forceinline__ float2 ldv(const float2* p) { return *p; }
+__device__ __forceinline__ double2 ldv(const double2* p) { return *p; }
 __device__ __forceinline__ float2 ldp(const float2* p) { return __ldcg(p); }
 __device__ __forceinline__ double2 ldp(const double2* p) { return __ldcg(p); }
 __device__ __forceinline__ double ldd(const double* p) { return __ldcg(p); }
@@ -411,16 +421,16 @@ __device__ __forceinline__ V stencil_scaled(const V* __restrict__ u, int p, cons
     const Nb b = neighbours(p, pr.nx, pr.ny, pr.nz);
     V s;
     {
-        const V l = ldp(u + b.xm), r = ldp(u + b.xp);
+        const V l = ldv(u + b.xm), r = ldv(u + b.xp);
         s = mk2(a0t * (l.x + r.x), a0t * (l.y + r.y));
     }
     if (pr.ny > 1) {
-        const V l = ldp(u + b.ym), r = ldp(u + b.yp);
+        const V l = ldv(u + b.ym), r = ldv(u + b.yp);
         s.x += a1t * (l.x + r.x);
         s.y += a1t * (l.y + r.y);
     }
     if (pr.nz > 1) {
-        const V l = ldp(u + b.zm), r = ldp(u + b.zp);
+        const V l = ldv(u + b.zm), r = ldv(u + b.zp);
         s.x += a2t * (l.x + r.x);
         s.y += a2t * (l.y + r.y);
     }
@@ -434,24 +444,27 @@ __device__ __forceinline__ V stencil_scaled(const V* __restrict__ u, int p, cons
     return s;
 }
 
-template <typename T, typename V>
+// kL1: vector loads that may be served by L1 (ldv) or L2-only loads (ldp).
+template <bool kL1, typename V> __device__ __forceinline__ V ldsel(const V* p) { return kL1 ? ldv(p) : ldp(p); }
+
+template <typename T, typename V, bool kL1 = true>
 __device__ __forceinline__ V stencil_apply(const V* __restrict__ u, int p, const ProblemDesc& pr,
                                            const T* __restrict__ diag, const T a0, const T a1,
                                            const T a2, const V shift) {
     const Nb b = neighbours(p, pr.nx, pr.ny, pr.nz);
-    const V c = ldp(u + p);
+    const V c = ldsel<kL1>(u + p);
     V s;
     {
-        const V l = ldp(u + b.xm), r = ldp(u + b.xp);
+        const V l = ldsel<kL1>(u + b.xm), r = ldsel<kL1>(u + b.xp);
         s = mk2(a0 * (l.x + r.x), a0 * (l.y + r.y));
     }
     if (pr.ny > 1) {
-        const V l = ldp(u + b.ym), r = ldp(u + b.yp);
+        const V l = ldsel<kL1>(u + b.ym), r = ldsel<kL1>(u + b.yp);
         s.x += a1 * (l.x + r.x);
         s.y += a1 * (l.y + r.y);
     }
     if (pr.nz > 1) {
-        const V l = ldp(u + b.zm), r = ldp(u + b.zp);
+        const V l = ldsel<kL1>(u + b.zm), r = ldsel<kL1>(u + b.zp);
         s.x += a2 * (l.x + r.x);
         s.y += a2 * (l.y + r.y);
     }
@@ -731,7 +744,7 @@ struct Phases {
 #pragma unroll
             for (int r = 0; r < kPPT; ++r) {
                 const int p = p0 + r * kBlock + threadIdx.x;
-                rv[r] = p < pend ? ldp(b + p) : make_double2(0.0, 0.0);
+                rv[r] = p < pend ? ldv(b + p) : make_double2(0.0, 0.0);
             }
             if (cycles == 0) {
                 // x0 = 0; in a step launch a pole on a shared first cycle gets x assigned by its
@@ -818,7 +831,7 @@ struct Phases {
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int pl = (row + k) * 32 + lane;
-                    u[k] = (row + k < d.row1 && p0 + pl < pend) ? ldp(uq + pl) : mk2(T(0), T(0));
+                    u[k] = (row + k < d.row1 && p0 + pl < pend) ? ldv(uq + pl) : mk2(T(0), T(0));
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
@@ -902,7 +915,7 @@ struct Phases {
 #pragma unroll
             for (int r = 0; r < kPPT; ++r) {
                 const int p = p0 + r * kBlock + threadIdx.x;
-                const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                const V u = p < pend ? ldv(uq + p) : mk2(T(0), T(0));
                 w[r] = cfms(w[r], c, u);
             }
         }
@@ -912,7 +925,7 @@ struct Phases {
 #pragma unroll
         for (int r = 0; r < kPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
-            w[r] = p < pend ? ldp(src + p) : mk2(T(0), T(0));
+            w[r] = p < pend ? ldv(src + p) : mk2(T(0), T(0));
         }
     }
 
@@ -1077,7 +1090,7 @@ struct Phases {
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int pl = (row + k) * 32 + lane;
-                    u[k] = (row + k < d.row1 && p0 + pl < pend) ? dot_f2(ldp(uq + pl)) : make_float2(0.f, 0.f);
+                    u[k] = (row + k < d.row1 && p0 + pl < pend) ? dot_f2(ldv(uq + pl)) : make_float2(0.f, 0.f);
                 }
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
@@ -1125,6 +1138,10 @@ struct Phases {
              (j - j0 + 1) * (long long)sizeof(V) + (matvec ? (long long)sizeof(V) + (long long)sizeof(T) : 0));
         if (sizeof(T) == 8)
             acctf(sm, run_points(it_n, it_tile, tb, te), matvec ? stencil_flops(pr) : 0);
+        if (matvec && j + 1 - j0 <= 4) {
+            dx_window(sm, it, U0, uj, wv, n, pr, diag, tj, a0t, a1t, a2t, sht, tjf, tb, te, j + 1 - j0);
+            return;
+        }
         const DotPlan d = dot_plan(j + 1 - j0, it_tile);
         float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};   // FP32 inner products
         float br[4] = {0.f, 0.f, 0.f, 0.f}, bi[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1136,7 +1153,7 @@ struct Phases {
                 float2 vf = make_float2(0.f, 0.f);
                 V w = mk2(T(0), T(0));
                 if (p < pend) {
-                    const V u = ldp(uj + p);
+                    const V u = ldv(uj + p);
                     const float2 uf = dot_f2(u);
                     vf = make_float2(tjf * uf.x, tjf * uf.y);      // v_j = t_j u_j, only its FP32 copy is needed
                     if (matvec) {
@@ -1155,6 +1172,57 @@ struct Phases {
         else dot_finish(sm, it, it.part1, tb, j + 1 - j0, d, ar, ai);
     }
 
+    // X for a step with at most 4 vectors in the window (slots j0 .. j): every
+    // thread accumulates the FP32 inner products of its own points inside the
+    // stencil sweep, so the window vectors' loads overlap the stencil's and
+    // the tile needs no staging pass.  The run's partials are a warp
+    // transpose-reduce and a fixed-order sum over the warps, in the layout of
+    // the staged path (part1: a and c, part2: b and d).
+    static __device__ void dx_window(Smem& sm, const ItemDesc& it, const V* U0, const V* uj, V* wv, size_t n,
+                                     const ProblemDesc& pr, const T* diag, T tj, T a0t, T a1t, T a2t, V sht,
+                                     float tjf, int tb, int te, int J) {
+        const int it_n = it.n, it_tile = it.tile;
+        float v[16];                      // [2k, 2k+1]: conj(u_k) v_j; [8 + 2k, 9 + 2k]: conj(u_k) w
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = 0.f;
+        for (int tile = tb; tile < te; ++tile) {
+            const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
+#pragma unroll
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                if (p < pend) {
+                    const V u = ldv(uj + p);
+                    const V w = stencil_scaled<T, V>(uj, p, pr, diag, tj, a0t, a1t, a2t, sht, u);
+                    wv[p] = w;
+                    const float2 uf = dot_f2(u), wf = dot_f2(w);
+                    const float2 vf = make_float2(tjf * uf.x, tjf * uf.y);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (k < J) {
+                            const float2 q = k < J - 1 ? dot_f2(ldv(U0 + (size_t)k * n + p)) : uf;
+                            v[2 * k] = fmaf(q.x, vf.x, fmaf(q.y, vf.y, v[2 * k]));
+                            v[2 * k + 1] = fmaf(q.x, vf.y, fmaf(-q.y, vf.x, v[2 * k + 1]));
+                            v[8 + 2 * k] = fmaf(q.x, wf.x, fmaf(q.y, wf.y, v[8 + 2 * k]));
+                            v[9 + 2 * k] = fmaf(q.x, wf.y, fmaf(-q.y, wf.x, v[9 + 2 * k]));
+                        }
+                    }
+                }
+            }
+        }
+        const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+        const float sre = warp_transpose_reduce<16, float>(v, lane);       // lane l: value l % 16
+        const float sim = __shfl_down_sync(0xffffffffu, sre, 1);
+        if (lane < 16 && (lane & 1) == 0) sm.red[wp][lane >> 1] = make_double2((double)sre, (double)sim);
+        __syncthreads();
+        const int q = threadIdx.x & 31, set = threadIdx.x >> 5;          // warp 0: a, c; warp 1: b, d
+        if (set < 2 && q < J) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int w = 0; w < kWarps; ++w) acc = cadd(acc, sm.red[w][4 * set + q]);
+            (set == 0 ? it.part1 : it.part2)[(size_t)(it.tile_off + tb) * sm.A.pv + q] = acc;
+        }
+        __syncthreads();
+    }
+
     // Y prologue: every CTA of the item reduces X's partials and forms the
     // step's coefficients; the CTA owning tile 0 also stores the columns.
     static __device__ void dy_pro(Smem& sm, int item, const Runs& R, int j, bool last) {
@@ -1162,6 +1230,17 @@ struct Phases {
         const ItemDesc& it = A.item[item];
         ItemState* S = it.st;
         const int j0 = win_start(A, j);                                    // rows j0 .. j
+        // the stored Hessenberg entries this step reads are loaded first, so
+        // their latency overlaps the reduction below
+        double2* Hw = sm.scratch;                                          // columns j0..j-2, pitch kHld
+        const int ncol = max(0, j - 1 - j0);
+        const bool hpre = ncol * kHld <= kBlock;
+        double2 hreg = make_double2(0.0, 0.0), freg = make_double2(0.0, 0.0);
+        if (hpre && threadIdx.x < ncol * kHld) {
+            const int l = j0 + threadIdx.x / kHld, i = threadIdx.x - (threadIdx.x / kHld) * kHld;
+            if (i <= l + 1) hreg = ldp(&S->H[l * (l + 3) / 2 + i]);
+        }
+        if (threadIdx.x < j) freg = ldp(((j - 1) & 1 ? S->hcol2 : S->hcol) + threadIdx.x);
         if (threadIdx.x <= j) {
             sm.ssm[threadIdx.x] = threadIdx.x < j ? 1.0 : ldd(&S->vt[j & 1]);
             if (threadIdx.x < j0) {
@@ -1176,13 +1255,15 @@ struct Phases {
             reduce_partials<float>(sm, it.part1, it, R, j + 1 - j0, sm.ssm + j0, sm.h1 + j0);      // a_i, c
             if (!last) reduce_partials<float>(sm, it.part2, it, R, j + 1 - j0, sm.ssm + j0, sm.h2 + j0);  // b_i, d
         }
-        double2* Hw = sm.scratch;                                          // columns j0..j-2, pitch kHld
-        const int ncol = max(0, j - 1 - j0);
-        for (int t = threadIdx.x; t < ncol * kHld; t += kBlock) {
-            const int l = j0 + t / kHld, i = t - (t / kHld) * kHld;
-            if (i <= l + 1) Hw[t] = ldp(&S->H[l * (l + 3) / 2 + i]);
+        if (hpre) {
+            if (threadIdx.x < ncol * kHld) Hw[threadIdx.x] = hreg;
+        } else {
+            for (int t = threadIdx.x; t < ncol * kHld; t += kBlock) {
+                const int l = j0 + t / kHld, i = t - (t / kHld) * kHld;
+                if (i <= l + 1) Hw[t] = ldp(&S->H[l * (l + 3) / 2 + i]);
+            }
         }
-        if (threadIdx.x < j) sm.hfin[threadIdx.x] = ldp(((j - 1) & 1 ? S->hcol2 : S->hcol) + threadIdx.x);
+        if (threadIdx.x < j) sm.hfin[threadIdx.x] = freg;
         __syncthreads();
         // Thread i <= j finishes row i on its own (the window sums are recomputed
         // by every such thread): nu from one reciprocal square root, row i of
@@ -1260,8 +1341,8 @@ struct Phases {
 #pragma unroll
                 for (int r = 0; r < kChunk; ++r) {
                     const int p = base + r * nthr + tid;
-                    const V u = p < pend ? ldp(uj + p) : mk2(T(0), T(0));
-                    const V w = p < pend ? ldp(wv + p) : mk2(T(0), T(0));
+                    const V u = p < pend ? ldv(uj + p) : mk2(T(0), T(0));
+                    const V w = p < pend ? ldv(wv + p) : mk2(T(0), T(0));
                     qa[r] = mk2(tq * u.x, tq * u.y);
                     va[r] = mk2(tw * w.x, tw * w.y);
                 }
@@ -1272,7 +1353,7 @@ struct Phases {
 #pragma unroll
                     for (int r = 0; r < kChunk; ++r) {
                         const int p = base + r * nthr + tid;
-                        const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                        const V u = p < pend ? ldv(uq + p) : mk2(T(0), T(0));
                         qa[r] = cfms(qa[r], ca, u);
                         va[r] = cfms(va[r], cg, u);
                     }
@@ -1348,14 +1429,14 @@ struct Phases {
 #pragma unroll
                     for (int r = 0; r < kChunk; ++r) {
                         const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
-                        const V u = p < pend ? ldp(uq + p) : mk2(T(0), T(0));
+                        const V u = p < pend ? ldv(uq + p) : mk2(T(0), T(0));
                         d[r] = cfma(d[r], c, u);
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < kChunk; ++r) {
                     const int p = p0 + (r0 + r) * kBlock + threadIdx.x;
-                    if (p < pend) x[p] = assign ? up2(d[r]) : cadd(ldp(x + p), up2(d[r]));
+                    if (p < pend) x[p] = assign ? up2(d[r]) : cadd(ldv(x + p), up2(d[r]));
                 }
             }
         }
@@ -1851,7 +1932,7 @@ __device__ void task_pole_sum(Smem& sm, int prob, int tile, int sub) {
 #pragma unroll
     for (int r = 0; r < kPsPPT; ++r) {
         const int p = p0 + r * kBlock + threadIdx.x;
-        acc[r] = p < pend ? cmul(pr.alpha0, ldp(b + p)) : make_double2(0.0, 0.0);
+        acc[r] = p < pend ? cmul(pr.alpha0, ldv(b + p)) : make_double2(0.0, 0.0);
     }
 #pragma unroll 4
     for (int k = 0; k < pr.K; ++k) {
@@ -1861,7 +1942,7 @@ __device__ void task_pole_sum(Smem& sm, int prob, int tile, int sub) {
 #pragma unroll
         for (int r = 0; r < kPsPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
-            if (p < pend) acc[r] = cfma(acc[r], al, ldp(xk + p));
+            if (p < pend) acc[r] = cfma(acc[r], al, ldv(xk + p));
         }
     }
     const V* Ug = (const V*)sm.gbasis;
@@ -1872,7 +1953,7 @@ __device__ void task_pole_sum(Smem& sm, int prob, int tile, int sub) {
 #pragma unroll
         for (int r = 0; r < kPsPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
-            if (p < pend) acc[r] = cfma(acc[r], c, up2(ldp(ui + p)));
+            if (p < pend) acc[r] = cfma(acc[r], c, up2(ldv(ui + p)));
         }
     }
 #pragma unroll
@@ -1896,7 +1977,7 @@ __device__ void task_adjoint(Smem& sm, int prob, int tile, int bs) {
 #pragma unroll
     for (int r = 0; r < kPsPPT; ++r) {
         const int p = p0 + r * kBlock + threadIdx.x;
-        g[r] = p < pend ? cmul(cconj(pr.alpha0), ldp(gin + p)) : make_double2(0.0, 0.0);
+        g[r] = p < pend ? cmul(cconj(pr.alpha0), ldv(gin + p)) : make_double2(0.0, 0.0);
         dv[r] = 0.0;
     }
 #pragma unroll 2
@@ -1908,7 +1989,7 @@ __device__ void task_adjoint(Smem& sm, int prob, int tile, int bs) {
         for (int r = 0; r < kPsPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
             if (p < pend) {
-                const double2 xv = ldp(X + p), yv = ldp(Y + p);
+                const double2 xv = ldv(X + p), yv = ldv(Y + p);
                 g[r] = cfma(g[r], cconj(al), yv);
                 dv[r] += cmul(al, cmul(cconj(yv), xv)).x;
             }
@@ -1930,8 +2011,6 @@ __device__ __forceinline__ void my_range(int ntasks, int* s, int* e) {
     *e = (int)(((long long)(blockIdx.x + 1) * ntasks) / gridDim.x);
 }
 
-// resident CTAs per SM the register budget is sized for: three for the FP32
-// basis; two for FP64 (its staging tiles limit residency to two anyway)
 // MINB: CTAs per SM the register budget is sized for (FP64: 2 at 128
 // registers, or 1 at up to 255 with wider update chunks; c64: 3).
 template <typename T, int VG, int MINB>
@@ -2025,12 +2104,18 @@ __global__ void __launch_bounds__(kBlock, MINB) engine_kernel(const __grid_const
                     t = prefix[l] + te;
                 }
                 if (!phase_sync(A, TR_DX, &tcount)) return;
+                // Each item's commit (column store and rotations) runs on a CTA
+                // without tiles when the task range leaves some (CTA b is then
+                // idle rank b - s, and items go round-robin over the idle CTAs),
+                // so the serial rotations share no SM with a sweep; otherwise on
+                // the owner of the item's tile 0.
+                const int nidle = sm.ntasks < (int)gridDim.x ? (int)gridDim.x - sm.ntasks : 0;
                 for (int t = s; t < e;) {
                     const int l = find_slot(prefix, sm.nl, t);
                     const int te = min(prefix[l + 1], e) - prefix[l];
                     const int tb = t - prefix[l];
                     P::dy_pro(sm, list[l], item_runs(prefix, l, sm.ntasks), j, last);
-                    if (tb == 0) {
+                    if (tb == 0 && nidle == 0) {
                         // warp 0 applies the rotations while warps 1.. sweep this CTA's tiles
                         dy_commit(A, sm, list[l], j, last, ws, 2 * kTile * sizeof(*ws));
                         if (!last && threadIdx.x >= 32) P::dy(sm, list[l], tb, te, j, threadIdx.x - 32, kBlock - 32);
@@ -2039,6 +2124,13 @@ __global__ void __launch_bounds__(kBlock, MINB) engine_kernel(const __grid_const
                         P::dy(sm, list[l], tb, te, j, threadIdx.x, kBlock);
                     }
                     t = prefix[l] + te;
+                }
+                if (nidle > 0 && s == e) {
+                    for (int l = (int)blockIdx.x - s; l < sm.nl; l += nidle) {
+                        P::dy_pro(sm, list[l], item_runs(prefix, l, sm.ntasks), j, last);
+                        dy_commit(A, sm, list[l], j, last, ws, 2 * kTile * sizeof(*ws));
+                        __syncthreads();
+                    }
                 }
                 if (!phase_sync(A, TR_DY, &tcount)) return;
             }
@@ -2141,7 +2233,7 @@ __global__ void __launch_bounds__(kBlock) cheb_kernel(const __grid_constant__ Ch
     for (int k = N - 1; k >= 1; --k) {
         const double2 ck = __ldg(a.coef + k);
         for (int p = gt; p < n; p += gs) {
-            const double2 h = stencil_apply<double, double2>(X, p, pr, diag, a0, a1, a2, zero);
+            const double2 h = stencil_apply<double, double2, false>(X, p, pr, diag, a0, a1, a2, zero);
             const double2 u = ldp(a.psi + p);
             const double2 y = ldp(Y + p);
             // b_k = c_k u + 2 Ht b_{k+1} - b_{k+2}, three fused multiply-adds per component
@@ -2158,7 +2250,7 @@ __global__ void __launch_bounds__(kBlock) cheb_kernel(const __grid_constant__ Ch
         const double2 u = ldp(a.psi + p);
         double2 r = cmul(c0, u);
         if (N > 0) {
-            const double2 h = stencil_apply<double, double2>(X, p, pr, diag, a0, a1, a2, zero);
+            const double2 h = stencil_apply<double, double2, false>(X, p, pr, diag, a0, a1, a2, zero);
             const double2 y = ldp(Y + p);
             r = make_double2(r.x + a.scale * h.x - y.x, r.y + a.scale * h.y - y.y);
         }
