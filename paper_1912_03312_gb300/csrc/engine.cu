@@ -1123,7 +1123,9 @@ struct Phases {
         V* U = (V*)it.basis;
         const V* uj = U + (size_t)j * n;
         V* wv = U + (size_t)(j + 1) * n;
-        const T tj = (T)ldd(&it.st->vt[j & 1]);
+        // v_j = t_j u_j: t_0 = 1/beta of the cycle's start (s[0]); every later
+        // v_j is stored unscaled by the previous step's sweep, t_j = 1
+        const T tj = j == 0 ? (T)ldd(&it.st->s[0]) : T(1);
         const V shift = item_shift<V>(it);
         const T* diag = prob_diag<T>(pr);
         const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
@@ -1242,7 +1244,7 @@ struct Phases {
         }
         if (threadIdx.x < j) freg = ldp(((j - 1) & 1 ? S->hcol2 : S->hcol) + threadIdx.x);
         if (threadIdx.x <= j) {
-            sm.ssm[threadIdx.x] = threadIdx.x < j ? 1.0 : ldd(&S->vt[j & 1]);
+            sm.ssm[threadIdx.x] = (threadIdx.x < j || j > 0) ? 1.0 : ldd(&S->s[0]);   // t_j (X phase)
             if (threadIdx.x < j0) {
                 sm.h1[threadIdx.x] = make_double2(0.0, 0.0);
                 sm.h2[threadIdx.x] = make_double2(0.0, 0.0);
@@ -1371,6 +1373,63 @@ struct Phases {
         }
     }
 
+    // Y for a run of one tile swept by the whole CTA, with at most two older
+    // vectors in the window: the sweep's loads (u_j, w and the window
+    // vectors) are issued before the prologue, whose reduction and
+    // coefficient recurrences then hide their latency.  The arithmetic is
+    // the one of dy, in the same order.  Needs the register budget of one
+    // CTA per SM (4 vectors x kPPT points per thread).
+    static __device__ void dy_pre(Smem& sm, int item, const Runs& R, int tb, int j) {
+        const ItemDesc& it = sm.A.item[item];
+        const int it_n = it.n, it_tile = it.tile;
+        const size_t n = (size_t)it_n;
+        V* U = (V*)it.basis;
+        V* uj = U + (size_t)j * n;
+        V* wv = U + (size_t)(j + 1) * n;
+        const int j0 = win_start(sm.A, j);
+        const int nq = j - j0;                                  // 0, 1 or 2
+        const int p0 = tb * it_tile, pend = min(it_n, p0 + it_tile);
+        const V zero = mk2(T(0), T(0));
+        V u[kPPT], w[kPPT], q0[kPPT], q1[kPPT];
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            const bool in = p < pend;
+            u[r] = in ? ldv(uj + p) : zero;
+            w[r] = in ? ldv(wv + p) : zero;
+            q0[r] = (in && nq > 0) ? ldv(U + (size_t)j0 * n + p) : zero;
+            q1[r] = (in && nq > 1) ? ldv(U + (size_t)(j0 + 1) * n + p) : zero;
+        }
+        dy_pro(sm, item, R, j, false);
+        if (threadIdx.x == 0) {
+            sm.nbytes += (unsigned long long)(run_points(it_n, it_tile, tb, tb + 1) * ((nq + 4) * (long long)sizeof(V)));
+            if (sizeof(T) == 8)
+                sm.nflops += (unsigned long long)(run_points(it_n, it_tile, tb, tb + 1) * (16 * nq + 12));
+        }
+        const T tq = (T)sm.yscal[1], tw = (T)sm.yscal[2];
+        const V gq = cvt2<V>(sm.ygq);
+        const V ca0 = nq > 0 ? coef_at<V>(sm, j0) : zero, cg0 = nq > 0 ? coefg_at<V>(sm, j0) : zero;
+        const V ca1 = nq > 1 ? coef_at<V>(sm, j0 + 1) : zero, cg1 = nq > 1 ? coefg_at<V>(sm, j0 + 1) : zero;
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) {
+            const int p = p0 + r * kBlock + threadIdx.x;
+            V qa = mk2(tq * u[r].x, tq * u[r].y), va = mk2(tw * w[r].x, tw * w[r].y);
+            if (nq > 0) {
+                qa = cfms(qa, ca0, q0[r]);
+                va = cfms(va, cg0, q0[r]);
+            }
+            if (nq > 1) {
+                qa = cfms(qa, ca1, q1[r]);
+                va = cfms(va, cg1, q1[r]);
+            }
+            va = cfms(va, gq, qa);
+            if (p < pend) {
+                uj[p] = qa;
+                wv[p] = va;
+            }
+        }
+    }
+
     // E2 prologue: y = R^{-1} g (back substitution, FP64), coefficients y_i s_i.
     static __device__ void e2_pro(Smem& sm, int item) {
         __syncthreads();                       // the previous run's sweep has read kk and basis
@@ -1473,7 +1532,6 @@ __device__ void item_e4(const EngineArgs& A, int item, const Runs& R, const int*
     if (it.is_group) {                              // shared Krylov basis of the members
         if (cycles == 0 && beta > 0.0 && beta <= 1e300) {
             S->s[0] = 1.0 / beta;
-            S->vt[0] = 1.0 / beta;
             S->k = 0;
             S->cycles = 1;
             S->total_iters = 0;
@@ -1496,7 +1554,6 @@ __device__ void item_e4(const EngineArgs& A, int item, const Runs& R, const int*
         status = shared ? ST_SHARED : ST_ARNOLDI;
         S->shared = shared ? 1 : 0;
         S->s[0] = 1.0 / beta;
-        S->vt[0] = 1.0 / beta;
         S->g[0] = make_double2(beta, 0.0);
         S->k = 0;
         S->cycles = cycles + 1;
@@ -1806,7 +1863,6 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
     }
     if (j >= 1 && threadIdx.x <= j) S->H[(j - 1) * (j + 2) / 2 + threadIdx.x] = sm.hfin[threadIdx.x];
     if (!last && threadIdx.x <= j) ((j & 1) ? S->hcol2 : S->hcol)[threadIdx.x] = sm.hnew[threadIdx.x];
-    if (threadIdx.x == 0) S->vt[(j + 1) & 1] = 1.0;                 // v_{j+1} is stored raw
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
     if (!it.is_group) {
@@ -2114,6 +2170,11 @@ __global__ void __launch_bounds__(kBlock, MINB) engine_kernel(const __grid_const
                     const int l = find_slot(prefix, sm.nl, t);
                     const int te = min(prefix[l + 1], e) - prefix[l];
                     const int tb = t - prefix[l];
+                    if (MINB == 1 && !last && !(tb == 0 && nidle == 0) && te - tb == 1 && j - win_start(A, j) <= 2) {
+                        P::dy_pre(sm, list[l], item_runs(prefix, l, sm.ntasks), tb, j);
+                        t = prefix[l] + te;
+                        continue;
+                    }
                     P::dy_pro(sm, list[l], item_runs(prefix, l, sm.ntasks), j, last);
                     if (tb == 0 && nidle == 0) {
                         // warp 0 applies the rotations while warps 1.. sweep this CTA's tiles

@@ -95,13 +95,12 @@ struct ItemState {
     int sub_iters, sub_cycles, sum_k2, shared;
     int ydone, pad_y;                      // ST_DIRECT: y computed
     double bnorm, beta, cycle_tol_abs, relres;
-    double s[kMaxM + 1];
+    double s[kMaxM + 1];                   // CGS2: column scales; s[0] = 1/beta of the cycle's start
     double cs[kMaxM];
     double2 sn[kMaxM];
     double2 g[kMaxM + 1];
     double2 hcol[kMaxM + 1];               // pending column (CGS2; delayed CGS2: even steps)
     double2 hcol2[kMaxM + 1];              // delayed CGS2: pending column of odd steps
-    double vt[2];                          // delayed CGS2: scale of v_j, by parity of j
     double2 R[kMaxM * (kMaxM + 1) / 2];    // packed upper triangle, column j at j(j+1)/2
     double2 H[kMaxM * (kMaxM + 3) / 2];    // unrotated Hessenberg, column l (l+2 entries) at l(l+3)/2
     double2 y[kMaxM];                      // ST_DIRECT poles: least-squares solution on the shared basis
