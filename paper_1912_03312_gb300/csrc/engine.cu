@@ -94,9 +94,10 @@ __device__ __forceinline__ float2 cfms(float2 acc, float2 c, float2 u) {
 //
 // Vector data (basis vectors, w, x, the step states) is loaded with plain
 // loads, which may be served by L1: every read of such data is separated from
-// the stores it depends on by a grid barrier (release by the arriving CTAs,
-// ld.acquire.gpu plus fence by each waiting CTA, then a CTA barrier), so by the
-// PTX memory model the load observes those stores whatever the cache operator.
+// the stores it depends on by a grid barrier (fence and arrival by each CTA,
+// release by the completing one, ld.acquire.gpu by each waiting CTA, then a
+// CTA barrier), so by the PTX memory model the load observes those stores
+// whatever the cache operator.
 // The stencil's neighbour loads then mostly hit the lines of the CTA's own
 // centre loads.
 __device__ __forceinline__ float2 ldv(const float2* p) { return *p; }
@@ -132,24 +133,29 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// All CTAs of the co-resident (cooperative) grid meet here.  Every wait is
-// bounded by timeout_ns; on expiry the sticky error word is set and every CTA
-// leaves the kernel at its next barrier.  Returns false when the launch must end.
+// All CTAs of the co-resident (cooperative) grid meet here.  bar[0] counts
+// arrivals and bar[1] completed barriers; both are zeroed before every launch.
+// The arrival that makes the count a multiple of the grid size completes
+// barrier count / G and publishes that number with a release store; every
+// other CTA waits until the published number reaches its own barrier's (the
+// count never resets, so no generation word has to be read before arriving).
+// Every wait is bounded by timeout_ns; on expiry the sticky error word is set
+// and every CTA leaves the kernel at its next barrier.  Returns false when the
+// launch must end.
 __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long timeout_ns) {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned* count = bar;
-        unsigned* gen = bar + 1;
-        const unsigned g = ld_acquire_u32(gen);
-        __threadfence();
+        unsigned* done = bar + 1;
+        __threadfence();                                   // the CTA's writes before its arrival
         const unsigned prev = atomicAdd(count, 1u);
-        if (prev == gridDim.x - 1) {
-            atomicExch(count, 0u);
+        const unsigned target = prev / gridDim.x + 1u;     // the barrier this arrival belongs to
+        if (prev + 1u == target * gridDim.x) {
             __threadfence();
-            st_release_u32(gen, g + 1u);
+            st_release_u32(done, target);
         } else {
             const unsigned long long t0 = global_ns();
-            while (ld_acquire_u32(gen) == g) {
+            while ((int)(ld_acquire_u32(done) - target) < 0) {
                 if (global_ns() - t0 > timeout_ns) {
                     atomicExch(err, kErrTimeout);
                     break;
@@ -157,7 +163,6 @@ __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long timeout_ns
                 __nanosleep(32);
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return *(volatile int*)err == 0;

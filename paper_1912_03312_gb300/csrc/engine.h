@@ -127,7 +127,7 @@ struct EngineArgs {
     unsigned long long timeout_ns;
     const ProblemDesc* prob;
     const ItemDesc* item;
-    unsigned* bar;       // [2]: count, generation
+    unsigned* bar;       // [2]: arrivals, completed barriers (zeroed before every launch)
     unsigned* epoch;     // bumped when an Arnoldi item leaves the Arnoldi state (list rebuilds)
     int* err;            // sticky error word
     unsigned long long* trace;   // optional: [1 + 2*cap] (count, then (phase, ns) pairs)
@@ -157,7 +157,7 @@ struct ChebArgs {
     int N;
     int n;
     double scale;                // 1 / (tau W)
-    unsigned* bar;               // [2] grid barrier
+    unsigned* bar;               // [2] grid barrier: arrivals, completed barriers (zeroed per launch)
     int* err;
     unsigned long long timeout_ns;
     unsigned long long* counters;   // optional [2]: algorithmic bytes, FP64 flops
