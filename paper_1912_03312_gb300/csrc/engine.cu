@@ -133,6 +133,54 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// ---- bulk copies into shared memory (1D, completion on an mbarrier) ---------
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+// One arrival that also announces the bytes the phase's copies will deliver.
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Global to shared copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) whose completion is counted on mbarrier b.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+// Orders this thread's generic-proxy accesses before its later bulk copies.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+// Bounded wait for phase `parity` of mbarrier b.  On expiry the sticky error
+// word is set and a second bounded wait gives copies still in flight time to
+// land before the buffer is reused; the launch then ends at its next barrier.
+__device__ bool mbar_wait(unsigned long long* b, unsigned parity, int* err, unsigned long long timeout_ns) {
+    unsigned long long t0 = global_ns();
+    while (!mbar_test(b, parity)) {
+        if (global_ns() - t0 > timeout_ns) {
+            atomicExch(err, kErrTimeout);
+            t0 = global_ns();
+            while (!mbar_test(b, parity) && global_ns() - t0 <= timeout_ns) {
+            }
+            return false;
+        }
+    }
+    return true;
+}
+
 // All CTAs of the co-resident (cooperative) grid meet here.  bar[0] counts
 // arrivals and bar[1] completed barriers; both are zeroed before every launch.
 // The arrival that makes the count a multiple of the grid size completes
@@ -230,6 +278,8 @@ __device__ __forceinline__ double2 shfl2(double2 v, int src) {
 struct Smem {
     EngineArgs A;
     IOArgs io;
+    unsigned long long mbar;       // completion of the X phase's bulk copies
+    unsigned mphase;               // its current phase parity
     double2 red[kWarps][32];
     double redn[kWarps];
     double2 h1[kMaxM + 1];
@@ -420,26 +470,21 @@ __device__ __forceinline__ Nb neighbours(int p, int nx, int ny, int nz) {
 // and the pole shift fused.
 // t A u at point p with the scale t folded into the coefficients (at = t a_d,
 // st = t shift): sum_d at_d (u_{p+e_d} + u_{p-e_d}) + (t diag_p - st) u_p.
+// The arithmetic of t A u at one point from its loaded neighbours (x, y, z
+// pairs; dims of them used) and diagonal entry dg.
 template <typename T, typename V>
-__device__ __forceinline__ V stencil_scaled(const V* __restrict__ u, int p, const ProblemDesc& pr,
-                                            const T* __restrict__ diag, T t, T a0t, T a1t, T a2t, V st, V c) {
-    const Nb b = neighbours(p, pr.nx, pr.ny, pr.nz);
-    V s;
-    {
-        const V l = ldv(u + b.xm), r = ldv(u + b.xp);
-        s = mk2(a0t * (l.x + r.x), a0t * (l.y + r.y));
+__device__ __forceinline__ V stencil_combine(V c, V xl, V xr, V yl, V yr, V zl, V zr, int dims, T dg, T t,
+                                             T a0t, T a1t, T a2t, V st) {
+    V s = mk2(a0t * (xl.x + xr.x), a0t * (xl.y + xr.y));
+    if (dims > 1) {
+        s.x += a1t * (yl.x + yr.x);
+        s.y += a1t * (yl.y + yr.y);
     }
-    if (pr.ny > 1) {
-        const V l = ldv(u + b.ym), r = ldv(u + b.yp);
-        s.x += a1t * (l.x + r.x);
-        s.y += a1t * (l.y + r.y);
+    if (dims > 2) {
+        s.x += a2t * (zl.x + zr.x);
+        s.y += a2t * (zl.y + zr.y);
     }
-    if (pr.nz > 1) {
-        const V l = ldv(u + b.zm), r = ldv(u + b.zp);
-        s.x += a2t * (l.x + r.x);
-        s.y += a2t * (l.y + r.y);
-    }
-    const T dd = fmat(__ldg(diag + p), t, -st.x);
+    const T dd = fmat(dg, t, -st.x);
     s.x = fmat(dd, c.x, s.x);
     s.y = fmat(dd, c.y, s.y);
     if (st.y != T(0)) {                 // uniform: a shared basis has no shift
@@ -447,6 +492,18 @@ __device__ __forceinline__ V stencil_scaled(const V* __restrict__ u, int p, cons
         s.y = fmat(-st.y, c.x, s.y);
     }
     return s;
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ V stencil_scaled(const V* __restrict__ u, int p, const ProblemDesc& pr,
+                                            const T* __restrict__ diag, T t, T a0t, T a1t, T a2t, V st, V c) {
+    const Nb b = neighbours(p, pr.nx, pr.ny, pr.nz);
+    const int dims = 1 + (pr.ny > 1) + (pr.nz > 1);
+    const V z = mk2(T(0), T(0));
+    const V xl = ldv(u + b.xm), xr = ldv(u + b.xp);
+    const V yl = dims > 1 ? ldv(u + b.ym) : z, yr = dims > 1 ? ldv(u + b.yp) : z;
+    const V zl = dims > 2 ? ldv(u + b.zm) : z, zr = dims > 2 ? ldv(u + b.zp) : z;
+    return stencil_combine<T, V>(c, xl, xr, yl, yr, zl, zr, dims, __ldg(diag + p), t, a0t, a1t, a2t, st);
 }
 
 // kL1: vector loads that may be served by L1 (ldv) or L2-only loads (ldp).
@@ -1146,7 +1203,15 @@ struct Phases {
         if (sizeof(T) == 8)
             acctf(sm, run_points(it_n, it_tile, tb, te), matvec ? stencil_flops(pr) : 0);
         if (matvec && j + 1 - j0 <= 4) {
-            dx_window(sm, it, U0, uj, wv, n, pr, diag, tj, a0t, a1t, a2t, sht, tjf, tb, te, j + 1 - j0);
+            // staged neighbours: FP64 basis (16-byte entries, so every piece is a
+            // legal bulk copy), one CTA per SM (registers for the prefetched
+            // vectors), 1D/2D grids whose tile and halos fit the buffer
+            const int halo = pr.ny > 1 ? pr.nx : 1;
+            if (sizeof(T) == 8 && MINB == 1 && pr.nz == 1 && it_tile + 2 * halo <= 2 * kTile)
+                dx_window_staged(sm, wsv, it, U0, uj, wv, n, pr, diag, tj, a0t, a1t, a2t, sht, tjf, tb, te,
+                                 j + 1 - j0);
+            else
+                dx_window(sm, it, U0, uj, wv, n, pr, diag, tj, a0t, a1t, a2t, sht, tjf, tb, te, j + 1 - j0);
             return;
         }
         const DotPlan d = dot_plan(j + 1 - j0, it_tile);
@@ -1216,6 +1281,11 @@ struct Phases {
                 }
             }
         }
+        window_finish(sm, it, tb, J, v);
+    }
+
+    // The run's partials of a windowed X step from the per-thread sums v.
+    static __device__ void window_finish(Smem& sm, const ItemDesc& it, int tb, int J, float (&v)[16]) {
         const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
         const float sre = warp_transpose_reduce<16, float>(v, lane);       // lane l: value l % 16
         const float sim = __shfl_down_sync(0xffffffffu, sre, 1);
@@ -1228,6 +1298,91 @@ struct Phases {
             (set == 0 ? it.part1 : it.part2)[(size_t)(it.tile_off + tb) * sm.A.pv + q] = acc;
         }
         __syncthreads();
+    }
+
+    // dx_window on a 1D or 2D grid with the staging buffer `stage` (2 kTile
+    // vector entries): the tile and one halo on each side (a row in 2D, a
+    // point in 1D) form a contiguous range of points up to the periodic wrap,
+    // which at most three bulk copies bring into shared memory; the window
+    // vectors and the diagonal of the thread's points are loaded meanwhile,
+    // and the stencil reads its neighbours from the staged range.  The
+    // arithmetic is the one of dx_window (stencil_combine), point by point.
+    static __device__ void dx_window_staged(Smem& sm, V* stage, const ItemDesc& it, const V* U0, const V* uj,
+                                            V* wv, size_t n, const ProblemDesc& pr, const T* diag, T tj, T a0t,
+                                            T a1t, T a2t, V sht, float tjf, int tb, int te, int J) {
+        const int it_n = it.n, it_tile = it.tile;
+        const int nx = pr.nx;
+        const bool two = pr.ny > 1;
+        const int H = two ? nx : 1;
+        const V zero = mk2(T(0), T(0));
+        unsigned par = sm.mphase;                   // written by thread 0 before the last grid barrier
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = 0.f;
+        for (int tile = tb; tile < te; ++tile) {
+            const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
+            const int cnt = pend - p0 + 2 * H;      // staged points p0 - H .. pend + H - 1 (mod n)
+            __syncthreads();                        // earlier readers of the buffer are done
+            if (threadIdx.x == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(&sm.mbar, (unsigned)cnt * (unsigned)sizeof(V));
+                for (int done = 0; done < cnt;) {
+                    int g = p0 - H + done;
+                    g = g < 0 ? g + it_n : (g >= it_n ? g - it_n : g);
+                    const int len = min(cnt - done, it_n - g);
+                    bulk_g2s(stage + done, uj + g, (unsigned)len * (unsigned)sizeof(V), &sm.mbar);
+                    done += len;
+                }
+            }
+            V q0[kPPT], q1[kPPT], q2[kPPT];
+            T dg[kPPT];
+#pragma unroll
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                const bool in = p < pend;
+                dg[r] = in ? __ldg(diag + p) : T(0);
+                q0[r] = (in && J > 1) ? ldv(U0 + p) : zero;
+                q1[r] = (in && J > 2) ? ldv(U0 + n + p) : zero;
+                q2[r] = (in && J > 3) ? ldv(U0 + 2 * n + p) : zero;
+            }
+            mbar_wait(&sm.mbar, par, sm.A.err, sm.A.timeout_ns);
+            par ^= 1u;
+#pragma unroll
+            for (int r = 0; r < kPPT; ++r) {
+                const int p = p0 + r * kBlock + threadIdx.x;
+                if (p < pend) {
+                    const int lp = p - p0 + H;
+                    const V u = stage[lp];
+                    V xl, xr;
+                    if (two) {
+                        const int ix = p % nx;
+                        xl = stage[ix == 0 ? lp + nx - 1 : lp - 1];
+                        xr = stage[ix == nx - 1 ? lp - nx + 1 : lp + 1];
+                    } else {
+                        xl = stage[lp - 1];
+                        xr = stage[lp + 1];
+                    }
+                    const V yl = two ? stage[lp - nx] : zero, yr = two ? stage[lp + nx] : zero;
+                    const V w = stencil_combine<T, V>(u, xl, xr, yl, yr, zero, zero, two ? 2 : 1, dg[r], tj, a0t,
+                                                      a1t, a2t, sht);
+                    wv[p] = w;
+                    const float2 uf = dot_f2(u), wf = dot_f2(w);
+                    const float2 vf = make_float2(tjf * uf.x, tjf * uf.y);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (k < J) {
+                            const float2 q = k == J - 1 ? uf : dot_f2(k == 0 ? q0[r] : (k == 1 ? q1[r] : q2[r]));
+                            v[2 * k] = fmaf(q.x, vf.x, fmaf(q.y, vf.y, v[2 * k]));
+                            v[2 * k + 1] = fmaf(q.x, vf.y, fmaf(-q.y, vf.x, v[2 * k + 1]));
+                            v[8 + 2 * k] = fmaf(q.x, wf.x, fmaf(q.y, wf.y, v[8 + 2 * k]));
+                            v[9 + 2 * k] = fmaf(q.x, wf.y, fmaf(-q.y, wf.x, v[9 + 2 * k]));
+                        }
+                    }
+                }
+            }
+        }
+        if (threadIdx.x == 0) sm.mphase = par;
+        window_finish(sm, it, tb, J, v);
     }
 
     // Y prologue: every CTA of the item reduces X's partials and forms the
@@ -2078,9 +2233,13 @@ template <typename T, int VG, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) engine_kernel(const __grid_constant__ EngineArgs gA,
                                                             const __grid_constant__ IOArgs gio) {
     typedef Phases<T, VG, MINB> P;
-    extern __shared__ int dyn[];
+    extern __shared__ __align__(16) int dyn[];
     __shared__ Smem sm;
-    if (threadIdx.x == 0) sm.A = gA;
+    if (threadIdx.x == 0) {
+        sm.A = gA;
+        mbar_init(&sm.mbar, 1);
+        sm.mphase = 0;
+    }
     for (int q = threadIdx.x; q < kMaxBatch; q += kBlock) {
         sm.io.in[q] = gio.in[q];
         sm.io.out[q] = gio.out[q];
