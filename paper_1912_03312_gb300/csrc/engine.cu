@@ -613,8 +613,8 @@ __device__ __forceinline__ Runs item_runs(const int* prefix, int l, int T) {
 // Each warp's lanes split into nvp-wide groups (nvp = nv rounded up to a power
 // of two) that stride over the runs; the groups are summed with shuffles and
 // the warps through shared memory (one block barrier).  AT is the accumulation
-// type: float where the partials are FP32 inner products (the one-reduction
-// Arnoldi), double otherwise.
+// type and the stored format: float2 partials where they are FP32 inner
+// products (the one-reduction Arnoldi), double2 otherwise (CGS2).
 template <typename AT>
 __device__ void reduce_partials(Smem& sm, const double2* part, const ItemDesc& it, const Runs& R, int nv,
                                 const double* scale, double2* out) {
@@ -624,14 +624,20 @@ __device__ void reduce_partials(Smem& sm, const double2* part, const ItemDesc& i
     const int v = lane & (nvp - 1), rl = lane / nvp, rpw = 32 / nvp;
     AT ax = AT(0), ay = AT(0);
     if (v < nv) {
-        const double2* pv = part + (size_t)it.tile_off * sm.A.pv + v;
+        const size_t off = (size_t)it.tile_off * sm.A.pv + v;
 #pragma unroll 4
         for (int r = warp * rpw + rl; r < R.count; r += rpw * kWarps) {
             const int tl = R.tile(r);
             if (tl >= 0) {
-                const double2 q = ldp(pv + (size_t)tl * sm.A.pv);
-                ax += (AT)q.x;
-                ay += (AT)q.y;
+                if (sizeof(AT) == 4) {
+                    const float2 q = ldp((const float2*)part + off + (size_t)tl * sm.A.pv);
+                    ax += (AT)q.x;
+                    ay += (AT)q.y;
+                } else {
+                    const double2 q = ldp(part + off + (size_t)tl * sm.A.pv);
+                    ax += (AT)q.x;
+                    ay += (AT)q.y;
+                }
             }
         }
     }
@@ -664,12 +670,12 @@ __device__ void reduce_partials2(Smem& sm, const double2* partA, const double2* 
         for (int r = warp * rpw + rl; r < R.count; r += rpw * kWarps) {
             const int tl = R.tile(r);
             if (tl >= 0) {
-                const double2 qa = ldp(partA + off + (size_t)tl * sm.A.pv);
-                const double2 qb = ldp(partB + off + (size_t)tl * sm.A.pv);
-                ax += (float)qa.x;
-                ay += (float)qa.y;
-                bx += (float)qb.x;
-                by += (float)qb.y;
+                const float2 qa = ldp((const float2*)partA + off + (size_t)tl * sm.A.pv);
+                const float2 qb = ldp((const float2*)partB + off + (size_t)tl * sm.A.pv);
+                ax += qa.x;
+                ay += qa.y;
+                bx += qb.x;
+                by += qb.y;
             }
         }
     }
@@ -912,8 +918,9 @@ struct Phases {
         }
     }
 
-    // End of a run: partial dots of the warps' vectors into part[tb][0..J).
-    template <typename AT>
+    // End of a run: partial dots of the warps' vectors into part[tb][0..J),
+    // stored as float2 (kF32: the one-reduction Arnoldi) or double2 (CGS2).
+    template <bool kF32, typename AT>
     static __device__ void dot_finish(Smem& sm, const ItemDesc& it, double2* part, int tb, int J,
                                       const DotPlan& d, AT (&ar)[4], AT (&ai)[4]) {
         const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -933,7 +940,9 @@ struct Phases {
                 const int vpw = kWarps / J;
                 for (int w = q * vpw; w < (q + 1) * vpw; ++w) acc = cadd(acc, sm.red[w][0]);
             }
-            part[(size_t)(it.tile_off + tb) * sm.A.pv + q] = acc;
+            const size_t at = (size_t)(it.tile_off + tb) * sm.A.pv + q;
+            if (kF32) ((float2*)part)[at] = make_float2((float)acc.x, (float)acc.y);
+            else part[at] = acc;
         }
         __syncthreads();
     }
@@ -962,7 +971,8 @@ struct Phases {
                 const int vpw = kWarps / J;
                 for (int w = q * vpw; w < (q + 1) * vpw; ++w) acc = cadd(acc, sm.red[w][4 * set]);
             }
-            (set == 0 ? it.part1 : it.part2)[(size_t)(it.tile_off + tb) * sm.A.pv + q] = acc;
+            ((float2*)(set == 0 ? it.part1 : it.part2))[(size_t)(it.tile_off + tb) * sm.A.pv + q] =
+                make_float2((float)acc.x, (float)acc.y);
         }
         __syncthreads();
     }
@@ -1035,7 +1045,7 @@ struct Phases {
             dot_tile(U, n, ws, p0, pend, d, ar, ai);
             __syncthreads();
         }
-        dot_finish(sm, it, it.part1, tb, j + 1, d, ar, ai);
+        dot_finish<false>(sm, it, it.part1, tb, j + 1, d, ar, ai);
     }
 
     // P2 prologue: h1_i = s_i sum p1_i; coefficients s_i h1_i of u_i.
@@ -1073,7 +1083,7 @@ struct Phases {
             dot_tile(U, n, ws, p0, pend, d, ar, ai);
             __syncthreads();
         }
-        dot_finish(sm, it, it.part2, tb, j + 1, d, ar, ai);
+        dot_finish<false>(sm, it, it.part2, tb, j + 1, d, ar, ai);
     }
 
     // P3 prologue: h = h1 + h2; coefficients s_i h_i.
@@ -1241,7 +1251,7 @@ struct Phases {
             __syncthreads();
         }
         if (matvec) dot_finish2(sm, it, tb, j + 1 - j0, d, ar, ai, br, bi);
-        else dot_finish(sm, it, it.part1, tb, j + 1 - j0, d, ar, ai);
+        else dot_finish<true>(sm, it, it.part1, tb, j + 1 - j0, d, ar, ai);
     }
 
     // X for a step with at most 4 vectors in the window (slots j0 .. j): every
@@ -1289,13 +1299,18 @@ struct Phases {
         const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
         const float sre = warp_transpose_reduce<16, float>(v, lane);       // lane l: value l % 16
         const float sim = __shfl_down_sync(0xffffffffu, sre, 1);
-        if (lane < 16 && (lane & 1) == 0) sm.red[wp][lane >> 1] = make_double2((double)sre, (double)sim);
+        float2* redf = (float2*)sm.red;                                   // [kWarps][8]
+        if (lane < 16 && (lane & 1) == 0) redf[wp * 8 + (lane >> 1)] = make_float2(sre, sim);
         __syncthreads();
         const int q = threadIdx.x & 31, set = threadIdx.x >> 5;          // warp 0: a, c; warp 1: b, d
         if (set < 2 && q < J) {
-            double2 acc = make_double2(0.0, 0.0);
-            for (int w = 0; w < kWarps; ++w) acc = cadd(acc, sm.red[w][4 * set + q]);
-            (set == 0 ? it.part1 : it.part2)[(size_t)(it.tile_off + tb) * sm.A.pv + q] = acc;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int w = 0; w < kWarps; ++w) {
+                const float2 t = redf[w * 8 + 4 * set + q];
+                acc.x += t.x;
+                acc.y += t.y;
+            }
+            ((float2*)(set == 0 ? it.part1 : it.part2))[(size_t)(it.tile_off + tb) * sm.A.pv + q] = acc;
         }
         __syncthreads();
     }
@@ -1467,10 +1482,12 @@ struct Phases {
                 if (i < j) {
                     const double2 ca = cscale(sm.h1[i], sm.ssm[i] * inv);  // q_j = t_j/nu u_j - sum ca_i u_i
                     sm.coef[i] = ca;
-                    sm.coeff[i] = make_float2((float)ca.x, (float)ca.y);
                     const double2 cg = cscale(gam, sm.ssm[i]);              // v_{j+1} = w/nu - sum cg_i u_i - gam_j q_j
                     sm.coefG[i] = cg;
-                    sm.coefGf[i] = make_float2((float)cg.x, (float)cg.y);
+                    if (sizeof(T) == 4) {                                   // rounded copies for a c64 basis
+                        sm.coeff[i] = make_float2((float)ca.x, (float)ca.y);
+                        sm.coefGf[i] = make_float2((float)cg.x, (float)cg.y);
+                    }
                 } else {
                     sm.ygq = gam;                                           // gamma_j
                 }
