@@ -685,18 +685,23 @@ __device__ void reduce_partials2(Smem& sm, const double2* partA, const double2* 
         bx += __shfl_xor_sync(0xffffffffu, bx, o);
         by += __shfl_xor_sync(0xffffffffu, by, o);
     }
+    float2* redf = (float2*)sm.red;                                   // [kWarps][32]
     if (rl == 0) {
-        sm.red[warp][v] = make_double2((double)ax, (double)ay);
-        sm.red[warp][16 + v] = make_double2((double)bx, (double)by);
+        redf[warp * 32 + v] = make_float2(ax, ay);
+        redf[warp * 32 + 16 + v] = make_float2(bx, by);
     }
     __syncthreads();
     if (threadIdx.x < 2 * nv) {
         const int t = threadIdx.x < nv ? threadIdx.x : threadIdx.x - nv;
         const int col = threadIdx.x < nv ? t : 16 + t;
-        double2 s2 = make_double2(0.0, 0.0);
+        float sx = 0.f, sy = 0.f;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) s2 = cadd(s2, sm.red[w][col]);
-        (threadIdx.x < nv ? outA : outB)[t] = cscale(s2, scale[t]);
+        for (int w = 0; w < kWarps; ++w) {
+            const float2 q = redf[w * 32 + col];
+            sx += q.x;
+            sy += q.y;
+        }
+        (threadIdx.x < nv ? outA : outB)[t] = cscale(make_double2((double)sx, (double)sy), scale[t]);
     }
     __syncthreads();
 }
