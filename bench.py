@@ -158,11 +158,13 @@ def algorithmic_bytes(st, n, K, s_bytes, n_sub):
     return tot
 
 
-def roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, survey_bytes, flops_per_step, ms):
+def roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, survey_bytes, flops_per_step, ms,
+             ctas_per_sm=0):
     """The engine kernel against HBM (kernel-counted bytes) and, for the FP64
     path, against the FP64 ALU (kernel-counted flops); the roof it is nearer
     is reported, the other beside it."""
-    kernel = "engine_kernel<%s> (one launch per step)" % ("float, 32" if args.precision == "mixed" else "double, 16")
+    inst = "float, 32, 3" if args.precision == "mixed" else ("double, 16, 1" if ctas_per_sm == 1 else "double, 16, 2")
+    kernel = "engine_kernel<%s> (one launch per step)" % inst
     hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
            "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
            "algorithmic_bytes_per_launch": bytes_per_step,
@@ -495,7 +497,7 @@ def ours(args):
                        "autotuned": tuned},
             "grid_pts_poles_per_s": value * n * K * info["n_sub"],
             "roofline": roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, survey_bytes,
-                                 flops_per_step, ms),
+                                 flops_per_step, ms, (tuned or {}).get("ctas_per_sm", 0)),
             "cpu_baseline": cpu,
             "e2e": None if e2e_s is None else {"value": job_throughput(1, ws, e2e_s * 1e3), "unit": "REXI steps/s",
                                                "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 16 * n},

@@ -291,6 +291,14 @@ int rexi_substep_static(const rexi_grid* g, const double* V, double tau, double 
 /* Status of the last call on the plan (synchronises the plan's last stream). */
 int rexi_plan_last_status(rexi_plan* plan);
 
+/* Limit of every device-side wait of the plan's launches (grid barriers,
+ * bulk-copy completions): seconds > 0, at most 3600; seconds <= 0 restores the
+ * default of 4 s.  A wait that runs out sets the launch's error word, every CTA
+ * leaves the kernel at its next barrier, and the call (or
+ * rexi_plan_last_status) returns REXI_ETIMEOUT; the context stays usable.
+ * REXI_EINVAL for a NULL plan, NaN or more than an hour. */
+int rexi_plan_set_timeout(rexi_plan* plan, double seconds);
+
 /* Work decomposition of the plan's launches (the autotuner's knobs):
  * pole_tile / group_tile = points per task of pole items / shared-cycle group
  * items, each a multiple of 256 up to 2048; ctas_per_sm caps the resident CTAs

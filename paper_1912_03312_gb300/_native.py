@@ -80,6 +80,7 @@ SIGNATURES = {
     "rexi_plan_last_launches": (C.c_int, [_P]),
     "rexi_plan_set_trace": (C.c_int, [_P, C.c_int]),
     "rexi_plan_set_tiles": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
+    "rexi_plan_set_timeout": (C.c_int, [_P, C.c_double]),
     "rexi_plan_read_trace": (C.c_int, [_P, C.POINTER(C.c_longlong), C.c_int]),
     "rexi_plan_set_cta_trace": (C.c_int, [_P, C.c_int]),
     "rexi_cheb_step": (C.c_int, [_P, _P, _P, C.c_double, _P, C.POINTER(C.c_int)]),

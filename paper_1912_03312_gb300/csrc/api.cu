@@ -62,6 +62,7 @@ struct rexi_plan {
     int tile_group = rexi::kBlock * 2;           // points per tile of shared-cycle group items
     int max_tiles = 0;                           // partial-buffer slots per item (256-point tiles)
     int ctas_per_sm = 0;                         // 0: as many as fit
+    unsigned long long timeout_ns = kTimeoutNs;  // limit of every device-side wait
     int warn = REXI_OK;
     // device memory
     std::vector<void*> allocs;
@@ -360,7 +361,7 @@ EngineArgs base_args(const rexi_plan* p, int mode, const DescSet& set, int nprob
     A.window = p->opt.window;
     A.tol = p->tol;
     A.inner_tol = p->fp32 ? p->opt.inner_tol : 0.0;
-    A.timeout_ns = kTimeoutNs;
+    A.timeout_ns = p->timeout_ns;
     A.prob = set.d_prob;
     A.item = set.d_items;
     A.bar = p->d_bar;
@@ -781,7 +782,7 @@ int rexi_cheb_step(rexi_plan* p, const void* psi_in, void* psi_out, double tol, 
     a.scale = 1.0 / (p->tau * p->W);
     a.bar = p->d_bar;
     a.err = p->d_err;
-    a.timeout_ns = kTimeoutNs;
+    a.timeout_ns = p->timeout_ns;
     a.counters = p->d_bytes;
     const int maxg = rexi::cheb_max_grid(p->device);
     if (maxg <= 0) return p->last_status = REXI_ECUDA;
@@ -1033,6 +1034,13 @@ int rexi_plan_last_status(rexi_plan* p) {
 }
 
 int rexi_plan_last_launches(const rexi_plan* p) { return p ? p->last_launches : 0; }
+
+int rexi_plan_set_timeout(rexi_plan* p, double seconds) {
+    if (!p || !(seconds == seconds) || seconds > 3600.0) return REXI_EINVAL;
+    if (seconds <= 0.0) p->timeout_ns = kTimeoutNs;
+    else p->timeout_ns = std::max(1ull, (unsigned long long)(seconds * 1e9));
+    return REXI_OK;
+}
 
 int rexi_plan_set_tiles(rexi_plan* p, int pole_tile, int group_tile, int ctas_per_sm) {
     if (!p) return REXI_EINVAL;

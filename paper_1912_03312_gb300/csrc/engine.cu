@@ -165,15 +165,17 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
 // Bounded wait for phase `parity` of mbarrier b.  On expiry the sticky error
-// word is set and a second bounded wait gives copies still in flight time to
-// land before the buffer is reused; the launch then ends at its next barrier.
+// word is set and a second wait (at least 10 ms, whatever the limit) gives
+// copies still in flight time to land before the buffer is reused or the CTA
+// leaves; the launch then ends at its next barrier.
 __device__ bool mbar_wait(unsigned long long* b, unsigned parity, int* err, unsigned long long timeout_ns) {
     unsigned long long t0 = global_ns();
     while (!mbar_test(b, parity)) {
         if (global_ns() - t0 > timeout_ns) {
             atomicExch(err, kErrTimeout);
+            const unsigned long long drain = timeout_ns > 10000000ull ? timeout_ns : 10000000ull;
             t0 = global_ns();
-            while (!mbar_test(b, parity) && global_ns() - t0 <= timeout_ns) {
+            while (!mbar_test(b, parity) && global_ns() - t0 <= drain) {
             }
             return false;
         }
@@ -722,13 +724,10 @@ __device__ __forceinline__ int win_start(const EngineArgs& A, int j) {
     return A.window > 0 ? max(0, j - A.window) : 0;
 }
 
-// Residual estimate |g_{k+1}| of a cycle with k columns as a bound on the
-// true residual: with a windowed basis the columns are orthonormal only
-// locally, and ||r|| <= sqrt(k + 1) |g_{k+1}| (unit columns).
-__device__ __forceinline__ double res_bound(const EngineArgs& A, double res, int k) {
-    return A.window > 0 ? res * sqrt((double)(k + 1)) : res;
-}
-// Its square from g_{k+1} (no square root on the per-step path).
+// Square of the residual estimate |g_{k+1}| of a cycle with k columns taken
+// as a bound on the true residual: with a windowed basis the columns are
+// orthonormal only locally, and ||r|| <= sqrt(k + 1) |g_{k+1}| (unit columns).
+// Squared, so the per-step test needs no square root.
 __device__ __forceinline__ double res2_bound(const EngineArgs& A, double2 g, int k) {
     const double r2 = g.x * g.x + g.y * g.y;
     return A.window > 0 ? r2 * (double)(k + 1) : r2;
@@ -1056,7 +1055,6 @@ struct Phases {
     // P2 prologue: h1_i = s_i sum p1_i; coefficients s_i h1_i of u_i.
     static __device__ void p2_pro(Smem& sm, int item, const Runs& R, int j) {
         const ItemDesc& it = sm.A.item[item];
-        const int it_n = it.n, it_tile = it.tile;
         load_scales(sm, it.st, j + 1);
         reduce_partials<double>(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);
         if (threadIdx.x <= j) {
@@ -1094,7 +1092,6 @@ struct Phases {
     // P3 prologue: h = h1 + h2; coefficients s_i h_i.
     static __device__ void p3_pro(Smem& sm, int item, const Runs& R, int j) {
         const ItemDesc& it = sm.A.item[item];
-        const int it_n = it.n, it_tile = it.tile;
         load_scales(sm, it.st, j + 1);
         reduce_partials<double>(sm, it.part1, it, R, j + 1, sm.ssm, sm.h1);
         reduce_partials<double>(sm, it.part2, it, R, j + 1, sm.ssm, sm.h2);
@@ -1616,7 +1613,6 @@ struct Phases {
     static __device__ void e2_pro(Smem& sm, int item) {
         __syncthreads();                       // the previous run's sweep has read kk and basis
         const ItemDesc& it = sm.A.item[item];
-        const int it_n = it.n, it_tile = it.tile;
         const ItemState* S = it.st;
         const int k = ldi(&S->k);
         const bool shared = ldi(&S->shared) != 0;

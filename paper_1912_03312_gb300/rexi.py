@@ -248,6 +248,10 @@ class Plan:
               4: "CGS sweep 2", 5: "CGS update", 6: "Givens", 7: "x update", 8: "pole sum",
               9: "DCGS2 matvec + dots", 10: "DCGS2 update + Givens", 99: "launch"}
 
+    def set_timeout(self, seconds=0.0):
+        """Limit of every device-side wait (``rexi_plan_set_timeout``; <= 0: the 4 s default)."""
+        N.check(N.load().rexi_plan_set_timeout(self._h, float(seconds)), "rexi_plan_set_timeout")
+
     def set_trace(self, capacity=65536):
         N.check(N.load().rexi_plan_set_trace(self._h, int(capacity)), "rexi_plan_set_trace")
 
