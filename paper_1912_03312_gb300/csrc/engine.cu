@@ -486,7 +486,9 @@ __device__ __forceinline__ V stencil_combine(V c, V xl, V xr, V yl, V yr, V zl, 
         s.x += a2t * (zl.x + zr.x);
         s.y += a2t * (zl.y + zr.y);
     }
-    const T dd = fmat(dg, t, -st.x);
+    // t = 1 and no shift (the shared basis after its first step): dd = dg
+    // exactly, so the FMA is skipped (uniform branch)
+    const T dd = (t == T(1) && st.x == T(0)) ? dg : fmat(dg, t, -st.x);
     s.x = fmat(dd, c.x, s.x);
     s.y = fmat(dd, c.y, s.y);
     if (st.y != T(0)) {                 // uniform: a shared basis has no shift
