@@ -294,7 +294,7 @@ struct Smem {
     double2 hnew[kMaxM + 2];       // Y: column j (pending)
     double2 coefG[kMaxM + 1];      // Y: coefficients of v_{j+1}
     float2 coefGf[kMaxM + 1];
-    double yscal[4];               // Y: nu, t_j / nu, 1 / nu
+    double yscal[4];               // Y: nu, s_j = t_j / nu, t_{j+1} = 1 / nu, 1 / t_j
     double gcs_s[kMaxM];           // Y: staged Givens cosines of the committed item
     double2 gsn_s[kMaxM];          //    and sines
     double2 ygq;                   // Y: gamma_j (coefficient of q_j in v_{j+1})
@@ -1199,9 +1199,9 @@ struct Phases {
         V* U = (V*)it.basis;
         const V* uj = U + (size_t)j * n;
         V* wv = U + (size_t)(j + 1) * n;
-        // v_j = t_j u_j: t_0 = 1/beta of the cycle's start (s[0]); every later
-        // v_j is stored unscaled by the previous step's sweep, t_j = 1
-        const T tj = j == 0 ? (T)ldd(&it.st->s[0]) : T(1);
+        // v_j = t_j x slot j (t_0 = 1/beta; later t_j = 1/nu_{j-1}, set by the
+        // previous step's commit)
+        const T tj = (T)ldp(&it.st->vt[j & 1]).x;
         const V shift = item_shift<V>(it);
         const T* diag = prob_diag<T>(pr);
         const T a0 = prob_a<T>(pr, 0), a1 = prob_a<T>(pr, 1), a2 = prob_a<T>(pr, 2);
@@ -1423,7 +1423,10 @@ struct Phases {
         }
         if (threadIdx.x < j) freg = ldp(((j - 1) & 1 ? S->hcol2 : S->hcol) + threadIdx.x);
         if (threadIdx.x <= j) {
-            sm.ssm[threadIdx.x] = (threadIdx.x < j || j > 0) ? 1.0 : ldd(&S->s[0]);   // t_j (X phase)
+            // s_i of the window's stored columns, t_j of the stored v_j
+            sm.ssm[threadIdx.x] = threadIdx.x < j ? (threadIdx.x >= j0 ? ldd(&S->s[threadIdx.x]) : 1.0)
+                                                  : ldp(&S->vt[j & 1]).x;
+            if (threadIdx.x == j) sm.yscal[3] = ldp(&S->vt[j & 1]).y;                // 1/t_j
             if (threadIdx.x < j0) {
                 sm.h1[threadIdx.x] = make_double2(0.0, 0.0);
                 sm.h2[threadIdx.x] = make_double2(0.0, 0.0);
@@ -1468,8 +1471,8 @@ struct Phases {
             }
             if (i == 0) {
                 sm.yscal[0] = nu;
-                sm.yscal[1] = sm.ssm[j] * inv;
-                sm.yscal[2] = inv;
+                sm.yscal[1] = sm.ssm[j] * inv;                              // s_j = t_j / nu
+                sm.yscal[2] = inv;                                          // t_{j+1} = 1 / nu
             }
             if (!last) {
                 double2 Ha = make_double2(0.0, 0.0);                        // (H a)_i over columns l < j
@@ -1483,17 +1486,22 @@ struct Phases {
                 else h = cscale(csub(cscale(csub(sm.h2[j], ab), inv), Ha), inv);
                 sm.hnew[i] = h;
                 const double2 gam = cadd(cscale(Ha, inv), h);
+                // The sweep stores q_j and v_{j+1} unnormalised, with the scale
+                // of each folded into its coefficients (no multiply per point):
+                //   slot j   <- u_j - sum_i ca_i u_i,            q_j     = (t_j / nu) slot j,
+                //   slot j+1 <- w - sum_i cg_i u_i - gq slot j,  v_{j+1} = (1 / nu) slot j+1,
+                // u_i the stored window columns (q_i = s_i u_i), u_j = slot j, w = A v_j.
                 if (i < j) {
-                    const double2 ca = cscale(sm.h1[i], sm.ssm[i] * inv);  // q_j = t_j/nu u_j - sum ca_i u_i
+                    const double2 ca = cscale(sm.h1[i], sm.ssm[i] * sm.yscal[3]);   // a_i s_i / t_j
                     sm.coef[i] = ca;
-                    const double2 cg = cscale(gam, sm.ssm[i]);              // v_{j+1} = w/nu - sum cg_i u_i - gam_j q_j
+                    const double2 cg = cscale(gam, sm.ssm[i] * nu);                 // gamma_i s_i nu
                     sm.coefG[i] = cg;
                     if (sizeof(T) == 4) {                                   // rounded copies for a c64 basis
                         sm.coeff[i] = make_float2((float)ca.x, (float)ca.y);
                         sm.coefGf[i] = make_float2((float)cg.x, (float)cg.y);
                     }
                 } else {
-                    sm.ygq = gam;                                           // gamma_j
+                    sm.ygq = cscale(gam, sm.ssm[j]);                                // gamma_j t_j
                 }
             }
         }
@@ -1509,13 +1517,12 @@ struct Phases {
         V* U = (V*)it.basis;
         V* uj = U + (size_t)j * n;
         V* wv = U + (size_t)(j + 1) * n;
-        const T tq = (T)sm.yscal[1], tw = (T)sm.yscal[2];
         const V gq = cvt2<V>(sm.ygq);
         const int j0 = win_start(sm.A, j);
         if (tid == 0) {
             sm.nbytes += (unsigned long long)(run_points(it_n, it_tile, tb, te) * ((j - j0 + 4) * (long long)sizeof(V)));
             if (sizeof(T) == 8)
-                sm.nflops += (unsigned long long)(run_points(it_n, it_tile, tb, te) * (16 * (j - j0) + 12));
+                sm.nflops += (unsigned long long)(run_points(it_n, it_tile, tb, te) * (16 * (j - j0) + 8));
         }
         for (int tile = tb; tile < te; ++tile) {
             const int p0 = tile * it_tile, pend = min(it_n, p0 + it_tile);
@@ -1524,10 +1531,8 @@ struct Phases {
 #pragma unroll
                 for (int r = 0; r < kChunk; ++r) {
                     const int p = base + r * nthr + tid;
-                    const V u = p < pend ? ldv(uj + p) : mk2(T(0), T(0));
-                    const V w = p < pend ? ldv(wv + p) : mk2(T(0), T(0));
-                    qa[r] = mk2(tq * u.x, tq * u.y);
-                    va[r] = mk2(tw * w.x, tw * w.y);
+                    qa[r] = p < pend ? ldv(uj + p) : mk2(T(0), T(0));
+                    va[r] = p < pend ? ldv(wv + p) : mk2(T(0), T(0));
                 }
 #pragma unroll 2
                 for (int q = j0; q < j; ++q) {
@@ -1585,16 +1590,15 @@ struct Phases {
         if (threadIdx.x == 0) {
             sm.nbytes += (unsigned long long)(run_points(it_n, it_tile, tb, tb + 1) * ((nq + 4) * (long long)sizeof(V)));
             if (sizeof(T) == 8)
-                sm.nflops += (unsigned long long)(run_points(it_n, it_tile, tb, tb + 1) * (16 * nq + 12));
+                sm.nflops += (unsigned long long)(run_points(it_n, it_tile, tb, tb + 1) * (16 * nq + 8));
         }
-        const T tq = (T)sm.yscal[1], tw = (T)sm.yscal[2];
         const V gq = cvt2<V>(sm.ygq);
         const V ca0 = nq > 0 ? coef_at<V>(sm, j0) : zero, cg0 = nq > 0 ? coefg_at<V>(sm, j0) : zero;
         const V ca1 = nq > 1 ? coef_at<V>(sm, j0 + 1) : zero, cg1 = nq > 1 ? coefg_at<V>(sm, j0 + 1) : zero;
 #pragma unroll
         for (int r = 0; r < kPPT; ++r) {
             const int p = p0 + r * kBlock + threadIdx.x;
-            V qa = mk2(tq * u[r].x, tq * u[r].y), va = mk2(tw * w[r].x, tw * w[r].y);
+            V qa = u[r], va = w[r];
             if (nq > 0) {
                 qa = cfms(qa, ca0, q0[r]);
                 va = cfms(va, cg0, q0[r]);
@@ -1624,7 +1628,7 @@ struct Phases {
         for (int t = threadIdx.x; t < nR; t += kBlock) Rs[t] = ldp(&S->R[t]);
         if (threadIdx.x < k) {
             sm.gsm[threadIdx.x] = ldp(&S->g[threadIdx.x]);
-            sm.ssm[threadIdx.x] = sm.A.ortho ? 1.0 : ldd(&src.st->s[threadIdx.x]);
+            sm.ssm[threadIdx.x] = ldd(&src.st->s[threadIdx.x]);
         }
         if (threadIdx.x == 0) {
             sm.kk = k;
@@ -1712,6 +1716,7 @@ __device__ void item_e4(const EngineArgs& A, int item, const Runs& R, const int*
     if (it.is_group) {                              // shared Krylov basis of the members
         if (cycles == 0 && beta > 0.0 && beta <= 1e300) {
             S->s[0] = 1.0 / beta;
+            S->vt[0] = make_double2(1.0 / beta, beta);
             S->k = 0;
             S->cycles = 1;
             S->total_iters = 0;
@@ -1734,6 +1739,7 @@ __device__ void item_e4(const EngineArgs& A, int item, const Runs& R, const int*
         status = shared ? ST_SHARED : ST_ARNOLDI;
         S->shared = shared ? 1 : 0;
         S->s[0] = 1.0 / beta;
+        S->vt[0] = make_double2(1.0 / beta, beta);
         S->g[0] = make_double2(beta, 0.0);
         S->k = 0;
         S->cycles = cycles + 1;
@@ -1844,7 +1850,7 @@ __device__ void load_problem_items(Smem& sm, int prob) {
                 kmax = max(kmax, kk);
                 if (i < kk) acc = cadd(acc, cmul(sm.alpha[k], ldp(&M->y[i])));
             }
-            const double si = A.ortho ? 1.0 : ldd(&gd.st->s[i]);
+            const double si = ldd(&gd.st->s[i]);
             sm.yhat[i] = cscale(acc, si);
             if (i == 0) {
                 sm.kyhat = kmax;
@@ -2043,6 +2049,10 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
     }
     if (j >= 1 && threadIdx.x <= j) S->H[(j - 1) * (j + 2) / 2 + threadIdx.x] = sm.hfin[threadIdx.x];
     if (!last && threadIdx.x <= j) ((j & 1) ? S->hcol2 : S->hcol)[threadIdx.x] = sm.hnew[threadIdx.x];
+    if (!last && threadIdx.x == 0) {                 // scales of the swept slots j and j + 1
+        S->s[j] = sm.yscal[1];
+        S->vt[(j + 1) & 1] = make_double2(sm.yscal[2], sm.yscal[0]);
+    }
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
     if (!it.is_group) {

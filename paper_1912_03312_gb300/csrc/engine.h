@@ -95,7 +95,10 @@ struct ItemState {
     int sub_iters, sub_cycles, sum_k2, shared;
     int ydone, pad_y;                      // ST_DIRECT: y computed
     double bnorm, beta, cycle_tol_abs, relres;
-    double s[kMaxM + 1];                   // CGS2: column scales; s[0] = 1/beta of the cycle's start
+    double s[kMaxM + 1];                   // scales of the stored columns (column i = s_i x slot i);
+                                           // s[0] = 1/beta at a cycle's start
+    double2 vt[2];                         // delayed CGS2: (t_j, 1/t_j) of the stored v_j (v_j = t_j x
+                                           // slot j), by parity of j
     double cs[kMaxM];
     double2 sn[kMaxM];
     double2 g[kMaxM + 1];
