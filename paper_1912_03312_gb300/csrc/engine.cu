@@ -1366,15 +1366,22 @@ struct Phases {
             }
             mbar_wait(&sm.mbar, par, sm.A.err, sm.A.timeout_ns);
             par ^= 1u;
+            // x index of the thread's point: one division per tile, then steps
+            // of kBlock mod nx (each at most one wrap)
+            const int xstep = two ? kBlock % nx : 0;
+            int ix = two ? (p0 + (int)threadIdx.x) % nx : 0;
 #pragma unroll
             for (int r = 0; r < kPPT; ++r) {
                 const int p = p0 + r * kBlock + threadIdx.x;
+                if (r > 0 && two) {
+                    ix += xstep;
+                    if (ix >= nx) ix -= nx;
+                }
                 if (p < pend) {
                     const int lp = p - p0 + H;
                     const V u = stage[lp];
                     V xl, xr;
                     if (two) {
-                        const int ix = p % nx;
                         xl = stage[ix == 0 ? lp + nx - 1 : lp - 1];
                         xr = stage[ix == nx - 1 ? lp - nx + 1 : lp + 1];
                     } else {
