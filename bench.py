@@ -204,10 +204,16 @@ def engine_traffic(kernel_src_hash, key):
 
 
 def src_hash():
+    """SHA-256 of the engine's code with comments and whitespace removed (a
+    comment edit leaves a recorded profile valid; any code change does not)."""
+    import re
     h = hashlib.sha256()
     for f in ("engine.cu", "engine.h"):
-        with open(os.path.join(ROOT, "paper_1912_03312_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1912_03312_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update("".join(src.split()).encode())
     return h.hexdigest()
 
 

@@ -19,9 +19,10 @@
 //                  dL/dV -= tau Re sum alpha_k conj(Y_k) X_k
 //
 // A "phase" is the flat list of (item, tile) tasks of the items in the right
-// state, split evenly over the CTAs.  Partial dot products are written per tile
-// and reduced in FP64 by the CTAs of the next phase.  Basis vectors u_i are
-// stored unnormalised; v_i = s_i u_i with an FP64 scale s_i.
+// state, split evenly over the CTAs.  Partial dot products are written per run
+// and reduced (FP64 for CGS2, FP32 for the one-reduction Arnoldi) by the CTAs
+// of the next phase.  Basis vectors u_i are stored unnormalised; the column is
+// s_i u_i with an FP64 scale s_i.
 #include <algorithm>
 #include <cstdint>
 
@@ -1139,9 +1140,10 @@ struct Phases {
 
     // ---- delayed CGS2 (one global reduction per Arnoldi step) -------------
     //
-    // Entering step j, slots 0..j-1 hold the orthonormal q_0..q_{j-1} and slot
-    // j holds v_j = t_j u_j: A q_{j-1} projected once against them (j = 0: the
-    // normalised residual).  X computes w = A v_j and, in the same sweep,
+    // Entering step j, slots 0..j-1 hold the (locally) orthonormal q_0..q_{j-1}
+    // up to their scales (q_i = s_i u_i) and slot j holds v_j = t_j u_j: A q_{j-1}
+    // projected once against them (j = 0: the residual, t_0 = 1/beta).  X
+    // computes w = A v_j and, in the same sweep,
     // a = Q^H v_j, c = v_j^H v_j, b = Q^H w, d = v_j^H w.  Y reorthogonalises
     // and normalises v_j (q_j = (v_j - Q a)/nu, nu^2 = c - |a|^2), which
     // completes Hessenberg column j-1 (h += a, h_{j,j-1} = nu), and uses the
@@ -1439,7 +1441,7 @@ struct Phases {
                 sm.h2[threadIdx.x] = make_double2(0.0, 0.0);
             }
         }
-        __syncthreads();                                                   // q_i normalised; t_j
+        __syncthreads();                                                   // scales s_i, t_j
         if (!last && j + 1 - j0 <= 16) {                                   // a_i, c and b_i, d together
             reduce_partials2(sm, it.part1, it.part2, it, R, j + 1 - j0, sm.ssm + j0, sm.h1 + j0, sm.h2 + j0);
         } else {
