@@ -313,7 +313,6 @@ struct Smem {
                                    // R (E2) or Hessenberg columns (Y), kScratch entries
     double2 yhat[kMaxM];           // PS: sum of alpha_k y_k of the poles completed on the shared basis
     int kyhat;                     //     its length (0: none)
-    int ps_tile;                   //     points per pole-sum / adjoint task
     int nxlive;                    //     poles whose x the pole sum reads
     unsigned long long nbytes;     // algorithmic bytes this CTA moved (thread 0)
     unsigned long long nflops;     // FP64 flops of its arithmetic (thread 0)
@@ -415,27 +414,21 @@ __device__ void build_list(Smem& sm, int* list, int* prefix, unsigned mask, bool
 }
 
 // Problems live in (backward) substep `sub`, with their tile prefix sums.
-// The pole sum and the adjoint accumulation are FP64 work with no reuse: the
-// task size is the live points over the grid, rounded up to whole blocks (so
-// one round of tasks covers every point) and clamped to [kBlock, kBlock ppt]
-// (ppt points per thread: 8 where one CTA per SM leaves the registers, else 4).
+// The pole sum and the adjoint accumulation are FP64 work with no reuse:
+// small tasks spread them over every SM.
+constexpr int kPsPPT = 4;
+constexpr int kPsTile = kBlock * kPsPPT;
 
-__device__ void build_problem_list(Smem& sm, int* list, int* prefix, int sub, int ppt) {
+__device__ void build_problem_list(Smem& sm, int* list, int* prefix, int sub) {
     const EngineArgs& A = sm.A;
     if (threadIdx.x == 0) {
-        long long pts = 0;
-        for (int p = 0; p < A.nproblems; ++p)
-            if (sub < A.prob[p].nsub) pts += A.prob[p].n;
-        const long long per = (pts + gridDim.x - 1) / gridDim.x;
-        const int pt = (int)min((long long)kBlock * ppt, max((long long)kBlock, (per + kBlock - 1) / kBlock * kBlock));
-        sm.ps_tile = pt;
         int c = 0, t = 0;
         for (int p = 0; p < A.nproblems; ++p) {
             if (sub < A.prob[p].nsub) {
                 list[c] = p;
                 prefix[c] = t;
                 ++c;
-                t += (A.prob[p].n + pt - 1) / pt;
+                t += (A.prob[p].n + kPsTile - 1) / kPsTile;
             }
         }
         prefix[c] = t;
@@ -2181,13 +2174,13 @@ __device__ void dy_commit(const EngineArgs& A, Smem& sm, int item, int j, bool l
 
 // PS: psi' = alpha_0 b + sum_k alpha_k x_k for one tile of a problem (poles
 // completed on the shared basis enter as sum_i yhat_i u_i).
-template <typename T, int kPsPPT>
+template <typename T>
 __device__ void task_pole_sum(Smem& sm, int prob, int tile, int sub) {
     typedef typename C2<T>::t V;
     const ProblemDesc& pr = sm.A.prob[prob];
     const double2* b = step_in(sm.io, pr, prob, sub);
     double2* out = step_out(sm.io, pr, prob, sub);
-    const int p0 = tile * sm.ps_tile, pend = min(pr.n, p0 + sm.ps_tile);
+    const int p0 = tile * kPsTile, pend = min(pr.n, p0 + kPsTile);
     acct(sm, pend - p0, 32 + 16 * (long long)sm.nxlive + (long long)sm.kyhat * (long long)sizeof(V));
     acctf(sm, pend - p0, 6 + 8 * ((long long)sm.nxlive + sm.kyhat));
     double2 acc[kPsPPT];
@@ -2226,13 +2219,12 @@ __device__ void task_pole_sum(Smem& sm, int prob, int tile, int sub) {
 }
 
 // BA: adjoint accumulation for one tile of a problem (backward substep bs).
-template <int kPsPPT>
 __device__ void task_adjoint(Smem& sm, int prob, int tile, int bs) {
     const ProblemDesc& pr = sm.A.prob[prob];
     const double2* gin = adj_in(sm.io, pr, prob, bs);
     double2* gout = adj_out(sm.io, pr, prob, bs);
     double* dV = sm.io.dLdV[prob];
-    const int p0 = tile * sm.ps_tile, pend = min(pr.n, p0 + sm.ps_tile);
+    const int p0 = tile * kPsTile, pend = min(pr.n, p0 + kPsTile);
     acct(sm, pend - p0, 32 + 32 * (long long)pr.K + 16);
     acctf(sm, pend - p0, 6 + 20 * (long long)pr.K + 2);
     double2 g[kPsPPT];
@@ -2460,16 +2452,15 @@ __global__ void __launch_bounds__(kBlock, MINB) engine_kernel(const __grid_const
         }
 
         if (A.mode != MODE_SOLVE) {
-            constexpr int kPs = MINB == 1 ? 8 : 4;                  // pole-sum points per thread
-            build_problem_list(sm, list, prefix, sub, kPs);
+            build_problem_list(sm, list, prefix, sub);
             int s, e;
             my_range(sm.ntasks, &s, &e);
             int cur = -1;
             for (int t = s; t < e; ++t) {
                 const int l = find_slot(prefix, sm.nl, t);
                 if (list[l] != cur) { cur = list[l]; load_problem_items(sm, cur); }
-                if (A.mode == MODE_STEP) task_pole_sum<T, kPs>(sm, cur, t - prefix[l], sub);
-                else task_adjoint<kPs>(sm, cur, t - prefix[l], sub);
+                if (A.mode == MODE_STEP) task_pole_sum<T>(sm, cur, t - prefix[l], sub);
+                else task_adjoint(sm, cur, t - prefix[l], sub);
             }
             if (!phase_sync(A, TR_SUM, &tcount)) return;
         }
