@@ -158,7 +158,7 @@ def algorithmic_bytes(st, n, K, s_bytes, n_sub):
     return tot
 
 
-def roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, survey_bytes, flops_per_step, ms,
+def roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, independent_bytes, flops_per_step, ms,
              ctas_per_sm=0):
     """The engine kernel against HBM (kernel-counted bytes) and, for the FP64
     path, against the FP64 ALU (kernel-counted flops); the roof it is nearer
@@ -169,8 +169,8 @@ def roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, survey_by
            "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
            "algorithmic_bytes_per_launch": bytes_per_step,
            "bytes_source": "kernel count of the vectors its passes read and write",
-           "independent_pole_bytes_per_launch": survey_bytes,
-           "independent_pole_effective_gbs": survey_bytes / (ms * 1e-3) / 1e9}
+           "independent_pole_bytes_per_launch": independent_bytes,
+           "independent_pole_effective_gbs": independent_bytes / (ms * 1e-3) / 1e9}
     tf = flops_per_step / (ms * 1e-3) / 1e12
     alu = {"bound": "alu", "achieved": tf, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
            "frac": tf / NOMINAL_FP64_TFLOPS, "traffic": traffic,
@@ -459,16 +459,16 @@ def ours(args):
     # kernel's own count of the bytes its passes move, and the count of the
     # independent-pole method for context
     cur = psi0.clone()
-    alg, survey, flops = [], [], []
+    alg, indep, flops = [], [], []
     for i in range(args.steps):
         cur, st = plan.step(cur, stats=True)
         alg.append(st["bytes"])
         flops.append(st["flops64"])
-        survey.append(algorithmic_bytes(st, n, K, s_bytes, info["n_sub"]))
+        indep.append(algorithmic_bytes(st, n, K, s_bytes, info["n_sub"]))
         stats.append(st)
     bytes_per_step = statistics.mean(alg)
     flops_per_step = statistics.mean(flops)
-    survey_bytes = statistics.mean(survey)
+    independent_bytes = statistics.mean(indep)
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_per_step / (ms * 1e-3) / 1e9
     traffic = engine_traffic(src_hash(), config_key(args))
@@ -594,7 +594,7 @@ def ours(args):
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "autotuned": tuned},
             "grid_pts_poles_per_s": value * n * K * info["n_sub"],
-            "roofline": roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, survey_bytes,
+            "roofline": roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, independent_bytes,
                                  flops_per_step, ms, (tuned or {}).get("ctas_per_sm", 0)),
             "cpu_baseline": cpu,
             "cpu_baseline_all_cores": cpu_all,

@@ -21,7 +21,7 @@ Schroedinger equation" (arXiv:1912.03312):
   Eq. (8)), the Maclaurin coefficients c_j of r^cf, and the K x K linear system
   for beta.
 
-Readings of garbled or silent passages (listed in the design doc as well):
+Readings of garbled or silent passages:
 
 * In Algorithm 1 the polynomial q is v_{L+1} + v_L z + ... + v_1 z^L and p is
   u_1 + u_2 z + ... + u_{L+1} z^L (the printed indices K+1 / k+1 are typos,
