@@ -63,3 +63,31 @@ def test_wide_kernel_matches_oracle(n, box, dt, gt, window):
     assert relerr(out, default) < bound
     # the same launch twice is bitwise reproducible
     assert np.array_equal(lp.step(x).cpu().numpy(), out)
+
+
+def test_wide_kernel_batched_matches_singles_and_oracle():
+    # one launch over problems with different row lengths and dimensions: the
+    # staged stencil stages each item's own halo, and CTAs walk several tiles
+    # (the mbarrier phase flips per tile)
+    from paper_1912_03312_gb300 import autotune, step_batched
+    specs = [((130, 101), 8.0, 16, 24.0, 0.5), ((700,), 40.0, 16, 24.0, 1.0), ((256, 40), 20.0, 32, 68.0, 0.5),
+             ((24, 20, 10), 8.0, 8, 8.0, 0.2)]
+    tol = 1e-13
+    plans, psis, singles, refs = [], [], [], []
+    for i, (n, box, K, R1, dt) in enumerate(specs):
+        g, V, psi = wl.random_problem(80 + i, n, box=box)
+        lp = library_plan(g, V, dt, K, R1, precision="fp64", tol=tol, window=2, restart=64, max_iters=20000)
+        singles.append(lp.step(to_dev(psi)).cpu().numpy())
+        autotune.apply(lp, {"pole_tile": 1024, "group_tile": 1792, "ctas_per_sm": 1})
+        plans.append(lp)
+        psis.append(to_dev(psi))
+        orc = OraclePlan(g, V, dt, K, R1)
+        ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
+        refs.append((ref, orc.A))
+    outs, sts = step_batched(plans, psis, stats=True)
+    for o, s1, (ref, A), st in zip(outs, singles, refs, sts):
+        assert st["status"] == 0
+        o = o.cpu().numpy()
+        bound = max(1e-10, 2.0 * A * tol)
+        assert relerr(o, s1) < bound
+        assert relerr(o, ref) < bound
