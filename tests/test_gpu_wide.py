@@ -91,3 +91,33 @@ def test_wide_kernel_batched_matches_singles_and_oracle():
         bound = max(1e-10, 2.0 * A * tol)
         assert relerr(o, s1) < bound
         assert relerr(o, ref) < bound
+
+
+def test_wide_kernel_plane_wave_and_zero_state_512():
+    # The benchmarked configuration on exact cases: a plane wave (an
+    # eigenvector: the shared Krylov process breaks down after one step, so
+    # the published scales meet nu -> 0) is multiplied by the scalar
+    # alpha_0 + sum alpha_k / (tau lambda - z_k) of Eq. (4)-(5) per substep, and
+    # the zero state (every pole's right-hand side zero) stays exactly zero.
+    from paper_1912_03312_gb300 import autotune
+    n = (512, 512)
+    g = wl.make_grid(n, (-30.0, -30.0), (30.0, 30.0))
+    V = np.full((512, 512), -0.8)
+    lp = library_plan(g, V, 0.5, 32, 68.0, precision="fp64", window=2, restart=64)
+    autotune.apply(lp, {"pole_tile": 1024, "group_tile": 1792, "ctas_per_sm": 1})
+    X = wl.coords(g)
+    mx, my = -7, 4
+    psi = np.exp(1j * (2 * np.pi * mx * (X[0] + 30.0) / 60.0 + 2 * np.pi * my * (X[1] + 30.0) / 60.0))
+    out, st = lp.step(to_dev(psi), stats=True)
+    assert st["status"] == 0
+    z, alpha, a0, ns = lp.poles()
+    h = 60.0 / 512
+    lam = -0.8 + 0.5 * ((2 - 2 * np.cos(2 * np.pi * mx / 512)) + (2 - 2 * np.cos(2 * np.pi * my / 512))) / h ** 2
+    tau = lp.info()["tau"]
+    r = a0 + np.sum(alpha / (tau * lam - z))
+    info = lp.info()
+    out = out.cpu().numpy()
+    assert np.all(np.isfinite(out))
+    assert relerr(out, psi * r ** ns) < max(1e-9, 2.0 * info["amplification"] * info["tol"] * ns)
+    zero, stz = lp.step(torch.zeros_like(to_dev(psi)), stats=True)
+    assert stz["status"] == 0 and float(zero.abs().max()) == 0.0
