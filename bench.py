@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--restart", type=int, default=0,
                     help="GMRES restart length (0: 64 with a window, 30 without)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-workers", type=int, default=0,
+                    help="processes for the all-cores oracle timings (0: every host core)")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -333,7 +335,9 @@ def run_parallel_sample(R1, tol, workers, nsteps, budget):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def host_cores():
+def host_cores(requested=0):
+    if requested > 0:
+        return requested
     try:
         return len(os.sched_getaffinity(0))
     except AttributeError:
@@ -349,7 +353,7 @@ def reference_arm(args):
     n = 512 * 512
     # whole user steps of the oracle (n_sub rounds of K pole solves, one solve
     # per task) on all host cores; at most about three minutes of wall time
-    cores = host_cores()
+    cores = host_cores(args.cpu_workers)
     d = run_parallel_sample(68.0, 4e-14, cores, args.warmup + args.steps, 180.0)
     st = d["step_seconds"]
     timed = st[args.warmup:] if len(st) > args.warmup else st[-1:]
@@ -565,7 +569,7 @@ def ours(args):
             cpu = {"value": None, "unit": "REXI steps/s", "cores": 1, "kind": "oracle", "sample": "failed: %s" % e}
     cpu_all = None
     if rank == 0 and not args.no_cpu_baseline:
-        cores = host_cores()
+        cores = host_cores(args.cpu_workers)
         try:
             d = run_parallel_sample(R1, 4e-14, cores, 2, 20.0)
             t = d["step_seconds"][-1]
