@@ -203,10 +203,6 @@ int rexi_step(rexi_plan* plan, const void* psi_in, void* psi_out, void* stream, 
 int rexi_step_host(rexi_plan* plan, const double* psi_in, double* psi_out, void* stream,
                    rexi_stats* st);
 
-/* B independent problems (each with its own plan, grid, K and n_sub) in one
- * persistent launch: all problems x all poles share the GPU.  All plans must
- * be on the same device and have the same precision, restart length and orthogonalisation.
- * psi_in[b], psi_out[b] : device c128 of plan b's size.  st: B entries or NULL. */
 /* The Chebyshev propagator the paper compares REXI with (Sec. 4): psi_out =
  * p(Ht) psi_in with p(x) = sum_{k<=N} a_k T_k(x) approximating exp(-i R x) on
  * [-1, 1], Ht = (H - c)/W on the plan's spectral enclosure, R = dt W / hbar,
@@ -222,6 +218,13 @@ int rexi_step_host(rexi_plan* plan, const double* psi_in, double* psi_out, void*
 int rexi_cheb_step(rexi_plan* plan, const void* psi_in, void* psi_out, double tol, void* stream,
                    int* degree);
 
+/* B independent problems (each with its own plan, grid, K and n_sub) in one
+ * persistent launch: all problems x all poles share the GPU (the K solves of
+ * every problem are the independent tasks of Sec. 3.1).  All plans must be on
+ * the same device and have the same precision, restart length and
+ * orthogonalisation; B <= 128.
+ * psi_in[b], psi_out[b] : device c128 of plan b's size.  st: B entries or NULL
+ * (with st the call synchronises and returns the first failing status). */
 int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
                       void* const* psi_out, void* stream, rexi_stats* st);
 
@@ -258,7 +261,7 @@ int rexi_pole_sum(rexi_plan* plan, const void* psi, const void* x, void* out, vo
  * allocate device memory: code running inside a custom allocator or memory-pool
  * callback, hosts that reserve all GPU memory for themselves up front, and
  * sandboxes in which cudaMalloc is unavailable.  rexi_plan_create allocates, so
- * these callers use this call instead: one rational evaluation of Eq. (5),
+ * these callers use this call instead: one rational evaluation
  *     psi_out = alpha0 psi_in + sum_k alpha_k (tau H - z_k I)^{-1} psi_in,
  * with every byte of engine workspace taken from a fixed 32 MiB array compiled
  * into the library (REXI_STATIC_SCRATCH_BYTES; every GPU that loads the library
@@ -270,12 +273,21 @@ int rexi_pole_sum(rexi_plan* plan, const void* psi, const void* x, void* out, vo
  *                  (rexi_plan_info.tau and .c of an equivalent plan).
  *   K, z, alpha  : host, K poles z[2K] and weights alpha[2K] (interleaved re, im),
  *                  alpha0[2]; e.g. from rexi_plan_poles.
- *   opt          : host, precision / restart_m / tol (must be > 0) / inner_tol /
- *                  max_iters are used; NULL = defaults except tol, which is required.
+ *   opt          : host, required (NULL is REXI_EINVAL): precision, restart_m,
+ *                  max_iters, tol (finite, > 0: there is no amplification-based
+ *                  default here), inner_tol (finite, >= 0), ortho and window
+ *                  (the orthogonalisation, validated as in rexi_plan_create)
+ *                  are used; every solve has its own basis (no shared cycle).
  *   psi_in, psi_out : device c128[n]; may be the same buffer.
- *   st           : host, may be NULL; when given the call synchronises.
- * Returns REXI_EINVAL when the workspace (about K (m+1) n 8 bytes for REXI_MIXED,
- * twice that for REXI_FP64, plus K n 16 bytes) exceeds the static array.
+ *   st           : host, may be NULL.  With st the call synchronises and
+ *                  returns REXI_ENOCONV / REXI_ETIMEOUT when a solve failed.
+ *                  Without st the call only enqueues the work and returns
+ *                  argument and launch errors: convergence failures and
+ *                  timeouts of that call are then not reported anywhere, so a
+ *                  caller that needs them passes st.
+ * Returns REXI_EINVAL for a grid of more than 2^30 points, and when the
+ * workspace (about K (m+1) n 8 bytes for REXI_MIXED, twice that for REXI_FP64,
+ * plus K n 16 bytes) exceeds the static array.
  * The first call on a device looks the array's address up (cudaGetSymbolAddress,
  * done once per device with that device current); make that first call before
  * any stream capture.  All calls share the one array and it keeps the previous

@@ -539,11 +539,11 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     double h[3] = {1.0, 1.0, 1.0};
     for (int d = 0; d < g->ndim; ++d) {
         if (g->n[d] < 1 || !(g->hi[d] > g->lo[d]) || !std::isfinite(g->hi[d] - g->lo[d])) return REXI_EINVAL;
+        if (n > (1ll << 30) / g->n[d]) return REXI_EINVAL;   // checked before the product can overflow
         dims[d] = g->n[d];
         h[d] = (g->hi[d] - g->lo[d]) / g->n[d];
         n *= g->n[d];
     }
-    if (n > (1ll << 30)) return REXI_EINVAL;
     if (!finite_all(V, (size_t)n)) return REXI_EINVAL;
 
     static std::atomic<unsigned long long> next_uid{1};

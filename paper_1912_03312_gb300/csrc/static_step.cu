@@ -62,13 +62,13 @@ extern "C" int rexi_substep_static(const rexi_grid* g, const double* V, double t
                                    const double* z, const double* alpha, const double* alpha0,
                                    const rexi_options* opt_in, const void* psi_in, void* psi_out, void* stream,
                                    rexi_stats* st) {
-    if (!g || !V || !z || !alpha || !alpha0 || !psi_in || !psi_out) return REXI_EINVAL;
+    if (!g || !V || !z || !alpha || !alpha0 || !psi_in || !psi_out || !opt_in) return REXI_EINVAL;
     if (!(tau > 0.0) || !std::isfinite(tau) || !std::isfinite(c) || K < 1 || K > REXI_MAX_POLES) return REXI_EINVAL;
     if (g->ndim < 1 || g->ndim > 3 || !(g->hbar > 0.0) || !(g->mass > 0.0)) return REXI_EINVAL;
-    rexi_options opt;
-    if (opt_in) opt = *opt_in; else rexi_options_default(&opt);
+    const rexi_options opt = *opt_in;
     if (opt.precision != REXI_FP64 && opt.precision != REXI_MIXED) return REXI_EINVAL;
-    if (opt.restart_m < 1 || opt.restart_m > REXI_MAX_RESTART || opt.max_iters < 1 || !(opt.tol > 0.0))
+    if (opt.restart_m < 1 || opt.restart_m > REXI_MAX_RESTART || opt.max_iters < 1) return REXI_EINVAL;
+    if (!(opt.tol > 0.0) || !std::isfinite(opt.tol) || !(opt.inner_tol >= 0.0) || !std::isfinite(opt.inner_tol))
         return REXI_EINVAL;
     if (opt.ortho != 0 && opt.ortho != 1) return REXI_EINVAL;
     if (opt.window == 0 && opt.restart_m > (opt.ortho == 1 ? REXI_MAX_RESTART_FULL : REXI_MAX_RESTART_FULL + 1))
@@ -79,7 +79,8 @@ extern "C" int rexi_substep_static(const rexi_grid* g, const double* V, double t
     int dims[3] = {1, 1, 1};
     double a[3] = {0.0, 0.0, 0.0};
     for (int d = 0; d < g->ndim; ++d) {
-        if (g->n[d] < 1 || !(g->hi[d] > g->lo[d])) return REXI_EINVAL;
+        if (g->n[d] < 1 || !(g->hi[d] > g->lo[d]) || !std::isfinite(g->hi[d] - g->lo[d])) return REXI_EINVAL;
+        if (n > (1ll << 30) / g->n[d]) return REXI_EINVAL;   // checked before the product can overflow
         dims[d] = g->n[d];
         n *= g->n[d];
         const double h = (g->hi[d] - g->lo[d]) / g->n[d];

@@ -38,3 +38,34 @@ def relerr(a, b):
     a = np.asarray(a).ravel()
     b = np.asarray(b).ravel()
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+METRIC_TOL = 1e-6     # the step error the benchmark metric allows against FP64
+
+
+def solve_tol(A, cap=1e-13):
+    """Per-pole relative residual for a step parity case: `cap`, or less where
+    the pole-sum amplification A would otherwise let two solvers that each stop
+    at that residual differ by more than the metric's 1e-6 (2 A tol <= 0.95e-6;
+    for K = 32, R1 = 68: A = 2.5e7, tol = 1.9e-14)."""
+    return min(cap, 0.475 * METRIC_TOL / A)
+
+
+def step_bound(A, tol, precision):
+    """Step tolerance of two solvers at relative residual tol: the precision's
+    floor (1e-10 FP64, 1e-6 mixed) or 2 A tol, whichever is larger."""
+    return max(1e-10 if precision == "fp64" else METRIC_TOL, 2.0 * A * tol)
+
+
+def log_parity(name, err, bound, **extra):
+    """Append one measured parity error to $REXI_PARITY_LOG (JSON lines) when
+    that variable is set; a no-op otherwise."""
+    import json
+    import os
+    path = os.environ.get("REXI_PARITY_LOG")
+    if not path:
+        return
+    rec = dict(name=name, err=float(err), bound=float(bound))
+    rec.update({k: (float(v) if isinstance(v, (int, float, np.floating)) else str(v)) for k, v in extra.items()})
+    with open(path, "a") as f:
+        f.write(json.dumps(rec) + "\n")

@@ -141,3 +141,41 @@ def test_no_device_is_an_error_not_a_fallback(lib):
     V = (C.c_double * 8)(*([0.0] * 8))
     h = C.c_void_p()
     assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 8, None) == N.REXI_ECUDA
+
+
+def test_grid_size_overflow_is_rejected_before_any_device_call(lib):
+    # Three extents whose product exceeds 2^63 (and 2^30 long before): both
+    # entry points that take a grid reject it with REXI_EINVAL before any
+    # allocation, copy or launch, so a wrapped point count can never size a
+    # buffer that the stencil then indexes past.
+    from paper_1912_03312_gb300 import _native as N
+    g = N.Grid()
+    g.ndim = 3
+    g.n[0], g.n[1], g.n[2] = 1 << 22, 1 << 22, 1 << 20
+    for d in range(3):
+        g.lo[d], g.hi[d] = -1.0, 1.0
+    g.hbar = g.mass = 1.0
+    V = (C.c_double * 8)(*([0.0] * 8))
+    h = C.c_void_p()
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, None) == N.REXI_EINVAL
+    assert h.value is None
+    o = N.Options()
+    lib.rexi_options_default(C.byref(o))
+    o.tol = 1e-12
+    z = (C.c_double * 8)(*([0.0] * 8))
+    a0 = (C.c_double * 2)(0.0, 0.0)
+    dummy = C.c_void_p(16)                      # never dereferenced: validation comes first
+    call = lambda grid, opt: lib.rexi_substep_static(C.byref(grid), dummy, 0.1, 0.0, 4, z, z, a0, opt,
+                                                      dummy, dummy, None, None)
+    assert call(g, C.byref(o)) == N.REXI_EINVAL
+    # a grid whose extent is not finite, a missing or non-finite option set
+    g.n[0], g.n[1], g.n[2] = 8, 8, 8
+    g.hi[1] = float("inf")
+    assert call(g, C.byref(o)) == N.REXI_EINVAL
+    g.hi[1] = 1.0
+    assert call(g, None) == N.REXI_EINVAL
+    o.tol = float("nan")
+    assert call(g, C.byref(o)) == N.REXI_EINVAL
+    o.tol = 1e-12
+    o.inner_tol = -1.0
+    assert call(g, C.byref(o)) == N.REXI_EINVAL

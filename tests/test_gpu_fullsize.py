@@ -22,7 +22,7 @@ import pytest
 import workloads as wl
 from oracle import step as ostep
 
-from _common import OraclePlan, library_plan, relerr, to_dev
+from _common import OraclePlan, library_plan, log_parity, relerr, solve_tol, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +53,38 @@ def test_2d_wells_512_step_matches_oracle():
     assert orc.n_sub == info["n_sub"]
     ref, _ = ostep.step(cfg["V"], orc.h, cfg["psi0"], orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0,
                         tol=1e-14)
-    assert relerr(out.cpu().numpy(), ref) < 1e-6
+    err = relerr(out.cpu().numpy(), ref)
+    log_parity("2d_wells_512_default_plan[mixed]", err, 1e-6)
+    assert err < 1e-6
+
+
+@pytest.mark.parametrize("tiles", [None, {"pole_tile": 1024, "group_tile": 1792, "ctas_per_sm": 1}])
+def test_2d_wells_512_benchmarked_path_matches_oracle(tiles):
+    # The configuration the benchmark times: FP64 basis, shared first cycle,
+    # window 2, restart 64, the plan's own tolerance, direct accumulation of the
+    # poles finished on the shared basis; under the default work decomposition
+    # and under the one-CTA-per-SM tiles the autotuner picks for this workload.
+    # Two user steps, each element-wise against the oracle's step (GMRES(30),
+    # MGS, relative residual 1e-14), to the metric's 1e-6 outright.
+    from paper_1912_03312_gb300 import autotune
+    cfg = wl.config_2d_wells()
+    g = cfg["grid"]
+    lp = _plan(cfg, g, cfg["V"], cfg["K"], precision="fp64", window=2, restart=64)
+    if tiles is not None:
+        autotune.apply(lp, tiles)
+    info = lp.info()
+    assert info["R1"] == 68.0 and info["n_sub"] == 2
+    orc = OraclePlan(g, cfg["V"], cfg["dt"], cfg["K"], info["R1"])
+    cur_gpu = to_dev(cfg["psi0"])
+    ref = cfg["psi0"]
+    for _ in range(2):
+        cur_gpu, st = lp.step(cur_gpu, stats=True)
+        assert st["status"] == 0
+        ref, _ = ostep.step(cfg["V"], orc.h, ref, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
+        err = relerr(cur_gpu.cpu().numpy(), ref)
+        log_parity("2d_wells_512_benchmarked_path[%s]" % ("default" if tiles is None else "1cta"), err, 1e-6,
+                   iters=st["total_iters"])
+        assert err < 1e-6, err
 
 
 def test_3d_coulomb_K64_is_refused():
@@ -65,13 +96,20 @@ def test_3d_coulomb_K64_is_refused():
     assert e.value.code == N.REXI_EPLAN
 
 
-def test_3d_coulomb_128_sampled_poles_and_plane_wave():
+_ORACLE_3D = {}
+
+
+@pytest.mark.parametrize("precision,tol_pole", [("mixed", 1e-6), ("fp64", 1e-10)])
+def test_3d_coulomb_128_sampled_poles_and_plane_wave(precision, tol_pole):
     cfg = wl.config_3d_coulomb()
     g = cfg["grid"]
     K = 32
-    lp = _plan(cfg, g, cfg["V"], K)
+    R1 = 68.0
+    orc = OraclePlan(g, cfg["V"], cfg["dt"], K, R1)
+    tol = solve_tol(orc.A * orc.n_sub)
+    lp = _plan(cfg, g, cfg["V"], K, precision=precision, tol=tol, max_iters=20000)
     info = lp.info()
-    orc = OraclePlan(g, cfg["V"], cfg["dt"], K, info["R1"])
+    assert info["R1"] == R1
     assert orc.n_sub == info["n_sub"] == 1
     psi = cfg["psi0"]
     x, st = lp.solve_poles(to_dev(psi), stats=True)
@@ -81,9 +119,13 @@ def test_3d_coulomb_128_sampled_poles_and_plane_wave():
     picks = sorted(set(np.argsort(-np.abs(alpha))[:2]) | set(np.argsort(np.abs(z.imag))[:2]))
     for k in picks:
         kk = int(np.argmin(np.abs(orc.z - z[k])))
-        xo, oi = ostep.solve_pole(cfg["V"], orc.h, psi, orc.tau, orc.z[kk], tol=1e-14)
-        assert oi["converged"]
-        assert relerr(x[k].cpu().numpy(), xo) < 1e-6, k
+        if kk not in _ORACLE_3D:
+            xo, oi = ostep.solve_pole(cfg["V"], orc.h, psi, orc.tau, orc.z[kk], tol=1e-14)
+            assert oi["converged"]
+            _ORACLE_3D[kk] = xo
+        err = relerr(x[k].cpu().numpy(), _ORACLE_3D[kk])
+        log_parity("3d_coulomb_128_pole[%s,%d]" % (precision, k), err, tol_pole)
+        assert err < tol_pole, (k, err)
     del x
     # whole step: the approximation is within its error of the unitary
     # propagator, so the norm changes by at most ||e|| + A delta
@@ -92,9 +134,10 @@ def test_3d_coulomb_128_sampled_poles_and_plane_wave():
     nrm0 = np.linalg.norm(psi)
     nrm1 = float(torch.linalg.vector_norm(out))
     assert abs(nrm1 - nrm0) / nrm0 < 2e-9 + 2.0 * info["amplification"] * info["tol"]
+    del out, lp
     # plane wave on a constant potential: the step is the scalar rational
     V0 = -0.3
-    lw = _plan(cfg, g, np.full(g["n"][::-1], V0), K)
+    lw = _plan(cfg, g, np.full(g["n"][::-1], V0), K, precision=precision, tol=tol, max_iters=20000)
     X = wl.coords(g)
     L = 30.0
     m = (2, -1, 3)
@@ -107,7 +150,10 @@ def test_3d_coulomb_128_sampled_poles_and_plane_wave():
     zz, aa, a0, ns = lw.poles()
     r = a0 + np.sum(aa / (lw.info()["tau"] * lam - zz))
     wi = lw.info()
-    assert relerr(ow.cpu().numpy(), wave * r ** ns) < max(1e-9, 2.0 * wi["amplification"] * wi["tol"] * ns)
+    bound = max(1e-9, 2.0 * wi["amplification"] * wi["tol"] * ns)
+    err = relerr(ow.cpu().numpy(), wave * r ** ns)
+    log_parity("3d_coulomb_128_plane_wave[%s]" % precision, err, bound)
+    assert err < bound
     assert abs(r ** ns - np.exp(-1j * cfg["dt"] * lam)) < 1e-8
 
 
@@ -115,25 +161,30 @@ def test_batched_64_problems():
     cfg = wl.config_batched()
     from paper_1912_03312_gb300 import step_batched
     probs = cfg["problems"]
-    plans = [_plan(cfg, p["grid"], p["V"], cfg["K"]) for p in probs]
+    # per-pole tolerance such that 2 A n_sub tol <= 0.95e-6 for every problem
+    orcs = [OraclePlan(p["grid"], p["V"], cfg["dt"], cfg["K"], 68.0) for p in probs]
+    tols = [solve_tol(o.A * o.n_sub) for o in orcs]
+    plans = [_plan(cfg, p["grid"], p["V"], cfg["K"], tol=t, max_iters=20000) for p, t in zip(probs, tols)]
     psis = [to_dev(p["psi0"]) for p in probs]
     singles = [pl.step(ps).cpu().numpy() for pl, ps in zip(plans, psis)]
     outs, sts = step_batched(plans, psis, stats=True)
     assert all(s["status"] == 0 for s in sts)
     # the batched grid splits tiles into runs differently, so reductions are
     # summed in another order: both are solves to the plan's tolerance
-    for o, s1, pl in zip(outs, singles, plans):
-        i = pl.info()
-        assert relerr(o.cpu().numpy(), s1) < max(1e-6, 2.0 * i["amplification"] * i["tol"] * i["n_sub"])
+    for o, s1 in zip(outs, singles):
+        assert relerr(o.cpu().numpy(), s1) < 1e-6
     again = step_batched(plans, psis)                 # a fixed launch is reproducible bit for bit
     assert all(np.array_equal(a.cpu().numpy(), o.cpu().numpy()) for a, o in zip(again, outs))
     sizes = [int(np.prod(p["grid"]["n"])) for p in probs]
     for i in sorted(range(len(probs)), key=lambda i: sizes[i])[:2]:
         p = probs[i]
-        orc = OraclePlan(p["grid"], p["V"], cfg["dt"], cfg["K"], plans[i].info()["R1"])
+        orc = orcs[i]
+        assert plans[i].info()["R1"] == 68.0
         ref, _ = ostep.step(p["V"], orc.h, p["psi0"], orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0,
                             tol=1e-14)
-        assert relerr(outs[i].cpu().numpy(), ref) < 1e-6
+        err = relerr(outs[i].cpu().numpy(), ref)
+        log_parity("batched_64_problem[%d]" % i, err, 1e-6)
+        assert err < 1e-6
 
 
 def test_learnable_256_gradient_and_adjoint_identity():

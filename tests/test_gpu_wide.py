@@ -17,7 +17,7 @@ import pytest
 import workloads as wl
 from oracle import step as ostep
 
-from _common import OraclePlan, library_plan, relerr, to_dev
+from _common import OraclePlan, library_plan, log_parity, relerr, solve_tol, step_bound, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +59,7 @@ def test_wide_kernel_matches_oracle(n, box, dt, gt, window):
     orc = OraclePlan(g, V, dt, K, R1)
     ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
     bound = max(1e-10, 2.0 * orc.A * tol)
+    log_parity("wide[L%d,%s]" % (window, "x".join(map(str, n))), relerr(out, ref), bound)
     assert relerr(out, ref) < bound
     assert relerr(out, default) < bound
     # the same launch twice is bitwise reproducible
@@ -72,23 +73,24 @@ def test_wide_kernel_batched_matches_singles_and_oracle():
     from paper_1912_03312_gb300 import autotune, step_batched
     specs = [((130, 101), 8.0, 16, 24.0, 0.5), ((700,), 40.0, 16, 24.0, 1.0), ((256, 40), 20.0, 32, 68.0, 0.5),
              ((24, 20, 10), 8.0, 8, 8.0, 0.2)]
-    tol = 1e-13
     plans, psis, singles, refs = [], [], [], []
     for i, (n, box, K, R1, dt) in enumerate(specs):
         g, V, psi = wl.random_problem(80 + i, n, box=box)
+        orc = OraclePlan(g, V, dt, K, R1)
+        tol = solve_tol(orc.A * orc.n_sub)
         lp = library_plan(g, V, dt, K, R1, precision="fp64", tol=tol, window=2, restart=64, max_iters=20000)
         singles.append(lp.step(to_dev(psi)).cpu().numpy())
         autotune.apply(lp, {"pole_tile": 1024, "group_tile": 1792, "ctas_per_sm": 1})
         plans.append(lp)
         psis.append(to_dev(psi))
-        orc = OraclePlan(g, V, dt, K, R1)
         ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
-        refs.append((ref, orc.A))
+        refs.append((ref, orc.A * orc.n_sub, tol))
     outs, sts = step_batched(plans, psis, stats=True)
-    for o, s1, (ref, A), st in zip(outs, singles, refs, sts):
+    for i, (o, s1, (ref, A, tol), st) in enumerate(zip(outs, singles, refs, sts)):
         assert st["status"] == 0
         o = o.cpu().numpy()
-        bound = max(1e-10, 2.0 * A * tol)
+        bound = step_bound(A, tol, "fp64")
+        log_parity("wide_batched[%d]" % i, relerr(o, ref), bound)
         assert relerr(o, s1) < bound
         assert relerr(o, ref) < bound
 
