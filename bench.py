@@ -4,10 +4,11 @@
 Workload: the 2D four-well problem -- 512 x 512 periodic grid on [-30, 30)^2,
 V = four Gaussian wells (seeded), Gaussian packet at (-10, 0) with k0 = (3, 0),
 K = 32 FCF poles (R1 = 68), user step dt = 0.5 (two rational substeps).  The
-timed path is the plan's FP64 path with the shared first cycle and a
-two-vector orthogonalisation window (--precision, --window select others);
-the FP64 path with full orthogonalisation is the accuracy reference and the
-mixed-precision path is timed beside it.  One benchmark step = one user step
+timed path is the FP64 shared-basis Lanczos kernel (--ortho, --precision,
+--window select the item engine's paths instead); the item engine's FP64 path
+with full orthogonalisation is the accuracy reference, and its windowed FP64
+and mixed-precision paths and the Chebyshev propagator are timed beside it.
+The first timed step is compared with the oracle's step from the same state.  One benchmark step = one user step
 psi <- S(dt) psi through rexi_step; the state evolves from step to step.
 
     python bench.py [--steps 20] [--warmup 3] [--impl ours|reference] [--gpus N]
@@ -45,10 +46,13 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64")
+    ap.add_argument("--ortho", choices=["lanczos", "dcgs2", "cgs2"], default="lanczos",
+                    help="lanczos: the shared-basis Lanczos kernel; dcgs2/cgs2: the item engine")
     ap.add_argument("--window", type=int, default=2,
-                    help="orthogonalisation window (0 = whole basis)")
+                    help="orthogonalisation window of the item engine (0 = whole basis)")
     ap.add_argument("--restart", type=int, default=0,
-                    help="GMRES restart length (0: 64 with a window, 30 without)")
+                    help="GMRES restart length (0: 64 with a window, 30 without) or, with lanczos, the "
+                         "largest Krylov dimension (0: 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-workers", type=int, default=0,
                     help="processes for the all-cores oracle timings (0: every host core)")
@@ -162,13 +166,19 @@ def algorithmic_bytes(st, n, K, s_bytes, n_sub):
     return tot
 
 
+def kernel_name(args, ctas_per_sm=0):
+    if args.ortho == "lanczos":
+        return "lanczos_kernel"
+    inst = "float, 32, 3" if args.precision == "mixed" else ("double, 16, 1" if ctas_per_sm == 1 else "double, 16, 2")
+    return "engine_kernel<%s>" % inst
+
+
 def roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, independent_bytes, flops_per_step, ms,
              ctas_per_sm=0):
-    """The engine kernel against HBM (kernel-counted bytes) and, for the FP64
-    path, against the FP64 ALU (kernel-counted flops); the roof it is nearer
-    is reported, the other beside it."""
-    inst = "float, 32, 3" if args.precision == "mixed" else ("double, 16, 1" if ctas_per_sm == 1 else "double, 16, 2")
-    kernel = "engine_kernel<%s> (one launch per step)" % inst
+    """The kernel of the timed path against HBM (kernel-counted bytes) and, for
+    the FP64 path, against the FP64 ALU (kernel-counted flops); the roof it is
+    nearer is reported, the other beside it."""
+    kernel = "%s (one launch per step)" % kernel_name(args, ctas_per_sm)
     hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
            "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
            "algorithmic_bytes_per_launch": bytes_per_step,
@@ -189,13 +199,15 @@ def roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, independe
 
 
 def config_key(args):
+    if args.ortho == "lanczos":
+        return "%s|lanczos" % args.precision
     return "%s|window=%d" % (args.precision, args.window)
 
 
 def engine_traffic(kernel_src_hash, key):
     """ncu DRAM bytes per launch recorded under profiles/, if taken on this
     source, workload and path."""
-    p = os.path.join(ROOT, "profiles", "engine_traffic.json")
+    p = os.path.join(ROOT, "profiles", "lanczos_traffic.json" if key.endswith("lanczos") else "engine_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
@@ -212,7 +224,7 @@ def src_hash():
     comment edit leaves a recorded profile valid; any code change does not)."""
     import re
     h = hashlib.sha256()
-    for f in ("engine.cu", "engine.h"):
+    for f in ("engine.cu", "engine.h", "lanczos.cu", "lanczos.h", "devsync.cuh"):
         with open(os.path.join(ROOT, "paper_1912_03312_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
@@ -444,9 +456,13 @@ def ours(args):
     n = int(np.prod(g["n"]))
     K = cfg["K"]
     R1 = 68.0
-    restart = args.restart or (64 if args.window else 30)
+    if args.ortho == "lanczos":
+        args.window = 0
+        restart = args.restart or 256
+    else:
+        restart = args.restart or (64 if args.window else 30)
     plan = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], K, precision=args.precision, R1=R1,
-                window=args.window, restart=restart)
+                window=args.window, restart=restart, ortho=args.ortho)
     info = plan.info()
     s_bytes = 8 if args.precision == "mixed" else 16
     stream = torch.cuda.current_stream()
@@ -537,8 +553,9 @@ def ours(args):
         out = plan.step(psi0)
         ref = None
         paths = {}
-        for name, prec, win in (("fp64_full", "fp64", 0), ("mixed_full", "mixed", 0), ("mixed_window", "mixed", 2)):
-            if prec == args.precision and win == args.window:
+        for name, prec, win in (("fp64_full", "fp64", 0), ("fp64_window2_engine", "fp64", 2),
+                                ("mixed_full", "mixed", 0), ("mixed_window", "mixed", 2)):
+            if prec == args.precision and win == args.window and args.ortho == "dcgs2":
                 continue
             p2 = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], K, precision=prec, R1=R1, window=win,
                       restart=64 if win else 30)
@@ -654,9 +671,9 @@ def ours(args):
             "config": {"workload": WORKLOAD if args.n == 512 else "2d_wells_%dx%d_K32_dt0.5" % (args.n, args.n),
                        "grid": list(g["n"]), "K": K, "dt": cfg["dt"], "n_sub": info["n_sub"],
                        "R1": info["R1"], "restart": info["restart_m"], "precision": args.precision,
-                       "window": args.window, "shared_first_cycle": True,
+                       "ortho": args.ortho, "window": args.window, "shared_first_cycle": True,
                        "tol": info["tol"], "amplification": info["amplification"],
-                       "l2": "flushed (256 MiB write) before every timed step; Krylov basis 2 GB > L2",
+                       "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "autotuned": tuned},
             "grid_pts_poles_per_s": value * n * K * info["n_sub"],

@@ -57,6 +57,7 @@ extern "C" {
 #define REXI_MAX_RESTART 64   /* windowed bases; with full orthogonalisation 31 (delayed
                                  CGS2) or 32 (CGS2) */
 #define REXI_MAX_RESTART_FULL 31
+#define REXI_MAX_KRYLOV  512  /* ortho = 2 (Lanczos): largest Krylov dimension per substep */
 
 /* Periodic grid: N_d points on [lo_d, hi_d), h_d = (hi_d - lo_d) / N_d,
  * points x_j = lo_d + j h_d.  ndim in {1, 2, 3}; unused n[] entries ignored. */
@@ -70,7 +71,8 @@ typedef struct {
 typedef struct {
     int    precision;      /* REXI_FP64 or REXI_MIXED (default REXI_MIXED)                */
     int    restart_m;      /* GMRES restart length (default 30): 1..REXI_MAX_RESTART with a
-                              window, else 1..REXI_MAX_RESTART_FULL (32 with CGS2)        */
+                              window, else 1..REXI_MAX_RESTART_FULL (32 with CGS2); with
+                              ortho = 2 the largest Krylov dimension, 1..REXI_MAX_KRYLOV    */
     int    max_iters;      /* Arnoldi iterations per pole solve before ENOCONV (default 2000) */
     double tol;            /* per-pole stop: ||b - A x|| <= tol ||b||; 0 = choose from the
                               pole-sum amplification (see rexi_plan_info.tol)              */
@@ -97,7 +99,20 @@ typedef struct {
                               Schmidt with reorthogonalisation, one global reduction per step
                               (the previous vector is reorthogonalised and normalised together
                               with the projection of the new one); 0: CGS2, two reductions
-                              per step                                                     */
+                              per step; 2: Lanczos -- REXI_FP64 only, window 0: every substep
+                              builds ONE basis for all K poles (the shifted-systems observation
+                              of Sec. 5) by the three-term recurrence of the real symmetric
+                              tau (H - c) with real coefficients, one global reduction and one
+                              grid barrier per step, no restarts: restart_m (up to
+                              REXI_MAX_KRYLOV) is then the largest Krylov dimension, and a pole
+                              that has not met its bound by then fails with REXI_ENOCONV.  Each
+                              pole solves its least-squares problem on the shared basis (GMRES
+                              with the columns orthonormal only locally, so the stop uses the
+                              bound sqrt(k+1) |g_{k+1}| as with a window) and the pole sum is one
+                              pass over the basis.  rexi_step and rexi_solve_poles run on this
+                              path; rexi_step_backward runs on the item engine (shared first
+                              cycle, window 2, restart min(restart_m, 64)), allocated at its
+                              first call; rexi_step_batched rejects such plans (REXI_EINVAL)  */
     int    window;         /* with ortho = 1: 0 (default) orthogonalise every new vector against
                               the whole basis; L >= 2: only against the last L vectors (a
                               truncated, quasi-GMRES basis).  H is real symmetric, so tau H - z
@@ -316,7 +331,10 @@ int rexi_plan_set_timeout(rexi_plan* plan, double seconds);
  * items, each a multiple of 256 up to 2048; ctas_per_sm caps the resident CTAs
  * per SM of the persistent grid (0 = as many as fit; 1 on an FP64 plan selects
  * the kernel compiled for one CTA per SM, with twice the registers per thread
- * and wider update sweeps).  Synchronises the device
+ * and wider update sweeps).  On a Lanczos plan (ortho = 2) group_tile bounds
+ * the interior points of the kernel's box-shaped tiles (the box is chosen to
+ * balance the CTAs' work) and ctas_per_sm (0 = 2, at most 8) sets the resident
+ * CTAs per SM; pole_tile is not used.  Synchronises the device
  * and rewrites the plan's descriptors; results do not depend on these values
  * beyond floating-point summation order. */
 int rexi_plan_set_tiles(rexi_plan* plan, int pole_tile, int group_tile, int ctas_per_sm);

@@ -27,6 +27,15 @@ DEFAULT_CANDIDATES = {
 }
 
 
+# Lanczos plans: group_tile bounds the points of a tile box, ctas_per_sm sets
+# the resident CTAs per SM; pole_tile is not used.
+LANCZOS_CANDIDATES = {
+    "pole_tile": (1024,),
+    "group_tile": (512, 768, 1024, 1280, 1536, 1792, 2048),
+    "ctas_per_sm": (1, 2),
+}
+
+
 def cache_path():
     return os.environ.get("REXI_AUTOTUNE_CACHE",
                           os.path.join(os.path.expanduser("~"), ".cache", "rexi_autotune.json"))
@@ -75,7 +84,7 @@ def autotune(plan, psi, candidates=None, steps=3, use_cache=True):
         apply(plan, cfg)
         cfg["cached"] = True
         return cfg
-    cand = candidates or DEFAULT_CANDIDATES
+    cand = candidates or (LANCZOS_CANDIDATES if plan.opts.ortho == 2 else DEFAULT_CANDIDATES)
     stream = torch.cuda.current_stream()
     out = torch.empty_like(psi)
     best = None

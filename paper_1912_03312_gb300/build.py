@@ -2,8 +2,8 @@
 
     python -m paper_1912_03312_gb300.build [--force]
 
-Three translation units are compiled in parallel (the CUDA engine, the C ABI,
-and the host-side FCF construction in double-double arithmetic, which needs
+The translation units are compiled in parallel (the CUDA engine, the shared-basis
+Lanczos kernel, the C ABI, the allocation-free entry point, and the host-side FCF construction in double-double arithmetic, which needs
 floating-point contraction disabled) and linked with the shared CUDA runtime.
 """
 
@@ -55,6 +55,8 @@ def build(force=False, verbose=False):
         [nvcc] + ARCH + common + ["-c", os.path.join(CSRC, "api.cu"), "-o", os.path.join(BUILD, "api.o")],
         [nvcc] + ARCH + common + ["-c", os.path.join(CSRC, "static_step.cu"),
                                   "-o", os.path.join(BUILD, "static_step.o")],
+        [nvcc] + ARCH + common + ["-lineinfo", "-c", os.path.join(CSRC, "lanczos.cu"),
+                                  "-o", os.path.join(BUILD, "lanczos.o")],
         ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-c", os.path.join(CSRC, "fcf.cpp"),
          "-o", os.path.join(BUILD, "fcf.o")],
     ]
@@ -72,6 +74,7 @@ def build(force=False, verbose=False):
     link = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp,
                             os.path.join(BUILD, "engine.o"), os.path.join(BUILD, "api.o"),
                             os.path.join(BUILD, "fcf.o"), os.path.join(BUILD, "static_step.o"),
+                            os.path.join(BUILD, "lanczos.o"),
                             "-Xlinker", "-rpath," + os.path.join(CUDA_HOME, "lib64")]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:

@@ -15,6 +15,7 @@
 #include "../../include/rexi.h"
 #include "engine.h"
 #include "fcf.h"
+#include "lanczos.h"
 
 using rexi::EngineArgs;
 using rexi::IOArgs;
@@ -92,6 +93,28 @@ struct rexi_plan {
     double* d_partn = nullptr;
     double2* d_ckpt = nullptr;
     DescSet fwd, one, bwd;
+    // engine settings of the general (item) engine; a Lanczos plan uses it only
+    // for the calls the Lanczos kernel does not cover (adjoint, single stages)
+    int eng_ortho = 1, eng_window = 0;
+    // shared-basis Lanczos path (opt.ortho == 2)
+    bool lanczos = false;
+    int lz_m = 0;                                // largest Krylov dimension per substep
+    int lz_tx = 1, lz_ty = 1, lz_tz = 1;         // tile box
+    int lz_cps = 2;                              // CTAs per SM
+    int lz_target = 0;                           // largest interior points per tile (0: choose)
+    int lz_grid = 0, lz_stage = 1;
+    size_t lz_smem = 0;
+    int lz_part_cap = 0;                         // CTAs the partial buffer holds
+    double2* d_lz_basis = nullptr;
+    double2* d_lz_wt = nullptr;
+    double2* d_lz_part = nullptr;
+    double2* d_lz_rows = nullptr;
+    double2* d_lz_ybuf = nullptr;
+    double2* d_lz_coef = nullptr;
+    double* d_lz_rho = nullptr;
+    int* d_lz_stop = nullptr;
+    int* d_lz_cols = nullptr;
+    double2* d_lz_shift = nullptr;
     ProblemDesc hprob{};                         // forward problem descriptor (host copy)
     int last_status = REXI_OK;
     int last_launches = 0;
@@ -224,6 +247,7 @@ ItemDesc make_item(const rexi_plan* p, int idx, int pole, bool adjoint, int prob
     it.shift = make_double2(sh.real(), sh.imag());
     it.shiftf = make_float2((float)sh.real(), (float)sh.imag());
     const size_t esz = p->fp32 ? sizeof(float2) : sizeof(double2);
+    if (idx >= p->nit_cap) return it;            // no item workspace (a Lanczos plan before its first adjoint)
     it.x = p->d_x + (size_t)idx * p->n;
     it.basis = (char*)p->d_basis + (size_t)idx * (p->m + 1) * p->n * esz;
     it.st = p->d_st + idx;
@@ -250,6 +274,7 @@ ItemDesc make_group(const rexi_plan* p, int g, bool adjoint, int problem, int me
     it.shiftf = make_float2(0.0f, 0.0f);
     it.x = nullptr;
     const size_t esz = p->fp32 ? sizeof(float2) : sizeof(double2);
+    if (p->nit_cap == 0) return it;              // no item workspace
     it.basis = (char*)p->d_basis + (size_t)idx * (p->m + 1) * p->n * esz;
     it.group = -1;
     it.is_group = 1;
@@ -357,8 +382,8 @@ EngineArgs base_args(const rexi_plan* p, int mode, const DescSet& set, int nprob
     A.max_iters = p->opt.max_iters;
     A.max_sub = max_sub;
     A.pv = p->pv;
-    A.ortho = p->opt.ortho;
-    A.window = p->opt.window;
+    A.ortho = p->eng_ortho;
+    A.window = p->eng_window;
     A.tol = p->tol;
     A.inner_tol = p->fp32 ? p->opt.inner_tol : 0.0;
     A.timeout_ns = p->timeout_ns;
@@ -458,6 +483,150 @@ int collect(rexi_plan* p, cudaStream_t stream, int nitems, int item_offset, int 
     return status;
 }
 
+// ---- shared-basis Lanczos path ----------------------------------------------
+
+// Tile box of the Lanczos kernel: the box (at most `target` interior points,
+// tile plus halo within the kernel's staging limit) that minimises the work of
+// the busiest CTA, counting 10 units per interior point (update and stencil)
+// and 6 per point of the extended box (the update, recomputed on the halo).
+// Then the grid (CTAs per SM as requested, within occupancy), the dynamic
+// shared memory and the rows the control CTA stages per chunk.
+int lz_configure(rexi_plan* p) {
+    const int sms = sm_count(p->device);
+    const int hx = p->a[0] != 0.0 ? 1 : 0, hy = p->a[1] != 0.0 ? 1 : 0, hz = p->a[2] != 0.0 ? 1 : 0;
+    const int nx = p->dims[0], ny = p->dims[1], nz = p->dims[2];
+    const int target = p->lz_target > 0 ? std::min(p->lz_target, rexi::kLzMaxInterior) : rexi::kLzMaxInterior;
+    const int cps = std::max(1, std::min(p->lz_cps, 8));
+    const int tile_ctas = std::max(1, cps * sms - 1);
+    long long best = -1;
+    int bx = 1, by = 1, bz = 1;
+    const int widths[] = {16, 32, 64, 128, 256, 512, 1024, 2048};
+    std::vector<int> txs;
+    for (int w : widths)
+        if (w < nx) txs.push_back(w);
+    if (nx <= 2048) txs.push_back(nx);
+    for (int tx : txs) {
+        if (tx > target) continue;
+        for (int tz = 1; tz <= std::min(nz, target / tx); ++tz) {
+            for (int ty = 1; ty <= std::min(ny, target / (tx * tz)); ++ty) {
+                const long long I = (long long)tx * ty * tz;
+                const long long E = (long long)(tx + 2 * hx) * (ty + 2 * hy) * (tz + 2 * hz);
+                if (E > rexi::kLzMaxExt) continue;
+                const long long ntiles =
+                    (long long)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty) * ((nz + tz - 1) / tz);
+                const long long rounds = (ntiles + tile_ctas - 1) / tile_ctas;
+                const long long cost = rounds * (10 * I + 6 * E);
+                if (best < 0 || cost < best || (cost == best && tx > bx)) {
+                    best = cost;
+                    bx = tx;
+                    by = ty;
+                    bz = tz;
+                }
+            }
+        }
+    }
+    if (best < 0) return REXI_EINVAL;               // a row longer than 2048 points and no narrower box
+    p->lz_tx = bx;
+    p->lz_ty = by;
+    p->lz_tz = bz;
+    size_t smem = rexi::lanczos_smem_bytes(bx, by, bz, hx, hy, hz);
+    // the control CTA stages rows of R (K poles x 3 entries) through the same memory
+    const size_t row_bytes = (size_t)p->K * 3 * sizeof(double2);
+    smem = std::max(smem, std::min<size_t>(8 * row_bytes, 96 * 1024));
+    p->lz_stage = (int)std::max<size_t>(1, std::min<size_t>(64, smem / row_bytes));
+    p->lz_smem = smem;
+    const int maxg = rexi::lanczos_max_grid(smem, p->device);
+    if (maxg < 2) return REXI_ECUDA;
+    p->lz_grid = std::min(maxg, cps * sms);
+    if (p->lz_grid > p->lz_part_cap) return REXI_EINVAL;
+    return REXI_OK;
+}
+
+int lz_alloc(rexi_plan* p) {
+    const size_t n = (size_t)p->n, K = (size_t)p->K, m = (size_t)p->lz_m;
+    int st;
+    p->lz_part_cap = 8 * sm_count(p->device);
+    if ((st = dalloc(p, &p->d_lz_basis, (m + 2) * n))) return st;
+    if ((st = dalloc(p, &p->d_lz_wt, 2 * n))) return st;
+    if ((st = dalloc(p, &p->d_lz_part, 4 * (size_t)p->lz_part_cap))) return st;
+    if ((st = dalloc(p, &p->d_lz_rows, m * K * 3))) return st;
+    if ((st = dalloc(p, &p->d_lz_ybuf, m * K))) return st;
+    if ((st = dalloc(p, &p->d_lz_coef, m * K))) return st;
+    if ((st = dalloc(p, &p->d_lz_rho, m + 2))) return st;
+    if ((st = dalloc(p, &p->d_lz_stop, (size_t)std::max(1, p->n_sub)))) return st;
+    if ((st = dalloc(p, &p->d_lz_cols, 2 * (size_t)std::max(1, p->n_sub)))) return st;
+    if ((st = dalloc(p, &p->d_lz_shift, K))) return st;
+    if (!p->d_stats && (st = dalloc(p, &p->d_stats, K))) return st;
+    std::vector<double2> sh(K);
+    for (size_t k = 0; k < K; ++k) {
+        const cd v = p->z[k] - p->tau * p->c;
+        sh[k] = make_double2(v.real(), v.imag());
+    }
+    if (cudaMemcpy(p->d_lz_shift, sh.data(), sizeof(double2) * K, cudaMemcpyHostToDevice) != cudaSuccess)
+        return REXI_ECUDA;
+    return lz_configure(p);
+}
+
+// One launch of the Lanczos kernel: n_sub substeps (mode LZ_STEP) or the K
+// solves of one substep (LZ_SOLVE, x = out [K][n]).
+int lz_launch(rexi_plan* p, int mode, const void* in, void* out, cudaStream_t stream) {
+    const int nsub = mode == rexi::LZ_STEP ? p->n_sub : 1;
+    cudaError_t e = cudaMemsetAsync(p->d_bar, 0, 3 * sizeof(unsigned), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, 2 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stats, 0, sizeof(ItemStats) * p->K, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_lz_stop, 0xFF, sizeof(int) * nsub, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    rexi::LzArgs A{};
+    A.mode = mode;
+    A.n = p->n;
+    A.nx = p->dims[0];
+    A.ny = p->dims[1];
+    A.nz = p->dims[2];
+    A.K = p->K;
+    A.nsub = nsub;
+    A.m = std::min(p->lz_m, p->opt.max_iters);
+    for (int d = 0; d < 3; ++d) A.a[d] = p->a[d];
+    A.diag = p->d_diag;
+    A.shift = p->d_lz_shift;
+    A.alpha = p->d_alpha;
+    A.alpha0 = make_double2(p->alpha0.real(), p->alpha0.imag());
+    A.tol = p->tol;
+    A.stage_rows = p->lz_stage;
+    A.tx = p->lz_tx;
+    A.ty = p->lz_ty;
+    A.tz = p->lz_tz;
+    A.gx = (A.nx + A.tx - 1) / A.tx;
+    A.gy = (A.ny + A.ty - 1) / A.ty;
+    A.gz = (A.nz + A.tz - 1) / A.tz;
+    A.ntiles = A.gx * A.gy * A.gz;
+    A.in = (const double2*)in;
+    A.out = (double2*)out;
+    A.tmp0 = p->d_tmp0;
+    A.tmp1 = p->d_tmp1;
+    A.basis = p->d_lz_basis;
+    A.wt = p->d_lz_wt;
+    A.part = p->d_lz_part;
+    A.rows = p->d_lz_rows;
+    A.ybuf = p->d_lz_ybuf;
+    A.coef = p->d_lz_coef;
+    A.rho = p->d_lz_rho;
+    A.stop = p->d_lz_stop;
+    A.cols = p->d_lz_cols;
+    A.stats = p->d_stats;
+    A.bar = p->d_bar;
+    A.err = p->d_err;
+    A.timeout_ns = p->timeout_ns;
+    A.trace = p->trace_cap > 0 ? p->d_trace : nullptr;
+    A.trace_cap = p->trace_cap;
+    A.bytes = p->d_bytes;
+    e = rexi::launch_lanczos(A, p->lz_grid, p->lz_smem, stream);
+    p->last_stream = stream;
+    p->last_launches = 1;
+    p->last_grid = p->lz_grid;
+    return e == cudaSuccess ? REXI_OK : cuda_fail(e);
+}
+
 }  // namespace
 
 extern "C" {
@@ -524,13 +693,21 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     rexi_options opt;
     if (opt_in) opt = *opt_in; else rexi_options_default(&opt);
     if (opt.precision != REXI_FP64 && opt.precision != REXI_MIXED) return REXI_EINVAL;
-    if (opt.restart_m < 1 || opt.restart_m > REXI_MAX_RESTART || opt.max_iters < 1) return REXI_EINVAL;
-    if (opt.ortho != 0 && opt.ortho != 1) return REXI_EINVAL;
-    // full orthogonalisation keeps m + 1 dot products per step in registers
-    if (opt.window == 0 && opt.restart_m > (opt.ortho == 1 ? REXI_MAX_RESTART_FULL : REXI_MAX_RESTART_FULL + 1))
-        return REXI_EINVAL;
-    if (opt.window < 0 || opt.window == 1 || opt.window > REXI_MAX_RESTART || (opt.window > 0 && opt.ortho != 1))
-        return REXI_EINVAL;
+    if (opt.restart_m < 1 || opt.max_iters < 1) return REXI_EINVAL;
+    if (opt.ortho < 0 || opt.ortho > 2) return REXI_EINVAL;
+    const bool lanczos = opt.ortho == 2;
+    if (lanczos) {
+        // one shared basis per substep, no restarts: FP64 only, no window
+        if (opt.precision != REXI_FP64 || opt.window != 0 || opt.restart_m > REXI_MAX_KRYLOV) return REXI_EINVAL;
+    } else {
+        if (opt.restart_m > REXI_MAX_RESTART) return REXI_EINVAL;
+        // full orthogonalisation keeps m + 1 dot products per step in registers
+        if (opt.window == 0 &&
+            opt.restart_m > (opt.ortho == 1 ? REXI_MAX_RESTART_FULL : REXI_MAX_RESTART_FULL + 1))
+            return REXI_EINVAL;
+        if (opt.window < 0 || opt.window == 1 || opt.window > REXI_MAX_RESTART || (opt.window > 0 && opt.ortho != 1))
+            return REXI_EINVAL;
+    }
     if (!(opt.tol >= 0.0) || !(opt.R1 >= 0.0) || !(opt.inner_tol >= 0.0) || !(opt.stabilize_eps >= 0.0) ||
         !(opt.stabilize_eps < 1.0))
         return REXI_EINVAL;
@@ -555,6 +732,17 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     p->n = (int)n;
     p->K = K;
     p->m = opt.restart_m;
+    p->eng_ortho = opt.ortho;
+    p->eng_window = opt.window;
+    if (lanczos) {
+        // the item engine serves the adjoint of a Lanczos plan: shared first
+        // cycle, two-vector window, restart length up to 64
+        p->lanczos = true;
+        p->lz_m = opt.restart_m;
+        p->m = std::min(opt.restart_m, REXI_MAX_RESTART);
+        p->eng_ortho = 1;
+        p->eng_window = 2;
+    }
     p->dt = dt;
     p->fp32 = opt.precision == REXI_MIXED;
     p->shared = opt.shared_first_cycle != 0;
@@ -635,9 +823,10 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     if (opt.want_backward) {
         if ((st = alloc_items(p, 2 * K))) return fail(st);
         if ((st = dalloc(p, &p->d_ckpt, (size_t)std::max(1, p->n_sub) * n))) return fail(st);
-    } else {
+    } else if (!p->lanczos) {
         if ((st = alloc_items(p, K))) return fail(st);
     }
+    if (p->lanczos && (st = lz_alloc(p))) return fail(st);
     if ((st = build_sets(p))) return fail(st);
     *out = p;
     return p->warn;
@@ -656,7 +845,7 @@ int rexi_plan_get_info(const rexi_plan* p, rexi_plan_info* info) {
     info->K = p->K;
     info->n_sub = p->n_sub;
     info->n_total = p->n;
-    info->restart_m = p->m;
+    info->restart_m = p->lanczos ? p->lz_m : p->m;
     info->precision = p->opt.precision;
     info->dt = p->dt;
     info->tau = p->tau;
@@ -721,6 +910,12 @@ int rexi_step(rexi_plan* p, const void* psi_in, void* psi_out, void* stream, rex
     if (!p || !psi_in || !psi_out) return REXI_EINVAL;
     DeviceGuard guard(p->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->lanczos) {
+        int r = lz_launch(p, rexi::LZ_STEP, psi_in, psi_out, s);
+        if (r) return p->last_status = r;
+        if (!st) return p->last_status = REXI_OK;
+        return p->last_status = collect(p, s, p->K, 0, p->K, st, p->n_sub);
+    }
     IOArgs io{};
     io.in[0] = (const double2*)psi_in;
     io.out[0] = (double2*)psi_out;
@@ -826,6 +1021,12 @@ int rexi_solve_poles(rexi_plan* p, const void* b, void* x, void* stream, rexi_st
     if (!p || !b || !x) return REXI_EINVAL;
     DeviceGuard guard(p->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->lanczos) {
+        int r = lz_launch(p, rexi::LZ_SOLVE, b, x, s);
+        if (r) return p->last_status = r;
+        if (!st) return p->last_status = REXI_OK;
+        return p->last_status = collect(p, s, p->K, 0, p->K, st, 1);
+    }
     IOArgs io{};
     io.in[0] = (const double2*)b;
     EngineArgs A = base_args(p, rexi::MODE_SOLVE, p->one, 1, 1);
@@ -897,7 +1098,7 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
     int total_items = 0, max_sub = 0, total_tiles = 0;
     for (int b = 0; b < B; ++b) {
         rexi_plan* p = plans[b];
-        if (!p || !psi_in[b] || !psi_out[b]) return REXI_EINVAL;
+        if (!p || !psi_in[b] || !psi_out[b] || p->lanczos) return REXI_EINVAL;
         if (p->device != p0->device || p->fp32 != p0->fp32 || p->m != p0->m ||
             p->opt.ortho != p0->opt.ortho || p->opt.window != p0->opt.window) return REXI_EINVAL;
         const int ng = p->shared ? 1 : 0;
@@ -1048,6 +1249,21 @@ int rexi_plan_set_tiles(rexi_plan* p, int pole_tile, int group_tile, int ctas_pe
     if (!ok(pole_tile) || !ok(group_tile) || ctas_per_sm < 0 || ctas_per_sm > 32) return REXI_EINVAL;
     DeviceGuard guard(p->device);
     if (cudaDeviceSynchronize() != cudaSuccess) return REXI_ECUDA;
+    if (p->lanczos) {
+        // Lanczos plans: group_tile bounds the interior points of a tile,
+        // ctas_per_sm the resident CTAs per SM (0: two)
+        if (ctas_per_sm > 8) return REXI_EINVAL;
+        const int old_target = p->lz_target, old_cps = p->lz_cps;
+        p->lz_target = group_tile;
+        p->lz_cps = ctas_per_sm > 0 ? ctas_per_sm : 2;
+        const int r = lz_configure(p);
+        if (r) {
+            p->lz_target = old_target;
+            p->lz_cps = old_cps;
+            lz_configure(p);
+            return r;
+        }
+    }
     p->tile_pole = pole_tile;
     p->tile_group = group_tile;
     p->ctas_per_sm = ctas_per_sm;

@@ -1,0 +1,73 @@
+// Device primitives shared by the persistent kernels: a bounded grid barrier
+// for co-resident (cooperative) grids, acquire/release accesses, the global
+// timer, and an integer-only FP64 -> FP32 conversion for inner products.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace rexi {
+namespace dev {
+
+constexpr int kErrTimeout = -5;   // REXI_ETIMEOUT
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Double to float by integer operations only (rounding toward zero; results
+// below the float range become signed zero, above it (and NaN) signed
+// infinity), so the conversion does not occupy the FP64 pipe.
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
+// All CTAs of the co-resident grid meet here.  bar[0] counts arrivals and
+// bar[1] completed barriers; both are zeroed before every launch.  The arrival
+// that makes the count a multiple of the grid size publishes the barrier's
+// number with a release store; the others poll it with acquire loads.  Every
+// wait is bounded by timeout_ns: on expiry the sticky error word is set, and
+// the function returns false (as it does whenever the error word is set), so
+// every CTA leaves the kernel at its next barrier.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* err, unsigned long long timeout_ns) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned* count = bar;
+        unsigned* done = bar + 1;
+        __threadfence();
+        const unsigned prev = atomicAdd(count, 1u);
+        const unsigned target = prev / gridDim.x + 1u;
+        if (prev + 1u == target * gridDim.x) {
+            __threadfence();
+            st_release_u32(done, target);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while ((int)(ld_acquire_u32(done) - target) < 0) {
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicExch(err, kErrTimeout);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+    }
+    __syncthreads();
+    return *(volatile int*)err == 0;
+}
+
+}  // namespace dev
+}  // namespace rexi

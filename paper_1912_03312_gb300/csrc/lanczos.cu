@@ -1,0 +1,756 @@
+// Shared-basis Lanczos kernel for sm_103a: all K shifted solves of a rational
+// evaluation (Eq. (5) of Rittich & Speck, arXiv:1912.03312) on one Krylov
+// basis of B = tau (H - c), one grid barrier per Krylov step.
+//
+// Krylov step j (one sweep; every tile CTA, own tile plus a one-point halo):
+//
+//   u_j  = rho_{j-1} (B u_{j-1} - a_{j-1} u_{j-1} - b_{j-1} u_{j-2})   (pointwise,
+//          recomputed on the halo from the stored vectors so no second barrier
+//          is needed before the stencil)
+//   B u_j                                      (stencil from shared memory)
+//   partial sums of ||u_j||^2, Re u_j^H B u_j, Re u_{j-1}^H B u_j
+//
+// The inner products are compensated sums of FP32 hi/lo pieces (about 1e-13
+// relative; the FP64 pipe stays free for the recurrence), then one grid
+// barrier; every CTA reduces the partials in FP64 in the same fixed order
+// and derives the same coefficients: rho_j = 1/||u_j||, a_j = (u_j^H B u_j) /
+// ||u_j||^2 (the Rayleigh quotient, real because B is real symmetric), b_j =
+// (u_{j-1}^H B u_j) / ||u_{j-1}||^2.  With q_j = rho_j u_j the recurrence reads
+//
+//   B q_j = (1/rho_{j+1}) q_{j+1} + a_j q_j + (rho_j b_j / rho_{j-1}) q_{j-1},
+//
+// exactly for the coefficients used (whatever the accuracy of the inner
+// products that chose them), so B Q_k = Q_{k+1} T_k holds to FP64 rounding
+// with T_k tridiagonal.  The shifted systems (B - s_k I) x = psi share Q_k
+// (Sec. 5 of the paper: the Krylov spaces of shifted systems coincide); pole k
+// minimises ||beta e_1 - (T_k - s_k [I; 0]) y|| by its own Givens rotations
+// (GMRES on the shared basis).  The columns are unit vectors but orthogonal
+// only locally, so the stop uses the bound ||r_k|| <= ||Q_{k+1}|| |g_{k+1}| <=
+// sqrt(k+1) |g_{k+1}| (times a 1e-4 margin for the computed norms).
+//
+// CTA 0 is the control CTA: it owns no tiles, runs the per-pole Givens
+// recurrences one step behind the sweeps, stops the iteration once every pole
+// has met its bound, and back-substitutes y_k.  The result of the evaluation
+// is psi' = alpha_0 psi + sum_k alpha_k Q y_k = alpha_0 psi + Q (sum_k alpha_k
+// y_k): one pass over the basis (the pole sum of Eq. (5)).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "devsync.cuh"
+#include "lanczos.h"
+
+namespace rexi {
+
+namespace {
+
+using dev::global_ns;
+using dev::grid_sync;
+
+constexpr int kLzWarps = kLzBlock / 32;
+constexpr int kErrInternal = -3;        // REXI_ECUDA: the iteration outran its workspace
+
+struct LzSmem {
+    double rho, a, b;        // coefficients of the next update (those of the last reduced sweep)
+    double n_last;           // ||u_{j-1}||^2 of the last reduced sweep
+    double n_prev;           // ||u_{j-2}||^2
+    double n0;               // ||u_0||^2 of the substep
+    double hrho[3], ha[3], hb[3];   // control: (rho, a, b) of sweeps j-1, j-2, j-3
+    double red[kLzWarps][3];
+    int stop;
+    double2 coef[kLzMaxM];   // final pass: coefficients of the stored vectors
+};
+
+struct Tile {
+    int x0, y0, z0;          // first interior point
+    int tx, ty, tz;          // interior extent (ragged at the grid's edge)
+    int ex, ey;              // extended extent in x and y (interior plus halo)
+    int E, I;                // extended and interior point counts
+};
+
+__device__ __forceinline__ int wrapi(int x, int N) { return x < 0 ? x + N : (x >= N ? x - N : x); }
+
+__device__ __forceinline__ Tile tile_of(const LzArgs& A, int t, int hx, int hy, int hz) {
+    Tile T;
+    const int ix = t % A.gx, r = t / A.gx, iy = r % A.gy, iz = r / A.gy;
+    T.x0 = ix * A.tx;
+    T.y0 = iy * A.ty;
+    T.z0 = iz * A.tz;
+    T.tx = min(A.tx, A.nx - T.x0);
+    T.ty = min(A.ty, A.ny - T.y0);
+    T.tz = min(A.tz, A.nz - T.z0);
+    T.ex = T.tx + 2 * hx;
+    T.ey = T.ty + 2 * hy;
+    T.E = T.ex * T.ey * (T.tz + 2 * hz);
+    T.I = T.tx * T.ty * T.tz;
+    return T;
+}
+
+// u_r: u_0 is the substep's input state, u_1.. live in the basis.
+__device__ __forceinline__ const double2* uvec(const LzArgs& A, const double2* u0, int r) {
+    return r == 0 ? u0 : A.basis + (size_t)(r - 1) * (size_t)A.n;
+}
+__device__ __forceinline__ double2* uvec_w(const LzArgs& A, int r) {
+    return A.basis + (size_t)(r - 1) * (size_t)A.n;
+}
+
+// acc + c u (complex), two fused multiply-adds per component.
+__device__ __forceinline__ double2 cfma(double2 acc, double2 c, double2 u) {
+    acc.x = fma(c.x, u.x, acc.x);
+    acc.x = fma(-c.y, u.y, acc.x);
+    acc.y = fma(c.x, u.y, acc.y);
+    acc.y = fma(c.y, u.x, acc.y);
+    return acc;
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 csc(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// Complex Givens rotation G = [c s; -conj(s) c] (c real) with G [x; h] = [r; 0]
+// for complex x and real h >= 0; inv = 1 / r (0 when the column vanishes).
+__device__ __forceinline__ void givens(double2 x, double h, double* c, double2* s, double2* r, double2* inv) {
+    const double xx = x.x * x.x + x.y * x.y;
+    if (h == 0.0) {
+        *c = 1.0;
+        *s = make_double2(0.0, 0.0);
+        *r = x;
+        *inv = xx > 0.0 ? make_double2(x.x / xx, -x.y / xx) : make_double2(0.0, 0.0);
+        return;
+    }
+    if (xx == 0.0) {
+        *c = 0.0;
+        *s = make_double2(1.0, 0.0);
+        *r = make_double2(h, 0.0);
+        *inv = make_double2(1.0 / h, 0.0);
+        return;
+    }
+    const double nx = sqrt(xx), nu = sqrt(xx + h * h);
+    const double2 ph = make_double2(x.x / nx, x.y / nx);
+    *c = nx / nu;
+    *s = csc(ph, h / nu);
+    *r = csc(ph, nu);
+    *inv = make_double2(ph.x / nu, -ph.y / nu);
+}
+
+__device__ __forceinline__ void trace_mark(const LzArgs& A, int code, int* tcount) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int c = *tcount;
+        if (A.trace != nullptr && c < A.trace_cap) {
+            A.trace[1 + 2 * c] = (unsigned long long)code;
+            A.trace[2 + 2 * c] = global_ns();
+            A.trace[0] = (unsigned long long)(c + 1);
+        }
+        *tcount = c + 1;
+    }
+}
+
+// Sum of the partials of sweep `par` over the tile CTAs (1..G-1), in FP64 and
+// the same fixed order in every CTA; warp 0 computes, every lane gets the sums.
+__device__ __forceinline__ double3 reduce_partials(const LzArgs& A, int par) {
+    double3 s = make_double3(0.0, 0.0, 0.0);
+    const int lane = threadIdx.x & 31;
+    const double2* p = A.part + (size_t)par * gridDim.x * 2;
+    for (int c = 1 + lane; c < (int)gridDim.x; c += 32) {
+        const double2 v = __ldcg(p + 2 * c), w = __ldcg(p + 2 * c + 1);
+        s.x += v.x;
+        s.y += v.y;
+        s.z += w.x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
+    }
+    return s;
+}
+
+// ---- compensated (double-float) inner products on the FP32 pipe -------------
+//
+// The coefficients a_j, b_j and the norms set the local orthogonality of the
+// basis; FP32 inner products leave components of relative size ~1e-7 (a wave
+// packet that is an eigenvector then no longer breaks the recurrence down).
+// Each FP64 operand is split into float hi + lo by integer operations only
+// (48 of its 53 significand bits), products are formed exactly up to the lo*lo
+// term (Dekker's product with a fused multiply-add) and summed with Knuth's
+// two-sum; per-thread sums then continue in FP64.  Relative accuracy ~1e-13,
+// without occupying the FP64 pipe.
+
+// x ~= h + l with h the leading 24 significand bits (truncated) and l the next
+// 24 (truncated); values below the float range become zero.
+__device__ __forceinline__ void split_f64(double x, float* h, float* l) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sign = hi & 0x80000000u;
+    const int E = (int)((hi >> 20) & 0x7FFu);
+    const int eh = E - 1023 + 127;
+    if (eh <= 0 || eh >= 255) {
+        *h = __uint_as_float(eh >= 255 ? (sign | 0x7F800000u) : sign);
+        *l = __uint_as_float(sign);
+        return;
+    }
+    *h = __uint_as_float(sign | ((unsigned)eh << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+    const unsigned m = lo & 0x1FFFFFFFu;                  // the remaining 29 bits, unit 2^(E - 1075)
+    const int k = 31 - __clz(m | 1u);                      // leading one of m (m = 0 handled below)
+    const int el = k + E - 1075 + 127;
+    if (m == 0u || el <= 0) {
+        *l = __uint_as_float(sign);
+        return;
+    }
+    const unsigned frac = k >= 23 ? (m >> (k - 23)) : (m << (23 - k));
+    *l = __uint_as_float(sign | ((unsigned)el << 23) | (frac & 0x7FFFFFu));
+}
+
+// (sh, sl) += (ah + al)(bh + bl), dropping al*bl.
+__device__ __forceinline__ void df_madd(float& sh, float& sl, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = fmaf(ah, bh, -p);                            // exact rounding error of the product
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float t = __fadd_rn(sh, p);
+    const float z = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+constexpr int kCh = 4;          // points per thread whose loads are issued together
+
+// Global index of extended point e of tile T (periodic wrap), and its interior
+// index (-1 on the halo).
+__device__ __forceinline__ size_t ext_point(const LzArgs& A, const Tile& T, int e, int hx, int hy, int hz,
+                                            int* inner) {
+    const int ex = e % T.ex, r = e / T.ex, ey = r % T.ey, ez = r / T.ey;
+    const int gxx = wrapi(T.x0 - hx + ex, A.nx);
+    const int gyy = wrapi(T.y0 - hy + ey, A.ny);
+    const int gzz = wrapi(T.z0 - hz + ez, A.nz);
+    const int ix = ex - hx, iy = ey - hy, iz = ez - hz;
+    *inner = (ix >= 0 && ix < T.tx && iy >= 0 && iy < T.ty && iz >= 0 && iz < T.tz) ? ix + T.tx * (iy + T.ty * iz)
+                                                                                   : -1;
+    return (size_t)gxx + (size_t)A.nx * ((size_t)gyy + (size_t)A.ny * (size_t)gzz);
+}
+
+// Global index of interior point i of tile T and its extended index.
+__device__ __forceinline__ size_t int_point(const LzArgs& A, const Tile& T, int i, int hx, int hy, int hz,
+                                            int* e) {
+    const int ix = i % T.tx, r = i / T.tx, iy = r % T.ty, iz = r / T.ty;
+    *e = (ix + hx) + T.ex * ((iy + hy) + T.ey * (iz + hz));
+    return (size_t)(T.x0 + ix) + (size_t)A.nx * ((size_t)(T.y0 + iy) + (size_t)A.ny * (size_t)(T.z0 + iz));
+}
+
+// One Krylov sweep j over the tiles of this CTA; thread 0 receives the CTA's
+// partial sums.
+__device__ void sweep(const LzArgs& A, LzSmem& sm, double2* S, double2* U1, const double2* u0, int j, int hx,
+                      int hy, int hz, double* pn, double* pp, double* pd) {
+    const int G1 = gridDim.x - 1;
+    const double rho = sm.rho, ca = sm.a, cb = sm.b;
+    const double2* wprev = A.wt + (size_t)((j - 1) & 1) * A.n;
+    double2* wcur = A.wt + (size_t)(j & 1) * A.n;
+    const double2* u1p = j >= 1 ? uvec(A, u0, j - 1) : nullptr;
+    const double2* u2p = j >= 2 ? uvec(A, u0, j - 2) : nullptr;
+    double2* ujw = j >= 1 ? uvec_w(A, j) : nullptr;
+    const double ax = A.a[0], ay = A.a[1], az = A.a[2];
+    const double2 zero = make_double2(0.0, 0.0);
+    float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f, dh = 0.f, dl = 0.f;
+    for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
+        const Tile T = tile_of(A, t, hx, hy, hz);
+        // phase A: u_j on the tile and its halo (loads of kCh points in flight)
+        for (int e0 = threadIdx.x; e0 < T.E; e0 += kCh * kLzBlock) {
+            size_t g[kCh];
+            int inner[kCh];
+            double2 w[kCh], u1[kCh], u2[kCh];
+#pragma unroll
+            for (int q = 0; q < kCh; ++q) {
+                const int e = e0 + q * kLzBlock;
+                inner[q] = -1;
+                g[q] = 0;
+                w[q] = u1[q] = u2[q] = zero;
+                if (e < T.E) {
+                    g[q] = ext_point(A, T, e, hx, hy, hz, &inner[q]);
+                    if (j == 0) {
+                        w[q] = u0[g[q]];
+                    } else {
+                        w[q] = wprev[g[q]];
+                        u1[q] = u1p[g[q]];
+                        if (j >= 2) u2[q] = u2p[g[q]];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kCh; ++q) {
+                const int e = e0 + q * kLzBlock;
+                if (e < T.E) {
+                    double2 v = w[q];
+                    if (j >= 1) {
+                        double vx = fma(-ca, u1[q].x, w[q].x), vy = fma(-ca, u1[q].y, w[q].y);
+                        if (j >= 2) {
+                            vx = fma(-cb, u2[q].x, vx);
+                            vy = fma(-cb, u2[q].y, vy);
+                        }
+                        v = make_double2(rho * vx, rho * vy);
+                    }
+                    S[e] = v;
+                    if (inner[q] >= 0) {
+                        U1[inner[q]] = u1[q];
+                        if (j >= 1) ujw[g[q]] = v;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // phase B: B u_j on the tile, and the inner products
+        const int sy = T.ex, sz = T.ex * T.ey;
+        for (int i0 = threadIdx.x; i0 < T.I; i0 += kCh * kLzBlock) {
+            size_t g[kCh];
+            int ee[kCh];
+            double dg[kCh];
+#pragma unroll
+            for (int q = 0; q < kCh; ++q) {
+                const int i = i0 + q * kLzBlock;
+                g[q] = 0;
+                ee[q] = 0;
+                dg[q] = 0.0;
+                if (i < T.I) {
+                    g[q] = int_point(A, T, i, hx, hy, hz, &ee[q]);
+                    dg[q] = A.diag[g[q]];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kCh; ++q) {
+                const int i = i0 + q * kLzBlock;
+                if (i < T.I) {
+                    const int e = ee[q];
+                    const double2 c = S[e];
+                    double wx = dg[q] * c.x, wy = dg[q] * c.y;
+                    if (hx) {
+                        const double2 l = S[e - 1], rr = S[e + 1];
+                        wx = fma(ax, l.x + rr.x, wx);
+                        wy = fma(ax, l.y + rr.y, wy);
+                    }
+                    if (hy) {
+                        const double2 l = S[e - sy], rr = S[e + sy];
+                        wx = fma(ay, l.x + rr.x, wx);
+                        wy = fma(ay, l.y + rr.y, wy);
+                    }
+                    if (hz) {
+                        const double2 l = S[e - sz], rr = S[e + sz];
+                        wx = fma(az, l.x + rr.x, wx);
+                        wy = fma(az, l.y + rr.y, wy);
+                    }
+                    wcur[g[q]] = make_double2(wx, wy);
+                    float cxh, cxl, cyh, cyl, wxh, wxl, wyh, wyl, uxh, uxl, uyh, uyl;
+                    split_f64(c.x, &cxh, &cxl);
+                    split_f64(c.y, &cyh, &cyl);
+                    split_f64(wx, &wxh, &wxl);
+                    split_f64(wy, &wyh, &wyl);
+                    const double2 u1 = U1[i];
+                    split_f64(u1.x, &uxh, &uxl);
+                    split_f64(u1.y, &uyh, &uyl);
+                    df_madd(nh, nl, cxh, cxl, cxh, cxl);
+                    df_madd(nh, nl, cyh, cyl, cyh, cyl);
+                    df_madd(ph, pl, cxh, cxl, wxh, wxl);
+                    df_madd(ph, pl, cyh, cyl, wyh, wyl);
+                    df_madd(dh, dl, uxh, uxl, wxh, wxl);
+                    df_madd(dh, dl, uyh, uyl, wyh, wyl);
+                }
+            }
+        }
+        __syncthreads();                          // S and U1 are reused by the next tile
+    }
+    double fn = (double)nh + (double)nl, fp = (double)ph + (double)pl, fd = (double)dh + (double)dl;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fn += __shfl_xor_sync(0xffffffffu, fn, o);
+        fp += __shfl_xor_sync(0xffffffffu, fp, o);
+        fd += __shfl_xor_sync(0xffffffffu, fd, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sm.red[warp][0] = fn;
+        sm.red[warp][1] = fp;
+        sm.red[warp][2] = fd;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int w = 0; w < kLzWarps; ++w) {
+            a += sm.red[w][0];
+            b += sm.red[w][1];
+            c += sm.red[w][2];
+        }
+        *pn = a;
+        *pp = b;
+        *pd = c;
+    }
+}
+
+// Final pass over this CTA's tiles: dst = sum_{q < J} coef_q u_q (the
+// coefficients staged in shared memory).
+__device__ void combine(const LzArgs& A, const double2* coef, const double2* u0, double2* dst, int J, int hx,
+                        int hy, int hz) {
+    const int G1 = gridDim.x - 1;
+    for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
+        const Tile T = tile_of(A, t, hx, hy, hz);
+        for (int i0 = threadIdx.x; i0 < T.I; i0 += kCh * kLzBlock) {
+            size_t g[kCh];
+            double2 acc[kCh];
+#pragma unroll
+            for (int q = 0; q < kCh; ++q) {
+                int e;
+                const int i = i0 + q * kLzBlock;
+                g[q] = i < T.I ? int_point(A, T, i, hx, hy, hz, &e) : 0;
+                acc[q] = make_double2(0.0, 0.0);
+            }
+            for (int r = 0; r < J; ++r) {
+                const double2 c = coef[r];
+                const double2* u = uvec(A, u0, r);
+#pragma unroll
+                for (int q = 0; q < kCh; ++q)
+                    if (i0 + q * kLzBlock < T.I) acc[q] = cfma(acc[q], c, u[g[q]]);
+            }
+#pragma unroll
+            for (int q = 0; q < kCh; ++q)
+                if (i0 + q * kLzBlock < T.I) dst[g[q]] = acc[q];
+        }
+    }
+}
+
+// Per-pole state of the control CTA (thread k < K owns pole k).
+struct PoleState {
+    double c1, c2;           // rotations G_{c-1}, G_{c-2} (cosines)
+    double2 s1, s2;          //                           (sines)
+    double2 g;               // g_c, the right-hand side entry the next rotation acts on
+    double2 g1, inv1;        // row c-1: g (final), 1 / R(c-1, c-1)
+    double2 g2, inv2, r12;   // row c-2: g, 1 / R, R(c-2, c-1)
+    double2 shift;
+    int kk;                  // columns used (set when the pole stops)
+    int done;                // 1 converged, 2 failed
+    double bound;            // relative residual bound at the stop
+};
+
+__device__ __forceinline__ void put_row(const LzArgs& A, int r, int k, double2 g, double2 inv, double2 r1, double2 r2) {
+    double2* p = A.rows + ((size_t)r * A.K + k) * 3;
+    p[0] = cmul(g, inv);
+    p[1] = cmul(r1, inv);
+    p[2] = cmul(r2, inv);
+}
+
+// Givens step of pole k on column c of T - s_k [I; 0]: entries up (row c-1),
+// a_c - s_k (row c), lo (row c+1).  Returns true when the pole stops here.
+__device__ bool pole_column(const LzArgs& A, PoleState& P, int k, int c, double up, double ac, double lo,
+                            double tol_abs2, double bnorm) {
+    const double2 dg = make_double2(ac - P.shift.x, -P.shift.y);
+    double2 xm1 = make_double2(up, 0.0);                   // row c-1 entry
+    double2 r0 = make_double2(0.0, 0.0);                   // R(c-2, c)
+    if (c >= 2) {
+        r0 = csc(P.s2, up);
+        xm1 = make_double2(P.c2 * up, 0.0);
+    }
+    double2 r1 = make_double2(0.0, 0.0);                   // R(c-1, c)
+    double2 xc = dg;
+    if (c >= 1) {
+        r1 = cfma(csc(xm1, P.c1), P.s1, dg);
+        const double2 cs1 = make_double2(-P.s1.x, P.s1.y);    // -conj(s1)
+        xc = cfma(csc(dg, P.c1), cs1, xm1);
+    }
+    double c0;
+    double2 s0, rcc, inv;
+    givens(xc, lo, &c0, &s0, &rcc, &inv);
+    const double2 gc = csc(P.g, c0);
+    const double2 gn = cmul(make_double2(-s0.x, s0.y), P.g);   // -conj(s0) g
+    if (c >= 2) put_row(A, c - 2, k, P.g2, P.inv2, P.r12, r0);
+    // shift the pending rows and rotations
+    P.g2 = P.g1;
+    P.inv2 = P.inv1;
+    P.r12 = r1;
+    P.g1 = gc;
+    P.inv1 = inv;
+    P.c2 = P.c1;
+    P.s2 = P.s1;
+    P.c1 = c0;
+    P.s1 = s0;
+    P.g = gn;
+    const double gg = gn.x * gn.x + gn.y * gn.y;
+    if (gg * (double)(c + 2) <= tol_abs2) {
+        // stop with c + 1 columns: rows c-1 and c complete with zeros
+        const double2 z = make_double2(0.0, 0.0);
+        if (c >= 1) put_row(A, c - 1, k, P.g2, P.inv2, P.r12, z);
+        put_row(A, c, k, P.g1, P.inv1, z, z);
+        P.kk = c + 1;
+        P.done = 1;
+        P.bound = bnorm > 0.0 ? sqrt(gg * (double)(c + 2)) / bnorm : 0.0;
+        return true;
+    }
+    return false;
+}
+
+// Control CTA after the sweeps of a substep stopped at J columns: y_k =
+// R_k^{-1} g_k for every pole (rows staged through shared memory in chunks),
+// then the coefficients of the final pass.
+__device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int stage_rows, PoleState& P, int J,
+                               int s) {
+    const int K = A.K;
+    const int k = threadIdx.x;
+    double2 y1 = make_double2(0.0, 0.0), y2 = make_double2(0.0, 0.0);
+    for (int top = J; top > 0; top -= stage_rows) {
+        const int lo = max(0, top - stage_rows);
+        const int cnt = (top - lo) * K * 3;
+        __syncthreads();
+        for (int q = threadIdx.x; q < cnt; q += kLzBlock) stage[q] = A.rows[(size_t)lo * K * 3 + q];
+        __syncthreads();
+        if (k < K) {
+            for (int r = top - 1; r >= lo; --r) {
+                double2 y = make_double2(0.0, 0.0);
+                if (r < P.kk) {
+                    const double2* q = stage + ((size_t)(r - lo) * K + k) * 3;
+                    const double2 mr1 = make_double2(-q[1].x, -q[1].y), mr2 = make_double2(-q[2].x, -q[2].y);
+                    y = cfma(cfma(q[0], mr2, y2), mr1, y1);
+                }
+                if (A.mode == LZ_STEP)
+                    A.ybuf[(size_t)r * K + k] = y;
+                else
+                    A.coef[(size_t)k * A.m + r] = csc(y, A.rho[r]);
+                y2 = y1;
+                y1 = y;
+            }
+        }
+    }
+    __syncthreads();
+    if (A.mode == LZ_STEP) {
+        // coef_r = rho_r sum_k alpha_k y_{k,r} (+ alpha_0 at r = 0): eight
+        // threads per row, a fixed summation order
+        const int q = threadIdx.x & 7;
+        const int Jn = max(J, 1);
+        for (int r0 = 0; r0 < Jn; r0 += kLzBlock / 8) {
+            const int r = r0 + (threadIdx.x >> 3);
+            double2 acc = make_double2(0.0, 0.0);
+            if (r < J)
+                for (int kq = q; kq < K; kq += 8) acc = cfma(acc, A.alpha[kq], A.ybuf[(size_t)r * K + kq]);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            }
+            if (q == 0 && r < Jn) {
+                double2 c = r < J ? csc(acc, A.rho[r]) : make_double2(0.0, 0.0);
+                if (r == 0) {
+                    c.x += A.alpha0.x;
+                    c.y += A.alpha0.y;
+                }
+                A.coef[r] = c;
+            }
+        }
+    }
+    if (k < K) {
+        ItemStats& st = A.stats[k];
+        st.iters += P.kk;
+        st.cycles += 1;
+        st.iters_sq += P.kk * P.kk;
+        st.max_sub_iters = max(st.max_sub_iters, P.kk);
+        st.resid = fmax(st.resid, P.bound);
+        if (P.done != 1) st.failed = 1;
+    }
+    if (threadIdx.x == 0) A.cols[s] = J;
+    (void)sm;
+}
+
+__global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_constant__ LzArgs A) {
+    extern __shared__ double2 dyn[];
+    __shared__ LzSmem sm;
+    const bool control = blockIdx.x == 0;
+    const int hx = A.a[0] != 0.0 ? 1 : 0, hy = A.a[1] != 0.0 ? 1 : 0, hz = A.a[2] != 0.0 ? 1 : 0;
+    // dynamic shared memory: tile plus halo of u_j, then u_{j-1} on the interior
+    const int ext_max = (A.tx + 2 * hx) * (A.ty + 2 * hy) * (A.tz + 2 * hz);
+    double2* S = dyn;
+    double2* U1 = dyn + ext_max;
+    const int stage_rows = A.stage_rows;
+    int tcount = 0;
+    trace_mark(A, 99, &tcount);
+    PoleState P;
+    for (int s = 0; s < A.nsub; ++s) {
+        const double2* u0 = s == 0 ? A.in : ((s - 1) & 1 ? A.tmp1 : A.tmp0);
+        double2* out = s == A.nsub - 1 ? A.out : (s & 1 ? A.tmp1 : A.tmp0);
+        if (control && threadIdx.x < A.K) {
+            P.c1 = P.c2 = 1.0;
+            P.s1 = P.s2 = make_double2(0.0, 0.0);
+            P.g = P.g1 = P.inv1 = P.g2 = P.inv2 = P.r12 = make_double2(0.0, 0.0);
+            P.shift = A.shift[threadIdx.x];
+            P.kk = 0;
+            P.done = 0;
+            P.bound = 0.0;
+        }
+        if (threadIdx.x == 0) {
+            sm.n_last = sm.n_prev = sm.n0 = 0.0;
+            for (int q = 0; q < 3; ++q) sm.hrho[q] = sm.ha[q] = sm.hb[q] = 0.0;
+        }
+        __syncthreads();
+        double tol_abs2 = 0.0, bnorm = 0.0;
+        int J = -1, sweeps = 0;
+        for (int j = 0;; ++j) {
+            if (j >= 1) {
+                // coefficients of sweep j-1, the same in every CTA
+                if (threadIdx.x < 32) {
+                    const double3 t = reduce_partials(A, (j - 1) & 1);
+                    if (threadIdx.x == 0) {
+                        const double n = t.x, p = t.y, d = t.z;
+                        const double rho = n > 0.0 ? 1.0 / sqrt(n) : 0.0;
+                        const double a = n > 0.0 ? p / n : 0.0;
+                        const double b = (j - 1 >= 1 && sm.n_last > 0.0) ? d / sm.n_last : 0.0;
+                        sm.n_prev = sm.n_last;
+                        sm.n_last = n;
+                        if (j == 1) sm.n0 = n;
+                        sm.rho = rho;
+                        sm.a = a;
+                        sm.b = b;
+                        sm.hrho[2] = sm.hrho[1];
+                        sm.hrho[1] = sm.hrho[0];
+                        sm.hrho[0] = rho;
+                        sm.ha[2] = sm.ha[1];
+                        sm.ha[1] = sm.ha[0];
+                        sm.ha[0] = a;
+                        sm.hb[2] = sm.hb[1];
+                        sm.hb[1] = sm.hb[0];
+                        sm.hb[0] = b;
+                        sm.stop = __ldcg(A.stop + s);
+                        if (control) A.rho[j - 1] = rho;
+                    }
+                }
+                __syncthreads();
+                if (sm.stop >= 0) {
+                    J = sm.stop;
+                    sweeps = j;
+                    break;
+                }
+                if (j > A.m + 2) {                     // the control CTA stops by then: never taken
+                    if (threadIdx.x == 0) atomicExch(A.err, kErrInternal);
+                    return;
+                }
+            }
+            if (!control) {
+                double pn = 0.0, pp = 0.0, pd = 0.0;
+                sweep(A, sm, S, U1, u0, j, hx, hy, hz, &pn, &pp, &pd);
+                if (threadIdx.x == 0) {
+                    double2* slot = A.part + ((size_t)(j & 1) * gridDim.x + blockIdx.x) * 2;
+                    slot[0] = make_double2(pn, pp);
+                    slot[1] = make_double2(pd, 0.0);
+                }
+            } else if (j >= 1) {
+                // the control CTA works one column behind: column c = j - 2 is
+                // complete once the norm of u_{j-1} (its subdiagonal) is known
+                if (j == 1) {
+                    const double n0 = sm.n0;
+                    bnorm = sqrt(n0);
+                    const double ta = A.tol * bnorm / 1.0001;
+                    tol_abs2 = ta * ta;
+                    if (threadIdx.x < A.K) P.g = make_double2(n0 > 0.0 ? 1.0 / sm.hrho[0] : 0.0, 0.0);
+                    if (threadIdx.x == 0 && !(n0 > 0.0 && n0 <= 3.0e38)) {
+                        // a zero state needs no columns; a non-finite one fails every pole
+                        __stcg(A.stop + s, 0);
+                    }
+                    if (threadIdx.x < A.K && !(n0 > 0.0)) {
+                        P.done = n0 == 0.0 ? 1 : 2;
+                    }
+                    if (threadIdx.x < A.K && !(n0 <= 3.0e38)) P.done = 2;
+                } else {
+                    const int c = j - 2;
+                    const double rho_c = sm.hrho[1], rho_next = sm.hrho[0];
+                    const double up = (c >= 1 && sm.hrho[2] > 0.0) ? rho_c * sm.hb[1] / sm.hrho[2] : 0.0;
+                    const double lo = rho_next > 0.0 ? 1.0 / rho_next : 0.0;
+                    const double ac = sm.ha[1];
+                    int active = 0;
+                    if (threadIdx.x < A.K && P.done == 0) {
+                        pole_column(A, P, threadIdx.x, c, up, ac, lo, tol_abs2, bnorm);
+                        if (P.done == 0 && c + 1 >= A.m) {
+                            P.done = 2;
+                            P.kk = c + 1;
+                            const double gg = P.g.x * P.g.x + P.g.y * P.g.y;
+                            P.bound = bnorm > 0.0 ? sqrt(gg * (double)(c + 2)) / bnorm : 0.0;
+                            const double2 z = make_double2(0.0, 0.0);
+                            if (c >= 1) put_row(A, c - 1, threadIdx.x, P.g2, P.inv2, P.r12, z);
+                            put_row(A, c, threadIdx.x, P.g1, P.inv1, z, z);
+                        }
+                        active = P.done == 0;
+                    }
+                    const int still = __syncthreads_count(active);
+                    if (still == 0 && threadIdx.x == 0) __stcg(A.stop + s, c + 1);
+                }
+            }
+            if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+            trace_mark(A, TR_LZ_SWEEP, &tcount);
+        }
+        // y_k and the coefficients of the final pass
+        if (control) {
+            if (threadIdx.x == 0) {
+                A.cols[A.nsub + s] = sweeps;
+                // the work the specified recurrence moves and computes (halo
+                // re-reads not counted): sweep 0 reads u_0 and the diagonal and
+                // writes B u_0; sweep 1 also reads B u_0 and writes u_1; later
+                // sweeps read B u_{j-1}, u_{j-1}, u_{j-2} and write u_j, B u_j
+                const double n = (double)A.n;
+                const int d = hx + hy + hz;
+                const double st_fl = 2.0 * (1 + 3 * d);
+                double by = 0.0, fl = 0.0;
+                for (int q = 0; q < sweeps; ++q) {
+                    by += q == 0 ? 40.0 : (q == 1 ? 72.0 : 88.0);
+                    fl += st_fl + (q == 0 ? 0.0 : (q == 1 ? 6.0 : 10.0));
+                }
+                const int Jn = A.mode == LZ_STEP ? max(J, 1) : J;
+                const int outs = A.mode == LZ_STEP ? 1 : A.K;
+                by += outs * 16.0 * (Jn + 1);
+                fl += outs * 8.0 * Jn;
+                if (A.bytes != nullptr) {
+                    A.bytes[0] += (unsigned long long)(by * n);
+                    A.bytes[1] += (unsigned long long)(fl * n);
+                }
+            }
+            control_finish(A, sm, S, stage_rows, P, J, s);
+        }
+        if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+        trace_mark(A, TR_LZ_SOLVE, &tcount);
+        if (!control) {
+            if (A.mode == LZ_STEP) {
+                const int Jn = max(J, 1);
+                for (int r = threadIdx.x; r < Jn; r += kLzBlock) sm.coef[r] = __ldcg(A.coef + r);
+                __syncthreads();
+                combine(A, sm.coef, u0, out, Jn, hx, hy, hz);
+            } else {
+                for (int k = 0; k < A.K; ++k) {
+                    __syncthreads();
+                    for (int r = threadIdx.x; r < J; r += kLzBlock) sm.coef[r] = __ldcg(A.coef + (size_t)k * A.m + r);
+                    __syncthreads();
+                    combine(A, sm.coef, u0, A.out + (size_t)k * A.n, J, hx, hy, hz);
+                }
+            }
+        }
+        if (s + 1 < A.nsub) {
+            if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+            trace_mark(A, TR_LZ_SUM, &tcount);
+        }
+    }
+}
+
+}  // namespace
+
+size_t lanczos_smem_bytes(int tx, int ty, int tz, int hx, int hy, int hz) {
+    const size_t ext = (size_t)(tx + 2 * hx) * (ty + 2 * hy) * (tz + 2 * hz);
+    return (ext + (size_t)tx * ty * tz) * sizeof(double2);
+}
+
+int lanczos_max_grid(size_t smem, int device) {
+    int per_sm = 0, sms = 0;
+    if (cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_kernel, kLzBlock, smem) != cudaSuccess)
+        return -1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1;
+    return per_sm * sms;
+}
+
+cudaError_t launch_lanczos(const LzArgs& args, int grid, size_t smem, cudaStream_t stream) {
+    cudaError_t e = cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* params[] = {(void*)&args};
+    return cudaLaunchCooperativeKernel((const void*)lanczos_kernel, dim3(grid), dim3(kLzBlock), params, smem, stream);
+}
+
+}  // namespace rexi

@@ -1,0 +1,70 @@
+// Shared-basis Lanczos path of the engine (host/device descriptor).
+//
+// All K shifted systems (tau H - z_k I) x_k = psi of one rational evaluation
+// (Eq. (5)) share one Krylov space K_m(B, psi), B = tau (H - c) (Sec. 5: the
+// spaces of shifted systems coincide).  B is real symmetric, so the basis obeys
+// a three-term recurrence with real coefficients; every pole keeps its own
+// Givens QR of the tridiagonal T_k - s_k [I; 0] (s_k = z_k - tau c) and stops on
+// a rigorous bound of its true residual.  One persistent cooperative launch
+// runs all substeps; one grid barrier per Krylov step.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "engine.h"
+
+namespace rexi {
+
+constexpr int kLzBlock = 256;          // threads per CTA
+constexpr int kLzMaxM = 512;           // largest Krylov dimension per substep
+constexpr int kLzMaxInterior = 2048;   // interior points of one tile
+constexpr int kLzMaxExt = 4096;        // tile plus its halo
+
+enum : int { LZ_STEP = 0, LZ_SOLVE = 1 };
+
+// trace codes (after the phase codes of the engine)
+enum : int { TR_LZ_SWEEP = 11, TR_LZ_SOLVE = 12, TR_LZ_SUM = 13 };
+
+struct LzArgs {
+    int mode;                  // LZ_STEP: nsub substeps ending in the pole sum; LZ_SOLVE: x_k for every pole
+    int n, nx, ny, nz;         // grid (x fastest); unused dimensions have extent 1
+    int K;                     // poles
+    int nsub;                  // substeps (1 in LZ_SOLVE)
+    int m;                     // largest Krylov dimension (columns) per substep
+    double a[3];               // stencil coefficients -tau hbar^2/(2 m h_d^2); 0 for extent-1 dimensions
+    const double* diag;        // [n] tau (V - c) - 2 sum_d a_d
+    const double2* shift;      // [K] centred shifts s_k = z_k - tau c
+    const double2* alpha;      // [K] weights
+    double2 alpha0;
+    double tol;                // per-pole stop: bound of ||b - A_k x_k|| <= tol ||b||
+    int stage_rows;            // rows of R the control CTA stages per chunk (fit the dynamic shared memory)
+    int tx, ty, tz;            // tile box
+    int gx, gy, gz;            // tiles per dimension
+    int ntiles;
+    const double2* in;         // LZ_STEP: psi_in; LZ_SOLVE: right-hand side b
+    double2* out;              // LZ_STEP: psi_out; LZ_SOLVE: x [K][n]
+    double2* tmp0;             // substep states (ping-pong)
+    double2* tmp1;
+    double2* basis;            // [m + 2][n]: u_1 .. u_{m+2} (u_0 is the substep's input state)
+    double2* wt;               // [2][n]: B u_j by parity of j
+    double2* part;             // [2][grid][2]: per-CTA partial sums (||u_j||^2, Re u_j^H B u_j), (Re u_{j-1}^H B u_j, 0)
+    double2* rows;             // [m][K][3]: scaled rows of every pole's R for the back substitution
+    double2* ybuf;             // [m][K]: y_k of the last substep (LZ_STEP) / unused
+    double2* coef;             // LZ_STEP: [m] coefficients of u_r in psi'; LZ_SOLVE: [K][m]
+    double* rho;               // [m + 2]: scale of every stored vector (q_j = rho_j u_j)
+    int* stop;                 // [nsub]: columns of substep s once every pole has stopped (-1 before)
+    int* cols;                 // [2 nsub]: columns and Krylov sweeps of every substep
+    ItemStats* stats;          // [K] per pole (zeroed before the launch)
+    unsigned* bar;             // [2] grid barrier (zeroed before the launch)
+    int* err;                  // sticky error word
+    unsigned long long timeout_ns;
+    unsigned long long* trace; // optional [1 + 2 cap]: (phase, ns) at every barrier
+    int trace_cap;
+    unsigned long long* bytes; // [2]: algorithmic bytes and FP64 flops of the launch (added by the control CTA)
+};
+
+cudaError_t launch_lanczos(const LzArgs& args, int grid, size_t smem, cudaStream_t stream);
+int lanczos_max_grid(size_t smem, int device);      // co-resident CTAs (<= 0: error)
+size_t lanczos_smem_bytes(int tx, int ty, int tz, int hx, int hy, int hz);
+
+}  // namespace rexi

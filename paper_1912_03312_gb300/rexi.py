@@ -31,9 +31,14 @@ def _check_state(t, n, name):
         raise ValueError("%s must be contiguous with %d elements" % (name, n))
 
 
-def options(precision="mixed", restart=30, max_iters=2000, tol=0.0, inner_tol=1e-5, R1=0.0,
+def options(precision="mixed", restart=None, max_iters=2000, tol=0.0, inner_tol=1e-5, R1=0.0,
             eps_target=1e-9, allow_substeps=True, stabilize_eps=0.0, want_backward=False, device=-1,
             shared_first_cycle=True, ortho="dcgs2", window=0):
+    """Plan options (``rexi_options``).  ``restart`` is the GMRES restart length
+    (default 30), or with ``ortho="lanczos"`` the largest Krylov dimension of a
+    substep's shared basis (default 256; there are no restarts)."""
+    if restart is None:
+        restart = 256 if ortho == "lanczos" else 30
     o = N.Options()
     N.load().rexi_options_default(C.byref(o))
     o.precision = N.REXI_MIXED if precision == "mixed" else N.REXI_FP64
@@ -48,9 +53,9 @@ def options(precision="mixed", restart=30, max_iters=2000, tol=0.0, inner_tol=1e
     o.want_backward = 1 if want_backward else 0
     o.device = int(device)
     o.shared_first_cycle = 1 if shared_first_cycle else 0
-    if ortho not in ("dcgs2", "cgs2"):
-        raise ValueError("ortho must be 'dcgs2' or 'cgs2'")
-    o.ortho = 1 if ortho == "dcgs2" else 0
+    if ortho not in ("dcgs2", "cgs2", "lanczos"):
+        raise ValueError("ortho must be 'dcgs2', 'cgs2' or 'lanczos'")
+    o.ortho = {"cgs2": 0, "dcgs2": 1, "lanczos": 2}[ortho]
     o.window = int(window)
     return o
 
@@ -246,7 +251,8 @@ class Plan:
 
     PHASES = {0: "substep start", 1: "FP64 residual", 2: "cycle decision", 3: "matvec + dot sweep 1",
               4: "CGS sweep 2", 5: "CGS update", 6: "Givens", 7: "x update", 8: "pole sum",
-              9: "DCGS2 matvec + dots", 10: "DCGS2 update + Givens", 99: "launch"}
+              9: "DCGS2 matvec + dots", 10: "DCGS2 update + Givens", 11: "Lanczos sweep",
+              12: "Lanczos back substitution", 13: "Lanczos pole sum", 99: "launch"}
 
     def set_timeout(self, seconds=0.0):
         """Limit of every device-side wait (``rexi_plan_set_timeout``; <= 0: the 4 s default)."""
