@@ -58,6 +58,8 @@ def parse_args():
                     help="processes for the all-cores oracle timings (0: every host core)")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the timings of the other configurations (1D, 3D, batched, learnable)")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip the comparison of the first timed step with the oracle's step")
     ap.add_argument("--no-autotune", action="store_true")
@@ -285,18 +287,31 @@ def run_cpu_sample(R1, budget, tol, max_solves=64):
 _PW = None
 
 
-def _pole_worker_init(root, R1):
+def _workload_problem(wl, name):
+    """(grid, V, psi0, K, dt) of a benchmark workload: "c2" the 2D four-well
+    problem, "c1" the 1D harmonic oscillator, "c4:i" problem i of the batch."""
+    if name == "c1":
+        cfg = wl.config_1d_harmonic()
+    elif name.startswith("c4:"):
+        cb = wl.config_batched()
+        p = cb["problems"][int(name[3:])]
+        return p["grid"], p["V"], p["psi0"], cb["K"], cb["dt"]
+    else:
+        cfg = wl.config_2d_wells()
+    return cfg["grid"], cfg["V"], cfg["psi0"], cfg["K"], cfg["dt"]
+
+
+def _pole_worker_init(root, R1, name="c2"):
     global _PW
     sys.path.insert(0, root)
     import workloads as wl
     from oracle import plan as oplan, step as ostep, tables
-    cfg = wl.config_2d_wells()
-    g, V = cfg["grid"], cfg["V"]
+    g, V, _, K, dt = _workload_problem(wl, name)
     h = oplan.grid_spacing(g["n"], g["lo"], g["hi"])
     _, _, c, W = oplan.spectral_enclosure(V, h)
-    ns = oplan.substeps(cfg["dt"], W, R1)
-    tau = cfg["dt"] / ns
-    sig, bet, _ = tables.poles(cfg["K"], R1)
+    ns = oplan.substeps(dt, W, R1)
+    tau = dt / ns
+    sig, bet, _ = tables.poles(K, R1)
     z, alpha, alpha0 = oplan.physical_poles(sig, bet, tau, c)
     _PW = {"ostep": ostep, "V": V, "h": h, "tau": tau, "z": z, "alpha": alpha, "alpha0": alpha0, "ns": ns}
 
@@ -313,7 +328,7 @@ def _pole_worker_ready(_):
     return _PW["ns"], len(_PW["z"]), _PW["alpha0"]
 
 
-def _oracle_steps_parallel(R1, tol, workers, nsteps, budget, out_path=None):
+def _oracle_steps_parallel(R1, tol, workers, nsteps, budget, out_path=None, name="c2"):
     """Whole user steps of the oracle on `workers` processes, from the
     workload's initial state: every substep solves the K poles of Eq. (5) for
     the current state (one solve per task) and sums alpha_0 psi + sum_k
@@ -325,10 +340,10 @@ def _oracle_steps_parallel(R1, tol, workers, nsteps, budget, out_path=None):
     import numpy as np
     sys.path.insert(0, ROOT)
     import workloads as wl
-    psi = np.ascontiguousarray(wl.config_2d_wells()["psi0"], dtype=np.complex128)
+    psi = np.ascontiguousarray(_workload_problem(wl, name)[2], dtype=np.complex128)
     ctx = mp.get_context("spawn")
     with ProcessPoolExecutor(max_workers=workers, mp_context=ctx, initializer=_pole_worker_init,
-                             initargs=(ROOT, R1)) as ex:
+                             initargs=(ROOT, R1, name)) as ex:
         ns, K, alpha0 = list(ex.map(_pole_worker_ready, range(workers)))[0]   # every worker started
         times, iters = [], 0
         t_all = time.perf_counter()
@@ -353,30 +368,30 @@ import json, sys
 sys.path.insert(0, %(root)r)
 import bench
 print(json.dumps(bench._oracle_steps_parallel(%(R1)r, %(tol)r, %(workers)d, %(nsteps)d, %(budget)r,
-                                              %(out_path)r)))
+                                              %(out_path)r, %(name)r)))
 """
 
 
-def run_parallel_sample(R1, tol, workers, nsteps, budget, out_path=None):
+def run_parallel_sample(R1, tol, workers, nsteps, budget, out_path=None, name="c2"):
     """_oracle_steps_parallel in a child process (single-threaded BLAS per worker)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = PARALLEL_SAMPLE % {"root": ROOT, "R1": R1, "tol": tol, "workers": workers, "nsteps": nsteps,
-                              "budget": budget, "out_path": out_path}
+                              "budget": budget, "out_path": out_path, "name": name}
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError("parallel oracle sample failed: " + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_first_step(R1, workers):
-    """The oracle's state after one user step of the benchmark workload from its
-    initial state (pole solves to relative residual 1e-14), computed on the host
-    cores; the reference for the GPU path's rel_err_vs_oracle."""
+def oracle_first_step(R1, workers, name="c2"):
+    """The oracle's state after one user step of a workload from its initial
+    state (pole solves to relative residual 1e-14), computed on the host cores;
+    the reference for the GPU path's rel_err_vs_oracle."""
     import numpy as np
     fd, path = tempfile.mkstemp(suffix=".npy")
     os.close(fd)
     try:
-        d = run_parallel_sample(R1, 1e-14, workers, 1, 0.0, out_path=path)
+        d = run_parallel_sample(R1, 1e-14, workers, 1, 0.0, out_path=path, name=name)
         return np.load(path), d
     finally:
         os.unlink(path)
@@ -424,6 +439,172 @@ def reference_arm(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _timed_ms(fn, flush, stream, warm=2, nt=5):
+    """Mean ms of fn() over nt calls: CUDA events on `stream`, L2 flushed before each."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(nt):
+        flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / nt
+
+
+def _work_line(name, ms, units_per_call, n_pts_poles, bytes_, flops, extra=None):
+    d = {"ms_per_step": ms, "steps_per_s": units_per_call * 1000.0 / ms,
+         "grid_pts_poles_per_s": n_pts_poles * 1000.0 / ms,
+         "fp64_tflops": flops / (ms * 1e-3) / 1e12, "fp64_frac_of_nominal": flops / (ms * 1e-3) / 1e12 /
+         NOMINAL_FP64_TFLOPS, "gbs": bytes_ / (ms * 1e-3) / 1e9,
+         "counts": "kernel-counted bytes and FP64 flops of the launches"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def other_workloads(args, flush, stream, dev):
+    """The other configurations, each timed the same way as the headline (CUDA
+    events, L2 flushed before every call, states evolving where the workload
+    has several steps): 1D harmonic (K=16, dt=1, tol 1e-12), 3D softened
+    Coulomb 128^3 (K=32: K=64 is refused by the plan), 64 batched 2D problems
+    (one graph-captured batched launch of the item engine in the workload's
+    mixed precision, and 64 graph-captured single launches of the Lanczos
+    kernel), and the learnable 256^2 problem (forward step plus adjoint)."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_1912_03312_gb300 import Plan, RexiEvolve, step_batched
+    res = {}
+    cores = host_cores(args.cpu_workers)
+
+    # C1: 1D harmonic oscillator
+    cfg = wl.config_1d_harmonic()
+    g = cfg["grid"]
+    p = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], cfg["K"], precision="fp64", ortho="lanczos",
+             tol=cfg["tol"])
+    info = p.info()
+    x = torch.from_numpy(cfg["psi0"]).to(dev)
+    out = torch.empty_like(x)
+    first, st = p.step(x, stats=True)
+    ms = _timed_ms(lambda: p.step(x, out=out), flush, stream, nt=20)
+    line = _work_line("c1", ms, 1, 256 * cfg["K"] * info["n_sub"], st["bytes"], st["flops64"],
+                      {"workload": cfg["name"], "n_sub": info["n_sub"], "R1": info["R1"],
+                       "krylov_columns_max": st["max_iters_seen"], "path": "Lanczos kernel, FP64",
+                       "roofline_note": "n = 256 fits in L2: launch-latency bound, the fractions mean little"})
+    if not args.no_oracle_check:
+        try:
+            ref_np, _ = oracle_first_step(info["R1"], cores, "c1")
+            got = first.cpu().numpy().ravel()
+            line["rel_err_vs_oracle"] = float(np.linalg.norm(got - ref_np.ravel()) / np.linalg.norm(ref_np))
+        except Exception as e:  # reported, not fatal
+            line["rel_err_vs_oracle"] = "failed: %s" % e
+    res["c1_1d_harmonic_N256_K16"] = line
+    del p
+
+    # C3: 3D softened Coulomb, 128^3, K=32, dt=0.25, states evolving
+    cfg = wl.config_3d_coulomb()
+    g = cfg["grid"]
+    p = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], 32, precision="fp64", ortho="lanczos")
+    info = p.info()
+    n = int(np.prod(g["n"]))
+    bufs = [torch.from_numpy(cfg["psi0"]).to(dev), None]
+    bufs[1] = torch.empty_like(bufs[0])
+
+    def step3():                        # the state evolves: ping-pong between two buffers
+        p.step(bufs[0], out=bufs[1])
+        bufs.reverse()
+    _, st = p.step(bufs[0], stats=True)
+    ms = _timed_ms(step3, flush, stream, nt=5)
+    res["c3_3d_coulomb_128cube_K32"] = _work_line(
+        "c3", ms, 1, n * 32 * info["n_sub"], st["bytes"], st["flops64"],
+        {"workload": "3d_coulomb_128cube (K=32; K=64 refused: double-double plan arithmetic)",
+         "n_sub": info["n_sub"], "R1": info["R1"], "krylov_columns_max": st["max_iters_seen"],
+         "path": "Lanczos kernel, FP64", "parity": "tests: per-pole 1e-10 at 128^3, plane wave"})
+    del p, bufs
+
+    # C4: 64 uneven 2D problems
+    cfg = wl.config_batched()
+    probs = cfg["problems"]
+    sizes = [int(np.prod(q["grid"]["n"])) for q in probs]
+    ins = [torch.from_numpy(q["psi0"]).to(dev) for q in probs]
+    outs = [torch.empty_like(t) for t in ins]
+    plans = [Plan(q["grid"]["n"], q["grid"]["lo"], q["grid"]["hi"], q["V"], cfg["dt"], cfg["K"], precision="mixed")
+             for q in probs]
+    nsub = [pl.info()["n_sub"] for pl in plans]
+    work = sum(sz * cfg["K"] * ns_ for sz, ns_ in zip(sizes, nsub))
+    _, sts = step_batched(plans, ins, outs, stats=True)
+    step_batched(plans, ins, outs)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step_batched(plans, ins, outs)
+    ms = _timed_ms(graph.replay, flush, stream, nt=5)
+    smallest = int(np.argmin(sizes))
+    line = _work_line("c4", ms, 1, work, sts[0]["bytes"], sts[0]["flops64"],
+                      {"workload": cfg["name"], "problems": len(probs), "points_total": sum(sizes),
+                       "path": "item engine, c64 Krylov + FP64 refinement (the workload's precision), one "
+                               "graph-captured batched launch",
+                       "unit_note": "one step = one step of all 64 problems"})
+    batched_first = outs[smallest].clone()
+    del plans, graph
+    lplans = [Plan(q["grid"]["n"], q["grid"]["lo"], q["grid"]["hi"], q["V"], cfg["dt"], cfg["K"], precision="fp64",
+                   ortho="lanczos") for q in probs]
+    for pl, a, b in zip(lplans, ins, outs):
+        pl.step(a, out=b)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for pl, a, b in zip(lplans, ins, outs):
+            pl.step(a, out=b)
+    ms_l = _timed_ms(graph.replay, flush, stream, nt=5)
+    line["lanczos_singles"] = {"ms_per_step": ms_l, "steps_per_s": 1000.0 / ms_l,
+                               "grid_pts_poles_per_s": work * 1000.0 / ms_l,
+                               "path": "64 graph-captured single launches of the Lanczos kernel, FP64"}
+    if not args.no_oracle_check:
+        try:
+            ref_np, _ = oracle_first_step(68.0, cores, "c4:%d" % smallest)
+            for key, got in (("rel_err_vs_oracle", batched_first), ("lanczos_rel_err_vs_oracle", outs[smallest])):
+                got = got.cpu().numpy().ravel()
+                line[key] = float(np.linalg.norm(got - ref_np.ravel()) / np.linalg.norm(ref_np))
+            line["oracle_problem"] = "the smallest problem (%s)" % "x".join(map(str, probs[smallest]["grid"]["n"]))
+        except Exception as e:  # reported, not fatal
+            line["rel_err_vs_oracle"] = "failed: %s" % e
+    res["c4_batched_64x2d_K32"] = line
+    del lplans, graph, ins, outs
+
+    # C5: learnable potential, forward step + adjoint (10 steps each way)
+    cfg = wl.config_learnable()
+    g = cfg["grid"]
+    p = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], cfg["K"], precision="fp64", ortho="lanczos")
+    info = p.info()
+    n = int(np.prod(g["n"]))
+    psi0 = torch.from_numpy(cfg["psi0"]).to(dev)
+    target = torch.from_numpy(wl.wave_packet(g, (-8.0, 1.0), 1.0, (3.0, 0.5))).to(dev)
+    Vt = torch.tensor(cfg["V"], dtype=torch.float64, device=dev, requires_grad=True)
+
+    def fwd_bwd():
+        Vt.grad = None
+        psiT = RexiEvolve.apply(Vt, psi0, p, cfg["nsteps"])
+        loss = (psiT - target).abs().pow(2).sum()
+        loss.backward()
+    ms = _timed_ms(fwd_bwd, flush, stream, warm=1, nt=3)
+    res["c5_learnable_256x256_K32"] = _work_line(
+        "c5", ms, cfg["nsteps"], n * cfg["K"] * info["n_sub"] * cfg["nsteps"] * 3, 0.0, 0.0,
+        {"workload": cfg["name"], "n_sub": info["n_sub"],
+         "path": "forward: Lanczos kernel (FP64); adjoint: item engine (FP64, shared first cycle, window 2); "
+                 "autograd through RexiEvolve",
+         "unit_note": "steps_per_s counts forward+adjoint step pairs; grid_pts_poles counts the forward "
+                      "solves and the two adjoint solve sets", "fp64_tflops": None, "gbs": None})
+    del p
+    return res
 
 
 def ours(args):
@@ -597,6 +778,12 @@ def ours(args):
                                            "gbs": cb / (cms * 1e-3) / 1e9,
                                            "hbm_frac_of_measured": cb / (cms * 1e-3) / 1e9 / peak}}
         extra["other_paths"] = paths
+
+    if not args.no_other_workloads and rank == 0 and args.n == 512:
+        try:
+            extra["other_workloads"] = other_workloads(args, flush, stream, dev)
+        except Exception as e:  # reported, not fatal
+            extra["other_workloads"] = {"failed": repr(e)}
 
     # end to end through the C ABI with host buffers (copies inside the timed
     # region), on every state the device-timed steps started from, with the same

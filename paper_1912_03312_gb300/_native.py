@@ -24,6 +24,7 @@ REXI_MIXED = 1
 REXI_MAX_POLES = 256
 REXI_MAX_RESTART = 64
 REXI_MAX_RESTART_FULL = 31
+REXI_MAX_KRYLOV = 512
 
 
 class Grid(C.Structure):

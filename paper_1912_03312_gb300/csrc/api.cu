@@ -103,11 +103,12 @@ struct rexi_plan {
     int lz_cps = 2;                              // CTAs per SM
     int lz_target = 0;                           // largest interior points per tile (0: choose)
     int lz_grid = 0, lz_stage = 1;
+    bool lz_resident = false;                    // one tile per CTA, state kept in shared memory
     size_t lz_smem = 0;
     int lz_part_cap = 0;                         // CTAs the partial buffer holds
     double2* d_lz_basis = nullptr;
     double2* d_lz_wt = nullptr;
-    double2* d_lz_part = nullptr;
+    float4* d_lz_part = nullptr;
     double2* d_lz_rows = nullptr;
     double2* d_lz_ybuf = nullptr;
     double2* d_lz_coef = nullptr;
@@ -486,18 +487,28 @@ int collect(rexi_plan* p, cudaStream_t stream, int nitems, int item_offset, int 
 // ---- shared-basis Lanczos path ----------------------------------------------
 
 // Tile box of the Lanczos kernel: the box (at most `target` interior points,
-// tile plus halo within the kernel's staging limit) that minimises the work of
-// the busiest CTA, counting 10 units per interior point (update and stencil)
-// and 6 per point of the extended box (the update, recomputed on the halo).
-// Then the grid (CTAs per SM as requested, within occupancy), the dynamic
-// shared memory and the rows the control CTA stages per chunk.
+// tile plus halo within the kernel's staging limit, shared memory for the
+// requested CTAs per SM) that minimises the work of the busiest SM, counting
+// 10 units per interior point (update and stencil), 6 per point of the
+// extended box (the update, recomputed on the halo) and 4600 per tile, with tile t on CTA
+// 1 + t mod (G - 1) and CTA c on SM c mod (SMs) (the order in which the
+// resident grid fills the SMs).  Then the grid, the dynamic shared memory and
+// the rows the control CTA stages per chunk.
 int lz_configure(rexi_plan* p) {
     const int sms = sm_count(p->device);
     const int hx = p->a[0] != 0.0 ? 1 : 0, hy = p->a[1] != 0.0 ? 1 : 0, hz = p->a[2] != 0.0 ? 1 : 0;
     const int nx = p->dims[0], ny = p->dims[1], nz = p->dims[2];
     const int target = p->lz_target > 0 ? std::min(p->lz_target, rexi::kLzMaxInterior) : rexi::kLzMaxInterior;
     const int cps = std::max(1, std::min(p->lz_cps, 8));
-    const int tile_ctas = std::max(1, cps * sms - 1);
+    const int G = cps * sms;
+    const int tile_ctas = std::max(1, G - 1);
+    int smem_sm = 0;
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device) != cudaSuccess)
+        return REXI_ECUDA;
+    const size_t stat = rexi::lanczos_static_smem();
+    const size_t per_cta = (size_t)smem_sm / cps;
+    const size_t row_bytes = (size_t)p->K * 3 * sizeof(double2);
+    const size_t ctl_min = std::min<size_t>(8 * row_bytes, 96 * 1024);
     long long best = -1;
     int bx = 1, by = 1, bz = 1;
     const int widths[] = {16, 32, 64, 128, 256, 512, 1024, 2048};
@@ -505,6 +516,7 @@ int lz_configure(rexi_plan* p) {
     for (int w : widths)
         if (w < nx) txs.push_back(w);
     if (nx <= 2048) txs.push_back(nx);
+    std::vector<long long> load(sms);
     for (int tx : txs) {
         if (tx > target) continue;
         for (int tz = 1; tz <= std::min(nz, target / tx); ++tz) {
@@ -512,12 +524,28 @@ int lz_configure(rexi_plan* p) {
                 const long long I = (long long)tx * ty * tz;
                 const long long E = (long long)(tx + 2 * hx) * (ty + 2 * hy) * (tz + 2 * hz);
                 if (E > rexi::kLzMaxExt) continue;
-                const long long ntiles =
-                    (long long)((nx + tx - 1) / tx) * ((ny + ty - 1) / ty) * ((nz + tz - 1) / tz);
-                const long long rounds = (ntiles + tile_ctas - 1) / tile_ctas;
-                const long long cost = rounds * (10 * I + 6 * E);
-                if (best < 0 || cost < best || (cost == best && tx > bx)) {
-                    best = cost;
+                const size_t smem = std::max(rexi::lanczos_smem_bytes(tx, ty, tz, hx, hy, hz, false), ctl_min);
+                if (smem + stat + 1024 > per_cta) continue;
+                const int gx = (nx + tx - 1) / tx, gy = (ny + ty - 1) / ty, gz = (nz + tz - 1) / tz;
+                const long long ntiles = (long long)gx * gy * gz;
+                if (ntiles > 64LL * tile_ctas) continue;
+                std::fill(load.begin(), load.end(), 0LL);
+                long long worst = 0;
+                for (long long t = 0; t < ntiles; ++t) {
+                    // the actual (ragged) extent of tile t
+                    const int ix = (int)(t % gx), iy = (int)((t / gx) % gy), iz = (int)(t / ((long long)gx * gy));
+                    const long long ax = std::min(tx, nx - ix * tx), ay = std::min(ty, ny - iy * ty),
+                                    az = std::min(tz, nz - iz * tz);
+                    // plus a fixed cost per tile (staging, three CTA barriers), measured
+                    // at about the work of 450 interior points
+                    const long long cost =
+                        10 * ax * ay * az + 6 * (ax + 2 * hx) * (ay + 2 * hy) * (az + 2 * hz) + 4600;
+                    const int sm_of = (int)((1 + t % tile_ctas) % sms);
+                    load[sm_of] += cost;
+                    worst = std::max(worst, load[sm_of]);
+                }
+                if (best < 0 || worst < best || (worst == best && tx > bx)) {
+                    best = worst;
                     bx = tx;
                     by = ty;
                     bz = tz;
@@ -525,19 +553,21 @@ int lz_configure(rexi_plan* p) {
             }
         }
     }
-    if (best < 0) return REXI_EINVAL;               // a row longer than 2048 points and no narrower box
+    if (best < 0) return REXI_EINVAL;               // no box fits (a row longer than 2048 points)
     p->lz_tx = bx;
     p->lz_ty = by;
     p->lz_tz = bz;
-    size_t smem = rexi::lanczos_smem_bytes(bx, by, bz, hx, hy, hz);
-    // the control CTA stages rows of R (K poles x 3 entries) through the same memory
-    const size_t row_bytes = (size_t)p->K * 3 * sizeof(double2);
-    smem = std::max(smem, std::min<size_t>(8 * row_bytes, 96 * 1024));
+    // resident mode when every tile CTA owns at most one tile and its state fits
+    const long long ntiles = (long long)((nx + bx - 1) / bx) * ((ny + by - 1) / by) * ((nz + bz - 1) / bz);
+    const size_t smem_res = std::max(rexi::lanczos_smem_bytes(bx, by, bz, hx, hy, hz, true), ctl_min);
+    p->lz_resident = ntiles <= tile_ctas && smem_res + stat + 1024 <= per_cta;
+    const size_t smem =
+        p->lz_resident ? smem_res : std::max(rexi::lanczos_smem_bytes(bx, by, bz, hx, hy, hz, false), ctl_min);
     p->lz_stage = (int)std::max<size_t>(1, std::min<size_t>(64, smem / row_bytes));
     p->lz_smem = smem;
     const int maxg = rexi::lanczos_max_grid(smem, p->device);
     if (maxg < 2) return REXI_ECUDA;
-    p->lz_grid = std::min(maxg, cps * sms);
+    p->lz_grid = std::min(maxg, G);
     if (p->lz_grid > p->lz_part_cap) return REXI_EINVAL;
     return REXI_OK;
 }
@@ -548,7 +578,7 @@ int lz_alloc(rexi_plan* p) {
     p->lz_part_cap = 8 * sm_count(p->device);
     if ((st = dalloc(p, &p->d_lz_basis, (m + 2) * n))) return st;
     if ((st = dalloc(p, &p->d_lz_wt, 2 * n))) return st;
-    if ((st = dalloc(p, &p->d_lz_part, 4 * (size_t)p->lz_part_cap))) return st;
+    if ((st = dalloc(p, &p->d_lz_part, 2 * (size_t)p->lz_part_cap))) return st;
     if ((st = dalloc(p, &p->d_lz_rows, m * K * 3))) return st;
     if ((st = dalloc(p, &p->d_lz_ybuf, m * K))) return st;
     if ((st = dalloc(p, &p->d_lz_coef, m * K))) return st;
@@ -600,6 +630,7 @@ int lz_launch(rexi_plan* p, int mode, const void* in, void* out, cudaStream_t st
     A.gy = (A.ny + A.ty - 1) / A.ty;
     A.gz = (A.nz + A.tz - 1) / A.tz;
     A.ntiles = A.gx * A.gy * A.gz;
+    A.resident = p->lz_resident ? 1 : 0;
     A.in = (const double2*)in;
     A.out = (double2*)out;
     A.tmp0 = p->d_tmp0;

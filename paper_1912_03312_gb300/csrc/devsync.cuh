@@ -36,6 +36,62 @@ __device__ __forceinline__ float f64_to_f32_rz(double x) {
     return __uint_as_float(sign | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
 }
 
+// ---- bulk copies global -> shared with completion on an mbarrier -----------
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+// Makes the initialised mbarrier visible to the asynchronous proxy.
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One arrival that also announces the bytes the phase's copies will deliver.
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Global to shared copy of `bytes` (a multiple of 16, both addresses 16-byte
+// aligned) whose completion is counted on mbarrier b.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(b))
+                 : "memory");
+}
+// Orders this thread's earlier generic-proxy accesses (and those it has
+// acquired) before its later bulk copies.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+// Bounded wait for phase `parity` of mbarrier b.  On expiry the sticky error
+// word is set and a second wait (at least 10 ms) lets copies still in flight
+// land before the buffer is reused or the CTA leaves; the launch then ends at
+// its next grid barrier.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, int* err,
+                                          unsigned long long timeout_ns) {
+    unsigned long long t0 = global_ns();
+    while (!mbar_test(b, parity)) {
+        if (global_ns() - t0 > timeout_ns) {
+            atomicExch(err, kErrTimeout);
+            const unsigned long long drain = timeout_ns > 10000000ull ? timeout_ns : 10000000ull;
+            t0 = global_ns();
+            while (!mbar_test(b, parity) && global_ns() - t0 <= drain) {
+            }
+            return false;
+        }
+    }
+    return true;
+}
+
 // All CTAs of the co-resident grid meet here.  bar[0] counts arrivals and
 // bar[1] completed barriers; both are zeroed before every launch.  The arrival
 // that makes the count a multiple of the grid size publishes the barrier's
@@ -48,7 +104,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* err, unsigned long
     if (threadIdx.x == 0) {
         unsigned* count = bar;
         unsigned* done = bar + 1;
-        __threadfence();
+        __threadfence();                                   // the CTA's writes before its arrival
         const unsigned prev = atomicAdd(count, 1u);
         const unsigned target = prev / gridDim.x + 1u;
         if (prev + 1u == target * gridDim.x) {

@@ -8,16 +8,20 @@
 //          recomputed on the halo from the stored vectors so no second barrier
 //          is needed before the stencil)
 //   B u_j                                      (stencil from shared memory)
-//   partial sums of ||u_j||^2, Re u_j^H B u_j, Re u_{j-1}^H B u_j
+//   partial sums of ||u_j||^2 and Re u_j^H B u_j
 //
-// The inner products are compensated sums of FP32 hi/lo pieces (about 1e-13
-// relative; the FP64 pipe stays free for the recurrence), then one grid
-// barrier; every CTA reduces the partials in FP64 in the same fixed order
-// and derives the same coefficients: rho_j = 1/||u_j||, a_j = (u_j^H B u_j) /
-// ||u_j||^2 (the Rayleigh quotient, real because B is real symmetric), b_j =
-// (u_{j-1}^H B u_j) / ||u_{j-1}||^2.  With q_j = rho_j u_j the recurrence reads
+// The inputs of the update (B u_{j-1}, u_{j-1}, u_{j-2} on the tile and its
+// halo, the diagonal on the tile) are staged in shared memory by asynchronous
+// copies issued as soon as the barrier opens, while the CTA reduces the
+// partials; the inner products are compensated sums of FP32 hi/lo pieces
+// (about 1e-13 relative; the FP64 pipe stays free for the recurrence).  Every
+// CTA reduces the partials in FP64 in the same fixed order and derives the
+// same coefficients: rho_j = 1/||u_j||, a_j = (u_j^H B u_j) / ||u_j||^2 (the
+// Rayleigh quotient, real because B is real symmetric) and the Lanczos
+// coefficient of u_{j-1}, b_j = rho_{j-1} / rho_j^2, which makes the
+// tridiagonal matrix symmetric.  With q_j = rho_j u_j the recurrence reads
 //
-//   B q_j = (1/rho_{j+1}) q_{j+1} + a_j q_j + (rho_j b_j / rho_{j-1}) q_{j-1},
+//   B q_j = (1/rho_{j+1}) q_{j+1} + a_j q_j + (1/rho_j) q_{j-1},
 //
 // exactly for the coefficients used (whatever the accuracy of the inner
 // products that chose them), so B Q_k = Q_{k+1} T_k holds to FP64 rounding
@@ -55,8 +59,8 @@ struct LzSmem {
     double n_last;           // ||u_{j-1}||^2 of the last reduced sweep
     double n_prev;           // ||u_{j-2}||^2
     double n0;               // ||u_0||^2 of the substep
-    double hrho[3], ha[3], hb[3];   // control: (rho, a, b) of sweeps j-1, j-2, j-3
-    double red[kLzWarps][3];
+    double hrho[3], ha[3], hn[3];   // (rho, a, n) of sweeps j-1, j-2, j-3
+    float red[kLzWarps][4];  // per-warp double-float sums (n_hi, n_lo, p_hi, p_lo)
     int stop;
     double2 coef[kLzMaxM];   // final pass: coefficients of the stored vectors
 };
@@ -115,22 +119,25 @@ __device__ __forceinline__ void givens(double2 x, double h, double* c, double2* 
         *c = 1.0;
         *s = make_double2(0.0, 0.0);
         *r = x;
-        *inv = xx > 0.0 ? make_double2(x.x / xx, -x.y / xx) : make_double2(0.0, 0.0);
+        const double rx = xx > 0.0 ? rsqrt(xx) : 0.0;
+        *inv = make_double2(x.x * rx * rx, -x.y * rx * rx);
         return;
     }
     if (xx == 0.0) {
         *c = 0.0;
         *s = make_double2(1.0, 0.0);
         *r = make_double2(h, 0.0);
-        *inv = make_double2(1.0 / h, 0.0);
+        const double rh = rsqrt(h * h);
+        *inv = make_double2(rh, 0.0);
         return;
     }
-    const double nx = sqrt(xx), nu = sqrt(xx + h * h);
-    const double2 ph = make_double2(x.x / nx, x.y / nx);
-    *c = nx / nu;
-    *s = csc(ph, h / nu);
-    *r = csc(ph, nu);
-    *inv = make_double2(ph.x / nu, -ph.y / nu);
+    // two reciprocal square roots, no division
+    const double rnx = rsqrt(xx), nu2 = fma(h, h, xx), rnu = rsqrt(nu2);
+    const double2 ph = make_double2(x.x * rnx, x.y * rnx);
+    *c = xx * rnx * rnu;
+    *s = csc(ph, h * rnu);
+    *r = csc(ph, nu2 * rnu);
+    *inv = make_double2(ph.x * rnu, -ph.y * rnu);
 }
 
 __device__ __forceinline__ void trace_mark(const LzArgs& A, int code, int* tcount) {
@@ -145,26 +152,95 @@ __device__ __forceinline__ void trace_mark(const LzArgs& A, int code, int* tcoun
     }
 }
 
-// Sum of the partials of sweep `par` over the tile CTAs (1..G-1), in FP64 and
-// the same fixed order in every CTA; warp 0 computes, every lane gets the sums.
-__device__ __forceinline__ double3 reduce_partials(const LzArgs& A, int par) {
-    double3 s = make_double3(0.0, 0.0, 0.0);
-    const int lane = threadIdx.x & 31;
-    const double2* p = A.part + (size_t)par * gridDim.x * 2;
-    for (int c = 1 + lane; c < (int)gridDim.x; c += 32) {
-        const double2 v = __ldcg(p + 2 * c), w = __ldcg(p + 2 * c + 1);
-        s.x += v.x;
-        s.y += v.y;
-        s.z += w.x;
-    }
+// (h, l) += (bh, bl) in double-float: Knuth's two-sum of the leading parts,
+// the trailing parts added to its error, renormalised.  Symmetric in its two
+// operands, so butterfly reductions leave the same sum in every lane.
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+    const float s = __fadd_rn(h, bh);
+    const float z = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, z)), __fsub_rn(bh, z));
+    const float t = __fadd_rn(__fadd_rn(l, bl), e);
+    h = __fadd_rn(s, t);
+    l = __fsub_rn(t, __fsub_rn(h, s));
+}
+
+// Sum over the warp of the double-float pair (n, p) (butterfly: every lane
+// ends with the same sums); FP32 pipe only.
+__device__ __forceinline__ void warp_df_sum(float& nh, float& nl, float& ph, float& pl) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-        s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
+        const float a = __shfl_xor_sync(0xffffffffu, nh, o), b = __shfl_xor_sync(0xffffffffu, nl, o);
+        const float c = __shfl_xor_sync(0xffffffffu, ph, o), d = __shfl_xor_sync(0xffffffffu, pl, o);
+        df_add(nh, nl, a, b);
+        df_add(ph, pl, c, d);
     }
-    return s;
 }
+
+// CTA sum of the pair; thread 0 receives (n_hi, n_lo, p_hi, p_lo).
+__device__ __forceinline__ float4 cta_df_sum(LzSmem& sm, float nh, float nl, float ph, float pl) {
+    warp_df_sum(nh, nl, ph, pl);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();                               // sm.red may still be read from the last sum
+    if (lane == 0) {
+        sm.red[warp][0] = nh;
+        sm.red[warp][1] = nl;
+        sm.red[warp][2] = ph;
+        sm.red[warp][3] = pl;
+    }
+    __syncthreads();
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kLzWarps; ++w) {
+            df_add(t.x, t.y, sm.red[w][0], sm.red[w][1]);
+            df_add(t.z, t.w, sm.red[w][2], sm.red[w][3]);
+        }
+    return t;
+}
+
+// Partials (||u||^2, Re u^H B u, each as a double-float pair) of sweep `par`
+// of the tile CTAs (1..G-1): every thread loads its share (one round of loads,
+// issued before the sweep's copies so they are not queued behind them) ...
+struct PartLoad {
+    float4 v[5];
+};
+__device__ __forceinline__ void load_partials(const LzArgs& A, int par, PartLoad& L) {
+    const float4* p = A.part + (size_t)par * gridDim.x;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int c = 1 + threadIdx.x + q * kLzBlock;
+        L.v[q] = c < (int)gridDim.x ? __ldcg(p + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+// ... and the CTA sums them in double-float on the FP32 pipe (the FP64 pipe is
+// busy with the co-resident CTA's sweep), in the same fixed order in every
+// CTA; thread 0 receives the sums as FP64.
+__device__ __forceinline__ double2 reduce_partials(const LzArgs& A, LzSmem& sm, int par, const PartLoad& L) {
+    float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        df_add(nh, nl, L.v[q].x, L.v[q].y);
+        df_add(ph, pl, L.v[q].z, L.v[q].w);
+    }
+    const float4* p = A.part + (size_t)par * gridDim.x;
+    for (int c = 1 + threadIdx.x + 5 * kLzBlock; c < (int)gridDim.x; c += kLzBlock) {
+        const float4 w = __ldcg(p + c);
+        df_add(nh, nl, w.x, w.y);
+        df_add(ph, pl, w.z, w.w);
+    }
+    const float4 t = cta_df_sum(sm, nh, nl, ph, pl);
+    return make_double2((double)t.x + (double)t.y, (double)t.z + (double)t.w);
+}
+
+// ---- asynchronous copies global -> shared (completion per thread) ---------
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ---- compensated (double-float) inner products on the FP32 pipe -------------
 //
@@ -216,181 +292,249 @@ __device__ __forceinline__ void df_madd(float& sh, float& sl, float ah, float al
 
 constexpr int kCh = 4;          // points per thread whose loads are issued together
 
-// Global index of extended point e of tile T (periodic wrap), and its interior
-// index (-1 on the halo).
-__device__ __forceinline__ size_t ext_point(const LzArgs& A, const Tile& T, int e, int hx, int hy, int hz,
+// Coordinates of the points e, e + kLzBlock, e + 2 kLzBlock, ... of a box
+// (x fastest) kept incrementally: no division per point.
+struct Walk {
+    int x, y, z, dx, dy, dz;
+    __device__ __forceinline__ void init(int e, int bx, int by) {
+        x = e % bx;
+        const int r = e / bx;
+        y = r % by;
+        z = r / by;
+        dx = kLzBlock % bx;
+        const int dr = kLzBlock / bx;
+        dy = dr % by;
+        dz = dr / by;
+    }
+    __device__ __forceinline__ void next(int bx, int by) {
+        x += dx;
+        y += dy;
+        z += dz;
+        if (x >= bx) {
+            x -= bx;
+            ++y;
+        }
+        if (y >= by) {
+            y -= by;
+            ++z;
+        }
+    }
+};
+
+// Global and extended index of the interior point at (x, y, z) of tile T.
+__device__ __forceinline__ size_t int_index(const LzArgs& A, const Tile& T, const Walk& w, int hx, int hy, int hz,
+                                            int* e) {
+    *e = (w.x + hx) + T.ex * ((w.y + hy) + T.ey * (w.z + hz));
+    return (size_t)(T.x0 + w.x) + (size_t)A.nx * ((size_t)(T.y0 + w.y) + (size_t)A.ny * (size_t)(T.z0 + w.z));
+}
+
+// Global index of the extended-box point at walk coordinates w of tile T
+// (periodic wrap) and its interior index (-1 on the halo).
+__device__ __forceinline__ size_t ext_index(const LzArgs& A, const Tile& T, const Walk& w, int hx, int hy, int hz,
                                             int* inner) {
-    const int ex = e % T.ex, r = e / T.ex, ey = r % T.ey, ez = r / T.ey;
-    const int gxx = wrapi(T.x0 - hx + ex, A.nx);
-    const int gyy = wrapi(T.y0 - hy + ey, A.ny);
-    const int gzz = wrapi(T.z0 - hz + ez, A.nz);
-    const int ix = ex - hx, iy = ey - hy, iz = ez - hz;
+    const int ix = w.x - hx, iy = w.y - hy, iz = w.z - hz;
     *inner = (ix >= 0 && ix < T.tx && iy >= 0 && iy < T.ty && iz >= 0 && iz < T.tz) ? ix + T.tx * (iy + T.ty * iz)
                                                                                    : -1;
+    const int gxx = wrapi(T.x0 + ix, A.nx), gyy = wrapi(T.y0 + iy, A.ny), gzz = wrapi(T.z0 + iz, A.nz);
     return (size_t)gxx + (size_t)A.nx * ((size_t)gyy + (size_t)A.ny * (size_t)gzz);
 }
 
-// Global index of interior point i of tile T and its extended index.
-__device__ __forceinline__ size_t int_point(const LzArgs& A, const Tile& T, int i, int hx, int hy, int hz,
-                                            int* e) {
-    const int ix = i % T.tx, r = i / T.tx, iy = r % T.ty, iz = r / T.ty;
-    *e = (ix + hx) + T.ex * ((iy + hy) + T.ey * (iz + hz));
-    return (size_t)(T.x0 + ix) + (size_t)A.nx * ((size_t)(T.y0 + iy) + (size_t)A.ny * (size_t)(T.z0 + iz));
-}
+// Shared memory of a tile CTA (all on the extended box of the tile, rows of
+// T.ex points, except D, the diagonal on the interior):
+//
+//  streamed mode (a CTA with several tiles): every sweep stages the update's
+//    inputs, W = B u_{j-1} (u_0 in sweep 0), U1 = u_{j-1}, U2 = u_{j-2}; W is
+//    overwritten in place by u_j;
+//  resident mode (one tile per CTA): the tile keeps its state between sweeps --
+//    R[j mod 3] = u_j, u_{j-1}, u_{j-2} on the extended box (the halo values are
+//    recomputed by this CTA exactly as the neighbours compute them), W = B u_{j-1}
+//    (the interior from this CTA's own stencil), D loaded once.  A sweep needs
+//    from the other CTAs only the halo ring of B u_{j-1}.
+struct Stage {
+    double2* W;
+    double2* U1;       // streamed: u_{j-1}
+    double2* U2;       // streamed: u_{j-2}
+    double2* R0;       // resident: the last three vectors, R0 + k ext_max for k = 0, 1, 2
+    int ext_max;
+    double* D;
+    __device__ __forceinline__ double2* R(int k) const { return R0 + (size_t)k * ext_max; }
+};
 
-// One Krylov sweep j over the tiles of this CTA; thread 0 receives the CTA's
-// partial sums.
-__device__ void sweep(const LzArgs& A, LzSmem& sm, double2* S, double2* U1, const double2* u0, int j, int hx,
-                      int hy, int hz, double* pn, double* pp, double* pd) {
-    const int G1 = gridDim.x - 1;
-    const double rho = sm.rho, ca = sm.a, cb = sm.b;
+// Streamed mode: issue the copies sweep j of tile t needs (one commit group).
+__device__ void stage_tile(const LzArgs& A, const Stage& st, const double2* u0, int t, int j, int hx, int hy,
+                           int hz) {
+    const Tile T = tile_of(A, t, hx, hy, hz);
     const double2* wprev = A.wt + (size_t)((j - 1) & 1) * A.n;
-    double2* wcur = A.wt + (size_t)(j & 1) * A.n;
     const double2* u1p = j >= 1 ? uvec(A, u0, j - 1) : nullptr;
     const double2* u2p = j >= 2 ? uvec(A, u0, j - 2) : nullptr;
-    double2* ujw = j >= 1 ? uvec_w(A, j) : nullptr;
-    const double ax = A.a[0], ay = A.a[1], az = A.a[2];
-    const double2 zero = make_double2(0.0, 0.0);
-    float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f, dh = 0.f, dl = 0.f;
-    for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
-        const Tile T = tile_of(A, t, hx, hy, hz);
-        // phase A: u_j on the tile and its halo (loads of kCh points in flight)
-        for (int e0 = threadIdx.x; e0 < T.E; e0 += kCh * kLzBlock) {
-            size_t g[kCh];
-            int inner[kCh];
-            double2 w[kCh], u1[kCh], u2[kCh];
-#pragma unroll
-            for (int q = 0; q < kCh; ++q) {
-                const int e = e0 + q * kLzBlock;
-                inner[q] = -1;
-                g[q] = 0;
-                w[q] = u1[q] = u2[q] = zero;
-                if (e < T.E) {
-                    g[q] = ext_point(A, T, e, hx, hy, hz, &inner[q]);
-                    if (j == 0) {
-                        w[q] = u0[g[q]];
-                    } else {
-                        w[q] = wprev[g[q]];
-                        u1[q] = u1p[g[q]];
-                        if (j >= 2) u2[q] = u2p[g[q]];
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < kCh; ++q) {
-                const int e = e0 + q * kLzBlock;
-                if (e < T.E) {
-                    double2 v = w[q];
-                    if (j >= 1) {
-                        double vx = fma(-ca, u1[q].x, w[q].x), vy = fma(-ca, u1[q].y, w[q].y);
-                        if (j >= 2) {
-                            vx = fma(-cb, u2[q].x, vx);
-                            vy = fma(-cb, u2[q].y, vy);
-                        }
-                        v = make_double2(rho * vx, rho * vy);
-                    }
-                    S[e] = v;
-                    if (inner[q] >= 0) {
-                        U1[inner[q]] = u1[q];
-                        if (j >= 1) ujw[g[q]] = v;
-                    }
-                }
-            }
+    Walk w;
+    w.init(threadIdx.x, T.ex, T.ey);
+    for (int e = threadIdx.x; e < T.E; e += kLzBlock, w.next(T.ex, T.ey)) {
+        int inner;
+        const size_t g = ext_index(A, T, w, hx, hy, hz, &inner);
+        if (j == 0) {
+            cp_async16(st.W + e, u0 + g);
+        } else {
+            cp_async16(st.W + e, wprev + g);
+            cp_async16(st.U1 + e, u1p + g);
+            if (j >= 2) cp_async16(st.U2 + e, u2p + g);
         }
-        __syncthreads();
-        // phase B: B u_j on the tile, and the inner products
-        const int sy = T.ex, sz = T.ex * T.ey;
-        for (int i0 = threadIdx.x; i0 < T.I; i0 += kCh * kLzBlock) {
-            size_t g[kCh];
-            int ee[kCh];
-            double dg[kCh];
-#pragma unroll
-            for (int q = 0; q < kCh; ++q) {
-                const int i = i0 + q * kLzBlock;
-                g[q] = 0;
-                ee[q] = 0;
-                dg[q] = 0.0;
-                if (i < T.I) {
-                    g[q] = int_point(A, T, i, hx, hy, hz, &ee[q]);
-                    dg[q] = A.diag[g[q]];
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < kCh; ++q) {
-                const int i = i0 + q * kLzBlock;
-                if (i < T.I) {
-                    const int e = ee[q];
-                    const double2 c = S[e];
-                    double wx = dg[q] * c.x, wy = dg[q] * c.y;
-                    if (hx) {
-                        const double2 l = S[e - 1], rr = S[e + 1];
-                        wx = fma(ax, l.x + rr.x, wx);
-                        wy = fma(ax, l.y + rr.y, wy);
-                    }
-                    if (hy) {
-                        const double2 l = S[e - sy], rr = S[e + sy];
-                        wx = fma(ay, l.x + rr.x, wx);
-                        wy = fma(ay, l.y + rr.y, wy);
-                    }
-                    if (hz) {
-                        const double2 l = S[e - sz], rr = S[e + sz];
-                        wx = fma(az, l.x + rr.x, wx);
-                        wy = fma(az, l.y + rr.y, wy);
-                    }
-                    wcur[g[q]] = make_double2(wx, wy);
-                    float cxh, cxl, cyh, cyl, wxh, wxl, wyh, wyl, uxh, uxl, uyh, uyl;
-                    split_f64(c.x, &cxh, &cxl);
-                    split_f64(c.y, &cyh, &cyl);
-                    split_f64(wx, &wxh, &wxl);
-                    split_f64(wy, &wyh, &wyl);
-                    const double2 u1 = U1[i];
-                    split_f64(u1.x, &uxh, &uxl);
-                    split_f64(u1.y, &uyh, &uyl);
-                    df_madd(nh, nl, cxh, cxl, cxh, cxl);
-                    df_madd(nh, nl, cyh, cyl, cyh, cyl);
-                    df_madd(ph, pl, cxh, cxl, wxh, wxl);
-                    df_madd(ph, pl, cyh, cyl, wyh, wyl);
-                    df_madd(dh, dl, uxh, uxl, wxh, wxl);
-                    df_madd(dh, dl, uyh, uyl, wyh, wyl);
-                }
-            }
+    }
+    Walk wi;
+    wi.init(threadIdx.x, T.tx, T.ty);
+    for (int i = threadIdx.x; i < T.I; i += kLzBlock, wi.next(T.tx, T.ty)) {
+        int e;
+        cp_async8(st.D + i, A.diag + int_index(A, T, wi, hx, hy, hz, &e));
+    }
+    cp_async_commit();
+}
+
+// Resident mode: issue the copies of sweep j -- the extended box of u_0 in
+// sweep 0, else the halo ring of B u_{j-1} (written by the neighbours).
+__device__ void stage_resident(const LzArgs& A, const Stage& st, const double2* u0, int j, int hx, int hy, int hz) {
+    const Tile T = tile_of(A, blockIdx.x - 1, hx, hy, hz);
+    const double2* wprev = A.wt + (size_t)((j - 1) & 1) * A.n;
+    Walk w;
+    w.init(threadIdx.x, T.ex, T.ey);
+    for (int e = threadIdx.x; e < T.E; e += kLzBlock, w.next(T.ex, T.ey)) {
+        int inner;
+        const size_t g = ext_index(A, T, w, hx, hy, hz, &inner);
+        if (j == 0)
+            cp_async16(st.R(0) + e, u0 + g);
+        else if (inner < 0)
+            cp_async16(st.W + e, wprev + g);
+    }
+    cp_async_commit();
+}
+
+// Resident mode, once per launch: the diagonal on the tile.
+__device__ void load_diag_resident(const LzArgs& A, const Stage& st, int hx, int hy, int hz) {
+    const Tile T = tile_of(A, blockIdx.x - 1, hx, hy, hz);
+    Walk wi;
+    wi.init(threadIdx.x, T.tx, T.ty);
+    for (int i = threadIdx.x; i < T.I; i += kLzBlock, wi.next(T.tx, T.ty)) {
+        int e;
+        cp_async8(st.D + i, A.diag + int_index(A, T, wi, hx, hy, hz, &e));
+    }
+    cp_async_commit();
+}
+
+// Phase A on one tile: v = rho (w - a u1 - b u2) on the extended box (in place
+// of W in streamed mode, into R[j mod 3] in resident mode); the tile's own
+// points are stored (they are u_j of the basis).
+__device__ __forceinline__ void phase_a(const LzArgs& A, const Tile& T, const double2* W, const double2* U1,
+                                        const double2* U2, double2* out, double2* ujw, int j, double rho, double ca,
+                                        double cb, int hx, int hy, int hz) {
+    Walk wa;
+    wa.init(threadIdx.x, T.ex, T.ey);
+    for (int e = threadIdx.x; e < T.E; e += kLzBlock, wa.next(T.ex, T.ey)) {
+        const double2 w = W[e], u1 = U1[e];
+        double vx = fma(-ca, u1.x, w.x), vy = fma(-ca, u1.y, w.y);
+        if (j >= 2) {
+            const double2 u2 = U2[e];
+            vx = fma(-cb, u2.x, vx);
+            vy = fma(-cb, u2.y, vy);
         }
-        __syncthreads();                          // S and U1 are reused by the next tile
-    }
-    double fn = (double)nh + (double)nl, fp = (double)ph + (double)pl, fd = (double)dh + (double)dl;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        fn += __shfl_xor_sync(0xffffffffu, fn, o);
-        fp += __shfl_xor_sync(0xffffffffu, fp, o);
-        fd += __shfl_xor_sync(0xffffffffu, fd, o);
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        sm.red[warp][0] = fn;
-        sm.red[warp][1] = fp;
-        sm.red[warp][2] = fd;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0, c = 0.0;
-        for (int w = 0; w < kLzWarps; ++w) {
-            a += sm.red[w][0];
-            b += sm.red[w][1];
-            c += sm.red[w][2];
-        }
-        *pn = a;
-        *pp = b;
-        *pd = c;
+        const double2 v = make_double2(rho * vx, rho * vy);
+        out[e] = v;
+        const int ix = wa.x - hx, iy = wa.y - hy, iz = wa.z - hz;
+        if (ix >= 0 && ix < T.tx && iy >= 0 && iy < T.ty && iz >= 0 && iz < T.tz)
+            ujw[(size_t)(T.x0 + ix) + (size_t)A.nx * ((size_t)(T.y0 + iy) + (size_t)A.ny * (size_t)(T.z0 + iz))] = v;
     }
 }
 
-// Final pass over this CTA's tiles: dst = sum_{q < J} coef_q u_q (the
-// coefficients staged in shared memory).
-__device__ void combine(const LzArgs& A, const double2* coef, const double2* u0, double2* dst, int J, int hx,
-                        int hy, int hz) {
+// Phase B on one tile: B u_j from S (the extended box of u_j), stored to the
+// global B u_j (and, resident mode, into Wown at the interior points); the
+// compensated partial sums of ||u_j||^2 and Re u_j^H B u_j accumulate.
+__device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const double2* S, const double* D,
+                                        double2* Wown, double2* wcur, int hx, int hy, int hz, float& nh, float& nl,
+                                        float& ph, float& pl) {
+    const double ax = A.a[0], ay = A.a[1], az = A.a[2];
+    const int sy = T.ex, sz = T.ex * T.ey;
+    Walk wb;
+    wb.init(threadIdx.x, T.tx, T.ty);
+    for (int i = threadIdx.x; i < T.I; i += kLzBlock, wb.next(T.tx, T.ty)) {
+        int e;
+        const size_t g = int_index(A, T, wb, hx, hy, hz, &e);
+        const double2 c = S[e];
+        const double dg = D[i];
+        double wx = dg * c.x, wy = dg * c.y;
+        if (hx) {
+            const double2 l = S[e - 1], rr = S[e + 1];
+            wx = fma(ax, l.x + rr.x, wx);
+            wy = fma(ax, l.y + rr.y, wy);
+        }
+        if (hy) {
+            const double2 l = S[e - sy], rr = S[e + sy];
+            wx = fma(ay, l.x + rr.x, wx);
+            wy = fma(ay, l.y + rr.y, wy);
+        }
+        if (hz) {
+            const double2 l = S[e - sz], rr = S[e + sz];
+            wx = fma(az, l.x + rr.x, wx);
+            wy = fma(az, l.y + rr.y, wy);
+        }
+        const double2 wv = make_double2(wx, wy);
+        wcur[g] = wv;
+        if (Wown) Wown[e] = wv;
+        float cxh, cxl, cyh, cyl, wxh, wxl, wyh, wyl;
+        split_f64(c.x, &cxh, &cxl);
+        split_f64(c.y, &cyh, &cyl);
+        split_f64(wx, &wxh, &wxl);
+        split_f64(wy, &wyh, &wyl);
+        df_madd(nh, nl, cxh, cxl, cxh, cxl);
+        df_madd(nh, nl, cyh, cyl, cyh, cyl);
+        df_madd(ph, pl, cxh, cxl, wxh, wxl);
+        df_madd(ph, pl, cyh, cyl, wyh, wyl);
+    }
+}
+
+// One Krylov sweep j over the tiles of this CTA (the first tile's copies were
+// issued by the caller); part receives the CTA's partial sums (thread 0).
+__device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double2* u0, int j, int hx, int hy, int hz,
+                      float4* part) {
+    const int G1 = gridDim.x - 1;
+    const double rho = sm.rho, ca = sm.a, cb = sm.b;
+    double2* wcur = A.wt + (size_t)(j & 1) * A.n;
+    double2* ujw = j >= 1 ? uvec_w(A, j) : nullptr;
+    float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f;
+    if (A.resident) {
+        if ((int)blockIdx.x - 1 < A.ntiles) {
+            const Tile T = tile_of(A, blockIdx.x - 1, hx, hy, hz);
+            double2* S = st.R(j % 3);
+            cp_async_wait_all();
+            __syncthreads();
+            if (j >= 1) {
+                phase_a(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, ujw, j, rho, ca, cb, hx, hy, hz);
+                __syncthreads();
+            }
+            phase_b(A, T, S, st.D, st.W, wcur, hx, hy, hz, nh, nl, ph, pl);
+        }
+    } else {
+        for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
+            if (t != (int)blockIdx.x - 1) stage_tile(A, st, u0, t, j, hx, hy, hz);
+            const Tile T = tile_of(A, t, hx, hy, hz);
+            cp_async_wait_all();
+            __syncthreads();
+            if (j >= 1) {
+                phase_a(A, T, st.W, st.U1, st.U2, st.W, ujw, j, rho, ca, cb, hx, hy, hz);
+                __syncthreads();
+            }
+            phase_b(A, T, st.W, st.D, nullptr, wcur, hx, hy, hz, nh, nl, ph, pl);
+            __syncthreads();                      // shared memory is restaged for the next tile
+        }
+    }
+    *part = cta_df_sum(sm, nh, nl, ph, pl);
+}
+
+// Final pass over this CTA's tiles: dst = sum_{q < J} coef_q u_q in FP64.
+__device__ void combine(const LzArgs& A, const double2* coef, const double2* u0, double2* dst, int J, int hx, int hy,
+                        int hz) {
     const int G1 = gridDim.x - 1;
     for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
         const Tile T = tile_of(A, t, hx, hy, hz);
+        Walk wb;
+        wb.init(threadIdx.x, T.tx, T.ty);
         for (int i0 = threadIdx.x; i0 < T.I; i0 += kCh * kLzBlock) {
             size_t g[kCh];
             double2 acc[kCh];
@@ -398,9 +542,14 @@ __device__ void combine(const LzArgs& A, const double2* coef, const double2* u0,
             for (int q = 0; q < kCh; ++q) {
                 int e;
                 const int i = i0 + q * kLzBlock;
-                g[q] = i < T.I ? int_point(A, T, i, hx, hy, hz, &e) : 0;
+                g[q] = 0;
+                if (i < T.I) {
+                    g[q] = int_index(A, T, wb, hx, hy, hz, &e);
+                    wb.next(T.tx, T.ty);
+                }
                 acc[q] = make_double2(0.0, 0.0);
             }
+#pragma unroll 4
             for (int r = 0; r < J; ++r) {
                 const double2 c = coef[r];
                 const double2* u = uvec(A, u0, r);
@@ -496,7 +645,8 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
         const int lo = max(0, top - stage_rows);
         const int cnt = (top - lo) * K * 3;
         __syncthreads();
-        for (int q = threadIdx.x; q < cnt; q += kLzBlock) stage[q] = A.rows[(size_t)lo * K * 3 + q];
+#pragma unroll 8
+        for (int q = threadIdx.x; q < cnt; q += kLzBlock) stage[q] = __ldcg(A.rows + (size_t)lo * K * 3 + q);
         __syncthreads();
         if (k < K) {
             for (int r = top - 1; r >= lo; --r) {
@@ -524,8 +674,10 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
         for (int r0 = 0; r0 < Jn; r0 += kLzBlock / 8) {
             const int r = r0 + (threadIdx.x >> 3);
             double2 acc = make_double2(0.0, 0.0);
-            if (r < J)
-                for (int kq = q; kq < K; kq += 8) acc = cfma(acc, A.alpha[kq], A.ybuf[(size_t)r * K + kq]);
+            if (r < J) {
+#pragma unroll 4
+                for (int kq = q; kq < K; kq += 8) acc = cfma(acc, __ldg(A.alpha + kq), A.ybuf[(size_t)r * K + kq]);
+            }
 #pragma unroll
             for (int o = 4; o > 0; o >>= 1) {
                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
@@ -558,12 +710,18 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
     extern __shared__ double2 dyn[];
     __shared__ LzSmem sm;
     const bool control = blockIdx.x == 0;
+    const bool has_tile = !control && (int)blockIdx.x - 1 < A.ntiles;
     const int hx = A.a[0] != 0.0 ? 1 : 0, hy = A.a[1] != 0.0 ? 1 : 0, hz = A.a[2] != 0.0 ? 1 : 0;
-    // dynamic shared memory: tile plus halo of u_j, then u_{j-1} on the interior
     const int ext_max = (A.tx + 2 * hx) * (A.ty + 2 * hy) * (A.tz + 2 * hz);
-    double2* S = dyn;
-    double2* U1 = dyn + ext_max;
+    Stage st;
+    st.W = dyn;
+    st.U1 = dyn + ext_max;
+    st.U2 = dyn + 2 * ext_max;
+    st.R0 = dyn + ext_max;
+    st.ext_max = ext_max;
+    st.D = (double*)(dyn + (A.resident ? 4 : 3) * ext_max);
     const int stage_rows = A.stage_rows;
+    if (has_tile && A.resident) load_diag_resident(A, st, hx, hy, hz);
     int tcount = 0;
     trace_mark(A, 99, &tcount);
     PoleState P;
@@ -581,59 +739,71 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
         }
         if (threadIdx.x == 0) {
             sm.n_last = sm.n_prev = sm.n0 = 0.0;
-            for (int q = 0; q < 3; ++q) sm.hrho[q] = sm.ha[q] = sm.hb[q] = 0.0;
+            for (int q = 0; q < 3; ++q) sm.hrho[q] = sm.ha[q] = sm.hn[q] = 0.0;
         }
         __syncthreads();
         double tol_abs2 = 0.0, bnorm = 0.0;
         int J = -1, sweeps = 0;
         for (int j = 0;; ++j) {
+            // as the barrier opens: the partials and the stop word, then the
+            // copies of this CTA's first tile
+            PartLoad L;
+            int stop_word = -1;
+            if (j >= 1) {
+                load_partials(A, (j - 1) & 1, L);
+                if (threadIdx.x == 0) stop_word = __ldcg(A.stop + s);
+            }
+            if (has_tile) {
+                if (A.resident)
+                    stage_resident(A, st, u0, j, hx, hy, hz);
+                else
+                    stage_tile(A, st, u0, blockIdx.x - 1, j, hx, hy, hz);
+            }
             if (j >= 1) {
                 // coefficients of sweep j-1, the same in every CTA
-                if (threadIdx.x < 32) {
-                    const double3 t = reduce_partials(A, (j - 1) & 1);
-                    if (threadIdx.x == 0) {
-                        const double n = t.x, p = t.y, d = t.z;
-                        const double rho = n > 0.0 ? 1.0 / sqrt(n) : 0.0;
-                        const double a = n > 0.0 ? p / n : 0.0;
-                        const double b = (j - 1 >= 1 && sm.n_last > 0.0) ? d / sm.n_last : 0.0;
-                        sm.n_prev = sm.n_last;
-                        sm.n_last = n;
-                        if (j == 1) sm.n0 = n;
-                        sm.rho = rho;
-                        sm.a = a;
-                        sm.b = b;
-                        sm.hrho[2] = sm.hrho[1];
-                        sm.hrho[1] = sm.hrho[0];
-                        sm.hrho[0] = rho;
-                        sm.ha[2] = sm.ha[1];
-                        sm.ha[1] = sm.ha[0];
-                        sm.ha[0] = a;
-                        sm.hb[2] = sm.hb[1];
-                        sm.hb[1] = sm.hb[0];
-                        sm.hb[0] = b;
-                        sm.stop = __ldcg(A.stop + s);
-                        if (control) A.rho[j - 1] = rho;
-                    }
+                const double2 t = reduce_partials(A, sm, (j - 1) & 1, L);
+                if (threadIdx.x == 0) {
+                    // rho = 1/||u_{j-1}||, a = p rho^2 (Rayleigh quotient), b = rho_{j-2} / rho_{j-1}^2
+                    // = rho_{j-2} n (symmetric tridiagonal): one reciprocal square root
+                    const double n = t.x, p = t.y;
+                    const double rho = n > 0.0 ? rsqrt(n) : 0.0;
+                    const double a = p * rho * rho;
+                    const double b = j - 1 >= 1 ? sm.hrho[0] * n : 0.0;
+                    sm.n_prev = sm.n_last;
+                    sm.n_last = n;
+                    if (j == 1) sm.n0 = n;
+                    sm.rho = rho;
+                    sm.a = a;
+                    sm.b = b;
+                    sm.hrho[2] = sm.hrho[1];
+                    sm.hrho[1] = sm.hrho[0];
+                    sm.hrho[0] = rho;
+                    sm.ha[2] = sm.ha[1];
+                    sm.ha[1] = sm.ha[0];
+                    sm.ha[0] = a;
+                    sm.hn[2] = sm.hn[1];
+                    sm.hn[1] = sm.hn[0];
+                    sm.hn[0] = n;
+                    sm.stop = stop_word;
+                    if (control) A.rho[j - 1] = rho;
                 }
                 __syncthreads();
                 if (sm.stop >= 0) {
                     J = sm.stop;
                     sweeps = j;
+                    cp_async_wait_all();               // no copy may land after the stage is reused
                     break;
                 }
                 if (j > A.m + 2) {                     // the control CTA stops by then: never taken
+                    cp_async_wait_all();
                     if (threadIdx.x == 0) atomicExch(A.err, kErrInternal);
                     return;
                 }
             }
             if (!control) {
-                double pn = 0.0, pp = 0.0, pd = 0.0;
-                sweep(A, sm, S, U1, u0, j, hx, hy, hz, &pn, &pp, &pd);
-                if (threadIdx.x == 0) {
-                    double2* slot = A.part + ((size_t)(j & 1) * gridDim.x + blockIdx.x) * 2;
-                    slot[0] = make_double2(pn, pp);
-                    slot[1] = make_double2(pd, 0.0);
-                }
+                float4 part;
+                sweep(A, sm, st, u0, j, hx, hy, hz, &part);
+                if (threadIdx.x == 0) A.part[(size_t)(j & 1) * gridDim.x + blockIdx.x] = part;
             } else if (j >= 1) {
                 // the control CTA works one column behind: column c = j - 2 is
                 // complete once the norm of u_{j-1} (its subdiagonal) is known
@@ -642,20 +812,18 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                     bnorm = sqrt(n0);
                     const double ta = A.tol * bnorm / 1.0001;
                     tol_abs2 = ta * ta;
-                    if (threadIdx.x < A.K) P.g = make_double2(n0 > 0.0 ? 1.0 / sm.hrho[0] : 0.0, 0.0);
+                    if (threadIdx.x < A.K) P.g = make_double2(n0 * sm.hrho[0], 0.0);   // 1/rho_0
                     if (threadIdx.x == 0 && !(n0 > 0.0 && n0 <= 3.0e38)) {
                         // a zero state needs no columns; a non-finite one fails every pole
                         __stcg(A.stop + s, 0);
                     }
-                    if (threadIdx.x < A.K && !(n0 > 0.0)) {
-                        P.done = n0 == 0.0 ? 1 : 2;
-                    }
+                    if (threadIdx.x < A.K && !(n0 > 0.0)) P.done = n0 == 0.0 ? 1 : 2;
                     if (threadIdx.x < A.K && !(n0 <= 3.0e38)) P.done = 2;
                 } else {
                     const int c = j - 2;
-                    const double rho_c = sm.hrho[1], rho_next = sm.hrho[0];
-                    const double up = (c >= 1 && sm.hrho[2] > 0.0) ? rho_c * sm.hb[1] / sm.hrho[2] : 0.0;
-                    const double lo = rho_next > 0.0 ? 1.0 / rho_next : 0.0;
+                    // T[c-1, c] = 1 / rho_c = n_c rho_c and T[c+1, c] = 1 / rho_{c+1}
+                    const double up = c >= 1 ? sm.hn[1] * sm.hrho[1] : 0.0;
+                    const double lo = sm.hn[0] * sm.hrho[0];
                     const double ac = sm.ha[1];
                     int active = 0;
                     if (threadIdx.x < A.K && P.done == 0) {
@@ -694,6 +862,7 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                     by += q == 0 ? 40.0 : (q == 1 ? 72.0 : 88.0);
                     fl += st_fl + (q == 0 ? 0.0 : (q == 1 ? 6.0 : 10.0));
                 }
+                // the final pass reads J vectors and writes one output per pole set
                 const int Jn = A.mode == LZ_STEP ? max(J, 1) : J;
                 const int outs = A.mode == LZ_STEP ? 1 : A.K;
                 by += outs * 16.0 * (Jn + 1);
@@ -703,7 +872,7 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                     A.bytes[1] += (unsigned long long)(fl * n);
                 }
             }
-            control_finish(A, sm, S, stage_rows, P, J, s);
+            control_finish(A, sm, dyn, stage_rows, P, J, s);
         }
         if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
         trace_mark(A, TR_LZ_SOLVE, &tcount);
@@ -716,7 +885,8 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
             } else {
                 for (int k = 0; k < A.K; ++k) {
                     __syncthreads();
-                    for (int r = threadIdx.x; r < J; r += kLzBlock) sm.coef[r] = __ldcg(A.coef + (size_t)k * A.m + r);
+                    for (int r = threadIdx.x; r < J; r += kLzBlock)
+                        sm.coef[r] = __ldcg(A.coef + (size_t)k * A.m + r);
                     __syncthreads();
                     combine(A, sm.coef, u0, A.out + (size_t)k * A.n, J, hx, hy, hz);
                 }
@@ -731,9 +901,15 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
 
 }  // namespace
 
-size_t lanczos_smem_bytes(int tx, int ty, int tz, int hx, int hy, int hz) {
+size_t lanczos_smem_bytes(int tx, int ty, int tz, int hx, int hy, int hz, bool resident) {
     const size_t ext = (size_t)(tx + 2 * hx) * (ty + 2 * hy) * (tz + 2 * hz);
-    return (ext + (size_t)tx * ty * tz) * sizeof(double2);
+    return (resident ? 4 : 3) * ext * sizeof(double2) + (size_t)tx * ty * tz * sizeof(double);
+}
+
+size_t lanczos_static_smem() {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, lanczos_kernel) != cudaSuccess) return 0;
+    return fa.sharedSizeBytes;
 }
 
 int lanczos_max_grid(size_t smem, int device) {

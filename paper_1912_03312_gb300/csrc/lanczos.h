@@ -41,13 +41,14 @@ struct LzArgs {
     int tx, ty, tz;            // tile box
     int gx, gy, gz;            // tiles per dimension
     int ntiles;
+    int resident;              // 1: at most one tile per CTA, its state kept in shared memory between sweeps
     const double2* in;         // LZ_STEP: psi_in; LZ_SOLVE: right-hand side b
     double2* out;              // LZ_STEP: psi_out; LZ_SOLVE: x [K][n]
     double2* tmp0;             // substep states (ping-pong)
     double2* tmp1;
     double2* basis;            // [m + 2][n]: u_1 .. u_{m+2} (u_0 is the substep's input state)
     double2* wt;               // [2][n]: B u_j by parity of j
-    double2* part;             // [2][grid][2]: per-CTA partial sums (||u_j||^2, Re u_j^H B u_j), (Re u_{j-1}^H B u_j, 0)
+    float4* part;              // [2][grid]: per-CTA partial sums (||u_j||^2, Re u_j^H B u_j) as double-float pairs
     double2* rows;             // [m][K][3]: scaled rows of every pole's R for the back substitution
     double2* ybuf;             // [m][K]: y_k of the last substep (LZ_STEP) / unused
     double2* coef;             // LZ_STEP: [m] coefficients of u_r in psi'; LZ_SOLVE: [K][m]
@@ -65,6 +66,7 @@ struct LzArgs {
 
 cudaError_t launch_lanczos(const LzArgs& args, int grid, size_t smem, cudaStream_t stream);
 int lanczos_max_grid(size_t smem, int device);      // co-resident CTAs (<= 0: error)
-size_t lanczos_smem_bytes(int tx, int ty, int tz, int hx, int hy, int hz);
+size_t lanczos_smem_bytes(int tx, int ty, int tz, int hx, int hy, int hz, bool resident);
+size_t lanczos_static_smem();                       // static shared memory of the kernel (0: error)
 
 }  // namespace rexi

@@ -123,6 +123,20 @@ def test_argument_validation_before_device(lib):
     o.window = 3
     o.ortho = 0                               # windows are a delayed-CGS2 option
     assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    # the Lanczos path (ortho = 2): FP64 only, no window, Krylov dimension <= REXI_MAX_KRYLOV
+    o.ortho = 2
+    o.window = 0
+    o.precision = N.REXI_MIXED
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    o.precision = N.REXI_FP64
+    o.window = 2
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    o.window = 0
+    o.restart_m = 513
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    o.restart_m = 256
+    o.ortho = 3
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
     assert h.value is None
 
 
