@@ -116,6 +116,8 @@ struct rexi_plan {
     int* d_lz_stop = nullptr;
     int* d_lz_cols = nullptr;
     double2* d_lz_shift = nullptr;
+    double* d_lz_diag = nullptr;                 // diagonal divided by the stencil fold factor
+    double lz_fold = 1.0;
     ProblemDesc hprob{};                         // forward problem descriptor (host copy)
     int last_status = REXI_OK;
     int last_launches = 0;
@@ -182,6 +184,15 @@ int upload_diag(rexi_plan* p, cudaStream_t stream, bool sync) {
     cudaError_t e = cudaMemcpyAsync(p->d_diag, d.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->d_diagf, f.data(), sizeof(float) * p->n, cudaMemcpyHostToDevice, stream);
+    std::vector<double> dl;
+    if (e == cudaSuccess && p->d_lz_diag) {
+        // the Lanczos kernel's copy, divided by the stencil's fold factor
+        dl.resize(p->n);
+        for (int i = 0; i < p->n; ++i) dl[i] = d[i] / p->lz_fold;
+        e = cudaMemcpyAsync(p->d_lz_diag, dl.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice, stream);
+    }
+    // pageable host buffers: the copies have read them when the calls return;
+    // sync waits for the device side as well
     if (e == cudaSuccess && sync) e = cudaStreamSynchronize(stream);
     return e == cudaSuccess ? REXI_OK : cuda_fail(e);
 }
@@ -586,6 +597,9 @@ int lz_alloc(rexi_plan* p) {
     if ((st = dalloc(p, &p->d_lz_stop, (size_t)std::max(1, p->n_sub)))) return st;
     if ((st = dalloc(p, &p->d_lz_cols, 2 * (size_t)std::max(1, p->n_sub)))) return st;
     if ((st = dalloc(p, &p->d_lz_shift, K))) return st;
+    p->lz_fold = p->a[0] != 0.0 ? p->a[0] : (p->a[1] != 0.0 ? p->a[1] : (p->a[2] != 0.0 ? p->a[2] : 1.0));
+    if ((st = dalloc(p, &p->d_lz_diag, n))) return st;
+    if ((st = upload_diag(p, 0, true))) return st;
     if (!p->d_stats && (st = dalloc(p, &p->d_stats, K))) return st;
     std::vector<double2> sh(K);
     for (size_t k = 0; k < K; ++k) {
@@ -616,8 +630,12 @@ int lz_launch(rexi_plan* p, int mode, const void* in, void* out, cudaStream_t st
     A.K = p->K;
     A.nsub = nsub;
     A.m = std::min(p->lz_m, p->opt.max_iters);
-    for (int d = 0; d < 3; ++d) A.a[d] = p->a[d];
-    A.diag = p->d_diag;
+    for (int d = 0; d < 3; ++d) {
+        A.a[d] = p->a[d];
+        A.ratio[d] = p->a[d] / p->lz_fold;
+    }
+    A.fold = p->lz_fold;
+    A.diag = p->d_lz_diag;
     A.shift = p->d_lz_shift;
     A.alpha = p->d_alpha;
     A.alpha0 = make_double2(p->alpha0.real(), p->alpha0.imag());

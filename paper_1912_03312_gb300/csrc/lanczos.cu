@@ -56,6 +56,8 @@ constexpr int kErrInternal = -3;        // REXI_ECUDA: the iteration outran its 
 
 struct LzSmem {
     double rho, a, b;        // coefficients of the next update (those of the last reduced sweep)
+    double cw, ca, cb;       // the update as applied: u_j = cw w' - ca u_{j-1} - cb u_{j-2}
+    int nring;               // resident mode: halo ring points of the tile
     double n_last;           // ||u_{j-1}||^2 of the last reduced sweep
     double n_prev;           // ||u_{j-2}||^2
     double n0;               // ||u_0||^2 of the substep
@@ -357,6 +359,8 @@ struct Stage {
     double2* R0;       // resident: the last three vectors, R0 + k ext_max for k = 0, 1, 2
     int ext_max;
     double* D;
+    int* ringE;        // resident: extended-box index and global index of every halo ring point
+    int* ringG;
     __device__ __forceinline__ double2* R(int k) const { return R0 + (size_t)k * ext_max; }
 };
 
@@ -391,24 +395,26 @@ __device__ void stage_tile(const LzArgs& A, const Stage& st, const double2* u0, 
 
 // Resident mode: issue the copies of sweep j -- the extended box of u_0 in
 // sweep 0, else the halo ring of B u_{j-1} (written by the neighbours).
-__device__ void stage_resident(const LzArgs& A, const Stage& st, const double2* u0, int j, int hx, int hy, int hz) {
-    const Tile T = tile_of(A, blockIdx.x - 1, hx, hy, hz);
-    const double2* wprev = A.wt + (size_t)((j - 1) & 1) * A.n;
-    Walk w;
-    w.init(threadIdx.x, T.ex, T.ey);
-    for (int e = threadIdx.x; e < T.E; e += kLzBlock, w.next(T.ex, T.ey)) {
-        int inner;
-        const size_t g = ext_index(A, T, w, hx, hy, hz, &inner);
-        if (j == 0)
-            cp_async16(st.R(0) + e, u0 + g);
-        else if (inner < 0)
-            cp_async16(st.W + e, wprev + g);
+__device__ void stage_resident(const LzArgs& A, const LzSmem& sm, const Stage& st, const double2* u0, int j, int hx,
+                               int hy, int hz) {
+    if (j == 0) {
+        const Tile T = tile_of(A, blockIdx.x - 1, hx, hy, hz);
+        Walk w;
+        w.init(threadIdx.x, T.ex, T.ey);
+        for (int e = threadIdx.x; e < T.E; e += kLzBlock, w.next(T.ex, T.ey)) {
+            int inner;
+            cp_async16(st.R(0) + e, u0 + ext_index(A, T, w, hx, hy, hz, &inner));
+        }
+    } else {
+        const double2* wprev = A.wt + (size_t)((j - 1) & 1) * A.n;
+        for (int q = threadIdx.x; q < sm.nring; q += kLzBlock) cp_async16(st.W + st.ringE[q], wprev + st.ringG[q]);
     }
     cp_async_commit();
 }
 
-// Resident mode, once per launch: the diagonal on the tile.
-__device__ void load_diag_resident(const LzArgs& A, const Stage& st, int hx, int hy, int hz) {
+// Resident mode, once per launch: the diagonal on the tile, and the list of
+// the halo ring points (order immaterial: they are only copied).
+__device__ void setup_resident(const LzArgs& A, LzSmem& sm, const Stage& st, int hx, int hy, int hz) {
     const Tile T = tile_of(A, blockIdx.x - 1, hx, hy, hz);
     Walk wi;
     wi.init(threadIdx.x, T.tx, T.ty);
@@ -417,25 +423,39 @@ __device__ void load_diag_resident(const LzArgs& A, const Stage& st, int hx, int
         cp_async8(st.D + i, A.diag + int_index(A, T, wi, hx, hy, hz, &e));
     }
     cp_async_commit();
+    if (threadIdx.x == 0) sm.nring = 0;
+    __syncthreads();
+    Walk w;
+    w.init(threadIdx.x, T.ex, T.ey);
+    for (int e = threadIdx.x; e < T.E; e += kLzBlock, w.next(T.ex, T.ey)) {
+        int inner;
+        const size_t g = ext_index(A, T, w, hx, hy, hz, &inner);
+        if (inner < 0) {
+            const int q = atomicAdd(&sm.nring, 1);
+            st.ringE[q] = e;
+            st.ringG[q] = (int)g;
+        }
+    }
+    __syncthreads();
 }
 
 // Phase A on one tile: v = rho (w - a u1 - b u2) on the extended box (in place
 // of W in streamed mode, into R[j mod 3] in resident mode); the tile's own
 // points are stored (they are u_j of the basis).
 __device__ __forceinline__ void phase_a(const LzArgs& A, const Tile& T, const double2* W, const double2* U1,
-                                        const double2* U2, double2* out, double2* ujw, int j, double rho, double ca,
+                                        const double2* U2, double2* out, double2* ujw, int j, double cw, double ca,
                                         double cb, int hx, int hy, int hz) {
     Walk wa;
     wa.init(threadIdx.x, T.ex, T.ey);
     for (int e = threadIdx.x; e < T.E; e += kLzBlock, wa.next(T.ex, T.ey)) {
         const double2 w = W[e], u1 = U1[e];
-        double vx = fma(-ca, u1.x, w.x), vy = fma(-ca, u1.y, w.y);
+        double vx = fma(-ca, u1.x, cw * w.x), vy = fma(-ca, u1.y, cw * w.y);
         if (j >= 2) {
             const double2 u2 = U2[e];
             vx = fma(-cb, u2.x, vx);
             vy = fma(-cb, u2.y, vy);
         }
-        const double2 v = make_double2(rho * vx, rho * vy);
+        const double2 v = make_double2(vx, vy);
         out[e] = v;
         const int ix = wa.x - hx, iy = wa.y - hy, iz = wa.z - hz;
         if (ix >= 0 && ix < T.tx && iy >= 0 && iy < T.ty && iz >= 0 && iz < T.tz)
@@ -449,7 +469,11 @@ __device__ __forceinline__ void phase_a(const LzArgs& A, const Tile& T, const do
 __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const double2* S, const double* D,
                                         double2* Wown, double2* wcur, int hx, int hy, int hz, float& nh, float& nl,
                                         float& ph, float& pl) {
-    const double ax = A.a[0], ay = A.a[1], az = A.a[2];
+    // w' = B u / f with f = the coefficient of the first dimension the stencil
+    // reaches: that dimension's neighbour pair enters with weight one, the
+    // others with r_d = a_d / f, the diagonal (D = diag / f) with one fused
+    // multiply-add -- four FP64 operations per component in 2D
+    const double ry = A.ratio[1], rz = A.ratio[2];
     const int sy = T.ex, sz = T.ex * T.ey;
     Walk wb;
     wb.init(threadIdx.x, T.tx, T.ty);
@@ -458,22 +482,34 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
         const size_t g = int_index(A, T, wb, hx, hy, hz, &e);
         const double2 c = S[e];
         const double dg = D[i];
-        double wx = dg * c.x, wy = dg * c.y;
+        double wx = 0.0, wy = 0.0;
         if (hx) {
             const double2 l = S[e - 1], rr = S[e + 1];
-            wx = fma(ax, l.x + rr.x, wx);
-            wy = fma(ax, l.y + rr.y, wy);
+            wx = l.x + rr.x;
+            wy = l.y + rr.y;
         }
         if (hy) {
             const double2 l = S[e - sy], rr = S[e + sy];
-            wx = fma(ay, l.x + rr.x, wx);
-            wy = fma(ay, l.y + rr.y, wy);
+            if (hx) {
+                wx = fma(ry, l.x + rr.x, wx);
+                wy = fma(ry, l.y + rr.y, wy);
+            } else {
+                wx = l.x + rr.x;
+                wy = l.y + rr.y;
+            }
         }
         if (hz) {
             const double2 l = S[e - sz], rr = S[e + sz];
-            wx = fma(az, l.x + rr.x, wx);
-            wy = fma(az, l.y + rr.y, wy);
+            if (hx || hy) {
+                wx = fma(rz, l.x + rr.x, wx);
+                wy = fma(rz, l.y + rr.y, wy);
+            } else {
+                wx = l.x + rr.x;
+                wy = l.y + rr.y;
+            }
         }
+        wx = fma(dg, c.x, wx);
+        wy = fma(dg, c.y, wy);
         const double2 wv = make_double2(wx, wy);
         wcur[g] = wv;
         if (Wown) Wown[e] = wv;
@@ -494,7 +530,7 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
 __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double2* u0, int j, int hx, int hy, int hz,
                       float4* part) {
     const int G1 = gridDim.x - 1;
-    const double rho = sm.rho, ca = sm.a, cb = sm.b;
+    const double cw = sm.cw, ca = sm.ca, cb = sm.cb;
     double2* wcur = A.wt + (size_t)(j & 1) * A.n;
     double2* ujw = j >= 1 ? uvec_w(A, j) : nullptr;
     float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f;
@@ -505,7 +541,7 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
             cp_async_wait_all();
             __syncthreads();
             if (j >= 1) {
-                phase_a(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, ujw, j, rho, ca, cb, hx, hy, hz);
+                phase_a(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, ujw, j, cw, ca, cb, hx, hy, hz);
                 __syncthreads();
             }
             phase_b(A, T, S, st.D, st.W, wcur, hx, hy, hz, nh, nl, ph, pl);
@@ -517,7 +553,7 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
             cp_async_wait_all();
             __syncthreads();
             if (j >= 1) {
-                phase_a(A, T, st.W, st.U1, st.U2, st.W, ujw, j, rho, ca, cb, hx, hy, hz);
+                phase_a(A, T, st.W, st.U1, st.U2, st.W, ujw, j, cw, ca, cb, hx, hy, hz);
                 __syncthreads();
             }
             phase_b(A, T, st.W, st.D, nullptr, wcur, hx, hy, hz, nh, nl, ph, pl);
@@ -720,8 +756,18 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
     st.R0 = dyn + ext_max;
     st.ext_max = ext_max;
     st.D = (double*)(dyn + (A.resident ? 4 : 3) * ext_max);
+    const int int_max = A.tx * A.ty * A.tz;
+    st.ringE = (int*)(st.D + int_max);
+    st.ringG = st.ringE + (ext_max - int_max);
     const int stage_rows = A.stage_rows;
-    if (has_tile && A.resident) load_diag_resident(A, st, hx, hy, hz);
+    if (A.resident && !control) {
+        if (has_tile) {
+            setup_resident(A, sm, st, hx, hy, hz);
+        } else {
+            if (threadIdx.x == 0) sm.nring = 0;
+            __syncthreads();
+        }
+    }
     int tcount = 0;
     trace_mark(A, 99, &tcount);
     PoleState P;
@@ -755,7 +801,7 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
             }
             if (has_tile) {
                 if (A.resident)
-                    stage_resident(A, st, u0, j, hx, hy, hz);
+                    stage_resident(A, sm, st, u0, j, hx, hy, hz);
                 else
                     stage_tile(A, st, u0, blockIdx.x - 1, j, hx, hy, hz);
             }
@@ -765,7 +811,8 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                 if (threadIdx.x == 0) {
                     // rho = 1/||u_{j-1}||, a = p rho^2 (Rayleigh quotient), b = rho_{j-2} / rho_{j-1}^2
                     // = rho_{j-2} n (symmetric tridiagonal): one reciprocal square root
-                    const double n = t.x, p = t.y;
+                    const double n = t.x, p = t.y * A.fold;       // Re u^H B u = f Re u^H w'
+
                     const double rho = n > 0.0 ? rsqrt(n) : 0.0;
                     const double a = p * rho * rho;
                     const double b = j - 1 >= 1 ? sm.hrho[0] * n : 0.0;
@@ -775,6 +822,9 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                     sm.rho = rho;
                     sm.a = a;
                     sm.b = b;
+                    sm.cw = rho * A.fold;
+                    sm.ca = rho * a;
+                    sm.cb = rho * b;
                     sm.hrho[2] = sm.hrho[1];
                     sm.hrho[1] = sm.hrho[0];
                     sm.hrho[0] = rho;
@@ -856,7 +906,7 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                 // sweeps read B u_{j-1}, u_{j-1}, u_{j-2} and write u_j, B u_j
                 const double n = (double)A.n;
                 const int d = hx + hy + hz;
-                const double st_fl = 2.0 * (1 + 3 * d);
+                const double st_fl = 6.0 * d;
                 double by = 0.0, fl = 0.0;
                 for (int q = 0; q < sweeps; ++q) {
                     by += q == 0 ? 40.0 : (q == 1 ? 72.0 : 88.0);
@@ -903,7 +953,9 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
 
 size_t lanczos_smem_bytes(int tx, int ty, int tz, int hx, int hy, int hz, bool resident) {
     const size_t ext = (size_t)(tx + 2 * hx) * (ty + 2 * hy) * (tz + 2 * hz);
-    return (resident ? 4 : 3) * ext * sizeof(double2) + (size_t)tx * ty * tz * sizeof(double);
+    const size_t inner = (size_t)tx * ty * tz;
+    return (resident ? 4 : 3) * ext * sizeof(double2) + inner * sizeof(double) +
+           (resident ? 2 * (ext - inner) * sizeof(int) : 0);
 }
 
 size_t lanczos_static_smem() {
