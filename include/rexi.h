@@ -43,6 +43,8 @@ extern "C" {
 #define REXI_ETIMEOUT   -5   /* a bounded device-side wait gave up               */
 #define REXI_EPLAN      -6   /* FCF construction failed (root count, spurious pole,
                                 non-unique CF approximant)                        */
+#define REXI_EBOUNDS    -7   /* an index check of a debug build failed; the access
+                                was skipped (rexi_plan_debug_record has the site)  */
 #define REXI_WACCURACY   1   /* Eq. (10) violated: tau*W/hbar > R1 (only with
                                 allow_substeps = 0, or a potential outside the
                                 plan's spectral enclosure)                         */
@@ -317,6 +319,30 @@ int rexi_substep_static(const rexi_grid* g, const double* V, double tau, double 
 
 /* Status of the last call on the plan (synchronises the plan's last stream). */
 int rexi_plan_last_status(rexi_plan* plan);
+
+/* Index checks.  A library built with REXI_DEBUG defined (librexi_debug.so)
+ * checks every indexed access of the Lanczos kernel (ortho = 2) against the
+ * extent of the buffer it addresses: shared-memory staging, the halo ring
+ * list, the basis, B u, the partial sums, the rows of R, y_k and the
+ * coefficients, the states; and, at the start of a launch, that the tile
+ * layout fits the dynamic shared memory and the grid fits the partial-sum
+ * slots.  A failed check records the first failure, skips the access (nothing
+ * outside a buffer is touched), and the launch ends at its next grid barrier
+ * with REXI_EBOUNDS.
+ * rexi_debug_checks: 1 in such a build, 0 otherwise.
+ * rexi_plan_debug_record: rec[0..3] = site (LZ_SITE_* of csrc/lanczos.h; 0 =
+ *   no failure), index, extent of the first failed check of the plan's last
+ *   Lanczos launch, and the number of failed checks; synchronises the plan's
+ *   last stream.  REXI_EINVAL for a plan of a build without checks, or a plan
+ *   that is not a Lanczos plan.
+ * rexi_plan_debug_trip: make every check of `site` (1 .. 11) fail in the
+ *   plan's later launches, 0 = none: the accesses of that site are skipped and
+ *   the launch reports REXI_EBOUNDS, which tests the reporting path without an
+ *   out-of-range index.  REXI_EINVAL as for rexi_plan_debug_record, or for a
+ *   site out of range. */
+int rexi_debug_checks(void);
+int rexi_plan_debug_record(rexi_plan* plan, long long rec[4]);
+int rexi_plan_debug_trip(rexi_plan* plan, int site);
 
 /* Limit of every device-side wait of the plan's launches (grid barriers,
  * bulk-copy completions): seconds > 0, at most 3600; seconds <= 0 restores the

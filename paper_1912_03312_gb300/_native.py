@@ -9,7 +9,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "librexi.so")
+# REXI_DEBUG=1 selects the build with index checks of the Lanczos kernel
+DEBUG_LIB_PATH = os.path.join(HERE, "librexi_debug.so")
+LIB_PATH = DEBUG_LIB_PATH if os.environ.get("REXI_DEBUG") == "1" else os.path.join(HERE, "librexi.so")
 
 REXI_OK = 0
 REXI_EINVAL = -1
@@ -18,6 +20,7 @@ REXI_ECUDA = -3
 REXI_ENOCONV = -4
 REXI_ETIMEOUT = -5
 REXI_EPLAN = -6
+REXI_EBOUNDS = -7
 REXI_WACCURACY = 1
 REXI_FP64 = 0
 REXI_MIXED = 1
@@ -25,6 +28,10 @@ REXI_MAX_POLES = 256
 REXI_MAX_RESTART = 64
 REXI_MAX_RESTART_FULL = 31
 REXI_MAX_KRYLOV = 512
+
+# sites of the index checks of the debug build (csrc/lanczos.h)
+LZ_SITES = {1: "smem", 2: "stage", 3: "stage_src", 4: "ring", 5: "basis", 6: "stencil", 7: "wt", 8: "part",
+            9: "rows", 10: "y", 11: "state"}
 
 
 class Grid(C.Structure):
@@ -79,6 +86,9 @@ SIGNATURES = {
     "rexi_pole_sum": (C.c_int, [_P, _P, _P, _P, _P]),
     "rexi_plan_last_status": (C.c_int, [_P]),
     "rexi_plan_last_launches": (C.c_int, [_P]),
+    "rexi_debug_checks": (C.c_int, []),
+    "rexi_plan_debug_record": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
+    "rexi_plan_debug_trip": (C.c_int, [_P, C.c_int]),
     "rexi_plan_set_trace": (C.c_int, [_P, C.c_int]),
     "rexi_plan_set_tiles": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "rexi_plan_set_timeout": (C.c_int, [_P, C.c_double]),
@@ -109,8 +119,8 @@ def load(path=None):
         return _lib
     p = path or LIB_PATH
     if not os.path.exists(p):
-        raise RuntimeError("librexi.so not found at %s: build it with "
-                           "`python -m paper_1912_03312_gb300.build` (no CPU fallback exists)" % p)
+        raise RuntimeError("%s not found: build it with `python -m paper_1912_03312_gb300.build` "
+                           "(no CPU fallback exists)" % p)
     lib = C.CDLL(p)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)

@@ -1,10 +1,15 @@
-"""Build the in-tree shared library ``librexi.so`` (sm_103a).
+"""Build the in-tree shared libraries ``librexi.so`` and ``librexi_debug.so``
+(sm_103a).
 
     python -m paper_1912_03312_gb300.build [--force]
 
-The translation units are compiled in parallel (the CUDA engine, the shared-basis
-Lanczos kernel, the C ABI, the allocation-free entry point, and the host-side FCF construction in double-double arithmetic, which needs
+The translation units are compiled in parallel (the CUDA engine, the
+shared-basis Lanczos kernel, the C ABI, the allocation-free entry point, and the
+host-side FCF construction in double-double arithmetic, which needs
 floating-point contraction disabled) and linked with the shared CUDA runtime.
+``librexi_debug.so`` is the same library with the Lanczos kernel and the C ABI
+compiled with REXI_DEBUG (index checks on every access of the kernel; the
+binding loads it when the environment sets REXI_DEBUG=1).
 """
 
 from __future__ import annotations
@@ -18,6 +23,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librexi.so")
+DEBUG_LIB = os.path.join(HERE, "librexi_debug.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,14 +42,25 @@ def _sources():
 
 
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(DEBUG_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(DEBUG_LIB))
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
+def _link(nvcc, lib, objs):
+    tmp = lib + ".tmp"
+    link = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + [os.path.join(BUILD, o) for o in objs] + \
+        ["-Xlinker", "-rpath," + os.path.join(CUDA_HOME, "lib64")]
+    r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("librexi link failed:\n" + " ".join(link) + "\n" + r.stdout)
+    os.replace(tmp, lib)
+
+
 def build(force=False, verbose=False):
-    """Compile and link librexi.so unless it is newer than every source."""
+    """Compile and link both libraries unless they are newer than every source;
+    returns the path of librexi.so."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
@@ -57,6 +74,10 @@ def build(force=False, verbose=False):
                                   "-o", os.path.join(BUILD, "static_step.o")],
         [nvcc] + ARCH + common + ["-lineinfo", "-c", os.path.join(CSRC, "lanczos.cu"),
                                   "-o", os.path.join(BUILD, "lanczos.o")],
+        [nvcc] + ARCH + common + ["-DREXI_DEBUG", "-c", os.path.join(CSRC, "api.cu"),
+                                  "-o", os.path.join(BUILD, "api_dbg.o")],
+        [nvcc] + ARCH + common + ["-DREXI_DEBUG", "-lineinfo", "-c", os.path.join(CSRC, "lanczos.cu"),
+                                  "-o", os.path.join(BUILD, "lanczos_dbg.o")],
         ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-c", os.path.join(CSRC, "fcf.cpp"),
          "-o", os.path.join(BUILD, "fcf.o")],
     ]
@@ -70,16 +91,8 @@ def build(force=False, verbose=False):
             print(out)
     if errors:
         raise RuntimeError("librexi build failed:\n" + "\n".join(errors))
-    tmp = LIB + ".tmp"
-    link = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp,
-                            os.path.join(BUILD, "engine.o"), os.path.join(BUILD, "api.o"),
-                            os.path.join(BUILD, "fcf.o"), os.path.join(BUILD, "static_step.o"),
-                            os.path.join(BUILD, "lanczos.o"),
-                            "-Xlinker", "-rpath," + os.path.join(CUDA_HOME, "lib64")]
-    r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("librexi link failed:\n" + " ".join(link) + "\n" + r.stdout)
-    os.replace(tmp, LIB)
+    _link(nvcc, LIB, ["engine.o", "api.o", "fcf.o", "static_step.o", "lanczos.o"])
+    _link(nvcc, DEBUG_LIB, ["engine.o", "api_dbg.o", "fcf.o", "static_step.o", "lanczos_dbg.o"])
     return LIB
 
 

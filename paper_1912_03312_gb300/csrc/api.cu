@@ -117,6 +117,8 @@ struct rexi_plan {
     int* d_lz_cols = nullptr;
     double2* d_lz_shift = nullptr;
     double* d_lz_diag = nullptr;                 // diagonal divided by the stencil fold factor
+    long long* d_dbg = nullptr;                  // index-check builds: record of the last Lanczos launch
+    int dbg_trip = 0;                            // index-check builds: site made to fail
     double lz_fold = 1.0;
     ProblemDesc hprob{};                         // forward problem descriptor (host copy)
     int last_status = REXI_OK;
@@ -532,7 +534,6 @@ int lz_configure(rexi_plan* p) {
         if (tx > target) continue;
         for (int tz = 1; tz <= std::min(nz, target / tx); ++tz) {
             for (int ty = 1; ty <= std::min(ny, target / (tx * tz)); ++ty) {
-                const long long I = (long long)tx * ty * tz;
                 const long long E = (long long)(tx + 2 * hx) * (ty + 2 * hy) * (tz + 2 * hz);
                 if (E > rexi::kLzMaxExt) continue;
                 const size_t smem = std::max(rexi::lanczos_smem_bytes(tx, ty, tz, hx, hy, hz, false), ctl_min);
@@ -600,6 +601,10 @@ int lz_alloc(rexi_plan* p) {
     p->lz_fold = p->a[0] != 0.0 ? p->a[0] : (p->a[1] != 0.0 ? p->a[1] : (p->a[2] != 0.0 ? p->a[2] : 1.0));
     if ((st = dalloc(p, &p->d_lz_diag, n))) return st;
     if ((st = upload_diag(p, 0, true))) return st;
+#ifdef REXI_DEBUG
+    if ((st = dalloc(p, &p->d_dbg, 4))) return st;
+    if (cudaMemset(p->d_dbg, 0, 4 * sizeof(long long)) != cudaSuccess) return REXI_ECUDA;
+#endif
     if (!p->d_stats && (st = dalloc(p, &p->d_stats, K))) return st;
     std::vector<double2> sh(K);
     for (size_t k = 0; k < K; ++k) {
@@ -620,6 +625,7 @@ int lz_launch(rexi_plan* p, int mode, const void* in, void* out, cudaStream_t st
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, 2 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stats, 0, sizeof(ItemStats) * p->K, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_lz_stop, 0xFF, sizeof(int) * nsub, stream);
+    if (e == cudaSuccess && p->d_dbg) e = cudaMemsetAsync(p->d_dbg, 0, 4 * sizeof(long long), stream);
     if (e != cudaSuccess) return cuda_fail(e);
     rexi::LzArgs A{};
     A.mode = mode;
@@ -669,6 +675,9 @@ int lz_launch(rexi_plan* p, int mode, const void* in, void* out, cudaStream_t st
     A.trace = p->trace_cap > 0 ? p->d_trace : nullptr;
     A.trace_cap = p->trace_cap;
     A.bytes = p->d_bytes;
+    A.part_cap = p->lz_part_cap;
+    A.dbg = p->d_dbg;
+    A.dbg_trip = p->dbg_trip;
     e = rexi::launch_lanczos(A, p->lz_grid, p->lz_smem, stream);
     p->last_stream = stream;
     p->last_launches = 1;
@@ -689,6 +698,7 @@ const char* rexi_status_string(int s) {
         case REXI_ENOCONV: return "REXI_ENOCONV: a pole solve did not converge";
         case REXI_ETIMEOUT: return "REXI_ETIMEOUT: bounded device wait expired";
         case REXI_EPLAN: return "REXI_EPLAN: FCF construction failed";
+        case REXI_EBOUNDS: return "REXI_EBOUNDS: an index check of the debug build failed (access skipped)";
         case REXI_WACCURACY: return "REXI_WACCURACY: accuracy condition (Eq. (10)) violated";
         default: return "unknown status";
     }
@@ -1284,6 +1294,29 @@ int rexi_plan_last_status(rexi_plan* p) {
 }
 
 int rexi_plan_last_launches(const rexi_plan* p) { return p ? p->last_launches : 0; }
+
+int rexi_debug_checks(void) {
+#ifdef REXI_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int rexi_plan_debug_record(rexi_plan* p, long long rec[4]) {
+    if (!p || !rec || !p->d_dbg) return REXI_EINVAL;
+    DeviceGuard guard(p->device);
+    if (cudaMemcpyAsync(rec, p->d_dbg, 4 * sizeof(long long), cudaMemcpyDeviceToHost, p->last_stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->last_stream) != cudaSuccess)
+        return REXI_ECUDA;
+    return REXI_OK;
+}
+
+int rexi_plan_debug_trip(rexi_plan* p, int site) {
+    if (!p || !p->d_dbg || site < 0 || site >= rexi::LZ_SITE_COUNT) return REXI_EINVAL;
+    p->dbg_trip = site;
+    return REXI_OK;
+}
 
 int rexi_plan_set_timeout(rexi_plan* p, double seconds) {
     if (!p || !(seconds == seconds) || seconds > 3600.0) return REXI_EINVAL;

@@ -96,9 +96,10 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
 // bar[1] completed barriers; both are zeroed before every launch.  The arrival
 // that makes the count a multiple of the grid size publishes the barrier's
 // number with a release store; the others poll it with acquire loads.  Every
-// wait is bounded by timeout_ns: on expiry the sticky error word is set, and
-// the function returns false (as it does whenever the error word is set), so
-// every CTA leaves the kernel at its next barrier.
+// wait is bounded by timeout_ns: on expiry the sticky error word is set.  A
+// wait also ends when another CTA has set the error word (it may have left the
+// kernel and never arrive).  The function returns false whenever the error
+// word is set, so every CTA leaves the kernel at its next barrier.
 __device__ __forceinline__ bool grid_sync(unsigned* bar, int* err, unsigned long long timeout_ns) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -113,6 +114,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* err, unsigned long
         } else {
             const unsigned long long t0 = global_ns();
             while ((int)(ld_acquire_u32(done) - target) < 0) {
+                if (*(volatile int*)err != 0) break;
                 if (global_ns() - t0 > timeout_ns) {
                     atomicExch(err, kErrTimeout);
                     break;

@@ -54,6 +54,54 @@ using dev::grid_sync;
 constexpr int kLzWarps = kLzBlock / 32;
 constexpr int kErrInternal = -3;        // REXI_ECUDA: the iteration outran its workspace
 
+// ---- index checks (builds with REXI_DEBUG defined) --------------------------
+//
+// LZ_OK(i, extent, site) is true when 0 <= i < extent; LZ_AT(base, i, extent,
+// site) is base[i] then.  A failed check records the first failure (site,
+// index, extent) and a count in A.dbg, sets the launch's error word to
+// REXI_EBOUNDS and skips the access (LZ_AT redirects it to a scratch slot), so
+// nothing outside a buffer is touched; every CTA then leaves at its next grid
+// barrier.  A.dbg_trip makes every check of one site fail (its accesses are
+// skipped), which exercises the reporting path without any bad index.  Without
+// REXI_DEBUG both macros compile to the plain access.
+#ifdef REXI_DEBUG
+constexpr int kErrBounds = -7;          // REXI_EBOUNDS
+__device__ double2 g_lz_sink[2];
+
+__device__ __noinline__ void lz_fail(const LzArgs& A, int site, long long i, long long extent) {
+    unsigned long long* r = reinterpret_cast<unsigned long long*>(A.dbg);
+    if (r != nullptr) {
+        if (atomicCAS(r, 0ull, (unsigned long long)site) == 0ull) {
+            A.dbg[1] = i;
+            A.dbg[2] = extent;
+        }
+        atomicAdd(r + 3, 1ull);
+    }
+    atomicExch(A.err, kErrBounds);
+}
+__device__ __forceinline__ bool lz_ok(const LzArgs& A, long long i, long long extent, int site) {
+    if (i >= 0 && i < extent && site != A.dbg_trip) return true;
+    lz_fail(A, site, i, extent);
+    return false;
+}
+template <class T>
+__device__ __forceinline__ T& lz_at(const LzArgs& A, T* base, long long i, long long extent, int site) {
+    return lz_ok(A, i, extent, site) ? base[i] : *reinterpret_cast<T*>(g_lz_sink);
+}
+#define LZ_OK(i, extent, site) lz_ok(A, (long long)(i), (long long)(extent), (site))
+#define LZ_AT(base, i, extent, site) lz_at(A, (base), (long long)(i), (long long)(extent), (site))
+
+// Dynamic shared memory of the launch in bytes.
+__device__ __forceinline__ unsigned dyn_bytes() {
+    unsigned v;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+#else
+#define LZ_OK(i, extent, site) true
+#define LZ_AT(base, i, extent, site) ((base)[i])
+#endif
+
 struct LzSmem {
     double rho, a, b;        // coefficients of the next update (those of the last reduced sweep)
     double cw, ca, cb;       // the update as applied: u_j = cw w' - ca u_{j-1} - cb u_{j-2}
@@ -210,7 +258,9 @@ __device__ __forceinline__ void load_partials(const LzArgs& A, int par, PartLoad
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const int c = 1 + threadIdx.x + q * kLzBlock;
-        L.v[q] = c < (int)gridDim.x ? __ldcg(p + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        L.v[q] = c < (int)gridDim.x && LZ_OK(par * gridDim.x + c, 2 * A.part_cap, LZ_SITE_PART)
+                     ? __ldcg(p + c)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 // ... and the CTA sums them in double-float on the FP32 pipe (the FP64 pipe is
@@ -225,6 +275,7 @@ __device__ __forceinline__ double2 reduce_partials(const LzArgs& A, LzSmem& sm, 
     }
     const float4* p = A.part + (size_t)par * gridDim.x;
     for (int c = 1 + threadIdx.x + 5 * kLzBlock; c < (int)gridDim.x; c += kLzBlock) {
+        if (!LZ_OK(par * gridDim.x + c, 2 * A.part_cap, LZ_SITE_PART)) continue;
         const float4 w = __ldcg(p + c);
         df_add(nh, nl, w.x, w.y);
         df_add(ph, pl, w.z, w.w);
@@ -357,7 +408,8 @@ struct Stage {
     double2* U1;       // streamed: u_{j-1}
     double2* U2;       // streamed: u_{j-2}
     double2* R0;       // resident: the last three vectors, R0 + k ext_max for k = 0, 1, 2
-    int ext_max;
+    int ext_max;       // points of the largest extended box and of the largest interior
+    int int_max;
     double* D;
     int* ringE;        // resident: extended-box index and global index of every halo ring point
     int* ringG;
@@ -376,6 +428,7 @@ __device__ void stage_tile(const LzArgs& A, const Stage& st, const double2* u0, 
     for (int e = threadIdx.x; e < T.E; e += kLzBlock, w.next(T.ex, T.ey)) {
         int inner;
         const size_t g = ext_index(A, T, w, hx, hy, hz, &inner);
+        if (!LZ_OK(e, st.ext_max, LZ_SITE_STAGE) || !LZ_OK(g, A.n, LZ_SITE_STAGE_SRC)) continue;
         if (j == 0) {
             cp_async16(st.W + e, u0 + g);
         } else {
@@ -388,7 +441,8 @@ __device__ void stage_tile(const LzArgs& A, const Stage& st, const double2* u0, 
     wi.init(threadIdx.x, T.tx, T.ty);
     for (int i = threadIdx.x; i < T.I; i += kLzBlock, wi.next(T.tx, T.ty)) {
         int e;
-        cp_async8(st.D + i, A.diag + int_index(A, T, wi, hx, hy, hz, &e));
+        const size_t g = int_index(A, T, wi, hx, hy, hz, &e);
+        if (LZ_OK(i, st.int_max, LZ_SITE_STAGE) && LZ_OK(g, A.n, LZ_SITE_STAGE_SRC)) cp_async8(st.D + i, A.diag + g);
     }
     cp_async_commit();
 }
@@ -403,11 +457,16 @@ __device__ void stage_resident(const LzArgs& A, const LzSmem& sm, const Stage& s
         w.init(threadIdx.x, T.ex, T.ey);
         for (int e = threadIdx.x; e < T.E; e += kLzBlock, w.next(T.ex, T.ey)) {
             int inner;
-            cp_async16(st.R(0) + e, u0 + ext_index(A, T, w, hx, hy, hz, &inner));
+            const size_t g = ext_index(A, T, w, hx, hy, hz, &inner);
+            if (LZ_OK(e, st.ext_max, LZ_SITE_STAGE) && LZ_OK(g, A.n, LZ_SITE_STAGE_SRC)) cp_async16(st.R(0) + e, u0 + g);
         }
     } else {
         const double2* wprev = A.wt + (size_t)((j - 1) & 1) * A.n;
-        for (int q = threadIdx.x; q < sm.nring; q += kLzBlock) cp_async16(st.W + st.ringE[q], wprev + st.ringG[q]);
+        for (int q = threadIdx.x; q < sm.nring; q += kLzBlock) {
+            if (!LZ_OK(q, st.ext_max - st.int_max, LZ_SITE_RING)) continue;
+            const int e = st.ringE[q], g = st.ringG[q];
+            if (LZ_OK(e, st.ext_max, LZ_SITE_STAGE) && LZ_OK(g, A.n, LZ_SITE_STAGE_SRC)) cp_async16(st.W + e, wprev + g);
+        }
     }
     cp_async_commit();
 }
@@ -420,7 +479,8 @@ __device__ void setup_resident(const LzArgs& A, LzSmem& sm, const Stage& st, int
     wi.init(threadIdx.x, T.tx, T.ty);
     for (int i = threadIdx.x; i < T.I; i += kLzBlock, wi.next(T.tx, T.ty)) {
         int e;
-        cp_async8(st.D + i, A.diag + int_index(A, T, wi, hx, hy, hz, &e));
+        const size_t g = int_index(A, T, wi, hx, hy, hz, &e);
+        if (LZ_OK(i, st.int_max, LZ_SITE_STAGE) && LZ_OK(g, A.n, LZ_SITE_STAGE_SRC)) cp_async8(st.D + i, A.diag + g);
     }
     cp_async_commit();
     if (threadIdx.x == 0) sm.nring = 0;
@@ -432,6 +492,7 @@ __device__ void setup_resident(const LzArgs& A, LzSmem& sm, const Stage& st, int
         const size_t g = ext_index(A, T, w, hx, hy, hz, &inner);
         if (inner < 0) {
             const int q = atomicAdd(&sm.nring, 1);
+            if (!LZ_OK(q, st.ext_max - st.int_max, LZ_SITE_RING)) continue;
             st.ringE[q] = e;
             st.ringG[q] = (int)g;
         }
@@ -458,8 +519,13 @@ __device__ __forceinline__ void phase_a(const LzArgs& A, const Tile& T, const do
         const double2 v = make_double2(vx, vy);
         out[e] = v;
         const int ix = wa.x - hx, iy = wa.y - hy, iz = wa.z - hz;
-        if (ix >= 0 && ix < T.tx && iy >= 0 && iy < T.ty && iz >= 0 && iz < T.tz)
-            ujw[(size_t)(T.x0 + ix) + (size_t)A.nx * ((size_t)(T.y0 + iy) + (size_t)A.ny * (size_t)(T.z0 + iz))] = v;
+        if (ix >= 0 && ix < T.tx && iy >= 0 && iy < T.ty && iz >= 0 && iz < T.tz) {
+            const size_t g =
+                (size_t)(T.x0 + ix) + (size_t)A.nx * ((size_t)(T.y0 + iy) + (size_t)A.ny * (size_t)(T.z0 + iz));
+            if (LZ_OK((long long)(j - 1) * A.n + (long long)g, (long long)(A.m + 2) * A.n, LZ_SITE_BASIS) &&
+                LZ_OK(g, A.n, LZ_SITE_BASIS))
+                ujw[g] = v;
+        }
     }
 }
 
@@ -480,16 +546,16 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
     for (int i = threadIdx.x; i < T.I; i += kLzBlock, wb.next(T.tx, T.ty)) {
         int e;
         const size_t g = int_index(A, T, wb, hx, hy, hz, &e);
-        const double2 c = S[e];
-        const double dg = D[i];
+        const double2 c = LZ_AT(S, e, T.E, LZ_SITE_STENCIL);
+        const double dg = LZ_AT(D, i, T.I, LZ_SITE_STENCIL);
         double wx = 0.0, wy = 0.0;
         if (hx) {
-            const double2 l = S[e - 1], rr = S[e + 1];
+            const double2 l = LZ_AT(S, e - 1, T.E, LZ_SITE_STENCIL), rr = LZ_AT(S, e + 1, T.E, LZ_SITE_STENCIL);
             wx = l.x + rr.x;
             wy = l.y + rr.y;
         }
         if (hy) {
-            const double2 l = S[e - sy], rr = S[e + sy];
+            const double2 l = LZ_AT(S, e - sy, T.E, LZ_SITE_STENCIL), rr = LZ_AT(S, e + sy, T.E, LZ_SITE_STENCIL);
             if (hx) {
                 wx = fma(ry, l.x + rr.x, wx);
                 wy = fma(ry, l.y + rr.y, wy);
@@ -499,7 +565,7 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
             }
         }
         if (hz) {
-            const double2 l = S[e - sz], rr = S[e + sz];
+            const double2 l = LZ_AT(S, e - sz, T.E, LZ_SITE_STENCIL), rr = LZ_AT(S, e + sz, T.E, LZ_SITE_STENCIL);
             if (hx || hy) {
                 wx = fma(rz, l.x + rr.x, wx);
                 wy = fma(rz, l.y + rr.y, wy);
@@ -511,8 +577,8 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
         wx = fma(dg, c.x, wx);
         wy = fma(dg, c.y, wy);
         const double2 wv = make_double2(wx, wy);
-        wcur[g] = wv;
-        if (Wown) Wown[e] = wv;
+        if (LZ_OK(g, A.n, LZ_SITE_WT)) wcur[g] = wv;
+        if (Wown) LZ_AT(Wown, e, T.E, LZ_SITE_STENCIL) = wv;
         float cxh, cxl, cyh, cyl, wxh, wxl, wyh, wyl;
         split_f64(c.x, &cxh, &cxl);
         split_f64(c.y, &cyh, &cyl);
@@ -540,11 +606,13 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
             double2* S = st.R(j % 3);
             cp_async_wait_all();
             __syncthreads();
-            if (j >= 1) {
-                phase_a(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, ujw, j, cw, ca, cb, hx, hy, hz);
-                __syncthreads();
+            if (LZ_OK(T.E, st.ext_max + 1, LZ_SITE_SMEM) && LZ_OK(T.I, st.int_max + 1, LZ_SITE_SMEM)) {
+                if (j >= 1) {
+                    phase_a(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, ujw, j, cw, ca, cb, hx, hy, hz);
+                    __syncthreads();
+                }
+                phase_b(A, T, S, st.D, st.W, wcur, hx, hy, hz, nh, nl, ph, pl);
             }
-            phase_b(A, T, S, st.D, st.W, wcur, hx, hy, hz, nh, nl, ph, pl);
         }
     } else {
         for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
@@ -552,6 +620,7 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
             const Tile T = tile_of(A, t, hx, hy, hz);
             cp_async_wait_all();
             __syncthreads();
+            if (!LZ_OK(T.E, st.ext_max + 1, LZ_SITE_SMEM) || !LZ_OK(T.I, st.int_max + 1, LZ_SITE_SMEM)) break;
             if (j >= 1) {
                 phase_a(A, T, st.W, st.U1, st.U2, st.W, ujw, j, cw, ca, cb, hx, hy, hz);
                 __syncthreads();
@@ -582,11 +651,14 @@ __device__ void combine(const LzArgs& A, const double2* coef, const double2* u0,
                 if (i < T.I) {
                     g[q] = int_index(A, T, wb, hx, hy, hz, &e);
                     wb.next(T.tx, T.ty);
+                    if (!LZ_OK(g[q], A.n, LZ_SITE_STATE)) g[q] = 0;
                 }
                 acc[q] = make_double2(0.0, 0.0);
             }
 #pragma unroll 4
             for (int r = 0; r < J; ++r) {
+                // u_r is the input state (r = 0) or basis row r - 1 < m + 2
+                if (!LZ_OK(r, kLzMaxM, LZ_SITE_Y) || !LZ_OK(r, A.m + 3, LZ_SITE_BASIS)) break;
                 const double2 c = coef[r];
                 const double2* u = uvec(A, u0, r);
 #pragma unroll
@@ -614,6 +686,7 @@ struct PoleState {
 };
 
 __device__ __forceinline__ void put_row(const LzArgs& A, int r, int k, double2 g, double2 inv, double2 r1, double2 r2) {
+    if (!LZ_OK(r, A.m, LZ_SITE_ROWS) || !LZ_OK(k, A.K, LZ_SITE_ROWS)) return;
     double2* p = A.rows + ((size_t)r * A.K + k) * 3;
     p[0] = cmul(g, inv);
     p[1] = cmul(r1, inv);
@@ -679,7 +752,10 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
     double2 y1 = make_double2(0.0, 0.0), y2 = make_double2(0.0, 0.0);
     for (int top = J; top > 0; top -= stage_rows) {
         const int lo = max(0, top - stage_rows);
-        const int cnt = (top - lo) * K * 3;
+        int cnt = (top - lo) * K * 3;
+        if (!LZ_OK(cnt - 1, (long long)dyn_bytes() / sizeof(double2), LZ_SITE_ROWS) ||
+            !LZ_OK((long long)top * K * 3 - 1, (long long)A.m * K * 3, LZ_SITE_ROWS))
+            cnt = 0;
         __syncthreads();
 #pragma unroll 8
         for (int q = threadIdx.x; q < cnt; q += kLzBlock) stage[q] = __ldcg(A.rows + (size_t)lo * K * 3 + q);
@@ -687,15 +763,17 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
         if (k < K) {
             for (int r = top - 1; r >= lo; --r) {
                 double2 y = make_double2(0.0, 0.0);
-                if (r < P.kk) {
+                if (r < P.kk && cnt > 0) {
                     const double2* q = stage + ((size_t)(r - lo) * K + k) * 3;
                     const double2 mr1 = make_double2(-q[1].x, -q[1].y), mr2 = make_double2(-q[2].x, -q[2].y);
                     y = cfma(cfma(q[0], mr2, y2), mr1, y1);
                 }
-                if (A.mode == LZ_STEP)
-                    A.ybuf[(size_t)r * K + k] = y;
-                else
+                if (A.mode == LZ_STEP) {
+                    if (LZ_OK((long long)r * K + k, (long long)A.m * K, LZ_SITE_Y)) A.ybuf[(size_t)r * K + k] = y;
+                } else if (LZ_OK((long long)k * A.m + r, (long long)A.m * K, LZ_SITE_Y) &&
+                           LZ_OK(r, A.m + 2, LZ_SITE_Y)) {
                     A.coef[(size_t)k * A.m + r] = csc(y, A.rho[r]);
+                }
                 y2 = y1;
                 y1 = y;
             }
@@ -710,7 +788,7 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
         for (int r0 = 0; r0 < Jn; r0 += kLzBlock / 8) {
             const int r = r0 + (threadIdx.x >> 3);
             double2 acc = make_double2(0.0, 0.0);
-            if (r < J) {
+            if (r < J && LZ_OK((long long)r * K + K - 1, (long long)A.m * K, LZ_SITE_Y)) {
 #pragma unroll 4
                 for (int kq = q; kq < K; kq += 8) acc = cfma(acc, __ldg(A.alpha + kq), A.ybuf[(size_t)r * K + kq]);
             }
@@ -719,7 +797,7 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
                 acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
             }
-            if (q == 0 && r < Jn) {
+            if (q == 0 && r < Jn && LZ_OK(r, A.m, LZ_SITE_Y) && LZ_OK(r, A.m + 2, LZ_SITE_Y)) {
                 double2 c = r < J ? csc(acc, A.rho[r]) : make_double2(0.0, 0.0);
                 if (r == 0) {
                     c.x += A.alpha0.x;
@@ -738,7 +816,7 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
         st.resid = fmax(st.resid, P.bound);
         if (P.done != 1) st.failed = 1;
     }
-    if (threadIdx.x == 0) A.cols[s] = J;
+    if (threadIdx.x == 0 && LZ_OK(s, 2 * A.nsub, LZ_SITE_Y)) A.cols[s] = J;
     (void)sm;
 }
 
@@ -757,9 +835,21 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
     st.ext_max = ext_max;
     st.D = (double*)(dyn + (A.resident ? 4 : 3) * ext_max);
     const int int_max = A.tx * A.ty * A.tz;
+    st.int_max = int_max;
     st.ringE = (int*)(st.D + int_max);
     st.ringG = st.ringE + (ext_max - int_max);
     const int stage_rows = A.stage_rows;
+#ifdef REXI_DEBUG
+    {
+        // the layout above (tile CTAs) and the row staging (control CTA) fit the
+        // launch's dynamic shared memory; the grid fits the partial-sum slots
+        const long long need = control ? (long long)stage_rows * A.K * 3 * 16
+                                       : (long long)(A.resident ? 4 : 3) * ext_max * 16 + (long long)int_max * 8 +
+                                             (A.resident ? 8LL * (ext_max - int_max) : 0LL);
+        if (!LZ_OK(need, (long long)dyn_bytes() + 1, LZ_SITE_SMEM) || !LZ_OK(gridDim.x, A.part_cap + 1, LZ_SITE_PART))
+            return;
+    }
+#endif
     if (A.resident && !control) {
         if (has_tile) {
             setup_resident(A, sm, st, hx, hy, hz);
@@ -797,7 +887,7 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
             int stop_word = -1;
             if (j >= 1) {
                 load_partials(A, (j - 1) & 1, L);
-                if (threadIdx.x == 0) stop_word = __ldcg(A.stop + s);
+                if (threadIdx.x == 0 && LZ_OK(s, A.nsub, LZ_SITE_Y)) stop_word = __ldcg(A.stop + s);
             }
             if (has_tile) {
                 if (A.resident)
@@ -835,7 +925,7 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                     sm.hn[1] = sm.hn[0];
                     sm.hn[0] = n;
                     sm.stop = stop_word;
-                    if (control) A.rho[j - 1] = rho;
+                    if (control && LZ_OK(j - 1, A.m + 2, LZ_SITE_Y)) A.rho[j - 1] = rho;
                 }
                 __syncthreads();
                 if (sm.stop >= 0) {
@@ -853,7 +943,8 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
             if (!control) {
                 float4 part;
                 sweep(A, sm, st, u0, j, hx, hy, hz, &part);
-                if (threadIdx.x == 0) A.part[(size_t)(j & 1) * gridDim.x + blockIdx.x] = part;
+                if (threadIdx.x == 0 && LZ_OK((j & 1) * gridDim.x + blockIdx.x, 2 * A.part_cap, LZ_SITE_PART))
+                    A.part[(size_t)(j & 1) * gridDim.x + blockIdx.x] = part;
             } else if (j >= 1) {
                 // the control CTA works one column behind: column c = j - 2 is
                 // complete once the norm of u_{j-1} (its subdiagonal) is known
@@ -899,7 +990,7 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
         // y_k and the coefficients of the final pass
         if (control) {
             if (threadIdx.x == 0) {
-                A.cols[A.nsub + s] = sweeps;
+                if (LZ_OK(A.nsub + s, 2 * A.nsub, LZ_SITE_Y)) A.cols[A.nsub + s] = sweeps;
                 // the work the specified recurrence moves and computes (halo
                 // re-reads not counted): sweep 0 reads u_0 and the diagonal and
                 // writes B u_0; sweep 1 also reads B u_0 and writes u_1; later
@@ -929,14 +1020,16 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
         if (!control) {
             if (A.mode == LZ_STEP) {
                 const int Jn = max(J, 1);
-                for (int r = threadIdx.x; r < Jn; r += kLzBlock) sm.coef[r] = __ldcg(A.coef + r);
+                for (int r = threadIdx.x; r < Jn; r += kLzBlock)
+                    if (LZ_OK(r, kLzMaxM, LZ_SITE_Y) && LZ_OK(r, A.m, LZ_SITE_Y)) sm.coef[r] = __ldcg(A.coef + r);
                 __syncthreads();
                 combine(A, sm.coef, u0, out, Jn, hx, hy, hz);
             } else {
                 for (int k = 0; k < A.K; ++k) {
                     __syncthreads();
                     for (int r = threadIdx.x; r < J; r += kLzBlock)
-                        sm.coef[r] = __ldcg(A.coef + (size_t)k * A.m + r);
+                        if (LZ_OK(r, kLzMaxM, LZ_SITE_Y) && LZ_OK(r, A.m, LZ_SITE_Y))
+                            sm.coef[r] = __ldcg(A.coef + (size_t)k * A.m + r);
                     __syncthreads();
                     combine(A, sm.coef, u0, A.out + (size_t)k * A.n, J, hx, hy, hz);
                 }

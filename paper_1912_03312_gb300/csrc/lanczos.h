@@ -25,6 +25,23 @@ enum : int { LZ_STEP = 0, LZ_SOLVE = 1 };
 // trace codes (after the phase codes of the engine)
 enum : int { TR_LZ_SWEEP = 11, TR_LZ_SOLVE = 12, TR_LZ_SUM = 13 };
 
+// Sites of the index checks of a build with REXI_DEBUG defined (the numbers a
+// failed check records; 0 = none).
+enum : int {
+    LZ_SITE_SMEM = 1,        // shared-memory layout of the launch, tile boxes
+    LZ_SITE_STAGE = 2,       // copies into shared memory (extended box, diagonal)
+    LZ_SITE_STAGE_SRC = 3,   // their global sources
+    LZ_SITE_RING = 4,        // halo ring list of a resident tile
+    LZ_SITE_BASIS = 5,       // basis vectors (stores of phase A, reads of the final pass)
+    LZ_SITE_STENCIL = 6,     // stencil and diagonal reads of phase B
+    LZ_SITE_WT = 7,          // B u stores
+    LZ_SITE_PART = 8,        // per-CTA partial sums
+    LZ_SITE_ROWS = 9,        // rows of R (stores, staging for the back substitution)
+    LZ_SITE_Y = 10,          // y_k, coefficients and scales of the final pass
+    LZ_SITE_STATE = 11,      // input, output and substep states
+    LZ_SITE_COUNT = 12
+};
+
 struct LzArgs {
     int mode;                  // LZ_STEP: nsub substeps ending in the pole sum; LZ_SOLVE: x_k for every pole
     int n, nx, ny, nz;         // grid (x fastest); unused dimensions have extent 1
@@ -64,6 +81,9 @@ struct LzArgs {
     unsigned long long* trace; // optional [1 + 2 cap]: (phase, ns) at every barrier
     int trace_cap;
     unsigned long long* bytes; // [2]: algorithmic bytes and FP64 flops of the launch (added by the control CTA)
+    int part_cap;              // slots per parity of part (>= grid)
+    long long* dbg;            // REXI_DEBUG builds: [4] first failed check (site, index, extent), count
+    int dbg_trip;              // REXI_DEBUG builds: a site whose every check fails (0: none)
 };
 
 cudaError_t launch_lanczos(const LzArgs& args, int grid, size_t smem, cudaStream_t stream);

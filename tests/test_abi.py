@@ -40,6 +40,20 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, nm), nm
 
 
+def test_debug_build_exports_the_same_symbols_and_says_so(lib):
+    # librexi_debug.so (index checks in the Lanczos kernel) is the same ABI
+    from paper_1912_03312_gb300 import _native as N
+    dbg = C.CDLL(N.DEBUG_LIB_PATH)
+    for nm in header_functions():
+        assert hasattr(dbg, nm), nm
+    dbg.rexi_debug_checks.restype = C.c_int
+    assert dbg.rexi_debug_checks() == 1 and lib.rexi_debug_checks() == 0
+    rec = (C.c_longlong * 4)()
+    assert lib.rexi_plan_debug_record(None, rec) == N.REXI_EINVAL
+    assert lib.rexi_plan_debug_trip(None, 1) == N.REXI_EINVAL
+    assert "REXI_EBOUNDS" in N.status_string(N.REXI_EBOUNDS)
+
+
 def test_binding_covers_header():
     from paper_1912_03312_gb300 import _native
     assert sorted(_native.SIGNATURES) == header_functions()

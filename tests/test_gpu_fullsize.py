@@ -76,14 +76,54 @@ def test_2d_wells_512_benchmarked_path_matches_oracle(tiles):
     assert info["R1"] == 68.0 and info["n_sub"] == 2
     orc = OraclePlan(g, cfg["V"], cfg["dt"], cfg["K"], info["R1"])
     cur_gpu = to_dev(cfg["psi0"])
-    ref = cfg["psi0"]
-    for _ in range(2):
+    for ref in _oracle_2d_steps(cfg, orc, 2):
         cur_gpu, st = lp.step(cur_gpu, stats=True)
         assert st["status"] == 0
-        ref, _ = ostep.step(cfg["V"], orc.h, ref, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
         err = relerr(cur_gpu.cpu().numpy(), ref)
         log_parity("2d_wells_512_benchmarked_path[%s]" % ("default" if tiles is None else "1cta"), err, 1e-6,
                    iters=st["total_iters"])
+        assert err < 1e-6, err
+
+
+_ORACLE_2D = []
+
+
+def _oracle_2d_steps(cfg, orc, n):
+    """The oracle's first n user steps of the benchmark workload (cached)."""
+    while len(_ORACLE_2D) < n:
+        prev = _ORACLE_2D[-1] if _ORACLE_2D else cfg["psi0"]
+        ref, _ = ostep.step(cfg["V"], orc.h, prev, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
+        _ORACLE_2D.append(ref)
+    return _ORACLE_2D[:n]
+
+
+@pytest.mark.parametrize("tiles", [None, {"pole_tile": 1024, "group_tile": 1024, "ctas_per_sm": 2},
+                                   {"pole_tile": 1024, "group_tile": 2048, "ctas_per_sm": 1},
+                                   {"pole_tile": 1024, "group_tile": 512, "ctas_per_sm": 1}])
+def test_2d_wells_512_lanczos_path_matches_oracle(tiles):
+    # The path the benchmark times: the shared-basis Lanczos kernel (FP64, one
+    # basis per substep for all 32 poles, the plan's own tolerance, at most 256
+    # columns per substep), under the default tile boxes and under tile settings
+    # the autotuner chooses between (two CTAs per SM with resident tiles, one CTA
+    # per SM, and boxes small enough that CTAs stream several tiles).  Two user
+    # steps, each element-wise against the oracle's step to the metric's 1e-6.
+    from paper_1912_03312_gb300 import autotune
+    cfg = wl.config_2d_wells()
+    g = cfg["grid"]
+    lp = _plan(cfg, g, cfg["V"], cfg["K"], precision="fp64", ortho="lanczos")
+    if tiles is not None:
+        autotune.apply(lp, tiles)
+    info = lp.info()
+    assert info["R1"] == 68.0 and info["n_sub"] == 2 and info["restart_m"] == 256
+    orc = OraclePlan(g, cfg["V"], cfg["dt"], cfg["K"], info["R1"])
+    refs = _oracle_2d_steps(cfg, orc, 2)
+    cur = to_dev(cfg["psi0"])
+    name = "default" if tiles is None else "%d_%d" % (tiles["group_tile"], tiles["ctas_per_sm"])
+    for s, ref in enumerate(refs):
+        cur, st = lp.step(cur, stats=True)
+        assert st["status"] == 0
+        err = relerr(cur.cpu().numpy(), ref)
+        log_parity("2d_wells_512_lanczos[%s,step%d]" % (name, s), err, 1e-6, iters=st["total_iters"])
         assert err < 1e-6, err
 
 
@@ -99,15 +139,18 @@ def test_3d_coulomb_K64_is_refused():
 _ORACLE_3D = {}
 
 
-@pytest.mark.parametrize("precision,tol_pole", [("mixed", 1e-6), ("fp64", 1e-10)])
+@pytest.mark.parametrize("precision,tol_pole", [("mixed", 1e-6), ("fp64", 1e-10), ("lanczos", 1e-10)])
 def test_3d_coulomb_128_sampled_poles_and_plane_wave(precision, tol_pole):
+    # "lanczos": the shared-basis Lanczos kernel (FP64) with streamed tiles
     cfg = wl.config_3d_coulomb()
     g = cfg["grid"]
     K = 32
     R1 = 68.0
     orc = OraclePlan(g, cfg["V"], cfg["dt"], K, R1)
     tol = solve_tol(orc.A * orc.n_sub)
-    lp = _plan(cfg, g, cfg["V"], K, precision=precision, tol=tol, max_iters=20000)
+    kw = dict(precision="fp64", ortho="lanczos") if precision == "lanczos" else dict(precision=precision,
+                                                                                      max_iters=20000)
+    lp = _plan(cfg, g, cfg["V"], K, tol=tol, **kw)
     info = lp.info()
     assert info["R1"] == R1
     assert orc.n_sub == info["n_sub"] == 1
@@ -137,7 +180,7 @@ def test_3d_coulomb_128_sampled_poles_and_plane_wave(precision, tol_pole):
     del out, lp
     # plane wave on a constant potential: the step is the scalar rational
     V0 = -0.3
-    lw = _plan(cfg, g, np.full(g["n"][::-1], V0), K, precision=precision, tol=tol, max_iters=20000)
+    lw = _plan(cfg, g, np.full(g["n"][::-1], V0), K, tol=tol, **kw)
     X = wl.coords(g)
     L = 30.0
     m = (2, -1, 3)
