@@ -112,7 +112,12 @@ struct LzSmem {
     double hrho[3], ha[3], hn[3];   // (rho, a, n) of sweeps j-1, j-2, j-3
     float red[kLzWarps][4];  // per-warp double-float sums (n_hi, n_lo, p_hi, p_lo)
     int stop;
-    double2 coef[kLzMaxM];   // final pass: coefficients of the stored vectors
+    int cexp;                // final pass, resident mode: largest biased exponent of the coefficients c_r, r >= 1
+    double2 c0;              //                            coefficient of the input state
+    union {
+        double2 coef[kLzMaxM];   // final pass: coefficients of the stored vectors
+        float4 coefs[kLzMaxM];   //             resident mode: their hi/lo splits, scaled by 2^-E (r >= 1)
+    };
 };
 
 struct Tile {
@@ -501,8 +506,8 @@ __device__ void setup_resident(const LzArgs& A, LzSmem& sm, const Stage& st, int
 }
 
 // Phase A on one tile: v = rho (w - a u1 - b u2) on the extended box (in place
-// of W in streamed mode, into R[j mod 3] in resident mode); the tile's own
-// points are stored (they are u_j of the basis).
+// of W in streamed mode, into R[j mod 3] in resident mode); with ujw given
+// (streamed mode) the tile's own points are stored (they are u_j of the basis).
 __device__ __forceinline__ void phase_a(const LzArgs& A, const Tile& T, const double2* W, const double2* U1,
                                         const double2* U2, double2* out, double2* ujw, int j, double cw, double ca,
                                         double cb, int hx, int hy, int hz) {
@@ -519,7 +524,7 @@ __device__ __forceinline__ void phase_a(const LzArgs& A, const Tile& T, const do
         const double2 v = make_double2(vx, vy);
         out[e] = v;
         const int ix = wa.x - hx, iy = wa.y - hy, iz = wa.z - hz;
-        if (ix >= 0 && ix < T.tx && iy >= 0 && iy < T.ty && iz >= 0 && iz < T.tz) {
+        if (ujw != nullptr && ix >= 0 && ix < T.tx && iy >= 0 && iy < T.ty && iz >= 0 && iz < T.tz) {
             const size_t g =
                 (size_t)(T.x0 + ix) + (size_t)A.nx * ((size_t)(T.y0 + iy) + (size_t)A.ny * (size_t)(T.z0 + iz));
             if (LZ_OK((long long)(j - 1) * A.n + (long long)g, (long long)(A.m + 2) * A.n, LZ_SITE_BASIS) &&
@@ -531,10 +536,12 @@ __device__ __forceinline__ void phase_a(const LzArgs& A, const Tile& T, const do
 
 // Phase B on one tile: B u_j from S (the extended box of u_j), stored to the
 // global B u_j (and, resident mode, into Wown at the interior points); the
-// compensated partial sums of ||u_j||^2 and Re u_j^H B u_j accumulate.
+// compensated partial sums of ||u_j||^2 and Re u_j^H B u_j accumulate.  With
+// ujs given (resident mode) u_j is stored to the basis as its hi/lo split
+// (the pieces the inner products use): (re_hi, re_lo, im_hi, im_lo).
 __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const double2* S, const double* D,
-                                        double2* Wown, double2* wcur, int hx, int hy, int hz, float& nh, float& nl,
-                                        float& ph, float& pl) {
+                                        double2* Wown, double2* wcur, float4* ujs, int hx, int hy, int hz,
+                                        float& nh, float& nl, float& ph, float& pl) {
     // w' = B u / f with f = the coefficient of the first dimension the stencil
     // reaches: that dimension's neighbour pair enters with weight one, the
     // others with r_d = a_d / f, the diagonal (D = diag / f) with one fused
@@ -582,6 +589,7 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
         float cxh, cxl, cyh, cyl, wxh, wxl, wyh, wyl;
         split_f64(c.x, &cxh, &cxl);
         split_f64(c.y, &cyh, &cyl);
+        if (ujs != nullptr && LZ_OK(g, A.n, LZ_SITE_BASIS)) ujs[g] = make_float4(cxh, cxl, cyh, cyl);
         split_f64(wx, &wxh, &wxl);
         split_f64(wy, &wyh, &wyl);
         df_madd(nh, nl, cxh, cxl, cxh, cxl);
@@ -608,10 +616,12 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
             __syncthreads();
             if (LZ_OK(T.E, st.ext_max + 1, LZ_SITE_SMEM) && LZ_OK(T.I, st.int_max + 1, LZ_SITE_SMEM)) {
                 if (j >= 1) {
-                    phase_a(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, ujw, j, cw, ca, cb, hx, hy, hz);
+                    phase_a(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, nullptr, j, cw, ca, cb, hx, hy,
+                            hz);
                     __syncthreads();
                 }
-                phase_b(A, T, S, st.D, st.W, wcur, hx, hy, hz, nh, nl, ph, pl);
+                float4* ujs = j >= 1 && LZ_OK(j - 1, A.m + 2, LZ_SITE_BASIS) ? reinterpret_cast<float4*>(ujw) : nullptr;
+                phase_b(A, T, S, st.D, st.W, wcur, ujs, hx, hy, hz, nh, nl, ph, pl);
             }
         }
     } else {
@@ -625,7 +635,7 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
                 phase_a(A, T, st.W, st.U1, st.U2, st.W, ujw, j, cw, ca, cb, hx, hy, hz);
                 __syncthreads();
             }
-            phase_b(A, T, st.W, st.D, nullptr, wcur, hx, hy, hz, nh, nl, ph, pl);
+            phase_b(A, T, st.W, st.D, nullptr, wcur, nullptr, hx, hy, hz, nh, nl, ph, pl);
             __syncthreads();                      // shared memory is restaged for the next tile
         }
     }
@@ -668,6 +678,98 @@ __device__ void combine(const LzArgs& A, const double2* coef, const double2* u0,
 #pragma unroll
             for (int q = 0; q < kCh; ++q)
                 if (i0 + q * kLzBlock < T.I) dst[g[q]] = acc[q];
+        }
+    }
+}
+
+// Resident mode (the basis holds the hi/lo splits of u_1, u_2, ...): the
+// coefficients in sm.coef become c0 = c_0 (FP64, the input state's term) and,
+// for r >= 1, the splits of 2^-E c_r with 2^E above the largest |Re|, |Im|, so
+// the double-float products stay in the FP32 range; returns 2^E.
+__device__ double split_coefficients(LzSmem& sm, int J) {
+    if (threadIdx.x == 0) {
+        sm.cexp = 0;
+        sm.c0 = J >= 1 ? sm.coef[0] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    double2 c[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int r = threadIdx.x + q * kLzBlock;
+        c[q] = r >= 1 && r < J ? sm.coef[r] : make_double2(0.0, 0.0);
+        const int ex = (__double2hiint(c[q].x) >> 20) & 0x7FF, ey = (__double2hiint(c[q].y) >> 20) & 0x7FF;
+        if (r >= 1 && r < J) atomicMax(&sm.cexp, max(ex, ey));
+    }
+    __syncthreads();
+    // 2^-E with E = (largest biased exponent) - 1022: scaled values below one
+    const int k = min(1000, max(-1000, 1022 - sm.cexp));
+    const double down = __hiloint2double((1023 + k) << 20, 0);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int r = threadIdx.x + q * kLzBlock;
+        if (r >= 1 && r < J) {
+            float xh, xl, yh, yl;
+            split_f64(c[q].x * down, &xh, &xl);
+            split_f64(c[q].y * down, &yh, &yl);
+            sm.coefs[r] = make_float4(xh, xl, yh, yl);
+        }
+    }
+    __syncthreads();
+    return __hiloint2double((1023 - k) << 20, 0);
+}
+
+// Final pass, resident mode: dst = c_0 u_0 + 2^E sum_{1 <= r < J} (2^-E c_r) u_r;
+// the sum in double-float on the FP32 pipe from the stored splits (products
+// exact up to the lo*lo term, two-sum accumulation; about 2^-47 relative per
+// term), the input state's term and the scaling in FP64.
+__device__ void combine_split(const LzArgs& A, const LzSmem& sm, double up, const double2* u0, double2* dst, int J,
+                              int hx, int hy, int hz) {
+    const int G1 = gridDim.x - 1;
+    const double2 c0 = sm.c0;
+    for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
+        const Tile T = tile_of(A, t, hx, hy, hz);
+        Walk wb;
+        wb.init(threadIdx.x, T.tx, T.ty);
+        for (int i0 = threadIdx.x; i0 < T.I; i0 += kCh * kLzBlock) {
+            size_t g[kCh];
+            float rh[kCh], rl[kCh], ih[kCh], il[kCh];
+#pragma unroll
+            for (int q = 0; q < kCh; ++q) {
+                int e;
+                const int i = i0 + q * kLzBlock;
+                g[q] = 0;
+                if (i < T.I) {
+                    g[q] = int_index(A, T, wb, hx, hy, hz, &e);
+                    wb.next(T.tx, T.ty);
+                    if (!LZ_OK(g[q], A.n, LZ_SITE_STATE)) g[q] = 0;
+                }
+                rh[q] = rl[q] = ih[q] = il[q] = 0.f;
+            }
+#pragma unroll 4
+            for (int r = 1; r < J; ++r) {
+                // u_r is basis row r - 1 < m + 2
+                if (!LZ_OK(r, kLzMaxM, LZ_SITE_Y) || !LZ_OK(r, A.m + 3, LZ_SITE_BASIS)) break;
+                const float4 c = sm.coefs[r];
+                const float4* u = reinterpret_cast<const float4*>(uvec(A, u0, r));
+#pragma unroll
+                for (int q = 0; q < kCh; ++q) {
+                    if (i0 + q * kLzBlock < T.I) {
+                        const float4 v = u[g[q]];
+                        df_madd(rh[q], rl[q], c.x, c.y, v.x, v.y);      // Re c Re u
+                        df_madd(rh[q], rl[q], -c.z, -c.w, v.z, v.w);    // - Im c Im u
+                        df_madd(ih[q], il[q], c.x, c.y, v.z, v.w);      // Re c Im u
+                        df_madd(ih[q], il[q], c.z, c.w, v.x, v.y);      // Im c Re u
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kCh; ++q) {
+                if (i0 + q * kLzBlock < T.I) {
+                    const double2 a = cmul(c0, u0[g[q]]);
+                    dst[g[q]] = make_double2(fma(up, (double)rh[q] + (double)rl[q], a.x),
+                                             fma(up, (double)ih[q] + (double)il[q], a.y));
+                }
+            }
         }
     }
 }
@@ -1003,11 +1105,14 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                     by += q == 0 ? 40.0 : (q == 1 ? 72.0 : 88.0);
                     fl += st_fl + (q == 0 ? 0.0 : (q == 1 ? 6.0 : 10.0));
                 }
-                // the final pass reads J vectors and writes one output per pole set
+                // the final pass reads J vectors and writes one output per pole set;
+                // its FP64 work: a complex multiply-add per vector, or (resident
+                // mode, the sum in double-float on the FP32 pipe) the input
+                // state's term and the scaling
                 const int Jn = A.mode == LZ_STEP ? max(J, 1) : J;
                 const int outs = A.mode == LZ_STEP ? 1 : A.K;
                 by += outs * 16.0 * (Jn + 1);
-                fl += outs * 8.0 * Jn;
+                fl += outs * (A.resident ? 12.0 : 8.0 * Jn);
                 if (A.bytes != nullptr) {
                     A.bytes[0] += (unsigned long long)(by * n);
                     A.bytes[1] += (unsigned long long)(fl * n);
@@ -1023,7 +1128,12 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                 for (int r = threadIdx.x; r < Jn; r += kLzBlock)
                     if (LZ_OK(r, kLzMaxM, LZ_SITE_Y) && LZ_OK(r, A.m, LZ_SITE_Y)) sm.coef[r] = __ldcg(A.coef + r);
                 __syncthreads();
-                combine(A, sm.coef, u0, out, Jn, hx, hy, hz);
+                if (A.resident) {
+                    const double up = split_coefficients(sm, Jn);
+                    combine_split(A, sm, up, u0, out, Jn, hx, hy, hz);
+                } else {
+                    combine(A, sm.coef, u0, out, Jn, hx, hy, hz);
+                }
             } else {
                 for (int k = 0; k < A.K; ++k) {
                     __syncthreads();
@@ -1031,7 +1141,12 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                         if (LZ_OK(r, kLzMaxM, LZ_SITE_Y) && LZ_OK(r, A.m, LZ_SITE_Y))
                             sm.coef[r] = __ldcg(A.coef + (size_t)k * A.m + r);
                     __syncthreads();
-                    combine(A, sm.coef, u0, A.out + (size_t)k * A.n, J, hx, hy, hz);
+                    if (A.resident) {
+                        const double up = split_coefficients(sm, J);
+                        combine_split(A, sm, up, u0, A.out + (size_t)k * A.n, J, hx, hy, hz);
+                    } else {
+                        combine(A, sm.coef, u0, A.out + (size_t)k * A.n, J, hx, hy, hz);
+                    }
                 }
             }
         }
