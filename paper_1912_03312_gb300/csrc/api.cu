@@ -598,7 +598,8 @@ int lz_alloc(rexi_plan* p) {
     if ((st = dalloc(p, &p->d_lz_stop, (size_t)std::max(1, p->n_sub)))) return st;
     if ((st = dalloc(p, &p->d_lz_cols, 2 * (size_t)std::max(1, p->n_sub)))) return st;
     if ((st = dalloc(p, &p->d_lz_shift, K))) return st;
-    p->lz_fold = p->a[0] != 0.0 ? p->a[0] : (p->a[1] != 0.0 ? p->a[1] : (p->a[2] != 0.0 ? p->a[2] : 1.0));
+    // f = |first nonzero stencil coefficient| (the coefficients are negative)
+    p->lz_fold = std::fabs(p->a[0] != 0.0 ? p->a[0] : (p->a[1] != 0.0 ? p->a[1] : (p->a[2] != 0.0 ? p->a[2] : 1.0)));
     if ((st = dalloc(p, &p->d_lz_diag, n))) return st;
     if ((st = upload_diag(p, 0, true))) return st;
 #ifdef REXI_DEBUG
@@ -641,6 +642,10 @@ int lz_launch(rexi_plan* p, int mode, const void* in, void* out, cudaStream_t st
         A.ratio[d] = p->a[d] / p->lz_fold;
     }
     A.fold = p->lz_fold;
+    // the unscaled recurrence grows a vector by at most ||B|| / f = tau W / f
+    // per step; below 2^16 its norms stay far inside the FP32 range of the
+    // compensated inner products between rescalings
+    A.unit_ok = p->tau * p->W / p->lz_fold <= 65536.0 ? 1 : 0;
     A.diag = p->d_lz_diag;
     A.shift = p->d_lz_shift;
     A.alpha = p->d_alpha;

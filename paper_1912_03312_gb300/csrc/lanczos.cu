@@ -4,33 +4,39 @@
 //
 // Krylov step j (one sweep; every tile CTA, own tile plus a one-point halo):
 //
-//   u_j  = rho_{j-1} (B u_{j-1} - a_{j-1} u_{j-1} - b_{j-1} u_{j-2})   (pointwise,
+//   u_j  = s_j (w'_{j-1} - alpha_{j-1} u_{j-1} - beta_{j-1} u_{j-2})   (pointwise,
 //          recomputed on the halo from the stored vectors so no second barrier
-//          is needed before the stencil)
-//   B u_j                                      (stencil from shared memory)
-//   partial sums of ||u_j||^2 and Re u_j^H B u_j
+//          is needed before the stencil; w' = B u / f, f = |first stencil
+//          coefficient|)
+//   w'_j = B u_j / f                          (stencil from shared memory)
+//   partial sums of ||u_j||^2 and Re u_j^H w'_j
 //
-// The inputs of the update (B u_{j-1}, u_{j-1}, u_{j-2} on the tile and its
+// The inputs of the update (w'_{j-1}, u_{j-1}, u_{j-2} on the tile and its
 // halo, the diagonal on the tile) are staged in shared memory by asynchronous
 // copies issued as soon as the barrier opens, while the CTA reduces the
 // partials; the inner products are compensated sums of FP32 hi/lo pieces
-// (about 1e-13 relative; the FP64 pipe stays free for the recurrence).  Every
-// CTA reduces the partials in FP64 in the same fixed order and derives the
-// same coefficients: rho_j = 1/||u_j||, a_j = (u_j^H B u_j) / ||u_j||^2 (the
-// Rayleigh quotient, real because B is real symmetric) and the Lanczos
-// coefficient of u_{j-1}, b_j = rho_{j-1} / rho_j^2, which makes the
-// tridiagonal matrix symmetric.  With q_j = rho_j u_j the recurrence reads
+// (about 1e-13 relative; the FP64 pipe stays free for the recurrence; sweep 0,
+// on the caller's state of any scale, sums in FP64).  Every CTA reduces the
+// partials in FP64 in the same fixed order and derives the same coefficients:
+// with n_j = ||u_j||^2, alpha_j = Re u_j^H w'_j / n_j (f alpha_j is the
+// Rayleigh quotient of B, real because B is real symmetric) and beta_j = n_j /
+// (s_j n_{j-1}), which makes the tridiagonal matrix symmetric.  With q_j = u_j
+// / ||u_j|| the recurrence reads
 //
-//   B q_j = (1/rho_{j+1}) q_{j+1} + a_j q_j + (1/rho_j) q_{j-1},
+//   B q_j = T(j+1, j) q_{j+1} + T(j, j) q_j + T(j, j-1) q_{j-1},
+//   T(j, j) = f alpha_j,  T(j+1, j) = f sqrt(n_{j+1} / n_j) / s_{j+1},
 //
 // exactly for the coefficients used (whatever the accuracy of the inner
 // products that chose them), so B Q_k = Q_{k+1} T_k holds to FP64 rounding
-// with T_k tridiagonal.  The shifted systems (B - s_k I) x = psi share Q_k
-// (Sec. 5 of the paper: the Krylov spaces of shifted systems coincide); pole k
-// minimises ||beta e_1 - (T_k - s_k [I; 0]) y|| by its own Givens rotations
-// (GMRES on the shared basis).  The columns are unit vectors but orthogonal
-// only locally, so the stop uses the bound ||r_k|| <= ||Q_{k+1}|| |g_{k+1}| <=
-// sqrt(k+1) |g_{k+1}| (times a 1e-4 margin for the computed norms).
+// with T_k tridiagonal.  The scale s_j is one (two fused multiply-adds per
+// component) while n stays within [2^-30, 2^30], else the power of two that
+// brings u_j back to unit scale.  The shifted systems (B - s_k I) x = psi share
+// Q_k (Sec. 5 of the paper: the Krylov spaces of shifted systems coincide);
+// pole k minimises ||beta e_1 - (T_k - s_k [I; 0]) y|| by its own Givens
+// rotations (GMRES on the shared basis).  The columns are unit vectors but
+// orthogonal only locally, so the stop uses the bound ||r_k|| <=
+// ||Q_{k+1}|| |g_{k+1}| <= sqrt(k+1) |g_{k+1}| (times a 1e-4 margin for the
+// computed norms).
 //
 // CTA 0 is the control CTA: it owns no tiles, runs the per-pole Givens
 // recurrences one step behind the sweeps, stops the iteration once every pole
@@ -103,14 +109,15 @@ __device__ __forceinline__ unsigned dyn_bytes() {
 #endif
 
 struct LzSmem {
-    double rho, a, b;        // coefficients of the next update (those of the last reduced sweep)
     double cw, ca, cb;       // the update as applied: u_j = cw w' - ca u_{j-1} - cb u_{j-2}
     int nring;               // resident mode: halo ring points of the tile
-    double n_last;           // ||u_{j-1}||^2 of the last reduced sweep
-    double n_prev;           // ||u_{j-2}||^2
     double n0;               // ||u_0||^2 of the substep
-    double hrho[3], ha[3], hn[3];   // (rho, a, n) of sweeps j-1, j-2, j-3
+    double s_last, inv_s_last;   // scale s of the last update (u_{j-1} = s_{j-1} (...)), a power of two
+    double hrho[3];          // rho = 1 / ||u|| of sweeps j-1, j-2, j-3
+    double ha[3], hsub[3];   // T(i, i) and T(i, i-1) for i = j-1, j-2, j-3
+    int unit_steps;          // updates of the substep with s = 1
     float red[kLzWarps][4];  // per-warp double-float sums (n_hi, n_lo, p_hi, p_lo)
+    double redd[kLzWarps][2];  // per-warp FP64 sums (sweep 0)
     int stop;
     int cexp;                // final pass, resident mode: largest biased exponent of the coefficients c_r, r >= 1
     double2 c0;              //                            coefficient of the input state
@@ -252,6 +259,39 @@ __device__ __forceinline__ float4 cta_df_sum(LzSmem& sm, float nh, float nl, flo
     return t;
 }
 
+// Sweep 0 (u_0 = the caller's state, of any scale): the sums in FP64, CTA sum
+// in a fixed order (thread 0 receives it), carried in the 16 bytes of a
+// partial slot.
+__device__ __forceinline__ double2 cta_f64_sum(LzSmem& sm, double n, double p) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+        p += __shfl_xor_sync(0xffffffffu, p, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) {
+        sm.redd[warp][0] = n;
+        sm.redd[warp][1] = p;
+    }
+    __syncthreads();
+    double2 t = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kLzWarps; ++w) {
+            t.x += sm.redd[w][0];
+            t.y += sm.redd[w][1];
+        }
+    return t;
+}
+__device__ __forceinline__ float4 pack_f64(double2 d) {
+    return make_float4(__int_as_float(__double2loint(d.x)), __int_as_float(__double2hiint(d.x)),
+                       __int_as_float(__double2loint(d.y)), __int_as_float(__double2hiint(d.y)));
+}
+__device__ __forceinline__ double2 unpack_f64(float4 f) {
+    return make_double2(__hiloint2double(__float_as_int(f.y), __float_as_int(f.x)),
+                        __hiloint2double(__float_as_int(f.w), __float_as_int(f.z)));
+}
+
 // Partials (||u||^2, Re u^H B u, each as a double-float pair) of sweep `par`
 // of the tile CTAs (1..G-1): every thread loads its share (one round of loads,
 // issued before the sweep's copies so they are not queued behind them) ...
@@ -271,7 +311,25 @@ __device__ __forceinline__ void load_partials(const LzArgs& A, int par, PartLoad
 // ... and the CTA sums them in double-float on the FP32 pipe (the FP64 pipe is
 // busy with the co-resident CTA's sweep), in the same fixed order in every
 // CTA; thread 0 receives the sums as FP64.
-__device__ __forceinline__ double2 reduce_partials(const LzArgs& A, LzSmem& sm, int par, const PartLoad& L) {
+__device__ __forceinline__ double2 reduce_partials(const LzArgs& A, LzSmem& sm, int par, const PartLoad& L, bool f64) {
+    if (f64) {
+        // sweep 0: FP64 sums in the slots
+        double n = 0.0, p = 0.0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const double2 d = unpack_f64(L.v[q]);
+            n += d.x;
+            p += d.y;
+        }
+        const float4* pp = A.part + (size_t)par * gridDim.x;
+        for (int c = 1 + threadIdx.x + 5 * kLzBlock; c < (int)gridDim.x; c += kLzBlock) {
+            if (!LZ_OK(par * gridDim.x + c, 2 * A.part_cap, LZ_SITE_PART)) continue;
+            const double2 d = unpack_f64(__ldcg(pp + c));
+            n += d.x;
+            p += d.y;
+        }
+        return cta_f64_sum(sm, n, p);
+    }
     float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -508,6 +566,7 @@ __device__ void setup_resident(const LzArgs& A, LzSmem& sm, const Stage& st, int
 // Phase A on one tile: v = rho (w - a u1 - b u2) on the extended box (in place
 // of W in streamed mode, into R[j mod 3] in resident mode); with ujw given
 // (streamed mode) the tile's own points are stored (they are u_j of the basis).
+template <bool kUnit>
 __device__ __forceinline__ void phase_a(const LzArgs& A, const Tile& T, const double2* W, const double2* U1,
                                         const double2* U2, double2* out, double2* ujw, int j, double cw, double ca,
                                         double cb, int hx, int hy, int hz) {
@@ -515,7 +574,8 @@ __device__ __forceinline__ void phase_a(const LzArgs& A, const Tile& T, const do
     wa.init(threadIdx.x, T.ex, T.ey);
     for (int e = threadIdx.x; e < T.E; e += kLzBlock, wa.next(T.ex, T.ey)) {
         const double2 w = W[e], u1 = U1[e];
-        double vx = fma(-ca, u1.x, cw * w.x), vy = fma(-ca, u1.y, cw * w.y);
+        // kUnit: cw = 1, two fused multiply-adds per component
+        double vx = fma(-ca, u1.x, kUnit ? w.x : cw * w.x), vy = fma(-ca, u1.y, kUnit ? w.y : cw * w.y);
         if (j >= 2) {
             const double2 u2 = U2[e];
             vx = fma(-cb, u2.x, vx);
@@ -536,16 +596,19 @@ __device__ __forceinline__ void phase_a(const LzArgs& A, const Tile& T, const do
 
 // Phase B on one tile: B u_j from S (the extended box of u_j), stored to the
 // global B u_j (and, resident mode, into Wown at the interior points); the
-// compensated partial sums of ||u_j||^2 and Re u_j^H B u_j accumulate.  With
+// compensated partial sums of ||u_j||^2 and Re u_j^H B u_j accumulate (kF64,
+// sweep 0: FP64 sums, since u_0 may lie outside the FP32 range).  With
 // ujs given (resident mode) u_j is stored to the basis as its hi/lo split
 // (the pieces the inner products use): (re_hi, re_lo, im_hi, im_lo).
+template <bool kF64>
 __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const double2* S, const double* D,
                                         double2* Wown, double2* wcur, float4* ujs, int hx, int hy, int hz,
-                                        float& nh, float& nl, float& ph, float& pl) {
-    // w' = B u / f with f = the coefficient of the first dimension the stencil
-    // reaches: that dimension's neighbour pair enters with weight one, the
-    // others with r_d = a_d / f, the diagonal (D = diag / f) with one fused
-    // multiply-add -- four FP64 operations per component in 2D
+                                        float& nh, float& nl, float& ph, float& pl, double& dn, double& dp) {
+    // w' = B u / f with f = |a_d| of the first dimension the stencil reaches
+    // (the a_d are negative): that dimension's neighbour pair enters with
+    // weight -1 (one addition of negated operands), the others with r_d = a_d
+    // / f, the diagonal (D = diag / f) with one fused multiply-add -- four FP64
+    // operations per component in 2D
     const double ry = A.ratio[1], rz = A.ratio[2];
     const int sy = T.ex, sz = T.ex * T.ey;
     Walk wb;
@@ -558,8 +621,8 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
         double wx = 0.0, wy = 0.0;
         if (hx) {
             const double2 l = LZ_AT(S, e - 1, T.E, LZ_SITE_STENCIL), rr = LZ_AT(S, e + 1, T.E, LZ_SITE_STENCIL);
-            wx = l.x + rr.x;
-            wy = l.y + rr.y;
+            wx = -l.x - rr.x;
+            wy = -l.y - rr.y;
         }
         if (hy) {
             const double2 l = LZ_AT(S, e - sy, T.E, LZ_SITE_STENCIL), rr = LZ_AT(S, e + sy, T.E, LZ_SITE_STENCIL);
@@ -567,8 +630,8 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
                 wx = fma(ry, l.x + rr.x, wx);
                 wy = fma(ry, l.y + rr.y, wy);
             } else {
-                wx = l.x + rr.x;
-                wy = l.y + rr.y;
+                wx = -l.x - rr.x;
+                wy = -l.y - rr.y;
             }
         }
         if (hz) {
@@ -577,8 +640,8 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
                 wx = fma(rz, l.x + rr.x, wx);
                 wy = fma(rz, l.y + rr.y, wy);
             } else {
-                wx = l.x + rr.x;
-                wy = l.y + rr.y;
+                wx = -l.x - rr.x;
+                wy = -l.y - rr.y;
             }
         }
         wx = fma(dg, c.x, wx);
@@ -586,6 +649,12 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
         const double2 wv = make_double2(wx, wy);
         if (LZ_OK(g, A.n, LZ_SITE_WT)) wcur[g] = wv;
         if (Wown) LZ_AT(Wown, e, T.E, LZ_SITE_STENCIL) = wv;
+        if (kF64) {
+            // sweep 0: u_0 at the caller's scale, the sums in FP64
+            dn = fma(c.x, c.x, fma(c.y, c.y, dn));
+            dp = fma(c.x, wx, fma(c.y, wy, dp));
+            continue;
+        }
         float cxh, cxl, cyh, cyl, wxh, wxl, wyh, wyl;
         split_f64(c.x, &cxh, &cxl);
         split_f64(c.y, &cyh, &cyl);
@@ -599,6 +668,14 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
     }
 }
 
+// Sweep 0's phase B, kept out of line (it runs once per substep).
+__device__ __noinline__ void phase_b_first(const LzArgs& A, const Tile& T, const double2* S, const double* D,
+                                           double2* Wown, double2* wcur, int hx, int hy, int hz, double& dn,
+                                           double& dp) {
+    float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f;
+    phase_b<true>(A, T, S, D, Wown, wcur, nullptr, hx, hy, hz, nh, nl, ph, pl, dn, dp);
+}
+
 // One Krylov sweep j over the tiles of this CTA (the first tile's copies were
 // issued by the caller); part receives the CTA's partial sums (thread 0).
 __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double2* u0, int j, int hx, int hy, int hz,
@@ -608,6 +685,7 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
     double2* wcur = A.wt + (size_t)(j & 1) * A.n;
     double2* ujw = j >= 1 ? uvec_w(A, j) : nullptr;
     float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f;
+    double dn = 0.0, dp = 0.0;
     if (A.resident) {
         if ((int)blockIdx.x - 1 < A.ntiles) {
             const Tile T = tile_of(A, blockIdx.x - 1, hx, hy, hz);
@@ -616,12 +694,19 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
             __syncthreads();
             if (LZ_OK(T.E, st.ext_max + 1, LZ_SITE_SMEM) && LZ_OK(T.I, st.int_max + 1, LZ_SITE_SMEM)) {
                 if (j >= 1) {
-                    phase_a(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, nullptr, j, cw, ca, cb, hx, hy,
-                            hz);
+                    if (cw == 1.0)
+                        phase_a<true>(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, nullptr, j, cw, ca, cb,
+                                      hx, hy, hz);
+                    else
+                        phase_a<false>(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, nullptr, j, cw, ca, cb,
+                                       hx, hy, hz);
                     __syncthreads();
                 }
                 float4* ujs = j >= 1 && LZ_OK(j - 1, A.m + 2, LZ_SITE_BASIS) ? reinterpret_cast<float4*>(ujw) : nullptr;
-                phase_b(A, T, S, st.D, st.W, wcur, ujs, hx, hy, hz, nh, nl, ph, pl);
+                if (j == 0)
+                    phase_b_first(A, T, S, st.D, st.W, wcur, hx, hy, hz, dn, dp);
+                else
+                    phase_b<false>(A, T, S, st.D, st.W, wcur, ujs, hx, hy, hz, nh, nl, ph, pl, dn, dp);
             }
         }
     } else {
@@ -632,54 +717,20 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
             __syncthreads();
             if (!LZ_OK(T.E, st.ext_max + 1, LZ_SITE_SMEM) || !LZ_OK(T.I, st.int_max + 1, LZ_SITE_SMEM)) break;
             if (j >= 1) {
-                phase_a(A, T, st.W, st.U1, st.U2, st.W, ujw, j, cw, ca, cb, hx, hy, hz);
+                if (cw == 1.0)
+                    phase_a<true>(A, T, st.W, st.U1, st.U2, st.W, ujw, j, cw, ca, cb, hx, hy, hz);
+                else
+                    phase_a<false>(A, T, st.W, st.U1, st.U2, st.W, ujw, j, cw, ca, cb, hx, hy, hz);
                 __syncthreads();
             }
-            phase_b(A, T, st.W, st.D, nullptr, wcur, nullptr, hx, hy, hz, nh, nl, ph, pl);
+            if (j == 0)
+                phase_b_first(A, T, st.W, st.D, nullptr, wcur, hx, hy, hz, dn, dp);
+            else
+                phase_b<false>(A, T, st.W, st.D, nullptr, wcur, nullptr, hx, hy, hz, nh, nl, ph, pl, dn, dp);
             __syncthreads();                      // shared memory is restaged for the next tile
         }
     }
-    *part = cta_df_sum(sm, nh, nl, ph, pl);
-}
-
-// Final pass over this CTA's tiles: dst = sum_{q < J} coef_q u_q in FP64.
-__device__ void combine(const LzArgs& A, const double2* coef, const double2* u0, double2* dst, int J, int hx, int hy,
-                        int hz) {
-    const int G1 = gridDim.x - 1;
-    for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
-        const Tile T = tile_of(A, t, hx, hy, hz);
-        Walk wb;
-        wb.init(threadIdx.x, T.tx, T.ty);
-        for (int i0 = threadIdx.x; i0 < T.I; i0 += kCh * kLzBlock) {
-            size_t g[kCh];
-            double2 acc[kCh];
-#pragma unroll
-            for (int q = 0; q < kCh; ++q) {
-                int e;
-                const int i = i0 + q * kLzBlock;
-                g[q] = 0;
-                if (i < T.I) {
-                    g[q] = int_index(A, T, wb, hx, hy, hz, &e);
-                    wb.next(T.tx, T.ty);
-                    if (!LZ_OK(g[q], A.n, LZ_SITE_STATE)) g[q] = 0;
-                }
-                acc[q] = make_double2(0.0, 0.0);
-            }
-#pragma unroll 4
-            for (int r = 0; r < J; ++r) {
-                // u_r is the input state (r = 0) or basis row r - 1 < m + 2
-                if (!LZ_OK(r, kLzMaxM, LZ_SITE_Y) || !LZ_OK(r, A.m + 3, LZ_SITE_BASIS)) break;
-                const double2 c = coef[r];
-                const double2* u = uvec(A, u0, r);
-#pragma unroll
-                for (int q = 0; q < kCh; ++q)
-                    if (i0 + q * kLzBlock < T.I) acc[q] = cfma(acc[q], c, u[g[q]]);
-            }
-#pragma unroll
-            for (int q = 0; q < kCh; ++q)
-                if (i0 + q * kLzBlock < T.I) dst[g[q]] = acc[q];
-        }
-    }
+    *part = j == 0 ? pack_f64(cta_f64_sum(sm, dn, dp)) : cta_df_sum(sm, nh, nl, ph, pl);
 }
 
 // Resident mode (the basis holds the hi/lo splits of u_1, u_2, ...): the
@@ -718,56 +769,120 @@ __device__ double split_coefficients(LzSmem& sm, int J) {
     return __hiloint2double((1023 - k) << 20, 0);
 }
 
-// Final pass, resident mode: dst = c_0 u_0 + 2^E sum_{1 <= r < J} (2^-E c_r) u_r;
-// the sum in double-float on the FP32 pipe from the stored splits (products
-// exact up to the lo*lo term, two-sum accumulation; about 2^-47 relative per
-// term), the input state's term and the scaling in FP64.
-__device__ void combine_split(const LzArgs& A, const LzSmem& sm, double up, const double2* u0, double2* dst, int J,
-                              int hx, int hy, int hz) {
+// cp.async.wait_group with a run-time count (at most n groups pending).
+__device__ __forceinline__ void cp_async_wait_upto(int n) {
+    switch (n) {
+        case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+        case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+        case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
+    }
+}
+
+constexpr int kMaxDepth = 8;    // basis vectors a thread prefetches in the final pass
+
+// Final pass over this CTA's tiles, dst = sum_{r < J} c_r u_r:
+//  kSplit (resident mode; the basis holds the hi/lo splits of u_1, u_2, ...):
+//    dst = c_0 u_0 + 2^E sum_{1 <= r < J} (2^-E c_r) u_r, the sum in
+//    double-float on the FP32 pipe (products exact up to the lo*lo term,
+//    two-sum accumulation; about 2^-47 relative per term), the input state's
+//    term and the scaling in FP64; sm.coefs holds the scaled splits;
+//  else: FP64 complex multiply-adds with sm.coef.
+// Every thread streams the basis entries of its own points through its own
+// slots of the (then unused) dynamic shared memory by cp.async, `depth`
+// vectors ahead, so depth * kCh loads per thread are in flight and no barrier
+// is needed between a copy and its use (depth 0: plain loads).
+template <bool kSplit>
+__device__ void final_pass(const LzArgs& A, const LzSmem& sm, double up, const double2* u0, double2* dst, int J,
+                           int hx, int hy, int hz, float4* slots, int depth) {
     const int G1 = gridDim.x - 1;
-    const double2 c0 = sm.c0;
+    const int rb = kSplit ? 1 : 0;                 // first vector through the slots
     for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
         const Tile T = tile_of(A, t, hx, hy, hz);
         Walk wb;
         wb.init(threadIdx.x, T.tx, T.ty);
         for (int i0 = threadIdx.x; i0 < T.I; i0 += kCh * kLzBlock) {
             size_t g[kCh];
-            float rh[kCh], rl[kCh], ih[kCh], il[kCh];
+            bool on[kCh];
 #pragma unroll
             for (int q = 0; q < kCh; ++q) {
                 int e;
-                const int i = i0 + q * kLzBlock;
+                on[q] = i0 + q * kLzBlock < T.I;
                 g[q] = 0;
-                if (i < T.I) {
+                if (on[q]) {
                     g[q] = int_index(A, T, wb, hx, hy, hz, &e);
                     wb.next(T.tx, T.ty);
-                    if (!LZ_OK(g[q], A.n, LZ_SITE_STATE)) g[q] = 0;
+                    if (!LZ_OK(g[q], A.n, LZ_SITE_STATE)) on[q] = false;
                 }
-                rh[q] = rl[q] = ih[q] = il[q] = 0.f;
             }
-#pragma unroll 4
-            for (int r = 1; r < J; ++r) {
-                // u_r is basis row r - 1 < m + 2
-                if (!LZ_OK(r, kLzMaxM, LZ_SITE_Y) || !LZ_OK(r, A.m + 3, LZ_SITE_BASIS)) break;
-                const float4 c = sm.coefs[r];
-                const float4* u = reinterpret_cast<const float4*>(uvec(A, u0, r));
+            // copies of vector r into slot b (one commit group, possibly empty)
+            auto issue = [&](int r, int b) {
+                if (depth > 0 && r < J && LZ_OK(r, A.m + 3, LZ_SITE_BASIS)) {
+                    const double2* u = uvec(A, u0, r);
 #pragma unroll
-                for (int q = 0; q < kCh; ++q) {
-                    if (i0 + q * kLzBlock < T.I) {
-                        const float4 v = u[g[q]];
-                        df_madd(rh[q], rl[q], c.x, c.y, v.x, v.y);      // Re c Re u
-                        df_madd(rh[q], rl[q], -c.z, -c.w, v.z, v.w);    // - Im c Im u
-                        df_madd(ih[q], il[q], c.x, c.y, v.z, v.w);      // Re c Im u
-                        df_madd(ih[q], il[q], c.z, c.w, v.x, v.y);      // Im c Re u
+                    for (int q = 0; q < kCh; ++q)
+                        if (on[q]) cp_async16(slots + ((size_t)(b * kCh + q) * kLzBlock + threadIdx.x), u + g[q]);
+                }
+                cp_async_commit();
+            };
+            for (int b = 0; b + 1 < depth; ++b) issue(rb + b, b);
+            float rh[kCh], rl[kCh], ih[kCh], il[kCh];
+            double2 acc[kCh];
+#pragma unroll
+            for (int q = 0; q < kCh; ++q) {
+                rh[q] = rl[q] = ih[q] = il[q] = 0.f;
+                acc[q] = make_double2(0.0, 0.0);
+            }
+            for (int r = rb; r < J; ++r) {
+                if (!LZ_OK(r, kLzMaxM, LZ_SITE_Y) || !LZ_OK(r, A.m + 3, LZ_SITE_BASIS)) break;
+                const int k = r - rb;
+                int b = 0;
+                if (depth > 0) {
+                    issue(r + depth - 1, (k + depth - 1) % depth);
+                    cp_async_wait_upto(depth - 1);
+                    b = k % depth;
+                }
+                const double2* u = uvec(A, u0, r);
+                if (kSplit) {
+                    const float4 c = sm.coefs[r];
+#pragma unroll
+                    for (int q = 0; q < kCh; ++q) {
+                        if (on[q]) {
+                            const float4 v = depth > 0 ? slots[(size_t)(b * kCh + q) * kLzBlock + threadIdx.x]
+                                                       : reinterpret_cast<const float4*>(u)[g[q]];
+                            df_madd(rh[q], rl[q], c.x, c.y, v.x, v.y);      // Re c Re u
+                            df_madd(rh[q], rl[q], -c.z, -c.w, v.z, v.w);    // - Im c Im u
+                            df_madd(ih[q], il[q], c.x, c.y, v.z, v.w);      // Re c Im u
+                            df_madd(ih[q], il[q], c.z, c.w, v.x, v.y);      // Im c Re u
+                        }
+                    }
+                } else {
+                    const double2 c = sm.coef[r];
+#pragma unroll
+                    for (int q = 0; q < kCh; ++q) {
+                        if (on[q]) {
+                            const double2 v = depth > 0 ? reinterpret_cast<const double2*>(
+                                                              slots)[(size_t)(b * kCh + q) * kLzBlock + threadIdx.x]
+                                                        : u[g[q]];
+                            acc[q] = cfma(acc[q], c, v);
+                        }
                     }
                 }
             }
+            cp_async_wait_all();
 #pragma unroll
             for (int q = 0; q < kCh; ++q) {
-                if (i0 + q * kLzBlock < T.I) {
-                    const double2 a = cmul(c0, u0[g[q]]);
+                if (!on[q]) continue;
+                if (kSplit) {
+                    const double2 a = cmul(sm.c0, u0[g[q]]);
                     dst[g[q]] = make_double2(fma(up, (double)rh[q] + (double)rl[q], a.x),
                                              fma(up, (double)ih[q] + (double)il[q], a.y));
+                } else {
+                    dst[g[q]] = acc[q];
                 }
             }
         }
@@ -787,18 +902,29 @@ struct PoleState {
     double bound;            // relative residual bound at the stop
 };
 
-__device__ __forceinline__ void put_row(const LzArgs& A, int r, int k, double2 g, double2 inv, double2 r1, double2 r2) {
+// Row r of pole k's R, scaled by 1 / R(r, r), and its right-hand side entry:
+// to the global rows and, for r < srows_cap, to the control CTA's shared
+// memory (where the back substitution reads it without staging).
+__device__ __forceinline__ void put_row(const LzArgs& A, int r, int k, double2 g, double2 inv, double2 r1, double2 r2,
+                                        double2* srows, int srows_cap) {
     if (!LZ_OK(r, A.m, LZ_SITE_ROWS) || !LZ_OK(k, A.K, LZ_SITE_ROWS)) return;
+    const double2 a = cmul(g, inv), b = cmul(r1, inv), c = cmul(r2, inv);
     double2* p = A.rows + ((size_t)r * A.K + k) * 3;
-    p[0] = cmul(g, inv);
-    p[1] = cmul(r1, inv);
-    p[2] = cmul(r2, inv);
+    p[0] = a;
+    p[1] = b;
+    p[2] = c;
+    if (r < srows_cap) {
+        double2* q = srows + ((size_t)r * A.K + k) * 3;
+        q[0] = a;
+        q[1] = b;
+        q[2] = c;
+    }
 }
 
 // Givens step of pole k on column c of T - s_k [I; 0]: entries up (row c-1),
 // a_c - s_k (row c), lo (row c+1).  Returns true when the pole stops here.
 __device__ bool pole_column(const LzArgs& A, PoleState& P, int k, int c, double up, double ac, double lo,
-                            double tol_abs2, double bnorm) {
+                            double tol_abs2, double2* srows, int srows_cap) {
     const double2 dg = make_double2(ac - P.shift.x, -P.shift.y);
     double2 xm1 = make_double2(up, 0.0);                   // row c-1 entry
     double2 r0 = make_double2(0.0, 0.0);                   // R(c-2, c)
@@ -818,7 +944,7 @@ __device__ bool pole_column(const LzArgs& A, PoleState& P, int k, int c, double 
     givens(xc, lo, &c0, &s0, &rcc, &inv);
     const double2 gc = csc(P.g, c0);
     const double2 gn = cmul(make_double2(-s0.x, s0.y), P.g);   // -conj(s0) g
-    if (c >= 2) put_row(A, c - 2, k, P.g2, P.inv2, P.r12, r0);
+    if (c >= 2) put_row(A, c - 2, k, P.g2, P.inv2, P.r12, r0, srows, srows_cap);
     // shift the pending rows and rotations
     P.g2 = P.g1;
     P.inv2 = P.inv1;
@@ -834,23 +960,26 @@ __device__ bool pole_column(const LzArgs& A, PoleState& P, int k, int c, double 
     if (gg * (double)(c + 2) <= tol_abs2) {
         // stop with c + 1 columns: rows c-1 and c complete with zeros
         const double2 z = make_double2(0.0, 0.0);
-        if (c >= 1) put_row(A, c - 1, k, P.g2, P.inv2, P.r12, z);
-        put_row(A, c, k, P.g1, P.inv1, z, z);
+        if (c >= 1) put_row(A, c - 1, k, P.g2, P.inv2, P.r12, z, srows, srows_cap);
+        put_row(A, c, k, P.g1, P.inv1, z, z, srows, srows_cap);
         P.kk = c + 1;
         P.done = 1;
-        P.bound = bnorm > 0.0 ? sqrt(gg * (double)(c + 2)) / bnorm : 0.0;
+        P.bound = sqrt(gg * (double)(c + 2));
         return true;
     }
     return false;
 }
 
 // Control CTA after the sweeps of a substep stopped at J columns: y_k =
-// R_k^{-1} g_k for every pole (rows staged through shared memory in chunks),
-// then the coefficients of the final pass.
+// R_k^{-1} g_k for every pole, then the coefficients of the final pass.  With
+// J <= stage_rows the rows are already in shared memory (written there as they
+// were formed) and y_k replaces each row's first entry; otherwise the rows are
+// staged from global memory in chunks and y_k goes through global memory.
 __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int stage_rows, PoleState& P, int J,
-                               int s) {
+                               int s, double bnorm) {
     const int K = A.K;
     const int k = threadIdx.x;
+    const bool inplace = J <= stage_rows;
     double2 y1 = make_double2(0.0, 0.0), y2 = make_double2(0.0, 0.0);
     for (int top = J; top > 0; top -= stage_rows) {
         const int lo = max(0, top - stage_rows);
@@ -859,22 +988,27 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
             !LZ_OK((long long)top * K * 3 - 1, (long long)A.m * K * 3, LZ_SITE_ROWS))
             cnt = 0;
         __syncthreads();
+        if (!inplace) {
 #pragma unroll 8
-        for (int q = threadIdx.x; q < cnt; q += kLzBlock) stage[q] = __ldcg(A.rows + (size_t)lo * K * 3 + q);
-        __syncthreads();
+            for (int q = threadIdx.x; q < cnt; q += kLzBlock) stage[q] = __ldcg(A.rows + (size_t)lo * K * 3 + q);
+            __syncthreads();
+        }
         if (k < K) {
             for (int r = top - 1; r >= lo; --r) {
                 double2 y = make_double2(0.0, 0.0);
+                double2* q = stage + ((size_t)(r - lo) * K + k) * 3;
                 if (r < P.kk && cnt > 0) {
-                    const double2* q = stage + ((size_t)(r - lo) * K + k) * 3;
                     const double2 mr1 = make_double2(-q[1].x, -q[1].y), mr2 = make_double2(-q[2].x, -q[2].y);
                     y = cfma(cfma(q[0], mr2, y2), mr1, y1);
                 }
                 if (A.mode == LZ_STEP) {
-                    if (LZ_OK((long long)r * K + k, (long long)A.m * K, LZ_SITE_Y)) A.ybuf[(size_t)r * K + k] = y;
+                    if (inplace)
+                        q[0] = y;
+                    else if (LZ_OK((long long)r * K + k, (long long)A.m * K, LZ_SITE_Y))
+                        A.ybuf[(size_t)r * K + k] = y;
                 } else if (LZ_OK((long long)k * A.m + r, (long long)A.m * K, LZ_SITE_Y) &&
                            LZ_OK(r, A.m + 2, LZ_SITE_Y)) {
-                    A.coef[(size_t)k * A.m + r] = csc(y, A.rho[r]);
+                    A.coef[(size_t)k * A.m + r] = csc(y, A.rho[r] * bnorm);
                 }
                 y2 = y1;
                 y1 = y;
@@ -883,7 +1017,7 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
     }
     __syncthreads();
     if (A.mode == LZ_STEP) {
-        // coef_r = rho_r sum_k alpha_k y_{k,r} (+ alpha_0 at r = 0): eight
+        // coef_r = ||psi|| rho_r sum_k alpha_k y_{k,r} (+ alpha_0 at r = 0): eight
         // threads per row, a fixed summation order
         const int q = threadIdx.x & 7;
         const int Jn = max(J, 1);
@@ -892,7 +1026,9 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
             double2 acc = make_double2(0.0, 0.0);
             if (r < J && LZ_OK((long long)r * K + K - 1, (long long)A.m * K, LZ_SITE_Y)) {
 #pragma unroll 4
-                for (int kq = q; kq < K; kq += 8) acc = cfma(acc, __ldg(A.alpha + kq), A.ybuf[(size_t)r * K + kq]);
+                for (int kq = q; kq < K; kq += 8)
+                    acc = cfma(acc, __ldg(A.alpha + kq),
+                               inplace ? stage[((size_t)r * K + kq) * 3] : A.ybuf[(size_t)r * K + kq]);
             }
 #pragma unroll
             for (int o = 4; o > 0; o >>= 1) {
@@ -900,7 +1036,7 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
                 acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
             }
             if (q == 0 && r < Jn && LZ_OK(r, A.m, LZ_SITE_Y) && LZ_OK(r, A.m + 2, LZ_SITE_Y)) {
-                double2 c = r < J ? csc(acc, A.rho[r]) : make_double2(0.0, 0.0);
+                double2 c = r < J ? csc(acc, A.rho[r] * bnorm) : make_double2(0.0, 0.0);
                 if (r == 0) {
                     c.x += A.alpha0.x;
                     c.y += A.alpha0.y;
@@ -941,6 +1077,10 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
     st.ringE = (int*)(st.D + int_max);
     st.ringG = st.ringE + (ext_max - int_max);
     const int stage_rows = A.stage_rows;
+    // final pass: the staging area (dead after the sweeps; the diagonal and the
+    // ring list behind it stay) as prefetch slots of kCh * kLzBlock entries
+    float4* slots = reinterpret_cast<float4*>(dyn);
+    const int depth = min(kMaxDepth, (A.resident ? 4 : 3) * ext_max / (kCh * kLzBlock));
 #ifdef REXI_DEBUG
     {
         // the layout above (tile CTAs) and the row staging (control CTA) fit the
@@ -976,11 +1116,13 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
             P.bound = 0.0;
         }
         if (threadIdx.x == 0) {
-            sm.n_last = sm.n_prev = sm.n0 = 0.0;
-            for (int q = 0; q < 3; ++q) sm.hrho[q] = sm.ha[q] = sm.hn[q] = 0.0;
+            sm.n0 = 0.0;
+            sm.s_last = sm.inv_s_last = 1.0;
+            for (int q = 0; q < 3; ++q) sm.hrho[q] = sm.ha[q] = sm.hsub[q] = 0.0;
         }
         __syncthreads();
         double tol_abs2 = 0.0, bnorm = 0.0;
+        double upd_fl = 0.0;                           // FP64 flops per point of the updates (control CTA)
         int J = -1, sweeps = 0;
         for (int j = 0;; ++j) {
             // as the barrier opens: the partials and the stop word, then the
@@ -999,33 +1141,46 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
             }
             if (j >= 1) {
                 // coefficients of sweep j-1, the same in every CTA
-                const double2 t = reduce_partials(A, sm, (j - 1) & 1, L);
+                const double2 t = reduce_partials(A, sm, (j - 1) & 1, L, j == 1);
                 if (threadIdx.x == 0) {
-                    // rho = 1/||u_{j-1}||, a = p rho^2 (Rayleigh quotient), b = rho_{j-2} / rho_{j-1}^2
-                    // = rho_{j-2} n (symmetric tridiagonal): one reciprocal square root
-                    const double n = t.x, p = t.y * A.fold;       // Re u^H B u = f Re u^H w'
-
-                    const double rho = n > 0.0 ? rsqrt(n) : 0.0;
-                    const double a = p * rho * rho;
-                    const double b = j - 1 >= 1 ? sm.hrho[0] * n : 0.0;
-                    sm.n_prev = sm.n_last;
-                    sm.n_last = n;
+                    // sweep j-1 gave n = ||u_{j-1}||^2 and p = Re u_{j-1}^H w'
+                    // (w' = B u_{j-1} / f).  The update u_j = s_j (w' - alpha
+                    // u_{j-1} - beta u_{j-2}) with alpha = p / n and beta = n /
+                    // (s_{j-1} n_{j-2}) makes T symmetric: T(j-1, j-1) = f alpha
+                    // (the Rayleigh quotient), T(j-1, j-2) = f sqrt(n / n_{j-2}) /
+                    // s_{j-1}.  s_j = 1 (two fused multiply-adds per component)
+                    // while n stays in [2^-30, 2^30], else the power of two that
+                    // brings u_j back to unit scale: one reciprocal square root, no
+                    // division
+                    const double n = t.x;
+                    const double rho = n > 0.0 ? rsqrt(n) : 0.0;        // q_{j-1} = rho u_{j-1}
+                    const double alpha = t.y * rho * rho;
+                    const double rho2 = sm.hrho[0];                      // rho_{j-2}
+                    const double inv_s = sm.inv_s_last;
+                    const double beta = j >= 2 ? n * rho2 * rho2 * inv_s : 0.0;
+                    const double sub = j >= 2 ? A.fold * n * rho * rho2 * inv_s : 0.0;
+                    double sj = 1.0, inv_sj = 1.0;
+                    if (!A.unit_ok || !(n >= 0x1p-30 && n <= 0x1p30)) {
+                        const int be = (__double2hiint(n) >> 20) & 0x7FF;
+                        const int k = -((be - 1023) >> 1);               // s^2 n in [1/2, 4) for normal n
+                        sj = __hiloint2double((1023 + k) << 20, 0);
+                        inv_sj = __hiloint2double((1023 - k) << 20, 0);
+                    }
                     if (j == 1) sm.n0 = n;
-                    sm.rho = rho;
-                    sm.a = a;
-                    sm.b = b;
-                    sm.cw = rho * A.fold;
-                    sm.ca = rho * a;
-                    sm.cb = rho * b;
+                    sm.cw = sj;
+                    sm.ca = sj * alpha;
+                    sm.cb = sj * beta;
+                    sm.s_last = sj;
+                    sm.inv_s_last = inv_sj;
                     sm.hrho[2] = sm.hrho[1];
                     sm.hrho[1] = sm.hrho[0];
                     sm.hrho[0] = rho;
                     sm.ha[2] = sm.ha[1];
                     sm.ha[1] = sm.ha[0];
-                    sm.ha[0] = a;
-                    sm.hn[2] = sm.hn[1];
-                    sm.hn[1] = sm.hn[0];
-                    sm.hn[0] = n;
+                    sm.ha[0] = A.fold * alpha;
+                    sm.hsub[2] = sm.hsub[1];
+                    sm.hsub[1] = sm.hsub[0];
+                    sm.hsub[0] = sub;
                     sm.stop = stop_word;
                     if (control && LZ_OK(j - 1, A.m + 2, LZ_SITE_Y)) A.rho[j - 1] = rho;
                 }
@@ -1041,6 +1196,10 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                     if (threadIdx.x == 0) atomicExch(A.err, kErrInternal);
                     return;
                 }
+                // sweep j's update: a multiply and two (sweep 1: one) fused
+                // multiply-adds per component, without the multiply when s = 1
+                if (control && threadIdx.x == 0)
+                    upd_fl += (sm.cw == 1.0 ? 0.0 : 2.0) + (j == 1 ? 4.0 : 8.0);
             }
             if (!control) {
                 float4 part;
@@ -1052,33 +1211,35 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                 // complete once the norm of u_{j-1} (its subdiagonal) is known
                 if (j == 1) {
                     const double n0 = sm.n0;
+                    // the poles solve for psi / ||psi|| (right-hand side e_1, for
+                    // any scale of psi); ||psi|| enters the final coefficients
                     bnorm = sqrt(n0);
-                    const double ta = A.tol * bnorm / 1.0001;
+                    const double ta = A.tol / 1.0001;
                     tol_abs2 = ta * ta;
-                    if (threadIdx.x < A.K) P.g = make_double2(n0 * sm.hrho[0], 0.0);   // 1/rho_0
-                    if (threadIdx.x == 0 && !(n0 > 0.0 && n0 <= 3.0e38)) {
+                    if (threadIdx.x < A.K) P.g = make_double2(1.0, 0.0);
+                    if (threadIdx.x == 0 && !(n0 > 0.0 && n0 <= 1.0e300)) {
                         // a zero state needs no columns; a non-finite one fails every pole
                         __stcg(A.stop + s, 0);
                     }
                     if (threadIdx.x < A.K && !(n0 > 0.0)) P.done = n0 == 0.0 ? 1 : 2;
-                    if (threadIdx.x < A.K && !(n0 <= 3.0e38)) P.done = 2;
+                    if (threadIdx.x < A.K && !(n0 <= 1.0e300)) P.done = 2;
                 } else {
                     const int c = j - 2;
-                    // T[c-1, c] = 1 / rho_c = n_c rho_c and T[c+1, c] = 1 / rho_{c+1}
-                    const double up = c >= 1 ? sm.hn[1] * sm.hrho[1] : 0.0;
-                    const double lo = sm.hn[0] * sm.hrho[0];
+                    // T[c-1, c] = T[c, c-1] and T[c+1, c], from the last two reductions
+                    const double up = c >= 1 ? sm.hsub[1] : 0.0;
+                    const double lo = sm.hsub[0];
                     const double ac = sm.ha[1];
                     int active = 0;
                     if (threadIdx.x < A.K && P.done == 0) {
-                        pole_column(A, P, threadIdx.x, c, up, ac, lo, tol_abs2, bnorm);
+                        pole_column(A, P, threadIdx.x, c, up, ac, lo, tol_abs2, dyn, stage_rows);
                         if (P.done == 0 && c + 1 >= A.m) {
                             P.done = 2;
                             P.kk = c + 1;
                             const double gg = P.g.x * P.g.x + P.g.y * P.g.y;
-                            P.bound = bnorm > 0.0 ? sqrt(gg * (double)(c + 2)) / bnorm : 0.0;
+                            P.bound = sqrt(gg * (double)(c + 2));
                             const double2 z = make_double2(0.0, 0.0);
-                            if (c >= 1) put_row(A, c - 1, threadIdx.x, P.g2, P.inv2, P.r12, z);
-                            put_row(A, c, threadIdx.x, P.g1, P.inv1, z, z);
+                            if (c >= 1) put_row(A, c - 1, threadIdx.x, P.g2, P.inv2, P.r12, z, dyn, stage_rows);
+                            put_row(A, c, threadIdx.x, P.g1, P.inv1, z, z, dyn, stage_rows);
                         }
                         active = P.done == 0;
                     }
@@ -1090,50 +1251,44 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
             trace_mark(A, TR_LZ_SWEEP, &tcount);
         }
         // y_k and the coefficients of the final pass
-        if (control) {
-            if (threadIdx.x == 0) {
-                if (LZ_OK(A.nsub + s, 2 * A.nsub, LZ_SITE_Y)) A.cols[A.nsub + s] = sweeps;
-                // the work the specified recurrence moves and computes (halo
-                // re-reads not counted): sweep 0 reads u_0 and the diagonal and
-                // writes B u_0; sweep 1 also reads B u_0 and writes u_1; later
-                // sweeps read B u_{j-1}, u_{j-1}, u_{j-2} and write u_j, B u_j
-                const double n = (double)A.n;
-                const int d = hx + hy + hz;
-                const double st_fl = 6.0 * d;
-                double by = 0.0, fl = 0.0;
-                for (int q = 0; q < sweeps; ++q) {
-                    by += q == 0 ? 40.0 : (q == 1 ? 72.0 : 88.0);
-                    fl += st_fl + (q == 0 ? 0.0 : (q == 1 ? 6.0 : 10.0));
-                }
-                // the final pass reads J vectors and writes one output per pole set;
-                // its FP64 work: a complex multiply-add per vector, or (resident
-                // mode, the sum in double-float on the FP32 pipe) the input
-                // state's term and the scaling
-                const int Jn = A.mode == LZ_STEP ? max(J, 1) : J;
-                const int outs = A.mode == LZ_STEP ? 1 : A.K;
-                by += outs * 16.0 * (Jn + 1);
-                fl += outs * (A.resident ? 12.0 : 8.0 * Jn);
-                if (A.bytes != nullptr) {
-                    A.bytes[0] += (unsigned long long)(by * n);
-                    A.bytes[1] += (unsigned long long)(fl * n);
-                }
-            }
-            control_finish(A, sm, dyn, stage_rows, P, J, s);
-        }
+        if (control) control_finish(A, sm, dyn, stage_rows, P, J, s, bnorm);
         if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
         trace_mark(A, TR_LZ_SOLVE, &tcount);
+        if (control && threadIdx.x == 0) {
+            // (the control CTA is idle during the final pass)
+            if (LZ_OK(A.nsub + s, 2 * A.nsub, LZ_SITE_Y)) A.cols[A.nsub + s] = sweeps;
+            // the work the specified recurrence moves and computes (halo
+            // re-reads not counted): sweep 0 reads u_0 and the diagonal and
+            // writes B u_0; sweep 1 also reads B u_0 and writes u_1; later
+            // sweeps read B u_{j-1}, u_{j-1}, u_{j-2} and write u_j, B u_j
+            const double n = (double)A.n;
+            const int d = hx + hy + hz;
+            const double later = (double)max(sweeps - 2, 0);
+            double by = (sweeps >= 1 ? 40.0 : 0.0) + (sweeps >= 2 ? 72.0 : 0.0) + 88.0 * later;
+            double fl = 6.0 * d * sweeps + upd_fl;
+            // the final pass reads J vectors and writes one output per pole set;
+            // its FP64 work: a complex multiply-add per vector, or (resident
+            // mode, the sum in double-float on the FP32 pipe) the input
+            // state's term and the scaling
+            const int Jn = A.mode == LZ_STEP ? max(J, 1) : J;
+            const int outs = A.mode == LZ_STEP ? 1 : A.K;
+            by += outs * 16.0 * (Jn + 1);
+            fl += outs * (A.resident ? 12.0 : 8.0 * Jn);
+            if (A.bytes != nullptr) {
+                A.bytes[0] += (unsigned long long)(by * n);
+                A.bytes[1] += (unsigned long long)(fl * n);
+            }
+        }
         if (!control) {
             if (A.mode == LZ_STEP) {
                 const int Jn = max(J, 1);
                 for (int r = threadIdx.x; r < Jn; r += kLzBlock)
                     if (LZ_OK(r, kLzMaxM, LZ_SITE_Y) && LZ_OK(r, A.m, LZ_SITE_Y)) sm.coef[r] = __ldcg(A.coef + r);
                 __syncthreads();
-                if (A.resident) {
-                    const double up = split_coefficients(sm, Jn);
-                    combine_split(A, sm, up, u0, out, Jn, hx, hy, hz);
-                } else {
-                    combine(A, sm.coef, u0, out, Jn, hx, hy, hz);
-                }
+                if (A.resident)
+                    final_pass<true>(A, sm, split_coefficients(sm, Jn), u0, out, Jn, hx, hy, hz, slots, depth);
+                else
+                    final_pass<false>(A, sm, 1.0, u0, out, Jn, hx, hy, hz, slots, depth);
             } else {
                 for (int k = 0; k < A.K; ++k) {
                     __syncthreads();
@@ -1141,12 +1296,11 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                         if (LZ_OK(r, kLzMaxM, LZ_SITE_Y) && LZ_OK(r, A.m, LZ_SITE_Y))
                             sm.coef[r] = __ldcg(A.coef + (size_t)k * A.m + r);
                     __syncthreads();
-                    if (A.resident) {
-                        const double up = split_coefficients(sm, J);
-                        combine_split(A, sm, up, u0, A.out + (size_t)k * A.n, J, hx, hy, hz);
-                    } else {
-                        combine(A, sm.coef, u0, A.out + (size_t)k * A.n, J, hx, hy, hz);
-                    }
+                    double2* xk = A.out + (size_t)k * A.n;
+                    if (A.resident)
+                        final_pass<true>(A, sm, split_coefficients(sm, J), u0, xk, J, hx, hy, hz, slots, depth);
+                    else
+                        final_pass<false>(A, sm, 1.0, u0, xk, J, hx, hy, hz, slots, depth);
                 }
             }
         }

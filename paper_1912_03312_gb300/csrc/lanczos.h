@@ -49,8 +49,9 @@ struct LzArgs {
     int nsub;                  // substeps (1 in LZ_SOLVE)
     int m;                     // largest Krylov dimension (columns) per substep
     double a[3];               // stencil coefficients -tau hbar^2/(2 m h_d^2); 0 for extent-1 dimensions
-    double fold;               // f: the first nonzero a_d (1 if none); the kernel stores w' = B u / f
-    double ratio[3];           // a_d / f
+    double fold;               // f = |a_d| of the first nonzero a_d (1 if none); the kernel stores w' = B u / f
+    double ratio[3];           // a_d / f (-1 for that first dimension)
+    int unit_ok;               // 1: the recurrence may run unscaled (||B|| / f <= 2^16)
     const double* diag;        // [n] (tau (V - c) - 2 sum_d a_d) / f
     const double2* shift;      // [K] centred shifts s_k = z_k - tau c
     const double2* alpha;      // [K] weights

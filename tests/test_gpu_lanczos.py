@@ -9,7 +9,8 @@ sum as one pass over the basis.  Cases: 1D/2D/3D grids, degenerate dimensions
 (length 1 and 2), tiles that wrap on both sides, ragged tiles, K = 8/16/32,
 several substeps; per-pole solutions to 1e-10; steps to max(1e-10, 2 A tol)
 with tol chosen so that bound stays below the metric's 1e-6; plane wave and
-zero state at 512^2; NaN input, too few iterations, the bounded waits, graph
+zero state at 512^2; states far outside the FP32 range (scale invariance);
+NaN input, too few iterations, the bounded waits, graph
 capture, reproducibility, in place, host buffers, the adjoint on the item
 engine, and tile settings.
 """
@@ -91,6 +92,25 @@ def test_lanczos_solve_poles_match_oracle(n, box, K, R1, dt):
         log_parity("lanczos_pole[%s,K%d,%d]" % ("x".join(map(str, n)), K, k), err, 1e-10)
         assert err < 1e-10, (k, err)
         assert st["resid"][k] <= 1e-13
+
+
+@pytest.mark.parametrize("scale_exp", [-500, -200, 200, 450])
+def test_lanczos_step_is_scale_invariant(scale_exp):
+    # psi of any finite norm: sweep 0 forms its inner products in FP64 (the
+    # later vectors are normalised), so 2^e psi steps to 2^e times the step
+    # of psi, far outside the FP32 range of the compensated products
+    g, V, psi = wl.random_problem(95, (130, 101), box=8.0)
+    K, R1, dt = 16, 24.0, 0.5
+    lp = lz_plan(g, V, dt, K, R1, tol=1e-13)
+    ref, st = lp.step(to_dev(psi), stats=True)
+    assert st["status"] == 0
+    s = 2.0 ** scale_exp
+    out, st2 = lp.step(to_dev(psi * s), stats=True)
+    # the same Krylov columns up to the rounding of the rescaled vectors
+    assert st2["status"] == 0 and abs(st2["total_iters"] - st["total_iters"]) <= K
+    err = relerr(out.cpu().numpy() / s, ref.cpu().numpy())
+    log_parity("lanczos_scale[2^%d]" % scale_exp, err, 1e-13)
+    assert err < 1e-13, err
 
 
 def test_lanczos_tiles_and_grid_settings_agree():
