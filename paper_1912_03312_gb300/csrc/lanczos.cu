@@ -109,22 +109,24 @@ __device__ __forceinline__ unsigned dyn_bytes() {
 #endif
 
 struct LzSmem {
-    double cw, ca, cb;       // the update as applied: u_j = cw w' - ca u_{j-1} - cb u_{j-2}
-    int nring;               // resident mode: halo ring points of the tile
-    double n0;               // ||u_0||^2 of the substep
-    double s_last, inv_s_last;   // scale s of the last update (u_{j-1} = s_{j-1} (...)), a power of two
-    double hrho[3];          // rho = 1 / ||u|| of sweeps j-1, j-2, j-3
-    double ha[3], hsub[3];   // T(i, i) and T(i, i-1) for i = j-1, j-2, j-3
-    int unit_steps;          // updates of the substep with s = 1
-    float red[kLzWarps][4];  // per-warp double-float sums (n_hi, n_lo, p_hi, p_lo)
-    double redd[kLzWarps][2];  // per-warp FP64 sums (sweep 0)
-    int stop;
-    int cexp;                // final pass, resident mode: largest biased exponent of the coefficients c_r, r >= 1
-    double2 c0;              //                            coefficient of the input state
     union {
         double2 coef[kLzMaxM];   // final pass: coefficients of the stored vectors
         float4 coefs[kLzMaxM];   //             resident mode: their hi/lo splits, scaled by 2^-E (r >= 1)
     };
+    double2 c0;              //                            coefficient of the input state
+    double cw, ca, cb;       // the update as applied: u_j = cw w' - ca u_{j-1} - cb u_{j-2}
+    double n0;               // ||u_0||^2 of the substep
+    double s_last, inv_s_last;   // scale s of the last update (u_{j-1} = s_{j-1} (...)), a power of two
+    double hrho[2];          // rho = 1 / ||u|| of sweeps j-1, j-2 (from sweep 3 on: control CTA only)
+    double hn[2];            // n = ||u||^2 of sweeps j-1, j-2 (idem)
+    double ha[2], hsub[2], hsup[2];   // control CTA: T(i, i), T(i, i-1), T(i-1, i) for i = j-1, j-2
+    double redd[kLzWarps][2];  // per-warp FP64 sums (sweep 0)
+    float red[kLzWarps][4];  // per-warp double-float sums (n_hi, n_lo, p_hi, p_lo)
+    float rprev_h, rprev_l;  // 1 / n_{j-1} in double-float
+    float inv_sf_last;       // 1 / s_{j-1} (a power of two)
+    int nring;               // resident mode: halo ring points of the tile
+    int stop;
+    int cexp;                // final pass, resident mode: largest biased exponent of the coefficients c_r, r >= 1
 };
 
 struct Tile {
@@ -250,12 +252,18 @@ __device__ __forceinline__ float4 cta_df_sum(LzSmem& sm, float nh, float nl, flo
         sm.red[warp][3] = pl;
     }
     __syncthreads();
+    // the warps' sums: a butterfly over the first kLzWarps lanes of warp 0
     float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (threadIdx.x == 0)
-        for (int w = 0; w < kLzWarps; ++w) {
-            df_add(t.x, t.y, sm.red[w][0], sm.red[w][1]);
-            df_add(t.z, t.w, sm.red[w][2], sm.red[w][3]);
+    if (warp == 0) {
+        if (lane < kLzWarps) t = make_float4(sm.red[lane][0], sm.red[lane][1], sm.red[lane][2], sm.red[lane][3]);
+#pragma unroll
+        for (int o = kLzWarps / 2; o > 0; o >>= 1) {
+            const float a = __shfl_xor_sync(0xffffffffu, t.x, o), b = __shfl_xor_sync(0xffffffffu, t.y, o);
+            const float c = __shfl_xor_sync(0xffffffffu, t.z, o), d = __shfl_xor_sync(0xffffffffu, t.w, o);
+            df_add(t.x, t.y, a, b);
+            df_add(t.z, t.w, c, d);
         }
+    }
     return t;
 }
 
@@ -311,7 +319,7 @@ __device__ __forceinline__ void load_partials(const LzArgs& A, int par, PartLoad
 // ... and the CTA sums them in double-float on the FP32 pipe (the FP64 pipe is
 // busy with the co-resident CTA's sweep), in the same fixed order in every
 // CTA; thread 0 receives the sums as FP64.
-__device__ __forceinline__ double2 reduce_partials(const LzArgs& A, LzSmem& sm, int par, const PartLoad& L, bool f64) {
+__device__ __forceinline__ float4 reduce_partials(const LzArgs& A, LzSmem& sm, int par, const PartLoad& L, bool f64) {
     if (f64) {
         // sweep 0: FP64 sums in the slots
         double n = 0.0, p = 0.0;
@@ -328,7 +336,7 @@ __device__ __forceinline__ double2 reduce_partials(const LzArgs& A, LzSmem& sm, 
             n += d.x;
             p += d.y;
         }
-        return cta_f64_sum(sm, n, p);
+        return pack_f64(cta_f64_sum(sm, n, p));
     }
     float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f;
 #pragma unroll
@@ -343,8 +351,36 @@ __device__ __forceinline__ double2 reduce_partials(const LzArgs& A, LzSmem& sm, 
         df_add(nh, nl, w.x, w.y);
         df_add(ph, pl, w.z, w.w);
     }
-    const float4 t = cta_df_sum(sm, nh, nl, ph, pl);
-    return make_double2((double)t.x + (double)t.y, (double)t.z + (double)t.w);
+    return cta_df_sum(sm, nh, nl, ph, pl);
+}
+
+// (h, l) = (ah + al)(bh + bl) in double-float (Dekker's product with a fused
+// multiply-add, renormalised); about 2^-46 relative.
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& h, float& l) {
+    const float p = __fmul_rn(ah, bh);
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    h = __fadd_rn(p, e);
+    l = __fsub_rn(e, __fsub_rn(h, p));
+}
+// (h, l) = 1 / (nh + nl) in double-float: one Newton step from the FP32 reciprocal.
+__device__ __forceinline__ void df_recip(float nh, float nl, float& h, float& l) {
+    const float r0 = __frcp_rn(nh);
+    float e = fmaf(-nh, r0, 1.0f);
+    e = fmaf(-nl, r0, e);
+    const float c = __fmul_rn(r0, e);
+    h = __fadd_rn(r0, c);
+    l = __fsub_rn(c, __fsub_rn(h, r0));
+}
+// float -> double by integer operations (exact; subnormal floats become zero),
+// so the scalar path of a Krylov step leaves the FP64 pipe to the sweeps.
+__device__ __forceinline__ double f2d_int(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+    if (e == 0u) return __hiloint2double((int)sign, 0);
+    const unsigned ex = e == 0xFFu ? 0x7FFu : e - 127u + 1023u;      // infinity and NaN stay so
+    return __hiloint2double((int)(sign | (ex << 20) | (m >> 3)), (int)(m << 29));
 }
 
 // ---- asynchronous copies global -> shared (completion per thread) ---------
@@ -677,9 +713,10 @@ __device__ __noinline__ void phase_b_first(const LzArgs& A, const Tile& T, const
 }
 
 // One Krylov sweep j over the tiles of this CTA (the first tile's copies were
-// issued by the caller); part receives the CTA's partial sums (thread 0).
+// issued by the caller, and with `staged` already waited for and published by
+// a barrier); part receives the CTA's partial sums (thread 0).
 __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double2* u0, int j, int hx, int hy, int hz,
-                      float4* part) {
+                      bool staged, float4* part) {
     const int G1 = gridDim.x - 1;
     const double cw = sm.cw, ca = sm.ca, cb = sm.cb;
     double2* wcur = A.wt + (size_t)(j & 1) * A.n;
@@ -690,8 +727,10 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
         if ((int)blockIdx.x - 1 < A.ntiles) {
             const Tile T = tile_of(A, blockIdx.x - 1, hx, hy, hz);
             double2* S = st.R(j % 3);
-            cp_async_wait_all();
-            __syncthreads();
+            if (!staged) {
+                cp_async_wait_all();
+                __syncthreads();
+            }
             if (LZ_OK(T.E, st.ext_max + 1, LZ_SITE_SMEM) && LZ_OK(T.I, st.int_max + 1, LZ_SITE_SMEM)) {
                 if (j >= 1) {
                     if (cw == 1.0)
@@ -711,10 +750,13 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
         }
     } else {
         for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
-            if (t != (int)blockIdx.x - 1) stage_tile(A, st, u0, t, j, hx, hy, hz);
+            const bool first = t == (int)blockIdx.x - 1;
+            if (!first) stage_tile(A, st, u0, t, j, hx, hy, hz);
             const Tile T = tile_of(A, t, hx, hy, hz);
-            cp_async_wait_all();
-            __syncthreads();
+            if (!(first && staged)) {
+                cp_async_wait_all();
+                __syncthreads();
+            }
             if (!LZ_OK(T.E, st.ext_max + 1, LZ_SITE_SMEM) || !LZ_OK(T.I, st.int_max + 1, LZ_SITE_SMEM)) break;
             if (j >= 1) {
                 if (cw == 1.0)
@@ -1118,7 +1160,9 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
         if (threadIdx.x == 0) {
             sm.n0 = 0.0;
             sm.s_last = sm.inv_s_last = 1.0;
-            for (int q = 0; q < 3; ++q) sm.hrho[q] = sm.ha[q] = sm.hsub[q] = 0.0;
+            for (int q = 0; q < 2; ++q) sm.hrho[q] = sm.hn[q] = sm.ha[q] = sm.hsub[q] = sm.hsup[q] = 0.0;
+            sm.rprev_h = sm.rprev_l = 0.f;
+            sm.inv_sf_last = 1.0f;
         }
         __syncthreads();
         double tol_abs2 = 0.0, bnorm = 0.0;
@@ -1141,54 +1185,119 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
             }
             if (j >= 1) {
                 // coefficients of sweep j-1, the same in every CTA
-                const double2 t = reduce_partials(A, sm, (j - 1) & 1, L, j == 1);
+                const float4 q = reduce_partials(A, sm, (j - 1) & 1, L, j == 1);
                 if (threadIdx.x == 0) {
                     // sweep j-1 gave n = ||u_{j-1}||^2 and p = Re u_{j-1}^H w'
-                    // (w' = B u_{j-1} / f).  The update u_j = s_j (w' - alpha
+                    // (w' = B u_{j-1} / f).  The update is u_j = s_j (w' - alpha
                     // u_{j-1} - beta u_{j-2}) with alpha = p / n and beta = n /
-                    // (s_{j-1} n_{j-2}) makes T symmetric: T(j-1, j-1) = f alpha
-                    // (the Rayleigh quotient), T(j-1, j-2) = f sqrt(n / n_{j-2}) /
-                    // s_{j-1}.  s_j = 1 (two fused multiply-adds per component)
-                    // while n stays in [2^-30, 2^30], else the power of two that
-                    // brings u_j back to unit scale: one reciprocal square root, no
-                    // division
-                    const double n = t.x;
-                    const double rho = n > 0.0 ? rsqrt(n) : 0.0;        // q_{j-1} = rho u_{j-1}
-                    const double alpha = t.y * rho * rho;
-                    const double rho2 = sm.hrho[0];                      // rho_{j-2}
-                    const double inv_s = sm.inv_s_last;
-                    const double beta = j >= 2 ? n * rho2 * rho2 * inv_s : 0.0;
-                    const double sub = j >= 2 ? A.fold * n * rho * rho2 * inv_s : 0.0;
-                    double sj = 1.0, inv_sj = 1.0;
-                    if (!A.unit_ok || !(n >= 0x1p-30 && n <= 0x1p30)) {
-                        const int be = (__double2hiint(n) >> 20) & 0x7FF;
-                        const int k = -((be - 1023) >> 1);               // s^2 n in [1/2, 4) for normal n
-                        sj = __hiloint2double((1023 + k) << 20, 0);
-                        inv_sj = __hiloint2double((1023 - k) << 20, 0);
+                    // (s_{j-1} n_{j-2}); s_j = 1 (two fused multiply-adds per
+                    // component) while n stays in [2^-30, 2^30], else the power of
+                    // two that brings u_j back to unit scale.  With q_i = u_i / ||u_i||
+                    // the columns of T follow from the coefficients as used:
+                    // T(j-1, j-1) = f alpha, T(j-1, j-2) = f sqrt(n / n_{j-2}) /
+                    // s_{j-1}, T(j-2, j-1) = f beta sqrt(n_{j-2} / n) (equal in exact
+                    // arithmetic).  From sweep 2 on the tile CTAs form alpha and beta
+                    // in double-float on the FP32 pipe (about 2^-46 relative; the
+                    // control CTA takes T from the values actually used), so the
+                    // step's scalar path costs two FP64 instructions.
+                    double sj, inv_sj, ca, cb;
+                    if (j <= 2) {
+                        // FP64: sweep 0's sums may lie outside the FP32 range, and
+                        // beta at j = 2 divides by n_0
+                        const double2 t = j == 1 ? unpack_f64(q)
+                                                 : make_double2(f2d_int(q.x) + f2d_int(q.y), f2d_int(q.z) + f2d_int(q.w));
+                        const double n = t.x;
+                        const double rho = n > 0.0 ? rsqrt(n) : 0.0;
+                        const double alpha = t.y * rho * rho;
+                        const double rho2 = sm.hrho[0];
+                        const double beta = j >= 2 ? n * rho2 * rho2 * sm.inv_s_last : 0.0;
+                        sj = inv_sj = 1.0;
+                        if (!A.unit_ok || !(n >= 0x1p-30 && n <= 0x1p30)) {
+                            const int be = (__double2hiint(n) >> 20) & 0x7FF;
+                            const int k = -((be - 1023) >> 1);           // s^2 n in [1/2, 4) for normal n
+                            sj = __hiloint2double((1023 + k) << 20, 0);
+                            inv_sj = __hiloint2double((1023 - k) << 20, 0);
+                        }
+                        ca = sj * alpha;
+                        cb = sj * beta;
+                        if (j == 1) sm.n0 = n;
+                        sm.hrho[1] = sm.hrho[0];
+                        sm.hrho[0] = rho;
+                        sm.hn[1] = sm.hn[0];
+                        sm.hn[0] = n;
+                        if (control) {
+                            const double sub = j >= 2 ? A.fold * n * rho * rho2 * sm.inv_s_last : 0.0;
+                            sm.ha[1] = sm.ha[0];
+                            sm.ha[0] = A.fold * alpha;
+                            sm.hsub[1] = sm.hsub[0];
+                            sm.hsub[0] = sub;
+                            sm.hsup[1] = sm.hsup[0];
+                            sm.hsup[0] = sub;
+                            if (LZ_OK(j - 1, A.m + 2, LZ_SITE_Y)) A.rho[j - 1] = rho;
+                        }
+                    } else {
+                        float sf = 1.0f;
+                        sj = inv_sj = 1.0;
+                        if (!A.unit_ok || !(q.x >= 0x1p-30f && q.x <= 0x1p30f)) {
+                            const int be = (int)((__float_as_uint(q.x) >> 23) & 0xFFu);
+                            const int k = -((be - 127) >> 1);
+                            sf = __uint_as_float((unsigned)(127 + k) << 23);
+                            sj = __hiloint2double((1023 + k) << 20, 0);
+                            inv_sj = __hiloint2double((1023 - k) << 20, 0);
+                        }
+                        float rh = 0.f, rl = 0.f;
+                        if (q.x > 0.f) df_recip(q.x, q.y, rh, rl);
+                        float ah, al, bh, bl;
+                        df_mul(q.z, q.w, rh, rl, ah, al);                     // alpha = p / n
+                        df_mul(q.x, q.y, sm.rprev_h, sm.rprev_l, bh, bl);     // n / n_{j-2}
+                        const float sb = __fmul_rn(sf, sm.inv_sf_last);        // s_j / s_{j-1}: a power of two
+                        ca = f2d_int(__fmul_rn(ah, sf)) + f2d_int(__fmul_rn(al, sf));
+                        cb = f2d_int(__fmul_rn(bh, sb)) + f2d_int(__fmul_rn(bl, sb));
+                        if (control) {
+                            // the exact columns of T for these coefficients, in FP64
+                            const double n = f2d_int(q.x) + f2d_int(q.y);
+                            const double rho = n > 0.0 ? rsqrt(n) : 0.0;
+                            const double rho2 = sm.hrho[0], n2 = sm.hn[0];
+                            const double sub = A.fold * n * rho * rho2 * sm.inv_s_last;
+                            sm.ha[1] = sm.ha[0];
+                            sm.ha[0] = A.fold * (ca * inv_sj);
+                            sm.hsub[1] = sm.hsub[0];
+                            sm.hsub[0] = sub;
+                            sm.hsup[1] = sm.hsup[0];
+                            sm.hsup[0] = A.fold * (cb * inv_sj) * rho * (n2 * rho2);
+                            sm.hrho[1] = sm.hrho[0];
+                            sm.hrho[0] = rho;
+                            sm.hn[1] = sm.hn[0];
+                            sm.hn[0] = n;
+                            if (LZ_OK(j - 1, A.m + 2, LZ_SITE_Y)) A.rho[j - 1] = rho;
+                        }
+                        sm.inv_sf_last = 1.0f / sf;
                     }
-                    if (j == 1) sm.n0 = n;
+                    if (j >= 2) {
+                        // 1 / n_{j-1} for the next step's beta (n_{j-1} is in the FP32 range)
+                        float rh = 0.f, rl = 0.f;
+                        if (q.x > 0.f) df_recip(q.x, q.y, rh, rl);
+                        sm.rprev_h = rh;
+                        sm.rprev_l = rl;
+                    }
+                    if (j <= 2) {
+                        // (only j = 2's value is used, and s_2 is within the FP32 range)
+                        const int k = min(126, max(-126, ((__double2hiint(sj) >> 20) & 0x7FF) - 1023));
+                        sm.inv_sf_last = __uint_as_float((unsigned)(127 - k) << 23);
+                    }
                     sm.cw = sj;
-                    sm.ca = sj * alpha;
-                    sm.cb = sj * beta;
+                    sm.ca = ca;
+                    sm.cb = cb;
                     sm.s_last = sj;
                     sm.inv_s_last = inv_sj;
-                    sm.hrho[2] = sm.hrho[1];
-                    sm.hrho[1] = sm.hrho[0];
-                    sm.hrho[0] = rho;
-                    sm.ha[2] = sm.ha[1];
-                    sm.ha[1] = sm.ha[0];
-                    sm.ha[0] = A.fold * alpha;
-                    sm.hsub[2] = sm.hsub[1];
-                    sm.hsub[1] = sm.hsub[0];
-                    sm.hsub[0] = sub;
                     sm.stop = stop_word;
-                    if (control && LZ_OK(j - 1, A.m + 2, LZ_SITE_Y)) A.rho[j - 1] = rho;
                 }
+                // this barrier also publishes the first tile's copies to the sweep
+                cp_async_wait_all();
                 __syncthreads();
                 if (sm.stop >= 0) {
                     J = sm.stop;
-                    sweeps = j;
-                    cp_async_wait_all();               // no copy may land after the stage is reused
+                    sweeps = j;                        // (no copy is in flight: waited above)
                     break;
                 }
                 if (j > A.m + 2) {                     // the control CTA stops by then: never taken
@@ -1203,7 +1312,7 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
             }
             if (!control) {
                 float4 part;
-                sweep(A, sm, st, u0, j, hx, hy, hz, &part);
+                sweep(A, sm, st, u0, j, hx, hy, hz, j >= 1, &part);
                 if (threadIdx.x == 0 && LZ_OK((j & 1) * gridDim.x + blockIdx.x, 2 * A.part_cap, LZ_SITE_PART))
                     A.part[(size_t)(j & 1) * gridDim.x + blockIdx.x] = part;
             } else if (j >= 1) {
@@ -1226,7 +1335,7 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                 } else {
                     const int c = j - 2;
                     // T[c-1, c] = T[c, c-1] and T[c+1, c], from the last two reductions
-                    const double up = c >= 1 ? sm.hsub[1] : 0.0;
+                    const double up = c >= 1 ? sm.hsup[1] : 0.0;
                     const double lo = sm.hsub[0];
                     const double ac = sm.ha[1];
                     int active = 0;
