@@ -476,8 +476,9 @@ def other_workloads(args, flush, stream, dev):
     has several steps): 1D harmonic (K=16, dt=1, tol 1e-12), 3D softened
     Coulomb 128^3 (K=32: K=64 is refused by the plan), 64 batched 2D problems
     (one graph-captured batched launch of the item engine in the workload's
-    mixed precision, and 64 graph-captured single launches of the Lanczos
-    kernel), and the learnable 256^2 problem (forward step plus adjoint)."""
+    mixed precision, 64 graph-captured single launches of the Lanczos kernel,
+    and one graph-captured batched launch of the Lanczos kernel), and the
+    learnable 256^2 problem (forward step plus adjoint)."""
     import numpy as np
     import torch
     import workloads as wl
@@ -568,17 +569,32 @@ def other_workloads(args, flush, stream, dev):
     line["lanczos_singles"] = {"ms_per_step": ms_l, "steps_per_s": 1000.0 / ms_l,
                                "grid_pts_poles_per_s": work * 1000.0 / ms_l,
                                "path": "64 graph-captured single launches of the Lanczos kernel, FP64"}
+    # all 64 problems in one launch of the Lanczos kernel (the first call
+    # uploads the descriptors; the captured call only launches)
+    outs_b = [torch.empty_like(t) for t in ins]
+    step_batched(lplans, ins, outs_b)
+    torch.cuda.synchronize()
+    graph_b = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_b):
+        step_batched(lplans, ins, outs_b)
+    ms_b = _timed_ms(graph_b.replay, flush, stream, nt=5)
+    line["lanczos_batched"] = {
+        "ms_per_step": ms_b, "steps_per_s": 1000.0 / ms_b, "grid_pts_poles_per_s": work * 1000.0 / ms_b,
+        "path": "one graph-captured batched launch of the Lanczos kernel, FP64 (CTAs divided among the problems)",
+        "rel_diff_vs_singles": max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+                                   for a, b in zip(outs_b, outs))}
     if not args.no_oracle_check:
         try:
             ref_np, _ = oracle_first_step(68.0, cores, "c4:%d" % smallest)
-            for key, got in (("rel_err_vs_oracle", batched_first), ("lanczos_rel_err_vs_oracle", outs[smallest])):
+            for key, got in (("rel_err_vs_oracle", batched_first), ("lanczos_rel_err_vs_oracle", outs[smallest]),
+                             ("lanczos_batched_rel_err_vs_oracle", outs_b[smallest])):
                 got = got.cpu().numpy().ravel()
                 line[key] = float(np.linalg.norm(got - ref_np.ravel()) / np.linalg.norm(ref_np))
             line["oracle_problem"] = "the smallest problem (%s)" % "x".join(map(str, probs[smallest]["grid"]["n"]))
         except Exception as e:  # reported, not fatal
             line["rel_err_vs_oracle"] = "failed: %s" % e
     res["c4_batched_64x2d_K32"] = line
-    del lplans, graph, ins, outs
+    del lplans, graph, graph_b, ins, outs, outs_b
 
     # C5: learnable potential, forward step + adjoint (10 steps each way)
     cfg = wl.config_learnable()

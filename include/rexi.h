@@ -114,7 +114,8 @@ typedef struct {
                               pass over the basis.  rexi_step and rexi_solve_poles run on this
                               path; rexi_step_backward runs on the item engine (shared first
                               cycle, window 2, restart min(restart_m, 64)), allocated at its
-                              first call; rexi_step_batched rejects such plans (REXI_EINVAL)  */
+                              first call; rexi_step_batched runs a batch of such plans as one
+                              launch of the Lanczos kernel                                    */
     int    window;         /* with ortho = 1: 0 (default) orthogonalise every new vector against
                               the whole basis; L >= 2: only against the last L vectors (a
                               truncated, quasi-GMRES basis).  H is real symmetric, so tau H - z
@@ -238,8 +239,16 @@ int rexi_cheb_step(rexi_plan* plan, const void* psi_in, void* psi_out, double to
 /* B independent problems (each with its own plan, grid, K and n_sub) in one
  * persistent launch: all problems x all poles share the GPU (the K solves of
  * every problem are the independent tasks of Sec. 3.1).  All plans must be on
- * the same device and have the same precision, restart length and
- * orthogonalisation; B <= 128.
+ * the same device, distinct, and either all item-engine plans with the same
+ * precision, restart length and orthogonalisation, or all Lanczos plans
+ * (ortho = 2); B <= 128.  For Lanczos plans the launch divides its CTAs among
+ * the problems in proportion to their points (a control CTA and at least one
+ * tile CTA each, so B <= the CTAs of the launch / 2), chooses every problem's
+ * tile boxes for its share, and each problem synchronises only its own CTAs;
+ * every plan's own workspace is used.  The first call with a combination of
+ * plans uploads its descriptors (synchronously, into memory owned by plans[0]);
+ * later calls with the same plans only launch, so they may be captured in a
+ * CUDA graph once the first call has run.
  * psi_in[b], psi_out[b] : device c128 of plan b's size.  st: B entries or NULL
  * (with st the call synchronises and returns the first failing status). */
 int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,

@@ -134,6 +134,13 @@ struct rexi_plan {
     int generation = 0;                          // bumped when the item workspace moves
     unsigned long long uid = 0;                  // unique over the process (never reused)
     // descriptors of the last batched combination led by this plan
+    std::vector<unsigned long long> lzb_key;     // Lanczos batches: uids of the plans, in order
+    std::vector<int> lzb_gens;
+    rexi::LzArgs* d_lzb_args = nullptr;          // per-problem descriptors of the cached batch
+    unsigned char* d_lzb_map = nullptr;          // problem of every CTA
+    size_t lzb_cap_args = 0, lzb_cap_map = 0;
+    int lzb_grid = 0;
+    size_t lzb_smem = 0;
     std::vector<unsigned long long> batch_key;   // uids of the plans, in order
     std::vector<int> batch_gens;
     ProblemDesc* d_batch_prob = nullptr;
@@ -507,13 +514,21 @@ int collect(rexi_plan* p, cudaStream_t stream, int nitems, int item_offset, int 
 // 1 + t mod (G - 1) and CTA c on SM c mod (SMs) (the order in which the
 // resident grid fills the SMs).  Then the grid, the dynamic shared memory and
 // the rows the control CTA stages per chunk.
-int lz_configure(rexi_plan* p) {
-    const int sms = sm_count(p->device);
+// Tile box and shared memory of one problem run by G CTAs (one control CTA
+// and G - 1 tile CTAs) at cps CTAs per SM; the load model spreads the tile
+// CTAs over model_sms SMs.
+struct LzChoice {
+    int tx = 1, ty = 1, tz = 1;
+    bool resident = false;
+    size_t smem = 0;
+    int stage = 1;
+};
+
+int lz_choose(const rexi_plan* p, int G, int cps, int model_sms, LzChoice* out) {
+    const int sms = std::max(1, model_sms);
     const int hx = p->a[0] != 0.0 ? 1 : 0, hy = p->a[1] != 0.0 ? 1 : 0, hz = p->a[2] != 0.0 ? 1 : 0;
     const int nx = p->dims[0], ny = p->dims[1], nz = p->dims[2];
     const int target = p->lz_target > 0 ? std::min(p->lz_target, rexi::kLzMaxInterior) : rexi::kLzMaxInterior;
-    const int cps = std::max(1, std::min(p->lz_cps, 8));
-    const int G = cps * sms;
     const int tile_ctas = std::max(1, G - 1);
     int smem_sm = 0;
     if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device) != cudaSuccess)
@@ -566,17 +581,33 @@ int lz_configure(rexi_plan* p) {
         }
     }
     if (best < 0) return REXI_EINVAL;               // no box fits (a row longer than 2048 points)
-    p->lz_tx = bx;
-    p->lz_ty = by;
-    p->lz_tz = bz;
+    out->tx = bx;
+    out->ty = by;
+    out->tz = bz;
     // resident mode when every tile CTA owns at most one tile and its state fits
     const long long ntiles = (long long)((nx + bx - 1) / bx) * ((ny + by - 1) / by) * ((nz + bz - 1) / bz);
     const size_t smem_res = std::max(rexi::lanczos_smem_bytes(bx, by, bz, hx, hy, hz, true), ctl_min);
-    p->lz_resident = ntiles <= tile_ctas && smem_res + stat + 1024 <= per_cta;
-    const size_t smem =
-        p->lz_resident ? smem_res : std::max(rexi::lanczos_smem_bytes(bx, by, bz, hx, hy, hz, false), ctl_min);
-    p->lz_stage = (int)std::max<size_t>(1, std::min<size_t>(64, smem / row_bytes));
-    p->lz_smem = smem;
+    out->resident = ntiles <= tile_ctas && smem_res + stat + 1024 <= per_cta;
+    out->smem =
+        out->resident ? smem_res : std::max(rexi::lanczos_smem_bytes(bx, by, bz, hx, hy, hz, false), ctl_min);
+    out->stage = (int)std::max<size_t>(1, std::min<size_t>(64, out->smem / row_bytes));
+    return REXI_OK;
+}
+
+int lz_configure(rexi_plan* p) {
+    const int sms = sm_count(p->device);
+    const int cps = std::max(1, std::min(p->lz_cps, 8));
+    const int G = cps * sms;
+    LzChoice c;
+    const int r = lz_choose(p, G, cps, sms, &c);
+    if (r) return r;
+    p->lz_tx = c.tx;
+    p->lz_ty = c.ty;
+    p->lz_tz = c.tz;
+    p->lz_resident = c.resident;
+    p->lz_stage = c.stage;
+    p->lz_smem = c.smem;
+    const size_t smem = c.smem;
     const int maxg = rexi::lanczos_max_grid(smem, p->device);
     if (maxg < 2) return REXI_ECUDA;
     p->lz_grid = std::min(maxg, G);
@@ -619,6 +650,8 @@ int lz_alloc(rexi_plan* p) {
 
 // One launch of the Lanczos kernel: n_sub substeps (mode LZ_STEP) or the K
 // solves of one substep (LZ_SOLVE, x = out [K][n]).
+rexi::LzArgs lz_args(rexi_plan* p, int mode, const void* in, void* out, const LzChoice& c, int cta0, int ncta);
+
 int lz_launch(rexi_plan* p, int mode, const void* in, void* out, cudaStream_t stream) {
     const int nsub = mode == rexi::LZ_STEP ? p->n_sub : 1;
     cudaError_t e = cudaMemsetAsync(p->d_bar, 0, 3 * sizeof(unsigned), stream);
@@ -628,6 +661,24 @@ int lz_launch(rexi_plan* p, int mode, const void* in, void* out, cudaStream_t st
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_lz_stop, 0xFF, sizeof(int) * nsub, stream);
     if (e == cudaSuccess && p->d_dbg) e = cudaMemsetAsync(p->d_dbg, 0, 4 * sizeof(long long), stream);
     if (e != cudaSuccess) return cuda_fail(e);
+    LzChoice c;
+    c.tx = p->lz_tx;
+    c.ty = p->lz_ty;
+    c.tz = p->lz_tz;
+    c.resident = p->lz_resident;
+    c.stage = p->lz_stage;
+    const rexi::LzArgs A = lz_args(p, mode, in, out, c, 0, p->lz_grid);
+    e = rexi::launch_lanczos(A, p->lz_grid, p->lz_smem, stream);
+    p->last_stream = stream;
+    p->last_launches = 1;
+    p->last_grid = p->lz_grid;
+    return e == cudaSuccess ? REXI_OK : cuda_fail(e);
+}
+
+// The descriptor of one Lanczos launch of plan p (tile choice c, CTAs cta0 ..
+// cta0 + ncta - 1 of the launch).
+rexi::LzArgs lz_args(rexi_plan* p, int mode, const void* in, void* out, const LzChoice& c, int cta0, int ncta) {
+    const int nsub = mode == rexi::LZ_STEP ? p->n_sub : 1;
     rexi::LzArgs A{};
     A.mode = mode;
     A.n = p->n;
@@ -651,15 +702,15 @@ int lz_launch(rexi_plan* p, int mode, const void* in, void* out, cudaStream_t st
     A.alpha = p->d_alpha;
     A.alpha0 = make_double2(p->alpha0.real(), p->alpha0.imag());
     A.tol = p->tol;
-    A.stage_rows = p->lz_stage;
-    A.tx = p->lz_tx;
-    A.ty = p->lz_ty;
-    A.tz = p->lz_tz;
+    A.stage_rows = c.stage;
+    A.tx = c.tx;
+    A.ty = c.ty;
+    A.tz = c.tz;
     A.gx = (A.nx + A.tx - 1) / A.tx;
     A.gy = (A.ny + A.ty - 1) / A.ty;
     A.gz = (A.nz + A.tz - 1) / A.tz;
     A.ntiles = A.gx * A.gy * A.gz;
-    A.resident = p->lz_resident ? 1 : 0;
+    A.resident = c.resident ? 1 : 0;
     A.in = (const double2*)in;
     A.out = (double2*)out;
     A.tmp0 = p->d_tmp0;
@@ -683,11 +734,104 @@ int lz_launch(rexi_plan* p, int mode, const void* in, void* out, cudaStream_t st
     A.part_cap = p->lz_part_cap;
     A.dbg = p->d_dbg;
     A.dbg_trip = p->dbg_trip;
-    e = rexi::launch_lanczos(A, p->lz_grid, p->lz_smem, stream);
-    p->last_stream = stream;
-    p->last_launches = 1;
-    p->last_grid = p->lz_grid;
-    return e == cudaSuccess ? REXI_OK : cuda_fail(e);
+    A.cta0 = cta0;
+    A.ncta = ncta;
+    return A;
+}
+
+// One step of several problems in one launch of the Lanczos kernel: the CTAs
+// are divided among the problems in proportion to their points (each problem
+// gets a control CTA and at least one tile CTA), every problem's tile boxes are
+// chosen for its share, and every problem synchronises only its own CTAs.
+// The descriptors are cached in the first plan, keyed like the item engine's.
+int lz_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in, void* const* psi_out, cudaStream_t s,
+                    rexi_stats* st) {
+    rexi_plan* p0 = plans[0];
+    const int sms = sm_count(p0->device);
+    const int cps = 2;
+    std::vector<unsigned long long> key(B);
+    std::vector<int> gens(B);
+    for (int b = 0; b < B; ++b) {
+        key[b] = plans[b]->uid;
+        gens[b] = plans[b]->generation;
+    }
+    if (p0->lzb_key != key || p0->lzb_gens != gens || !p0->d_lzb_args) {
+        int G = cps * sms;
+        if (G < 2 * B) return REXI_EINVAL;                  // a control and a tile CTA per problem
+        // CTAs in proportion to the points, at least two per problem
+        long long N = 0;
+        for (int b = 0; b < B; ++b) N += plans[b]->n;
+        std::vector<int> nct(B);
+        int used = 0;
+        for (int b = 0; b < B; ++b) {
+            nct[b] = 2 + (int)((long long)(G - 2 * B) * plans[b]->n / N);
+            used += nct[b];
+        }
+        for (int b = 0; used < G; b = (b + 1) % B, ++used) ++nct[b];
+        std::vector<LzChoice> ch(B);
+        size_t smem = 0;
+        for (int b = 0; b < B; ++b) {
+            const int r = lz_choose(plans[b], nct[b], cps, nct[b], &ch[b]);
+            if (r) return r;
+            smem = std::max(smem, ch[b].smem);
+        }
+        const int maxg = rexi::lanczos_max_grid(smem, p0->device, true);
+        if (maxg < G) return REXI_ECUDA;
+        std::vector<rexi::LzArgs> args(B);
+        std::vector<unsigned char> map(G);
+        int c0 = 0;
+        for (int b = 0; b < B; ++b) {
+            rexi_plan* p = plans[b];
+            if (nct[b] > p->lz_part_cap) return REXI_EINVAL;
+            // the control CTA stages rows in the launch's dynamic shared memory
+            ch[b].stage = (int)std::max<size_t>(1, std::min<size_t>(64, smem / ((size_t)p->K * 3 * sizeof(double2))));
+            args[b] = lz_args(p, rexi::LZ_STEP, nullptr, nullptr, ch[b], c0, nct[b]);
+            args[b].trace = nullptr;
+            args[b].trace_cap = 0;
+            for (int c = 0; c < nct[b]; ++c) map[c0 + c] = (unsigned char)b;
+            c0 += nct[b];
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) return REXI_ECUDA;   // old descriptors may be in use
+        int r;
+        if ((size_t)B > p0->lzb_cap_args) {
+            if ((r = dalloc(p0, &p0->d_lzb_args, (size_t)B))) return r;
+            p0->lzb_cap_args = (size_t)B;
+        }
+        if ((size_t)G > p0->lzb_cap_map) {
+            if ((r = dalloc(p0, &p0->d_lzb_map, (size_t)G))) return r;
+            p0->lzb_cap_map = (size_t)G;
+        }
+        p0->lzb_key.clear();                     // invalid until the copies succeed
+        if (cudaMemcpy(p0->d_lzb_args, args.data(), sizeof(rexi::LzArgs) * B, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(p0->d_lzb_map, map.data(), (size_t)G, cudaMemcpyHostToDevice) != cudaSuccess)
+            return REXI_ECUDA;
+        p0->lzb_key = key;
+        p0->lzb_gens = gens;
+        p0->lzb_grid = G;
+        p0->lzb_smem = smem;
+    }
+    rexi::LzIO io{};
+    for (int b = 0; b < B; ++b) {
+        io.in[b] = (const double2*)psi_in[b];
+        io.out[b] = (double2*)psi_out[b];
+    }
+    cudaError_t e = rexi::lanczos_reset(p0->d_lzb_args, B, s);
+    if (e == cudaSuccess)
+        e = rexi::launch_lanczos_batched(p0->d_lzb_args, p0->d_lzb_map, io, p0->lzb_grid, p0->lzb_smem, s);
+    for (int b = 0; b < B; ++b) {
+        plans[b]->last_stream = s;
+        plans[b]->last_launches = 1;
+        plans[b]->last_grid = p0->lzb_grid;
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (!st) return REXI_OK;
+    int status = REXI_OK;
+    for (int b = 0; b < B; ++b) {
+        const int r = collect(plans[b], s, plans[b]->K, 0, plans[b]->K, &st[b], plans[b]->n_sub);
+        plans[b]->last_status = r;
+        if (r != REXI_OK && status == REXI_OK) status = r;
+    }
+    return status;
 }
 
 }  // namespace
@@ -1159,6 +1303,17 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
     if (!plans || B < 1 || B > rexi::kMaxBatch || !psi_in || !psi_out) return REXI_EINVAL;
     rexi_plan* p0 = plans[0];
     if (!p0) return REXI_EINVAL;
+    if (p0->lanczos) {
+        // every plan a Lanczos plan on the same device, each plan once
+        for (int b = 0; b < B; ++b) {
+            rexi_plan* p = plans[b];
+            if (!p || !psi_in[b] || !psi_out[b] || !p->lanczos || p->device != p0->device) return REXI_EINVAL;
+            for (int c = 0; c < b; ++c)
+                if (plans[c] == p) return REXI_EINVAL;
+        }
+        DeviceGuard guard(p0->device);
+        return lz_step_batched(plans, B, psi_in, psi_out, (cudaStream_t)stream, st);
+    }
     int total_items = 0, max_sub = 0, total_tiles = 0;
     for (int b = 0; b < B; ++b) {
         rexi_plan* p = plans[b];

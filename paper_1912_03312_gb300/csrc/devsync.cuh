@@ -92,7 +92,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
     return true;
 }
 
-// All CTAs of the co-resident grid meet here.  bar[0] counts arrivals and
+// All `count` CTAs that share `bar` (a co-resident grid, or one problem's range
+// of CTAs in a batched launch) meet here.  bar[0] counts arrivals and
 // bar[1] completed barriers; both are zeroed before every launch.  The arrival
 // that makes the count a multiple of the grid size publishes the barrier's
 // number with a release store; the others poll it with acquire loads.  Every
@@ -100,15 +101,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
 // wait also ends when another CTA has set the error word (it may have left the
 // kernel and never arrive).  The function returns false whenever the error
 // word is set, so every CTA leaves the kernel at its next barrier.
-__device__ __forceinline__ bool grid_sync(unsigned* bar, int* err, unsigned long long timeout_ns) {
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned count, int* err, unsigned long long timeout_ns) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned* count = bar;
+        unsigned* arrived = bar;
         unsigned* done = bar + 1;
         __threadfence();                                   // the CTA's writes before its arrival
-        const unsigned prev = atomicAdd(count, 1u);
-        const unsigned target = prev / gridDim.x + 1u;
-        if (prev + 1u == target * gridDim.x) {
+        const unsigned prev = atomicAdd(arrived, 1u);
+        const unsigned target = prev / count + 1u;
+        if (prev + 1u == target * count) {
             __threadfence();
             st_release_u32(done, target);
         } else {

@@ -57,6 +57,10 @@ namespace {
 using dev::global_ns;
 using dev::grid_sync;
 
+// This CTA's index within its problem's range of CTAs, and the range's size.
+__device__ __forceinline__ int lz_bid(const LzArgs& A) { return (int)blockIdx.x - A.cta0; }
+__device__ __forceinline__ int lz_nct(const LzArgs& A) { return A.ncta; }
+
 constexpr int kLzWarps = kLzBlock / 32;
 constexpr int kErrInternal = -3;        // REXI_ECUDA: the iteration outran its workspace
 
@@ -205,7 +209,7 @@ __device__ __forceinline__ void givens(double2 x, double h, double* c, double2* 
 }
 
 __device__ __forceinline__ void trace_mark(const LzArgs& A, int code, int* tcount) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (threadIdx.x == 0 && lz_bid(A) == 0) {
         const int c = *tcount;
         if (A.trace != nullptr && c < A.trace_cap) {
             A.trace[1 + 2 * c] = (unsigned long long)code;
@@ -307,11 +311,11 @@ struct PartLoad {
     float4 v[5];
 };
 __device__ __forceinline__ void load_partials(const LzArgs& A, int par, PartLoad& L) {
-    const float4* p = A.part + (size_t)par * gridDim.x;
+    const float4* p = A.part + (size_t)par * lz_nct(A);
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
         const int c = 1 + threadIdx.x + q * kLzBlock;
-        L.v[q] = c < (int)gridDim.x && LZ_OK(par * gridDim.x + c, 2 * A.part_cap, LZ_SITE_PART)
+        L.v[q] = c < lz_nct(A) && LZ_OK(par * lz_nct(A) + c, 2 * A.part_cap, LZ_SITE_PART)
                      ? __ldcg(p + c)
                      : make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -329,9 +333,9 @@ __device__ __forceinline__ float4 reduce_partials(const LzArgs& A, LzSmem& sm, i
             n += d.x;
             p += d.y;
         }
-        const float4* pp = A.part + (size_t)par * gridDim.x;
-        for (int c = 1 + threadIdx.x + 5 * kLzBlock; c < (int)gridDim.x; c += kLzBlock) {
-            if (!LZ_OK(par * gridDim.x + c, 2 * A.part_cap, LZ_SITE_PART)) continue;
+        const float4* pp = A.part + (size_t)par * lz_nct(A);
+        for (int c = 1 + threadIdx.x + 5 * kLzBlock; c < lz_nct(A); c += kLzBlock) {
+            if (!LZ_OK(par * lz_nct(A) + c, 2 * A.part_cap, LZ_SITE_PART)) continue;
             const double2 d = unpack_f64(__ldcg(pp + c));
             n += d.x;
             p += d.y;
@@ -344,9 +348,9 @@ __device__ __forceinline__ float4 reduce_partials(const LzArgs& A, LzSmem& sm, i
         df_add(nh, nl, L.v[q].x, L.v[q].y);
         df_add(ph, pl, L.v[q].z, L.v[q].w);
     }
-    const float4* p = A.part + (size_t)par * gridDim.x;
-    for (int c = 1 + threadIdx.x + 5 * kLzBlock; c < (int)gridDim.x; c += kLzBlock) {
-        if (!LZ_OK(par * gridDim.x + c, 2 * A.part_cap, LZ_SITE_PART)) continue;
+    const float4* p = A.part + (size_t)par * lz_nct(A);
+    for (int c = 1 + threadIdx.x + 5 * kLzBlock; c < lz_nct(A); c += kLzBlock) {
+        if (!LZ_OK(par * lz_nct(A) + c, 2 * A.part_cap, LZ_SITE_PART)) continue;
         const float4 w = __ldcg(p + c);
         df_add(nh, nl, w.x, w.y);
         df_add(ph, pl, w.z, w.w);
@@ -551,7 +555,7 @@ __device__ void stage_tile(const LzArgs& A, const Stage& st, const double2* u0, 
 __device__ void stage_resident(const LzArgs& A, const LzSmem& sm, const Stage& st, const double2* u0, int j, int hx,
                                int hy, int hz) {
     if (j == 0) {
-        const Tile T = tile_of(A, blockIdx.x - 1, hx, hy, hz);
+        const Tile T = tile_of(A, lz_bid(A) - 1, hx, hy, hz);
         Walk w;
         w.init(threadIdx.x, T.ex, T.ey);
         for (int e = threadIdx.x; e < T.E; e += kLzBlock, w.next(T.ex, T.ey)) {
@@ -573,7 +577,7 @@ __device__ void stage_resident(const LzArgs& A, const LzSmem& sm, const Stage& s
 // Resident mode, once per launch: the diagonal on the tile, and the list of
 // the halo ring points (order immaterial: they are only copied).
 __device__ void setup_resident(const LzArgs& A, LzSmem& sm, const Stage& st, int hx, int hy, int hz) {
-    const Tile T = tile_of(A, blockIdx.x - 1, hx, hy, hz);
+    const Tile T = tile_of(A, lz_bid(A) - 1, hx, hy, hz);
     Walk wi;
     wi.init(threadIdx.x, T.tx, T.ty);
     for (int i = threadIdx.x; i < T.I; i += kLzBlock, wi.next(T.tx, T.ty)) {
@@ -717,15 +721,15 @@ __device__ __noinline__ void phase_b_first(const LzArgs& A, const Tile& T, const
 // a barrier); part receives the CTA's partial sums (thread 0).
 __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double2* u0, int j, int hx, int hy, int hz,
                       bool staged, float4* part) {
-    const int G1 = gridDim.x - 1;
+    const int G1 = lz_nct(A) - 1;
     const double cw = sm.cw, ca = sm.ca, cb = sm.cb;
     double2* wcur = A.wt + (size_t)(j & 1) * A.n;
     double2* ujw = j >= 1 ? uvec_w(A, j) : nullptr;
     float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f;
     double dn = 0.0, dp = 0.0;
     if (A.resident) {
-        if ((int)blockIdx.x - 1 < A.ntiles) {
-            const Tile T = tile_of(A, blockIdx.x - 1, hx, hy, hz);
+        if (lz_bid(A) - 1 < A.ntiles) {
+            const Tile T = tile_of(A, lz_bid(A) - 1, hx, hy, hz);
             double2* S = st.R(j % 3);
             if (!staged) {
                 cp_async_wait_all();
@@ -749,8 +753,8 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
             }
         }
     } else {
-        for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
-            const bool first = t == (int)blockIdx.x - 1;
+        for (int t = lz_bid(A) - 1; t < A.ntiles; t += G1) {
+            const bool first = t == lz_bid(A) - 1;
             if (!first) stage_tile(A, st, u0, t, j, hx, hy, hz);
             const Tile T = tile_of(A, t, hx, hy, hz);
             if (!(first && staged)) {
@@ -841,9 +845,9 @@ constexpr int kMaxDepth = 8;    // basis vectors a thread prefetches in the fina
 template <bool kSplit>
 __device__ void final_pass(const LzArgs& A, const LzSmem& sm, double up, const double2* u0, double2* dst, int J,
                            int hx, int hy, int hz, float4* slots, int depth) {
-    const int G1 = gridDim.x - 1;
+    const int G1 = lz_nct(A) - 1;
     const int rb = kSplit ? 1 : 0;                 // first vector through the slots
-    for (int t = blockIdx.x - 1; t < A.ntiles; t += G1) {
+    for (int t = lz_bid(A) - 1; t < A.ntiles; t += G1) {
         const Tile T = tile_of(A, t, hx, hy, hz);
         Walk wb;
         wb.init(threadIdx.x, T.tx, T.ty);
@@ -1100,11 +1104,10 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
     (void)sm;
 }
 
-__global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_constant__ LzArgs A) {
-    extern __shared__ double2 dyn[];
-    __shared__ LzSmem sm;
-    const bool control = blockIdx.x == 0;
-    const bool has_tile = !control && (int)blockIdx.x - 1 < A.ntiles;
+// The launch's work for one problem, run by CTAs cta0 .. cta0 + ncta - 1.
+__device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSmem& sm) {
+    const bool control = lz_bid(A) == 0;
+    const bool has_tile = !control && lz_bid(A) - 1 < A.ntiles;
     const int hx = A.a[0] != 0.0 ? 1 : 0, hy = A.a[1] != 0.0 ? 1 : 0, hz = A.a[2] != 0.0 ? 1 : 0;
     const int ext_max = (A.tx + 2 * hx) * (A.ty + 2 * hy) * (A.tz + 2 * hz);
     Stage st;
@@ -1130,7 +1133,7 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
         const long long need = control ? (long long)stage_rows * A.K * 3 * 16
                                        : (long long)(A.resident ? 4 : 3) * ext_max * 16 + (long long)int_max * 8 +
                                              (A.resident ? 8LL * (ext_max - int_max) : 0LL);
-        if (!LZ_OK(need, (long long)dyn_bytes() + 1, LZ_SITE_SMEM) || !LZ_OK(gridDim.x, A.part_cap + 1, LZ_SITE_PART))
+        if (!LZ_OK(need, (long long)dyn_bytes() + 1, LZ_SITE_SMEM) || !LZ_OK(lz_nct(A), A.part_cap + 1, LZ_SITE_PART))
             return;
     }
 #endif
@@ -1181,7 +1184,7 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                 if (A.resident)
                     stage_resident(A, sm, st, u0, j, hx, hy, hz);
                 else
-                    stage_tile(A, st, u0, blockIdx.x - 1, j, hx, hy, hz);
+                    stage_tile(A, st, u0, lz_bid(A) - 1, j, hx, hy, hz);
             }
             if (j >= 1) {
                 // coefficients of sweep j-1, the same in every CTA
@@ -1313,8 +1316,8 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
             if (!control) {
                 float4 part;
                 sweep(A, sm, st, u0, j, hx, hy, hz, j >= 1, &part);
-                if (threadIdx.x == 0 && LZ_OK((j & 1) * gridDim.x + blockIdx.x, 2 * A.part_cap, LZ_SITE_PART))
-                    A.part[(size_t)(j & 1) * gridDim.x + blockIdx.x] = part;
+                if (threadIdx.x == 0 && LZ_OK((j & 1) * lz_nct(A) + lz_bid(A), 2 * A.part_cap, LZ_SITE_PART))
+                    A.part[(size_t)(j & 1) * lz_nct(A) + lz_bid(A)] = part;
             } else if (j >= 1) {
                 // the control CTA works one column behind: column c = j - 2 is
                 // complete once the norm of u_{j-1} (its subdiagonal) is known
@@ -1356,12 +1359,12 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
                     if (still == 0 && threadIdx.x == 0) __stcg(A.stop + s, c + 1);
                 }
             }
-            if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+            if (!grid_sync(A.bar, (unsigned)A.ncta, A.err, A.timeout_ns)) return;
             trace_mark(A, TR_LZ_SWEEP, &tcount);
         }
         // y_k and the coefficients of the final pass
         if (control) control_finish(A, sm, dyn, stage_rows, P, J, s, bnorm);
-        if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+        if (!grid_sync(A.bar, (unsigned)A.ncta, A.err, A.timeout_ns)) return;
         trace_mark(A, TR_LZ_SOLVE, &tcount);
         if (control && threadIdx.x == 0) {
             // (the control CTA is idle during the final pass)
@@ -1414,10 +1417,49 @@ __global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_const
             }
         }
         if (s + 1 < A.nsub) {
-            if (!grid_sync(A.bar, A.err, A.timeout_ns)) return;
+            if (!grid_sync(A.bar, (unsigned)A.ncta, A.err, A.timeout_ns)) return;
             trace_mark(A, TR_LZ_SUM, &tcount);
         }
     }
+}
+
+__global__ void __launch_bounds__(kLzBlock, 2) lanczos_kernel(const __grid_constant__ LzArgs A) {
+    extern __shared__ double2 dyn[];
+    __shared__ LzSmem sm;
+    lanczos_body(A, dyn, sm);
+}
+
+// Several problems in one launch: CTA c works for problem cta_prob[c], whose
+// descriptor (with the call's input and output states) it copies to shared
+// memory; each problem's CTAs synchronise only among themselves.
+__global__ void __launch_bounds__(kLzBlock, 2)
+    lanczos_batched_kernel(const LzArgs* __restrict__ args, const unsigned char* __restrict__ cta_prob,
+                           const __grid_constant__ LzIO io) {
+    extern __shared__ double2 dyn[];
+    __shared__ LzSmem sm;
+    __shared__ LzArgs a;
+    if (threadIdx.x == 0) {
+        const int p = cta_prob[blockIdx.x];
+        a = args[p];
+        a.in = io.in[p];
+        a.out = io.out[p];
+    }
+    __syncthreads();
+    lanczos_body(a, dyn, sm);
+}
+
+// Before a batched launch: every problem's barrier, error, work counters,
+// statistics and stop words (block p: problem p).
+__global__ void lanczos_reset_kernel(const LzArgs* __restrict__ args) {
+    const LzArgs& A = args[blockIdx.x];
+    if (threadIdx.x < 3) A.bar[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) *A.err = 0;
+    if (threadIdx.x < 2 && A.bytes != nullptr) A.bytes[threadIdx.x] = 0ull;
+    if (threadIdx.x < 4 && A.dbg != nullptr) A.dbg[threadIdx.x] = 0;
+    int* st = reinterpret_cast<int*>(A.stats);
+    const int words = (int)(A.K * sizeof(ItemStats) / sizeof(int));
+    for (int q = threadIdx.x; q < words; q += blockDim.x) st[q] = 0;
+    for (int q = threadIdx.x; q < A.nsub; q += blockDim.x) A.stop[q] = -1;
 }
 
 }  // namespace
@@ -1430,17 +1472,18 @@ size_t lanczos_smem_bytes(int tx, int ty, int tz, int hx, int hy, int hz, bool r
 }
 
 size_t lanczos_static_smem() {
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, lanczos_kernel) != cudaSuccess) return 0;
-    return fa.sharedSizeBytes;
+    cudaFuncAttributes fa, fb;
+    if (cudaFuncGetAttributes(&fa, lanczos_kernel) != cudaSuccess ||
+        cudaFuncGetAttributes(&fb, lanczos_batched_kernel) != cudaSuccess)
+        return 0;
+    return std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
 }
 
-int lanczos_max_grid(size_t smem, int device) {
+int lanczos_max_grid(size_t smem, int device, bool batched) {
     int per_sm = 0, sms = 0;
-    if (cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lanczos_kernel, kLzBlock, smem) != cudaSuccess)
-        return -1;
+    const void* k = batched ? (const void*)lanczos_batched_kernel : (const void*)lanczos_kernel;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kLzBlock, smem) != cudaSuccess) return -1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return -1;
     return per_sm * sms;
 }
@@ -1450,6 +1493,21 @@ cudaError_t launch_lanczos(const LzArgs& args, int grid, size_t smem, cudaStream
     if (e != cudaSuccess) return e;
     void* params[] = {(void*)&args};
     return cudaLaunchCooperativeKernel((const void*)lanczos_kernel, dim3(grid), dim3(kLzBlock), params, smem, stream);
+}
+
+cudaError_t lanczos_reset(const LzArgs* d_args, int B, cudaStream_t stream) {
+    lanczos_reset_kernel<<<B, 128, 0, stream>>>(d_args);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_batched(const LzArgs* d_args, const unsigned char* d_cta_prob, const LzIO& io, int grid,
+                                   size_t smem, cudaStream_t stream) {
+    cudaError_t e =
+        cudaFuncSetAttribute(lanczos_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* params[] = {(void*)&d_args, (void*)&d_cta_prob, (void*)&io};
+    return cudaLaunchCooperativeKernel((const void*)lanczos_batched_kernel, dim3(grid), dim3(kLzBlock), params, smem,
+                                       stream);
 }
 
 }  // namespace rexi

@@ -82,13 +82,27 @@ struct LzArgs {
     unsigned long long* trace; // optional [1 + 2 cap]: (phase, ns) at every barrier
     int trace_cap;
     unsigned long long* bytes; // [2]: algorithmic bytes and FP64 flops of the launch (added by the control CTA)
-    int part_cap;              // slots per parity of part (>= grid)
+    int part_cap;              // slots per parity of part (>= ncta)
+    int cta0, ncta;            // the CTAs of the launch that work for this problem
     long long* dbg;            // REXI_DEBUG builds: [4] first failed check (site, index, extent), count
     int dbg_trip;              // REXI_DEBUG builds: a site whose every check fails (0: none)
 };
 
+// Input and output states of a batched launch (problem p: in[p], out[p]).
+struct LzIO {
+    const double2* in[kMaxBatch];
+    double2* out[kMaxBatch];
+};
+
 cudaError_t launch_lanczos(const LzArgs& args, int grid, size_t smem, cudaStream_t stream);
-int lanczos_max_grid(size_t smem, int device);      // co-resident CTAs (<= 0: error)
+// Several problems in one cooperative launch: d_args[p] (device) describes
+// problem p with its CTA range; d_cta_prob[c] (device) is the problem of CTA c.
+cudaError_t launch_lanczos_batched(const LzArgs* d_args, const unsigned char* d_cta_prob, const LzIO& io, int grid,
+                                   size_t smem, cudaStream_t stream);
+// Zero the barrier, error, work and statistics words and clear the stop words
+// of the B problems of d_args (device), before a batched launch.
+cudaError_t lanczos_reset(const LzArgs* d_args, int B, cudaStream_t stream);
+int lanczos_max_grid(size_t smem, int device, bool batched = false);   // co-resident CTAs (<= 0: error)
 size_t lanczos_smem_bytes(int tx, int ty, int tz, int hx, int hy, int hz, bool resident);
 size_t lanczos_static_smem();                       // static shared memory of the kernel (0: error)
 

@@ -9,8 +9,8 @@ times (one persistent launch per step, default options of the plan).
   a plane wave through the whole step against the scalar rational, and the
   norm bound of the approximation;
 * 64 batched 2D problems with sides from {128, 192, 256, 384}: one batched
-  launch against the single-problem launches, the smallest ones against the
-  oracle;
+  launch (item engine, and Lanczos kernel) against the single-problem launches,
+  the smallest ones against the oracle;
 * the learnable-potential 256^2 problem: loss and dL/dV of a 2-step evolution
   towards a fixed packet against the oracle's adjoint recursion, and the
   adjoint dot-product identity over the 10 steps of the workload.
@@ -227,6 +227,32 @@ def test_batched_64_problems():
                             tol=1e-14)
         err = relerr(outs[i].cpu().numpy(), ref)
         log_parity("batched_64_problem[%d]" % i, err, 1e-6)
+        assert err < 1e-6
+
+
+def test_batched_64_problems_lanczos():
+    # the same 64 problems as Lanczos plans (FP64) in one launch of the
+    # Lanczos kernel, CTAs divided among the problems: against the single
+    # launches and, for the smallest two, the oracle
+    cfg = wl.config_batched()
+    from paper_1912_03312_gb300 import step_batched
+    probs = cfg["problems"]
+    orcs = [OraclePlan(p["grid"], p["V"], cfg["dt"], cfg["K"], 68.0) for p in probs]
+    plans = [_plan(cfg, p["grid"], p["V"], cfg["K"], precision="fp64", ortho="lanczos") for p in probs]
+    psis = [to_dev(p["psi0"]) for p in probs]
+    singles = [pl.step(ps).cpu().numpy() for pl, ps in zip(plans, psis)]
+    outs, sts = step_batched(plans, psis, stats=True)
+    assert all(s["status"] == 0 for s in sts)
+    for o, s1 in zip(outs, singles):
+        assert relerr(o.cpu().numpy(), s1) < 1e-6
+    sizes = [int(np.prod(p["grid"]["n"])) for p in probs]
+    for i in sorted(range(len(probs)), key=lambda i: sizes[i])[:2]:
+        p = probs[i]
+        orc = orcs[i]
+        ref, _ = ostep.step(p["V"], orc.h, p["psi0"], orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0,
+                            tol=1e-14)
+        err = relerr(outs[i].cpu().numpy(), ref)
+        log_parity("batched_64_problem_lanczos[%d]" % i, err, 1e-6)
         assert err < 1e-6
 
 

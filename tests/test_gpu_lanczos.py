@@ -12,7 +12,7 @@ with tol chosen so that bound stays below the metric's 1e-6; plane wave and
 zero state at 512^2; states far outside the FP32 range (scale invariance);
 NaN input, too few iterations, the bounded waits, graph
 capture, reproducibility, in place, host buffers, the adjoint on the item
-engine, and tile settings.
+engine, tile settings, and several problems in one batched launch.
 """
 
 import numpy as np
@@ -245,8 +245,44 @@ def test_lanczos_plan_adjoint_and_batched_rules():
     # forward still on the Lanczos kernel after the adjoint workspace exists
     out, st = lp.step(to_dev(psi), stats=True)
     assert st["status"] == 0
-    with pytest.raises(RexiError):
-        step_batched([lp], [to_dev(psi)])
+    # a batch must not mix Lanczos and item-engine plans, nor repeat a plan
+    le = library_plan(g, V, dt, K, R1, precision="fp64", tol=1e-13)
+    for plans in ([lp, le], [le, lp], [lp, lp]):
+        with pytest.raises(RexiError):
+            step_batched(plans, [to_dev(psi)] * len(plans))
+
+
+def test_lanczos_batched_matches_singles_and_oracle():
+    # several problems (1D, 2D, 3D; K = 16 and 32; different substep counts)
+    # in one launch of the Lanczos kernel, each on its share of the CTAs:
+    # every step agrees with the problem's single launch and with the oracle
+    # to the step bound, repeats bit for bit, and leaves the plans usable alone
+    from paper_1912_03312_gb300 import step_batched
+    cases = [((300,), 8.0, 16, 24.0, 1.0), ((130, 101), 8.0, 16, 24.0, 0.5), ((96, 80), 8.0, 32, 68.0, 0.5),
+             ((20, 18, 14), 8.0, 16, 24.0, 0.3), ((64, 48), 8.0, 16, 24.0, 0.5), ((2, 17), 6.0, 8, 8.0, 0.3)]
+    plans, psis, singles, refs, bounds = [], [], [], [], []
+    for i, (n, box, K, R1, dt) in enumerate(cases):
+        g, V, psi = wl.random_problem(130 + i, n, box=box)
+        orc = OraclePlan(g, V, dt, K, R1)
+        tol = solve_tol(orc.A * orc.n_sub)
+        lp = lz_plan(g, V, dt, K, R1, tol=tol)
+        plans.append(lp)
+        psis.append(to_dev(psi))
+        singles.append(lp.step(to_dev(psi)).cpu().numpy())
+        refs.append(ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)[0])
+        bounds.append(step_bound(orc.A * orc.n_sub, tol, "fp64"))
+    outs, sts = step_batched(plans, psis, stats=True)
+    for i, (o, s_, r, b) in enumerate(zip(outs, sts, refs, bounds)):
+        assert s_["status"] == 0, (i, s_["status"])
+        o = o.cpu().numpy()
+        err = relerr(o, r)
+        log_parity("lanczos_batched[%s]" % "x".join(map(str, cases[i][0])), err, b)
+        assert err < b, (i, err, b)
+        assert relerr(o, singles[i]) < b, i
+    again = step_batched(plans, psis)
+    assert all(np.array_equal(a.cpu().numpy(), o.cpu().numpy()) for a, o in zip(again, outs))
+    for lp, p_, s1 in zip(plans, psis, singles):
+        assert np.array_equal(lp.step(p_).cpu().numpy(), s1)
 
 
 def test_lanczos_work_counts():
