@@ -242,7 +242,7 @@ int rexi_cheb_step(rexi_plan* plan, const void* psi_in, void* psi_out, double to
  * the same device, distinct, and either all item-engine plans with the same
  * precision, restart length and orthogonalisation, or all Lanczos plans
  * (ortho = 2); B <= 128.  For Lanczos plans the launch divides its CTAs among
- * the problems in proportion to their points (a control CTA and at least one
+ * the problems in proportion to points x substeps (a control CTA and at least one
  * tile CTA each, so B <= the CTAs of the launch / 2), chooses every problem's
  * tile boxes for its share, and each problem synchronises only its own CTAs;
  * every plan's own workspace is used.  The first call with a combination of

@@ -740,7 +740,7 @@ rexi::LzArgs lz_args(rexi_plan* p, int mode, const void* in, void* out, const Lz
 }
 
 // One step of several problems in one launch of the Lanczos kernel: the CTAs
-// are divided among the problems in proportion to their points (each problem
+// are divided among the problems in proportion to their work (each problem
 // gets a control CTA and at least one tile CTA), every problem's tile boxes are
 // chosen for its share, and every problem synchronises only its own CTAs.
 // The descriptors are cached in the first plan, keyed like the item engine's.
@@ -758,13 +758,13 @@ int lz_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in, v
     if (p0->lzb_key != key || p0->lzb_gens != gens || !p0->d_lzb_args) {
         int G = cps * sms;
         if (G < 2 * B) return REXI_EINVAL;                  // a control and a tile CTA per problem
-        // CTAs in proportion to the points, at least two per problem
+        // CTAs in proportion to the work (points x substeps), at least two per problem
         long long N = 0;
-        for (int b = 0; b < B; ++b) N += plans[b]->n;
+        for (int b = 0; b < B; ++b) N += (long long)plans[b]->n * plans[b]->n_sub;
         std::vector<int> nct(B);
         int used = 0;
         for (int b = 0; b < B; ++b) {
-            nct[b] = 2 + (int)((long long)(G - 2 * B) * plans[b]->n / N);
+            nct[b] = 2 + (int)((long long)(G - 2 * B) * plans[b]->n * plans[b]->n_sub / N);
             used += nct[b];
         }
         for (int b = 0; used < G; b = (b + 1) % B, ++used) ++nct[b];
