@@ -93,34 +93,31 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
 }
 
 // All `count` CTAs that share `bar` (a co-resident grid, or one problem's range
-// of CTAs in a batched launch) meet here.  bar[0] counts arrivals and
-// bar[1] completed barriers; both are zeroed before every launch.  The arrival
-// that makes the count a multiple of the grid size publishes the barrier's
-// number with a release store; the others poll it with acquire loads.  Every
-// wait is bounded by timeout_ns: on expiry the sticky error word is set.  A
-// wait also ends when another CTA has set the error word (it may have left the
-// kernel and never arrive).  The function returns false whenever the error
+// of CTAs in a batched launch) meet here.  bar[0] counts arrivals and is zeroed
+// before every launch; `gen` is the calling CTA's count of barriers passed
+// (thread 0's copy is the one used).  Every CTA adds one to bar[0] with a
+// release reduction -- after the CTA barrier, it orders all of the CTA's
+// earlier writes before the arrival -- and then waits with acquire loads until
+// the count reaches gen x count: every arrival is a release heading a release
+// sequence that contains the later arrivals, so reading the final count
+// synchronises with all of them, and no CTA has to publish for the others.
+// Every wait is bounded by timeout_ns: on expiry the sticky error word is set.
+// A wait also ends when another CTA has set the error word (it may have left
+// the kernel and never arrive).  The function returns false whenever the error
 // word is set, so every CTA leaves the kernel at its next barrier.
-__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned count, int* err, unsigned long long timeout_ns) {
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned count, unsigned& gen, int* err,
+                                          unsigned long long timeout_ns) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned* arrived = bar;
-        unsigned* done = bar + 1;
-        __threadfence();                                   // the CTA's writes before its arrival
-        const unsigned prev = atomicAdd(arrived, 1u);
-        const unsigned target = prev / count + 1u;
-        if (prev + 1u == target * count) {
-            __threadfence();
-            st_release_u32(done, target);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while ((int)(ld_acquire_u32(done) - target) < 0) {
-                if (*(volatile int*)err != 0) break;
-                if (global_ns() - t0 > timeout_ns) {
-                    atomicExch(err, kErrTimeout);
-                    break;
-                }
-                __nanosleep(32);
+        gen += 1u;
+        const unsigned target = gen * count;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        const unsigned long long t0 = global_ns();
+        while ((int)(ld_acquire_u32(bar) - target) < 0) {
+            if (*(volatile int*)err != 0) break;
+            if (global_ns() - t0 > timeout_ns) {
+                atomicExch(err, kErrTimeout);
+                break;
             }
         }
     }

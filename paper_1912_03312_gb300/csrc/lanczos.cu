@@ -1106,6 +1106,7 @@ __device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int 
 
 // The launch's work for one problem, run by CTAs cta0 .. cta0 + ncta - 1.
 __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSmem& sm) {
+    unsigned bar_gen = 0;                // grid barriers this CTA has passed (thread 0)
     const bool control = lz_bid(A) == 0;
     const bool has_tile = !control && lz_bid(A) - 1 < A.ntiles;
     const int hx = A.a[0] != 0.0 ? 1 : 0, hy = A.a[1] != 0.0 ? 1 : 0, hz = A.a[2] != 0.0 ? 1 : 0;
@@ -1359,12 +1360,12 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                     if (still == 0 && threadIdx.x == 0) __stcg(A.stop + s, c + 1);
                 }
             }
-            if (!grid_sync(A.bar, (unsigned)A.ncta, A.err, A.timeout_ns)) return;
+            if (!grid_sync(A.bar, (unsigned)A.ncta, bar_gen, A.err, A.timeout_ns)) return;
             trace_mark(A, TR_LZ_SWEEP, &tcount);
         }
         // y_k and the coefficients of the final pass
         if (control) control_finish(A, sm, dyn, stage_rows, P, J, s, bnorm);
-        if (!grid_sync(A.bar, (unsigned)A.ncta, A.err, A.timeout_ns)) return;
+        if (!grid_sync(A.bar, (unsigned)A.ncta, bar_gen, A.err, A.timeout_ns)) return;
         trace_mark(A, TR_LZ_SOLVE, &tcount);
         if (control && threadIdx.x == 0) {
             // (the control CTA is idle during the final pass)
@@ -1417,7 +1418,7 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
             }
         }
         if (s + 1 < A.nsub) {
-            if (!grid_sync(A.bar, (unsigned)A.ncta, A.err, A.timeout_ns)) return;
+            if (!grid_sync(A.bar, (unsigned)A.ncta, bar_gen, A.err, A.timeout_ns)) return;
             trace_mark(A, TR_LZ_SUM, &tcount);
         }
     }
