@@ -865,9 +865,13 @@ __device__ void final_pass(const LzArgs& A, const LzSmem& sm, double up, const d
                     if (!LZ_OK(g[q], A.n, LZ_SITE_STATE)) on[q] = false;
                 }
             }
-            // copies of vector r into slot b (one commit group, possibly empty)
-            auto issue = [&](int r, int b) {
-                if (depth > 0 && r < J && LZ_OK(r, A.m + 3, LZ_SITE_BASIS)) {
+            // the vectors newest first (the last ones written are the likeliest
+            // still in L2): the k-th vector streamed is r = J - 1 - k
+            const int nv = J - rb;
+            // copies of the k-th vector into slot b (one commit group, possibly empty)
+            auto issue = [&](int kv, int b) {
+                const int r = J - 1 - kv;
+                if (depth > 0 && kv < nv && LZ_OK(r, A.m + 3, LZ_SITE_BASIS)) {
                     const double2* u = uvec(A, u0, r);
 #pragma unroll
                     for (int q = 0; q < kCh; ++q)
@@ -875,7 +879,7 @@ __device__ void final_pass(const LzArgs& A, const LzSmem& sm, double up, const d
                 }
                 cp_async_commit();
             };
-            for (int b = 0; b + 1 < depth; ++b) issue(rb + b, b);
+            for (int b = 0; b + 1 < depth; ++b) issue(b, b);
             float rh[kCh], rl[kCh], ih[kCh], il[kCh];
             double2 acc[kCh];
 #pragma unroll
@@ -883,12 +887,12 @@ __device__ void final_pass(const LzArgs& A, const LzSmem& sm, double up, const d
                 rh[q] = rl[q] = ih[q] = il[q] = 0.f;
                 acc[q] = make_double2(0.0, 0.0);
             }
-            for (int r = rb; r < J; ++r) {
+            for (int k = 0; k < nv; ++k) {
+                const int r = J - 1 - k;
                 if (!LZ_OK(r, kLzMaxM, LZ_SITE_Y) || !LZ_OK(r, A.m + 3, LZ_SITE_BASIS)) break;
-                const int k = r - rb;
                 int b = 0;
                 if (depth > 0) {
-                    issue(r + depth - 1, (k + depth - 1) % depth);
+                    issue(k + depth - 1, (k + depth - 1) % depth);
                     cp_async_wait_upto(depth - 1);
                     b = k % depth;
                 }

@@ -7,6 +7,8 @@ Started by tests/test_gpu_debug_checks.py in a child process with REXI_DEBUG=1
 * every case runs with status 0, no failed check recorded, and the step (or
   each pole's solution) agrees with the oracle to the bounds of the release
   tests: steps to max(1e-10, 2 A tol), poles to 1e-10;
+* a batched launch of several of these problems (each on its share of the
+  CTAs) runs with no failed check and agrees with the single launches;
 * for every check site s = 1 .. 11 made to fail (rexi_plan_debug_trip), the
   launch ends with REXI_EBOUNDS and the record names s; afterwards the same
   plan, with no site tripped, reproduces the clean result bit for bit.
@@ -96,6 +98,24 @@ def main():
             worst = max(worst, relerr(x[k], xo))
         out["poles"].append({"case": "x".join(map(str, n)), "max_err": worst})
         assert worst < 1e-10, (n, worst)
+    # several problems in one batched launch (each on its own range of CTAs)
+    from paper_1912_03312_gb300 import step_batched
+    bplans, bpsis, bsingle, bbound = [], [], [], []
+    for i, (n, box, K, R1, dt, tiles) in enumerate(STEP_CASES[:6]):
+        g, V, psi = wl.random_problem(140 + i, n, box=box)
+        orc = OraclePlan(g, V, dt, K, R1)
+        tol = solve_tol(orc.A * orc.n_sub)
+        lp = plan(g, V, dt, K, R1, tol=tol)
+        bplans.append(lp)
+        bpsis.append(to_dev(psi))
+        bsingle.append(lp.step(to_dev(psi)).cpu().numpy())
+        bbound.append(step_bound(orc.A * orc.n_sub, tol, "fp64"))
+    bouts, bsts = step_batched(bplans, bpsis, stats=True)
+    for i, (o, st_, lp) in enumerate(zip(bouts, bsts, bplans)):
+        rec = record(lp)
+        assert st_["status"] == 0 and rec == [0, 0, 0, 0], (i, st_["status"], rec)
+        assert relerr(o.cpu().numpy(), bsingle[i]) < bbound[i], i
+    out["batched"] = {"problems": len(bplans), "records": "clean"}
     # every site made to fail: REXI_EBOUNDS with the site recorded, then recovery
     g, V, psi = wl.random_problem(94, (130, 101), box=8.0)
     lp = plan(g, V, 0.5, 16, 24.0, tol=1e-13)

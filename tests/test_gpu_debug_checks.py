@@ -36,5 +36,6 @@ def test_debug_build_runs_clean_and_reports_every_site():
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
     out = json.loads(r.stdout.strip().splitlines()[-1])
     assert len(out["steps"]) >= 10 and all(c["record"] == [0, 0, 0, 0] for c in out["steps"])
+    assert out["batched"]["records"] == "clean"
     assert {t["site"] for t in out["trips"]} == set(N.LZ_SITES)
     assert all(t["status"] == N.REXI_EBOUNDS and t["recovered"] for t in out["trips"])
