@@ -125,9 +125,6 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -185,33 +182,27 @@ __device__ bool mbar_wait(unsigned long long* b, unsigned parity, int* err, unsi
 }
 
 // All CTAs of the co-resident (cooperative) grid meet here.  bar[0] counts
-// arrivals and bar[1] completed barriers; both are zeroed before every launch.
-// The arrival that makes the count a multiple of the grid size completes
-// barrier count / G and publishes that number with a release store; every
-// other CTA waits until the published number reaches its own barrier's (the
-// count never resets, so no generation word has to be read before arriving).
-// Every wait is bounded by timeout_ns; on expiry the sticky error word is set
-// and every CTA leaves the kernel at its next barrier.  Returns false when the
-// launch must end.
+// arrivals and is zeroed before every launch (the count never resets, so the
+// barrier a CTA is at follows from the count its arrival returns).  Each CTA
+// publishes its earlier writes with a fence and arrives with an atomic add,
+// then waits with acquire loads until the count reaches the end of its
+// barrier: the arrivals form a release sequence, so reading the final count
+// synchronises with all of them and no CTA has to publish for the others.
+// Every wait is bounded by timeout_ns; on expiry the sticky error word is set,
+// a wait also ends when another CTA has set it, and every CTA leaves the
+// kernel at its next barrier.  Returns false when the launch must end.
 __device__ bool grid_sync(unsigned* bar, int* err, unsigned long long timeout_ns) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned* count = bar;
-        unsigned* done = bar + 1;
         __threadfence();                                   // the CTA's writes before its arrival
-        const unsigned prev = atomicAdd(count, 1u);
-        const unsigned target = prev / gridDim.x + 1u;     // the barrier this arrival belongs to
-        if (prev + 1u == target * gridDim.x) {
-            __threadfence();
-            st_release_u32(done, target);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while ((int)(ld_acquire_u32(done) - target) < 0) {
-                if (global_ns() - t0 > timeout_ns) {
-                    atomicExch(err, kErrTimeout);
-                    break;
-                }
-                __nanosleep(32);
+        const unsigned prev = atomicAdd(bar, 1u);
+        const unsigned target = (prev / gridDim.x + 1u) * gridDim.x;   // arrivals that end this barrier
+        const unsigned long long t0 = global_ns();
+        while ((int)(ld_acquire_u32(bar) - target) < 0) {
+            if (*(volatile int*)err != 0) break;
+            if (global_ns() - t0 > timeout_ns) {
+                atomicExch(err, kErrTimeout);
+                break;
             }
         }
     }
