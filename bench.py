@@ -37,6 +37,7 @@ METRIC = "REXI steps/s and grid-pts×poles/s at ≤1e-6 rel err vs FP64; % HBM r
 WORKLOAD = "2d_wells_512x512_K32_dt0.5"
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_FP64_TFLOPS = 1.25      # GB300 FP64 (non-tensor), nominal: no measured figure exists
+NOMINAL_FP32_TOPS = 152 * 128 * 2.07e9 / 1e12   # FP32-pipe instructions per lane and second: 152 SMs x 128 x 2070 MHz
 
 
 def parse_args():
@@ -45,7 +46,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "df64"], default="df64",
+                    help="df64 (default): the Lanczos recurrence in double-float pairs on the FP32 pipe")
     ap.add_argument("--ortho", choices=["lanczos", "dcgs2", "cgs2"], default="lanczos",
                     help="lanczos: the shared-basis Lanczos kernel; dcgs2/cgs2: the item engine")
     ap.add_argument("--window", type=int, default=2,
@@ -176,10 +178,12 @@ def kernel_name(args, ctas_per_sm=0):
 
 
 def roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, independent_bytes, flops_per_step, ms,
-             ctas_per_sm=0):
-    """The kernel of the timed path against HBM (kernel-counted bytes) and, for
-    the FP64 path, against the FP64 ALU (kernel-counted flops); the roof it is
-    nearer is reported, the other beside it."""
+             ctas_per_sm=0, ops32_per_step=0.0):
+    """The kernel of the timed path against HBM (kernel-counted bytes) and
+    against its ALU: the FP64 unit for the FP64 path (kernel-counted flops),
+    the FP32 pipe for the double-float path (kernel-counted FP32-pipe
+    instructions per lane); the roof it is nearer is reported, the other
+    beside it."""
     kernel = "%s (one launch per step)" % kernel_name(args, ctas_per_sm)
     hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
            "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
@@ -193,7 +197,16 @@ def roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, independe
            "peak_kind": "nominal FP64 (152 SMs x 2 FMA/clk x 2070 MHz)", "kernel": kernel,
            "fp64_flops_per_launch": flops_per_step,
            "flops_source": "kernel count of the FP64 arithmetic of its passes (FMA = 2)"}
-    if args.precision == "fp64" and alu["frac"] > hbm["frac"]:
+    if args.precision == "df64":
+        t32 = ops32_per_step / (ms * 1e-3) / 1e12
+        alu = {"bound": "alu", "achieved": t32, "peak": NOMINAL_FP32_TOPS, "unit": "TOP/s",
+               "frac": t32 / NOMINAL_FP32_TOPS, "traffic": traffic,
+               "peak_kind": "nominal FP32 pipe (152 SMs x 128 lanes x 2070 MHz, one instruction per lane "
+                            "and clock)", "kernel": kernel, "fp32_ops_per_launch": ops32_per_step,
+               "fp64_flops_per_launch": flops_per_step,
+               "ops_source": "kernel count of the FP32-pipe arithmetic instructions of its passes "
+                             "(double-float recurrence, compensated sums, final pass)"}
+    if args.precision != "mixed" and alu["frac"] > hbm["frac"]:
         alu["other"] = hbm
         return alu
     hbm["other"] = alu
@@ -459,12 +472,16 @@ def _timed_ms(fn, flush, stream, warm=2, nt=5):
     return tot / nt
 
 
-def _work_line(name, ms, units_per_call, n_pts_poles, bytes_, flops, extra=None):
+def _work_line(name, ms, units_per_call, n_pts_poles, bytes_, flops, extra=None, ops32=0.0):
     d = {"ms_per_step": ms, "steps_per_s": units_per_call * 1000.0 / ms,
          "grid_pts_poles_per_s": n_pts_poles * 1000.0 / ms,
          "fp64_tflops": flops / (ms * 1e-3) / 1e12, "fp64_frac_of_nominal": flops / (ms * 1e-3) / 1e12 /
          NOMINAL_FP64_TFLOPS, "gbs": bytes_ / (ms * 1e-3) / 1e9,
          "counts": "kernel-counted bytes and FP64 flops of the launches"}
+    if ops32:
+        d["fp32_pipe_tops"] = ops32 / (ms * 1e-3) / 1e12
+        d["fp32_pipe_frac_of_nominal"] = d["fp32_pipe_tops"] / NOMINAL_FP32_TOPS
+        d["counts"] = "kernel-counted bytes, FP64 flops and FP32-pipe instructions of the launches"
     if extra:
         d.update(extra)
     return d
@@ -478,7 +495,9 @@ def other_workloads(args, flush, stream, dev):
     (one graph-captured batched launch of the item engine in the workload's
     mixed precision, 64 graph-captured single launches of the Lanczos kernel,
     and one graph-captured batched launch of the Lanczos kernel), and the
-    learnable 256^2 problem (forward step plus adjoint)."""
+    learnable 256^2 problem (forward step plus adjoint); C3 and the batched
+    Lanczos launch of C4 with the recurrence in double-float pairs and in
+    FP64."""
     import numpy as np
     import torch
     import workloads as wl
@@ -510,26 +529,33 @@ def other_workloads(args, flush, stream, dev):
     res["c1_1d_harmonic_N256_K16"] = line
     del p
 
-    # C3: 3D softened Coulomb, 128^3, K=32, dt=0.25, states evolving
+    # C3: 3D softened Coulomb, 128^3, K=32, dt=0.25, states evolving; the
+    # Lanczos kernel with the recurrence in double-float pairs (the workload's
+    # mixed precision) and in FP64
     cfg = wl.config_3d_coulomb()
     g = cfg["grid"]
-    p = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], 32, precision="fp64", ortho="lanczos")
-    info = p.info()
     n = int(np.prod(g["n"]))
-    bufs = [torch.from_numpy(cfg["psi0"]).to(dev), None]
-    bufs[1] = torch.empty_like(bufs[0])
+    lines = {}
+    for prec in ("df64", "fp64"):
+        p = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], 32, precision=prec, ortho="lanczos")
+        info = p.info()
+        bufs = [torch.from_numpy(cfg["psi0"]).to(dev), None]
+        bufs[1] = torch.empty_like(bufs[0])
 
-    def step3():                        # the state evolves: ping-pong between two buffers
-        p.step(bufs[0], out=bufs[1])
-        bufs.reverse()
-    _, st = p.step(bufs[0], stats=True)
-    ms = _timed_ms(step3, flush, stream, nt=5)
-    res["c3_3d_coulomb_128cube_K32"] = _work_line(
-        "c3", ms, 1, n * 32 * info["n_sub"], st["bytes"], st["flops64"],
-        {"workload": "3d_coulomb_128cube (K=32; K=64 refused: double-double plan arithmetic)",
-         "n_sub": info["n_sub"], "R1": info["R1"], "krylov_columns_max": st["max_iters_seen"],
-         "path": "Lanczos kernel, FP64", "parity": "tests: per-pole 1e-10 at 128^3, plane wave"})
-    del p, bufs
+        def step3():                    # the state evolves: ping-pong between two buffers
+            p.step(bufs[0], out=bufs[1])
+            bufs.reverse()
+        _, st = p.step(bufs[0], stats=True)
+        ms = _timed_ms(step3, flush, stream, nt=5)
+        lines[prec] = _work_line(
+            "c3", ms, 1, n * 32 * info["n_sub"], st["bytes"], st["flops64"],
+            {"workload": "3d_coulomb_128cube (K=32; K=64 refused: double-double plan arithmetic)",
+             "n_sub": info["n_sub"], "R1": info["R1"], "krylov_columns_max": st["max_iters_seen"],
+             "path": "Lanczos kernel, " + ("recurrence in double-float pairs" if prec == "df64" else "FP64"),
+             "parity": "tests: per-pole 1e-10 at 128^3, plane wave"}, st["ops32"])
+        del p, bufs
+    lines["df64"]["lanczos_fp64"] = lines["fp64"]
+    res["c3_3d_coulomb_128cube_K32"] = lines["df64"]
 
     # C4: 64 uneven 2D problems
     cfg = wl.config_batched()
@@ -583,18 +609,34 @@ def other_workloads(args, flush, stream, dev):
         "path": "one graph-captured batched launch of the Lanczos kernel, FP64 (CTAs divided among the problems)",
         "rel_diff_vs_singles": max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
                                    for a, b in zip(outs_b, outs))}
+    # the same batched launch with the recurrence in double-float pairs
+    dplans = [Plan(q["grid"]["n"], q["grid"]["lo"], q["grid"]["hi"], q["V"], cfg["dt"], cfg["K"], precision="df64",
+                   ortho="lanczos") for q in probs]
+    outs_d = [torch.empty_like(t) for t in ins]
+    step_batched(dplans, ins, outs_d)
+    torch.cuda.synchronize()
+    graph_d = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph_d):
+        step_batched(dplans, ins, outs_d)
+    ms_d = _timed_ms(graph_d.replay, flush, stream, nt=5)
+    line["lanczos_batched_df64"] = {
+        "ms_per_step": ms_d, "steps_per_s": 1000.0 / ms_d, "grid_pts_poles_per_s": work * 1000.0 / ms_d,
+        "path": "one graph-captured batched launch of the Lanczos kernel, recurrence in double-float pairs",
+        "rel_diff_vs_fp64_batched": max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+                                        for a, b in zip(outs_d, outs_b))}
     if not args.no_oracle_check:
         try:
             ref_np, _ = oracle_first_step(68.0, cores, "c4:%d" % smallest)
             for key, got in (("rel_err_vs_oracle", batched_first), ("lanczos_rel_err_vs_oracle", outs[smallest]),
-                             ("lanczos_batched_rel_err_vs_oracle", outs_b[smallest])):
+                             ("lanczos_batched_rel_err_vs_oracle", outs_b[smallest]),
+                             ("lanczos_batched_df64_rel_err_vs_oracle", outs_d[smallest])):
                 got = got.cpu().numpy().ravel()
                 line[key] = float(np.linalg.norm(got - ref_np.ravel()) / np.linalg.norm(ref_np))
             line["oracle_problem"] = "the smallest problem (%s)" % "x".join(map(str, probs[smallest]["grid"]["n"]))
         except Exception as e:  # reported, not fatal
             line["rel_err_vs_oracle"] = "failed: %s" % e
     res["c4_batched_64x2d_K32"] = line
-    del lplans, graph, graph_b, ins, outs, outs_b
+    del lplans, dplans, graph, graph_b, graph_d, ins, outs, outs_b, outs_d
 
     # C5: learnable potential, forward step + adjoint (10 steps each way)
     cfg = wl.config_learnable()
@@ -715,15 +757,17 @@ def ours(args):
     # kernel's own count of the bytes its passes move, and the count of the
     # independent-pole method for context
     cur = psi0.clone()
-    alg, indep, flops = [], [], []
+    alg, indep, flops, ops32 = [], [], [], []
     for i in range(args.steps):
         cur, st = plan.step(cur, stats=True)
         alg.append(st["bytes"])
         flops.append(st["flops64"])
+        ops32.append(st["ops32"])
         indep.append(algorithmic_bytes(st, n, K, s_bytes, info["n_sub"]))
         stats.append(st)
     bytes_per_step = statistics.mean(alg)
     flops_per_step = statistics.mean(flops)
+    ops32_per_step = statistics.mean(ops32)
     independent_bytes = statistics.mean(indep)
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_per_step / (ms * 1e-3) / 1e9
@@ -732,6 +776,7 @@ def ours(args):
     # accuracy against the FP64 path with full orthogonalisation (one step), and
     # the other paths of the plan timed the same way
     extra = {}
+    other_first = None                  # the first step of the Lanczos kernel in the other arithmetic
     if not args.no_fp64_path and rank == 0:
         def timed(p, nt=3):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -769,6 +814,22 @@ def ours(args):
         if ref is None:                 # the timed path is the reference itself
             ref = out
         extra["rel_err_vs_fp64_full"] = float((out - ref).norm() / ref.norm())
+        if args.ortho == "lanczos":
+            # the Lanczos kernel in the other arithmetic (the plain FP64
+            # recurrence beside the double-float one, or the reverse)
+            other = "fp64" if args.precision == "df64" else "df64"
+            p2 = Plan(g["n"], g["lo"], g["hi"], cfg["V"], cfg["dt"], K, precision=other, R1=R1, ortho="lanczos",
+                      restart=restart)
+            if tuned:
+                autotune.apply(p2, tuned)
+            o2 = p2.step(psi0)
+            ms2 = timed(p2)
+            paths["lanczos_" + other] = {"ms_per_step": ms2, "steps_per_s": 1000.0 / ms2,
+                                         "rel_err_vs_fp64_full": float((o2 - ref).norm() / ref.norm()),
+                                         "rel_diff_vs_timed_path": float((o2 - out).norm() / out.norm()),
+                                         "tiles": "the timed path's"}
+            other_first = o2
+            del p2
         # the Chebyshev propagator the paper compares with (Sec. 4), same operator
         # and step, truncation 1e-10 (the FCF approximant's accuracy level)
         cheb_out, deg = plan.cheb_step(psi0, tol=1e-10)
@@ -856,6 +917,10 @@ def ours(args):
             ref_np, d = oracle_first_step(R1, host_cores(args.cpu_workers))
             got = first_out.cpu().numpy().reshape(-1)
             ref_np = ref_np.reshape(-1)
+            if other_first is not None:
+                o = other_first.cpu().numpy().reshape(-1)
+                extra["other_paths"][[k for k in extra["other_paths"] if k.startswith("lanczos_")][0]][
+                    "rel_err_vs_oracle"] = float(np.linalg.norm(o - ref_np) / np.linalg.norm(ref_np))
             oracle_check = {"rel_err_vs_oracle": float(np.linalg.norm(got - ref_np) / np.linalg.norm(ref_np)),
                             "oracle": "one user step of the oracle from the workload's initial state "
                                       "(GMRES(30), MGS, relative residual 1e-14 per pole, FP64)",
@@ -869,7 +934,7 @@ def ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "REXI steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64+c128" if args.precision == "mixed" else "c128",
+            "vs_baseline": None, "dtype": {"mixed": "c64+c128", "fp64": "c128", "df64": "df64+f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD if args.n == 512 else "2d_wells_%dx%d_K32_dt0.5" % (args.n, args.n),
                        "grid": list(g["n"]), "K": K, "dt": cfg["dt"], "n_sub": info["n_sub"],
@@ -881,7 +946,7 @@ def ours(args):
                        "autotuned": tuned},
             "grid_pts_poles_per_s": value * n * K * info["n_sub"],
             "roofline": roofline(args, achieved, peak, peak_kind, traffic, bytes_per_step, independent_bytes,
-                                 flops_per_step, ms, (tuned or {}).get("ctas_per_sm", 0)),
+                                 flops_per_step, ms, (tuned or {}).get("ctas_per_sm", 0), ops32_per_step),
             "cpu_baseline": cpu,
             "cpu_baseline_all_cores": cpu_all,
             "e2e": None if e2e_s is None else {"value": job_throughput(1, ws, e2e_s * 1e3), "unit": "REXI steps/s",

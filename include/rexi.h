@@ -54,6 +54,18 @@ extern "C" {
 #define REXI_MIXED  1   /* Krylov basis/matvecs/orthogonalisation in c64; FP64 for
                            the residual at every restart (iterative refinement),
                            the Hessenberg least squares and the pole sum          */
+#define REXI_DF64   2   /* ortho = 2 (Lanczos) only: the recurrence -- stencil,
+                           three-term update, inner products and the stored basis
+                           -- in double-float (pairs of floats, about 2^-47 per
+                           operation) on the FP32 pipe, from the second Krylov
+                           vector on; FP64 for the first sweep (any scale of psi),
+                           the tridiagonal matrix, every pole's least squares, the
+                           combined coefficients and the input state's term of
+                           the pole sum.  The recurrence's rounding enters psi'
+                           through the combined coefficients sum_k alpha_k y_k,
+                           not the individual weights, so its effect stays near
+                           1e-13 (the per-pole tolerance and the pole-sum
+                           amplification set the step error as in REXI_FP64)     */
 
 #define REXI_MAX_POLES   256
 #define REXI_MAX_RESTART 64   /* windowed bases; with full orthogonalisation 31 (delayed
@@ -71,7 +83,7 @@ typedef struct {
 } rexi_grid;
 
 typedef struct {
-    int    precision;      /* REXI_FP64 or REXI_MIXED (default REXI_MIXED)                */
+    int    precision;      /* REXI_FP64, REXI_MIXED (default) or REXI_DF64 (ortho = 2 only) */
     int    restart_m;      /* GMRES restart length (default 30): 1..REXI_MAX_RESTART with a
                               window, else 1..REXI_MAX_RESTART_FULL (32 with CGS2); with
                               ortho = 2 the largest Krylov dimension, 1..REXI_MAX_KRYLOV    */
@@ -101,8 +113,8 @@ typedef struct {
                               Schmidt with reorthogonalisation, one global reduction per step
                               (the previous vector is reorthogonalised and normalised together
                               with the projection of the new one); 0: CGS2, two reductions
-                              per step; 2: Lanczos -- REXI_FP64 only, window 0: every substep
-                              builds ONE basis for all K poles (the shifted-systems observation
+                              per step; 2: Lanczos -- REXI_FP64 or REXI_DF64, window 0: every
+                              substep builds ONE basis for all K poles (the shifted-systems observation
                               of Sec. 5) by the three-term recurrence of the real symmetric
                               tau (H - c) with real coefficients, one global reduction and one
                               grid barrier per step, no restarts: restart_m (up to
@@ -158,6 +170,10 @@ typedef struct {
                                          batched: the whole launch, in every entry        */
     double flops64;                   /* FP64 flops of the launch's arithmetic (an FMA is 2),
                                          counted the same way                              */
+    double ops32;                     /* FP32-pipe arithmetic instructions per lane of the
+                                         Lanczos kernel (compensated sums, double-float
+                                         recurrence and final pass), counted the same way;
+                                         0 on the item engine                             */
 } rexi_stats;
 
 typedef struct rexi_plan rexi_plan;   /* opaque, owned by the library */
@@ -241,7 +257,8 @@ int rexi_cheb_step(rexi_plan* plan, const void* psi_in, void* psi_out, double to
  * every problem are the independent tasks of Sec. 3.1).  All plans must be on
  * the same device, distinct, and either all item-engine plans with the same
  * precision, restart length and orthogonalisation, or all Lanczos plans
- * (ortho = 2); B <= 128.  For Lanczos plans the launch divides its CTAs among
+ * (ortho = 2; REXI_FP64 and REXI_DF64 plans may be mixed, each problem runs in
+ * its own arithmetic); B <= 128.  For Lanczos plans the launch divides its CTAs among
  * the problems in proportion to points x substeps (a control CTA and at least one
  * tile CTA each, so B <= the CTAs of the launch / 2), chooses every problem's
  * tile boxes for its share, and each problem synchronises only its own CTAs;

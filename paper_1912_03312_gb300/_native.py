@@ -24,6 +24,7 @@ REXI_EBOUNDS = -7
 REXI_WACCURACY = 1
 REXI_FP64 = 0
 REXI_MIXED = 1
+REXI_DF64 = 2
 REXI_MAX_POLES = 256
 REXI_MAX_RESTART = 64
 REXI_MAX_RESTART_FULL = 31
@@ -60,7 +61,7 @@ class Stats(C.Structure):
                 ("total_iters", C.c_int), ("total_cycles", C.c_int),
                 ("iters", C.c_int * REXI_MAX_POLES), ("cycles", C.c_int * REXI_MAX_POLES),
                 ("iters_sq", C.c_int * REXI_MAX_POLES), ("resid", C.c_double * REXI_MAX_POLES),
-                ("bytes", C.c_double), ("flops64", C.c_double)]
+                ("bytes", C.c_double), ("flops64", C.c_double), ("ops32", C.c_double)]
 
 
 _P = C.c_void_p

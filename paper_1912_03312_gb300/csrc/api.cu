@@ -76,7 +76,7 @@ struct rexi_plan {
     double2* d_hout = nullptr;
     unsigned* d_bar = nullptr;
     int* d_err = nullptr;
-    unsigned long long* d_bytes = nullptr;       // [2] algorithmic bytes and FP64 flops of the last launch
+    unsigned long long* d_bytes = nullptr;       // [3] algorithmic bytes, FP64 flops, FP32-pipe ops of the last launch
     double2* d_cheb = nullptr;                   // Chebyshev coefficients (rexi_cheb_step)
     int cheb_cap = 0;
     int nit_cap = 0;                             // pole items with workspace (K or 2K)
@@ -117,6 +117,7 @@ struct rexi_plan {
     int* d_lz_cols = nullptr;
     double2* d_lz_shift = nullptr;
     double* d_lz_diag = nullptr;                 // diagonal divided by the stencil fold factor
+    float2* d_lz_diagdf = nullptr;               // the same as double-float pairs (REXI_DF64)
     long long* d_dbg = nullptr;                  // index-check builds: record of the last Lanczos launch
     int dbg_trip = 0;                            // index-check builds: site made to fail
     double lz_fold = 1.0;
@@ -199,6 +200,16 @@ int upload_diag(rexi_plan* p, cudaStream_t stream, bool sync) {
         dl.resize(p->n);
         for (int i = 0; i < p->n; ++i) dl[i] = d[i] / p->lz_fold;
         e = cudaMemcpyAsync(p->d_lz_diag, dl.data(), sizeof(double) * p->n, cudaMemcpyHostToDevice, stream);
+    }
+    std::vector<float2> dp;
+    if (e == cudaSuccess && p->d_lz_diagdf && !dl.empty()) {
+        // and as double-float pairs: hi = fl32(x), lo = fl32(x - hi)
+        dp.resize(p->n);
+        for (int i = 0; i < p->n; ++i) {
+            const float hi = (float)dl[i];
+            dp[i] = make_float2(hi, (float)(dl[i] - (double)hi));
+        }
+        e = cudaMemcpyAsync(p->d_lz_diagdf, dp.data(), sizeof(float2) * p->n, cudaMemcpyHostToDevice, stream);
     }
     // pageable host buffers: the copies have read them when the calls return;
     // sync waits for the device side as well
@@ -449,7 +460,7 @@ int sm_count(int device) {
 int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(p->d_bar, 0, 3 * sizeof(unsigned), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, 2 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, 3 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stats, 0, sizeof(ItemStats) * A.nitems, stream);
     if (e != cudaSuccess) return cuda_fail(e);
     const size_t smem = rexi::engine_smem_bytes(A.nitems, p->fp32, A.ortho);
@@ -469,7 +480,7 @@ int launch(rexi_plan* p, const EngineArgs& A, const IOArgs& io, int total_tiles,
 int collect(rexi_plan* p, cudaStream_t stream, int nitems, int item_offset, int poles, rexi_stats* st,
             int n_sub) {
     int err = 0;
-    unsigned long long nbytes[2] = {0, 0};
+    unsigned long long nbytes[3] = {0, 0, 0};
     std::vector<ItemStats> s(nitems);
     cudaError_t e = cudaMemcpyAsync(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess)
@@ -500,6 +511,7 @@ int collect(rexi_plan* p, cudaStream_t stream, int nitems, int item_offset, int 
         st->status = status;
         st->bytes = (double)nbytes[0];
         st->flops64 = (double)nbytes[1];
+        st->ops32 = (double)nbytes[2];
     }
     return status;
 }
@@ -632,6 +644,7 @@ int lz_alloc(rexi_plan* p) {
     // f = |first nonzero stencil coefficient| (the coefficients are negative)
     p->lz_fold = std::fabs(p->a[0] != 0.0 ? p->a[0] : (p->a[1] != 0.0 ? p->a[1] : (p->a[2] != 0.0 ? p->a[2] : 1.0)));
     if ((st = dalloc(p, &p->d_lz_diag, n))) return st;
+    if ((st = dalloc(p, &p->d_lz_diagdf, n))) return st;
     if ((st = upload_diag(p, 0, true))) return st;
 #ifdef REXI_DEBUG
     if ((st = dalloc(p, &p->d_dbg, 4))) return st;
@@ -656,7 +669,7 @@ int lz_launch(rexi_plan* p, int mode, const void* in, void* out, cudaStream_t st
     const int nsub = mode == rexi::LZ_STEP ? p->n_sub : 1;
     cudaError_t e = cudaMemsetAsync(p->d_bar, 0, 3 * sizeof(unsigned), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, 2 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, 3 * sizeof(unsigned long long), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_stats, 0, sizeof(ItemStats) * p->K, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_lz_stop, 0xFF, sizeof(int) * nsub, stream);
     if (e == cudaSuccess && p->d_dbg) e = cudaMemsetAsync(p->d_dbg, 0, 4 * sizeof(long long), stream);
@@ -698,6 +711,8 @@ rexi::LzArgs lz_args(rexi_plan* p, int mode, const void* in, void* out, const Lz
     // compensated inner products between rescalings
     A.unit_ok = p->tau * p->W / p->lz_fold <= 65536.0 ? 1 : 0;
     A.diag = p->d_lz_diag;
+    A.diag_df = p->d_lz_diagdf;
+    A.df = p->opt.precision == REXI_DF64 ? 1 : 0;
     A.shift = p->d_lz_shift;
     A.alpha = p->d_alpha;
     A.alpha0 = make_double2(p->alpha0.real(), p->alpha0.imag());
@@ -900,14 +915,15 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     if (g->ndim < 1 || g->ndim > 3 || !(g->hbar > 0.0) || !(g->mass > 0.0)) return REXI_EINVAL;
     rexi_options opt;
     if (opt_in) opt = *opt_in; else rexi_options_default(&opt);
-    if (opt.precision != REXI_FP64 && opt.precision != REXI_MIXED) return REXI_EINVAL;
+    if (opt.precision != REXI_FP64 && opt.precision != REXI_MIXED && opt.precision != REXI_DF64) return REXI_EINVAL;
     if (opt.restart_m < 1 || opt.max_iters < 1) return REXI_EINVAL;
     if (opt.ortho < 0 || opt.ortho > 2) return REXI_EINVAL;
     const bool lanczos = opt.ortho == 2;
     if (lanczos) {
-        // one shared basis per substep, no restarts: FP64 only, no window
-        if (opt.precision != REXI_FP64 || opt.window != 0 || opt.restart_m > REXI_MAX_KRYLOV) return REXI_EINVAL;
+        // one shared basis per substep, no restarts: FP64 or double-float, no window
+        if (opt.precision == REXI_MIXED || opt.window != 0 || opt.restart_m > REXI_MAX_KRYLOV) return REXI_EINVAL;
     } else {
+        if (opt.precision == REXI_DF64) return REXI_EINVAL;   // the double-float form is the Lanczos kernel's
         if (opt.restart_m > REXI_MAX_RESTART) return REXI_EINVAL;
         // full orthogonalisation keeps m + 1 dot products per step in registers
         if (opt.window == 0 &&
@@ -1018,7 +1034,7 @@ int rexi_plan_create(rexi_plan** out, const rexi_grid* g, const double* V, doubl
     if ((st = dalloc(p, &p->d_hout, n))) return fail(st);
     if ((st = dalloc(p, &p->d_bar, 4))) return fail(st);
     if ((st = dalloc(p, &p->d_err, 1))) return fail(st);
-    if ((st = dalloc(p, &p->d_bytes, 2))) return fail(st);
+    if ((st = dalloc(p, &p->d_bytes, 3))) return fail(st);
     {
         std::vector<double2> al(K);
         for (int k = 0; k < K; ++k) al[k] = make_double2(p->alpha[k].real(), p->alpha[k].imag());
@@ -1171,7 +1187,7 @@ int rexi_cheb_step(rexi_plan* p, const void* psi_in, void* psi_out, double tol, 
     cudaError_t e = cudaMemcpyAsync(p->d_cheb, coef.data(), sizeof(double2) * (N + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bar, 0, 2 * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_bytes, 0, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return p->last_status = cuda_fail(e);
     rexi::ChebArgs a{};
     a.prob = p->fwd.d_prob;
@@ -1387,7 +1403,7 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
             return REXI_ECUDA;
     cudaError_t e = cudaMemsetAsync(p0->d_bar, 0, 3 * sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_bytes, 0, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_bytes, 0, 3 * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p0->d_stats, 0, sizeof(ItemStats) * (p0->K + p0->ngroups), s);
     if (e != cudaSuccess) return REXI_ECUDA;
     const size_t smem = rexi::engine_smem_bytes(A.nitems, p0->fp32, A.ortho);
@@ -1405,7 +1421,7 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
     if (e != cudaSuccess) return cuda_fail(e);
     if (!st) return REXI_OK;
     int status = REXI_OK;
-    unsigned long long nbytes[2] = {0, 0};
+    unsigned long long nbytes[3] = {0, 0, 0};
     if (cudaMemcpyAsync(nbytes, p0->d_bytes, sizeof(nbytes), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return REXI_ECUDA;
     for (int b = 0; b < B; ++b) {
@@ -1436,6 +1452,7 @@ int rexi_step_batched(rexi_plan* const* plans, int B, const void* const* psi_in,
         o.status = err ? err : (failed ? REXI_ENOCONV : REXI_OK);
         o.bytes = (double)nbytes[0];
         o.flops64 = (double)nbytes[1];
+        o.ops32 = (double)nbytes[2];
         if (o.status != REXI_OK && status == REXI_OK) status = o.status;
         p->last_status = o.status;
     }

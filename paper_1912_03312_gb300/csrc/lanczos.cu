@@ -27,8 +27,9 @@
 //   T(j, j) = f alpha_j,  T(j+1, j) = f sqrt(n_{j+1} / n_j) / s_{j+1},
 //
 // exactly for the coefficients used (whatever the accuracy of the inner
-// products that chose them), so B Q_k = Q_{k+1} T_k holds to FP64 rounding
-// with T_k tridiagonal.  The scale s_j is one (two fused multiply-adds per
+// products that chose them), so B Q_k = Q_{k+1} T_k holds to the rounding of
+// the recurrence (FP64, or double-float pairs on the FP32 pipe in the
+// double-float mode) with T_k tridiagonal.  The scale s_j is one (two fused multiply-adds per
 // component) while n stays within [2^-30, 2^30], else the power of two that
 // brings u_j back to unit scale.  The shifted systems (B - s_k I) x = psi share
 // Q_k (Sec. 5 of the paper: the Krylov spaces of shifted systems coincide);
@@ -119,6 +120,7 @@ struct LzSmem {
     };
     double2 c0;              //                            coefficient of the input state
     double cw, ca, cb;       // the update as applied: u_j = cw w' - ca u_{j-1} - cb u_{j-2}
+    float cwf, caf[2], cbf[2];   // double-float recurrence: cw, ca, cb as (hi, lo) pairs (j == 2: cb in FP64)
     double n0;               // ||u_0||^2 of the substep
     double s_last, inv_s_last;   // scale s of the last update (u_{j-1} = s_{j-1} (...)), a power of two
     double hrho[2];          // rho = 1 / ||u|| of sweeps j-1, j-2 (from sweep 3 on: control CTA only)
@@ -545,7 +547,8 @@ __device__ void stage_tile(const LzArgs& A, const Stage& st, const double2* u0, 
     for (int i = threadIdx.x; i < T.I; i += kLzBlock, wi.next(T.tx, T.ty)) {
         int e;
         const size_t g = int_index(A, T, wi, hx, hy, hz, &e);
-        if (LZ_OK(i, st.int_max, LZ_SITE_STAGE) && LZ_OK(g, A.n, LZ_SITE_STAGE_SRC)) cp_async8(st.D + i, A.diag + g);
+        if (LZ_OK(i, st.int_max, LZ_SITE_STAGE) && LZ_OK(g, A.n, LZ_SITE_STAGE_SRC))
+            cp_async8(st.D + i, A.df ? (const void*)(A.diag_df + g) : (const void*)(A.diag + g));
     }
     cp_async_commit();
 }
@@ -583,7 +586,8 @@ __device__ void setup_resident(const LzArgs& A, LzSmem& sm, const Stage& st, int
     for (int i = threadIdx.x; i < T.I; i += kLzBlock, wi.next(T.tx, T.ty)) {
         int e;
         const size_t g = int_index(A, T, wi, hx, hy, hz, &e);
-        if (LZ_OK(i, st.int_max, LZ_SITE_STAGE) && LZ_OK(g, A.n, LZ_SITE_STAGE_SRC)) cp_async8(st.D + i, A.diag + g);
+        if (LZ_OK(i, st.int_max, LZ_SITE_STAGE) && LZ_OK(g, A.n, LZ_SITE_STAGE_SRC))
+            cp_async8(st.D + i, A.df ? (const void*)(A.diag_df + g) : (const void*)(A.diag + g));
     }
     cp_async_commit();
     if (threadIdx.x == 0) sm.nring = 0;
@@ -642,8 +646,8 @@ __device__ __forceinline__ void phase_a(const LzArgs& A, const Tile& T, const do
 // (the pieces the inner products use): (re_hi, re_lo, im_hi, im_lo).
 template <bool kF64>
 __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const double2* S, const double* D,
-                                        double2* Wown, double2* wcur, float4* ujs, int hx, int hy, int hz,
-                                        float& nh, float& nl, float& ph, float& pl, double& dn, double& dp) {
+                                        const float2* Dd, double2* Wown, double2* wcur, float4* ujs, int hx, int hy,
+                                        int hz, float& nh, float& nl, float& ph, float& pl, double& dn, double& dp) {
     // w' = B u / f with f = |a_d| of the first dimension the stencil reaches
     // (the a_d are negative): that dimension's neighbour pair enters with
     // weight -1 (one addition of negated operands), the others with r_d = a_d
@@ -657,7 +661,13 @@ __device__ __forceinline__ void phase_b(const LzArgs& A, const Tile& T, const do
         int e;
         const size_t g = int_index(A, T, wb, hx, hy, hz, &e);
         const double2 c = LZ_AT(S, e, T.E, LZ_SITE_STENCIL);
-        const double dg = LZ_AT(D, i, T.I, LZ_SITE_STENCIL);
+        double dg;
+        if (kF64 && Dd != nullptr) {
+            const float2 q = LZ_AT(Dd, i, T.I, LZ_SITE_STENCIL);      // double-float mode: the diagonal as pairs
+            dg = (double)q.x + (double)q.y;
+        } else {
+            dg = LZ_AT(D, i, T.I, LZ_SITE_STENCIL);
+        }
         double wx = 0.0, wy = 0.0;
         if (hx) {
             const double2 l = LZ_AT(S, e - 1, T.E, LZ_SITE_STENCIL), rr = LZ_AT(S, e + 1, T.E, LZ_SITE_STENCIL);
@@ -713,7 +723,215 @@ __device__ __noinline__ void phase_b_first(const LzArgs& A, const Tile& T, const
                                            double2* Wown, double2* wcur, int hx, int hy, int hz, double& dn,
                                            double& dp) {
     float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f;
-    phase_b<true>(A, T, S, D, Wown, wcur, nullptr, hx, hy, hz, nh, nl, ph, pl, dn, dp);
+    const float2* Dd = A.df ? reinterpret_cast<const float2*>(D) : nullptr;
+    phase_b<true>(A, T, S, D, Dd, Wown, wcur, nullptr, hx, hy, hz, nh, nl, ph, pl, dn, dp);
+}
+
+// ---- the recurrence in double-float (A.df) ----------------------------------
+//
+// From sweep 1 on, every vector of the recurrence (u_j on the extended box,
+// w' = B u_j / f, the update's operands, the stored basis) is a pair of floats
+// per component, (re_hi, re_lo, im_hi, im_lo) in one float4, and every
+// operation runs on the FP32 pipe: the leading parts of a result's terms are
+// summed by Knuth's two-sum (exactly), products are Dekker's (exact up to the
+// lo*lo term, with a fused multiply-add), the trailing parts and the rounding
+// errors are summed in FP32, and the pair is renormalised once per result.
+// Each result is then within a few 2^-48 of the magnitude of its largest term:
+// the error model of FP64 arithmetic with a unit roundoff 2^5 larger.  The
+// recurrence's rounding enters psi' through the combined coefficients sum_k
+// alpha_k y_k, not the individual weights, so its effect is that unit
+// roundoff times sum_r |c_r| ||u_r|| (a few times 1e-14), far below the
+// per-pole stopping tolerance.  Sweep 0 (the caller's state, at any scale)
+// stays in FP64, sweep 1's update reads its FP64 results and rounds u_1 to
+// pairs, and sweep 2 forms its u_0 term in FP64.
+
+// (s, t) += x: two-sum of x into the leading sum s, its rounding error into t.
+__device__ __forceinline__ void df_acc(float& s, float& t, float x) {
+    const float r = __fadd_rn(s, x);
+    const float z = __fsub_rn(r, s);
+    t = __fadd_rn(t, __fadd_rn(__fsub_rn(s, __fsub_rn(r, z)), __fsub_rn(x, z)));
+    s = r;
+}
+// (s, t) += (ah + al)(bh + bl): the rounded leading product into s, its exact
+// error and the cross terms into t.
+__device__ __forceinline__ void df_acc_mul(float& s, float& t, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    df_acc(s, t, p);
+    t = __fadd_rn(t, e);
+}
+// (s, t) = (ah + al)(bh + bl), unnormalised.
+__device__ __forceinline__ void df_start_mul(float& s, float& t, float ah, float al, float bh, float bl) {
+    s = __fmul_rn(ah, bh);
+    float e = fmaf(ah, bh, -s);
+    e = fmaf(ah, bl, e);
+    t = fmaf(al, bh, e);
+}
+// (s, t) -= (lh + ll) + (rh + rl): a neighbour pair of weight -1.
+__device__ __forceinline__ void df_pair_unit(float& s, float& t, float lh, float ll, float rh, float rl) {
+    df_acc(s, t, -lh);
+    df_acc(s, t, -rh);
+    t = __fsub_rn(__fsub_rn(t, ll), rl);
+}
+// (s, t) += r ((lh + ll) + (rh + rl)): a neighbour pair of weight r (a pair).
+__device__ __forceinline__ void df_pair_ratio(float& s, float& t, float lh, float ll, float rh, float rl, float2 r) {
+    float ph = 0.f, pl = 0.f;
+    df_acc(ph, pl, lh);
+    df_acc(ph, pl, rh);
+    pl = __fadd_rn(pl, __fadd_rn(ll, rl));
+    df_acc_mul(s, t, r.x, r.y, ph, pl);
+}
+// The pair s + t renormalised (h = fl(s + t), l = the rest).
+__device__ __forceinline__ float2 df_norm(float s, float t) {
+    const float h = __fadd_rn(s, t);
+    return make_float2(h, __fsub_rn(t, __fsub_rn(h, s)));
+}
+// An FP64 value rounded to a pair (hi = fl32(x), lo = fl32(x - hi)).
+__device__ __forceinline__ float2 df_from(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// Sweep 1's update in double-float mode: v = cw w' - ca u_0 in FP64 from the
+// FP64 results of sweep 0, rounded to pairs (into out; streamed mode: in
+// place of W, and the tile's own points to ujw).
+__device__ __noinline__ void phase_a_first_df(const LzArgs& A, const Tile& T, const double2* W, const double2* U1,
+                                              float4* out, float4* ujw, double cw, double ca, int hx, int hy,
+                                              int hz) {
+    Walk wa;
+    wa.init(threadIdx.x, T.ex, T.ey);
+    for (int e = threadIdx.x; e < T.E; e += kLzBlock, wa.next(T.ex, T.ey)) {
+        const double2 w = LZ_AT(W, e, T.E, LZ_SITE_STENCIL), u1 = LZ_AT(U1, e, T.E, LZ_SITE_STENCIL);
+        const float2 vx = df_from(fma(-ca, u1.x, cw * w.x)), vy = df_from(fma(-ca, u1.y, cw * w.y));
+        const float4 v = make_float4(vx.x, vx.y, vy.x, vy.y);
+        LZ_AT(out, e, T.E, LZ_SITE_STENCIL) = v;
+        const int ix = wa.x - hx, iy = wa.y - hy, iz = wa.z - hz;
+        if (ujw != nullptr && ix >= 0 && ix < T.tx && iy >= 0 && iy < T.ty && iz >= 0 && iz < T.tz) {
+            const size_t g =
+                (size_t)(T.x0 + ix) + (size_t)A.nx * ((size_t)(T.y0 + iy) + (size_t)A.ny * (size_t)(T.z0 + iz));
+            if (LZ_OK((long long)g, (long long)(A.m + 2) * A.n, LZ_SITE_BASIS) &&
+                LZ_OK(g, A.n, LZ_SITE_BASIS))
+                ujw[g] = v;
+        }
+    }
+}
+
+// Phase A in double-float mode, sweeps j >= 2: v = cw w' - ca u_{j-1} - cb
+// u_{j-2} on the extended box (resident: into out = R[j mod 3]; streamed: in
+// place of W, and the tile's own points to ujw).  kU0 (j = 2): u_{j-2} is the
+// FP64 input state u_0, its term formed in FP64 with cb64 and rounded to pairs.
+template <bool kUnit, bool kU0>
+__device__ __forceinline__ void phase_a_df(const LzArgs& A, const Tile& Tr, const float4* __restrict__ W,
+                                        const float4* __restrict__ U1, const void* U2, float4* out, float4* ujw, int j,
+                                        float cw, float2 ca, float2 cb, double cb64, int hx, int hy, int hz) {
+    // the tile and the grid extents in registers (a store of the loop could
+    // alias a referenced object and force reloads)
+    const Tile T = Tr;
+    const size_t nx = (size_t)A.nx, nxy = (size_t)A.nx * (size_t)A.ny;
+    Walk wa;
+    wa.init(threadIdx.x, T.ex, T.ey);
+    for (int e = threadIdx.x; e < T.E; e += kLzBlock, wa.next(T.ex, T.ey)) {
+        const float4 w = LZ_AT(W, e, T.E, LZ_SITE_STENCIL), u1 = LZ_AT(U1, e, T.E, LZ_SITE_STENCIL);
+        float xs = w.x, xt = w.y, ys = w.z, yt = w.w;
+        if (!kUnit) {
+            xs = __fmul_rn(cw, xs);
+            xt = __fmul_rn(cw, xt);
+            ys = __fmul_rn(cw, ys);
+            yt = __fmul_rn(cw, yt);
+        }
+        df_acc_mul(xs, xt, -ca.x, -ca.y, u1.x, u1.y);
+        df_acc_mul(ys, yt, -ca.x, -ca.y, u1.z, u1.w);
+        if (kU0) {
+            const double2 u2 = LZ_AT(reinterpret_cast<const double2*>(U2), e, T.E, LZ_SITE_STENCIL);
+            const float2 px = df_from(-cb64 * u2.x), py = df_from(-cb64 * u2.y);
+            df_acc(xs, xt, px.x);
+            xt = __fadd_rn(xt, px.y);
+            df_acc(ys, yt, py.x);
+            yt = __fadd_rn(yt, py.y);
+        } else {
+            const float4 u2 = LZ_AT(reinterpret_cast<const float4*>(U2), e, T.E, LZ_SITE_STENCIL);
+            df_acc_mul(xs, xt, -cb.x, -cb.y, u2.x, u2.y);
+            df_acc_mul(ys, yt, -cb.x, -cb.y, u2.z, u2.w);
+        }
+        const float2 vx = df_norm(xs, xt), vy = df_norm(ys, yt);
+        const float4 v = make_float4(vx.x, vx.y, vy.x, vy.y);
+        LZ_AT(out, e, T.E, LZ_SITE_STENCIL) = v;
+        const int ix = wa.x - hx, iy = wa.y - hy, iz = wa.z - hz;
+        if (ujw != nullptr && ix >= 0 && ix < T.tx && iy >= 0 && iy < T.ty && iz >= 0 && iz < T.tz) {
+            const size_t g = (size_t)(T.x0 + ix) + nx * (size_t)(T.y0 + iy) + nxy * (size_t)(T.z0 + iz);
+            if (LZ_OK((long long)(j - 1) * A.n + (long long)g, (long long)(A.m + 2) * A.n, LZ_SITE_BASIS) &&
+                LZ_OK(g, A.n, LZ_SITE_BASIS))
+                ujw[g] = v;
+        }
+    }
+}
+
+// Phase B in double-float mode: w' = B u_j / f from S (u_j on the extended
+// box, as pairs): the diagonal term, then the neighbour pairs (weight -1 for
+// the first stencil dimension and wherever r_d = -1, as on a grid of equal
+// spacings; else r_d as a pair); stored to the global B u_j and (resident
+// mode) into Wown; u_j to the basis (ujs, resident mode); the compensated
+// partial sums of ||u_j||^2 and Re u_j^H w' added to acc (n_hi, n_lo, p_hi,
+// p_lo) and returned.  Out of line: its own register allocation (measured
+// faster than inlined, and than two points per iteration).
+__device__ __noinline__ float4 phase_b_df(const LzArgs& A, const Tile& Tr, const float4* __restrict__ S,
+                                          const float2* __restrict__ D, float4* Wown, float4* wcur, float4* ujs,
+                                          float2 ry, float2 rz, bool uy, bool uz, int hx, int hy, int hz,
+                                          float4 acc) {
+    // the tile, the grid extents and the sums in registers (a store of the
+    // loop could alias a referenced object and force reloads)
+    const Tile T = Tr;
+    const size_t nx = (size_t)A.nx, nxy = (size_t)A.nx * (size_t)A.ny;
+    float nh = acc.x, nl = acc.y, ph = acc.z, pl = acc.w;
+    const int sy = T.ex, sz = T.ex * T.ey;
+    Walk wb;
+    wb.init(threadIdx.x, T.tx, T.ty);
+    for (int i = threadIdx.x; i < T.I; i += kLzBlock, wb.next(T.tx, T.ty)) {
+        const int e = (wb.x + hx) + T.ex * ((wb.y + hy) + T.ey * (wb.z + hz));
+        const size_t g = (size_t)(T.x0 + wb.x) + nx * (size_t)(T.y0 + wb.y) + nxy * (size_t)(T.z0 + wb.z);
+        const float4 c = LZ_AT(S, e, T.E, LZ_SITE_STENCIL);
+        const float2 dg = LZ_AT(D, i, T.I, LZ_SITE_STENCIL);
+        float xs, xt, ys, yt;
+        df_start_mul(xs, xt, dg.x, dg.y, c.x, c.y);
+        df_start_mul(ys, yt, dg.x, dg.y, c.z, c.w);
+        if (hx) {
+            const float4 l = LZ_AT(S, e - 1, T.E, LZ_SITE_STENCIL), r = LZ_AT(S, e + 1, T.E, LZ_SITE_STENCIL);
+            df_pair_unit(xs, xt, l.x, l.y, r.x, r.y);
+            df_pair_unit(ys, yt, l.z, l.w, r.z, r.w);
+        }
+        if (hy) {
+            const float4 l = LZ_AT(S, e - sy, T.E, LZ_SITE_STENCIL), r = LZ_AT(S, e + sy, T.E, LZ_SITE_STENCIL);
+            if (uy) {
+                df_pair_unit(xs, xt, l.x, l.y, r.x, r.y);
+                df_pair_unit(ys, yt, l.z, l.w, r.z, r.w);
+            } else {
+                df_pair_ratio(xs, xt, l.x, l.y, r.x, r.y, ry);
+                df_pair_ratio(ys, yt, l.z, l.w, r.z, r.w, ry);
+            }
+        }
+        if (hz) {
+            const float4 l = LZ_AT(S, e - sz, T.E, LZ_SITE_STENCIL), r = LZ_AT(S, e + sz, T.E, LZ_SITE_STENCIL);
+            if (uz) {
+                df_pair_unit(xs, xt, l.x, l.y, r.x, r.y);
+                df_pair_unit(ys, yt, l.z, l.w, r.z, r.w);
+            } else {
+                df_pair_ratio(xs, xt, l.x, l.y, r.x, r.y, rz);
+                df_pair_ratio(ys, yt, l.z, l.w, r.z, r.w, rz);
+            }
+        }
+        const float2 wx = df_norm(xs, xt), wy = df_norm(ys, yt);
+        const float4 wv = make_float4(wx.x, wx.y, wy.x, wy.y);
+        if (LZ_OK(g, A.n, LZ_SITE_WT)) wcur[g] = wv;
+        if (Wown) LZ_AT(Wown, e, T.E, LZ_SITE_STENCIL) = wv;
+        if (ujs != nullptr && LZ_OK(g, A.n, LZ_SITE_BASIS)) ujs[g] = c;
+        df_madd(nh, nl, c.x, c.y, c.x, c.y);
+        df_madd(nh, nl, c.z, c.w, c.z, c.w);
+        df_madd(ph, pl, c.x, c.y, wv.x, wv.y);
+        df_madd(ph, pl, c.z, c.w, wv.z, wv.w);
+    }
+    return make_float4(nh, nl, ph, pl);
 }
 
 // One Krylov sweep j over the tiles of this CTA (the first tile's copies were
@@ -727,6 +945,12 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
     double2* ujw = j >= 1 ? uvec_w(A, j) : nullptr;
     float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f;
     double dn = 0.0, dp = 0.0;
+    // double-float mode: the update's coefficients and the stencil ratios as pairs
+    const bool df = A.df != 0;
+    const float cwf = sm.cwf;
+    const float2 caf = make_float2(sm.caf[0], sm.caf[1]), cbf = make_float2(sm.cbf[0], sm.cbf[1]);
+    const float2 ry = df_from(A.ratio[1]), rz = df_from(A.ratio[2]);
+    const bool uy = A.ratio[1] == -1.0, uz = A.ratio[2] == -1.0;
     if (A.resident) {
         if (lz_bid(A) - 1 < A.ntiles) {
             const Tile T = tile_of(A, lz_bid(A) - 1, hx, hy, hz);
@@ -735,7 +959,37 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
                 cp_async_wait_all();
                 __syncthreads();
             }
-            if (LZ_OK(T.E, st.ext_max + 1, LZ_SITE_SMEM) && LZ_OK(T.I, st.int_max + 1, LZ_SITE_SMEM)) {
+            const bool fits = LZ_OK(T.E, st.ext_max + 1, LZ_SITE_SMEM) && LZ_OK(T.I, st.int_max + 1, LZ_SITE_SMEM);
+            if (fits && df) {
+                float4* Sf = reinterpret_cast<float4*>(S);
+                const float4* Wf = reinterpret_cast<const float4*>(st.W);
+                if (j == 1) {
+                    phase_a_first_df(A, T, st.W, st.R(0), Sf, nullptr, cw, ca, hx, hy, hz);
+                } else if (j == 2) {
+                    phase_a_df<false, true>(A, T, Wf, reinterpret_cast<const float4*>(st.R(1)), st.R(0), Sf, nullptr,
+                                            j, cwf, caf, cbf, cb, hx, hy, hz);
+                } else if (j >= 3) {
+                    const float4* U1 = reinterpret_cast<const float4*>(st.R((j + 2) % 3));
+                    const float4* U2 = reinterpret_cast<const float4*>(st.R((j + 1) % 3));
+                    if (cw == 1.0)
+                        phase_a_df<true, false>(A, T, Wf, U1, U2, Sf, nullptr, j, cwf, caf, cbf, cb, hx, hy, hz);
+                    else
+                        phase_a_df<false, false>(A, T, Wf, U1, U2, Sf, nullptr, j, cwf, caf, cbf, cb, hx, hy, hz);
+                }
+                if (j >= 1) __syncthreads();
+                float4* ujs = j >= 1 && LZ_OK(j - 1, A.m + 2, LZ_SITE_BASIS) ? reinterpret_cast<float4*>(ujw) : nullptr;
+                if (j == 0) {
+                    phase_b_first(A, T, S, st.D, st.W, wcur, hx, hy, hz, dn, dp);
+                } else {
+                    const float4 q = phase_b_df(A, T, Sf, reinterpret_cast<const float2*>(st.D),
+                                                reinterpret_cast<float4*>(st.W), reinterpret_cast<float4*>(wcur), ujs,
+                                                ry, rz, uy, uz, hx, hy, hz, make_float4(nh, nl, ph, pl));
+                    nh = q.x;
+                    nl = q.y;
+                    ph = q.z;
+                    pl = q.w;
+                }
+            } else if (fits) {
                 if (j >= 1) {
                     if (cw == 1.0)
                         phase_a<true>(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, nullptr, j, cw, ca, cb,
@@ -749,7 +1003,7 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
                 if (j == 0)
                     phase_b_first(A, T, S, st.D, st.W, wcur, hx, hy, hz, dn, dp);
                 else
-                    phase_b<false>(A, T, S, st.D, st.W, wcur, ujs, hx, hy, hz, nh, nl, ph, pl, dn, dp);
+                    phase_b<false>(A, T, S, st.D, nullptr, st.W, wcur, ujs, hx, hy, hz, nh, nl, ph, pl, dn, dp);
             }
         }
     } else {
@@ -762,6 +1016,38 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
                 __syncthreads();
             }
             if (!LZ_OK(T.E, st.ext_max + 1, LZ_SITE_SMEM) || !LZ_OK(T.I, st.int_max + 1, LZ_SITE_SMEM)) break;
+            if (df) {
+                // in place of W; the tile's own points of u_j to the basis
+                float4* Wf = reinterpret_cast<float4*>(st.W);
+                float4* ujf = reinterpret_cast<float4*>(ujw);
+                if (j == 1) {
+                    phase_a_first_df(A, T, st.W, st.U1, Wf, ujf, cw, ca, hx, hy, hz);
+                } else if (j == 2) {
+                    phase_a_df<false, true>(A, T, Wf, reinterpret_cast<const float4*>(st.U1), st.U2, Wf, ujf, j, cwf,
+                                            caf, cbf, cb, hx, hy, hz);
+                } else if (j >= 3) {
+                    const float4* U1 = reinterpret_cast<const float4*>(st.U1);
+                    const float4* U2 = reinterpret_cast<const float4*>(st.U2);
+                    if (cw == 1.0)
+                        phase_a_df<true, false>(A, T, Wf, U1, U2, Wf, ujf, j, cwf, caf, cbf, cb, hx, hy, hz);
+                    else
+                        phase_a_df<false, false>(A, T, Wf, U1, U2, Wf, ujf, j, cwf, caf, cbf, cb, hx, hy, hz);
+                }
+                if (j >= 1) __syncthreads();
+                if (j == 0) {
+                    phase_b_first(A, T, st.W, st.D, nullptr, wcur, hx, hy, hz, dn, dp);
+                } else {
+                    const float4 q = phase_b_df(A, T, Wf, reinterpret_cast<const float2*>(st.D), nullptr,
+                                                reinterpret_cast<float4*>(wcur), nullptr, ry, rz, uy, uz, hx, hy, hz,
+                                                make_float4(nh, nl, ph, pl));
+                    nh = q.x;
+                    nl = q.y;
+                    ph = q.z;
+                    pl = q.w;
+                }
+                __syncthreads();                  // shared memory is restaged for the next tile
+                continue;
+            }
             if (j >= 1) {
                 if (cw == 1.0)
                     phase_a<true>(A, T, st.W, st.U1, st.U2, st.W, ujw, j, cw, ca, cb, hx, hy, hz);
@@ -772,14 +1058,14 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
             if (j == 0)
                 phase_b_first(A, T, st.W, st.D, nullptr, wcur, hx, hy, hz, dn, dp);
             else
-                phase_b<false>(A, T, st.W, st.D, nullptr, wcur, nullptr, hx, hy, hz, nh, nl, ph, pl, dn, dp);
+                phase_b<false>(A, T, st.W, st.D, nullptr, nullptr, wcur, nullptr, hx, hy, hz, nh, nl, ph, pl, dn, dp);
             __syncthreads();                      // shared memory is restaged for the next tile
         }
     }
     *part = j == 0 ? pack_f64(cta_f64_sum(sm, dn, dp)) : cta_df_sum(sm, nh, nl, ph, pl);
 }
 
-// Resident mode (the basis holds the hi/lo splits of u_1, u_2, ...): the
+// Resident or double-float mode (the basis holds u_1, u_2, ... as pairs): the
 // coefficients in sm.coef become c0 = c_0 (FP64, the input state's term) and,
 // for r >= 1, the splits of 2^-E c_r with 2^E above the largest |Re|, |Im|, so
 // the double-float products stay in the FP32 range; returns 2^E.
@@ -832,7 +1118,7 @@ __device__ __forceinline__ void cp_async_wait_upto(int n) {
 constexpr int kMaxDepth = 8;    // basis vectors a thread prefetches in the final pass
 
 // Final pass over this CTA's tiles, dst = sum_{r < J} c_r u_r:
-//  kSplit (resident mode; the basis holds the hi/lo splits of u_1, u_2, ...):
+//  kSplit (resident or double-float mode; the basis holds u_1, u_2, ... as pairs):
 //    dst = c_0 u_0 + 2^E sum_{1 <= r < J} (2^-E c_r) u_r, the sum in
 //    double-float on the FP32 pipe (products exact up to the lo*lo term,
 //    two-sum accumulation; about 2^-47 relative per term), the input state's
@@ -1228,6 +1514,16 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                         }
                         ca = sj * alpha;
                         cb = sj * beta;
+                        double alpha_used = alpha;
+                        if (A.df && j == 2) {
+                            // the pair the double-float update applies to u_1; T takes its value
+                            const float2 pa = df_from(ca);
+                            sm.caf[0] = pa.x;
+                            sm.caf[1] = pa.y;
+                            ca = (double)pa.x + (double)pa.y;
+                            alpha_used = ca * inv_sj;
+                        }
+                        sm.cwf = __double2float_rn(sj);      // (used from j = 2 on: s_2 is within the FP32 range)
                         if (j == 1) sm.n0 = n;
                         sm.hrho[1] = sm.hrho[0];
                         sm.hrho[0] = rho;
@@ -1236,7 +1532,7 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                         if (control) {
                             const double sub = j >= 2 ? A.fold * n * rho * rho2 * sm.inv_s_last : 0.0;
                             sm.ha[1] = sm.ha[0];
-                            sm.ha[0] = A.fold * alpha;
+                            sm.ha[0] = A.fold * alpha_used;
                             sm.hsub[1] = sm.hsub[0];
                             sm.hsub[0] = sub;
                             sm.hsup[1] = sm.hsup[0];
@@ -1259,8 +1555,16 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                         df_mul(q.z, q.w, rh, rl, ah, al);                     // alpha = p / n
                         df_mul(q.x, q.y, sm.rprev_h, sm.rprev_l, bh, bl);     // n / n_{j-2}
                         const float sb = __fmul_rn(sf, sm.inv_sf_last);        // s_j / s_{j-1}: a power of two
-                        ca = f2d_int(__fmul_rn(ah, sf)) + f2d_int(__fmul_rn(al, sf));
-                        cb = f2d_int(__fmul_rn(bh, sb)) + f2d_int(__fmul_rn(bl, sb));
+                        const float cah = __fmul_rn(ah, sf), cal = __fmul_rn(al, sf);
+                        const float cbh = __fmul_rn(bh, sb), cbl = __fmul_rn(bl, sb);
+                        ca = f2d_int(cah) + f2d_int(cal);
+                        cb = f2d_int(cbh) + f2d_int(cbl);
+                        // (the double-float update applies these pairs exactly)
+                        sm.cwf = sf;
+                        sm.caf[0] = cah;
+                        sm.caf[1] = cal;
+                        sm.cbf[0] = cbh;
+                        sm.cbf[1] = cbl;
                         if (control) {
                             // the exact columns of T for these coefficients, in FP64
                             const double n = f2d_int(q.x) + f2d_int(q.y);
@@ -1382,7 +1686,10 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
             const int d = hx + hy + hz;
             const double later = (double)max(sweeps - 2, 0);
             double by = (sweeps >= 1 ? 40.0 : 0.0) + (sweeps >= 2 ? 72.0 : 0.0) + 88.0 * later;
-            double fl = 6.0 * d * sweeps + upd_fl;
+            // (double-float mode: FP64 work in sweep 0's stencil, sweep 1's
+            // update and sweep 2's u_0 term only)
+            double fl = A.df ? 6.0 * d * min(sweeps, 1) + (sweeps >= 2 ? 4.0 : 0.0) + (sweeps >= 3 ? 2.0 : 0.0)
+                             : 6.0 * d * sweeps + upd_fl;
             // the final pass reads J vectors and writes one output per pole set;
             // its FP64 work: a complex multiply-add per vector, or (resident
             // mode, the sum in double-float on the FP32 pipe) the input
@@ -1390,10 +1697,28 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
             const int Jn = A.mode == LZ_STEP ? max(J, 1) : J;
             const int outs = A.mode == LZ_STEP ? 1 : A.K;
             by += outs * 16.0 * (Jn + 1);
-            fl += outs * (A.resident ? 12.0 : 8.0 * Jn);
+            fl += outs * (A.resident || A.df ? 12.0 : 8.0 * Jn);
+            // FP32-pipe arithmetic, as the code issues it: the compensated
+            // inner products of sweeps >= 1 (four Dekker multiply-adds of 12
+            // operations per point); double-float mode: also the stencil (per
+            // component a product of 4, a neighbour pair of weight -1: 14, a
+            // pair of weight r_d: 25, a renormalisation: 3) and the update of
+            // sweeps >= 2 (per component two multiply-adds of 11 and a
+            // renormalisation); the final pass in double-float (resident or
+            // double-float mode): four multiply-adds per vector u_1, u_2, ...
+            double ops = 48.0 * max(sweeps - 1, 0);
+            if (A.df) {
+                double pairs = 0.0;
+                for (int q = 0; q < 3; ++q)
+                    if ((q == 0 && hx) || (q == 1 && hy) || (q == 2 && hz))
+                        pairs += (q == 0 || A.ratio[q] == -1.0) ? 14.0 : 25.0;
+                ops += 2.0 * (7.0 + pairs) * max(sweeps - 1, 0) + 50.0 * max(sweeps - 2, 0);
+            }
+            if (A.resident || A.df) ops += outs * 48.0 * max(Jn - 1, 0);
             if (A.bytes != nullptr) {
                 A.bytes[0] += (unsigned long long)(by * n);
                 A.bytes[1] += (unsigned long long)(fl * n);
+                A.bytes[2] += (unsigned long long)(ops * n);
             }
         }
         if (!control) {
@@ -1402,7 +1727,7 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                 for (int r = threadIdx.x; r < Jn; r += kLzBlock)
                     if (LZ_OK(r, kLzMaxM, LZ_SITE_Y) && LZ_OK(r, A.m, LZ_SITE_Y)) sm.coef[r] = __ldcg(A.coef + r);
                 __syncthreads();
-                if (A.resident)
+                if (A.resident || A.df)
                     final_pass<true>(A, sm, split_coefficients(sm, Jn), u0, out, Jn, hx, hy, hz, slots, depth);
                 else
                     final_pass<false>(A, sm, 1.0, u0, out, Jn, hx, hy, hz, slots, depth);
@@ -1414,7 +1739,7 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                             sm.coef[r] = __ldcg(A.coef + (size_t)k * A.m + r);
                     __syncthreads();
                     double2* xk = A.out + (size_t)k * A.n;
-                    if (A.resident)
+                    if (A.resident || A.df)
                         final_pass<true>(A, sm, split_coefficients(sm, J), u0, xk, J, hx, hy, hz, slots, depth);
                     else
                         final_pass<false>(A, sm, 1.0, u0, xk, J, hx, hy, hz, slots, depth);
@@ -1459,7 +1784,7 @@ __global__ void lanczos_reset_kernel(const LzArgs* __restrict__ args) {
     const LzArgs& A = args[blockIdx.x];
     if (threadIdx.x < 3) A.bar[threadIdx.x] = 0u;
     if (threadIdx.x == 0) *A.err = 0;
-    if (threadIdx.x < 2 && A.bytes != nullptr) A.bytes[threadIdx.x] = 0ull;
+    if (threadIdx.x < 3 && A.bytes != nullptr) A.bytes[threadIdx.x] = 0ull;
     if (threadIdx.x < 4 && A.dbg != nullptr) A.dbg[threadIdx.x] = 0;
     int* st = reinterpret_cast<int*>(A.stats);
     const int words = (int)(A.K * sizeof(ItemStats) / sizeof(int));

@@ -53,6 +53,8 @@ struct LzArgs {
     double ratio[3];           // a_d / f (-1 for that first dimension)
     int unit_ok;               // 1: the recurrence may run unscaled (||B|| / f <= 2^16)
     const double* diag;        // [n] (tau (V - c) - 2 sum_d a_d) / f
+    const float2* diag_df;     // [n] the same diagonal as double-float pairs (hi, lo)
+    int df;                    // 1: the recurrence from sweep 1 on in double-float on the FP32 pipe
     const double2* shift;      // [K] centred shifts s_k = z_k - tau c
     const double2* alpha;      // [K] weights
     double2 alpha0;
@@ -66,7 +68,8 @@ struct LzArgs {
     double2* out;              // LZ_STEP: psi_out; LZ_SOLVE: x [K][n]
     double2* tmp0;             // substep states (ping-pong)
     double2* tmp1;
-    double2* basis;            // [m + 2][n]: u_1 .. u_{m+2} (u_0 is the substep's input state)
+    double2* basis;            // [m + 2][n]: u_1 .. u_{m+2} (u_0 is the substep's input state); resident
+                               // tiles or df: each entry the double-float pairs (re_hi, re_lo, im_hi, im_lo)
     double2* wt;               // [2][n]: B u_j by parity of j
     float4* part;              // [2][grid]: per-CTA partial sums (||u_j||^2, Re u_j^H B u_j) as double-float pairs
     double2* rows;             // [m][K][3]: scaled rows of every pole's R for the back substitution
@@ -81,7 +84,8 @@ struct LzArgs {
     unsigned long long timeout_ns;
     unsigned long long* trace; // optional [1 + 2 cap]: (phase, ns) at every barrier
     int trace_cap;
-    unsigned long long* bytes; // [2]: algorithmic bytes and FP64 flops of the launch (added by the control CTA)
+    unsigned long long* bytes; // [3]: algorithmic bytes, FP64 flops and FP32-pipe operations of the launch
+                               // (added by the control CTA)
     int part_cap;              // slots per parity of part (>= ncta)
     int cta0, ncta;            // the CTAs of the launch that work for this problem
     long long* dbg;            // REXI_DEBUG builds: [4] first failed check (site, index, extent), count

@@ -36,12 +36,16 @@ def options(precision="mixed", restart=None, max_iters=2000, tol=0.0, inner_tol=
             shared_first_cycle=True, ortho="dcgs2", window=0):
     """Plan options (``rexi_options``).  ``restart`` is the GMRES restart length
     (default 30), or with ``ortho="lanczos"`` the largest Krylov dimension of a
-    substep's shared basis (default 256; there are no restarts)."""
+    substep's shared basis (default 256; there are no restarts).  ``precision``:
+    "mixed" (c64 Krylov work with FP64 refinement), "fp64", or "df64" (Lanczos
+    only: the recurrence in double-float pairs on the FP32 pipe)."""
     if restart is None:
         restart = 256 if ortho == "lanczos" else 30
     o = N.Options()
     N.load().rexi_options_default(C.byref(o))
-    o.precision = N.REXI_MIXED if precision == "mixed" else N.REXI_FP64
+    if precision not in ("mixed", "fp64", "df64"):
+        raise ValueError("precision must be 'mixed', 'fp64' or 'df64'")
+    o.precision = {"mixed": N.REXI_MIXED, "fp64": N.REXI_FP64, "df64": N.REXI_DF64}[precision]
     o.restart_m = int(restart)
     o.max_iters = int(max_iters)
     o.tol = float(tol)
@@ -82,7 +86,7 @@ def stats_dict(st, K):
     return {"status": st.status, "n_sub": st.n_sub, "max_iters_seen": st.max_iters_seen,
             "total_iters": st.total_iters, "total_cycles": st.total_cycles,
             "iters": list(st.iters[:K]), "cycles": list(st.cycles[:K]), "iters_sq": list(st.iters_sq[:K]),
-            "resid": list(st.resid[:K]), "bytes": st.bytes, "flops64": st.flops64}
+            "resid": list(st.resid[:K]), "bytes": st.bytes, "flops64": st.flops64, "ops32": st.ops32}
 
 
 class Plan:

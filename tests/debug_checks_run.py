@@ -4,7 +4,8 @@ parity cases and on every check site made to fail; prints one JSON line.
 Started by tests/test_gpu_debug_checks.py in a child process with REXI_DEBUG=1
 (the binding then loads the checked build).  Exit status 0 when:
 
-* every case runs with status 0, no failed check recorded, and the step (or
+* every case (the recurrence in FP64, and in double-float pairs on resident
+  and streamed tiles) runs with status 0, no failed check recorded, and the step (or
   each pole's solution) agrees with the oracle to the bounds of the release
   tests: steps to max(1e-10, 2 A tol), poles to 1e-10;
 * a batched launch of several of these problems (each on its share of the
@@ -47,6 +48,16 @@ STEP_CASES = [                              # grid, box, K, R1, dt, tiles (group
     ((20, 18, 14), 8.0, 16, 24.0, 0.3, (256, 2)),
     ((5, 1, 3), 6.0, 8, 8.0, 0.3, None),
 ]
+# the recurrence in double-float pairs (precision "df64"): resident and
+# streamed tiles, unequal and equal spacings
+DF_CASES = [
+    ((130, 101), 8.0, 16, 24.0, 0.5, None),
+    ((130, 101), 8.0, 16, 24.0, 0.5, (256, 1)),
+    ((64, 64), 8.0, 16, 24.0, 0.5, None),
+    ((5000,), 250.0, 16, 24.0, 1.0, (256, 1)),
+    ((20, 18, 14), 8.0, 16, 24.0, 0.3, (256, 2)),
+    ((12, 12, 12), 8.0, 16, 24.0, 0.3, None),
+]
 POLE_CASES = [((130, 101), 8.0, 16, 24.0, 0.5), ((20, 18, 14), 8.0, 16, 24.0, 0.3)]
 
 
@@ -56,8 +67,8 @@ def record(lp):
     return [int(v) for v in rec]
 
 
-def plan(g, V, dt, K, R1, tiles=None, **kw):
-    lp = library_plan(g, V, dt, K, R1, precision="fp64", ortho="lanczos", **kw)
+def plan(g, V, dt, K, R1, tiles=None, precision="fp64", **kw):
+    lp = library_plan(g, V, dt, K, R1, precision=precision, ortho="lanczos", **kw)
     if tiles is not None:
         autotune.apply(lp, {"pole_tile": 1024, "group_tile": tiles[0], "ctas_per_sm": tiles[1]})
     return lp
@@ -68,18 +79,19 @@ def main():
     lib = N.load()
     assert N.LIB_PATH == N.DEBUG_LIB_PATH and lib.rexi_debug_checks() == 1, "not the index-checked build"
     out = {"steps": [], "poles": [], "trips": []}
-    for n, box, K, R1, dt, tiles in STEP_CASES:
+    cases = [c + ("fp64",) for c in STEP_CASES] + [c + ("df64",) for c in DF_CASES]
+    for n, box, K, R1, dt, tiles, prec in cases:
         g, V, psi = wl.random_problem(91, n, box=box)
         orc = OraclePlan(g, V, dt, K, R1)
         tol = solve_tol(orc.A * orc.n_sub)
-        lp = plan(g, V, dt, K, R1, tiles, tol=tol)
+        lp = plan(g, V, dt, K, R1, tiles, precision=prec, tol=tol)
         res, st = lp.step(to_dev(psi), stats=True)
         rec = record(lp)
         ref, _ = ostep.step(V, orc.h, psi, orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0, tol=1e-14)
         err = relerr(res.cpu().numpy(), ref)
         bound = step_bound(orc.A * orc.n_sub, tol, "fp64")
-        out["steps"].append({"case": "x".join(map(str, n)), "tiles": tiles, "status": st["status"], "record": rec,
-                             "err": err, "bound": bound})
+        out["steps"].append({"case": "x".join(map(str, n)), "tiles": tiles, "precision": prec,
+                             "status": st["status"], "record": rec, "err": err, "bound": bound})
         assert st["status"] == 0 and rec == [0, 0, 0, 0], (n, tiles, st["status"], rec)
         assert err < bound, (n, tiles, err, bound)
     for n, box, K, R1, dt in POLE_CASES:
@@ -105,7 +117,7 @@ def main():
         g, V, psi = wl.random_problem(140 + i, n, box=box)
         orc = OraclePlan(g, V, dt, K, R1)
         tol = solve_tol(orc.A * orc.n_sub)
-        lp = plan(g, V, dt, K, R1, tol=tol)
+        lp = plan(g, V, dt, K, R1, precision="df64" if i % 2 else "fp64", tol=tol)
         bplans.append(lp)
         bpsis.append(to_dev(psi))
         bsingle.append(lp.step(to_dev(psi)).cpu().numpy())
@@ -116,25 +128,27 @@ def main():
         assert st_["status"] == 0 and rec == [0, 0, 0, 0], (i, st_["status"], rec)
         assert relerr(o.cpu().numpy(), bsingle[i]) < bbound[i], i
     out["batched"] = {"problems": len(bplans), "records": "clean"}
-    # every site made to fail: REXI_EBOUNDS with the site recorded, then recovery
+    # every site made to fail (FP64 and double-float recurrences): REXI_EBOUNDS
+    # with the site recorded, then recovery
     g, V, psi = wl.random_problem(94, (130, 101), box=8.0)
-    lp = plan(g, V, 0.5, 16, 24.0, tol=1e-13)
-    clean = lp.step(to_dev(psi)).cpu().numpy()
-    assert lp.step(to_dev(psi), stats=True)[1]["status"] == 0
-    for site in sorted(N.LZ_SITES):
-        N.check(lib.rexi_plan_debug_trip(lp.handle, site), "rexi_plan_debug_trip")
-        try:
-            lp.step(to_dev(psi), stats=True)
-            code = 0
-        except N.RexiError as e:
-            code = e.code
-        rec = record(lp)
-        N.check(lib.rexi_plan_debug_trip(lp.handle, 0), "rexi_plan_debug_trip")
-        again = lp.step(to_dev(psi)).cpu().numpy()
-        out["trips"].append({"site": site, "name": N.LZ_SITES[site], "status": code, "record": rec,
-                             "recovered": bool(np.array_equal(again, clean))})
-        assert code == N.REXI_EBOUNDS and rec[0] == site and rec[3] >= 1, (site, code, rec)
-        assert np.array_equal(again, clean), site
+    for prec in ("fp64", "df64"):
+        lp = plan(g, V, 0.5, 16, 24.0, precision=prec, tol=1e-13)
+        clean = lp.step(to_dev(psi)).cpu().numpy()
+        assert lp.step(to_dev(psi), stats=True)[1]["status"] == 0
+        for site in sorted(N.LZ_SITES):
+            N.check(lib.rexi_plan_debug_trip(lp.handle, site), "rexi_plan_debug_trip")
+            try:
+                lp.step(to_dev(psi), stats=True)
+                code = 0
+            except N.RexiError as e:
+                code = e.code
+            rec = record(lp)
+            N.check(lib.rexi_plan_debug_trip(lp.handle, 0), "rexi_plan_debug_trip")
+            again = lp.step(to_dev(psi)).cpu().numpy()
+            out["trips"].append({"precision": prec, "site": site, "name": N.LZ_SITES[site], "status": code,
+                                 "record": rec, "recovered": bool(np.array_equal(again, clean))})
+            assert code == N.REXI_EBOUNDS and rec[0] == site and rec[3] >= 1, (prec, site, code, rec)
+            assert np.array_equal(again, clean), (prec, site)
     # a site out of range and a plan of the item engine are refused
     assert lib.rexi_plan_debug_trip(lp.handle, len(N.LZ_SITES) + 1) == N.REXI_EINVAL
     le = library_plan(g, V, 0.5, 16, 24.0, precision="fp64")

@@ -97,20 +97,22 @@ def _oracle_2d_steps(cfg, orc, n):
     return _ORACLE_2D[:n]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
 @pytest.mark.parametrize("tiles", [None, {"pole_tile": 1024, "group_tile": 1024, "ctas_per_sm": 2},
                                    {"pole_tile": 1024, "group_tile": 2048, "ctas_per_sm": 1},
                                    {"pole_tile": 1024, "group_tile": 512, "ctas_per_sm": 1}])
-def test_2d_wells_512_lanczos_path_matches_oracle(tiles):
-    # The path the benchmark times: the shared-basis Lanczos kernel (FP64, one
-    # basis per substep for all 32 poles, the plan's own tolerance, at most 256
-    # columns per substep), under the default tile boxes and under tile settings
-    # the autotuner chooses between (two CTAs per SM with resident tiles, one CTA
-    # per SM, and boxes small enough that CTAs stream several tiles).  Two user
-    # steps, each element-wise against the oracle's step to the metric's 1e-6.
+def test_2d_wells_512_lanczos_path_matches_oracle(tiles, precision):
+    # The paths the benchmark times: the shared-basis Lanczos kernel (one basis
+    # per substep for all 32 poles, the plan's own tolerance, at most 256
+    # columns per substep; the recurrence in FP64 or in double-float pairs),
+    # under the default tile boxes and under tile settings the autotuner
+    # chooses between (two CTAs per SM with resident tiles, one CTA per SM, and
+    # boxes small enough that CTAs stream several tiles).  Two user steps, each
+    # element-wise against the oracle's step to the metric's 1e-6.
     from paper_1912_03312_gb300 import autotune
     cfg = wl.config_2d_wells()
     g = cfg["grid"]
-    lp = _plan(cfg, g, cfg["V"], cfg["K"], precision="fp64", ortho="lanczos")
+    lp = _plan(cfg, g, cfg["V"], cfg["K"], precision=precision, ortho="lanczos")
     if tiles is not None:
         autotune.apply(lp, tiles)
     info = lp.info()
@@ -123,7 +125,8 @@ def test_2d_wells_512_lanczos_path_matches_oracle(tiles):
         cur, st = lp.step(cur, stats=True)
         assert st["status"] == 0
         err = relerr(cur.cpu().numpy(), ref)
-        log_parity("2d_wells_512_lanczos[%s,step%d]" % (name, s), err, 1e-6, iters=st["total_iters"])
+        log_parity("2d_wells_512_lanczos[%s,%s,step%d]" % (precision, name, s), err, 1e-6,
+                   iters=st["total_iters"])
         assert err < 1e-6, err
 
 
@@ -139,17 +142,21 @@ def test_3d_coulomb_K64_is_refused():
 _ORACLE_3D = {}
 
 
-@pytest.mark.parametrize("precision,tol_pole", [("mixed", 1e-6), ("fp64", 1e-10), ("lanczos", 1e-10)])
+@pytest.mark.parametrize("precision,tol_pole", [("mixed", 1e-6), ("fp64", 1e-10), ("lanczos", 1e-10),
+                                                 ("lanczos_df64", 1e-10)])
 def test_3d_coulomb_128_sampled_poles_and_plane_wave(precision, tol_pole):
-    # "lanczos": the shared-basis Lanczos kernel (FP64) with streamed tiles
+    # "lanczos": the shared-basis Lanczos kernel (FP64) with streamed tiles;
+    # "lanczos_df64": the same with the recurrence in double-float pairs
     cfg = wl.config_3d_coulomb()
     g = cfg["grid"]
     K = 32
     R1 = 68.0
     orc = OraclePlan(g, cfg["V"], cfg["dt"], K, R1)
     tol = solve_tol(orc.A * orc.n_sub)
-    kw = dict(precision="fp64", ortho="lanczos") if precision == "lanczos" else dict(precision=precision,
-                                                                                      max_iters=20000)
+    if precision.startswith("lanczos"):
+        kw = dict(precision="df64" if precision.endswith("df64") else "fp64", ortho="lanczos")
+    else:
+        kw = dict(precision=precision, max_iters=20000)
     lp = _plan(cfg, g, cfg["V"], K, tol=tol, **kw)
     info = lp.info()
     assert info["R1"] == R1
@@ -230,15 +237,17 @@ def test_batched_64_problems():
         assert err < 1e-6
 
 
-def test_batched_64_problems_lanczos():
-    # the same 64 problems as Lanczos plans (FP64) in one launch of the
-    # Lanczos kernel, CTAs divided among the problems: against the single
-    # launches and, for the smallest two, the oracle
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_batched_64_problems_lanczos(precision):
+    # the same 64 problems as Lanczos plans (recurrence in FP64 or in
+    # double-float pairs) in one launch of the Lanczos kernel, CTAs divided
+    # among the problems: against the single launches and, for the smallest
+    # two, the oracle
     cfg = wl.config_batched()
     from paper_1912_03312_gb300 import step_batched
     probs = cfg["problems"]
     orcs = [OraclePlan(p["grid"], p["V"], cfg["dt"], cfg["K"], 68.0) for p in probs]
-    plans = [_plan(cfg, p["grid"], p["V"], cfg["K"], precision="fp64", ortho="lanczos") for p in probs]
+    plans = [_plan(cfg, p["grid"], p["V"], cfg["K"], precision=precision, ortho="lanczos") for p in probs]
     psis = [to_dev(p["psi0"]) for p in probs]
     singles = [pl.step(ps).cpu().numpy() for pl, ps in zip(plans, psis)]
     outs, sts = step_batched(plans, psis, stats=True)
@@ -252,7 +261,7 @@ def test_batched_64_problems_lanczos():
         ref, _ = ostep.step(p["V"], orc.h, p["psi0"], orc.tau, orc.n_sub, orc.z, orc.alpha, orc.alpha0,
                             tol=1e-14)
         err = relerr(outs[i].cpu().numpy(), ref)
-        log_parity("batched_64_problem_lanczos[%d]" % i, err, 1e-6)
+        log_parity("batched_64_problem_lanczos[%s,%d]" % (precision, i), err, 1e-6)
         assert err < 1e-6
 
 
