@@ -15,8 +15,10 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -105,24 +107,46 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
 // A wait also ends when another CTA has set the error word (it may have left
 // the kernel and never arrive).  The function returns false whenever the error
 // word is set, so every CTA leaves the kernel at its next barrier.
+// Bounded wait (thread 0 of a CTA) until the arrival count *bar reaches
+// target.  Each poll reads the sticky error word (relaxed) and then the count
+// (acquire): the acquire orders only later accesses, so both loads are in
+// flight together (one L2 round trip per poll), and the acquire load that
+// observes the final count synchronises with the release arrivals.  The wait
+// also ends when the error word is set; on expiry it sets it.  Returns whether
+// the error word was clear at the last poll.
+__device__ __forceinline__ bool wait_count(const unsigned* bar, unsigned target, int* err,
+                                           unsigned long long timeout_ns) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        const int e = ld_relaxed_s32(err);
+        const unsigned v = ld_acquire_u32(bar);
+        if (e != 0) return false;
+        if ((int)(v - target) >= 0) return true;
+        if (global_ns() - t0 > timeout_ns) {
+            atomicExch(err, kErrTimeout);
+            return false;
+        }
+    }
+}
+
+// Grid barrier of `count` co-resident CTAs: thread 0 arrives with a release
+// reduction on the arrival count (gen: barriers this CTA has passed) and
+// polls it; the CTA learns the outcome through shared memory, so no other
+// thread reads global memory for it.  Returns false when the launch must end
+// (an error or a timeout anywhere: a CTA that passed the barrier before the
+// error word was set stops at its next barrier).
 __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned count, unsigned& gen, int* err,
                                           unsigned long long timeout_ns) {
+    __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         gen += 1u;
         const unsigned target = gen * count;
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
-        const unsigned long long t0 = global_ns();
-        while ((int)(ld_acquire_u32(bar) - target) < 0) {
-            if (*(volatile int*)err != 0) break;
-            if (global_ns() - t0 > timeout_ns) {
-                atomicExch(err, kErrTimeout);
-                break;
-            }
-        }
+        ok = wait_count(bar, target, err, timeout_ns) ? 1 : 0;
     }
     __syncthreads();
-    return *(volatile int*)err == 0;
+    return ok != 0;
 }
 
 }  // namespace dev

@@ -121,6 +121,9 @@ struct LzSmem {
     double2 c0;              //                            coefficient of the input state
     double cw, ca, cb;       // the update as applied: u_j = cw w' - ca u_{j-1} - cb u_{j-2}
     float cwf, caf[2], cbf[2];   // double-float recurrence: cw, ca, cb as (hi, lo) pairs (j == 2: cb in FP64)
+    int cw_unit;             // cw == 1 (set with the coefficients: no FP64 compare per thread)
+    float2 ry, rz;           // double-float recurrence: the stencil ratios r_y, r_z as pairs, and
+    int uy, uz;              //   whether they are -1 (set once per launch)
     double n0;               // ||u_0||^2 of the substep
     double s_last, inv_s_last;   // scale s of the last update (u_{j-1} = s_{j-1} (...)), a power of two
     double hrho[2];          // rho = 1 / ||u|| of sweeps j-1, j-2 (from sweep 3 on: control CTA only)
@@ -945,12 +948,15 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
     double2* ujw = j >= 1 ? uvec_w(A, j) : nullptr;
     float nh = 0.f, nl = 0.f, ph = 0.f, pl = 0.f;
     double dn = 0.0, dp = 0.0;
-    // double-float mode: the update's coefficients and the stencil ratios as pairs
+    // double-float mode: the update's coefficients and the stencil ratios as
+    // pairs, prepared in shared memory (an FP64 instruction per thread would
+    // hold its SMSP's FP64 unit for about 64 cycles per warp)
     const bool df = A.df != 0;
+    const bool unit = sm.cw_unit != 0;
     const float cwf = sm.cwf;
     const float2 caf = make_float2(sm.caf[0], sm.caf[1]), cbf = make_float2(sm.cbf[0], sm.cbf[1]);
-    const float2 ry = df_from(A.ratio[1]), rz = df_from(A.ratio[2]);
-    const bool uy = A.ratio[1] == -1.0, uz = A.ratio[2] == -1.0;
+    const float2 ry = sm.ry, rz = sm.rz;
+    const bool uy = sm.uy != 0, uz = sm.uz != 0;
     if (A.resident) {
         if (lz_bid(A) - 1 < A.ntiles) {
             const Tile T = tile_of(A, lz_bid(A) - 1, hx, hy, hz);
@@ -971,7 +977,7 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
                 } else if (j >= 3) {
                     const float4* U1 = reinterpret_cast<const float4*>(st.R((j + 2) % 3));
                     const float4* U2 = reinterpret_cast<const float4*>(st.R((j + 1) % 3));
-                    if (cw == 1.0)
+                    if (unit)
                         phase_a_df<true, false>(A, T, Wf, U1, U2, Sf, nullptr, j, cwf, caf, cbf, cb, hx, hy, hz);
                     else
                         phase_a_df<false, false>(A, T, Wf, U1, U2, Sf, nullptr, j, cwf, caf, cbf, cb, hx, hy, hz);
@@ -991,7 +997,7 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
                 }
             } else if (fits) {
                 if (j >= 1) {
-                    if (cw == 1.0)
+                    if (unit)
                         phase_a<true>(A, T, st.W, st.R((j + 2) % 3), st.R((j + 1) % 3), S, nullptr, j, cw, ca, cb,
                                       hx, hy, hz);
                     else
@@ -1028,7 +1034,7 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
                 } else if (j >= 3) {
                     const float4* U1 = reinterpret_cast<const float4*>(st.U1);
                     const float4* U2 = reinterpret_cast<const float4*>(st.U2);
-                    if (cw == 1.0)
+                    if (unit)
                         phase_a_df<true, false>(A, T, Wf, U1, U2, Wf, ujf, j, cwf, caf, cbf, cb, hx, hy, hz);
                     else
                         phase_a_df<false, false>(A, T, Wf, U1, U2, Wf, ujf, j, cwf, caf, cbf, cb, hx, hy, hz);
@@ -1049,7 +1055,7 @@ __device__ void sweep(const LzArgs& A, LzSmem& sm, const Stage& st, const double
                 continue;
             }
             if (j >= 1) {
-                if (cw == 1.0)
+                if (unit)
                     phase_a<true>(A, T, st.W, st.U1, st.U2, st.W, ujw, j, cw, ca, cb, hx, hy, hz);
                 else
                     phase_a<false>(A, T, st.W, st.U1, st.U2, st.W, ujw, j, cw, ca, cb, hx, hy, hz);
@@ -1214,9 +1220,11 @@ __device__ void final_pass(const LzArgs& A, const LzSmem& sm, double up, const d
             for (int q = 0; q < kCh; ++q) {
                 if (!on[q]) continue;
                 if (kSplit) {
+                    // (the pairs widened by integer operations: the FP64 unit
+                    // takes only the multiply-adds)
                     const double2 a = cmul(sm.c0, u0[g[q]]);
-                    dst[g[q]] = make_double2(fma(up, (double)rh[q] + (double)rl[q], a.x),
-                                             fma(up, (double)ih[q] + (double)il[q], a.y));
+                    dst[g[q]] = make_double2(fma(up, f2d_int(rh[q]), fma(up, f2d_int(rl[q]), a.x)),
+                                             fma(up, f2d_int(ih[q]), fma(up, f2d_int(il[q]), a.y)));
                 } else {
                     dst[g[q]] = acc[q];
                 }
@@ -1428,6 +1436,13 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
             return;
     }
 #endif
+    if (threadIdx.x == 0) {
+        sm.ry = df_from(A.ratio[1]);
+        sm.rz = df_from(A.ratio[2]);
+        sm.uy = A.ratio[1] == -1.0 ? 1 : 0;
+        sm.uz = A.ratio[2] == -1.0 ? 1 : 0;
+        sm.cw_unit = 1;
+    }
     if (A.resident && !control) {
         if (has_tile) {
             setup_resident(A, sm, st, hx, hy, hz);
@@ -1598,6 +1613,7 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                         sm.inv_sf_last = __uint_as_float((unsigned)(127 - k) << 23);
                     }
                     sm.cw = sj;
+                    sm.cw_unit = sj == 1.0 ? 1 : 0;
                     sm.ca = ca;
                     sm.cb = cb;
                     sm.s_last = sj;
