@@ -38,7 +38,7 @@ from paper_1912_03312_gb300 import autotune  # noqa: E402
 
 STEP_CASES = [                              # grid, box, K, R1, dt, tiles (group_tile, ctas_per_sm)
     ((300,), 8.0, 16, 24.0, 1.0, None),
-    ((5000,), 250.0, 16, 24.0, 1.0, (256, 1)),      # several tiles per CTA (streamed)
+    ((60000,), 3000.0, 16, 24.0, 1.0, (256, 1)),    # several tiles per CTA (streamed)
     ((130, 101), 8.0, 16, 24.0, 0.5, None),
     ((130, 101), 8.0, 16, 24.0, 0.5, (256, 1)),
     ((96, 80), 8.0, 32, 68.0, 0.5, None),
@@ -52,10 +52,10 @@ STEP_CASES = [                              # grid, box, K, R1, dt, tiles (group
 # streamed tiles, unequal and equal spacings
 DF_CASES = [
     ((130, 101), 8.0, 16, 24.0, 0.5, None),
-    ((130, 101), 8.0, 16, 24.0, 0.5, (256, 1)),
+    ((250, 200), 15.0, 16, 24.0, 0.5, (256, 1)),    # streamed (more tiles than CTAs)
     ((64, 64), 8.0, 16, 24.0, 0.5, None),
-    ((5000,), 250.0, 16, 24.0, 1.0, (256, 1)),
-    ((20, 18, 14), 8.0, 16, 24.0, 0.3, (256, 2)),
+    ((60000,), 3000.0, 16, 24.0, 1.0, (256, 1)),    # streamed
+    ((40, 36, 30), 16.0, 16, 24.0, 0.3, (256, 1)),  # streamed
     ((12, 12, 12), 8.0, 16, 24.0, 0.3, None),
 ]
 POLE_CASES = [((130, 101), 8.0, 16, 24.0, 0.5), ((20, 18, 14), 8.0, 16, 24.0, 0.3)]

@@ -45,29 +45,34 @@ def built():
 
 def df_plan(g, V, dt, K, R1, tiles=None, **kw):
     lp = library_plan(g, V, dt, K, R1, ortho="lanczos", precision=kw.pop("precision", "df64"), **kw)
+    if tiles == STREAMED:
+        # more tiles than tile CTAs: every CTA streams several tiles per sweep
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert int(np.prod(g["n"])) > STREAMED[0] * (sms * STREAMED[1] - 1)
     if tiles is not None:
         from paper_1912_03312_gb300 import autotune
         autotune.apply(lp, {"pole_tile": 1024, "group_tile": tiles[0], "ctas_per_sm": tiles[1]})
     return lp
 
 
-STREAMED = (256, 1)        # tile boxes of at most 256 points, one CTA per SM: several tiles per CTA
+STREAMED = (256, 1)        # tile boxes of at most 256 points, one CTA per SM: several tiles per CTA on
+                           # grids above 256 x (SMs - 1) points (asserted)
 
 CASES = [                                              # grid, box, K, R1, dt, tiles
     ((300,), 8.0, 16, 24.0, 1.0, None),                # 1D, many substeps
     ((5000,), 250.0, 16, 24.0, 1.0, None),             # 1D, ragged tiles
-    ((5000,), 250.0, 16, 24.0, 1.0, STREAMED),
+    ((60000,), 3000.0, 16, 24.0, 1.0, STREAMED),       # the same spacing, streamed
     ((37,), 6.0, 8, 8.0, 0.3, None),                   # 1D, tiny
     ((130, 101), 8.0, 16, 24.0, 0.5, None),            # 2D, unequal spacings, ragged both ways
-    ((130, 101), 8.0, 16, 24.0, 0.5, STREAMED),
+    ((250, 200), 15.0, 16, 24.0, 0.5, STREAMED),        # unequal spacings, streamed
     ((96, 80), 8.0, 32, 68.0, 0.5, None),              # 2D, K = 32
     ((64, 64), 8.0, 16, 24.0, 0.5, None),              # 2D, equal spacings (unit ratios)
-    ((64, 64), 8.0, 16, 24.0, 0.5, STREAMED),
+    ((224, 224), 28.0, 16, 24.0, 0.5, STREAMED),        # equal spacings, streamed
     ((2, 17), 6.0, 8, 8.0, 0.3, None),                 # a dimension of length 2
     ((1, 40), 6.0, 8, 8.0, 0.3, None),                 # x of length 1: y is the first stencil dimension
     ((16, 12), 8.0, 16, 24.0, 0.5, None),              # tiles wrap on both sides
     ((20, 18, 14), 8.0, 16, 24.0, 0.3, None),          # 3D
-    ((20, 18, 14), 8.0, 16, 24.0, 0.3, STREAMED),
+    ((40, 36, 30), 16.0, 16, 24.0, 0.3, STREAMED),      # 3D, streamed
     ((12, 12, 12), 8.0, 16, 24.0, 0.3, None),          # 3D, equal spacings
     ((5, 1, 3), 6.0, 8, 8.0, 0.3, None),               # y of length 1
 ]
@@ -132,7 +137,8 @@ def test_df64_step_is_scale_invariant(scale_exp, tiles):
     # sweep 0 runs in FP64 on the caller's state and s_1 brings u_1 to unit
     # scale before it is rounded to pairs, so 2^e psi steps to 2^e times the
     # step of psi although 2^e psi is far outside the FP32 range
-    g, V, psi = wl.random_problem(95, (130, 101), box=8.0)
+    n, box = ((250, 200), 15.0) if tiles == STREAMED else ((130, 101), 8.0)
+    g, V, psi = wl.random_problem(95, n, box=box)
     K, R1, dt = 16, 24.0, 0.5
     lp = df_plan(g, V, dt, K, R1, tiles, tol=1e-13)
     ref, st = lp.step(to_dev(psi), stats=True)
