@@ -226,9 +226,10 @@ def engine_traffic(kernel_src_hash, key):
     try:
         with open(p) as f:
             d = json.load(f)
-        if (d.get("engine_cu_sha256") == kernel_src_hash and d.get("workload") == WORKLOAD and
-                d.get("path") == key):
-            return float(d["dram_bytes_per_launch"])
+        for r in d.get("records", [d]):
+            if (r.get("engine_cu_sha256") == kernel_src_hash and r.get("workload") == WORKLOAD and
+                    r.get("path") == key):
+                return float(r["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
