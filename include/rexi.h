@@ -122,7 +122,8 @@ typedef struct {
                               that has not met its bound by then fails with REXI_ENOCONV.  Each
                               pole solves its least-squares problem on the shared basis (GMRES
                               with the columns orthonormal only locally, so the stop uses the
-                              bound sqrt(k+1) |g_{k+1}| as with a window) and the pole sum is one
+                              bound |g_{k+1}| L_k >= ||r_k||, L_k = c_k + |s_k| L_{k-1} <= sqrt(k+1)
+                              from the rotations) and the pole sum is one
                               pass over the basis.  rexi_step and rexi_solve_poles run on this
                               path; rexi_step_backward runs on the item engine (shared first
                               cycle, window 2, restart min(restart_m, 64)), allocated at its

@@ -35,9 +35,10 @@
 // Q_k (Sec. 5 of the paper: the Krylov spaces of shifted systems coincide);
 // pole k minimises ||beta e_1 - (T_k - s_k [I; 0]) y|| by its own Givens
 // rotations (GMRES on the shared basis).  The columns are unit vectors but
-// orthogonal only locally, so the stop uses the bound ||r_k|| <=
-// ||Q_{k+1}|| |g_{k+1}| <= sqrt(k+1) |g_{k+1}| (times a 1e-4 margin for the
-// computed norms).
+// orthogonal only locally, so the stop uses the bound ||r_k|| = ||Q_{k+1} z||
+// <= ||z||_1 = |g_{k+1}| L_k, z the residual's coordinates (the rotations
+// applied backwards to g_{k+1} e_{k+1}), L_k = c_k + |s_k| L_{k-1} <= sqrt(k+1)
+// (times a 1e-4 margin for the computed norms).
 //
 // CTA 0 is the control CTA: it owns no tiles, runs the per-pole Givens
 // recurrences one step behind the sweeps, stops the iteration once every pole
@@ -185,12 +186,15 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 __device__ __forceinline__ double2 csc(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 
 // Complex Givens rotation G = [c s; -conj(s) c] (c real) with G [x; h] = [r; 0]
-// for complex x and real h >= 0; inv = 1 / r (0 when the column vanishes).
-__device__ __forceinline__ void givens(double2 x, double h, double* c, double2* s, double2* r, double2* inv) {
+// for complex x and real h >= 0; sabs = |s|; inv = 1 / r (0 when the column
+// vanishes).
+__device__ __forceinline__ void givens(double2 x, double h, double* c, double2* s, double* sabs, double2* r,
+                                       double2* inv) {
     const double xx = x.x * x.x + x.y * x.y;
     if (h == 0.0) {
         *c = 1.0;
         *s = make_double2(0.0, 0.0);
+        *sabs = 0.0;
         *r = x;
         const double rx = xx > 0.0 ? rsqrt(xx) : 0.0;
         *inv = make_double2(x.x * rx * rx, -x.y * rx * rx);
@@ -199,6 +203,7 @@ __device__ __forceinline__ void givens(double2 x, double h, double* c, double2* 
     if (xx == 0.0) {
         *c = 0.0;
         *s = make_double2(1.0, 0.0);
+        *sabs = 1.0;
         *r = make_double2(h, 0.0);
         const double rh = rsqrt(h * h);
         *inv = make_double2(rh, 0.0);
@@ -209,6 +214,7 @@ __device__ __forceinline__ void givens(double2 x, double h, double* c, double2* 
     const double2 ph = make_double2(x.x * rnx, x.y * rnx);
     *c = xx * rnx * rnu;
     *s = csc(ph, h * rnu);
+    *sabs = fabs(h) * rnu;
     *r = csc(ph, nu2 * rnu);
     *inv = make_double2(ph.x * rnu, -ph.y * rnu);
 }
@@ -1243,7 +1249,8 @@ struct PoleState {
     double2 shift;
     int kk;                  // columns used (set when the pole stops)
     int done;                // 1 converged, 2 failed
-    double bound;            // relative residual bound at the stop
+    double bound;            // while the pole runs: L = ||z||_1 / |g| of the residual's coordinates
+                             // (see pole_column); at the stop: the relative residual bound
 };
 
 // Row r of pole k's R, scaled by 1 / R(r, r), and its right-hand side entry:
@@ -1283,9 +1290,9 @@ __device__ bool pole_column(const LzArgs& A, PoleState& P, int k, int c, double 
         const double2 cs1 = make_double2(-P.s1.x, P.s1.y);    // -conj(s1)
         xc = cfma(csc(dg, P.c1), cs1, xm1);
     }
-    double c0;
+    double c0, sa0;
     double2 s0, rcc, inv;
-    givens(xc, lo, &c0, &s0, &rcc, &inv);
+    givens(xc, lo, &c0, &s0, &sa0, &rcc, &inv);
     const double2 gc = csc(P.g, c0);
     const double2 gn = cmul(make_double2(-s0.x, s0.y), P.g);   // -conj(s0) g
     if (c >= 2) put_row(A, c - 2, k, P.g2, P.inv2, P.r12, r0, srows, srows_cap);
@@ -1300,15 +1307,23 @@ __device__ bool pole_column(const LzArgs& A, PoleState& P, int k, int c, double 
     P.c1 = c0;
     P.s1 = s0;
     P.g = gn;
+    // The residual is Q_{c+2} z with z = G_0^H ... G_c^H (g_{c+1} e_{c+1}):
+    // |z_{c+1}| = |g| c_c, |z_c| = |g| |s_c| c_{c-1}, |z_{c-1}| = |g| |s_c s_{c-1}|
+    // c_{c-2}, ..., |z_0| = |g| |s_c ... s_0|, so with unit columns ||r|| <=
+    // ||z||_1 = |g| L, L = c_c + |s_c| L_prev (L = 1 before column 0).  L never
+    // exceeds sqrt(c + 2) (the bound for columns of unit norm without
+    // orthogonality) and stays near c / (1 - |s|) while the pole converges.
+    const double L = fma(sa0, P.bound, c0);
+    P.bound = L;
     const double gg = gn.x * gn.x + gn.y * gn.y;
-    if (gg * (double)(c + 2) <= tol_abs2) {
+    if (gg * (L * L) <= tol_abs2) {
         // stop with c + 1 columns: rows c-1 and c complete with zeros
         const double2 z = make_double2(0.0, 0.0);
         if (c >= 1) put_row(A, c - 1, k, P.g2, P.inv2, P.r12, z, srows, srows_cap);
         put_row(A, c, k, P.g1, P.inv1, z, z, srows, srows_cap);
         P.kk = c + 1;
         P.done = 1;
-        P.bound = sqrt(gg * (double)(c + 2));
+        P.bound = sqrt(gg) * L;
         return true;
     }
     return false;
@@ -1464,7 +1479,7 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
             P.shift = A.shift[threadIdx.x];
             P.kk = 0;
             P.done = 0;
-            P.bound = 0.0;
+            P.bound = 1.0;                       // L before the first column
         }
         if (threadIdx.x == 0) {
             sm.n0 = 0.0;
@@ -1660,6 +1675,7 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                     }
                     if (threadIdx.x < A.K && !(n0 > 0.0)) P.done = n0 == 0.0 ? 1 : 2;
                     if (threadIdx.x < A.K && !(n0 <= 1.0e300)) P.done = 2;
+                    if (threadIdx.x < A.K && P.done != 0) P.bound = 0.0;   // no columns: no residual bound
                 } else {
                     const int c = j - 2;
                     // T[c-1, c] = T[c, c-1] and T[c+1, c], from the last two reductions
@@ -1673,7 +1689,7 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                             P.done = 2;
                             P.kk = c + 1;
                             const double gg = P.g.x * P.g.x + P.g.y * P.g.y;
-                            P.bound = sqrt(gg * (double)(c + 2));
+                            P.bound = sqrt(gg) * P.bound;
                             const double2 z = make_double2(0.0, 0.0);
                             if (c >= 1) put_row(A, c - 1, threadIdx.x, P.g2, P.inv2, P.r12, z, dyn, stage_rows);
                             put_row(A, c, threadIdx.x, P.g1, P.inv1, z, z, dyn, stage_rows);
