@@ -1525,6 +1525,8 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                     // control CTA takes T from the values actually used), so the
                     // step's scalar path costs two FP64 instructions.
                     double sj, inv_sj, ca, cb;
+                    float rinv_h = 0.f, rinv_l = 0.f;          // 1 / n_{j-1} in double-float (j >= 3)
+                    bool have_rinv = false;
                     if (j <= 2) {
                         // FP64: sweep 0's sums may lie outside the FP32 range, and
                         // beta at j = 2 divides by n_0
@@ -1570,25 +1572,31 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                             if (LZ_OK(j - 1, A.m + 2, LZ_SITE_Y)) A.rho[j - 1] = rho;
                         }
                     } else {
-                        float sf = 1.0f;
+                        float sf = 1.0f, inv_sf = 1.0f;
                         sj = inv_sj = 1.0;
                         if (!A.unit_ok || !(q.x >= 0x1p-30f && q.x <= 0x1p30f)) {
                             const int be = (int)((__float_as_uint(q.x) >> 23) & 0xFFu);
                             const int k = -((be - 127) >> 1);
                             sf = __uint_as_float((unsigned)(127 + k) << 23);
+                            inv_sf = __uint_as_float((unsigned)(127 - k) << 23);
                             sj = __hiloint2double((1023 + k) << 20, 0);
                             inv_sj = __hiloint2double((1023 - k) << 20, 0);
                         }
-                        float rh = 0.f, rl = 0.f;
-                        if (q.x > 0.f) df_recip(q.x, q.y, rh, rl);
+                        if (q.x > 0.f) df_recip(q.x, q.y, rinv_h, rinv_l);
+                        have_rinv = true;
                         float ah, al, bh, bl;
-                        df_mul(q.z, q.w, rh, rl, ah, al);                     // alpha = p / n
+                        df_mul(q.z, q.w, rinv_h, rinv_l, ah, al);             // alpha = p / n
                         df_mul(q.x, q.y, sm.rprev_h, sm.rprev_l, bh, bl);     // n / n_{j-2}
                         const float sb = __fmul_rn(sf, sm.inv_sf_last);        // s_j / s_{j-1}: a power of two
                         const float cah = __fmul_rn(ah, sf), cal = __fmul_rn(al, sf);
                         const float cbh = __fmul_rn(bh, sb), cbl = __fmul_rn(bl, sb);
-                        ca = f2d_int(cah) + f2d_int(cal);
-                        cb = f2d_int(cbh) + f2d_int(cbl);
+                        // as doubles only where they are used: the FP64 update and the
+                        // control CTA's columns of T (two FP64 instructions)
+                        ca = cb = 0.0;
+                        if (!A.df || control) {
+                            ca = f2d_int(cah) + f2d_int(cal);
+                            cb = f2d_int(cbh) + f2d_int(cbl);
+                        }
                         // (the double-float update applies these pairs exactly)
                         sm.cwf = sf;
                         sm.caf[0] = cah;
@@ -1613,14 +1621,13 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                             sm.hn[0] = n;
                             if (LZ_OK(j - 1, A.m + 2, LZ_SITE_Y)) A.rho[j - 1] = rho;
                         }
-                        sm.inv_sf_last = 1.0f / sf;
+                        sm.inv_sf_last = inv_sf;
                     }
                     if (j >= 2) {
                         // 1 / n_{j-1} for the next step's beta (n_{j-1} is in the FP32 range)
-                        float rh = 0.f, rl = 0.f;
-                        if (q.x > 0.f) df_recip(q.x, q.y, rh, rl);
-                        sm.rprev_h = rh;
-                        sm.rprev_l = rl;
+                        if (!have_rinv && q.x > 0.f) df_recip(q.x, q.y, rinv_h, rinv_l);
+                        sm.rprev_h = rinv_h;
+                        sm.rprev_l = rinv_l;
                     }
                     if (j <= 2) {
                         // (only j = 2's value is used, and s_2 is within the FP32 range)
