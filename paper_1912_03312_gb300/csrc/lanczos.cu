@@ -1334,8 +1334,8 @@ __device__ bool pole_column(const LzArgs& A, PoleState& P, int k, int c, double 
 // J <= stage_rows the rows are already in shared memory (written there as they
 // were formed) and y_k replaces each row's first entry; otherwise the rows are
 // staged from global memory in chunks and y_k goes through global memory.
-__device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int stage_rows, PoleState& P, int J,
-                               int s, double bnorm) {
+__device__ __noinline__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int stage_rows,
+                                            PoleState& P, int J, int s, double bnorm) {
     const int K = A.K;
     const int k = threadIdx.x;
     const bool inplace = J <= stage_rows;
@@ -1492,6 +1492,7 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
         double tol_abs2 = 0.0, bnorm = 0.0;
         double upd_fl = 0.0;                           // FP64 flops per point of the updates (control CTA)
         int J = -1, sweeps = 0;
+        bool finished = false;                         // control CTA: y_k and the coefficients formed
         for (int j = 0;; ++j) {
             // as the barrier opens: the partials and the stop word, then the
             // copies of this CTA's first tile
@@ -1704,14 +1705,21 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                         active = P.done == 0;
                     }
                     const int still = __syncthreads_count(active);
-                    if (still == 0 && threadIdx.x == 0) __stcg(A.stop + s, c + 1);
+                    if (still == 0) {
+                        if (threadIdx.x == 0) __stcg(A.stop + s, c + 1);
+                        // every pole has stopped: back-substitute now, while the tile
+                        // CTAs run the sweep whose result is not needed (the barrier
+                        // below waits for it; the one after the loop then opens at once)
+                        control_finish(A, sm, dyn, stage_rows, P, c + 1, s, bnorm);
+                        finished = true;
+                    }
                 }
             }
             if (!grid_sync(A.bar, (unsigned)A.ncta, bar_gen, A.err, A.timeout_ns)) return;
             trace_mark(A, TR_LZ_SWEEP, &tcount);
         }
-        // y_k and the coefficients of the final pass
-        if (control) control_finish(A, sm, dyn, stage_rows, P, J, s, bnorm);
+        // y_k and the coefficients of the final pass (unless formed as the poles stopped)
+        if (control && !finished) control_finish(A, sm, dyn, stage_rows, P, J, s, bnorm);
         if (!grid_sync(A.bar, (unsigned)A.ncta, bar_gen, A.err, A.timeout_ns)) return;
         trace_mark(A, TR_LZ_SOLVE, &tcount);
         if (control && threadIdx.x == 0) {
