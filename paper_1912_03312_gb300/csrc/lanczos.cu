@@ -1329,13 +1329,13 @@ __device__ bool pole_column(const LzArgs& A, PoleState& P, int k, int c, double 
     return false;
 }
 
-// Control CTA after the sweeps of a substep stopped at J columns: y_k =
-// R_k^{-1} g_k for every pole, then the coefficients of the final pass.  With
+// Control CTA, as soon as every pole of the substep has stopped (J columns):
+// y_k = R_k^{-1} g_k for every pole, then the coefficients of the final pass.  With
 // J <= stage_rows the rows are already in shared memory (written there as they
 // were formed) and y_k replaces each row's first entry; otherwise the rows are
 // staged from global memory in chunks and y_k goes through global memory.
-__device__ __noinline__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int stage_rows,
-                                            PoleState& P, int J, int s, double bnorm) {
+__device__ void control_finish(const LzArgs& A, LzSmem& sm, double2* stage, int stage_rows, PoleState& P, int J,
+                               int s, double bnorm) {
     const int K = A.K;
     const int k = threadIdx.x;
     const bool inplace = J <= stage_rows;
@@ -1492,7 +1492,6 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
         double tol_abs2 = 0.0, bnorm = 0.0;
         double upd_fl = 0.0;                           // FP64 flops per point of the updates (control CTA)
         int J = -1, sweeps = 0;
-        bool finished = false;                         // control CTA: y_k and the coefficients formed
         for (int j = 0;; ++j) {
             // as the barrier opens: the partials and the stop word, then the
             // copies of this CTA's first tile
@@ -1669,6 +1668,7 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
             } else if (j >= 1) {
                 // the control CTA works one column behind: column c = j - 2 is
                 // complete once the norm of u_{j-1} (its subdiagonal) is known
+                int stop_now = -1;                     // the substep's column count, once known
                 if (j == 1) {
                     const double n0 = sm.n0;
                     // the poles solve for psi / ||psi|| (right-hand side e_1, for
@@ -1677,10 +1677,8 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                     const double ta = A.tol / 1.0001;
                     tol_abs2 = ta * ta;
                     if (threadIdx.x < A.K) P.g = make_double2(1.0, 0.0);
-                    if (threadIdx.x == 0 && !(n0 > 0.0 && n0 <= 1.0e300)) {
-                        // a zero state needs no columns; a non-finite one fails every pole
-                        __stcg(A.stop + s, 0);
-                    }
+                    // a zero state needs no columns; a non-finite one fails every pole
+                    if (!(n0 > 0.0 && n0 <= 1.0e300)) stop_now = 0;
                     if (threadIdx.x < A.K && !(n0 > 0.0)) P.done = n0 == 0.0 ? 1 : 2;
                     if (threadIdx.x < A.K && !(n0 <= 1.0e300)) P.done = 2;
                     if (threadIdx.x < A.K && P.done != 0) P.bound = 0.0;   // no columns: no residual bound
@@ -1705,21 +1703,22 @@ __device__ __forceinline__ void lanczos_body(const LzArgs& A, double2* dyn, LzSm
                         active = P.done == 0;
                     }
                     const int still = __syncthreads_count(active);
-                    if (still == 0) {
-                        if (threadIdx.x == 0) __stcg(A.stop + s, c + 1);
-                        // every pole has stopped: back-substitute now, while the tile
-                        // CTAs run the sweep whose result is not needed (the barrier
-                        // below waits for it; the one after the loop then opens at once)
-                        control_finish(A, sm, dyn, stage_rows, P, c + 1, s, bnorm);
-                        finished = true;
-                    }
+                    if (still == 0) stop_now = c + 1;
+                }
+                if (stop_now >= 0) {
+                    // every pole has stopped: publish the column count and form
+                    // y_k and the coefficients of the final pass now, while the
+                    // tile CTAs run the sweep whose result is not needed (the
+                    // barrier below waits for it; the one after the loop then
+                    // opens at once)
+                    if (threadIdx.x == 0) __stcg(A.stop + s, stop_now);
+                    control_finish(A, sm, dyn, stage_rows, P, stop_now, s, bnorm);
                 }
             }
             if (!grid_sync(A.bar, (unsigned)A.ncta, bar_gen, A.err, A.timeout_ns)) return;
             trace_mark(A, TR_LZ_SWEEP, &tcount);
         }
-        // y_k and the coefficients of the final pass (unless formed as the poles stopped)
-        if (control && !finished) control_finish(A, sm, dyn, stage_rows, P, J, s, bnorm);
+        // (the control CTA formed y_k and the coefficients as the poles stopped)
         if (!grid_sync(A.bar, (unsigned)A.ncta, bar_gen, A.err, A.timeout_ns)) return;
         trace_mark(A, TR_LZ_SOLVE, &tcount);
         if (control && threadIdx.x == 0) {
