@@ -137,10 +137,22 @@ def test_argument_validation_before_device(lib):
     o.window = 3
     o.ortho = 0                               # windows are a delayed-CGS2 option
     assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
-    # the Lanczos path (ortho = 2): FP64 only, no window, Krylov dimension <= REXI_MAX_KRYLOV
+    # the double-float recurrence is the Lanczos kernel's: the item engine refuses it
+    o.window = 0
+    o.restart_m = 30
+    for ortho in (0, 1):
+        o.ortho = ortho
+        o.precision = N.REXI_DF64
+        assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    o.precision = 7                           # not a precision form
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    # the Lanczos path (ortho = 2): FP64 or double-float, no window, Krylov dimension <= REXI_MAX_KRYLOV
     o.ortho = 2
     o.window = 0
     o.precision = N.REXI_MIXED
+    assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
+    o.precision = N.REXI_DF64
+    o.window = 2
     assert lib.rexi_plan_create(C.byref(h), C.byref(g), V, 0.1, 4, C.byref(o)) == N.REXI_EINVAL
     o.precision = N.REXI_FP64
     o.window = 2
@@ -207,3 +219,19 @@ def test_grid_size_overflow_is_rejected_before_any_device_call(lib):
     o.tol = 1e-12
     o.inner_tol = -1.0
     assert call(g, C.byref(o)) == N.REXI_EINVAL
+    o.inner_tol = 1e-5
+    o.precision = N.REXI_DF64                   # the allocation-free entry point runs the item engine
+    assert call(g, C.byref(o)) == N.REXI_EINVAL
+
+
+def test_binding_precision_names():
+    # the Python option names map onto the header's precision forms; an
+    # unknown name is refused before any call
+    from paper_1912_03312_gb300 import _native as N
+    from paper_1912_03312_gb300.rexi import options
+    assert (N.REXI_FP64, N.REXI_MIXED, N.REXI_DF64) == (0, 1, 2)
+    assert options(precision="fp64").precision == N.REXI_FP64
+    assert options(precision="mixed").precision == N.REXI_MIXED
+    assert options(precision="df64", ortho="lanczos").precision == N.REXI_DF64
+    with pytest.raises(ValueError):
+        options(precision="fp32")
