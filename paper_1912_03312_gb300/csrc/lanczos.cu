@@ -16,7 +16,9 @@
 // copies issued as soon as the barrier opens, while the CTA reduces the
 // partials; the inner products are compensated sums of FP32 hi/lo pieces
 // (about 1e-13 relative; the FP64 pipe stays free for the recurrence; sweep 0,
-// on the caller's state of any scale, sums in FP64).  Every CTA reduces the
+// on the caller's state of any scale, sums in FP64).  In the double-float mode
+// (LzArgs::df) the recurrence itself, from u_1 on, runs in pairs of floats on
+// the FP32 pipe as well (the section on that mode below).  Every CTA reduces the
 // partials in FP64 in the same fixed order and derives the same coefficients:
 // with n_j = ||u_j||^2, alpha_j = Re u_j^H w'_j / n_j (f alpha_j is the
 // Rayleigh quotient of B, real because B is real symmetric) and beta_j = n_j /
@@ -29,9 +31,9 @@
 // exactly for the coefficients used (whatever the accuracy of the inner
 // products that chose them), so B Q_k = Q_{k+1} T_k holds to the rounding of
 // the recurrence (FP64, or double-float pairs on the FP32 pipe in the
-// double-float mode) with T_k tridiagonal.  The scale s_j is one (two fused multiply-adds per
-// component) while n stays within [2^-30, 2^30], else the power of two that
-// brings u_j back to unit scale.  The shifted systems (B - s_k I) x = psi share
+// double-float mode) with T_k tridiagonal.  The scale s_j is one (two fused
+// multiply-adds per component) while n stays within [2^-30, 2^30], else the
+// power of two that brings u_j back to unit scale.  The shifted systems (B - s_k I) x = psi share
 // Q_k (Sec. 5 of the paper: the Krylov spaces of shifted systems coincide);
 // pole k minimises ||beta e_1 - (T_k - s_k [I; 0]) y|| by its own Givens
 // rotations (GMRES on the shared basis).  The columns are unit vectors but
@@ -41,10 +43,11 @@
 // (times a 1e-4 margin for the computed norms).
 //
 // CTA 0 is the control CTA: it owns no tiles, runs the per-pole Givens
-// recurrences one step behind the sweeps, stops the iteration once every pole
-// has met its bound, and back-substitutes y_k.  The result of the evaluation
-// is psi' = alpha_0 psi + sum_k alpha_k Q y_k = alpha_0 psi + Q (sum_k alpha_k
-// y_k): one pass over the basis (the pole sum of Eq. (5)).
+// recurrences one step behind the sweeps, and once every pole has met its
+// bound stops the iteration and back-substitutes y_k in the same step (while
+// the tile CTAs run the sweep whose result is not needed).  The result of the
+// evaluation is psi' = alpha_0 psi + sum_k alpha_k Q y_k = alpha_0 psi +
+// Q (sum_k alpha_k y_k): one pass over the basis (the pole sum of Eq. (5)).
 #include <cuda_runtime.h>
 
 #include <algorithm>
